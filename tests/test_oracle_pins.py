@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test names the passage it follows.  None of them re-types the oracle's own formula: they
+use closed forms, invariants, brute force, finite differences or limits.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+from oracle import oracle as O
+from paper_2501_00923_gb300 import workloads as W
+
+
+def _problem(mesh, grid, Kn=1.0, Ma=0.5, Tw=1.0, aoa=0.0, direction=(1.0, 0.0)):
+    return O.Problem(mesh.nodes, grid.vx, grid.vy, grid.w, Kn, Ma, Tw, aoa, direction)
+
+
+# ----------------------------------------------------------------------------- Sec. 2.1 / 2.2
+def test_maxwellian_moments_closed_form():
+    """Moments of the reduced Maxwellian (Eq. maxwell_reduce) through the moment tensor Psi
+    (Eq. macint_reduce): W = (rho, rho u, rho(|u|^2/2 + 3/2 T)) for a monatomic gas, on a wide,
+    fine grid where the trapezoid rule is spectrally accurate."""
+    grid = W.velocity_grid(96, 13.0 / W.A_INF)
+    mesh = W.omesh(8, 4)
+    for Ma, aoa in [(0.0, 0.0), (0.8, 0.3), (2.0, -0.2)]:
+        pr = _problem(mesh, grid, Ma=Ma, aoa=aoa)
+        Wm = pr.moments(pr.freestream())
+        u = Ma * W.A_INF * np.array([math.cos(aoa), math.sin(aoa)])
+        expect = np.array([1.0, u[0], u[1], 0.5 * u @ u + 1.5])
+        assert np.abs(Wm - expect).max() < 1e-12 * np.abs(expect).max()
+
+
+def test_collision_conserves_mass_momentum_energy():
+    """int Psi (g - f)/tau dXi = 0 (Sec. 2.1, conservation of the collision term) for an
+    arbitrary f, on a grid wide and fine enough that the quadrature is exact to round-off."""
+    grid = W.velocity_grid(64, 10.0 / W.A_INF)
+    mesh = W.omesh(8, 4)
+    pr = _problem(mesh, grid)
+    rng = np.random.default_rng(1)
+    f = W.random_state(pr.ncell, grid, rng, noise=0.2)
+    Q = pr.collision(f)
+    dW = np.einsum("k,ckq,qmk->cm", grid.w, Q,
+                   np.stack([np.stack([np.ones(grid.nv), grid.vx, grid.vy,
+                                       0.5 * (grid.vx**2 + grid.vy**2)]),
+                             np.stack([np.zeros(grid.nv)] * 3 + [np.ones(grid.nv)])]))
+    scale = np.abs(pr.moments(f)).max()
+    assert np.abs(dW).max() < 1e-12 * scale
+
+
+def test_collision_not_conservative_if_gamma_wrong():
+    """Guard of the previous pin: the same check fails for a Maxwellian whose temperature ignores
+    the v3 energy carried by f2 (gamma = 2 instead of 5/3), so the pin can see that mistake."""
+    grid = W.velocity_grid(64, 10.0 / W.A_INF)
+    rng = np.random.default_rng(2)
+    mesh = W.omesh(4, 2)
+    pr = _problem(mesh, grid)
+    f = W.random_state(pr.ncell, grid, rng)
+    Wm = pr.moments(f)[0]
+    rho, u = Wm[0], Wm[1:3] / Wm[0]
+    T_wrong = (Wm[3] / rho - 0.5 * u @ u)          # gamma=2 reading: E = |u|^2/2 + T
+    c2 = (grid.vx - u[0]) ** 2 + (grid.vy - u[1]) ** 2
+    g1 = rho / (2 * np.pi * T_wrong) * np.exp(-c2 / (2 * T_wrong))
+    e = np.sum(grid.w * (0.5 * (grid.vx**2 + grid.vy**2) * g1 + 0.5 * T_wrong * g1))
+    assert abs(e - Wm[3]) > 1e-3
+
+
+def test_uniform_maxwellian_is_stationary():
+    """With u_inf = 0 and T_w = T_inf, f = g_M(1,0,1) satisfies Eq. (numerpr_gov) up to the
+    quadrature defect of the collision term: interior faces cancel (closed cells), the far field
+    injects the same Maxwellian, and the wall re-emits it (Eq. formula_bgk_fdw on a grid symmetric
+    under v -> -v).  Collisionless (Kn -> inf) the residual vanishes to round-off on the config
+    grid; with collisions it vanishes on a wide fine grid."""
+    mesh = W.omesh(32, 16, np.array([0.004, -0.002, 0.001, 0.003]))
+    grid = W.velocity_grid(16, 4.0)
+    pr = _problem(mesh, grid, Kn=1e12, Ma=0.0)
+    f = pr.freestream()
+    R, _ = pr.residual(f)
+    V, S = pr.geometry()
+    flux_scale = np.abs(S).max() * np.abs(f).max() * np.abs(grid.vx).max()
+    assert np.abs(R).max() < 1e-13 * flux_scale
+    wide = W.velocity_grid(56, 10.0 / W.A_INF)
+    pr = _problem(mesh, wide, Kn=1.0, Ma=0.0)
+    R, _ = pr.residual(pr.freestream())
+    assert np.abs(R).max() < 1e-12 * flux_scale
+
+
+def _panel_closed_form(Uvec, n, Tw, d):
+    """Force per unit area on a panel (n into the body) in free-molecular flow with diffuse
+    re-emission at T_w: half-range moments of the free-stream Maxwellian (rho=1, RT=1)."""
+    t = np.array([-n[1], n[0]])
+    Un, Ut = Uvec @ n, Uvec @ t
+    c = math.sqrt(2.0)
+    s = Un / c
+    Ni = c * math.exp(-s * s) / (2 * math.sqrt(math.pi)) + 0.5 * Un * (1 + erf(s))
+    Pi = Un * c * math.exp(-s * s) / (2 * math.sqrt(math.pi)) + (Un * Un + 0.5 * c * c) * (1 + erf(s)) / 2
+    Pr = Ni * math.sqrt(math.pi * Tw / 2.0)
+    force = (Pi + Pr) * n + Ut * Ni * t
+    return force @ d
+
+
+@pytest.mark.parametrize("angle,Ma,Tw", [(0.0, 0.5, 1.0), (0.7, 2.0, 1.0), (2.4, 0.8, 0.6),
+                                         (-1.9, 1.3, 2.0)])
+def test_free_molecular_panel_closed_form(angle, Ma, Tw):
+    """The wall functional of Eq. (numer_J) with the discrete diffuse wall of Eq. (barg), fed with
+    the free-stream Maxwellian, equals the closed-form free-molecular panel force (flat plate at
+    incidence) when the velocity quadrature resolves each half range exactly (Gauss-Legendre on
+    v.n < 0 and v.n > 0 separately)."""
+    n = np.array([math.cos(angle), math.sin(angle)])
+    t = np.array([-n[1], n[0]])
+    L, m = 14.0, 72
+    xh, wh = np.polynomial.legendre.leggauss(m)
+    a = np.concatenate([-L / 2 * (xh + 1), L / 2 * (xh + 1)])      # (-L,0) and (0,L)
+    wa = np.concatenate([L / 2 * wh, L / 2 * wh])
+    b, wb = L * xh, L * wh
+    A, B = np.meshgrid(a, b, indexing="ij")
+    V = A[..., None] * n + B[..., None] * t
+    vx, vy = V[..., 0].ravel(), V[..., 1].ravel()
+    w = np.outer(wa, wb).ravel()
+    U = Ma * W.A_INF * np.array([1.0, 0.0])
+    f1 = np.exp(-((vx - U[0]) ** 2 + (vy - U[1]) ** 2) / 2) / (2 * np.pi)
+    area = 0.37
+    for d in ([1.0, 0.0], [0.0, 1.0]):
+        J = O.wall_face_functional(area * n, vx, vy, w, f1, Tw, d)
+        ref = area * _panel_closed_form(U, n, Tw, np.array(d))
+        assert abs(J - ref) <= 1e-11 * max(1.0, abs(ref))
+
+
+# ----------------------------------------------------------------------------- geometry, Eq. sens_nod
+def test_cell_geometry_closes_and_tiles_the_annulus():
+    mesh = W.omesh(48, 24, np.random.default_rng(3).uniform(-0.005, 0.005, 8))
+    pr = _problem(mesh, W.velocity_grid(4, 4.0))
+    V, S = pr.geometry()
+    assert V.min() > 0
+    assert np.abs(S.sum(axis=1)).max() < 1e-13          # closed cells: sum_e A_e n_e = 0
+
+    def shoelace(P):
+        return 0.5 * np.sum(P[:, 0] * np.roll(P[:, 1], -1) - np.roll(P[:, 0], -1) * P[:, 1])
+
+    annulus = shoelace(mesh.nodes[-1]) - shoelace(mesh.nodes[0])
+    assert abs(V.sum() - annulus) < 1e-11 * annulus
+    # wall faces point into the solid: from the wall centroid toward the airfoil interior
+    wall_mid = 0.5 * (mesh.nodes[0] + np.roll(mesh.nodes[0], -1, axis=0))
+    inward = np.array([0.5, 0.0]) - wall_mid
+    assert np.all(np.einsum("ic,ic->i", S[:48, 3], inward) > 0)
+
+
+def test_sens_nod_matches_finite_differences():
+    """Eq. (sens_nod) as printed against central differences of A = |x1 - x2| and of the unit
+    normal n(x1, x2) (either orientation)."""
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        x1, x2 = rng.uniform(-1, 1, 2), rng.uniform(-1, 1, 2)
+        sgn = rng.choice([-1.0, 1.0])
+
+        def normal(a, b):
+            e = a - b
+            return sgn * np.array([-e[1], e[0]]) / np.linalg.norm(e)
+
+        n = normal(x1, x2)
+        dA, dn = O.sens_nod(x1, x2, n)
+        h = 1e-6
+        for c in range(2):
+            e = np.zeros(2)
+            e[c] = h
+            fdA = (np.linalg.norm(x1 + e - x2) - np.linalg.norm(x1 - e - x2)) / (2 * h)
+            fdn = (normal(x1 + e, x2) - normal(x1 - e, x2)) / (2 * h)
+            assert abs(dA[c] - fdA) < 1e-8
+            assert np.abs(dn[:, c] - fdn).max() < 1e-8
+
+
+def test_hicks_henne_mesh_derivative_matches_fd():
+    alpha = np.random.default_rng(5).uniform(-0.01, 0.01, 8)
+    m = W.omesh(32, 12, alpha)
+    dn = m.dnodes()
+    h = 1e-7
+    for p in range(8):
+        a = alpha.copy(); a[p] += h
+        b = alpha.copy(); b[p] -= h
+        fd = (W.omesh(32, 12, a).nodes - W.omesh(32, 12, b).nodes) / (2 * h)
+        assert np.abs(fd - dn[p]).max() < 1e-8
+    assert np.all(dn[:, -1] == 0.0)                        # far field fixed
+    assert np.all(dn[:, :, :, 0] == 0.0)                   # xi fixed: only eta moves (Sec. 3.3)
+
+
+# ----------------------------------------------------------------------------- adjoint identities
+@pytest.fixture(scope="module")
+def tiny():
+    rng = np.random.default_rng(6)
+    mesh = W.omesh(16, 8, rng.uniform(-0.01, 0.01, 4))
+    grid = W.velocity_grid(8, 4.0)
+    pr = _problem(mesh, grid, Kn=1.0, Ma=0.5)
+    f, info = pr.primal_solve(tol=1e-30, max_sweeps=2400)
+    phi, ainfo = pr.adjoint_solve(f, tol=1e-30, max_sweeps=2400)
+    return mesh, grid, pr, f, phi
+
+
+def test_transpose_matches_forward_mode(tiny):
+    """<lam, (dR/df) df> = <(dR/df)^T lam, df>: the hand-written transpose against dual numbers
+    of the residual, at an arbitrary (not converged) state."""
+    mesh, grid, pr, f, phi = tiny
+    rng = np.random.default_rng(7)
+    fr = W.random_state(pr.ncell, grid, rng)
+    for _ in range(3):
+        df = rng.standard_normal(fr.shape)
+        lam = rng.standard_normal(fr.shape)
+        _, dR = pr.residual_dir(fr, df)
+        lhs = np.sum(lam * dR)
+        rhs = np.sum(pr.apply_RT(fr, lam) * df)
+        assert abs(lhs - rhs) < 1e-12 * np.sum(np.abs(lam * dR))
+        J, dJ = pr.functional_dir(fr, df)
+        assert abs(np.sum(pr.functional_grad(fr) * df) - dJ) < 1e-13 * max(1, abs(dJ))
+
+
+def test_dual_consistency(tiny):
+    """<w phi, (dR/df) df> = -(dJ/df) df for the converged adjoint: Lagrangian stationarity
+    dL(f; df) = 0 of Eq. (lagrangian) in discrete form, with both sides from forward-mode duals."""
+    mesh, grid, pr, f, phi = tiny
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        df = rng.standard_normal(f.shape)
+        _, dR = pr.residual_dir(f, df)
+        _, dJ = pr.functional_dir(f, df)
+        lhs = np.sum(grid.w[None, :, None] * phi * dR)
+        assert abs(lhs + dJ) < 1e-12 * abs(dJ)
+
+
+def test_full_discrete_sensitivity_matches_central_fd(tiny):
+    """dJ/dalpha from the adjoint equals the central difference of Eq. (fdm_x) on the same
+    discretisation, both solves to round-off, step 1e-5."""
+    mesh, grid, pr, f, phi = tiny
+    g_adj = pr.sens_full(f, phi, mesh.dnodes())
+    h = 1e-5
+    for p in range(mesh.alpha.size):
+        vals = []
+        for s in (1, -1):
+            a = mesh.alpha.copy()
+            a[p] += s * h
+            mm = W.omesh(16, 8, a)
+            pp = _problem(mm, grid, Kn=1.0, Ma=0.5)
+            ff, info = pp.primal_solve(tol=1e-30, max_sweeps=1200, f0=f)
+            vals.append(pp.functional(ff))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g_adj[p]) <= 1e-6 * abs(g_adj[p])
+
+
+def test_brute_force_newton_and_dense_transpose():
+    """On a problem of 4096 unknowns: assemble dR/df column by column with dual numbers, solve the
+    primal by Newton with dense LU and the adjoint by the dense transpose; both must match the
+    Gauss-Seidel oracle solves.  (Velocity grids much coarser than 8x8 on +-4 a_inf make the
+    plain nodal Maxwellian create mass and the steady problem has no positive solution.)"""
+    mesh = W.omesh(8, 4, np.array([0.006, -0.004]))
+    grid = W.velocity_grid(8, 4.0)
+    pr = _problem(mesh, grid, Kn=0.5, Ma=0.7)
+    n = pr.ncell * grid.nv * 2
+    f = pr.freestream()
+    for it in range(20):
+        R, _ = pr.residual(f)
+        Jm = np.zeros((n, n))
+        for col in range(n):
+            e = np.zeros(n); e[col] = 1.0
+            Jm[:, col] = pr.residual_dir(f, e.reshape(f.shape))[1].ravel()
+        step = np.linalg.solve(Jm, R.ravel())
+        f = f - step.reshape(f.shape)
+        if np.abs(step).max() < 1e-15:
+            break
+    f_gs, info = pr.primal_solve(tol=1e-30, max_sweeps=3000)
+    assert np.abs(f - f_gs).max() < 1e-12 * np.abs(f).max()
+    dJ = pr.functional_grad(f)
+    lam = np.linalg.solve(Jm.T, -dJ.ravel())
+    phi_lu = (lam.reshape(f.shape) / grid.w[None, :, None])
+    phi_gs, ainfo = pr.adjoint_solve(f_gs, tol=1e-30, max_sweeps=3000)
+    assert np.abs(phi_lu - phi_gs).max() < 1e-10 * np.abs(phi_lu).max()
+
+
+# ----------------------------------------------------------------------------- Sec. 3.2 and symmetry
+@pytest.mark.slow
+def test_paper_sensitivity_converges_to_exact_under_refinement():
+    """The paper's boundary sensitivity (Eq. sens_J_itf, sens_B_itf, gaussgrad, sens_nod) drops the
+    volume-mesh terms (Sec. 2.5: I and B_d do not vary with the boundary), so it differs from the
+    exact discrete gradient by a discretisation error that must shrink under refinement; the
+    paper reports adjoint vs FD agreement of a few tenths of a percent on fine meshes."""
+    alpha = np.array([0.004, -0.003, 0.002, 0.001, -0.002, 0.003])
+    grid = W.velocity_grid(10, 4.0)
+    gaps = []
+    for ni, nj in [(16, 8), (32, 16), (64, 32)]:
+        mesh = W.omesh(ni, nj, alpha)
+        pr = _problem(mesh, grid, Kn=1.0, Ma=0.5)
+        f, _ = pr.primal_solve(tol=1e-11, max_sweeps=3000)
+        phi, _ = pr.adjoint_solve(f, tol=1e-11, max_sweeps=3000)
+        gf = pr.sens_full(f, phi, mesh.dnodes())
+        gp, _, _ = pr.sens_paper(f, phi, mesh.dwall)
+        gaps.append(np.abs(gp - gf).max() / np.abs(gf).max())
+    assert gaps[0] > gaps[1] > gaps[2]
+    assert gaps[2] < 0.04
+
+
+def test_symmetric_airfoil_has_no_lift_and_mirror_sensitivities():
+    """Symmetric section at zero incidence on a mirror-symmetric mesh and velocity grid: the
+    y-force functional (m_J = v2) vanishes, and the sensitivities of matched upper/lower bumps
+    (which thicken both sides alike) are equal."""
+    mesh = W.omesh(32, 12, np.zeros(4))
+    grid = W.velocity_grid(10, 4.0)
+    pr = _problem(mesh, grid, Kn=1.0, Ma=0.5)
+    f, _ = pr.primal_solve(tol=1e-30, max_sweeps=1500)
+    drag = pr.functional(f)
+    lift = _problem(mesh, grid, Kn=1.0, Ma=0.5, direction=(0.0, 1.0)).functional(f)
+    assert abs(lift) < 1e-12 * abs(drag)
+    phi, _ = pr.adjoint_solve(f, tol=1e-30, max_sweeps=1500)
+    gf = pr.sens_full(f, phi, mesh.dnodes())
+    gp, _, _ = pr.sens_paper(f, phi, mesh.dwall)
+    for g in (gf, gp):
+        assert np.abs(g[:2] - g[2:]).max() < 1e-9 * np.abs(g).max()
