@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the DVM-BGK hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the whole path over the 256x128-cell, 48x48 Gauss-Legendre workload
+(Kn 0.1, Ma 0.8, 16 bump amplitudes, FP32 storage, FP64 reductions):
+  `--sweeps` primal point-implicit sweeps (one CUDA graph) with the fused moments, wall density,
+  drag and residual; `--sweeps` adjoint sweeps (one graph); the full-discrete and the paper
+  sensitivities over the 16 bump amplitudes.
+Metric: primal+adjoint (cell, velocity) updates per second, whole job.  f is 604 MB in FP32, far
+larger than the 126 MB L2, so no flush is needed between iterations.
+
+`--impl reference` times the FP64 CPU oracle (the only reference this method has) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_00923_gb300 import workloads as W  # noqa: E402
+
+METRIC = "primal+adjoint DVM updates/s"
+UNIT = "updates/s"
+WORKLOAD_INDEX = 1
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--sweeps", type=int, default=20, help="primal and adjoint sweeps per step (even)")
+    p.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--mesh", default=None, help="override the O-mesh size, e.g. 128x64 (profiling runs)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ----------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(wl, rows=16):
+    """One point-implicit primal sweep and one adjoint sweep of the FP64 oracle over the first
+    `rows` cell rows of the workload's mesh (same velocity grid and flow); updates/s."""
+    from oracle import oracle as O
+    cores = O.threads(os.cpu_count() or 1)
+    nodes = np.ascontiguousarray(wl.mesh.nodes[: rows + 1])
+    pr = O.Problem(nodes, wl.grid.vx, wl.grid.vy, wl.grid.w, wl.flow.Kn, wl.flow.Ma, wl.flow.Tw, wl.flow.aoa)
+    rng = np.random.default_rng(W.SEED_BASE + 99)
+    f = W.random_state(pr.ncell, wl.grid, rng)
+    phi = W.random_adjoint(pr.ncell, wl.grid.nv, rng)
+    t = time.perf_counter()
+    pr.jacobi(f)
+    pr.adjoint_jacobi(f, phi)
+    dt = time.perf_counter() - t
+    pairs = pr.ncell * wl.grid.nv
+    return {"value": 2 * pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "seconds": dt,
+            "sample": f"1 primal + 1 adjoint FP64 oracle sweep over the first {rows} cell rows "
+                      f"({pr.ncell} cells x {wl.grid.nv} velocities) of {wl.name}"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = W.config(WORKLOAD_INDEX)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, rows=4)
+    vals = [cpu_oracle_sample(wl, rows=8) for _ in range(args.steps)]
+    tot_t = sum(v["seconds"] for v in vals)
+    value = sum(v["value"] * v["seconds"] for v in vals) / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "sample": vals[0]["sample"], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2501_00923_gb300 import build, dvm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    wl = W.config(WORKLOAD_INDEX)
+    if args.mesh:
+        ni, nj = (int(x) for x in args.mesh.lower().split("x"))
+        wl.mesh = W.omesh(ni, nj, wl.mesh.alpha)
+        wl.name = wl.name.replace("omesh256x128", f"omesh{ni}x{nj}")
+    assert args.sweeps % 2 == 0 and args.sweeps >= 2
+    pairs = wl.pairs
+    P = wl.mesh.dwall.shape[0]
+
+    stream = torch.cuda.Stream()
+    ctx = dvm.Context(local, graph_iters=args.sweeps, stream=stream.cuda_stream)
+    mesh = dvm.Mesh(ctx, wl.mesh.nodes)
+    grid = dvm.VGrid(ctx, wl.grid.vx, wl.grid.vy, wl.grid.w)
+    Kn, Ma = wl.flow.Kn, wl.flow.Ma
+    st, _ = dvm.primal_solve(ctx, mesh, grid, Kn, Ma, tol=0.0, max_iter=args.sweeps, storage=args.storage)
+    ad, _ = dvm.adjoint_solve(ctx, st, tol=0.0, max_iter=args.sweeps)
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        dvm.primal_solve(ctx, mesh, grid, Kn, Ma, tol=0.0, max_iter=args.sweeps, storage=args.storage, state=st)
+        if events:
+            events[1].record(stream)
+        dvm.adjoint_solve(ctx, st, tol=0.0, max_iter=args.sweeps, adjoint=ad)
+        if events:
+            events[2].record(stream)
+        g_full = dvm.sensitivity(ctx, st, ad, wl.mesh.dwall, wl.mesh.s, mode="full")
+        g_paper = dvm.sensitivity(ctx, st, ad, wl.mesh.dwall, mode="paper")
+        if events:
+            events[3].record(stream)
+        return g_full, g_paper
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches0 = ctx.launches
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = ctx.launches - launches0
+    total_ms = t0.elapsed_time(t1)
+    prim_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+    adj_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    sens_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units = 2 * args.sweeps * pairs * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (algorithmic bytes: read f + write f' = 4S per primal update,
+    # read phi, f + write phi' = 6S per adjoint update; S = bytes per stored scalar)
+    S = {"fp32": 4, "bf16": 2, "fp64": 8}[args.storage]
+    n_sw = args.sweeps * args.steps
+    prim_sweep_ms, adj_sweep_ms = prim_ms / n_sw, adj_ms / n_sw
+    peak, peak_kind = hbm_peak()
+    k_prim = {"name": "k_primal_sweep", "ms": prim_sweep_ms, "bytes": pairs * 4 * S,
+              "GBps": pairs * 4 * S / (prim_sweep_ms * 1e6)}
+    k_adj = {"name": "k_adjoint_sweep", "ms": adj_sweep_ms, "bytes": pairs * 6 * S,
+             "GBps": pairs * 6 * S / (adj_sweep_ms * 1e6)}
+    dom = k_adj if adj_ms >= prim_ms else k_prim
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(f"{dom['name']}/{args.storage}")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": peak, "unit": "GB/s",
+                "frac": dom["GBps"] / peak, "traffic": traffic, "kernel": dom["name"],
+                "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": dom["bytes"], "launch_ms": dom["ms"],
+                "other": {k["name"]: {"GBps": k["GBps"], "frac": k["GBps"] / peak, "ms": k["ms"]}
+                          for k in (k_prim, k_adj)}}
+
+    # end-to-end through the public API with host buffers
+    e2e = run_e2e(args, ctx, wl, torch, dvm)
+
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.storage],
+            "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.mesh.ncell, "velocities": wl.grid.nv,
+                       "sweeps_per_phase": args.sweeps, "sensitivity_params": P,
+                       "l2": "inputs larger than L2 (f = %.0f MB)" % (pairs * 2 * S / 1e6),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "phase_ms_per_step": {"primal": prim_ms / args.steps, "adjoint": adj_ms / args.steps,
+                                             "sensitivity": sens_ms / args.steps}},
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample(wl).items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(line))
+    ad.close(); st.close(); grid.close(); mesh.close(); ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, ctx, wl, torch, dvm):
+    """Same metric through the C ABI per step: mesh, velocity grid and shape tangents copied from
+    pinned host memory, state and adjoint created, the sweeps run, gradients read back."""
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    nodes = pinned(wl.mesh.nodes)
+    vx, vy, w = pinned(wl.grid.vx), pinned(wl.grid.vy), pinned(wl.grid.w)
+    dwall, sj = pinned(wl.mesh.dwall), pinned(wl.mesh.s)
+    h2d = nodes.nbytes + vx.nbytes + vy.nbytes + w.nbytes + 2 * dwall.nbytes + sj.nbytes
+    n_graph = 2
+    d2h = 2 * dwall.shape[0] * 8 + 2 * n_graph * 16
+    if args.e2e_steps <= 0:
+        return None
+    times = []
+    for _ in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        m = dvm.Mesh(ctx, nodes)
+        g = dvm.VGrid(ctx, vx, vy, w)
+        st, _ = dvm.primal_solve(ctx, m, g, wl.flow.Kn, wl.flow.Ma, tol=0.0, max_iter=args.sweeps,
+                                 storage=args.storage)
+        ad, _ = dvm.adjoint_solve(ctx, st, tol=0.0, max_iter=args.sweeps)
+        dvm.sensitivity(ctx, st, ad, dwall, sj, mode="full")
+        dvm.sensitivity(ctx, st, ad, dwall, mode="paper")
+        ad.close(); st.close(); g.close(); m.close()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    dt = statistics.median(times[1:])
+    return {"value": 2 * args.sweeps * wl.pairs / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+            "note": "per step: mesh/grid/tangent upload, state+adjoint creation (includes the free-stream "
+                    "residual sweep and device allocation), the sweeps, both sensitivities, teardown"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

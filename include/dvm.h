@@ -1,0 +1,188 @@
+/*
+ * dvm.h -- C ABI of the GB300 (sm_103a) library for the steady discrete-velocity (DVM) BGK
+ * solve on a body-fitted O-mesh with diffuse walls, its discrete adjoint and the boundary
+ * sensitivities of Yuan & Wu, "Adjoint shape optimization from the continuum to free-molecular
+ * gas flows" (arXiv 2501.00923).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: rho_inf = 1, R T_inf = 1, chord = 1, monatomic gas (gamma = 5/3); velocities in units of
+ *   sqrt(R T_inf); free-stream speed Ma * sqrt(5/3).  tau = tau_inf / (rho sqrt(T)) (hard-sphere
+ *   mu ~ sqrt(T), tau = mu/p, Sec. 2.1) with tau_inf = (5/16) Kn sqrt(2 pi) (Eq. kndefine).
+ * Mesh: structured O-mesh, ni cells around (periodic), nj cells from the wall (j = 0) to the far
+ *   field (j = nj - 1).  Nodes are passed as double [(nj+1)][ni][2], j = 0 on the wall,
+ *   counter-clockwise around the body.  Cell c = j*ni + i.
+ * Velocities: any list (v_k, w_k), k < nv (uniform, Gauss-Legendre or unstructured, Sec. 4.3).
+ * Distribution layout (host side, every get/set call): double [ncell][nv][2] = (f1, f2) of
+ *   Eq. (f_reduce), velocity fastest.  The device keeps the same order in the storage precision
+ *   chosen at state creation (FP64, FP32 or BF16), the velocity count padded to a multiple of 4 with
+ *   zero-weight velocities.
+ * Ownership: host arrays are caller-owned and only read (or written, for outputs) during the call.
+ *   Every handle is library-owned and released by its *_destroy.  Device memory is allocated with
+ *   cudaMalloc on the context's device; the context's stream orders all work.
+ * Errors: every call returns a dvm_status; DVM_OK = 0.  No C++ exception crosses the ABI.  After
+ *   DVM_ERR_CUDA the context should be destroyed.  dvm_last_error() gives a message for the
+ *   calling thread.  Calls are thread-compatible per context (one thread at a time per context).
+ */
+#ifndef DVM_H
+#define DVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DVM_OK = 0,
+    DVM_ERR_INVALID_ARG = 1,
+    DVM_ERR_OOM = 2,
+    DVM_ERR_ADMISSION = 3,   /* request does not fit the context's HBM budget */
+    DVM_NOT_CONVERGED = 4,   /* max_iter reached; the result still holds the last residual */
+    DVM_ERR_NONFINITE = 5,   /* a residual or a moment became NaN/Inf */
+    DVM_ERR_CUDA = 6,
+    DVM_ERR_TIMEOUT = 7,
+    DVM_ERR_STAGNATED = 8    /* residual stopped decreasing (FP32/BF16 floor) before tol */
+} dvm_status;
+
+typedef enum { DVM_STORE_FP64 = 0, DVM_STORE_FP32 = 1, DVM_STORE_BF16 = 2 } dvm_storage;
+
+/* Objective of Eq. (formula_opt): J = sum_wall sum_k w m_k (v_k . n A) f1, m_k = v_k . d.
+ * DVM_DRAG: d = free-stream direction (m_J = v1 at zero incidence, Sec. 2.4);
+ * DVM_LIFT: d = free-stream direction rotated by +90 degrees. */
+typedef enum { DVM_DRAG = 0, DVM_LIFT = 1 } dvm_functional;
+
+/* DVM_SENS_PAPER: the boundary sensitivity of Sec. 3.2 (Eq. sens_J_itf, sens_B_itf, gaussgrad,
+ *   sens_nod), wall nodes only, as the paper computes it.
+ * DVM_SENS_FULL: the exact derivative of the discrete J, including the interior mesh motion
+ *   x(i,j) = x_w(i) + s_j (x_ff(i) - x_w(i)) (the terms the paper drops below Eq. sens_shape). */
+typedef enum { DVM_SENS_PAPER = 0, DVM_SENS_FULL = 1 } dvm_sens_mode;
+
+typedef struct dvm_context dvm_context;
+typedef struct dvm_mesh dvm_mesh;
+typedef struct dvm_vgrid dvm_vgrid;
+typedef struct dvm_state dvm_state;
+typedef struct dvm_adjoint dvm_adjoint;
+
+typedef struct {
+    int graph_iters;        /* sweeps captured per CUDA-graph launch (even, >= 2); 0 -> 20 */
+    size_t hbm_budget;      /* bytes the context may hold for states (admission); 0 -> no limit */
+    void* stream;           /* cudaStream_t to run on (e.g. torch's); NULL -> the library's own */
+} dvm_options;
+
+typedef struct {
+    double Kn;              /* Knudsen number with the chord and the free stream, Eq. (kndefine) */
+    double Ma;              /* free-stream Mach number */
+    double Tw;              /* wall temperature / free-stream temperature (u_w = 0), Eq. (formula_bgk_fdw0) */
+    double aoa;             /* free-stream direction, radians */
+} dvm_flow;
+
+typedef struct {
+    double tol;             /* stop when |R|/r0 <= tol; |R| = sqrt(sum_{c,k,comp} w_k (R/V_c)^2) */
+    int max_iter;           /* cap on point-implicit sweeps */
+    int stall_window;       /* stop with DVM_ERR_STAGNATED after this many sweeps without a 2% drop; 0 = off */
+} dvm_solve_opts;
+
+typedef struct {
+    double J;               /* drag functional of Eq. (numer_J) at the final state */
+    double Cd;              /* J / (rho_inf |u_inf|^2 / 2 * chord) */
+    double residual;        /* |R| / r0 of the last sweep's input state */
+    double r0;              /* |R| of the free-stream state */
+    int iters;              /* sweeps done by this call */
+    int status;             /* dvm_status of the solve */
+} dvm_primal_result;
+
+typedef struct {
+    double residual;        /* adjoint |R_a| / |R_a(phi = 0)| */
+    double r0;
+    int iters;
+    int status;
+} dvm_adjoint_result;
+
+/* ------------------------------------------------------------------------ context, B1 */
+/* Create a context on CUDA device `cuda_device`.  opt may be NULL (defaults).
+ * Errors: DVM_ERR_INVALID_ARG (bad device/options), DVM_ERR_CUDA. */
+int dvm_context_create(dvm_context** out, int cuda_device, const dvm_options* opt);
+void dvm_context_destroy(dvm_context* ctx);
+/* bytes currently held by states/adjoints of this context (admission accounting) */
+size_t dvm_context_bytes(const dvm_context* ctx);
+const char* dvm_status_string(int status);
+const char* dvm_last_error(void);
+/* number of kernel launches issued by this context since creation (graph launches count each
+ * captured kernel) */
+uint64_t dvm_context_launches(const dvm_context* ctx);
+
+/* ------------------------------------------------------------------------ mesh, B2 */
+/* Copy the O-mesh nodes (double [(nj+1)][ni][2]) and build on the host the cell volumes, the
+ * outward face vectors A n of Eq. (numerpr_gov) and the neighbour table.  Fails with
+ * DVM_ERR_INVALID_ARG if ni < 3, nj < 1, or a cell has non-positive area (tangled mesh). */
+int dvm_mesh_create(dvm_context* ctx, int ni, int nj, const double* nodes_xy, dvm_mesh** out);
+void dvm_mesh_destroy(dvm_mesh* mesh);
+
+/* ------------------------------------------------------------------------ velocity grid, B3 */
+/* Copy an arbitrary velocity list with quadrature weights (w_k > 0).  nv >= 1. */
+int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* vy, const double* w,
+                     dvm_vgrid** out);
+void dvm_vgrid_destroy(dvm_vgrid* grid);
+
+/* ------------------------------------------------------------------------ primal state, B4 */
+/* Allocate a primal state (two f buffers, per-cell moments, wall density) in the given storage
+ * precision and set it to the free-stream Maxwellian (Eq. drlt_maxwell).  Counts against the
+ * context's HBM budget (DVM_ERR_ADMISSION).  mesh and grid must outlive the state. */
+int dvm_state_create(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid,
+                     const dvm_flow* flow, int storage, dvm_state** out);
+void dvm_state_destroy(dvm_state* st);
+/* Upload f (host double [ncell][nv][2]) and recompute the moments W (Eq. macint_reduce) and the
+ * wall density F_rhow (Eq. formula_bgk_fdw) from it. */
+int dvm_state_set(dvm_state* st, const double* f_host);
+/* Download f (converted to double). */
+int dvm_state_get(const dvm_state* st, double* f_host);
+/* Download per-cell primitive variables (rho, u1, u2, T) [ncell][4] of the current f. */
+int dvm_state_moments(const dvm_state* st, double* prim_host);
+/* Run exactly n point-implicit sweeps (Eq. numerpr_gov solved for f_{c,k} with the neighbours,
+ * moments and wall density of the previous sweep):
+ *   f_new = [ V g/tau + sum_{a<=0} (-a) F_up ] / [ V/tau + sum_{a>0} a ],  a = A n . v_k.
+ * residual_out (optional, host double[n]) receives |R|/r0 of each sweep's input state. */
+int dvm_primal_iterate(dvm_state* st, int n, double* residual_out);
+/* Drag J (Eq. numer_J) of the state's current f, and the y-force for the same state. */
+int dvm_state_functional(dvm_state* st, int functional, double* J);
+/* Whole steady solve, B4.  *inout == NULL: create a state (storage from ctx-default FP32 unless
+ * flow-specific storage was chosen with dvm_state_create) and solve from the free stream;
+ * otherwise warm start from the given state (its mesh/grid/flow must match the arguments).
+ * Returns the solve status (DVM_OK, DVM_NOT_CONVERGED, DVM_ERR_STAGNATED, DVM_ERR_NONFINITE). */
+int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid,
+                     const dvm_flow* flow, const dvm_solve_opts* opts, int storage,
+                     dvm_state** inout, dvm_primal_result* out);
+
+/* ------------------------------------------------------------------------ adjoint, B5 */
+/* Allocate the adjoint phi of `st` (same storage), zero it, linearised at the state's current f.
+ * The state must not change while the adjoint is used. */
+int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out);
+void dvm_adjoint_destroy(dvm_adjoint* adj);
+int dvm_adjoint_set(dvm_adjoint* adj, const double* phi_host);
+int dvm_adjoint_get(const dvm_adjoint* adj, double* phi_host);
+/* Exactly n sweeps of the transposed (downwind) point-implicit update of Eq. (numerad_gov) in
+ * discrete form, (dR/df)^T (w phi) = -(dJ/df)^T:
+ *   D phi = -dJ/df/w + sum_{a>0, interior} a phi_nb + (V/tau) What.Psi
+ *           - (V/tau^2) rhohat (dtau/dW).Psi - [wall, a>0] (v.n) Lambda
+ * with What, rhohat of Eq. (adjoint_macdefines) and the wall coupling of Eq. (formula_adjointbgk)
+ * taken from the previous sweep.  residual_out as for the primal. */
+int dvm_adjoint_iterate(dvm_adjoint* adj, int n, double* residual_out);
+int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm_solve_opts* opts,
+                      dvm_adjoint** inout, dvm_adjoint_result* out);
+
+/* ------------------------------------------------------------------------ sensitivity, B6 */
+/* dJ/dalpha_p for n_params shape parameters that move the wall nodes by dwall_dalpha
+ * (double [n_params][ni][2], caller-owned) and the interior nodes by (1 - s_j) times that
+ * (s_j: double [nj+1], s_0 = 0, s_nj = 1; used by DVM_SENS_FULL only).  grad_out: double[n_params].
+ * node_grad_out (optional): DVM_SENS_PAPER -> dJ/dx of the wall nodes, double [ni][2];
+ * DVM_SENS_FULL -> dJ/dx of every node, double [(nj+1)][ni][2]. */
+int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* adj, int n_params,
+                    const double* dwall_dalpha, const double* s_j, int mode, double* grad_out,
+                    double* node_grad_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVM_H */

@@ -401,9 +401,9 @@ void apply_RT(const Prob& p, const Consts& K, const Geo<double>& g, const double
  * Nonlinear Gauss-Seidel, in place, alternating the four sweep directions of the O-mesh.  Each
  * cell update is the point-implicit solve of its own rows with the current neighbour values and
  * the cell's current moments. */
-void gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g, double* f, int c) {
+void gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g, const double* f, int c, double* dst) {
     const int nv = p.nv;
-    double* fc = f + (size_t)c * nv * 2;
+    const double* fc = f + (size_t)c * nv * 2;
     double W[4], rho, u1, u2, T;
     cell_moments(p, fc, W);
     primitives(W, rho, u1, u2, T);
@@ -430,7 +430,7 @@ void gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g, double
         nf[2 * k] = r1 / d;
         nf[2 * k + 1] = r2 / d;
     }
-    std::memcpy(fc, nf.data(), sizeof(double) * 2 * nv);
+    std::memcpy(dst, nf.data(), sizeof(double) * 2 * nv);
 }
 
 void gs_sweep(const Prob& p, const Consts& K, const Geo<double>& g, double* f, int dir) {
@@ -440,7 +440,7 @@ void gs_sweep(const Prob& p, const Consts& K, const Geo<double>& g, double* f, i
         int j = jup ? jj : nj - 1 - jj;
         for (int ii = 0; ii < ni; ++ii) {
             int i = iup ? ii : ni - 1 - ii;
-            gs_update_cell(p, K, g, f, j * ni + i);
+            gs_update_cell(p, K, g, f, j * ni + i, f + (size_t)(j * ni + i) * p.nv * 2);
         }
     }
 }
@@ -452,44 +452,48 @@ void gs_sweep(const Prob& p, const Consts& K, const Geo<double>& g, double* f, i
  * Convergence is measured with the scatter-form apply_RT above, not with this update. */
 /* d[(V/tau)(f - g(W))]_{k,comp} / dW_m for every cell, from dual numbers in each W component:
  * dC[((c*4 + m)*nv + k)*2 + comp].  f is fixed during an adjoint solve, so this is built once. */
+void collision_partials_cell(const Prob& p, const Consts& K, const Geo<double>& g, const double* f, int c,
+                             double* dCc /* [4][nv][2] */) {
+    const int nv = p.nv;
+    const double* fc = f + (size_t)c * nv * 2;
+    double W[4];
+    cell_moments(p, fc, W);
+    for (int m = 0; m < 4; ++m) {
+        Dual Wd[4];
+        for (int n = 0; n < 4; ++n) Wd[n] = Dual(W[n], n == m ? 1.0 : 0.0);
+        Dual rd, ud1, ud2, Td;
+        primitives(Wd, rd, ud1, ud2, Td);
+        Dual Vtd = Dual(g.V[c]) / relax_time(K.tau_inf, rd, Td);
+        double* out = dCc + (size_t)m * nv * 2;
+        for (int k = 0; k < nv; ++k) {
+            Dual g1, g2;
+            maxwellian(rd, ud1, ud2, Td, p.vx[k], p.vy[k], g1, g2);
+            out[2 * k] = (Vtd * (Dual(fc[2 * k]) - g1)).d;
+            out[2 * k + 1] = (Vtd * (Dual(fc[2 * k + 1]) - g2)).d;
+        }
+    }
+}
+
 void collision_partials(const Prob& p, const Consts& K, const Geo<double>& g, const double* f,
                         std::vector<double>& dC) {
     const int nv = p.nv, nc = p.ni * p.nj;
     dC.assign((size_t)nc * 4 * nv * 2, 0.0);
 #pragma omp parallel for schedule(static)
-    for (int c = 0; c < nc; ++c) {
-        const double* fc = f + (size_t)c * nv * 2;
-        double W[4];
-        cell_moments(p, fc, W);
-        for (int m = 0; m < 4; ++m) {
-            Dual Wd[4];
-            for (int n = 0; n < 4; ++n) Wd[n] = Dual(W[n], n == m ? 1.0 : 0.0);
-            Dual rd, ud1, ud2, Td;
-            primitives(Wd, rd, ud1, ud2, Td);
-            Dual Vtd = Dual(g.V[c]) / relax_time(K.tau_inf, rd, Td);
-            double* out = &dC[(((size_t)c * 4 + m) * nv) * 2];
-            for (int k = 0; k < nv; ++k) {
-                Dual g1, g2;
-                maxwellian(rd, ud1, ud2, Td, p.vx[k], p.vy[k], g1, g2);
-                out[2 * k] = (Vtd * (Dual(fc[2 * k]) - g1)).d;
-                out[2 * k + 1] = (Vtd * (Dual(fc[2 * k + 1]) - g2)).d;
-            }
-        }
-    }
+    for (int c = 0; c < nc; ++c) collision_partials_cell(p, K, g, f, c, &dC[(size_t)c * 4 * nv * 2]);
 }
 
 void adjoint_gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g, const double* f,
-                            const double* jsrc, const double* dC, double* phi, int c) {
+                            const double* jsrc, const double* dCc, const double* phi, int c, double* dst) {
     const int nv = p.nv;
     const double* fc = f + (size_t)c * nv * 2;
-    double* pc = phi + (size_t)c * nv * 2;
+    const double* pc = phi + (size_t)c * nv * 2;
     double W[4], rho, u1, u2, T;
     cell_moments(p, fc, W);
     primitives(W, rho, u1, u2, T);
     double Vt = g.V[c] / relax_time(K.tau_inf, rho, T);
     double q[4];
     for (int m = 0; m < 4; ++m) {
-        const double* dc = dC + (((size_t)c * 4 + m) * nv) * 2;
+        const double* dc = dCc + (size_t)m * nv * 2;
         double acc = 0.0;
         for (int k = 0; k < nv; ++k) acc += p.w[k] * (pc[2 * k] * dc[2 * k] + pc[2 * k + 1] * dc[2 * k + 1]);
         q[m] = acc;
@@ -532,7 +536,7 @@ void adjoint_gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g
         np[2 * k] = r1 / d;
         np[2 * k + 1] = r2 / d;
     }
-    std::memcpy(pc, np.data(), sizeof(double) * 2 * nv);
+    std::memcpy(dst, np.data(), sizeof(double) * 2 * nv);
 }
 
 /* adjoint residual in phi units: Ra = ((dR/df)^T (w phi) + dJ/df) / w */
@@ -753,6 +757,34 @@ int orc_adjoint_jacobi(const orc_problem* q, const double* f, const double* phi,
     return 0;
 }
 
+/* Point-implicit (Jacobi) update of selected cells only, out[n][nv][2]: the cell update of the
+ * Gauss-Seidel solver applied to the unmodified state (so it equals one Jacobi sweep there). */
+int orc_jacobi_cells(const orc_problem* q, const double* f, int n, const int* cells, double* out) {
+    Prob p = to_prob(q);
+    Consts K = make_consts(p);
+    Geo<double> g = geo_of(p);
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < n; ++s) gs_update_cell(p, K, g, f, cells[s], out + (size_t)s * p.nv * 2);
+    return 0;
+}
+
+/* Adjoint point-implicit update of selected cells (gather form, see adjoint_gs_update_cell). */
+int orc_adjoint_jacobi_cells(const orc_problem* q, const double* f, const double* phi, int n, const int* cells,
+                             double* out) {
+    Prob p = to_prob(q);
+    Consts K = make_consts(p);
+    Geo<double> g = geo_of(p);
+    std::vector<double> js((size_t)p.ni * p.nj * p.nv * 2);
+    functional_grad(p, K, g, f, js.data());
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < n; ++s) {
+        std::vector<double> dCc((size_t)4 * p.nv * 2);
+        collision_partials_cell(p, K, g, f, cells[s], dCc.data());
+        adjoint_gs_update_cell(p, K, g, f, js.data(), dCc.data(), phi, cells[s], out + (size_t)s * p.nv * 2);
+    }
+    return 0;
+}
+
 /* Solve R(f) = 0 in place by Gauss-Seidel sweeps until |R|/r0 <= tol, r0 = |R(free stream)|.
  * Returns 0 when converged, 4 otherwise. */
 int orc_primal_solve(const orc_problem* q, double* f, double tol, int max_sweeps, double* rel, int* sweeps) {
@@ -805,7 +837,9 @@ int orc_adjoint_solve(const orc_problem* q, const double* f, double* phi, double
             int j = jup ? jj : nj - 1 - jj;
             for (int ii = 0; ii < ni; ++ii) {
                 int i = iup ? ii : ni - 1 - ii;
-                adjoint_gs_update_cell(p, K, g, f, js.data(), dC.data(), phi, j * ni + i);
+                int c = j * ni + i;
+                adjoint_gs_update_cell(p, K, g, f, js.data(), dC.data() + (size_t)c * 4 * p.nv * 2, phi, c,
+                                       phi + (size_t)c * p.nv * 2);
             }
         }
     }

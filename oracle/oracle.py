@@ -66,6 +66,8 @@ def lib():
             "orc_sens_nod": (i, [_dp, _dp, _dp, _dp, _dp]),
             "orc_sens_paper": (i, [P, _dp, _dp, i, _dp, _dp, _dp, _dp]),
             "orc_wall_face_functional": (d, [_dp, i, _dp, _dp, _dp, _dp, d, _dp]),
+            "orc_jacobi_cells": (i, [P, _dp, i, C.POINTER(C.c_int), _dp]),
+            "orc_adjoint_jacobi_cells": (i, [P, _dp, _dp, i, C.POINTER(C.c_int), _dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -186,6 +188,21 @@ class Problem:
         nrm = C.c_double()
         lib().orc_adjoint_jacobi(self.ref, _ptr(_c(f)), _ptr(_c(phi)), _ptr(out), C.byref(nrm))
         return out, nrm.value
+
+    def jacobi_cells(self, f, cells):
+        """Point-implicit update of the listed cells only: [len(cells), nv, 2]."""
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((cells.size, self.nv, 2))
+        lib().orc_jacobi_cells(self.ref, _ptr(_c(f)), cells.size, cells.ctypes.data_as(C.POINTER(C.c_int)),
+                               _ptr(out))
+        return out
+
+    def adjoint_jacobi_cells(self, f, phi, cells):
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((cells.size, self.nv, 2))
+        lib().orc_adjoint_jacobi_cells(self.ref, _ptr(_c(f)), _ptr(_c(phi)), cells.size,
+                                       cells.ctypes.data_as(C.POINTER(C.c_int)), _ptr(out))
+        return out
 
     def primal_solve(self, tol=1e-12, max_sweeps=20000, f0=None):
         f = self.freestream() if f0 is None else _c(f0).copy()

@@ -1,0 +1,982 @@
+// Host side of the C ABI declared in include/dvm.h: handles, geometry preprocessing, the sweep
+// loops (captured as CUDA graphs), convergence control and the sensitivity driver.  Every step of
+// the DVM path runs in the kernels of dvm_kernels.cu; this file only prepares arguments,
+// allocates device memory and moves small results.
+#include "dvm.h"
+#include "dvm_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace dvm;
+
+struct dvm_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int graph_iters = 20;
+    size_t budget = 0;
+    size_t bytes = 0;
+    uint64_t launches = 0;
+    double* pinned = nullptr;   // 64 doubles for small device->host results
+};
+
+struct dvm_mesh {
+    dvm_context* ctx = nullptr;
+    DevMesh d;
+    std::vector<double> nodes;
+};
+
+struct dvm_vgrid {
+    dvm_context* ctx = nullptr;
+    DevGrid d;
+};
+
+struct dvm_state {
+    dvm_context* ctx = nullptr;
+    const dvm_mesh* mesh = nullptr;
+    const dvm_vgrid* grid = nullptr;
+    dvm_flow flow{};
+    int storage = 1;
+    DevFlow fl;
+    void* f[2] = {nullptr, nullptr};
+    double4* prim[2] = {nullptr, nullptr};
+    double* Fw[2] = {nullptr, nullptr};
+    double* Jpart = nullptr;
+    double* respart = nullptr;
+    double* out = nullptr;      // [2]: sum respart, J
+    double* scratch = nullptr;  // [ni + 2] functional scratch
+    int cur = 0;
+    double r0 = 0.0;
+    size_t bytes = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_n = 0;
+    int graph_cur = -1;
+    uint64_t version = 0;       // bumped whenever f changes (sweeps, uploads)
+};
+
+struct dvm_adjoint {
+    dvm_state* st = nullptr;
+    int functional = DVM_DRAG;
+    double dirx = 1.0, diry = 0.0;
+    double* wallM = nullptr;
+    void* cell = nullptr;       // AdjCell<TC>[ncell]: linearisation constants
+    uint64_t st_version = ~0ull; // state version the constants and couplings belong to
+    void* phi[2] = {nullptr, nullptr};
+    double4* Z[2] = {nullptr, nullptr};
+    double* Lam[2] = {nullptr, nullptr};
+    double* respart = nullptr;
+    double* out = nullptr;
+    int cur = 0;
+    double r0 = 0.0;
+    size_t bytes = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_n = 0;
+    int graph_cur = -1;
+    int graph_st_cur = -1;
+    // sensitivity scratch, allocated on first use
+    double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr;
+    double *vol = nullptr, *elem = nullptr, *dwall = nullptr, *sj = nullptr, *grad = nullptr;
+    int sens_P = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return DVM_ERR_CUDA;
+}
+
+#define CK(x)                                          \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #x); \
+    } while (0)
+
+template <class T>
+int dalloc(dvm_context* ctx, T** p, size_t count, size_t* acc = nullptr) {
+    size_t b = count * sizeof(T);
+    if (b == 0) b = sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(DVM_ERR_OOM, "cudaMalloc failed: out of device memory");
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if (acc) *acc += b;
+    (void)ctx;
+    return DVM_OK;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+double dir_angle(const dvm_flow& fl, int functional) {
+    return fl.aoa + (functional == DVM_LIFT ? 0.5 * M_PI : 0.0);
+}
+
+// ------------------------------------------------------------------ argument builders
+template <class TS, class TC>
+PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
+    PrimalArgs<TS, TC> a{};
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    constexpr int KV = 16 / (2 * (int)sizeof(TS));
+    a.ncell = m.ncell;
+    a.nq = g.nvp / KV;
+    a.nb = m.nb;
+    if constexpr (sizeof(TC) == 8) {
+        a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.fd = st->fl.fdd; a.gw = st->fl.gwd;
+    } else {
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.fd = st->fl.fdf; a.gw = st->fl.gwf;
+    }
+    a.wallD = st->fl.wallD;
+    a.inv_tau_inf = 1.0 / st->fl.tau_inf;
+    a.halfTw = (TC)(0.5 * st->fl.Tw);
+    const double ang = dir_angle(st->flow, DVM_DRAG);
+    a.dirx = (TC)cos(ang);
+    a.diry = (TC)sin(ang);
+    a.f_old = (const TS*)st->f[src];
+    a.f_new = (TS*)st->f[1 - src];
+    a.prim_old = st->prim[src];
+    a.prim_new = st->prim[1 - src];
+    a.Fw_old = st->Fw[src];
+    a.Fw_new = st->Fw[1 - src];
+    a.Jpart = st->Jpart;
+    a.respart = st->respart;
+    return a;
+}
+
+template <class TS, class TC>
+AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
+    AdjointArgs<TS, TC> a{};
+    const dvm_state* st = ad->st;
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    constexpr int KV = 16 / (2 * (int)sizeof(TS));
+    a.ncell = m.ncell;
+    a.nq = g.nvp / KV;
+    a.nb = m.nb;
+    if constexpr (sizeof(TC) == 8) {
+        a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.gw = st->fl.gwd;
+    } else {
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.gw = st->fl.gwf;
+    }
+    a.wallD = st->fl.wallD;
+    a.wallM = ad->wallM;
+    a.inv_tau_inf = 1.0 / st->fl.tau_inf;
+    a.halfTw = (TC)(0.5 * st->fl.Tw);
+    a.dirx = (TC)ad->dirx;
+    a.diry = (TC)ad->diry;
+    a.f = (const TS*)st->f[st->cur];
+    a.cell = (const AdjCell<TC>*)ad->cell;
+    a.phi_old = (const TS*)ad->phi[src];
+    a.phi_new = (TS*)ad->phi[1 - src];
+    a.Z_old = ad->Z[src];
+    a.Z_new = ad->Z[1 - src];
+    a.Lam_old = ad->Lam[src];
+    a.Lam_new = ad->Lam[1 - src];
+    a.respart = ad->respart;
+    return a;
+}
+
+cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
+    switch (st->storage) {
+        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); return launch_primal_sweep(0, &a, res, st->ctx->stream); }
+        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); return launch_primal_sweep(1, &a, res, st->ctx->stream); }
+        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); return launch_primal_sweep(2, &a, res, st->ctx->stream); }
+    }
+}
+
+cudaError_t enqueue_adjoint(dvm_adjoint* ad, int src, bool update = true, bool res = true) {
+    cudaStream_t s = ad->st->ctx->stream;
+    switch (ad->st->storage) {
+        case DVM_STORE_FP64: { auto a = adjoint_args<double, double>(ad, src); return launch_adjoint_sweep(0, &a, update, res, s); }
+        case DVM_STORE_FP32: { auto a = adjoint_args<float, float>(ad, src); return launch_adjoint_sweep(1, &a, update, res, s); }
+        default: { auto a = adjoint_args<__nv_bfloat16, float>(ad, src); return launch_adjoint_sweep(2, &a, update, res, s); }
+    }
+}
+
+// Recompute the linearisation constants from the state's current moments.
+cudaError_t adjoint_relinearise(dvm_adjoint* ad) {
+    const dvm_state* st = ad->st;
+    cudaError_t e = launch_adjoint_cellconst(st->storage, st->prim[st->cur], st->mesh->d, 1.0 / st->fl.tau_inf,
+                                             ad->cell, st->ctx->stream);
+    st->ctx->launches += 1;
+    ad->st_version = st->version;
+    return e;
+}
+
+// Rebuild the couplings (Z, Lambda) of phi[cur] in place: a non-updating pass whose outputs land in
+// the slot the next sweep reads.
+cudaError_t refresh_adjoint_couplings(dvm_adjoint* ad) {
+    // the non-updating pass reads phi[cur] and writes Z/Lam of slot 1-cur; copy them to slot cur
+    cudaError_t e = enqueue_adjoint(ad, ad->cur, false);
+    const DevMesh& m = ad->st->mesh->d;
+    cudaStream_t s = ad->st->ctx->stream;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ad->Z[ad->cur], ad->Z[1 - ad->cur], m.ncell * sizeof(double4), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ad->Lam[ad->cur], ad->Lam[1 - ad->cur], m.ni * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    ad->st->ctx->launches += 1;
+    return e;
+}
+
+cudaError_t enqueue_primal_finalize(dvm_state* st, int dst_state, double* out) {
+    const DevMesh& m = st->mesh->d;
+    return launch_finalize(st->respart, m.ncell, st->Jpart, st->Fw[dst_state], st->fl.wallM, m.ni, out,
+                           st->ctx->stream);
+}
+
+cudaError_t enqueue_adjoint_finalize(dvm_adjoint* ad, double* out) {
+    const DevMesh& m = ad->st->mesh->d;
+    return launch_finalize(ad->respart, m.ncell, nullptr, nullptr, nullptr, m.ni, out, ad->st->ctx->stream);
+}
+
+int check_finite(double v, const char* what) {
+    if (!std::isfinite(v)) return fail(DVM_ERR_NONFINITE, std::string(what) + " is not finite");
+    return DVM_OK;
+}
+
+// Run n primal sweeps without a graph; hist (device, [2n]) receives (sum respart, J) per sweep.
+int run_primal_plain(dvm_state* st, int n, double* hist) {
+    st->version += (uint64_t)n;
+    for (int i = 0; i < n; ++i) {
+        CK(enqueue_primal(st, st->cur));
+        CK(enqueue_primal_finalize(st, 1 - st->cur, hist ? hist + 2 * i : st->out));
+        st->cur = 1 - st->cur;
+        st->ctx->launches += 2;
+    }
+    return DVM_OK;
+}
+
+int run_adjoint_plain(dvm_adjoint* ad, int n, double* hist) {
+    for (int i = 0; i < n; ++i) {
+        CK(enqueue_adjoint(ad, ad->cur));
+        CK(enqueue_adjoint_finalize(ad, hist ? hist + 2 * i : ad->out));
+        ad->cur = 1 - ad->cur;
+        ad->st->ctx->launches += 2;
+    }
+    return DVM_OK;
+}
+
+bool graphs_ok(const dvm_context* ctx) { return ctx->stream != nullptr; }
+
+// Capture K (even) sweeps + one finalize.  Buffers return to the same parity after K sweeps.
+int build_primal_graph(dvm_state* st, int K) {
+    if (st->graph && st->graph_n == K && st->graph_cur == st->cur) return DVM_OK;
+    if (st->graph) { cudaGraphExecDestroy(st->graph); st->graph = nullptr; }
+    cudaStream_t s = st->ctx->stream;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int cur = st->cur;
+    for (int i = 0; i < K; ++i) {
+        enqueue_primal(st, cur, i == K - 1);
+        if (i == K - 1) enqueue_primal_finalize(st, 1 - cur, st->out);
+        cur = 1 - cur;
+    }
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&st->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    st->graph_n = K;
+    st->graph_cur = st->cur;
+    return DVM_OK;
+}
+
+int build_adjoint_graph(dvm_adjoint* ad, int K) {
+    if (ad->graph && ad->graph_n == K && ad->graph_cur == ad->cur && ad->graph_st_cur == ad->st->cur) return DVM_OK;
+    if (ad->graph) { cudaGraphExecDestroy(ad->graph); ad->graph = nullptr; }
+    cudaStream_t s = ad->st->ctx->stream;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int cur = ad->cur;
+    for (int i = 0; i < K; ++i) {
+        enqueue_adjoint(ad, cur, true, i == K - 1);
+        if (i == K - 1) enqueue_adjoint_finalize(ad, ad->out);
+        cur = 1 - cur;
+    }
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&ad->graph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    ad->graph_n = K;
+    ad->graph_cur = ad->cur;
+    ad->graph_st_cur = ad->st->cur;
+    return DVM_OK;
+}
+
+// read out[0..1] of the device into the pinned buffer and wait
+int fetch2(dvm_context* ctx, const double* dout, double* r) {
+    CK(cudaMemcpyAsync(ctx->pinned, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    r[0] = ctx->pinned[0];
+    r[1] = ctx->pinned[1];
+    return DVM_OK;
+}
+
+}  // namespace
+
+// ======================================================================================== C ABI
+extern "C" {
+
+const char* dvm_status_string(int s) {
+    switch (s) {
+        case DVM_OK: return "DVM_OK";
+        case DVM_ERR_INVALID_ARG: return "DVM_ERR_INVALID_ARG";
+        case DVM_ERR_OOM: return "DVM_ERR_OOM";
+        case DVM_ERR_ADMISSION: return "DVM_ERR_ADMISSION";
+        case DVM_NOT_CONVERGED: return "DVM_NOT_CONVERGED";
+        case DVM_ERR_NONFINITE: return "DVM_ERR_NONFINITE";
+        case DVM_ERR_CUDA: return "DVM_ERR_CUDA";
+        case DVM_ERR_TIMEOUT: return "DVM_ERR_TIMEOUT";
+        case DVM_ERR_STAGNATED: return "DVM_ERR_STAGNATED";
+        default: return "DVM_UNKNOWN_STATUS";
+    }
+}
+
+const char* dvm_last_error(void) { return g_err.c_str(); }
+
+int dvm_context_create(dvm_context** out, int cuda_device, const dvm_options* opt) {
+    if (!out) return fail(DVM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceCount");
+    if (cuda_device < 0 || cuda_device >= ndev) return fail(DVM_ERR_INVALID_ARG, "no such CUDA device");
+    if (opt && opt->graph_iters != 0 && (opt->graph_iters < 2 || opt->graph_iters % 2))
+        return fail(DVM_ERR_INVALID_ARG, "graph_iters must be even and >= 2");
+    DeviceGuard dg(cuda_device);
+    dvm_context* c = new (std::nothrow) dvm_context();
+    if (!c) return fail(DVM_ERR_OOM, "host allocation");
+    c->device = cuda_device;
+    if (opt) {
+        if (opt->graph_iters) c->graph_iters = opt->graph_iters;
+        c->budget = opt->hbm_budget;
+        c->stream = (cudaStream_t)opt->stream;
+    }
+    if (!opt || !opt->stream) {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return fail_cuda(e, "cudaStreamCreate"); }
+        c->own_stream = true;
+    }
+    e = cudaMallocHost((void**)&c->pinned, 64 * sizeof(double));
+    if (e != cudaSuccess) { if (c->own_stream) cudaStreamDestroy(c->stream); delete c; return fail_cuda(e, "cudaMallocHost"); }
+    *out = c;
+    return DVM_OK;
+}
+
+void dvm_context_destroy(dvm_context* c) {
+    if (!c) return;
+    DeviceGuard dg(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+size_t dvm_context_bytes(const dvm_context* c) { return c ? c->bytes : 0; }
+uint64_t dvm_context_launches(const dvm_context* c) { return c ? c->launches : 0; }
+
+// ------------------------------------------------------------------------------------- mesh
+int dvm_mesh_create(dvm_context* ctx, int ni, int nj, const double* X, dvm_mesh** out) {
+    if (!ctx || !X || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (ni < 3 || nj < 1) return fail(DVM_ERR_INVALID_ARG, "mesh needs ni >= 3 and nj >= 1");
+    DeviceGuard dg(ctx->device);
+    const int nc = ni * nj;
+    std::vector<int4> nb(nc);
+    std::vector<double2> S(4 * (size_t)nc);
+    std::vector<double> V(nc);
+    std::vector<float2> Sf(4 * (size_t)nc);
+    std::vector<float> Vf(nc);
+    auto node = [&](int j, int i) { return double2{X[2 * ((size_t)j * ni + i)], X[2 * ((size_t)j * ni + i) + 1]}; };
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+            const int c = j * ni + i, ir = (i + 1) % ni, il = (i + ni - 1) % ni;
+            // corners counter-clockwise: (j,i), (j+1,i), (j+1,i+1), (j,i+1)
+            const double2 q[4] = {node(j, i), node(j + 1, i), node(j + 1, ir), node(j, ir)};
+            double area2 = 0.0;
+            for (int e = 0; e < 4; ++e) {
+                const double2 a = q[e], b = q[(e + 1) & 3];
+                area2 += a.x * b.y - b.x * a.y;
+                S[4 * (size_t)c + e] = double2{b.y - a.y, a.x - b.x};
+                Sf[4 * (size_t)c + e] = float2{(float)(b.y - a.y), (float)(a.x - b.x)};
+            }
+            V[c] = 0.5 * area2;
+            Vf[c] = (float)V[c];
+            if (!(V[c] > 0.0)) {
+                char msg[128];
+                snprintf(msg, sizeof msg, "cell (i=%d, j=%d) has non-positive area %g", i, j, V[c]);
+                return fail(DVM_ERR_INVALID_ARG, msg);
+            }
+            nb[c] = int4{j * ni + il, j + 1 < nj ? (j + 1) * ni + i : kFar, j * ni + ir, j > 0 ? (j - 1) * ni + i : kWall};
+        }
+    dvm_mesh* m = new (std::nothrow) dvm_mesh();
+    if (!m) return fail(DVM_ERR_OOM, "host allocation");
+    m->ctx = ctx;
+    m->d.ni = ni; m->d.nj = nj; m->d.ncell = nc;
+    m->nodes.assign(X, X + 2 * (size_t)(nj + 1) * ni);
+    int rc = DVM_OK;
+    if ((rc = dalloc(ctx, &m->d.nb, nc)) || (rc = dalloc(ctx, &m->d.Sd, 4 * (size_t)nc)) ||
+        (rc = dalloc(ctx, &m->d.Vd, nc)) || (rc = dalloc(ctx, &m->d.Sf, 4 * (size_t)nc)) ||
+        (rc = dalloc(ctx, &m->d.Vf, nc)) || (rc = dalloc(ctx, &m->d.nodes, (size_t)(nj + 1) * ni))) {
+        dvm_mesh_destroy(m);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.nb, nb.data(), nc * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.Sd, S.data(), S.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.Vd, V.data(), nc * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.Sf, Sf.data(), Sf.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.Vf, Vf.data(), nc * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d.nodes, X, (size_t)(nj + 1) * ni * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { dvm_mesh_destroy(m); return fail_cuda(e, "mesh upload"); }
+    *out = m;
+    return DVM_OK;
+}
+
+void dvm_mesh_destroy(dvm_mesh* m) {
+    if (!m) return;
+    DeviceGuard dg(m->ctx->device);
+    dfree(m->d.nb); dfree(m->d.Sd); dfree(m->d.Vd); dfree(m->d.Sf); dfree(m->d.Vf); dfree(m->d.nodes);
+    delete m;
+}
+
+// ------------------------------------------------------------------------------------- velocity grid
+int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* vy, const double* w, dvm_vgrid** out) {
+    if (!ctx || !vx || !vy || !w || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (nv < 1) return fail(DVM_ERR_INVALID_ARG, "nv must be >= 1");
+    for (int k = 0; k < nv; ++k)
+        if (!(w[k] > 0.0) || !std::isfinite(vx[k]) || !std::isfinite(vy[k]))
+            return fail(DVM_ERR_INVALID_ARG, "weights must be positive and velocities finite");
+    DeviceGuard dg(ctx->device);
+    const int nvp = (nv + kPad - 1) / kPad * kPad;
+    std::vector<double4> vd(nvp, double4{0, 0, 0, 0});
+    std::vector<float4> vf(nvp, float4{0, 0, 0, 0});
+    for (int k = 0; k < nv; ++k) {
+        vd[k] = double4{vx[k], vy[k], w[k], 0.5 * (vx[k] * vx[k] + vy[k] * vy[k])};
+        vf[k] = float4{(float)vx[k], (float)vy[k], (float)w[k], (float)vd[k].w};
+    }
+    dvm_vgrid* g = new (std::nothrow) dvm_vgrid();
+    if (!g) return fail(DVM_ERR_OOM, "host allocation");
+    g->ctx = ctx;
+    g->d.nv = nv;
+    g->d.nvp = nvp;
+    int rc;
+    if ((rc = dalloc(ctx, &g->d.vd, nvp)) || (rc = dalloc(ctx, &g->d.vf, nvp))) { dvm_vgrid_destroy(g); return rc; }
+    cudaError_t e = cudaMemcpy(g->d.vd, vd.data(), nvp * sizeof(double4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d.vf, vf.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { dvm_vgrid_destroy(g); return fail_cuda(e, "grid upload"); }
+    *out = g;
+    return DVM_OK;
+}
+
+void dvm_vgrid_destroy(dvm_vgrid* g) {
+    if (!g) return;
+    DeviceGuard dg(g->ctx->device);
+    dfree(g->d.vd); dfree(g->d.vf);
+    delete g;
+}
+
+// ------------------------------------------------------------------------------------- state
+void dvm_state_destroy(dvm_state* st) {
+    if (!st) return;
+    DeviceGuard dg(st->ctx->device);
+    cudaStreamSynchronize(st->ctx->stream);
+    if (st->graph) cudaGraphExecDestroy(st->graph);
+    for (int b = 0; b < 2; ++b) { dfree(st->f[b]); dfree(st->prim[b]); dfree(st->Fw[b]); }
+    dfree(st->Jpart); dfree(st->respart); dfree(st->out); dfree(st->scratch);
+    dfree(st->fl.fdd); dfree(st->fl.fdf); dfree(st->fl.gwd); dfree(st->fl.gwf); dfree(st->fl.wallD); dfree(st->fl.wallM);
+    st->ctx->bytes -= st->bytes;
+    delete st;
+}
+
+static size_t state_bytes(const dvm_mesh* m, const dvm_vgrid* g, int storage) {
+    return 2 * (size_t)m->d.ncell * g->d.nvp * storage_bytes(storage) + (size_t)m->d.ncell * (2 * 32 + 8) +
+           (size_t)m->d.ni * 48 + (size_t)g->d.nvp * 48;
+}
+
+int dvm_state_create(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid, const dvm_flow* flow,
+                     int storage, dvm_state** out) {
+    if (!ctx || !mesh || !grid || !flow || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (storage < 0 || storage > 2) return fail(DVM_ERR_INVALID_ARG, "unknown storage");
+    if (!(flow->Kn > 0.0) || !(flow->Ma >= 0.0) || !(flow->Tw > 0.0) || !std::isfinite(flow->aoa))
+        return fail(DVM_ERR_INVALID_ARG, "flow needs Kn > 0, Ma >= 0, Tw > 0");
+    if (mesh->ctx != ctx || grid->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "mesh/grid from another context");
+    const size_t need = state_bytes(mesh, grid, storage);
+    if (ctx->budget && ctx->bytes + need > ctx->budget)
+        return fail(DVM_ERR_ADMISSION, "state does not fit the context's HBM budget");
+    DeviceGuard dg(ctx->device);
+    dvm_state* st = new (std::nothrow) dvm_state();
+    if (!st) return fail(DVM_ERR_OOM, "host allocation");
+    st->ctx = ctx; st->mesh = mesh; st->grid = grid; st->flow = *flow; st->storage = storage;
+    const DevMesh& m = mesh->d;
+    const DevGrid& g = grid->d;
+    st->fl.tau_inf = 5.0 / 16.0 * flow->Kn * sqrt(2.0 * M_PI);
+    const double U = flow->Ma * sqrt(5.0 / 3.0);
+    st->fl.u1 = U * cos(flow->aoa);
+    st->fl.u2 = U * sin(flow->aoa);
+    st->fl.Tw = flow->Tw;
+    st->fl.Ma = flow->Ma;
+    st->fl.aoa = flow->aoa;
+    size_t acc = 0;
+    const size_t pair = storage_bytes(storage), nfp = (size_t)m.ncell * g.nvp;
+    int rc = DVM_OK;
+    auto bail = [&](int r) { st->bytes = 0; dvm_state_destroy(st); return r; };
+    for (int b = 0; b < 2 && !rc; ++b) {
+        rc = dalloc(ctx, (unsigned char**)&st->f[b], nfp * pair, &acc);
+        if (!rc) rc = dalloc(ctx, &st->prim[b], m.ncell, &acc);
+        if (!rc) rc = dalloc(ctx, &st->Fw[b], m.ni, &acc);
+    }
+    if (!rc) rc = dalloc(ctx, &st->Jpart, m.ni, &acc);
+    if (!rc) rc = dalloc(ctx, &st->respart, m.ncell, &acc);
+    if (!rc) rc = dalloc(ctx, &st->out, 2, &acc);
+    if (!rc) rc = dalloc(ctx, &st->scratch, (size_t)m.ni + 2, &acc);
+    if (!rc) rc = dalloc(ctx, &st->fl.fdd, g.nvp, &acc);
+    if (!rc) rc = dalloc(ctx, &st->fl.fdf, g.nvp, &acc);
+    if (!rc) rc = dalloc(ctx, &st->fl.gwd, g.nvp, &acc);
+    if (!rc) rc = dalloc(ctx, &st->fl.gwf, g.nvp, &acc);
+    if (!rc) rc = dalloc(ctx, &st->fl.wallD, m.ni, &acc);
+    if (!rc) rc = dalloc(ctx, &st->fl.wallM, m.ni, &acc);
+    if (rc) return bail(rc);
+    st->bytes = acc;
+    ctx->bytes += acc;
+    cudaStream_t s = ctx->stream;
+    const double ang = dir_angle(*flow, DVM_DRAG);
+    cudaError_t e = launch_flow_tables(g, st->fl, s);
+    if (e == cudaSuccess) e = launch_wall_setup(m, g, st->fl, cos(ang), sin(ang), st->fl.wallD, st->fl.wallM, s);
+    if (e == cudaSuccess) e = launch_fill_freestream(storage, st->f[0], m.ncell, g, st->fl, s);
+    if (e == cudaSuccess) e = launch_moments(storage, st->f[0], m, g, st->prim[0], st->Fw[0], s);
+    ctx->launches += 5;
+    if (e != cudaSuccess) return bail(fail_cuda(e, "state setup"));
+    // r0: residual of the free-stream state, from one sweep whose output is discarded
+    e = enqueue_primal(st, 0);
+    if (e == cudaSuccess) e = enqueue_primal_finalize(st, 1, st->out);
+    ctx->launches += 2;
+    if (e != cudaSuccess) return bail(fail_cuda(e, "r0 sweep"));
+    double r[2];
+    if ((rc = fetch2(ctx, st->out, r))) return bail(rc);
+    st->r0 = sqrt(r[0]);
+    if (!std::isfinite(st->r0) || st->r0 <= 0.0) return bail(fail(DVM_ERR_NONFINITE, "free-stream residual not finite"));
+    *out = st;
+    return DVM_OK;
+}
+
+int dvm_state_set(dvm_state* st, const double* f_host) {
+    if (!st || !f_host) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(st->ctx->device);
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    double* tmp = nullptr;
+    const size_t n = (size_t)m.ncell * g.nv * 2;
+    int rc = dalloc(st->ctx, &tmp, n);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(tmp, f_host, n * sizeof(double), cudaMemcpyHostToDevice, st->ctx->stream);
+    if (e == cudaSuccess) e = launch_convert(st->storage, 1, tmp, st->f[st->cur], m.ncell, g.nv, g.nvp, st->ctx->stream);
+    if (e == cudaSuccess) e = launch_moments(st->storage, st->f[st->cur], m, g, st->prim[st->cur], st->Fw[st->cur], st->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
+    st->ctx->launches += 2;
+    st->version += 1;
+    dfree(tmp);
+    if (e != cudaSuccess) return fail_cuda(e, "state upload");
+    return DVM_OK;
+}
+
+int dvm_state_get(const dvm_state* st, double* f_host) {
+    if (!st || !f_host) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(st->ctx->device);
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    double* tmp = nullptr;
+    const size_t n = (size_t)m.ncell * g.nv * 2;
+    int rc = dalloc(st->ctx, &tmp, n);
+    if (rc) return rc;
+    cudaError_t e = launch_convert(st->storage, 0, st->f[st->cur], tmp, m.ncell, g.nv, g.nvp, st->ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
+    st->ctx->launches += 1;
+    dfree(tmp);
+    if (e != cudaSuccess) return fail_cuda(e, "state download");
+    return DVM_OK;
+}
+
+int dvm_state_moments(const dvm_state* st, double* prim_host) {
+    if (!st || !prim_host) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(st->ctx->device);
+    CK(cudaMemcpyAsync(prim_host, st->prim[st->cur], st->mesh->d.ncell * sizeof(double4), cudaMemcpyDeviceToHost,
+                       st->ctx->stream));
+    CK(cudaStreamSynchronize(st->ctx->stream));
+    return DVM_OK;
+}
+
+int dvm_primal_iterate(dvm_state* st, int n, double* residual_out) {
+    if (!st || n < 0) return fail(DVM_ERR_INVALID_ARG, "bad argument");
+    if (n == 0) return DVM_OK;
+    DeviceGuard dg(st->ctx->device);
+    double* hist = nullptr;
+    int rc = dalloc(st->ctx, &hist, 2 * (size_t)n);
+    if (rc) return rc;
+    rc = run_primal_plain(st, n, hist);
+    if (!rc) {
+        std::vector<double> h(2 * (size_t)n);
+        cudaError_t e = cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "residual history");
+        for (int i = 0; i < n && !rc; ++i) {
+            const double r = sqrt(h[2 * i]) / st->r0;
+            if (residual_out) residual_out[i] = r;
+            if (!std::isfinite(r)) rc = fail(DVM_ERR_NONFINITE, "residual is not finite");
+        }
+    }
+    dfree(hist);
+    return rc;
+}
+
+int dvm_state_functional(dvm_state* st, int functional, double* J) {
+    if (!st || !J) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(st->ctx->device);
+    const double ang = dir_angle(st->flow, functional);
+    CK(launch_functional(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->fl, st->Fw[st->cur], cos(ang),
+                         sin(ang), st->scratch, st->scratch + st->mesh->d.ni, st->ctx->stream));
+    st->ctx->launches += 2;
+    double r[2];
+    int rc = fetch2(st->ctx, st->scratch + st->mesh->d.ni, r);
+    if (rc) return rc;
+    *J = r[1];
+    return DVM_OK;
+}
+
+int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid, const dvm_flow* flow,
+                     const dvm_solve_opts* opts, int storage, dvm_state** inout, dvm_primal_result* res) {
+    if (!ctx || !mesh || !grid || !flow || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (opts->max_iter < 0 || !(opts->tol >= 0.0)) return fail(DVM_ERR_INVALID_ARG, "bad solve options");
+    DeviceGuard dg(ctx->device);
+    std::memset(res, 0, sizeof(*res));
+    int rc;
+    if (!*inout) {
+        if ((rc = dvm_state_create(ctx, mesh, grid, flow, storage, inout))) return rc;
+    } else {
+        const dvm_state* s = *inout;
+        if (s->mesh != mesh || s->grid != grid || s->ctx != ctx)
+            return fail(DVM_ERR_INVALID_ARG, "warm-start state belongs to another mesh/grid/context");
+        if (s->flow.Kn != flow->Kn || s->flow.Ma != flow->Ma || s->flow.Tw != flow->Tw || s->flow.aoa != flow->aoa)
+            return fail(DVM_ERR_INVALID_ARG, "warm-start state has another flow; create a new state");
+    }
+    dvm_state* st = *inout;
+    const int K = ctx->graph_iters;
+    const bool use_graph = graphs_ok(ctx);
+    int it = 0;
+    double r = INFINITY, best = INFINITY, J = 0.0;
+    int best_it = 0;
+    int status = DVM_NOT_CONVERGED;
+    while (it < opts->max_iter) {
+        const int k = std::min(K, opts->max_iter - it);
+        if (use_graph && k == K) {
+            if ((rc = build_primal_graph(st, K))) return rc;
+            CK(cudaGraphLaunch(st->graph, ctx->stream));
+            ctx->launches += K + 1;
+            st->version += (uint64_t)K;
+        } else if ((rc = run_primal_plain(st, k, nullptr))) {
+            return rc;
+        }
+        it += k;
+        double o[2];
+        if ((rc = fetch2(ctx, st->out, o))) return rc;
+        r = sqrt(o[0]) / st->r0;
+        J = o[1];
+        if (!std::isfinite(r) || !std::isfinite(J)) { status = DVM_ERR_NONFINITE; fail(status, "residual is not finite"); break; }
+        if (r <= opts->tol) { status = DVM_OK; break; }
+        if (r < 0.98 * best) { best = r; best_it = it; }
+        if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
+    }
+    if (opts->max_iter == 0) {
+        if ((rc = dvm_state_functional(st, DVM_DRAG, &J))) return rc;
+        r = NAN;
+    }
+    res->J = J;
+    const double U = flow->Ma * sqrt(5.0 / 3.0);
+    res->Cd = U > 0.0 ? J / (0.5 * U * U) : J;
+    res->residual = r;
+    res->r0 = st->r0;
+    res->iters = it;
+    res->status = status;
+    return status;
+}
+
+// ------------------------------------------------------------------------------------- adjoint
+void dvm_adjoint_destroy(dvm_adjoint* ad) {
+    if (!ad) return;
+    DeviceGuard dg(ad->st->ctx->device);
+    cudaStreamSynchronize(ad->st->ctx->stream);
+    if (ad->graph) cudaGraphExecDestroy(ad->graph);
+    for (int b = 0; b < 2; ++b) { dfree(ad->phi[b]); dfree(ad->Z[b]); dfree(ad->Lam[b]); }
+    dfree(ad->respart); dfree(ad->out); dfree(ad->wallM); dfree(ad->cell);
+    dfree(ad->GN); dfree(ad->GE); dfree(ad->GW); dfree(ad->node_grad); dfree(ad->vol); dfree(ad->elem);
+    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad);
+    ad->st->ctx->bytes -= ad->bytes;
+    delete ad;
+}
+
+static int adjoint_reset(dvm_adjoint* ad) {
+    const DevMesh& m = ad->st->mesh->d;
+    const DevGrid& g = ad->st->grid->d;
+    cudaStream_t s = ad->st->ctx->stream;
+    ad->cur = 0;
+    CK(cudaMemsetAsync(ad->phi[0], 0, (size_t)m.ncell * g.nvp * storage_bytes(ad->st->storage), s));
+    CK(cudaMemsetAsync(ad->Z[0], 0, m.ncell * sizeof(double4), s));
+    CK(cudaMemsetAsync(ad->Lam[0], 0, m.ni * sizeof(double), s));
+    return DVM_OK;
+}
+
+int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
+    if (!st || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (functional != DVM_DRAG && functional != DVM_LIFT) return fail(DVM_ERR_INVALID_ARG, "unknown functional");
+    *out = nullptr;
+    dvm_context* ctx = st->ctx;
+    DeviceGuard dg(ctx->device);
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    const size_t need = (size_t)m.ncell * g.nvp * storage_bytes(st->storage) * 2 + (size_t)m.ncell * 72;
+    if (ctx->budget && ctx->bytes + need > ctx->budget)
+        return fail(DVM_ERR_ADMISSION, "adjoint does not fit the context's HBM budget");
+    dvm_adjoint* ad = new (std::nothrow) dvm_adjoint();
+    if (!ad) return fail(DVM_ERR_OOM, "host allocation");
+    ad->st = st;
+    ad->functional = functional;
+    const double ang = dir_angle(st->flow, functional);
+    ad->dirx = cos(ang);
+    ad->diry = sin(ang);
+    size_t acc = 0;
+    int rc = DVM_OK;
+    for (int b = 0; b < 2 && !rc; ++b) {
+        rc = dalloc(ctx, (unsigned char**)&ad->phi[b], (size_t)m.ncell * g.nvp * storage_bytes(st->storage), &acc);
+        if (!rc) rc = dalloc(ctx, &ad->Z[b], m.ncell, &acc);
+        if (!rc) rc = dalloc(ctx, &ad->Lam[b], m.ni, &acc);
+    }
+    if (!rc) rc = dalloc(ctx, &ad->respart, m.ncell, &acc);
+    if (!rc) rc = dalloc(ctx, &ad->out, 2, &acc);
+    if (!rc) rc = dalloc(ctx, &ad->wallM, m.ni, &acc);
+    if (!rc) rc = dalloc(ctx, (unsigned char**)&ad->cell,
+                         (size_t)m.ncell * 16 * (st->storage == DVM_STORE_FP64 ? sizeof(double) : sizeof(float)), &acc);
+    if (rc) { dvm_adjoint_destroy(ad); return rc; }
+    ad->bytes = acc;
+    ctx->bytes += acc;
+    // M_l of this functional's direction (the normaliser D_l is the state's; recomputed into scratch)
+    double* dtmp = nullptr;
+    if ((rc = dalloc(ctx, &dtmp, m.ni))) { dvm_adjoint_destroy(ad); return rc; }
+    cudaError_t e = launch_wall_setup(m, g, st->fl, ad->dirx, ad->diry, dtmp, ad->wallM, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    ctx->launches += 1;
+    dfree(dtmp);
+    if (e != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(e, "adjoint setup"); }
+    if ((rc = adjoint_reset(ad))) { dvm_adjoint_destroy(ad); return rc; }
+    if ((e = adjoint_relinearise(ad)) != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(e, "adjoint constants"); }
+    // r0: adjoint residual at phi = 0 from one discarded sweep
+    e = enqueue_adjoint(ad, 0);
+    if (e == cudaSuccess) e = enqueue_adjoint_finalize(ad, ad->out);
+    ctx->launches += 2;
+    if (e != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(e, "adjoint r0"); }
+    double r[2];
+    if ((rc = fetch2(ctx, ad->out, r))) { dvm_adjoint_destroy(ad); return rc; }
+    ad->r0 = sqrt(r[0]);
+    if (!std::isfinite(ad->r0)) { dvm_adjoint_destroy(ad); return fail(DVM_ERR_NONFINITE, "adjoint source not finite"); }
+    if (ad->r0 == 0.0) ad->r0 = 1.0;
+    *out = ad;
+    return DVM_OK;
+}
+
+int dvm_adjoint_set(dvm_adjoint* ad, const double* phi_host) {
+    if (!ad || !phi_host) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(ad->st->ctx->device);
+    const DevMesh& m = ad->st->mesh->d;
+    const DevGrid& g = ad->st->grid->d;
+    cudaStream_t s = ad->st->ctx->stream;
+    double* tmp = nullptr;
+    const size_t n = (size_t)m.ncell * g.nv * 2;
+    int rc = dalloc(ad->st->ctx, &tmp, n);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(tmp, phi_host, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_convert(ad->st->storage, 1, tmp, ad->phi[ad->cur], m.ncell, g.nv, g.nvp, s);
+    if (e == cudaSuccess) e = refresh_adjoint_couplings(ad);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(tmp);
+    if (e != cudaSuccess) return fail_cuda(e, "adjoint upload");
+    return DVM_OK;
+}
+
+int dvm_adjoint_get(const dvm_adjoint* ad, double* phi_host) {
+    if (!ad || !phi_host) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(ad->st->ctx->device);
+    const DevMesh& m = ad->st->mesh->d;
+    const DevGrid& g = ad->st->grid->d;
+    cudaStream_t s = ad->st->ctx->stream;
+    double* tmp = nullptr;
+    const size_t n = (size_t)m.ncell * g.nv * 2;
+    int rc = dalloc(ad->st->ctx, &tmp, n);
+    if (rc) return rc;
+    cudaError_t e = launch_convert(ad->st->storage, 0, ad->phi[ad->cur], tmp, m.ncell, g.nv, g.nvp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(tmp);
+    if (e != cudaSuccess) return fail_cuda(e, "adjoint download");
+    return DVM_OK;
+}
+
+static int adjoint_follow_state(dvm_adjoint* ad) {
+    if (ad->st_version == ad->st->version) return DVM_OK;
+    CK(adjoint_relinearise(ad));
+    CK(refresh_adjoint_couplings(ad));
+    return DVM_OK;
+}
+
+int dvm_adjoint_iterate(dvm_adjoint* ad, int n, double* residual_out) {
+    if (!ad || n < 0) return fail(DVM_ERR_INVALID_ARG, "bad argument");
+    if (n == 0) return DVM_OK;
+    DeviceGuard dg(ad->st->ctx->device);
+    int rc0 = adjoint_follow_state(ad);
+    if (rc0) return rc0;
+    double* hist = nullptr;
+    int rc = dalloc(ad->st->ctx, &hist, 2 * (size_t)n);
+    if (rc) return rc;
+    rc = run_adjoint_plain(ad, n, hist);
+    if (!rc) {
+        std::vector<double> h(2 * (size_t)n);
+        cudaError_t e = cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ad->st->ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ad->st->ctx->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "residual history");
+        for (int i = 0; i < n && !rc; ++i) {
+            const double r = sqrt(h[2 * i]) / ad->r0;
+            if (residual_out) residual_out[i] = r;
+            if (!std::isfinite(r)) rc = fail(DVM_ERR_NONFINITE, "adjoint residual is not finite");
+        }
+    }
+    dfree(hist);
+    return rc;
+}
+
+int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm_solve_opts* opts,
+                      dvm_adjoint** inout, dvm_adjoint_result* res) {
+    if (!ctx || !st || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "state from another context");
+    DeviceGuard dg(ctx->device);
+    std::memset(res, 0, sizeof(*res));
+    int rc;
+    if (!*inout) {
+        if ((rc = dvm_adjoint_create(st, functional, inout))) return rc;
+    } else if ((*inout)->st != st || (*inout)->functional != functional) {
+        return fail(DVM_ERR_INVALID_ARG, "warm-start adjoint belongs to another state/functional");
+    }
+    dvm_adjoint* ad = *inout;
+    if ((rc = adjoint_follow_state(ad))) return rc;
+    const int K = ctx->graph_iters;
+    const bool use_graph = graphs_ok(ctx);
+    int it = 0, best_it = 0;
+    double r = INFINITY, best = INFINITY;
+    int status = DVM_NOT_CONVERGED;
+    while (it < opts->max_iter) {
+        const int k = std::min(K, opts->max_iter - it);
+        if (use_graph && k == K) {
+            if ((rc = build_adjoint_graph(ad, K))) return rc;
+            CK(cudaGraphLaunch(ad->graph, ctx->stream));
+            ctx->launches += K + 1;
+        } else if ((rc = run_adjoint_plain(ad, k, nullptr))) {
+            return rc;
+        }
+        it += k;
+        double o[2];
+        if ((rc = fetch2(ctx, ad->out, o))) return rc;
+        r = sqrt(o[0]) / ad->r0;
+        if (!std::isfinite(r)) { status = DVM_ERR_NONFINITE; fail(status, "adjoint residual is not finite"); break; }
+        if (r <= opts->tol) { status = DVM_OK; break; }
+        if (r < 0.98 * best) { best = r; best_it = it; }
+        if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
+    }
+    res->residual = r;
+    res->r0 = ad->r0;
+    res->iters = it;
+    res->status = status;
+    return status;
+}
+
+// ------------------------------------------------------------------------------------- sensitivity
+int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* cad, int P, const double* dwall,
+                    const double* s_j, int mode, double* grad_out, double* node_grad_out) {
+    if (!ctx || !st || !cad || (P > 0 && (!dwall || !grad_out))) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (mode != DVM_SENS_PAPER && mode != DVM_SENS_FULL) return fail(DVM_ERR_INVALID_ARG, "unknown mode");
+    if (mode == DVM_SENS_FULL && !s_j) return fail(DVM_ERR_INVALID_ARG, "full mode needs s_j");
+    if (cad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
+    if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
+    DeviceGuard dg(ctx->device);
+    dvm_adjoint* ad = const_cast<dvm_adjoint*>(cad);
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    cudaStream_t s = ctx->stream;
+    int rc = DVM_OK;
+    const int nnodes = (m.nj + 1) * m.ni;
+    if (!ad->GN) {
+        size_t acc = 0;
+        if ((rc = dalloc(ctx, &ad->GN, m.ncell, &acc)) || (rc = dalloc(ctx, &ad->GE, m.ncell, &acc)) ||
+            (rc = dalloc(ctx, &ad->GW, m.ni, &acc)) || (rc = dalloc(ctx, &ad->node_grad, nnodes, &acc)) ||
+            (rc = dalloc(ctx, &ad->vol, m.ncell, &acc)) || (rc = dalloc(ctx, &ad->elem, 5 * (size_t)m.ni, &acc)) ||
+            (rc = dalloc(ctx, &ad->sj, m.nj + 1, &acc)))
+            return rc;
+        ad->bytes += acc;
+        ctx->bytes += acc;
+    }
+    if (P > ad->sens_P) {
+        dfree(ad->dwall); dfree(ad->grad);
+        ad->dwall = nullptr; ad->grad = nullptr;
+        if ((rc = dalloc(ctx, &ad->dwall, (size_t)P * m.ni * 2)) || (rc = dalloc(ctx, &ad->grad, P))) return rc;
+        ad->sens_P = P;
+    }
+    if (P > 0) CK(cudaMemcpyAsync(ad->dwall, dwall, (size_t)P * m.ni * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    const void* f = st->f[st->cur];
+    const void* phi = ad->phi[ad->cur];
+    if (mode == DVM_SENS_PAPER) {
+        CK(launch_sens_paper(st->storage, m, g, st->fl, f, phi, st->Fw[st->cur], ad->dirx, ad->diry, ad->elem,
+                             (double*)ad->node_grad, s));
+        CK(launch_contract(ad->node_grad, 1, m.ni, nullptr, ad->dwall, P, ad->grad, s));
+        ctx->launches += 2 + (P > 0);
+        if (node_grad_out)
+            CK(cudaMemcpyAsync(node_grad_out, ad->node_grad, (size_t)m.ni * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    } else {
+        CK(cudaMemcpyAsync(ad->sj, s_j, (m.nj + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->dirx, ad->diry,
+                            ad->GN, ad->GE, ad->GW, ad->vol, ad->node_grad, s));
+        CK(launch_contract(ad->node_grad, m.nj + 1, m.ni, ad->sj, ad->dwall, P, ad->grad, s));
+        ctx->launches += 2 + (P > 0);
+        if (node_grad_out)
+            CK(cudaMemcpyAsync(node_grad_out, ad->node_grad, (size_t)nnodes * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (P > 0) CK(cudaMemcpyAsync(grad_out, ad->grad, P * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DVM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations of the DVM CUDA library: device-side data of meshes, velocity grids,
+// states and adjoints, and the kernel launchers.  Not part of the C ABI (see include/dvm.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstddef>
+#include <cstdint>
+#include <type_traits>
+
+namespace dvm {
+
+constexpr int kWall = -1;            // neighbour code of a wall face
+constexpr int kFar = -2;             // neighbour code of a far-field face
+constexpr int kWarpsPerBlock = 8;    // one warp per cell, 8 cells per 256-thread block
+constexpr int kPad = 4;              // velocity count padded to a multiple of this
+
+// Geometry of an O-mesh on the device.  Face e of cell c: 0 -> (i-1,j), 1 -> (i,j+1) or far field,
+// 2 -> (i+1,j), 3 -> (i,j-1) or wall.  S = A n points out of the cell (into the solid on the wall).
+struct DevMesh {
+    int ni = 0, nj = 0, ncell = 0;
+    int4* nb = nullptr;         // [ncell]  (face0, face1, face2, face3) neighbour or kWall/kFar
+    double2* Sd = nullptr;      // [ncell*4]
+    double* Vd = nullptr;       // [ncell]
+    float2* Sf = nullptr;       // [ncell*4]
+    float* Vf = nullptr;        // [ncell]
+    double2* nodes = nullptr;   // [(nj+1)*ni]
+};
+
+// Velocity list padded with zero-weight, zero-velocity entries: (vx, vy, w, |v|^2/2).
+struct DevGrid {
+    int nv = 0, nvp = 0;
+    double4* vd = nullptr;      // [nvp]
+    float4* vf = nullptr;       // [nvp]
+};
+
+// Per-flow tables for one state.
+struct DevFlow {
+    double tau_inf = 0, u1 = 0, u2 = 0, Tw = 1, Ma = 0, aoa = 0;
+    double2* fdd = nullptr;     // [nvp] far-field Maxwellian (g1, g2)
+    float2* fdf = nullptr;
+    double* gwd = nullptr;      // [nvp] wall Maxwellian g_M1(1, 0, Tw), unnormalised
+    float* gwf = nullptr;
+    double* wallD = nullptr;    // [ni] normaliser D_l = -sum_{a<=0} w (v.n) g_M1
+    double* wallM = nullptr;    // [ni] M_l = sum_{a<=0} w m a g_M1 / D_l for the drag direction
+};
+
+// Arguments of the primal sweep.  TS = storage type, TC = compute type.
+template <class TS, class TC>
+struct PrimalArgs {
+    int ncell, nq;                          // nq = nvp / KV  (16-byte chunks per cell)
+    const int4* nb;
+    const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
+    const TC* V;
+    const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
+    const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* fd;
+    const TC* gw;
+    const double* wallD;
+    double inv_tau_inf;
+    TC halfTw, dirx, diry;
+    const TS* f_old;
+    TS* f_new;
+    const double4* prim_old;
+    double4* prim_new;
+    const double* Fw_old;
+    double* Fw_new;
+    double* Jpart;
+    double* respart;
+};
+
+// Per-cell constants of the adjoint linearisation (see k_adjoint_cellconst).
+template <class TC>
+struct alignas(sizeof(TC) * 4) AdjCell {
+    TC n0, inv2T, halfT, Vt, u1, u2, ir, iT, iT2h, c0, c3, j30, j31, j32, j33, pad;
+};
+
+template <class TS, class TC>
+struct AdjointArgs {
+    int ncell, nq;
+    const int4* nb;
+    const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
+    const TC* V;
+    const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
+    const TC* gw;
+    const double* wallD;
+    const double* wallM;                    // for the functional's direction
+    double inv_tau_inf;
+    TC halfTw, dirx, diry;
+    const TS* f;                            // primal state (fixed)
+    const AdjCell<TC>* cell;                // constants of the linearisation at that state
+    const TS* phi_old;
+    TS* phi_new;
+    const double4* Z_old;                   // collision coupling (W space) of the previous sweep
+    double4* Z_new;
+    const double* Lam_old;                  // wall coupling of the previous sweep
+    double* Lam_new;
+    double* respart;
+};
+
+// ---------------------------------------------------------------------------------- launchers
+// All launchers enqueue on `s` and return cudaGetLastError().
+cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s);
+cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, double dirx,
+                              double diry, double* wallD, double* wallM, cudaStream_t s);
+cudaError_t launch_fill_freestream(int storage, void* f, int ncell, const DevGrid& g, const DevFlow& fl,
+                                   cudaStream_t s);
+cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
+                           double* Fw, cudaStream_t s);
+// res = false: skip the residual (only the sweeps whose residual is read need it)
+cudaError_t launch_primal_sweep(int storage, const void* args, bool res, cudaStream_t s);
+// update = false: no phi update, only the couplings (Z, Lambda) of phi_old into the *_new slots
+cudaError_t launch_adjoint_sweep(int storage, const void* args, bool update, bool res, cudaStream_t s);
+cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
+                                     void* out, cudaStream_t s);
+// out[0] = sum respart; out[1] = sum_l Jpart_l + Fw_l M_l (Fw/M may be null -> only sum Jpart)
+cudaError_t launch_finalize(const double* respart, int ncell, const double* Jpart, const double* Fw,
+                            const double* M, int ni, double* out, cudaStream_t s);
+cudaError_t launch_functional(int storage, const void* f, const DevMesh& m, const DevGrid& g,
+                              const DevFlow& fl, const double* Fw, double dirx, double diry,
+                              double* face_out, double* out, cudaStream_t s);
+// direction 0: device storage [ncell][nvp] -> double [ncell][nv]; 1: double [ncell][nv] -> storage [ncell][nvp]
+cudaError_t launch_convert(int storage, int direction, const void* src, void* dst, int ncell, int nv,
+                           int nvp, cudaStream_t s);
+// sensitivities
+cudaError_t launch_sens_paper(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
+                              const void* f, const void* phi, const double* Fw, double dirx, double diry,
+                              double* elem, double* node_grad, cudaStream_t s);
+cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
+                             const void* f, const void* phi, const double4* prim, const double* Fw,
+                             double dirx, double diry, double2* GN, double2* GE, double2* GW,
+                             double* vol, double2* node_grad, cudaStream_t s);
+cudaError_t launch_contract(const double2* node_grad, int nrows, int ni, const double* s_j,
+                            const double* dwall, int P, double* grad, cudaStream_t s);
+
+size_t storage_bytes(int storage);   // bytes of one (f1,f2) pair
+
+}  // namespace dvm

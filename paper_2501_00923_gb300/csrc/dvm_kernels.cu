@@ -1,0 +1,1061 @@
+// CUDA kernels (sm_103a) of the DVM-BGK primal sweep, the transposed adjoint sweep, the wall
+// reductions and the boundary sensitivities (Yuan & Wu, arXiv 2501.00923, Sec. 2-3).
+//
+// Layout: f[cell][k] = (f1, f2) pairs in the storage type, velocity fastest, nv padded to a
+// multiple of 4.  One warp owns one cell and walks its velocities in 16-byte chunks (1 pair in
+// FP64, 2 in FP32, 4 in BF16), so every load and store of a warp is 512 contiguous bytes.  Because
+// a warp holds all velocities of its cell, the velocity-space reductions (moments W, the wall
+// density F_rhow, the adjoint What / rhohat / Lambda, the residual) finish inside the warp with
+// no cross-block step: per-lane FP32 Kahan sums (FP64 sums for FP64 storage) combined in FP64 by a
+// fixed butterfly, so results are deterministic.
+#include "dvm_internal.h"
+
+#include <cstring>
+#include <type_traits>
+
+namespace dvm {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+template <class T> struct Vec;
+template <> struct Vec<float> { using v2 = float2; using v4 = float4; };
+template <> struct Vec<double> { using v2 = double2; using v4 = double4; };
+
+// ------------------------------------------------------------------ 16-byte chunks of (f1,f2)
+template <class TS> struct Pack;
+template <> struct Pack<double> {
+    using TC = double;
+    static constexpr int KV = 1;
+    __device__ static void unpack(const uint4& r, double (&a)[1], double (&b)[1]) {
+        a[0] = __hiloint2double((int)r.y, (int)r.x);
+        b[0] = __hiloint2double((int)r.w, (int)r.z);
+    }
+    __device__ static uint4 pack(const double (&a)[1], const double (&b)[1]) {
+        uint4 r;
+        r.x = (unsigned)__double2loint(a[0]); r.y = (unsigned)__double2hiint(a[0]);
+        r.z = (unsigned)__double2loint(b[0]); r.w = (unsigned)__double2hiint(b[0]);
+        return r;
+    }
+};
+template <> struct Pack<float> {
+    using TC = float;
+    static constexpr int KV = 2;
+    __device__ static void unpack(const uint4& r, float (&a)[2], float (&b)[2]) {
+        a[0] = __uint_as_float(r.x); b[0] = __uint_as_float(r.y);
+        a[1] = __uint_as_float(r.z); b[1] = __uint_as_float(r.w);
+    }
+    __device__ static uint4 pack(const float (&a)[2], const float (&b)[2]) {
+        return make_uint4(__float_as_uint(a[0]), __float_as_uint(b[0]), __float_as_uint(a[1]),
+                          __float_as_uint(b[1]));
+    }
+};
+template <> struct Pack<__nv_bfloat16> {
+    using TC = float;
+    static constexpr int KV = 4;
+    __device__ static void unpack(const uint4& r, float (&a)[4], float (&b)[4]) {
+        const unsigned wd[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            a[i] = __uint_as_float(wd[i] << 16);
+            b[i] = __uint_as_float(wd[i] & 0xffff0000u);
+        }
+    }
+    __device__ static uint4 pack(const float (&a)[4], const float (&b)[4]) {
+        unsigned wd[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(a[i], b[i]);
+            unsigned u;
+            memcpy(&u, &h, 4);
+            wd[i] = u;
+        }
+        return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+};
+
+// ------------------------------------------------------------------ accumulators
+template <class T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ void add(double x) { s += x; }
+    __device__ double get() const { return s; }
+};
+// Kahan-compensated FP32 sum: error independent of the number of terms.
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double get() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint4 ldg16(const uint4* p) { return __ldg(p); }
+__device__ __forceinline__ void stg16(uint4* p, const uint4& v) { __stcs(p, v); }
+
+template <class TC> __device__ __forceinline__ TC dexp(TC x);
+template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+
+template <class TC> __device__ __forceinline__ TC pos(TC a) { return a > TC(0) ? a : TC(0); }
+
+__device__ __forceinline__ double todbl(double x) { return x; }
+__device__ __forceinline__ double todbl(float x) { return (double)x; }
+__device__ __forceinline__ double todbl(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+template <class T> __device__ __forceinline__ T fromdbl(double x);
+template <> __device__ __forceinline__ double fromdbl<double>(double x) { return x; }
+template <> __device__ __forceinline__ float fromdbl<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 fromdbl<__nv_bfloat16>(double x) {
+    return __float2bfloat16_rn((float)x);
+}
+
+// ------------------------------------------------------------------ FP32 fast paths
+// In the FP32/BF16 path the exponential and the reciprocal use the hardware approximations
+// (__expf: 2 + 1.2|x| ulp; __fdividef: 2 ulp), well inside the storage rounding of the values they
+// produce; the FP64 path uses the correctly rounded library functions.
+template <class TC> __device__ __forceinline__ TC fexp(TC x);
+template <> __device__ __forceinline__ float fexp<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double fexp<double>(double x) { return exp(x); }
+template <class TC> __device__ __forceinline__ TC frcp(TC x);
+template <> __device__ __forceinline__ float frcp<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ double frcp<double>(double x) { return 1.0 / x; }
+
+// Double-float (hi + lo) value and its exact-error addition (two-sum), used to combine the
+// compensated per-lane sums across a warp with FP32 instructions only.
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float h = s + e;
+    return DF{h, e - (h - s)};
+}
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+// Per-lane sum, then warp total (same value on every lane, fixed order).
+template <class TC> struct Sum;
+template <> struct Sum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double total() const { return warp_sum(s); }
+};
+template <> struct Sum<float> {      // Kahan-compensated lane sum, double-float warp combine
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float total() const {
+        const DF d = warp_sum_df(DF{s, -c});
+        return d.hi + d.lo;
+    }
+};
+
+// Boundary class of a cell, fixed per warp: interior, wall row (j = 0), far-field row (j = nj-1),
+// or both (a one-layer mesh).  Each class gets its own compiled loop so that interior cells, which
+// are all but 2/nj of the mesh, carry no boundary logic.
+enum { kInterior = 0, kWallCell = 1, kFarCell = 2, kWallFar = 3 };
+constexpr int kBlockIters = 8;   // chunks summed in FP32 before one compensated add
+
+// ================================================================== primal sweep (K1)
+// One point-implicit sweep of Eq. (numerpr_gov), first-order upwind, fused with the moments of
+// the new state (Eq. macint_reduce), its wall density (Eq. formula_bgk_fdw), the drag partial of
+// Eq. (numer_J) and (kRes) the residual R(f_old) = D (f_old - f_new).
+// D = V/tau + sum_e max(a_e, 0) = V/tau + (1/2) sum_e |a_e| because the faces of a cell close
+// (sum_e A_e n_e = 0); the inflow faces add -min(a_e, 0) F_up to the right-hand side.  Neighbour
+// chunks are loaded whether or not a face is an inflow face (they come from L2: the rows j-1, j,
+// j+1 of the previous sweep's f are resident), which keeps the loop free of per-velocity branches.
+template <class TS, bool kRes, int kBnd>
+__device__ __forceinline__ void primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int lane,
+                                            const int4 nb) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
+    const TC2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
+    const double4 pr = P.prim_old[c];
+    const TC rho = (TC)pr.x, u1 = (TC)pr.y, u2 = (TC)pr.z, T = (TC)pr.w;
+    const TC iT = TC(1) / T;
+    const TC n0 = rho * iT * TC(0.15915494309189533577);          // rho / (2 pi T)
+    const TC inv2T = TC(0.5) * iT, halfT = TC(0.5) * T;
+    const TC Vt = P.V[c] * rho * sqrt(T) * (TC)P.inv_tau_inf;      // V / tau
+    TC cw1 = TC(0), cw2 = TC(0), invA = TC(0);
+    if (wall) {
+        cw1 = (TC)(P.Fw_old[c] / P.wallD[c]);
+        cw2 = cw1 * P.halfTw;
+        invA = TC(1) / sqrt(S3.x * S3.x + S3.y * S3.y);
+    }
+    const uint4* fo = reinterpret_cast<const uint4*>(P.f_old);
+    uint4* fw = reinterpret_cast<uint4*>(P.f_new);
+    const unsigned nq = (unsigned)P.nq;
+    const unsigned oc = (unsigned)c * nq, o0 = (unsigned)nb.x * nq, o2 = (unsigned)nb.z * nq;
+    const unsigned o1 = far ? oc : (unsigned)nb.y * nq, o3 = wall ? oc : (unsigned)nb.w * nq;
+
+    Sum<TC> m0, m1, m2, m3, fwa, ja, rs;
+    unsigned q = lane;
+    uint4 ro_next = q < nq ? ldg16(fo + oc + q) : make_uint4(0, 0, 0, 0);
+    while (q < nq) {
+        TC bm0 = TC(0), bm1 = TC(0), bm2 = TC(0), bm3 = TC(0), bfw = TC(0), bj = TC(0), brs = TC(0);
+        for (int it = 0; it < kBlockIters && q < nq; ++it, q += 32) {
+            const uint4 ro = ro_next;
+            if (q + 32 < nq) ro_next = ldg16(fo + oc + q + 32);
+            const uint4 r0 = ldg16(fo + o0 + q);
+            const uint4 r2 = ldg16(fo + o2 + q);
+            uint4 r1 = ro, r3 = ro;
+            if (!far) r1 = ldg16(fo + o1 + q);
+            if (!wall) r3 = ldg16(fo + o3 + q);
+            TC fo1[KV], fo2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV], e32[KV];
+            PK::unpack(ro, fo1, fo2);
+            PK::unpack(r0, e01, e02);
+            PK::unpack(r1, e11, e12);
+            PK::unpack(r2, e21, e22);
+            PK::unpack(r3, e31, e32);
+            TC fn1[KV], fn2[KV];
+#pragma unroll
+            for (int kk = 0; kk < KV; ++kk) {
+                const int k = q * KV + kk;
+                const TC4 t = P.vt[k];
+                const TC vx = t.x, vy = t.y, w = t.z, hv = t.w;
+                const TC a0 = S0.x * vx + S0.y * vy, a1 = S1.x * vx + S1.y * vy;
+                const TC a2 = S2.x * vx + S2.y * vy, a3 = S3.x * vx + S3.y * vy;
+                if (far) { const TC2 d = P.fd[k]; e11[kk] = d.x; e12[kk] = d.y; }
+                if (wall) { const TC gw = P.gw[k]; e31[kk] = cw1 * gw; e32[kk] = cw2 * gw; }
+                const TC D = Vt + TC(0.5) * ((fabs(a0) + fabs(a1)) + (fabs(a2) + fabs(a3)));
+                const TC dx = vx - u1, dy = vy - u2;
+                const TC g1 = n0 * fexp<TC>(-(dx * dx + dy * dy) * inv2T);
+                TC r1_ = Vt * g1;
+                TC r2_ = halfT * r1_;
+                const TC b0 = fmin(a0, TC(0)), b1 = fmin(a1, TC(0)), b2 = fmin(a2, TC(0)), b3 = fmin(a3, TC(0));
+                r1_ -= b0 * e01[kk]; r2_ -= b0 * e02[kk];
+                r1_ -= b1 * e11[kk]; r2_ -= b1 * e12[kk];
+                r1_ -= b2 * e21[kk]; r2_ -= b2 * e22[kk];
+                r1_ -= b3 * e31[kk]; r2_ -= b3 * e32[kk];
+                const TC iD = frcp<TC>(D);
+                fn1[kk] = r1_ * iD;
+                fn2[kk] = r2_ * iD;
+                if (kRes) {
+                    const TC R1 = D * (fo1[kk] - fn1[kk]), R2 = D * (fo2[kk] - fn2[kk]);
+                    brs += w * (R1 * R1 + R2 * R2);
+                }
+                const TC wf1 = w * fn1[kk];
+                bm0 += wf1;
+                bm1 += wf1 * vx;
+                bm2 += wf1 * vy;
+                bm3 += wf1 * hv + w * fn2[kk];
+                if (wall) {
+                    const TC p3 = a3 - b3;                       // max(a3, 0)
+                    bfw += wf1 * p3;
+                    bj += wf1 * p3 * (P.dirx * vx + P.diry * vy);
+                }
+            }
+            stg16(fw + oc + q, PK::pack(fn1, fn2));
+        }
+        m0.add(bm0); m1.add(bm1); m2.add(bm2); m3.add(bm3);
+        if (kRes) rs.add(brs);
+        if (wall) { fwa.add(bfw); ja.add(bj); }
+    }
+    const TC M0 = m0.total(), M1 = m1.total(), M2 = m2.total(), M3 = m3.total();
+    TC RS = TC(0), FW = TC(0), JA = TC(0);
+    if (kRes) RS = rs.total();
+    if (wall) { FW = fwa.total(); JA = ja.total(); }
+    if (lane == 0) {
+        const TC ir = TC(1) / M0;
+        const TC nu1 = M1 * ir, nu2 = M2 * ir;
+        const TC nT = TC(2.0 / 3.0) * (M3 * ir - TC(0.5) * (nu1 * nu1 + nu2 * nu2));
+        P.prim_new[c] = make_double4(M0, nu1, nu2, nT);
+        if (kRes) {
+            const TC V = P.V[c];
+            P.respart[c] = (double)(RS / (V * V));
+        }
+        if (wall) {
+            P.Fw_new[c] = (double)(FW * invA);
+            P.Jpart[c] = (double)JA;
+        }
+    }
+}
+
+template <class TS, bool kRes>
+__global__ void __launch_bounds__(256, 3) k_primal_sweep(PrimalArgs<TS, typename Pack<TS>::TC> P) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= P.ncell) return;
+    const int4 nb = P.nb[c];
+    const int bnd = (nb.w == kWall ? kWallCell : 0) | (nb.y < 0 ? kFarCell : 0);
+    switch (bnd) {
+        case kInterior: primal_cell<TS, kRes, kInterior>(P, c, lane, nb); break;
+        case kWallCell: primal_cell<TS, kRes, kWallCell>(P, c, lane, nb); break;
+        case kFarCell: primal_cell<TS, kRes, kFarCell>(P, c, lane, nb); break;
+        default: primal_cell<TS, kRes, kWallFar>(P, c, lane, nb); break;
+    }
+}
+
+// ================================================================== adjoint sweep (K2)
+// Transposed (downwind) point-implicit sweep of the discrete adjoint of Eq. (numerad_gov):
+//   D phi = -dJ/df/w + sum_{a>0, interior} a phi_nb + Z . Psi - [wall, a>0] (v.n) Lambda
+// Z = (V/tau) What - V rhohat' d(1/tau)/dW collects the linearised collision terms
+// (Eq. adjoint_eqdefines / adjoint_macdefines) of the previous sweep; it is rebuilt here from
+// the new phi: What = J_P^T Phat with Phat = sum_k w (phi1 dg1/dp + phi2 dg2/dp), p = (rho,u,T),
+// and rhohat' = sum_k w phi . (f - g).  Lambda = sum_{a<=0} w a phi . gbar_w (Eq. formula_adjointbgk).
+// The per-cell constants of the linearisation (Maxwellian parameters, V/tau, J_P, d(1/tau)/dp)
+// come precomputed in AdjCell.  kUpdate = false: phi is not advanced; the couplings of phi_old are
+// written to the *_new slots (used after an upload of phi or a change of the primal state).
+template <class TS, bool kUpdate, bool kRes, int kBnd>
+__device__ __forceinline__ void adjoint_cell(const AdjointArgs<TS, typename Pack<TS>::TC>& P, int c, int lane,
+                                             const int4 nb) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
+    const TC2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
+    const AdjCell<TC>* ccp = P.cell + c;
+    const TC u1 = __ldg(&ccp->u1), u2 = __ldg(&ccp->u2), n0 = __ldg(&ccp->n0), inv2T = __ldg(&ccp->inv2T);
+    const TC halfT = __ldg(&ccp->halfT), Vt = __ldg(&ccp->Vt);
+    const double4 Z = P.Z_old[c];
+    const TC z0 = (TC)Z.x, z1 = (TC)Z.y, z2 = (TC)Z.z, z3 = (TC)Z.w;
+    TC gb1s = TC(0), srcB = TC(0);
+    if (wall) {
+        const TC A = sqrt(S3.x * S3.x + S3.y * S3.y);
+        gb1s = (TC)(1.0 / P.wallD[c]);
+        srcB = (TC)((P.wallM[c] + P.Lam_old[c])) / A;             // (M + Lambda)/A multiplies a3
+    }
+    const uint4* po = reinterpret_cast<const uint4*>(P.phi_old);
+    const uint4* fp = reinterpret_cast<const uint4*>(P.f);
+    uint4* pw = reinterpret_cast<uint4*>(P.phi_new);
+    const unsigned nq = (unsigned)P.nq;
+    const unsigned oc = (unsigned)c * nq, o0 = (unsigned)nb.x * nq, o2 = (unsigned)nb.z * nq;
+    const unsigned o1 = far ? oc : (unsigned)nb.y * nq, o3 = wall ? oc : (unsigned)nb.w * nq;
+
+    Sum<TC> sh, shx, shy, shc, sg2, sr, lam, rs;
+    unsigned q = lane;
+    uint4 ro_next = make_uint4(0, 0, 0, 0), rf_next = make_uint4(0, 0, 0, 0);
+    if (q < nq) { ro_next = ldg16(po + oc + q); rf_next = ldg16(fp + oc + q); }
+    while (q < nq) {
+        TC bh = TC(0), bhx = TC(0), bhy = TC(0), bhc = TC(0), bg2 = TC(0), br = TC(0), bl = TC(0), brs = TC(0);
+        for (int it = 0; it < kBlockIters && q < nq; ++it, q += 32) {
+            const uint4 ro = ro_next, rf = rf_next;
+            if (q + 32 < nq) { ro_next = ldg16(po + oc + q + 32); rf_next = ldg16(fp + oc + q + 32); }
+            uint4 r0 = ro, r1 = ro, r2 = ro, r3 = ro;
+            if (kUpdate) {
+                r0 = ldg16(po + o0 + q);
+                r2 = ldg16(po + o2 + q);
+                if (!far) r1 = ldg16(po + o1 + q);
+                if (!wall) r3 = ldg16(po + o3 + q);
+            }
+            TC po1[KV], po2[KV], f1[KV], f2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV],
+                e32[KV];
+            PK::unpack(ro, po1, po2);
+            PK::unpack(rf, f1, f2);
+            PK::unpack(r0, e01, e02);
+            PK::unpack(r1, e11, e12);
+            PK::unpack(r2, e21, e22);
+            PK::unpack(r3, e31, e32);
+            TC pn1[KV], pn2[KV];
+#pragma unroll
+            for (int kk = 0; kk < KV; ++kk) {
+                const int k = q * KV + kk;
+                const TC4 t = P.vt[k];
+                const TC vx = t.x, vy = t.y, w = t.z, hv = t.w;
+                const TC a3 = S3.x * vx + S3.y * vy;
+                if (kUpdate) {
+                    const TC a0 = S0.x * vx + S0.y * vy, a1 = S1.x * vx + S1.y * vy, a2 = S2.x * vx + S2.y * vy;
+                    const TC D = Vt + TC(0.5) * ((fabs(a0) + fabs(a1)) + (fabs(a2) + fabs(a3)));
+                    TC r1_ = z0 + z1 * vx + z2 * vy + z3 * hv;
+                    TC r2_ = z3;
+                    const TC p0 = fmax(a0, TC(0)), p2 = fmax(a2, TC(0)), p3 = fmax(a3, TC(0));
+                    r1_ += p0 * e01[kk]; r2_ += p0 * e02[kk];
+                    r1_ += p2 * e21[kk]; r2_ += p2 * e22[kk];
+                    if (!far) { const TC p1 = fmax(a1, TC(0)); r1_ += p1 * e11[kk]; r2_ += p1 * e12[kk]; }
+                    if (wall) r1_ -= p3 * (P.dirx * vx + P.diry * vy + srcB);
+                    else { r1_ += p3 * e31[kk]; r2_ += p3 * e32[kk]; }
+                    const TC iD = frcp<TC>(D);
+                    pn1[kk] = r1_ * iD;
+                    pn2[kk] = r2_ * iD;
+                    if (kRes) {
+                        const TC R1 = D * (po1[kk] - pn1[kk]), R2 = D * (po2[kk] - pn2[kk]);
+                        brs += w * (R1 * R1 + R2 * R2);
+                    }
+                } else {
+                    pn1[kk] = po1[kk];
+                    pn2[kk] = po2[kk];
+                }
+                // couplings of the next sweep, from the new phi
+                const TC dx = vx - u1, dy = vy - u2, c2 = dx * dx + dy * dy;
+                const TC wg1 = w * n0 * fexp<TC>(-c2 * inv2T);
+                const TC h = wg1 * (pn1[kk] + halfT * pn2[kk]);
+                bh += h;
+                bhx += h * dx;
+                bhy += h * dy;
+                bhc += h * c2;
+                bg2 += wg1 * pn2[kk];
+                br += w * (pn1[kk] * f1[kk] + pn2[kk] * f2[kk]) - h;     // w phi.(f - g)
+                if (wall) bl += w * fmin(a3, TC(0)) * P.gw[k] * gb1s * (pn1[kk] + P.halfTw * pn2[kk]);
+            }
+            if (kUpdate) stg16(pw + oc + q, PK::pack(pn1, pn2));
+        }
+        sh.add(bh); shx.add(bhx); shy.add(bhy); shc.add(bhc); sg2.add(bg2); sr.add(br);
+        if (kRes) rs.add(brs);
+        if (wall) lam.add(bl);
+    }
+    const TC Sh = sh.total(), Shx = shx.total(), Shy = shy.total(), Shc = shc.total();
+    const TC Sg2 = sg2.total(), Sr = sr.total();
+    TC RS = TC(0), LAM = TC(0);
+    if (kRes) RS = rs.total();
+    if (wall) LAM = lam.total();
+    if (lane == 0) {
+        const AdjCell<TC> cc = *ccp;   // epilogue-only constants, loaded after the loop
+        // Phat in primitive variables, then p = (V/tau) Phat - V rhohat' d(1/tau)/dp, Z = J_P^T p
+        const TC ph0 = Sh * cc.ir, ph1 = Shx * cc.iT, ph2 = Shy * cc.iT;
+        const TC ph3 = Shc * cc.iT2h - Sh * cc.iT + TC(0.5) * Sg2;
+        const TC p0 = Vt * ph0 - Sr * cc.c0, p1 = Vt * ph1, p2 = Vt * ph2, p3 = Vt * ph3 - Sr * cc.c3;
+        double4 zn;
+        zn.x = (double)(p0 - (p1 * u1 + p2 * u2) * cc.ir + p3 * cc.j30);
+        zn.y = (double)(p1 * cc.ir + p3 * cc.j31);
+        zn.z = (double)(p2 * cc.ir + p3 * cc.j32);
+        zn.w = (double)(p3 * cc.j33);
+        P.Z_new[c] = zn;
+        if (kRes) {
+            const TC V = P.V[c];
+            P.respart[c] = (double)(RS / (V * V));
+        }
+        if (wall) P.Lam_new[c] = (double)LAM;
+    }
+}
+
+template <class TS, bool kUpdate, bool kRes>
+__global__ void __launch_bounds__(256, 3) k_adjoint_sweep(AdjointArgs<TS, typename Pack<TS>::TC> P) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= P.ncell) return;
+    const int4 nb = P.nb[c];
+    const int bnd = (nb.w == kWall ? kWallCell : 0) | (nb.y < 0 ? kFarCell : 0);
+    switch (bnd) {
+        case kInterior: adjoint_cell<TS, kUpdate, kRes, kInterior>(P, c, lane, nb); break;
+        case kWallCell: adjoint_cell<TS, kUpdate, kRes, kWallCell>(P, c, lane, nb); break;
+        case kFarCell: adjoint_cell<TS, kUpdate, kRes, kFarCell>(P, c, lane, nb); break;
+        default: adjoint_cell<TS, kUpdate, kRes, kWallFar>(P, c, lane, nb); break;
+    }
+}
+
+// Per-cell constants of the adjoint linearisation from the primal moments (fixed while the
+// primal state does not change): Maxwellian parameters, V/tau, the Jacobian J_P = d(rho,u,T)/dW
+// and V d(1/tau)/d(rho, T).
+template <class TC>
+__global__ void k_adjoint_cellconst(int ncell, const double4* prim, const double* V, double inv_tau_inf,
+                                    AdjCell<TC>* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double4 p = prim[c];
+    const double rho = p.x, u1 = p.y, u2 = p.z, T = p.w, sT = sqrt(T), ir = 1.0 / rho, iT = 1.0 / T;
+    AdjCell<TC> a;
+    a.n0 = (TC)(rho * iT / (2.0 * kPi));
+    a.inv2T = (TC)(0.5 * iT);
+    a.halfT = (TC)(0.5 * T);
+    a.Vt = (TC)(V[c] * rho * sT * inv_tau_inf);
+    a.u1 = (TC)u1;
+    a.u2 = (TC)u2;
+    a.ir = (TC)ir;
+    a.iT = (TC)iT;
+    a.iT2h = (TC)(0.5 * iT * iT);
+    a.c0 = (TC)(V[c] * sT * inv_tau_inf);
+    a.c3 = (TC)(V[c] * rho * inv_tau_inf / (2.0 * sT));
+    a.j30 = (TC)((u1 * u1 + u2 * u2) / 3.0 - T) * (TC)ir;
+    a.j31 = (TC)(-(2.0 / 3.0) * u1 * ir);
+    a.j32 = (TC)(-(2.0 / 3.0) * u2 * ir);
+    a.j33 = (TC)((2.0 / 3.0) * ir);
+    a.pad = (TC)0;
+    out[c] = a;
+}
+
+// ================================================================== setup kernels
+template <class TC>
+__global__ void k_flow_tables(int nvp, const typename Vec<TC>::v4* vt, double u1, double u2, double Tw,
+                              typename Vec<TC>::v2* fd, TC* gw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nvp) return;
+    const auto t = vt[k];
+    const TC dx = t.x - (TC)u1, dy = t.y - (TC)u2;
+    const TC g1 = (TC)(1.0 / (2.0 * kPi)) * dexp<TC>(-(dx * dx + dy * dy) * TC(0.5));
+    fd[k].x = g1;
+    fd[k].y = TC(0.5) * g1;
+    gw[k] = (TC)(1.0 / (2.0 * kPi * Tw)) * dexp<TC>(-(t.x * t.x + t.y * t.y) * (TC)(0.5 / Tw));
+}
+
+// Per wall face l: D_l = -sum_{a<=0} w (v.n) g_M1(1,0,Tw) (the normaliser of Eq. barg) and
+// M_l = sum_{a<=0} w (v.d) a g_M1 / D_l (the reflected part of J per unit F_rhow).
+__global__ void k_wall_setup(int nvp, const double2* S, const double4* vd, const double* gw, double dirx,
+                             double diry, double* wallD, double* wallM) {
+    const int l = blockIdx.x;
+    const double2 s = S[4 * l + 3];
+    const double A = sqrt(s.x * s.x + s.y * s.y);
+    double d = 0.0, m = 0.0;
+    for (int k = threadIdx.x; k < nvp; k += blockDim.x) {
+        const double4 t = vd[k];
+        const double a = s.x * t.x + s.y * t.y;
+        if (!(a > 0.0)) {
+            d -= t.z * (a / A) * gw[k];
+            m += t.z * (dirx * t.x + diry * t.y) * a * gw[k];
+        }
+    }
+    __shared__ double sd[32], sm[32];
+    d = warp_sum(d);
+    m = warp_sum(m);
+    if ((threadIdx.x & 31) == 0) { sd[threadIdx.x >> 5] = d; sm[threadIdx.x >> 5] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double D = 0.0, M = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { D += sd[i]; M += sm[i]; }
+        wallD[l] = D;
+        wallM[l] = M / D;
+    }
+}
+
+template <class TS>
+__global__ void k_fill_freestream(TS* f, size_t n_pairs, int nvp,
+                                  const typename Vec<typename Pack<TS>::TC>::v2* fd) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pairs) return;
+    const auto d = fd[i % nvp];
+    f[2 * i] = fromdbl<TS>((double)d.x);
+    f[2 * i + 1] = fromdbl<TS>((double)d.y);
+}
+
+template <class TS>
+__global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const double2* S, const double4* vd,
+                          double4* prim, double* Fw) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const bool wall = nb[c].w == kWall;
+    const double2 s = S[4 * c + 3];
+    double m0 = 0, m1 = 0, m2 = 0, m3 = 0, fw = 0;
+    for (int k = lane; k < nvp; k += 32) {
+        const double4 t = vd[k];
+        const double f1 = todbl(f[((size_t)c * nvp + k) * 2]), f2 = todbl(f[((size_t)c * nvp + k) * 2 + 1]);
+        m0 += t.z * f1;
+        m1 += t.z * t.x * f1;
+        m2 += t.z * t.y * f1;
+        m3 += t.z * (t.w * f1 + f2);
+        const double a = s.x * t.x + s.y * t.y;
+        if (wall && a > 0.0) fw += t.z * a * f1;
+    }
+    m0 = warp_sum(m0); m1 = warp_sum(m1); m2 = warp_sum(m2); m3 = warp_sum(m3); fw = warp_sum(fw);
+    if (lane == 0) {
+        const double u1 = m1 / m0, u2 = m2 / m0;
+        prim[c] = make_double4(m0, u1, u2, (2.0 / 3.0) * (m3 / m0 - 0.5 * (u1 * u1 + u2 * u2)));
+        if (wall) Fw[c] = fw / sqrt(s.x * s.x + s.y * s.y);
+    }
+}
+
+// Deterministic single-block reduction: out[0] = sum respart, out[1] = sum_l (Jpart_l + Fw_l M_l).
+__global__ void k_finalize(const double* respart, int ncell, const double* Jpart, const double* Fw,
+                           const double* M, int ni, double* out) {
+    __shared__ double s0[32], s1[32];
+    double a = 0.0, b = 0.0;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) a += respart[c];
+    if (Jpart)
+        for (int l = threadIdx.x; l < ni; l += blockDim.x) b += Jpart[l] + (Fw ? Fw[l] * M[l] : 0.0);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = a; s1[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { A += s0[i]; B += s1[i]; }
+        out[0] = A;
+        out[1] = B;
+    }
+}
+
+// J = sum_l sum_k w m a f1_l  (Eq. numer_J) for an arbitrary direction; one block per wall face.
+template <class TS>
+__global__ void k_functional(const TS* f, int nvp, const double2* S, const double4* vd, const double* gw,
+                             const double* wallD, const double* Fw, double dirx, double diry, double* face_out) {
+    const int l = blockIdx.x;
+    const double2 s = S[4 * l + 3];
+    const double cw = Fw[l] / wallD[l];
+    double j = 0.0;
+    for (int k = threadIdx.x; k < nvp; k += blockDim.x) {
+        const double4 t = vd[k];
+        const double a = s.x * t.x + s.y * t.y;
+        const double f1 = a > 0.0 ? todbl(f[((size_t)l * nvp + k) * 2]) : cw * gw[k];
+        j += t.z * (dirx * t.x + diry * t.y) * a * f1;
+    }
+    __shared__ double sj[32];
+    j = warp_sum(j);
+    if ((threadIdx.x & 31) == 0) sj[threadIdx.x >> 5] = j;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double J = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) J += sj[i];
+        face_out[l] = J;
+    }
+}
+
+template <class TA, class TB>
+__global__ void k_convert(const TA* src, TB* dst, int ncell, int nv_src, int nv_dst) {
+    // copies ncell x min(nv_src, nv_dst) pairs, zero-fills the rest of dst
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = (size_t)ncell * nv_dst;
+    if (i >= n) return;
+    const size_t c = i / nv_dst, k = i % nv_dst;
+    TB a = fromdbl<TB>(0.0), b = fromdbl<TB>(0.0);
+    if ((int)k < nv_src) {
+        a = fromdbl<TB>(todbl(src[(c * nv_src + k) * 2]));
+        b = fromdbl<TB>(todbl(src[(c * nv_src + k) * 2 + 1]));
+    }
+    dst[2 * i] = a;
+    dst[2 * i + 1] = b;
+}
+
+// ================================================================== paper sensitivity (K4a)
+// Per wall element l (one block): Eq. (sens_J_itf) and (sens_B_itf) with the Gauss gradient of
+// Eq. (gaussgrad) from the same interface values as the sweep, phi_w of Eq. (formula_adjointbgk).
+// elem[l] = (dL/dA, dL/dx (2), dL/dn (2)).  Sums in FP64 (NI x nv work only).
+template <class TS>
+__global__ void k_sens_paper_elem(const TS* f, const TS* phi, int nvp, const int4* nb, const double2* S,
+                                  const double* Vc, const double4* vd, const double2* fd, const double* gw,
+                                  const double* wallD, const double* Fw, double halfTw, double dirx,
+                                  double diry, double* elem) {
+    const int l = blockIdx.x;   // wall cell index (j = 0)
+    const int4 n = nb[l];
+    const double2 s[4] = {S[4 * l], S[4 * l + 1], S[4 * l + 2], S[4 * l + 3]};
+    const double A = sqrt(s[3].x * s[3].x + s[3].y * s[3].y);
+    const double nx = s[3].x / A, ny = s[3].y / A, iV = 1.0 / Vc[l];
+    const double cw = Fw[l] / wallD[l];
+    const int nbs[4] = {n.x, n.y, n.z, n.w};
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // 0 dA | 1,2 X1 | 3,4 Gp | 5 Pg | 6,7 Vf | 8,9 N1
+    for (int k = threadIdx.x; k < nvp; k += blockDim.x) {
+        const double4 t = vd[k];
+        const double vx = t.x, vy = t.y, w = t.z, m = dirx * vx + diry * vy;
+        const double fc1 = todbl(f[((size_t)l * nvp + k) * 2]), fc2 = todbl(f[((size_t)l * nvp + k) * 2 + 1]);
+        double F1[4], F2[4];
+        for (int e = 0; e < 4; ++e) {
+            const double a = s[e].x * vx + s[e].y * vy;
+            if (a > 0.0) { F1[e] = fc1; F2[e] = fc2; }
+            else if (nbs[e] >= 0) {
+                F1[e] = todbl(f[((size_t)nbs[e] * nvp + k) * 2]);
+                F2[e] = todbl(f[((size_t)nbs[e] * nvp + k) * 2 + 1]);
+            } else if (nbs[e] == kFar) { F1[e] = fd[k].x; F2[e] = fd[k].y; }
+            else { F1[e] = cw * gw[k]; F2[e] = cw * halfTw * gw[k]; }
+        }
+        double g1x = 0, g1y = 0, g2x = 0, g2y = 0;
+        for (int e = 0; e < 4; ++e) {
+            g1x += F1[e] * s[e].x; g1y += F1[e] * s[e].y;
+            g2x += F2[e] * s[e].x; g2y += F2[e] * s[e].y;
+        }
+        g1x *= iV; g1y *= iV; g2x *= iV; g2y *= iV;
+        const double vn = vx * nx + vy * ny, fl1 = F1[3];
+        acc[0] += w * m * vn * fl1;
+        acc[1] += w * m * vn * A * g1x;
+        acc[2] += w * m * vn * A * g1y;
+        acc[6] += w * vx * fl1;
+        acc[7] += w * vy * fl1;
+        acc[8] += w * m * vx * A * fl1;
+        acc[9] += w * m * vy * A * fl1;
+        if (vn > 0.0) {
+            acc[3] += w * vn * g1x;
+            acc[4] += w * vn * g1y;
+        } else {
+            const double p1 = todbl(phi[((size_t)l * nvp + k) * 2]), p2 = todbl(phi[((size_t)l * nvp + k) * 2 + 1]);
+            const double pw1 = -vn * (p1 + m), pw2 = -vn * p2;
+            const double gb1 = gw[k] / wallD[l];
+            acc[1] += w * A * (pw1 * g1x + pw2 * g2x);
+            acc[2] += w * A * (pw1 * g1y + pw2 * g2y);
+            acc[5] += w * (pw1 * gb1 + pw2 * halfTw * gb1);
+        }
+    }
+    __shared__ double sh[10][8];
+    for (int i = 0; i < 10; ++i) {
+        const double v = warp_sum(acc[i]);
+        if ((threadIdx.x & 31) == 0) sh[i][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[10];
+        for (int i = 0; i < 10; ++i) {
+            r[i] = 0.0;
+            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) r[i] += sh[i][j];
+        }
+        elem[5 * l + 0] = r[0];
+        elem[5 * l + 1] = r[1] - A * r[3] * r[5];
+        elem[5 * l + 2] = r[2] - A * r[4] * r[5];
+        elem[5 * l + 3] = r[8] - A * r[5] * r[6];
+        elem[5 * l + 4] = r[9] - A * r[5] * r[7];
+    }
+}
+
+// Element -> wall node (Eq. sens_nod): node m belongs to elements m-1 (as its first end X(0,m))
+// and m (as its second end).  For an end x_a with the other end x_b: dA/dx_a = (x_a - x_b)/A,
+// dx_l/dx_a = 1/2, dn/dx_a = sigma R90 n n^T / A, sigma = sign((x_a - x_b) x n).
+__global__ void k_sens_paper_nodes(int ni, const double2* nodes, const double2* S, const double* elem,
+                                   double* node_grad) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= ni) return;
+    double gx = 0.0, gy = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        // element l spans wall nodes l and l+1
+        const int l = side == 0 ? (m - 1 + ni) % ni : m;
+        const int ob = side == 0 ? (m - 1 + ni) % ni : (m + 1) % ni;
+        const double2 xa = nodes[m], xb = nodes[ob];
+        const double2 s = S[4 * l + 3];
+        const double A = sqrt(s.x * s.x + s.y * s.y);
+        const double nx = s.x / A, ny = s.y / A;
+        const double ex = xa.x - xb.x, ey = xa.y - xb.y;
+        const double cr = ex * ny - ey * nx;
+        const double sg = cr > 0.0 ? 1.0 : (cr < 0.0 ? -1.0 : 0.0);
+        const double* e = elem + 5 * l;
+        // (dn/dx_a)^T dL/dn with dn/dx_a[r][c] = sg/A * (R90 n)_r n_c, R90 n = (-ny, nx)
+        const double rn = sg / A * (-ny * e[3] + nx * e[4]);
+        gx += e[0] * ex / A + 0.5 * e[1] + rn * nx;
+        gy += e[0] * ey / A + 0.5 * e[2] + rn * ny;
+    }
+    node_grad[2 * m] = gx;
+    node_grad[2 * m + 1] = gy;
+}
+
+// ================================================================== full-discrete sensitivity (K4b)
+// dJ/dalpha = dJ/dalpha|_f + sum w phi . dR/dalpha|_f.  R depends on the geometry through the face
+// vectors S_f (linear in their two end nodes), the volumes V_c and, on the wall, through n_l in
+// F_rhow and gbar_w.  Per face f between L (owner) and R:
+//   G_f = sum_k w v_k (phi_L - phi_R) . F_{f,k}   (F the upwind interface value)
+// so that the face term is G_f . dS_f/dalpha; per cell vol_c = sum_k w phi . (f - g) / tau_c
+// multiplies dV_c/dalpha; the wall face adds J's own S-dependence and the n-dependence
+// (I - n n^T)/A * H * Vf with H = sum_{a<=0} w a (m gbar1 + phi . gbar), Vf = sum_k w v f1_l.
+template <class TS>
+__global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, int ncell, int nvp,
+                                                    const int4* nb, const double2* S, const double* Vc,
+                                                    const typename Vec<typename Pack<TS>::TC>::v4* vt,
+                                                    const typename Vec<typename Pack<TS>::TC>::v2* fd,
+                                                    const typename Pack<TS>::TC* gw, const double* wallD,
+                                                    const double4* prim, const double* Fw, double inv_tau_inf,
+                                                    double halfTw_d, double dirx_d, double diry_d, double2* GN,
+                                                    double2* GE, double2* GW, double* vol) {
+    using TC = typename Pack<TS>::TC;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const int4 n = nb[c];
+    const double2 s1d = S[4 * c + 1], s2d = S[4 * c + 2], s3d = S[4 * c + 3];
+    const TC s1x = (TC)s1d.x, s1y = (TC)s1d.y, s2x = (TC)s2d.x, s2y = (TC)s2d.y, s3x = (TC)s3d.x, s3y = (TC)s3d.y;
+    const double4 pr = prim[c];
+    const TC u1 = (TC)pr.y, u2 = (TC)pr.z, n0 = (TC)(pr.x / (2.0 * kPi * pr.w)), inv2T = (TC)(0.5 / pr.w);
+    const TC halfT = (TC)(0.5 * pr.w), halfTw = (TC)halfTw_d, dirx = (TC)dirx_d, diry = (TC)diry_d;
+    const bool wall = n.w == kWall;
+    const TC cw = wall ? (TC)(Fw[c] / wallD[c]) : TC(0);
+    const TC gbs = wall ? (TC)(1.0 / wallD[c]) : TC(0);
+    Acc<TC> gnx, gny, gex, gey, gwx, gwy, H, vfx, vfy, vs;
+    for (int k = lane; k < nvp; k += 32) {
+        const auto t = vt[k];
+        const TC vx = t.x, vy = t.y, w = t.z;
+        const size_t ic = ((size_t)c * nvp + k) * 2;
+        const TC fc1 = (TC)todbl(f[ic]), fc2 = (TC)todbl(f[ic + 1]);
+        const TC pc1 = (TC)todbl(phi[ic]), pc2 = (TC)todbl(phi[ic + 1]);
+        {   // north face
+            const TC a = s1x * vx + s1y * vy;
+            TC F1, F2, q1 = TC(0), q2 = TC(0);
+            if (n.y >= 0) {
+                const size_t ir = ((size_t)n.y * nvp + k) * 2;
+                q1 = (TC)todbl(phi[ir]); q2 = (TC)todbl(phi[ir + 1]);
+                if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + 1]); }
+            } else if (a > TC(0)) { F1 = fc1; F2 = fc2; }
+            else { F1 = fd[k].x; F2 = fd[k].y; }
+            const TC d = w * ((pc1 - q1) * F1 + (pc2 - q2) * F2);
+            gnx.add(d * vx); gny.add(d * vy);
+        }
+        {   // east face (always interior)
+            const TC a = s2x * vx + s2y * vy;
+            const size_t ir = ((size_t)n.z * nvp + k) * 2;
+            const TC q1 = (TC)todbl(phi[ir]), q2 = (TC)todbl(phi[ir + 1]);
+            TC F1, F2;
+            if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + 1]); }
+            const TC d = w * ((pc1 - q1) * F1 + (pc2 - q2) * F2);
+            gex.add(d * vx); gey.add(d * vy);
+        }
+        if (wall) {
+            const TC a = s3x * vx + s3y * vy;
+            const TC m = dirx * vx + diry * vy;
+            TC F1, F2;
+            if (a > TC(0)) { F1 = fc1; F2 = fc2; }
+            else {
+                const TC gb1 = gw[k] * gbs;
+                F1 = cw * gw[k]; F2 = cw * halfTw * gw[k];
+                H.add(w * a * gb1 * (m + pc1 + halfTw * pc2));
+            }
+            const TC d = w * (pc1 * F1 + pc2 * F2 + m * F1);
+            gwx.add(d * vx); gwy.add(d * vy);
+            vfx.add(w * vx * F1); vfy.add(w * vy * F1);
+        }
+        {   // volume term
+            const TC dx = vx - u1, dy = vy - u2;
+            const TC g1 = n0 * dexp<TC>(-(dx * dx + dy * dy) * inv2T);
+            vs.add(w * (pc1 * (fc1 - g1) + pc2 * (fc2 - halfT * g1)));
+        }
+    }
+    const double GNX = warp_sum(gnx.get()), GNY = warp_sum(gny.get()), GEX = warp_sum(gex.get());
+    const double GEY = warp_sum(gey.get()), VS = warp_sum(vs.get());
+    double GWX = 0, GWY = 0, HH = 0, VFX = 0, VFY = 0;
+    if (wall) {
+        GWX = warp_sum(gwx.get()); GWY = warp_sum(gwy.get()); HH = warp_sum(H.get());
+        VFX = warp_sum(vfx.get()); VFY = warp_sum(vfy.get());
+    }
+    if (lane == 0) {
+        GN[c] = make_double2(GNX, GNY);
+        GE[c] = make_double2(GEX, GEY);
+        vol[c] = VS * pr.x * sqrt(pr.w) * inv_tau_inf;   // / tau
+        if (wall) {
+            const double A = sqrt(s3d.x * s3d.x + s3d.y * s3d.y);
+            const double nx = s3d.x / A, ny = s3d.y / A;
+            const double px = HH * VFX / A, py = HH * VFY / A;     // H Vf / A
+            const double dn = px * nx + py * ny;                   // projected with (I - n n^T)
+            GW[c] = make_double2(GWX + px - dn * nx, GWY + py - dn * ny);
+        }
+    }
+}
+
+// Node gradient of the full-discrete sensitivity: each node gathers the face and cell terms it
+// belongs to (no atomics, fixed order).  Face vector S of an edge P->Q is (Q_y - P_y, P_x - Q_x), so
+// d(S.G)/dP = (G_y, -G_x), d(S.G)/dQ = (-G_y, G_x).  Cell volume (CCW corners):
+// dV/dP_e = ((P_{e+1} - P_{e-1})_y, (P_{e-1} - P_{e+1})_x) / 2.
+__global__ void k_sens_nodes(int ni, int nj, const double2* X, const double2* GN, const double2* GE,
+                             const double2* GW, const double* vol, double2* node_grad) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (nj + 1) * ni) return;
+    const int j = id / ni, i = id % ni;
+    const int im = (i - 1 + ni) % ni, ip = (i + 1) % ni;
+    auto x = [&](int jj, int ii) { return X[jj * ni + ii]; };
+    double gx = 0.0, gy = 0.0;
+    // circumferential edge (j,i) -> (j,i+1)
+    if (j >= 1) { const double2 G = GN[(j - 1) * ni + i]; gx += G.y; gy -= G.x; }       // node is P
+    else { const double2 G = GW[i]; gx -= G.y; gy += G.x; }                                // wall: node is Q
+    // circumferential edge (j,i-1) -> (j,i)
+    if (j >= 1) { const double2 G = GN[(j - 1) * ni + im]; gx -= G.y; gy += G.x; }     // node is Q
+    else { const double2 G = GW[im]; gx += G.y; gy -= G.x; }                               // wall: node is P
+    // radial edges: east face of cell (j, i-1) runs X(j+1,i) -> X(j,i); of cell (j-1,i-1) X(j,i) -> X(j-1,i)
+    if (j < nj) { const double2 G = GE[j * ni + im]; gx -= G.y; gy += G.x; }
+    if (j >= 1) { const double2 G = GE[(j - 1) * ni + im]; gx += G.y; gy -= G.x; }
+    // volumes of the (up to) four cells having this node as a corner
+    if (j < nj) {
+        double v = vol[j * ni + i];            // corner P0: next P1 = X(j+1,i), prev P3 = X(j,i+1)
+        double2 nx = x(j + 1, i), pv = x(j, ip);
+        gx += 0.5 * v * (nx.y - pv.y); gy += 0.5 * v * (pv.x - nx.x);
+        v = vol[j * ni + im];                  // corner P3 of cell (j,i-1): next P0 = X(j,i-1), prev P2 = X(j+1,i)
+        nx = x(j, im); pv = x(j + 1, i);
+        gx += 0.5 * v * (nx.y - pv.y); gy += 0.5 * v * (pv.x - nx.x);
+    }
+    if (j >= 1) {
+        double v = vol[(j - 1) * ni + i];      // corner P1 of cell (j-1,i): next P2 = X(j,i+1), prev P0 = X(j-1,i)
+        double2 nx = x(j, ip), pv = x(j - 1, i);
+        gx += 0.5 * v * (nx.y - pv.y); gy += 0.5 * v * (pv.x - nx.x);
+        v = vol[(j - 1) * ni + im];            // corner P2 of cell (j-1,i-1): next P3 = X(j-1,i), prev P1 = X(j,i-1)
+        nx = x(j - 1, i); pv = x(j, im);
+        gx += 0.5 * v * (nx.y - pv.y); gy += 0.5 * v * (pv.x - nx.x);
+    }
+    node_grad[id] = make_double2(gx, gy);
+}
+
+// grad[p] = sum_{rows j, i} (1 - s_j) node_grad(j,i) . dwall[p][i]  (s_j == nullptr -> rows = 1, weight 1)
+__global__ void k_contract(const double2* node_grad, int nrows, int ni, const double* s_j,
+                           const double* dwall, double* grad) {
+    const int p = blockIdx.x;
+    double acc = 0.0;
+    for (int id = threadIdx.x; id < nrows * ni; id += blockDim.x) {
+        const int j = id / ni, i = id % ni;
+        const double wgt = s_j ? 1.0 - s_j[j] : 1.0;
+        const double2 g = node_grad[id];
+        acc += wgt * (g.x * dwall[((size_t)p * ni + i) * 2] + g.y * dwall[((size_t)p * ni + i) * 2 + 1]);
+    }
+    __shared__ double sh[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+        grad[p] = s;
+    }
+}
+
+inline int cdiv(size_t a, size_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+// ================================================================== launchers
+size_t storage_bytes(int storage) { return storage == 0 ? 16 : (storage == 1 ? 8 : 4); }
+
+cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s) {
+    const int b = 256, n = cdiv(g.nvp, b);
+    k_flow_tables<double><<<n, b, 0, s>>>(g.nvp, g.vd, fl.u1, fl.u2, fl.Tw, fl.fdd, fl.gwd);
+    k_flow_tables<float><<<n, b, 0, s>>>(g.nvp, g.vf, fl.u1, fl.u2, fl.Tw, fl.fdf, fl.gwf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, double dirx, double diry,
+                              double* wallD, double* wallM, cudaStream_t s) {
+    k_wall_setup<<<m.ni, 256, 0, s>>>(g.nvp, m.Sd, g.vd, fl.gwd, dirx, diry, wallD, wallM);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_freestream(int storage, void* f, int ncell, const DevGrid& g, const DevFlow& fl,
+                                   cudaStream_t s) {
+    const size_t n = (size_t)ncell * g.nvp;
+    const int b = 256;
+    if (storage == 0) k_fill_freestream<double><<<cdiv(n, b), b, 0, s>>>((double*)f, n, g.nvp, fl.fdd);
+    else if (storage == 1) k_fill_freestream<float><<<cdiv(n, b), b, 0, s>>>((float*)f, n, g.nvp, fl.fdf);
+    else k_fill_freestream<__nv_bfloat16><<<cdiv(n, b), b, 0, s>>>((__nv_bfloat16*)f, n, g.nvp, fl.fdf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
+                           double* Fw, cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0) k_moments<double><<<nb, 256, 0, s>>>((const double*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw);
+    else if (storage == 1) k_moments<float><<<nb, 256, 0, s>>>((const float*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw);
+    else k_moments<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw);
+    return cudaGetLastError();
+}
+
+template <class TS, class TC>
+void primal_launch(const void* args, bool res, cudaStream_t s) {
+    const auto& a = *static_cast<const PrimalArgs<TS, TC>*>(args);
+    const int nb = cdiv(a.ncell, kWarpsPerBlock);
+    if (res) k_primal_sweep<TS, true><<<nb, 256, 0, s>>>(a);
+    else k_primal_sweep<TS, false><<<nb, 256, 0, s>>>(a);
+}
+
+cudaError_t launch_primal_sweep(int storage, const void* args, bool res, cudaStream_t s) {
+    if (storage == 0) primal_launch<double, double>(args, res, s);
+    else if (storage == 1) primal_launch<float, float>(args, res, s);
+    else primal_launch<__nv_bfloat16, float>(args, res, s);
+    return cudaGetLastError();
+}
+
+template <class TS, class TC>
+void adjoint_launch(const void* args, bool update, bool res, cudaStream_t s) {
+    const auto& a = *static_cast<const AdjointArgs<TS, TC>*>(args);
+    const int nb = cdiv(a.ncell, kWarpsPerBlock);
+    if (!update) k_adjoint_sweep<TS, false, false><<<nb, 256, 0, s>>>(a);
+    else if (res) k_adjoint_sweep<TS, true, true><<<nb, 256, 0, s>>>(a);
+    else k_adjoint_sweep<TS, true, false><<<nb, 256, 0, s>>>(a);
+}
+
+cudaError_t launch_adjoint_sweep(int storage, const void* args, bool update, bool res, cudaStream_t s) {
+    if (storage == 0) adjoint_launch<double, double>(args, update, res, s);
+    else if (storage == 1) adjoint_launch<float, float>(args, update, res, s);
+    else adjoint_launch<__nv_bfloat16, float>(args, update, res, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
+                                     void* out, cudaStream_t s) {
+    const int b = 256;
+    if (storage == 0) k_adjoint_cellconst<double><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, m.Vd, inv_tau_inf, (AdjCell<double>*)out);
+    else k_adjoint_cellconst<float><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, m.Vd, inv_tau_inf, (AdjCell<float>*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* respart, int ncell, const double* Jpart, const double* Fw,
+                            const double* M, int ni, double* out, cudaStream_t s) {
+    k_finalize<<<1, 1024, 0, s>>>(respart, ncell, Jpart, Fw, M, ni, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_functional(int storage, const void* f, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
+                              const double* Fw, double dirx, double diry, double* face_out, double* out,
+                              cudaStream_t s) {
+    if (storage == 0)
+        k_functional<double><<<m.ni, 256, 0, s>>>((const double*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, dirx, diry, face_out);
+    else if (storage == 1)
+        k_functional<float><<<m.ni, 256, 0, s>>>((const float*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, dirx, diry, face_out);
+    else
+        k_functional<__nv_bfloat16><<<m.ni, 256, 0, s>>>((const __nv_bfloat16*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, dirx, diry, face_out);
+    k_finalize<<<1, 1024, 0, s>>>(face_out, 0, face_out, nullptr, nullptr, m.ni, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int storage, int direction, const void* src, void* dst, int ncell, int nv, int nvp,
+                           cudaStream_t s) {
+    const int b = 256;
+    if (direction == 0) {   // device storage (nvp) -> double (nv)
+        const size_t n = (size_t)ncell * nv;
+        if (storage == 0) k_convert<double, double><<<cdiv(n, b), b, 0, s>>>((const double*)src, (double*)dst, ncell, nvp, nv);
+        else if (storage == 1) k_convert<float, double><<<cdiv(n, b), b, 0, s>>>((const float*)src, (double*)dst, ncell, nvp, nv);
+        else k_convert<__nv_bfloat16, double><<<cdiv(n, b), b, 0, s>>>((const __nv_bfloat16*)src, (double*)dst, ncell, nvp, nv);
+    } else {                 // double (nv) -> device storage (nvp)
+        const size_t n = (size_t)ncell * nvp;
+        if (storage == 0) k_convert<double, double><<<cdiv(n, b), b, 0, s>>>((const double*)src, (double*)dst, ncell, nv, nvp);
+        else if (storage == 1) k_convert<double, float><<<cdiv(n, b), b, 0, s>>>((const double*)src, (float*)dst, ncell, nv, nvp);
+        else k_convert<double, __nv_bfloat16><<<cdiv(n, b), b, 0, s>>>((const double*)src, (__nv_bfloat16*)dst, ncell, nv, nvp);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sens_paper(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl, const void* f,
+                              const void* phi, const double* Fw, double dirx, double diry, double* elem,
+                              double* node_grad, cudaStream_t s) {
+    const double hT = 0.5 * fl.Tw;
+    if (storage == 0)
+        k_sens_paper_elem<double><<<m.ni, 256, 0, s>>>((const double*)f, (const double*)phi, g.nvp, m.nb, m.Sd, m.Vd, g.vd,
+                                                       fl.fdd, fl.gwd, fl.wallD, Fw, hT, dirx, diry, elem);
+    else if (storage == 1)
+        k_sens_paper_elem<float><<<m.ni, 256, 0, s>>>((const float*)f, (const float*)phi, g.nvp, m.nb, m.Sd, m.Vd, g.vd,
+                                                      fl.fdd, fl.gwd, fl.wallD, Fw, hT, dirx, diry, elem);
+    else
+        k_sens_paper_elem<__nv_bfloat16><<<m.ni, 256, 0, s>>>((const __nv_bfloat16*)f, (const __nv_bfloat16*)phi, g.nvp,
+                                                              m.nb, m.Sd, m.Vd, g.vd, fl.fdd, fl.gwd, fl.wallD, Fw, hT,
+                                                              dirx, diry, elem);
+    k_sens_paper_nodes<<<cdiv(m.ni, 128), 128, 0, s>>>(m.ni, m.nodes, m.Sd, elem, node_grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl, const void* f,
+                             const void* phi, const double4* prim, const double* Fw, double dirx, double diry,
+                             double2* GN, double2* GE, double2* GW, double* vol, double2* node_grad, cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    const double hT = 0.5 * fl.Tw, it = 1.0 / fl.tau_inf;
+    if (storage == 0)
+        k_sens_faces<double><<<nb, 256, 0, s>>>((const double*)f, (const double*)phi, m.ncell, g.nvp, m.nb, m.Sd, m.Vd,
+                                                g.vd, fl.fdd, fl.gwd, fl.wallD, prim, Fw, it, hT, dirx, diry, GN, GE,
+                                                GW, vol);
+    else if (storage == 1)
+        k_sens_faces<float><<<nb, 256, 0, s>>>((const float*)f, (const float*)phi, m.ncell, g.nvp, m.nb, m.Sd, m.Vd,
+                                               g.vf, fl.fdf, fl.gwf, fl.wallD, prim, Fw, it, hT, dirx, diry, GN, GE,
+                                               GW, vol);
+    else
+        k_sens_faces<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, (const __nv_bfloat16*)phi, m.ncell,
+                                                       g.nvp, m.nb, m.Sd, m.Vd, g.vf, fl.fdf, fl.gwf, fl.wallD, prim,
+                                                       Fw, it, hT, dirx, diry, GN, GE, GW, vol);
+    const int nn = (m.nj + 1) * m.ni;
+    k_sens_nodes<<<cdiv(nn, 256), 256, 0, s>>>(m.ni, m.nj, m.nodes, GN, GE, GW, vol, node_grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract(const double2* node_grad, int nrows, int ni, const double* s_j, const double* dwall,
+                            int P, double* grad, cudaStream_t s) {
+    if (P > 0) k_contract<<<P, 256, 0, s>>>(node_grad, nrows, ni, s_j, dwall, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace dvm
