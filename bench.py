@@ -115,6 +115,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def ncu_traffic(kernel: str, storage: str):
+    """DRAM read+write bytes per launch from the committed ncu summary, scaled to this workload,
+    or None when the kernel source changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+        src = os.path.join(ROOT, "paper_2501_00923_gb300", "csrc", "dvm_kernels.cu")
+        with open(src, "rb") as fh:
+            cur = hashlib.sha256(fh.read()).hexdigest()[:16]
+        if rec.get("kernel_source_sha256_16") != cur:
+            return None
+        return rec.get(f"{kernel}/{storage}")
+    except Exception:
+        return None
+
+
 # ----------------------------------------------------------------------------------- CPU oracle
 def cpu_oracle_sample(wl, rows=16):
     """One point-implicit primal sweep and one adjoint sweep of the FP64 oracle over the first
@@ -242,13 +259,7 @@ def run_gpu(args):
     k_adj = {"name": "k_adjoint_sweep", "ms": adj_sweep_ms, "bytes": pairs * 6 * S,
              "GBps": pairs * 6 * S / (adj_sweep_ms * 1e6)}
     dom = k_adj if adj_ms >= prim_ms else k_prim
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get(f"{dom['name']}/{args.storage}")
-        except Exception:
-            traffic = None
+    traffic = ncu_traffic(dom["name"], args.storage) if not args.mesh else None
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": dom["GBps"] / peak, "traffic": traffic, "kernel": dom["name"],
                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
