@@ -182,6 +182,22 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ad
                     const double* dwall_dalpha, const double* s_j, int mode, double* grad_out,
                     double* node_grad_out);
 
+/* Same result as dvm_sensitivity, for callers that must not allocate device memory during the
+ * call (e.g. a serving loop whose device memory is reserved once, up front, by another allocator,
+ * or a host thread that must not stall on cudaMalloc's implicit synchronisation).  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ * Scratch: a static 8 MiB device array, present on every GPU that loads the library until the
+ * process exits.  A request whose intermediates exceed it (about 150 000 cells in the full mode)
+ * fails with DVM_ERR_INVALID_ARG and a message giving the size needed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ * All calls share the array and its contents persist between calls; each call writes every entry it
+ * reads, so nothing is cleared.  Calls whose GPU work overlaps (other contexts or threads on the same
+ * device) race on the array: serialise them.  Host arrays are as for dvm_sensitivity. */
+int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* adj, int n_params,
+                            const double* dwall_dalpha, const double* s_j, int mode, double* grad_out,
+                            double* node_grad_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -980,3 +981,111 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
 }
 
 }  // extern "C"
+
+// ======================================================================= no-allocation variant
+// dvm_sensitivity_noalloc keeps every intermediate of the sensitivity reduction in the static
+// device array below instead of device memory from cudaMalloc.  It exists for callers that must not
+// allocate device memory during the call (for example a serving loop whose device memory is carved
+// out once, up front, by another allocator, or a host thread that must not stall on cudaMalloc's
+// implicit device synchronisation).  The array costs kNoAllocScratchBytes on every GPU that loads
+// this library, for the life of the process.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on `device`, looked up once per device with that device
+// current (the host-side symbol is only a stand-in and must never be handed to a kernel).
+int noalloc_scratch(int device, unsigned char** out) {
+    if (device < 0 || device >= kMaxDevices) return fail(DVM_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        DeviceGuard dg(device);
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return fail_cuda(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress");
+        g_noalloc_addr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
+    return DVM_OK;
+}
+
+struct ScratchCarver {
+    unsigned char* base;
+    size_t used = 0;
+    template <class T>
+    T* take(size_t count) {
+        used = (used + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base ? base + used : nullptr);
+        used += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ad, int P,
+                                       const double* dwall, const double* s_j, int mode, double* grad_out,
+                                       double* node_grad_out) {
+    if (!ctx || !st || !ad || (P > 0 && (!dwall || !grad_out))) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (mode != DVM_SENS_PAPER && mode != DVM_SENS_FULL) return fail(DVM_ERR_INVALID_ARG, "unknown mode");
+    if (mode == DVM_SENS_FULL && !s_j) return fail(DVM_ERR_INVALID_ARG, "full mode needs s_j");
+    if (ad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
+    if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    const int nnodes = (m.nj + 1) * m.ni;
+    // layout first (base = nullptr), so an oversized request is rejected before any device work
+    ScratchCarver probe{nullptr};
+    probe.take<double2>(m.ncell); probe.take<double2>(m.ncell); probe.take<double2>(m.ni);
+    probe.take<double2>(nnodes); probe.take<double>(m.ncell); probe.take<double>(5 * (size_t)m.ni);
+    probe.take<double>((size_t)P * m.ni * 2); probe.take<double>(m.nj + 1); probe.take<double>(P > 0 ? P : 1);
+    if (probe.used > kNoAllocScratchBytes) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "dvm_sensitivity_noalloc needs %zu bytes of scratch; the static limit is %zu",
+                 probe.used, kNoAllocScratchBytes);
+        return fail(DVM_ERR_INVALID_ARG, msg);
+    }
+    DeviceGuard dg(ctx->device);
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(ctx->device, &base);
+    if (rc) return rc;
+    ScratchCarver sc{base};
+    double2* GN = sc.take<double2>(m.ncell);
+    double2* GE = sc.take<double2>(m.ncell);
+    double2* GW = sc.take<double2>(m.ni);
+    double2* node_grad = sc.take<double2>(nnodes);
+    double* vol = sc.take<double>(m.ncell);
+    double* elem = sc.take<double>(5 * (size_t)m.ni);
+    double* dw = sc.take<double>((size_t)P * m.ni * 2);
+    double* sj = sc.take<double>(m.nj + 1);
+    double* grad = sc.take<double>(P > 0 ? P : 1);
+    // every scratch entry read below is written earlier in the same call: nothing needs clearing
+    cudaStream_t s = ctx->stream;
+    if (P > 0) CK(cudaMemcpyAsync(dw, dwall, (size_t)P * m.ni * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    const void* f = st->f[st->cur];
+    const void* phi = ad->phi[ad->cur];
+    if (mode == DVM_SENS_PAPER) {
+        CK(launch_sens_paper(st->storage, m, g, st->fl, f, phi, st->Fw[st->cur], ad->dirx, ad->diry, elem,
+                             (double*)node_grad, s));
+        CK(launch_contract(node_grad, 1, m.ni, nullptr, dw, P, grad, s));
+        if (node_grad_out)
+            CK(cudaMemcpyAsync(node_grad_out, node_grad, (size_t)m.ni * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    } else {
+        CK(cudaMemcpyAsync(sj, s_j, (m.nj + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->dirx,
+                            ad->diry, GN, GE, GW, vol, node_grad, s));
+        CK(launch_contract(node_grad, m.nj + 1, m.ni, sj, dw, P, grad, s));
+        if (node_grad_out)
+            CK(cudaMemcpyAsync(node_grad_out, node_grad, (size_t)nnodes * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    ctx->launches += 2 + (P > 0);
+    if (P > 0) CK(cudaMemcpyAsync(grad_out, grad, P * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DVM_OK;
+}

@@ -91,6 +91,7 @@ def lib():
             "dvm_adjoint_iterate": (i, [_vp, i, _dp]),
             "dvm_adjoint_solve": (i, [_vp, _vp, i, C.POINTER(SolveOpts), pp, C.POINTER(AdjointResult)]),
             "dvm_sensitivity": (i, [_vp, _vp, _vp, i, _dp, _dp, i, _dp, _dp]),
+            "dvm_sensitivity_noalloc": (i, [_vp, _vp, _vp, i, _dp, _dp, i, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -345,8 +346,9 @@ def adjoint_solve(ctx: Context, state: State, functional="drag", tol=1e-8, max_i
 
 
 def sensitivity(ctx: Context, state: State, adjoint: Adjoint, dwall_dalpha, s_j=None, mode="full",
-                node_grad: bool = False):
-    """dJ/dalpha for wall-node tangents dwall_dalpha [P][ni][2] (interior nodes move by (1-s_j))."""
+                node_grad: bool = False, noalloc: bool = False):
+    """dJ/dalpha for wall-node tangents dwall_dalpha [P][ni][2] (interior nodes move by (1-s_j)).
+    noalloc=True calls dvm_sensitivity_noalloc, which keeps its scratch in a static device array."""
     dwall = _arr(dwall_dalpha)
     P = dwall.shape[0]
     ni, nj = state.mesh.ni, state.mesh.nj
@@ -359,5 +361,6 @@ def sensitivity(ctx: Context, state: State, adjoint: Adjoint, dwall_dalpha, s_j=
     ng = None
     if node_grad:
         ng = np.zeros((ni, 2)) if mode == "paper" else np.zeros((nj + 1, ni, 2))
-    _check(lib().dvm_sensitivity(ctx.h, state.h, adjoint.h, P, _p(dwall), _p(sj), SENS[mode], _p(g), _p(ng)))
+    fn = lib().dvm_sensitivity_noalloc if noalloc else lib().dvm_sensitivity
+    _check(fn(ctx.h, state.h, adjoint.h, P, _p(dwall), _p(sj), SENS[mode], _p(g), _p(ng)))
     return (g[:P], ng) if node_grad else g[:P]
