@@ -24,6 +24,7 @@ struct dvm_context {
     size_t bytes = 0;
     uint64_t launches = 0;
     double* pinned = nullptr;   // 64 doubles for small device->host results
+    int* derr = nullptr;        // device flag: a kernel's bounded wait ran out
 };
 
 struct dvm_mesh {
@@ -58,6 +59,7 @@ struct dvm_state {
     int graph_n = 0;
     int graph_cur = -1;
     uint64_t version = 0;       // bumped whenever f changes (sweeps, uploads)
+    TmaMaps maps[2];            // tiled-TMA descriptors of f[0], f[1]
 };
 
 struct dvm_adjoint {
@@ -79,6 +81,7 @@ struct dvm_adjoint {
     int graph_n = 0;
     int graph_cur = -1;
     int graph_st_cur = -1;
+    TmaMaps maps[2];            // tiled-TMA descriptors of phi[0], phi[1]
     // sensitivity scratch, allocated on first use
     double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr;
     double *vol = nullptr, *elem = nullptr, *dwall = nullptr, *sj = nullptr, *grad = nullptr;
@@ -149,6 +152,8 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     const DevGrid& g = st->grid->d;
     constexpr int KV = 16 / (2 * (int)sizeof(TS));
     a.ncell = m.ncell;
+    a.ni = m.ni;
+    a.nj = m.nj;
     a.nq = g.nvp / KV;
     a.nb = m.nb;
     if constexpr (sizeof(TC) == 8) {
@@ -170,6 +175,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     a.Fw_new = st->Fw[1 - src];
     a.Jpart = st->Jpart;
     a.respart = st->respart;
+    a.err = st->ctx->derr;
     return a;
 }
 
@@ -181,6 +187,8 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     const DevGrid& g = st->grid->d;
     constexpr int KV = 16 / (2 * (int)sizeof(TS));
     a.ncell = m.ncell;
+    a.ni = m.ni;
+    a.nj = m.nj;
     a.nq = g.nvp / KV;
     a.nb = m.nb;
     if constexpr (sizeof(TC) == 8) {
@@ -203,23 +211,26 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     a.Lam_old = ad->Lam[src];
     a.Lam_new = ad->Lam[1 - src];
     a.respart = ad->respart;
+    a.err = st->ctx->derr;
     return a;
 }
 
 cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
     switch (st->storage) {
-        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); return launch_primal_sweep(0, &a, res, st->ctx->stream); }
-        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); return launch_primal_sweep(1, &a, res, st->ctx->stream); }
-        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); return launch_primal_sweep(2, &a, res, st->ctx->stream); }
+        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); return launch_primal_sweep(0, &a, st->maps[src], res, st->ctx->stream); }
+        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); return launch_primal_sweep(1, &a, st->maps[src], res, st->ctx->stream); }
+        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); return launch_primal_sweep(2, &a, st->maps[src], res, st->ctx->stream); }
     }
 }
 
 cudaError_t enqueue_adjoint(dvm_adjoint* ad, int src, bool update = true, bool res = true) {
     cudaStream_t s = ad->st->ctx->stream;
+    const TmaMaps& pm = ad->maps[src];
+    const TmaMaps& fm = ad->st->maps[ad->st->cur];
     switch (ad->st->storage) {
-        case DVM_STORE_FP64: { auto a = adjoint_args<double, double>(ad, src); return launch_adjoint_sweep(0, &a, update, res, s); }
-        case DVM_STORE_FP32: { auto a = adjoint_args<float, float>(ad, src); return launch_adjoint_sweep(1, &a, update, res, s); }
-        default: { auto a = adjoint_args<__nv_bfloat16, float>(ad, src); return launch_adjoint_sweep(2, &a, update, res, s); }
+        case DVM_STORE_FP64: { auto a = adjoint_args<double, double>(ad, src); return launch_adjoint_sweep(0, &a, pm, fm, update, res, s); }
+        case DVM_STORE_FP32: { auto a = adjoint_args<float, float>(ad, src); return launch_adjoint_sweep(1, &a, pm, fm, update, res, s); }
+        default: { auto a = adjoint_args<__nv_bfloat16, float>(ad, src); return launch_adjoint_sweep(2, &a, pm, fm, update, res, s); }
     }
 }
 
@@ -330,12 +341,30 @@ int build_adjoint_graph(dvm_adjoint* ad, int K) {
     return DVM_OK;
 }
 
+// Read and clear the device error flag (after the stream has been synchronised).
+int check_device_flag(dvm_context* ctx) {
+    int e = 0;
+    CK(cudaMemcpy(&e, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(cudaMemset(ctx->derr, 0, sizeof(int)));
+        return fail(DVM_ERR_TIMEOUT, "a staged copy of a sweep did not complete within the wait limit");
+    }
+    return DVM_OK;
+}
+
 // read out[0..1] of the device into the pinned buffer and wait
 int fetch2(dvm_context* ctx, const double* dout, double* r) {
     CK(cudaMemcpyAsync(ctx->pinned, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pinned + 2, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     r[0] = ctx->pinned[0];
     r[1] = ctx->pinned[1];
+    int e = 0;
+    memcpy(&e, ctx->pinned + 2, sizeof(int));
+    if (e) {
+        CK(cudaMemset(ctx->derr, 0, sizeof(int)));
+        return fail(DVM_ERR_TIMEOUT, "a staged copy of a sweep did not complete within the wait limit");
+    }
     return DVM_OK;
 }
 
@@ -386,6 +415,14 @@ int dvm_context_create(dvm_context** out, int cuda_device, const dvm_options* op
     }
     e = cudaMallocHost((void**)&c->pinned, 64 * sizeof(double));
     if (e != cudaSuccess) { if (c->own_stream) cudaStreamDestroy(c->stream); delete c; return fail_cuda(e, "cudaMallocHost"); }
+    e = cudaMalloc((void**)&c->derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->derr, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFreeHost(c->pinned);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return fail_cuda(e, "error flag");
+    }
     *out = c;
     return DVM_OK;
 }
@@ -395,6 +432,7 @@ void dvm_context_destroy(dvm_context* c) {
     DeviceGuard dg(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->derr) cudaFree(c->derr);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -568,6 +606,13 @@ int dvm_state_create(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     if (rc) return bail(rc);
     st->bytes = acc;
     ctx->bytes += acc;
+    {
+        const int nq = g.nvp * (int)pair / 16;
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t me = make_tmamaps(st->f[b], m.ni, m.nj, nq, &st->maps[b]);
+            if (me != cudaSuccess) return bail(fail_cuda(me, "tensor map of f"));
+        }
+    }
     cudaStream_t s = ctx->stream;
     const double ang = dir_angle(*flow, DVM_DRAG);
     cudaError_t e = launch_flow_tables(g, st->fl, s);
@@ -649,6 +694,7 @@ int dvm_primal_iterate(dvm_state* st, int n, double* residual_out) {
         cudaError_t e = cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
         if (e != cudaSuccess) rc = fail_cuda(e, "residual history");
+        if (!rc) rc = check_device_flag(st->ctx);
         for (int i = 0; i < n && !rc; ++i) {
             const double r = sqrt(h[2 * i]) / st->r0;
             if (residual_out) residual_out[i] = r;
@@ -788,6 +834,13 @@ int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     if (rc) { dvm_adjoint_destroy(ad); return rc; }
     ad->bytes = acc;
     ctx->bytes += acc;
+    {
+        const int nq = g.nvp * (int)storage_bytes(st->storage) / 16;
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t me = make_tmamaps(ad->phi[b], m.ni, m.nj, nq, &ad->maps[b]);
+            if (me != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(me, "tensor map of phi"); }
+        }
+    }
     // M_l of this functional's direction (the normaliser D_l is the state's; recomputed into scratch)
     double* dtmp = nullptr;
     if ((rc = dalloc(ctx, &dtmp, m.ni))) { dvm_adjoint_destroy(ad); return rc; }
@@ -871,6 +924,7 @@ int dvm_adjoint_iterate(dvm_adjoint* ad, int n, double* residual_out) {
         cudaError_t e = cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ad->st->ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ad->st->ctx->stream);
         if (e != cudaSuccess) rc = fail_cuda(e, "residual history");
+        if (!rc) rc = check_device_flag(ad->st->ctx);
         for (int i = 0; i < n && !rc; ++i) {
             const double r = sqrt(h[2 * i]) / ad->r0;
             if (residual_out) residual_out[i] = r;

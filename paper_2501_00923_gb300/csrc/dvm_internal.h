@@ -1,6 +1,8 @@
 // Internal declarations of the DVM CUDA library: device-side data of meshes, velocity grids,
 // states and adjoints, and the kernel launchers.  Not part of the C ABI (see include/dvm.h).
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstddef>
@@ -44,10 +46,19 @@ struct DevFlow {
     double* wallM = nullptr;    // [ni] M_l = sum_{a<=0} w m a g_M1 / D_l for the drag direction
 };
 
+// Tiled-TMA descriptors of one distribution buffer viewed as [nj][ni][16-byte chunks]: boxes of
+// 32 chunks x 1 cell x 10 rows (a column with its halo rows) and x 8 rows (a side column).
+struct TmaMaps {
+    alignas(64) CUtensorMap col;
+    alignas(64) CUtensorMap side;
+};
+cudaError_t make_tmamaps(void* base, int ni, int nj, int nq, TmaMaps* out);
+
 // Arguments of the primal sweep.  TS = storage type, TC = compute type.
 template <class TS, class TC>
 struct PrimalArgs {
     int ncell, nq;                          // nq = nvp / KV  (16-byte chunks per cell)
+    int ni, nj;
     const int4* nb;
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
     const TC* V;
@@ -65,6 +76,7 @@ struct PrimalArgs {
     double* Fw_new;
     double* Jpart;
     double* respart;
+    int* err;                               // set when a staged copy never completed
 };
 
 // Per-cell constants of the adjoint linearisation (see k_adjoint_cellconst).
@@ -76,6 +88,7 @@ struct alignas(sizeof(TC) * 4) AdjCell {
 template <class TS, class TC>
 struct AdjointArgs {
     int ncell, nq;
+    int ni, nj;
     const int4* nb;
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
     const TC* V;
@@ -94,6 +107,7 @@ struct AdjointArgs {
     const double* Lam_old;                  // wall coupling of the previous sweep
     double* Lam_new;
     double* respart;
+    int* err;
 };
 
 // ---------------------------------------------------------------------------------- launchers
@@ -105,10 +119,12 @@ cudaError_t launch_fill_freestream(int storage, void* f, int ncell, const DevGri
                                    cudaStream_t s);
 cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
                            double* Fw, cudaStream_t s);
-// res = false: skip the residual (only the sweeps whose residual is read need it)
-cudaError_t launch_primal_sweep(int storage, const void* args, bool res, cudaStream_t s);
-// update = false: no phi update, only the couplings (Z, Lambda) of phi_old into the *_new slots
-cudaError_t launch_adjoint_sweep(int storage, const void* args, bool update, bool res, cudaStream_t s);
+// res = false: skip the residual (only the sweeps whose residual is read need it).  maps: of f_old.
+cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
+// update = false: no phi update, only the couplings (Z, Lambda) of phi_old into the *_new slots.
+// phi_maps: of phi_old; f_maps: of the primal f.
+cudaError_t launch_adjoint_sweep(int storage, const void* args, const TmaMaps& phi_maps, const TmaMaps& f_maps,
+                                 bool update, bool res, cudaStream_t s);
 cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
                                      void* out, cudaStream_t s);
 // out[0] = sum respart; out[1] = sum_l Jpart_l + Fw_l M_l (Fw/M may be null -> only sum Jpart)

@@ -173,19 +173,141 @@ template <> struct Sum<float> {      // Kahan-compensated lane sum, double-float
 // or both (a one-layer mesh).  Each class gets its own compiled loop so that interior cells, which
 // are all but 2/nj of the mesh, carry no boundary logic.
 enum { kInterior = 0, kWallCell = 1, kFarCell = 2, kWallFar = 3 };
-constexpr int kBlockIters = 8;   // chunks summed in FP32 before one compensated add
+constexpr int kBlockIters = 8;   // chunk rows summed in FP32 before one compensated add
+
+// ------------------------------------------------------------------ tiled-TMA pipeline
+// A block owns 8 radially adjacent cells (i, j0..j0+7), one warp per cell.  The distribution is a
+// 3D tensor [nj][ni][16-byte chunks]; for each row of 32 chunks (32 lanes x 16 B) the block needs
+// its column with one halo row on each side (rows j0-1..j0+8) and the columns i-1 and i+1 (rows
+// j0..j0+7).  Three tiled TMA loads (cp.async.bulk.tensor) bring them into one pipeline stage:
+// periodicity in i is a coordinate, rows outside [0, nj) are zero-filled and never used.  Thread 0
+// of warp 0 produces kStages chunk rows ahead; every warp waits on the stage's "full" mbarrier,
+// computes, and arrives on its "empty" mbarrier; the producer refills a stage once all warps have
+// released it.  Every wait is bounded (kWaitTries tries of about kSuspendNs each): a wait that
+// runs out sets *err, the block stops, and the producer drains the copies it issued.
+constexpr int kStages = 4;
+constexpr int kPrimalRows = 26;      // column 10 rows + west 8 + east 8
+constexpr int kAdjointRows = 34;     // phi column 10 + phi west 8 + phi east 8 + f 8
+constexpr unsigned kSuspendNs = 1000000;
+constexpr unsigned kWaitTries = 1000;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    for (unsigned t = 0; t < kWaitTries; ++t)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Producer side of a block's pipeline.
+struct Feed {
+    const CUtensorMap* col;      // box 32 chunks x 1 cell x 10 rows (the value being swept)
+    const CUtensorMap* side;     // box 32 chunks x 1 cell x 8 rows (the same buffer)
+    const CUtensorMap* extra;    // box 32 chunks x 1 cell x 8 rows of a second buffer (adjoint: f), or null
+    int i, im, ip, j0, rows;     // block column, its periodic neighbours, first row, rows per stage
+    uint4* stage;                // kStages x rows x 32 chunks
+    uint64_t* full;
+    uint64_t* empty;
+    __device__ __forceinline__ void issue(unsigned it) const {
+        const unsigned st = it % kStages;
+        uint4* d = stage + (size_t)st * rows * 32;
+        const int x = (int)(it * 32u * 4u);                   // uint32 elements: 16-byte aligned
+        mbar_expect_tx(&full[st], (unsigned)rows * 512u);
+        tma_load_3d(d, col, x, i, j0 - 1, &full[st]);
+        tma_load_3d(d + 10 * 32, side, x, im, j0, &full[st]);
+        tma_load_3d(d + 18 * 32, side, x, ip, j0, &full[st]);
+        if (extra) tma_load_3d(d + 26 * 32, extra, x, i, j0, &full[st]);
+    }
+};
+
+// 2^x by the hardware approximation (ex2.approx.ftz.f32: relative error 2^-22 on the fraction).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// g1 = n0 exp(-|v-u|^2/(2T)) written as 2^(t kA + kB) with t = |v|^2/2 - v.u (one FMA chain).
+// FP64: exp(t kA + kB) with the natural-log constants.
+template <class TC> struct Gauss;
+template <> struct Gauss<float> {
+    float kA, kB;
+    __device__ __forceinline__ void setup(float rho, float u1, float u2, float T) {   // FP32 only
+        constexpr float L2E = 1.44269504088896341f;
+        const float iT = 1.0f / T;
+        kA = -L2E * iT;
+        kB = log2f(rho * iT * 0.159154943091895336f) - L2E * 0.5f * (u1 * u1 + u2 * u2) * iT;
+    }
+    __device__ __forceinline__ float eval(float t) const { return ex2_approx(fmaf(t, kA, kB)); }
+};
+template <> struct Gauss<double> {
+    double kA, kB;
+    __device__ __forceinline__ void setup(double rho, double u1, double u2, double T) {
+        kA = -1.0 / T;
+        kB = log(rho / (2.0 * kPi * T)) - 0.5 * (u1 * u1 + u2 * u2) / T;
+    }
+    __device__ __forceinline__ double eval(double t) const { return exp(fma(t, kA, kB)); }
+};
+
+// One pipeline step shared by both sweeps: wait for stage `it`, run `body` on it, release it, and
+// (producer) refill it with chunk row it + kStages.  Returns false when a wait ran out.
+template <class Body>
+__device__ __forceinline__ bool pipeline_step(const Feed& F, unsigned it, unsigned niter, int lane, bool producer,
+                                              Body&& body) {
+    const unsigned st = it % kStages, ph = (it / kStages) & 1u;
+    const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&F.full[st], ph));
+    if (!got) return false;
+    body(F.stage + (size_t)st * F.rows * 32);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&F.empty[st]);
+    bool pok = true;
+    if (producer && it + kStages < niter) {
+        pok = mbar_wait_bounded(&F.empty[st], ph);
+        if (pok) {
+            fence_proxy_async();
+            F.issue(it + kStages);
+        }
+    }
+    return __shfl_sync(0xffffffffu, pok ? 1 : 0, 0) != 0;
+}
 
 // ================================================================== primal sweep (K1)
 // One point-implicit sweep of Eq. (numerpr_gov), first-order upwind, fused with the moments of
 // the new state (Eq. macint_reduce), its wall density (Eq. formula_bgk_fdw), the drag partial of
 // Eq. (numer_J) and (kRes) the residual R(f_old) = D (f_old - f_new).
 // D = V/tau + sum_e max(a_e, 0) = V/tau + (1/2) sum_e |a_e| because the faces of a cell close
-// (sum_e A_e n_e = 0); the inflow faces add -min(a_e, 0) F_up to the right-hand side.  Neighbour
-// chunks are loaded whether or not a face is an inflow face (they come from L2: the rows j-1, j,
-// j+1 of the previous sweep's f are resident), which keeps the loop free of per-velocity branches.
+// (sum_e A_e n_e = 0); the inflow faces add -min(a_e, 0) F_up to the right-hand side.  The staged
+// neighbour chunks are used whether or not a face is an inflow face (the factor min(a_e, 0) is 0),
+// which keeps the loop free of per-velocity branches.
 template <class TS, bool kRes, int kBnd>
-__device__ __forceinline__ void primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int lane,
-                                            const int4 nb) {
+__device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
+                                            int lane, const Feed& F, bool producer) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -195,85 +317,83 @@ __device__ __forceinline__ void primal_cell(const PrimalArgs<TS, typename Pack<T
     const TC2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
     const double4 pr = P.prim_old[c];
     const TC rho = (TC)pr.x, u1 = (TC)pr.y, u2 = (TC)pr.z, T = (TC)pr.w;
-    const TC iT = TC(1) / T;
-    const TC n0 = rho * iT * TC(0.15915494309189533577);          // rho / (2 pi T)
-    const TC inv2T = TC(0.5) * iT, halfT = TC(0.5) * T;
-    const TC Vt = P.V[c] * rho * sqrt(T) * (TC)P.inv_tau_inf;      // V / tau
+    Gauss<TC> G;
+    G.setup(rho, u1, u2, T);
+    const TC halfT = TC(0.5) * T;
+    const TC Vt = P.V[c] * rho * sqrt(T) * (TC)P.inv_tau_inf;        // V / tau
     TC cw1 = TC(0), cw2 = TC(0), invA = TC(0);
     if (wall) {
-        cw1 = (TC)(P.Fw_old[c] / P.wallD[c]);
+        cw1 = (TC)P.Fw_old[c] / (TC)P.wallD[c];
         cw2 = cw1 * P.halfTw;
         invA = TC(1) / sqrt(S3.x * S3.x + S3.y * S3.y);
     }
-    const uint4* fo = reinterpret_cast<const uint4*>(P.f_old);
     uint4* fw = reinterpret_cast<uint4*>(P.f_new);
-    const unsigned nq = (unsigned)P.nq;
-    const unsigned oc = (unsigned)c * nq, o0 = (unsigned)nb.x * nq, o2 = (unsigned)nb.z * nq;
-    const unsigned o1 = far ? oc : (unsigned)nb.y * nq, o3 = wall ? oc : (unsigned)nb.w * nq;
+    const unsigned nq = (unsigned)P.nq, niter = (nq + 31) / 32, oc = (unsigned)c * nq;
 
     Sum<TC> m0, m1, m2, m3, fwa, ja, rs;
-    unsigned q = lane;
-    uint4 ro_next = q < nq ? ldg16(fo + oc + q) : make_uint4(0, 0, 0, 0);
-    while (q < nq) {
+    bool ok = true;
+    unsigned it = 0;
+    while (it < niter && ok) {
         TC bm0 = TC(0), bm1 = TC(0), bm2 = TC(0), bm3 = TC(0), bfw = TC(0), bj = TC(0), brs = TC(0);
-        for (int it = 0; it < kBlockIters && q < nq; ++it, q += 32) {
-            const uint4 ro = ro_next;
-            if (q + 32 < nq) ro_next = ldg16(fo + oc + q + 32);
-            const uint4 r0 = ldg16(fo + o0 + q);
-            const uint4 r2 = ldg16(fo + o2 + q);
-            uint4 r1 = ro, r3 = ro;
-            if (!far) r1 = ldg16(fo + o1 + q);
-            if (!wall) r3 = ldg16(fo + o3 + q);
-            TC fo1[KV], fo2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV], e32[KV];
-            PK::unpack(ro, fo1, fo2);
-            PK::unpack(r0, e01, e02);
-            PK::unpack(r1, e11, e12);
-            PK::unpack(r2, e21, e22);
-            PK::unpack(r3, e31, e32);
-            TC fn1[KV], fn2[KV];
+        for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
+            ok = pipeline_step(F, it, niter, lane, producer, [&](const uint4* d) {
+                const unsigned q = it * 32 + lane;
+                if (q >= nq) return;
+                const uint4 ro = d[(w + 1) * 32 + lane];
+                const uint4 r0 = d[(10 + w) * 32 + lane], r2 = d[(18 + w) * 32 + lane];
+                const uint4 r1 = far ? ro : d[(w + 2) * 32 + lane];
+                const uint4 r3 = wall ? ro : d[w * 32 + lane];
+                TC fo1[KV], fo2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV], e32[KV];
+                PK::unpack(ro, fo1, fo2);
+                PK::unpack(r0, e01, e02);
+                PK::unpack(r1, e11, e12);
+                PK::unpack(r2, e21, e22);
+                PK::unpack(r3, e31, e32);
+                TC fn1[KV], fn2[KV];
 #pragma unroll
-            for (int kk = 0; kk < KV; ++kk) {
-                const int k = q * KV + kk;
-                const TC4 t = P.vt[k];
-                const TC vx = t.x, vy = t.y, w = t.z, hv = t.w;
-                const TC a0 = S0.x * vx + S0.y * vy, a1 = S1.x * vx + S1.y * vy;
-                const TC a2 = S2.x * vx + S2.y * vy, a3 = S3.x * vx + S3.y * vy;
-                if (far) { const TC2 d = P.fd[k]; e11[kk] = d.x; e12[kk] = d.y; }
-                if (wall) { const TC gw = P.gw[k]; e31[kk] = cw1 * gw; e32[kk] = cw2 * gw; }
-                const TC D = Vt + TC(0.5) * ((fabs(a0) + fabs(a1)) + (fabs(a2) + fabs(a3)));
-                const TC dx = vx - u1, dy = vy - u2;
-                const TC g1 = n0 * fexp<TC>(-(dx * dx + dy * dy) * inv2T);
-                TC r1_ = Vt * g1;
-                TC r2_ = halfT * r1_;
-                const TC b0 = fmin(a0, TC(0)), b1 = fmin(a1, TC(0)), b2 = fmin(a2, TC(0)), b3 = fmin(a3, TC(0));
-                r1_ -= b0 * e01[kk]; r2_ -= b0 * e02[kk];
-                r1_ -= b1 * e11[kk]; r2_ -= b1 * e12[kk];
-                r1_ -= b2 * e21[kk]; r2_ -= b2 * e22[kk];
-                r1_ -= b3 * e31[kk]; r2_ -= b3 * e32[kk];
-                const TC iD = frcp<TC>(D);
-                fn1[kk] = r1_ * iD;
-                fn2[kk] = r2_ * iD;
-                if (kRes) {
-                    const TC R1 = D * (fo1[kk] - fn1[kk]), R2 = D * (fo2[kk] - fn2[kk]);
-                    brs += w * (R1 * R1 + R2 * R2);
+                for (int kk = 0; kk < KV; ++kk) {
+                    const int k = q * KV + kk;
+                    const TC4 t = P.vt[k];
+                    const TC vx = t.x, vy = t.y, wk = t.z, hv = t.w;
+                    const TC a0 = S0.x * vx + S0.y * vy, a1 = S1.x * vx + S1.y * vy;
+                    const TC a2 = S2.x * vx + S2.y * vy, a3 = S3.x * vx + S3.y * vy;
+                    if (far) { const TC2 fd = P.fd[k]; e11[kk] = fd.x; e12[kk] = fd.y; }
+                    if (wall) { const TC gw = P.gw[k]; e31[kk] = cw1 * gw; e32[kk] = cw2 * gw; }
+                    const TC D = Vt + TC(0.5) * ((fabs(a0) + fabs(a1)) + (fabs(a2) + fabs(a3)));
+                    const TC g1 = G.eval(fma(vy, -u2, fma(vx, -u1, hv)));
+                    TC r1_ = Vt * g1;
+                    TC r2_ = halfT * r1_;
+                    const TC b0 = fmin(a0, TC(0)), b1 = fmin(a1, TC(0)), b2 = fmin(a2, TC(0)), b3 = fmin(a3, TC(0));
+                    r1_ -= b0 * e01[kk]; r2_ -= b0 * e02[kk];
+                    r1_ -= b1 * e11[kk]; r2_ -= b1 * e12[kk];
+                    r1_ -= b2 * e21[kk]; r2_ -= b2 * e22[kk];
+                    r1_ -= b3 * e31[kk]; r2_ -= b3 * e32[kk];
+                    const TC iD = frcp<TC>(D);
+                    fn1[kk] = r1_ * iD;
+                    fn2[kk] = r2_ * iD;
+                    if (kRes) {
+                        const TC R1 = D * (fo1[kk] - fn1[kk]), R2 = D * (fo2[kk] - fn2[kk]);
+                        brs += wk * (R1 * R1 + R2 * R2);
+                    }
+                    const TC wf1 = wk * fn1[kk];
+                    bm0 += wf1;
+                    bm1 += wf1 * vx;
+                    bm2 += wf1 * vy;
+                    bm3 += wf1 * hv + wk * fn2[kk];
+                    if (wall) {
+                        const TC p3 = a3 - b3;                   // max(a3, 0)
+                        bfw += wf1 * p3;
+                        bj += wf1 * p3 * (P.dirx * vx + P.diry * vy);
+                    }
                 }
-                const TC wf1 = w * fn1[kk];
-                bm0 += wf1;
-                bm1 += wf1 * vx;
-                bm2 += wf1 * vy;
-                bm3 += wf1 * hv + w * fn2[kk];
-                if (wall) {
-                    const TC p3 = a3 - b3;                       // max(a3, 0)
-                    bfw += wf1 * p3;
-                    bj += wf1 * p3 * (P.dirx * vx + P.diry * vy);
-                }
-            }
-            stg16(fw + oc + q, PK::pack(fn1, fn2));
+                stg16(fw + oc + q, PK::pack(fn1, fn2));
+            });
         }
         m0.add(bm0); m1.add(bm1); m2.add(bm2); m3.add(bm3);
         if (kRes) rs.add(brs);
         if (wall) { fwa.add(bfw); ja.add(bj); }
     }
+    if (!ok) return false;
     const TC M0 = m0.total(), M1 = m1.total(), M2 = m2.total(), M3 = m3.total();
     TC RS = TC(0), FW = TC(0), JA = TC(0);
     if (kRes) RS = rs.total();
@@ -292,20 +412,70 @@ __device__ __forceinline__ void primal_cell(const PrimalArgs<TS, typename Pack<T
             P.Jpart[c] = (double)JA;
         }
     }
+    return true;
+}
+
+constexpr int primal_smem_bytes() { return kStages * kPrimalRows * 512 + 2 * kStages * 8; }
+constexpr int adjoint_smem_bytes() { return kStages * kAdjointRows * 512 + 2 * kStages * 8; }
+
+// Block prologue/epilogue shared by both sweeps: barriers, active warps, the producer's first
+// stages and, on exit, the drain of copies still in flight.
+struct BlockPipe {
+    Feed F;
+    unsigned niter;
+    int A;                        // active warps (cells j0 .. j0+A-1 exist)
+};
+
+__device__ __forceinline__ bool block_pipe_setup(BlockPipe& B, unsigned char* smem, int rows, int nj, int ni,
+                                                 unsigned nq, const CUtensorMap* col, const CUtensorMap* side,
+                                                 const CUtensorMap* extra) {
+    const int i = blockIdx.x, j0 = blockIdx.y * kWarpsPerBlock;
+    B.A = min(kWarpsPerBlock, nj - j0);
+    B.niter = (nq + 31) / 32;
+    B.F.col = col; B.F.side = side; B.F.extra = extra;
+    B.F.i = i; B.F.im = (i - 1 + ni) % ni; B.F.ip = (i + 1) % ni; B.F.j0 = j0; B.F.rows = rows;
+    B.F.stage = reinterpret_cast<uint4*>(smem);
+    B.F.full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * rows * 512);
+    B.F.empty = B.F.full + kStages;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&B.F.full[s], 1);
+            mbar_init(&B.F.empty[s], (unsigned)B.A);
+        }
+        fence_mbar_init();
+        for (unsigned it = 0; it < min((unsigned)kStages, B.niter); ++it) B.F.issue(it);
+    }
+    __syncthreads();
+    return (int)(threadIdx.x >> 5) < B.A;
+}
+
+// Producer drain after an aborted sweep: wait (bounded) for every stage it may still have in flight.
+__device__ __forceinline__ void block_pipe_drain(const BlockPipe& B) {
+    for (int s = 0; s < kStages; ++s)
+        for (unsigned ph = 0; ph < 2; ++ph) mbar_try_wait(&B.F.full[s], ph);
 }
 
 template <class TS, bool kRes>
-__global__ void __launch_bounds__(256, 3) k_primal_sweep(PrimalArgs<TS, typename Pack<TS>::TC> P) {
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (c >= P.ncell) return;
-    const int4 nb = P.nb[c];
-    const int bnd = (nb.w == kWall ? kWallCell : 0) | (nb.y < 0 ? kFarCell : 0);
+__global__ void __launch_bounds__(256, 4) k_primal_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
+                                                         const __grid_constant__ CUtensorMap m10,
+                                                         const __grid_constant__ CUtensorMap m8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    BlockPipe B;
+    if (!block_pipe_setup(B, smem, kPrimalRows, P.nj, P.ni, (unsigned)P.nq, &m10, &m8, nullptr)) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = B.F.j0 + w, c = j * P.ni + B.F.i;
+    const bool producer = (threadIdx.x == 0);
+    const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
+    bool ok;
     switch (bnd) {
-        case kInterior: primal_cell<TS, kRes, kInterior>(P, c, lane, nb); break;
-        case kWallCell: primal_cell<TS, kRes, kWallCell>(P, c, lane, nb); break;
-        case kFarCell: primal_cell<TS, kRes, kFarCell>(P, c, lane, nb); break;
-        default: primal_cell<TS, kRes, kWallFar>(P, c, lane, nb); break;
+        case kInterior: ok = primal_cell<TS, kRes, kInterior>(P, c, w, lane, B.F, producer); break;
+        case kWallCell: ok = primal_cell<TS, kRes, kWallCell>(P, c, w, lane, B.F, producer); break;
+        case kFarCell: ok = primal_cell<TS, kRes, kFarCell>(P, c, w, lane, B.F, producer); break;
+        default: ok = primal_cell<TS, kRes, kWallFar>(P, c, w, lane, B.F, producer); break;
+    }
+    if (!ok) {
+        if (lane == 0) atomicExch(P.err, 1);
+        if (producer) block_pipe_drain(B);
     }
 }
 
@@ -320,8 +490,8 @@ __global__ void __launch_bounds__(256, 3) k_primal_sweep(PrimalArgs<TS, typename
 // come precomputed in AdjCell.  kUpdate = false: phi is not advanced; the couplings of phi_old are
 // written to the *_new slots (used after an upload of phi or a change of the primal state).
 template <class TS, bool kUpdate, bool kRes, int kBnd>
-__device__ __forceinline__ void adjoint_cell(const AdjointArgs<TS, typename Pack<TS>::TC>& P, int c, int lane,
-                                             const int4 nb) {
+__device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
+                                             int lane, const Feed& F, bool producer) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -337,87 +507,87 @@ __device__ __forceinline__ void adjoint_cell(const AdjointArgs<TS, typename Pack
     TC gb1s = TC(0), srcB = TC(0);
     if (wall) {
         const TC A = sqrt(S3.x * S3.x + S3.y * S3.y);
-        gb1s = (TC)(1.0 / P.wallD[c]);
+        gb1s = TC(1) / (TC)P.wallD[c];
         srcB = (TC)((P.wallM[c] + P.Lam_old[c])) / A;             // (M + Lambda)/A multiplies a3
     }
-    const uint4* po = reinterpret_cast<const uint4*>(P.phi_old);
-    const uint4* fp = reinterpret_cast<const uint4*>(P.f);
     uint4* pw = reinterpret_cast<uint4*>(P.phi_new);
-    const unsigned nq = (unsigned)P.nq;
-    const unsigned oc = (unsigned)c * nq, o0 = (unsigned)nb.x * nq, o2 = (unsigned)nb.z * nq;
-    const unsigned o1 = far ? oc : (unsigned)nb.y * nq, o3 = wall ? oc : (unsigned)nb.w * nq;
+    const unsigned nq = (unsigned)P.nq, niter = (nq + 31) / 32, oc = (unsigned)c * nq;
 
     Sum<TC> sh, shx, shy, shc, sg2, sr, lam, rs;
-    unsigned q = lane;
-    uint4 ro_next = make_uint4(0, 0, 0, 0), rf_next = make_uint4(0, 0, 0, 0);
-    if (q < nq) { ro_next = ldg16(po + oc + q); rf_next = ldg16(fp + oc + q); }
-    while (q < nq) {
+    bool ok = true;
+    unsigned it = 0;
+    while (it < niter && ok) {
         TC bh = TC(0), bhx = TC(0), bhy = TC(0), bhc = TC(0), bg2 = TC(0), br = TC(0), bl = TC(0), brs = TC(0);
-        for (int it = 0; it < kBlockIters && q < nq; ++it, q += 32) {
-            const uint4 ro = ro_next, rf = rf_next;
-            if (q + 32 < nq) { ro_next = ldg16(po + oc + q + 32); rf_next = ldg16(fp + oc + q + 32); }
-            uint4 r0 = ro, r1 = ro, r2 = ro, r3 = ro;
-            if (kUpdate) {
-                r0 = ldg16(po + o0 + q);
-                r2 = ldg16(po + o2 + q);
-                if (!far) r1 = ldg16(po + o1 + q);
-                if (!wall) r3 = ldg16(po + o3 + q);
-            }
-            TC po1[KV], po2[KV], f1[KV], f2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV],
-                e32[KV];
-            PK::unpack(ro, po1, po2);
-            PK::unpack(rf, f1, f2);
-            PK::unpack(r0, e01, e02);
-            PK::unpack(r1, e11, e12);
-            PK::unpack(r2, e21, e22);
-            PK::unpack(r3, e31, e32);
-            TC pn1[KV], pn2[KV];
-#pragma unroll
-            for (int kk = 0; kk < KV; ++kk) {
-                const int k = q * KV + kk;
-                const TC4 t = P.vt[k];
-                const TC vx = t.x, vy = t.y, w = t.z, hv = t.w;
-                const TC a3 = S3.x * vx + S3.y * vy;
+        for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
+            ok = pipeline_step(F, it, niter, lane, producer, [&](const uint4* d) {
+                const unsigned q = it * 32 + lane;
+                if (q >= nq) return;
+                const uint4 ro = d[(w + 1) * 32 + lane], rf = d[(26 + w) * 32 + lane];
+                uint4 r0 = ro, r1 = ro, r2 = ro, r3 = ro;
                 if (kUpdate) {
-                    const TC a0 = S0.x * vx + S0.y * vy, a1 = S1.x * vx + S1.y * vy, a2 = S2.x * vx + S2.y * vy;
-                    const TC D = Vt + TC(0.5) * ((fabs(a0) + fabs(a1)) + (fabs(a2) + fabs(a3)));
-                    TC r1_ = z0 + z1 * vx + z2 * vy + z3 * hv;
-                    TC r2_ = z3;
-                    const TC p0 = fmax(a0, TC(0)), p2 = fmax(a2, TC(0)), p3 = fmax(a3, TC(0));
-                    r1_ += p0 * e01[kk]; r2_ += p0 * e02[kk];
-                    r1_ += p2 * e21[kk]; r2_ += p2 * e22[kk];
-                    if (!far) { const TC p1 = fmax(a1, TC(0)); r1_ += p1 * e11[kk]; r2_ += p1 * e12[kk]; }
-                    if (wall) r1_ -= p3 * (P.dirx * vx + P.diry * vy + srcB);
-                    else { r1_ += p3 * e31[kk]; r2_ += p3 * e32[kk]; }
-                    const TC iD = frcp<TC>(D);
-                    pn1[kk] = r1_ * iD;
-                    pn2[kk] = r2_ * iD;
-                    if (kRes) {
-                        const TC R1 = D * (po1[kk] - pn1[kk]), R2 = D * (po2[kk] - pn2[kk]);
-                        brs += w * (R1 * R1 + R2 * R2);
-                    }
-                } else {
-                    pn1[kk] = po1[kk];
-                    pn2[kk] = po2[kk];
+                    r0 = d[(10 + w) * 32 + lane];
+                    r2 = d[(18 + w) * 32 + lane];
+                    if (!far) r1 = d[(w + 2) * 32 + lane];
+                    if (!wall) r3 = d[w * 32 + lane];
                 }
-                // couplings of the next sweep, from the new phi
-                const TC dx = vx - u1, dy = vy - u2, c2 = dx * dx + dy * dy;
-                const TC wg1 = w * n0 * fexp<TC>(-c2 * inv2T);
-                const TC h = wg1 * (pn1[kk] + halfT * pn2[kk]);
-                bh += h;
-                bhx += h * dx;
-                bhy += h * dy;
-                bhc += h * c2;
-                bg2 += wg1 * pn2[kk];
-                br += w * (pn1[kk] * f1[kk] + pn2[kk] * f2[kk]) - h;     // w phi.(f - g)
-                if (wall) bl += w * fmin(a3, TC(0)) * P.gw[k] * gb1s * (pn1[kk] + P.halfTw * pn2[kk]);
-            }
-            if (kUpdate) stg16(pw + oc + q, PK::pack(pn1, pn2));
+                TC po1[KV], po2[KV], f1[KV], f2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV],
+                    e31[KV], e32[KV];
+                PK::unpack(ro, po1, po2);
+                PK::unpack(rf, f1, f2);
+                PK::unpack(r0, e01, e02);
+                PK::unpack(r1, e11, e12);
+                PK::unpack(r2, e21, e22);
+                PK::unpack(r3, e31, e32);
+                TC pn1[KV], pn2[KV];
+#pragma unroll
+                for (int kk = 0; kk < KV; ++kk) {
+                    const int k = q * KV + kk;
+                    const TC4 t = P.vt[k];
+                    const TC vx = t.x, vy = t.y, wk = t.z, hv = t.w;
+                    const TC a3 = S3.x * vx + S3.y * vy;
+                    if (kUpdate) {
+                        const TC a0 = S0.x * vx + S0.y * vy, a1 = S1.x * vx + S1.y * vy;
+                        const TC a2 = S2.x * vx + S2.y * vy;
+                        const TC D = Vt + TC(0.5) * ((fabs(a0) + fabs(a1)) + (fabs(a2) + fabs(a3)));
+                        TC r1_ = z0 + z1 * vx + z2 * vy + z3 * hv;
+                        TC r2_ = z3;
+                        const TC p0 = fmax(a0, TC(0)), p2 = fmax(a2, TC(0)), p3 = fmax(a3, TC(0));
+                        r1_ += p0 * e01[kk]; r2_ += p0 * e02[kk];
+                        r1_ += p2 * e21[kk]; r2_ += p2 * e22[kk];
+                        if (!far) { const TC p1 = fmax(a1, TC(0)); r1_ += p1 * e11[kk]; r2_ += p1 * e12[kk]; }
+                        if (wall) r1_ -= p3 * (P.dirx * vx + P.diry * vy + srcB);
+                        else { r1_ += p3 * e31[kk]; r2_ += p3 * e32[kk]; }
+                        const TC iD = frcp<TC>(D);
+                        pn1[kk] = r1_ * iD;
+                        pn2[kk] = r2_ * iD;
+                        if (kRes) {
+                            const TC R1 = D * (po1[kk] - pn1[kk]), R2 = D * (po2[kk] - pn2[kk]);
+                            brs += wk * (R1 * R1 + R2 * R2);
+                        }
+                    } else {
+                        pn1[kk] = po1[kk];
+                        pn2[kk] = po2[kk];
+                    }
+                    // couplings of the next sweep, from the new phi
+                    const TC dx = vx - u1, dy = vy - u2, c2 = dx * dx + dy * dy;
+                    const TC wg1 = wk * n0 * fexp<TC>(-c2 * inv2T);
+                    const TC h = wg1 * (pn1[kk] + halfT * pn2[kk]);
+                    bh += h;
+                    bhx += h * dx;
+                    bhy += h * dy;
+                    bhc += h * c2;
+                    bg2 += wg1 * pn2[kk];
+                    br += wk * (pn1[kk] * f1[kk] + pn2[kk] * f2[kk]) - h;     // w phi.(f - g)
+                    if (wall) bl += wk * fmin(a3, TC(0)) * P.gw[k] * gb1s * (pn1[kk] + P.halfTw * pn2[kk]);
+                }
+                if (kUpdate) stg16(pw + oc + q, PK::pack(pn1, pn2));
+            });
         }
         sh.add(bh); shx.add(bhx); shy.add(bhy); shc.add(bhc); sg2.add(bg2); sr.add(br);
         if (kRes) rs.add(brs);
         if (wall) lam.add(bl);
     }
+    if (!ok) return false;
     const TC Sh = sh.total(), Shx = shx.total(), Shy = shy.total(), Shc = shc.total();
     const TC Sg2 = sg2.total(), Sr = sr.total();
     TC RS = TC(0), LAM = TC(0);
@@ -441,20 +611,31 @@ __device__ __forceinline__ void adjoint_cell(const AdjointArgs<TS, typename Pack
         }
         if (wall) P.Lam_new[c] = (double)LAM;
     }
+    return true;
 }
 
 template <class TS, bool kUpdate, bool kRes>
-__global__ void __launch_bounds__(256, 3) k_adjoint_sweep(AdjointArgs<TS, typename Pack<TS>::TC> P) {
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (c >= P.ncell) return;
-    const int4 nb = P.nb[c];
-    const int bnd = (nb.w == kWall ? kWallCell : 0) | (nb.y < 0 ? kFarCell : 0);
+__global__ void __launch_bounds__(256, 3) k_adjoint_sweep(const AdjointArgs<TS, typename Pack<TS>::TC> P,
+                                                          const __grid_constant__ CUtensorMap m10,
+                                                          const __grid_constant__ CUtensorMap m8,
+                                                          const __grid_constant__ CUtensorMap mf8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    BlockPipe B;
+    if (!block_pipe_setup(B, smem, kAdjointRows, P.nj, P.ni, (unsigned)P.nq, &m10, &m8, &mf8)) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = B.F.j0 + w, c = j * P.ni + B.F.i;
+    const bool producer = (threadIdx.x == 0);
+    const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
+    bool ok;
     switch (bnd) {
-        case kInterior: adjoint_cell<TS, kUpdate, kRes, kInterior>(P, c, lane, nb); break;
-        case kWallCell: adjoint_cell<TS, kUpdate, kRes, kWallCell>(P, c, lane, nb); break;
-        case kFarCell: adjoint_cell<TS, kUpdate, kRes, kFarCell>(P, c, lane, nb); break;
-        default: adjoint_cell<TS, kUpdate, kRes, kWallFar>(P, c, lane, nb); break;
+        case kInterior: ok = adjoint_cell<TS, kUpdate, kRes, kInterior>(P, c, w, lane, B.F, producer); break;
+        case kWallCell: ok = adjoint_cell<TS, kUpdate, kRes, kWallCell>(P, c, w, lane, B.F, producer); break;
+        case kFarCell: ok = adjoint_cell<TS, kUpdate, kRes, kFarCell>(P, c, w, lane, B.F, producer); break;
+        default: ok = adjoint_cell<TS, kUpdate, kRes, kWallFar>(P, c, w, lane, B.F, producer); break;
+    }
+    if (!ok) {
+        if (lane == 0) atomicExch(P.err, 1);
+        if (producer) block_pipe_drain(B);
     }
 }
 
@@ -938,34 +1119,80 @@ cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const D
 }
 
 template <class TS, class TC>
-void primal_launch(const void* args, bool res, cudaStream_t s) {
+void primal_launch(const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
     const auto& a = *static_cast<const PrimalArgs<TS, TC>*>(args);
-    const int nb = cdiv(a.ncell, kWarpsPerBlock);
-    if (res) k_primal_sweep<TS, true><<<nb, 256, 0, s>>>(a);
-    else k_primal_sweep<TS, false><<<nb, 256, 0, s>>>(a);
+    const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
+    constexpr int sm = primal_smem_bytes();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_primal_sweep<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_sweep<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    if (res) k_primal_sweep<TS, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    else k_primal_sweep<TS, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
 }
 
-cudaError_t launch_primal_sweep(int storage, const void* args, bool res, cudaStream_t s) {
-    if (storage == 0) primal_launch<double, double>(args, res, s);
-    else if (storage == 1) primal_launch<float, float>(args, res, s);
-    else primal_launch<__nv_bfloat16, float>(args, res, s);
+cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
+    if (storage == 0) primal_launch<double, double>(args, maps, res, s);
+    else if (storage == 1) primal_launch<float, float>(args, maps, res, s);
+    else primal_launch<__nv_bfloat16, float>(args, maps, res, s);
     return cudaGetLastError();
 }
 
 template <class TS, class TC>
-void adjoint_launch(const void* args, bool update, bool res, cudaStream_t s) {
+void adjoint_launch(const void* args, const TmaMaps& phi_maps, const TmaMaps& f_maps, bool update, bool res,
+                    cudaStream_t s) {
     const auto& a = *static_cast<const AdjointArgs<TS, TC>*>(args);
-    const int nb = cdiv(a.ncell, kWarpsPerBlock);
-    if (!update) k_adjoint_sweep<TS, false, false><<<nb, 256, 0, s>>>(a);
-    else if (res) k_adjoint_sweep<TS, true, true><<<nb, 256, 0, s>>>(a);
-    else k_adjoint_sweep<TS, true, false><<<nb, 256, 0, s>>>(a);
+    const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
+    constexpr int sm = adjoint_smem_bytes();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    if (!update) k_adjoint_sweep<TS, false, false><<<grid, 256, sm, s>>>(a, phi_maps.col, phi_maps.side, f_maps.side);
+    else if (res) k_adjoint_sweep<TS, true, true><<<grid, 256, sm, s>>>(a, phi_maps.col, phi_maps.side, f_maps.side);
+    else k_adjoint_sweep<TS, true, false><<<grid, 256, sm, s>>>(a, phi_maps.col, phi_maps.side, f_maps.side);
 }
 
-cudaError_t launch_adjoint_sweep(int storage, const void* args, bool update, bool res, cudaStream_t s) {
-    if (storage == 0) adjoint_launch<double, double>(args, update, res, s);
-    else if (storage == 1) adjoint_launch<float, float>(args, update, res, s);
-    else adjoint_launch<__nv_bfloat16, float>(args, update, res, s);
+cudaError_t launch_adjoint_sweep(int storage, const void* args, const TmaMaps& phi_maps, const TmaMaps& f_maps,
+                                 bool update, bool res, cudaStream_t s) {
+    if (storage == 0) adjoint_launch<double, double>(args, phi_maps, f_maps, update, res, s);
+    else if (storage == 1) adjoint_launch<float, float>(args, phi_maps, f_maps, update, res, s);
+    else adjoint_launch<__nv_bfloat16, float>(args, phi_maps, f_maps, update, res, s);
     return cudaGetLastError();
+}
+
+// Tensor maps of one distribution buffer: [nj][ni][nq*4 uint32], boxes of 32 chunks x 1 cell x
+// {10, 8} rows, zero fill outside the tensor.
+cudaError_t make_tmamaps(void* base, int ni, int nj, int nq, TmaMaps* out) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)nq * 4, (cuuint64_t)ni, (cuuint64_t)nj};
+    const cuuint64_t strides[2] = {(cuuint64_t)nq * 16, (cuuint64_t)nq * 16 * ni};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t box10[3] = {128, 1, 10}, box8[3] = {128, 1, 8};
+    CUresult r = encode(&out->col, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, base, dims, strides, box10, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+        r = encode(&out->side, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, base, dims, strides, box8, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
