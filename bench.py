@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--mesh", default=None, help="override the O-mesh size, e.g. 128x64 (profiling runs)")
+    p.add_argument("--serve", type=int, default=128, help="requests of the served trace to replay (0: skip)")
+    p.add_argument("--serve-max-iter", type=int, default=400, help="sweep cap per phase of a served request")
     return p.parse_args()
 
 
@@ -272,6 +274,7 @@ def run_gpu(args):
     e2e = run_e2e(args, ctx, wl, torch, dvm)
 
     clocks = clk.summary()
+    serving = run_serving(args, torch, dvm) if (args.serve > 0 and not args.mesh) else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.storage],
@@ -283,6 +286,8 @@ def run_gpu(args):
                        "phase_ms_per_step": {"primal": prim_ms / args.steps, "adjoint": adj_ms / args.steps,
                                              "sensitivity": sens_ms / args.steps}},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches)}
+    if serving:
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample(wl).items() if k != "seconds"}
     if rank == 0:
@@ -291,6 +296,34 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_serving(args, torch, dvm):
+    """Replay the served-request trace (Poisson arrivals at 20/s, random airfoil, Kn, Ma, mesh and
+    velocity grid; FP32) through the continuous-batching server and one request at a time."""
+    from paper_2501_00923_gb300 import serve
+    wl = W.config(3)
+    trace = wl.extra["trace"][: args.serve]
+    specs = serve.trace_specs(trace, max_iter=args.serve_max_iter, tol=1e-5)
+    arrivals = np.array([r["t"] for r in trace]) - trace[0]["t"]
+    out = {"trace": f"{len(trace)} requests, Poisson 20/s, meshes 64x32..192x96, grids 24^2..48^2, "
+                    f"Kn 1e-3..10, Ma 0.3..2, FP32, primal+adjoint+sensitivity, cap {args.serve_max_iter} "
+                    f"sweeps per phase, tol 1e-5"}
+    bstream = torch.cuda.Stream()
+    bctx = dvm.Context(torch.cuda.current_device(), graph_iters=20, stream=bstream.cuda_stream)
+    lat, span, res = serve.replay_batched(bctx, specs, arrivals, sweeps_per_tick=20)
+    out["batched"] = serve.latency_stats(lat, span)
+    out["batched"]["converged"] = int(sum(1 for r in res.values() if r["status"] == dvm.DVM_OK))
+    out["batched"]["failed"] = int(sum(1 for r in res.values()
+                                       if r["status"] not in (dvm.DVM_OK, dvm.DVM_NOT_CONVERGED)))
+    bctx.close()
+    sctx = dvm.Context(torch.cuda.current_device(), graphs=False)
+    slat, sspan, sfail = serve.replay_serial(sctx, specs, arrivals)
+    out["serial_fp32"] = serve.latency_stats(slat, sspan)
+    out["serial_fp32"]["failed"] = int(sum(1 for v in sfail.values() if v is not None))
+    sctx.close()
+    out["speedup_solves_per_s"] = out["batched"]["solves_per_s"] / out["serial_fp32"]["solves_per_s"]
+    return out
 
 
 def run_e2e(args, ctx, wl, torch, dvm):

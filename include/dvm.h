@@ -65,10 +65,13 @@ typedef struct dvm_vgrid dvm_vgrid;
 typedef struct dvm_state dvm_state;
 typedef struct dvm_adjoint dvm_adjoint;
 
+enum { DVM_OPT_NO_GRAPHS = 1 };   /* launch every sweep directly (no CUDA-graph capture) */
+
 typedef struct {
     int graph_iters;        /* sweeps captured per CUDA-graph launch (even, >= 2); 0 -> 20 */
     size_t hbm_budget;      /* bytes the context may hold for states (admission); 0 -> no limit */
     void* stream;           /* cudaStream_t to run on (e.g. torch's); NULL -> the library's own */
+    int flags;              /* DVM_OPT_* */
 } dvm_options;
 
 typedef struct {
@@ -181,6 +184,66 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
 int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* adj, int n_params,
                     const double* dwall_dalpha, const double* s_j, int mode, double* grad_out,
                     double* node_grad_out);
+
+/* ------------------------------------------------------------------------ served batch, B7 */
+/* Continuous batching of whole solve requests (primal solve, adjoint solve, sensitivity) on one
+ * context.  Requests are admitted in arrival order while their device footprint fits the batch's
+ * HBM budget; every tick advances each admitted request by `sweeps_per_tick` point-implicit
+ * sweeps of its current phase in one batched launch per sweep (all requests of the tick share the
+ * launch), then checks convergence; a converged primal moves to its adjoint, a converged adjoint to
+ * its sensitivity, and the request retires, freeing its memory.  Requests that arrive while others
+ * run are admitted at the next tick.  A request's result does not depend on what else is in the
+ * batch (same kernels, same per-request arithmetic, fixed reduction order).
+ * Warm start: a request with warm_key != 0 starts its f and phi from those of the last retired
+ * request with the same key and the same mesh/grid/storage, when that is still cached. */
+typedef struct dvm_batch dvm_batch;
+
+typedef struct {
+    size_t hbm_budget;          /* bytes for admitted requests and the warm cache; 0 -> no limit */
+    int sweeps_per_tick;        /* even, >= 2 */
+    int max_active;             /* cap on admitted requests; 0 -> no cap */
+} dvm_batch_options;
+
+typedef struct {
+    int ni, nj;
+    const double* nodes_xy;     /* [(nj+1)][ni][2], copied at submit */
+    int nv;
+    const double* vx;           /* [nv], copied */
+    const double* vy;
+    const double* w;
+    dvm_flow flow;
+    int storage;                /* dvm_storage */
+    double tol;                 /* primal and adjoint relative residual targets */
+    double adjoint_tol;
+    int max_iter;               /* per phase; a phase that reaches it moves on (status NOT_CONVERGED) */
+    int functional;             /* dvm_functional */
+    int n_params;               /* sensitivity parameters; 0 -> no adjoint/sensitivity */
+    const double* dwall_dalpha; /* [n_params][ni][2], copied */
+    const double* s_j;          /* [nj+1], copied (DVM_SENS_FULL) */
+    int sens_mode;              /* dvm_sens_mode */
+    uint64_t warm_key;          /* 0 -> no warm start */
+} dvm_request;
+
+typedef struct {
+    int done;                   /* 1 when retired */
+    int status;                 /* DVM_OK, DVM_NOT_CONVERGED (a phase hit max_iter), or an error */
+    int phase;                  /* 0 queued, 1 primal, 2 adjoint, 3 retired */
+    int primal_iters, adjoint_iters;
+    double J, Cd, residual, adjoint_residual;
+    int warm_started;
+} dvm_request_result;
+
+int dvm_batch_create(dvm_context* ctx, const dvm_batch_options* opt, dvm_batch** out);
+/* Frees every request and the cache.  Destroy a batch before its context. */
+void dvm_batch_destroy(dvm_batch* b);
+/* Queue a request (host arrays copied).  Fails with DVM_ERR_ADMISSION if it can never fit the budget. */
+int dvm_batch_submit(dvm_batch* b, const dvm_request* req, uint64_t* ticket);
+/* Admit what fits, run one tick, retire what converged.  n_active/n_queued (optional) report the
+ * state after the tick. */
+int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued);
+/* Result of a request; grad_out (optional, [n_params]) receives dJ/dalpha once retired.  A retired
+ * request is forgotten after it has been polled with forget = 1. */
+int dvm_batch_poll(dvm_batch* b, uint64_t ticket, dvm_request_result* out, double* grad_out, int forget);
 
 /* Same result as dvm_sensitivity, for callers that must not allocate device memory during the
  * call (e.g. a serving loop whose device memory is reserved once, up front, by another allocator,

@@ -7,10 +7,13 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 using namespace dvm;
@@ -25,6 +28,7 @@ struct dvm_context {
     uint64_t launches = 0;
     double* pinned = nullptr;   // 64 doubles for small device->host results
     int* derr = nullptr;        // device flag: a kernel's bounded wait ran out
+    int flags = 0;
 };
 
 struct dvm_mesh {
@@ -91,6 +95,35 @@ struct dvm_adjoint {
 namespace {
 
 thread_local std::string g_err;
+
+// Live-handle registry: every handle is registered at creation and removed by its destroy call, so a
+// destroy of an unknown (already released) handle is a no-op, and a context's destroy can release
+// whatever its caller left behind, in dependency order.
+enum HandleKind { kCtx = 1, kMesh, kGrid, kState, kAdjoint, kBatch };
+struct LiveEntry { int kind; const dvm_context* ctx; const void* parent; };
+std::mutex g_live_mu;
+std::unordered_map<const void*, LiveEntry> g_live;
+
+void live_add(const void* h, int kind, const dvm_context* ctx, const void* parent = nullptr) {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    g_live[h] = LiveEntry{kind, ctx, parent};
+}
+bool live_take(const void* h, int kind) {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    auto it = g_live.find(h);
+    if (it == g_live.end() || it->second.kind != kind) return false;
+    g_live.erase(it);
+    return true;
+}
+std::vector<const void*> live_children(int kind, const dvm_context* ctx, const void* parent = nullptr) {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    std::vector<const void*> out;
+    for (auto& kv : g_live)
+        if (kv.second.kind == kind && (ctx == nullptr || kv.second.ctx == ctx) &&
+            (parent == nullptr || kv.second.parent == parent))
+            out.push_back(kv.first);
+    return out;
+}
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -295,7 +328,7 @@ int run_adjoint_plain(dvm_adjoint* ad, int n, double* hist) {
     return DVM_OK;
 }
 
-bool graphs_ok(const dvm_context* ctx) { return ctx->stream != nullptr; }
+bool graphs_ok(const dvm_context* ctx) { return ctx->stream != nullptr && !(ctx->flags & DVM_OPT_NO_GRAPHS); }
 
 // Capture K (even) sweeps + one finalize.  Buffers return to the same parity after K sweeps.
 int build_primal_graph(dvm_state* st, int K) {
@@ -407,6 +440,7 @@ int dvm_context_create(dvm_context** out, int cuda_device, const dvm_options* op
         if (opt->graph_iters) c->graph_iters = opt->graph_iters;
         c->budget = opt->hbm_budget;
         c->stream = (cudaStream_t)opt->stream;
+        c->flags = opt->flags;
     }
     if (!opt || !opt->stream) {
         e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -423,12 +457,24 @@ int dvm_context_create(dvm_context** out, int cuda_device, const dvm_options* op
         delete c;
         return fail_cuda(e, "error flag");
     }
+    live_add(c, kCtx, c);
     *out = c;
     return DVM_OK;
 }
 
 void dvm_context_destroy(dvm_context* c) {
     if (!c) return;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        auto it = g_live.find(c);
+        if (it == g_live.end() || it->second.kind != kCtx) return;
+    }
+    for (const void* h : live_children(kBatch, c)) dvm_batch_destroy((dvm_batch*)h);
+    for (const void* h : live_children(kAdjoint, c)) dvm_adjoint_destroy((dvm_adjoint*)h);
+    for (const void* h : live_children(kState, c)) dvm_state_destroy((dvm_state*)h);
+    for (const void* h : live_children(kGrid, c)) dvm_vgrid_destroy((dvm_vgrid*)h);
+    for (const void* h : live_children(kMesh, c)) dvm_mesh_destroy((dvm_mesh*)h);
+    if (!live_take(c, kCtx)) return;
     DeviceGuard dg(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->pinned) cudaFreeHost(c->pinned);
@@ -483,6 +529,7 @@ int dvm_mesh_create(dvm_context* ctx, int ni, int nj, const double* X, dvm_mesh*
     if ((rc = dalloc(ctx, &m->d.nb, nc)) || (rc = dalloc(ctx, &m->d.Sd, 4 * (size_t)nc)) ||
         (rc = dalloc(ctx, &m->d.Vd, nc)) || (rc = dalloc(ctx, &m->d.Sf, 4 * (size_t)nc)) ||
         (rc = dalloc(ctx, &m->d.Vf, nc)) || (rc = dalloc(ctx, &m->d.nodes, (size_t)(nj + 1) * ni))) {
+        live_add(m, kMesh, ctx);
         dvm_mesh_destroy(m);
         return rc;
     }
@@ -493,13 +540,14 @@ int dvm_mesh_create(dvm_context* ctx, int ni, int nj, const double* X, dvm_mesh*
     if (e == cudaSuccess) e = cudaMemcpy(m->d.Sf, Sf.data(), Sf.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d.Vf, Vf.data(), nc * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d.nodes, X, (size_t)(nj + 1) * ni * sizeof(double2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { dvm_mesh_destroy(m); return fail_cuda(e, "mesh upload"); }
+    if (e != cudaSuccess) { live_add(m, kMesh, ctx); dvm_mesh_destroy(m); return fail_cuda(e, "mesh upload"); }
+    live_add(m, kMesh, ctx);
     *out = m;
     return DVM_OK;
 }
 
 void dvm_mesh_destroy(dvm_mesh* m) {
-    if (!m) return;
+    if (!m || !live_take(m, kMesh)) return;
     DeviceGuard dg(m->ctx->device);
     dfree(m->d.nb); dfree(m->d.Sd); dfree(m->d.Vd); dfree(m->d.Sf); dfree(m->d.Vf); dfree(m->d.nodes);
     delete m;
@@ -527,6 +575,7 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
     g->d.nv = nv;
     g->d.nvp = nvp;
     int rc;
+    live_add(g, kGrid, ctx);
     if ((rc = dalloc(ctx, &g->d.vd, nvp)) || (rc = dalloc(ctx, &g->d.vf, nvp))) { dvm_vgrid_destroy(g); return rc; }
     cudaError_t e = cudaMemcpy(g->d.vd, vd.data(), nvp * sizeof(double4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d.vf, vf.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
@@ -536,7 +585,7 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
 }
 
 void dvm_vgrid_destroy(dvm_vgrid* g) {
-    if (!g) return;
+    if (!g || !live_take(g, kGrid)) return;
     DeviceGuard dg(g->ctx->device);
     dfree(g->d.vd); dfree(g->d.vf);
     delete g;
@@ -545,6 +594,8 @@ void dvm_vgrid_destroy(dvm_vgrid* g) {
 // ------------------------------------------------------------------------------------- state
 void dvm_state_destroy(dvm_state* st) {
     if (!st) return;
+    for (const void* h : live_children(kAdjoint, nullptr, st)) dvm_adjoint_destroy((dvm_adjoint*)h);
+    if (!live_take(st, kState)) return;
     DeviceGuard dg(st->ctx->device);
     cudaStreamSynchronize(st->ctx->stream);
     if (st->graph) cudaGraphExecDestroy(st->graph);
@@ -575,6 +626,7 @@ int dvm_state_create(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     dvm_state* st = new (std::nothrow) dvm_state();
     if (!st) return fail(DVM_ERR_OOM, "host allocation");
     st->ctx = ctx; st->mesh = mesh; st->grid = grid; st->flow = *flow; st->storage = storage;
+    live_add(st, kState, ctx);
     const DevMesh& m = mesh->d;
     const DevGrid& g = grid->d;
     st->fl.tau_inf = 5.0 / 16.0 * flow->Kn * sqrt(2.0 * M_PI);
@@ -778,7 +830,7 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
 
 // ------------------------------------------------------------------------------------- adjoint
 void dvm_adjoint_destroy(dvm_adjoint* ad) {
-    if (!ad) return;
+    if (!ad || !live_take(ad, kAdjoint)) return;
     DeviceGuard dg(ad->st->ctx->device);
     cudaStreamSynchronize(ad->st->ctx->stream);
     if (ad->graph) cudaGraphExecDestroy(ad->graph);
@@ -816,6 +868,7 @@ int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     if (!ad) return fail(DVM_ERR_OOM, "host allocation");
     ad->st = st;
     ad->functional = functional;
+    live_add(ad, kAdjoint, st->ctx, st);
     const double ang = dir_angle(st->flow, functional);
     ad->dirx = cos(ang);
     ad->diry = sin(ang);
@@ -1143,3 +1196,463 @@ extern "C" int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, co
     CK(cudaStreamSynchronize(s));
     return DVM_OK;
 }
+
+// ======================================================================= served batch (continuous batching)
+namespace {
+
+struct BatchReq {
+    uint64_t ticket = 0;
+    dvm_request r{};
+    std::vector<double> nodes, vx, vy, w, dwall, sj;
+    int phase = 0;              // 0 queued, 1 primal, 2 adjoint, 3 retired
+    int status = DVM_OK;
+    int pstatus = DVM_OK, astatus = DVM_OK;
+    dvm_mesh* mesh = nullptr;
+    dvm_vgrid* grid = nullptr;
+    dvm_state* st = nullptr;
+    dvm_adjoint* ad = nullptr;
+    int pit = 0, ait = 0;
+    double res = NAN, ares = NAN, J = 0.0;
+    int warm = 0;
+    std::vector<double> grad;
+    size_t footprint = 0;
+};
+
+struct WarmEntry {
+    uint64_t key = 0, stamp = 0;
+    int ni = 0, nj = 0, nv = 0, storage = 0;
+    dvm_mesh* mesh = nullptr;
+    dvm_vgrid* grid = nullptr;
+    dvm_state* st = nullptr;
+    dvm_adjoint* ad = nullptr;
+    size_t footprint = 0;
+};
+
+size_t request_footprint(const dvm_request& r) {
+    const size_t nc = (size_t)r.ni * r.nj, nvp = (size_t)(r.nv + kPad - 1) / kPad * kPad;
+    const size_t pair = storage_bytes(r.storage), tc = r.storage == DVM_STORE_FP64 ? 8 : 4;
+    size_t b = 2 * nc * nvp * pair + nc * 72 + (size_t)r.ni * 48 + nvp * 48;          // state
+    b += nc * (4 * 16 + 4 * 8 + 16 + 8 + 4) + (size_t)(r.nj + 1) * r.ni * 16 + nvp * 48;  // mesh + grid
+    if (r.n_params > 0)
+        b += 2 * nc * nvp * pair + nc * (72 + 16 * tc) + nc * 40 + (size_t)(r.nj + 1) * r.ni * 16 +
+             (size_t)r.n_params * r.ni * 16;                                              // adjoint + sensitivity
+    return b;
+}
+
+}  // namespace
+
+struct dvm_batch {
+    dvm_context* ctx = nullptr;
+    dvm_batch_options opt{};
+    uint64_t next = 1, stamp = 0;
+    size_t used = 0;
+    std::deque<BatchReq*> queue;
+    std::vector<BatchReq*> active;
+    std::unordered_map<uint64_t, BatchReq*> all;
+    std::vector<WarmEntry> cache;
+    void* pdesc[3] = {nullptr, nullptr, nullptr};
+    size_t pdesc_cap[3] = {0, 0, 0};
+    void* adesc[3] = {nullptr, nullptr, nullptr};
+    size_t adesc_cap[3] = {0, 0, 0};
+    int4* items = nullptr;
+    size_t items_cap = 0;
+    FinalizeDesc* fdesc = nullptr;
+    size_t fdesc_cap = 0;
+    double* dout = nullptr;
+    size_t dout_cap = 0;
+    unsigned char* host = nullptr;   // pinned staging
+    size_t host_cap = 0;
+};
+
+namespace {
+
+template <class T>
+int grow_device(T** p, size_t* cap, size_t bytes) {
+    if (bytes <= *cap) return DVM_OK;
+    dfree(*p);
+    *p = nullptr;
+    size_t nb = std::max(bytes, *cap * 2);
+    cudaError_t e = cudaMalloc((void**)p, nb);
+    if (e != cudaSuccess) { *cap = 0; return fail_cuda(e, "batch table"); }
+    *cap = nb;
+    return DVM_OK;
+}
+
+int grow_host(dvm_batch* b, size_t bytes) {
+    if (bytes <= b->host_cap) return DVM_OK;
+    if (b->host) cudaFreeHost(b->host);
+    b->host = nullptr;
+    size_t nb = std::max(bytes, b->host_cap * 2);
+    CK(cudaMallocHost((void**)&b->host, nb));
+    b->host_cap = nb;
+    return DVM_OK;
+}
+
+void destroy_objects(dvm_adjoint*& ad, dvm_state*& st, dvm_vgrid*& g, dvm_mesh*& m) {
+    dvm_adjoint_destroy(ad); ad = nullptr;
+    dvm_state_destroy(st); st = nullptr;
+    dvm_vgrid_destroy(g); g = nullptr;
+    dvm_mesh_destroy(m); m = nullptr;
+}
+
+bool evict_one(dvm_batch* b) {
+    if (b->cache.empty()) return false;
+    size_t lru = 0;
+    for (size_t i = 1; i < b->cache.size(); ++i)
+        if (b->cache[i].stamp < b->cache[lru].stamp) lru = i;
+    WarmEntry& e = b->cache[lru];
+    destroy_objects(e.ad, e.st, e.grid, e.mesh);
+    b->used -= e.footprint;
+    b->cache.erase(b->cache.begin() + lru);
+    return true;
+}
+
+WarmEntry* find_warm(dvm_batch* b, const dvm_request& r) {
+    if (!r.warm_key) return nullptr;
+    for (auto& e : b->cache)
+        if (e.key == r.warm_key && e.ni == r.ni && e.nj == r.nj && e.nv == r.nv && e.storage == r.storage) return &e;
+    return nullptr;
+}
+
+int admit(dvm_batch* b, BatchReq* q) {
+    dvm_context* ctx = b->ctx;
+    const dvm_request& r = q->r;
+    int rc;
+    if ((rc = dvm_mesh_create(ctx, r.ni, r.nj, q->nodes.data(), &q->mesh))) return rc;
+    if ((rc = dvm_vgrid_create(ctx, r.nv, q->vx.data(), q->vy.data(), q->w.data(), &q->grid))) return rc;
+    if ((rc = dvm_state_create(ctx, q->mesh, q->grid, &r.flow, r.storage, &q->st))) return rc;
+    if (WarmEntry* e = find_warm(b, r)) {
+        dvm_state* st = q->st;
+        const size_t bytes = (size_t)st->mesh->d.ncell * st->grid->d.nvp * storage_bytes(st->storage);
+        CK(cudaMemcpyAsync(st->f[st->cur], e->st->f[e->st->cur], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(launch_moments(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur], st->Fw[st->cur],
+                          ctx->stream));
+        ctx->launches += 1;
+        st->version += 1;
+        q->warm = 1;
+        e->stamp = ++b->stamp;
+    }
+    q->phase = 1;
+    return DVM_OK;
+}
+
+void retire(dvm_batch* b, BatchReq* q) {
+    q->status = q->pstatus != DVM_OK ? q->pstatus : q->astatus;
+    q->phase = 3;
+    if (q->r.warm_key && q->status != DVM_ERR_NONFINITE) {
+        if (WarmEntry* e = find_warm(b, q->r)) {
+            destroy_objects(e->ad, e->st, e->grid, e->mesh);
+            b->used -= e->footprint;
+            b->cache.erase(b->cache.begin() + (e - b->cache.data()));
+        }
+        WarmEntry e;
+        e.key = q->r.warm_key; e.stamp = ++b->stamp;
+        e.ni = q->r.ni; e.nj = q->r.nj; e.nv = q->r.nv; e.storage = q->r.storage;
+        e.mesh = q->mesh; e.grid = q->grid; e.st = q->st; e.ad = q->ad;
+        e.footprint = q->footprint;
+        b->cache.push_back(e);
+        q->mesh = nullptr; q->grid = nullptr; q->st = nullptr; q->ad = nullptr;
+    } else {
+        destroy_objects(q->ad, q->st, q->grid, q->mesh);
+        b->used -= q->footprint;
+    }
+}
+
+int start_adjoint(dvm_batch* b, BatchReq* q) {
+    int rc;
+    if ((rc = dvm_adjoint_create(q->st, q->r.functional, &q->ad))) return rc;
+    if (WarmEntry* e = find_warm(b, q->r)) {
+        if (e->ad) {
+            dvm_adjoint* ad = q->ad;
+            const size_t bytes = (size_t)q->st->mesh->d.ncell * q->st->grid->d.nvp * storage_bytes(q->st->storage);
+            CK(cudaMemcpyAsync(ad->phi[ad->cur], e->ad->phi[e->ad->cur], bytes, cudaMemcpyDeviceToDevice,
+                               b->ctx->stream));
+            CK(refresh_adjoint_couplings(ad));
+        }
+    }
+    q->phase = 2;
+    return DVM_OK;
+}
+
+template <class TS>
+void fill_primal_desc(PrimalBatchDesc<TS>* d, dvm_state* st) {
+    using TC = typename std::conditional<sizeof(TS) == 8, double, float>::type;
+    d->maps[0] = st->maps[st->cur];
+    d->maps[1] = st->maps[1 - st->cur];
+    d->args[0] = primal_args<TS, TC>(st, st->cur);
+    d->args[1] = primal_args<TS, TC>(st, 1 - st->cur);
+}
+
+template <class TS>
+void fill_adjoint_desc(AdjointBatchDesc<TS>* d, dvm_adjoint* ad) {
+    using TC = typename std::conditional<sizeof(TS) == 8, double, float>::type;
+    d->phi_maps[0] = ad->maps[ad->cur];
+    d->phi_maps[1] = ad->maps[1 - ad->cur];
+    d->f_maps = ad->st->maps[ad->st->cur];
+    d->args[0] = adjoint_args<TS, TC>(ad, ad->cur);
+    d->args[1] = adjoint_args<TS, TC>(ad, 1 - ad->cur);
+}
+
+size_t pdesc_size(int storage) {
+    return storage == 0 ? sizeof(PrimalBatchDesc<double>)
+                        : (storage == 1 ? sizeof(PrimalBatchDesc<float>) : sizeof(PrimalBatchDesc<__nv_bfloat16>));
+}
+size_t adesc_size(int storage) {
+    return storage == 0 ? sizeof(AdjointBatchDesc<double>)
+                        : (storage == 1 ? sizeof(AdjointBatchDesc<float>) : sizeof(AdjointBatchDesc<__nv_bfloat16>));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+int dvm_batch_create(dvm_context* ctx, const dvm_batch_options* opt, dvm_batch** out) {
+    if (!ctx || !opt || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (opt->sweeps_per_tick < 2 || opt->sweeps_per_tick % 2) return fail(DVM_ERR_INVALID_ARG, "sweeps_per_tick must be even and >= 2");
+    if (!ctx->stream) return fail(DVM_ERR_INVALID_ARG, "the batch needs a context with a stream");
+    dvm_batch* b = new (std::nothrow) dvm_batch();
+    if (!b) return fail(DVM_ERR_OOM, "host allocation");
+    b->ctx = ctx;
+    b->opt = *opt;
+    live_add(b, kBatch, ctx);
+    *out = b;
+    return DVM_OK;
+}
+
+void dvm_batch_destroy(dvm_batch* b) {
+    if (!b || !live_take(b, kBatch)) return;
+    DeviceGuard dg(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    for (auto& kv : b->all) {
+        BatchReq* q = kv.second;
+        destroy_objects(q->ad, q->st, q->grid, q->mesh);
+        delete q;
+    }
+    for (auto& e : b->cache) destroy_objects(e.ad, e.st, e.grid, e.mesh);
+    for (int s = 0; s < 3; ++s) { dfree(b->pdesc[s]); dfree(b->adesc[s]); }
+    dfree(b->items); dfree(b->fdesc); dfree(b->dout);
+    if (b->host) cudaFreeHost(b->host);
+    delete b;
+}
+
+int dvm_batch_submit(dvm_batch* b, const dvm_request* r, uint64_t* ticket) {
+    if (!b || !r || !ticket) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (r->ni < 3 || r->nj < 1 || r->nv < 1 || !r->nodes_xy || !r->vx || !r->vy || !r->w)
+        return fail(DVM_ERR_INVALID_ARG, "request needs a mesh and a velocity grid");
+    if (r->storage < 0 || r->storage > 2 || r->max_iter < 0) return fail(DVM_ERR_INVALID_ARG, "bad request options");
+    if (r->n_params > 0 && (!r->dwall_dalpha || (r->sens_mode == DVM_SENS_FULL && !r->s_j)))
+        return fail(DVM_ERR_INVALID_ARG, "sensitivity needs dwall_dalpha (and s_j in full mode)");
+    BatchReq* q = new (std::nothrow) BatchReq();
+    if (!q) return fail(DVM_ERR_OOM, "host allocation");
+    q->r = *r;
+    q->nodes.assign(r->nodes_xy, r->nodes_xy + 2 * (size_t)(r->nj + 1) * r->ni);
+    q->vx.assign(r->vx, r->vx + r->nv);
+    q->vy.assign(r->vy, r->vy + r->nv);
+    q->w.assign(r->w, r->w + r->nv);
+    if (r->n_params > 0) {
+        q->dwall.assign(r->dwall_dalpha, r->dwall_dalpha + 2 * (size_t)r->n_params * r->ni);
+        if (r->s_j) q->sj.assign(r->s_j, r->s_j + r->nj + 1);
+    }
+    q->r.nodes_xy = q->nodes.data(); q->r.vx = q->vx.data(); q->r.vy = q->vy.data(); q->r.w = q->w.data();
+    q->r.dwall_dalpha = q->dwall.empty() ? nullptr : q->dwall.data();
+    q->r.s_j = q->sj.empty() ? nullptr : q->sj.data();
+    q->footprint = request_footprint(q->r);
+    if (b->opt.hbm_budget && q->footprint > b->opt.hbm_budget) {
+        delete q;
+        return fail(DVM_ERR_ADMISSION, "request larger than the batch's HBM budget");
+    }
+    q->ticket = b->next++;
+    b->all[q->ticket] = q;
+    b->queue.push_back(q);
+    *ticket = q->ticket;
+    return DVM_OK;
+}
+
+int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
+    if (!b) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    dvm_context* ctx = b->ctx;
+    DeviceGuard dg(ctx->device);
+    const int M = b->opt.sweeps_per_tick;
+    int rc;
+    // 1. admission, arrival order
+    while (!b->queue.empty()) {
+        BatchReq* q = b->queue.front();
+        if (b->opt.max_active && (int)b->active.size() >= b->opt.max_active) break;
+        if (b->opt.hbm_budget && b->used + q->footprint > b->opt.hbm_budget) {
+            if (evict_one(b)) continue;
+            break;
+        }
+        b->queue.pop_front();
+        b->used += q->footprint;
+        rc = admit(b, q);
+        if (rc) {                                    // this request fails, the batch goes on
+            q->pstatus = rc;
+            destroy_objects(q->ad, q->st, q->grid, q->mesh);
+            b->used -= q->footprint;
+            q->status = rc;
+            q->phase = 3;
+            continue;
+        }
+        b->active.push_back(q);
+    }
+    // 2. work lists and descriptors, per storage type and phase
+    std::vector<BatchReq*> plist[3], alist[3];
+    for (BatchReq* q : b->active) (q->phase == 1 ? plist : alist)[q->r.storage].push_back(q);
+    size_t n_items = 0;
+    std::vector<size_t> pitem0(3), pitemn(3), aitem0(3), aitemn(3);
+    for (int s = 0; s < 3; ++s) {
+        pitem0[s] = n_items;
+        for (BatchReq* q : plist[s]) n_items += (size_t)q->r.ni * ((q->r.nj + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        pitemn[s] = n_items - pitem0[s];
+        aitem0[s] = n_items;
+        for (BatchReq* q : alist[s]) n_items += (size_t)q->r.ni * ((q->r.nj + kWarpsPerBlock - 1) / kWarpsPerBlock);
+        aitemn[s] = n_items - aitem0[s];
+    }
+    const size_t nact = b->active.size();
+    size_t off_p[3], off_a[3], host_bytes = 0;
+    for (int s = 0; s < 3; ++s) {
+        off_p[s] = host_bytes;
+        host_bytes = align_up(host_bytes + plist[s].size() * pdesc_size(s), 128);
+        off_a[s] = host_bytes;
+        host_bytes = align_up(host_bytes + alist[s].size() * adesc_size(s), 128);
+    }
+    const size_t off_items = host_bytes;
+    host_bytes = align_up(host_bytes + n_items * sizeof(int4), 128);
+    const size_t off_fd = host_bytes;
+    host_bytes = align_up(host_bytes + nact * sizeof(FinalizeDesc), 128);
+    const size_t off_out = host_bytes;
+    host_bytes += 2 * nact * sizeof(double) + 64;
+    if (nact > 0) {
+        if ((rc = grow_host(b, host_bytes))) return rc;
+        int4* hitems = reinterpret_cast<int4*>(b->host + off_items);
+        size_t it = 0;
+        for (int s = 0; s < 3; ++s) {
+            for (size_t r = 0; r < plist[s].size(); ++r) {
+                dvm_state* st = plist[s][r]->st;
+                unsigned char* d = b->host + off_p[s] + r * pdesc_size(s);
+                if (s == 0) fill_primal_desc(reinterpret_cast<PrimalBatchDesc<double>*>(d), st);
+                else if (s == 1) fill_primal_desc(reinterpret_cast<PrimalBatchDesc<float>*>(d), st);
+                else fill_primal_desc(reinterpret_cast<PrimalBatchDesc<__nv_bfloat16>*>(d), st);
+                for (int i = 0; i < st->mesh->d.ni; ++i)
+                    for (int j0 = 0; j0 < st->mesh->d.nj; j0 += kWarpsPerBlock) hitems[it++] = int4{(int)r, i, j0, 0};
+            }
+            for (size_t r = 0; r < alist[s].size(); ++r) {
+                dvm_adjoint* ad = alist[s][r]->ad;
+                unsigned char* d = b->host + off_a[s] + r * adesc_size(s);
+                if (s == 0) fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<double>*>(d), ad);
+                else if (s == 1) fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<float>*>(d), ad);
+                else fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<__nv_bfloat16>*>(d), ad);
+                const DevMesh& m = ad->st->mesh->d;
+                for (int i = 0; i < m.ni; ++i)
+                    for (int j0 = 0; j0 < m.nj; j0 += kWarpsPerBlock) hitems[it++] = int4{(int)r, i, j0, 0};
+            }
+        }
+        FinalizeDesc* hfd = reinterpret_cast<FinalizeDesc*>(b->host + off_fd);
+        for (size_t k = 0; k < nact; ++k) {
+            BatchReq* q = b->active[k];
+            const DevMesh& m = q->st->mesh->d;
+            if (q->phase == 1) hfd[k] = FinalizeDesc{q->st->respart, m.ncell, m.ni, q->st->Jpart, q->st->Fw[q->st->cur], q->st->fl.wallM};
+            else hfd[k] = FinalizeDesc{q->ad->respart, m.ncell, m.ni, nullptr, nullptr, nullptr};
+        }
+        for (int s = 0; s < 3; ++s) {
+            if ((rc = grow_device((unsigned char**)&b->pdesc[s], &b->pdesc_cap[s], plist[s].size() * pdesc_size(s) + 64)) ||
+                (rc = grow_device((unsigned char**)&b->adesc[s], &b->adesc_cap[s], alist[s].size() * adesc_size(s) + 64)))
+                return rc;
+        }
+        if ((rc = grow_device(&b->items, &b->items_cap, n_items * sizeof(int4) + 16)) ||
+            (rc = grow_device(&b->fdesc, &b->fdesc_cap, nact * sizeof(FinalizeDesc))) ||
+            (rc = grow_device(&b->dout, &b->dout_cap, 2 * nact * sizeof(double))))
+            return rc;
+        cudaStream_t s = ctx->stream;
+        for (int t = 0; t < 3; ++t) {
+            if (!plist[t].empty()) CK(cudaMemcpyAsync(b->pdesc[t], b->host + off_p[t], plist[t].size() * pdesc_size(t), cudaMemcpyHostToDevice, s));
+            if (!alist[t].empty()) CK(cudaMemcpyAsync(b->adesc[t], b->host + off_a[t], alist[t].size() * adesc_size(t), cudaMemcpyHostToDevice, s));
+        }
+        CK(cudaMemcpyAsync(b->items, hitems, n_items * sizeof(int4), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(b->fdesc, hfd, nact * sizeof(FinalizeDesc), cudaMemcpyHostToDevice, s));
+        // 3. M sweeps of every active request, one batched launch per storage type and phase
+        for (int sw = 0; sw < M; ++sw) {
+            const bool res = sw == M - 1;
+            for (int t = 0; t < 3; ++t) {
+                CK(launch_primal_sweep_batch(t, b->pdesc[t], b->items + pitem0[t], (int)pitemn[t], sw & 1, res, s));
+                CK(launch_adjoint_sweep_batch(t, b->adesc[t], b->items + aitem0[t], (int)aitemn[t], sw & 1, res, s));
+                ctx->launches += (pitemn[t] > 0) + (aitemn[t] > 0);
+            }
+        }
+        CK(launch_finalize_batch(b->fdesc, (int)nact, b->dout, s));
+        ctx->launches += 1;
+        double* hout = reinterpret_cast<double*>(b->host + off_out);
+        CK(cudaMemcpyAsync(hout, b->dout, 2 * nact * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if ((rc = check_device_flag(ctx))) return rc;
+        // 4. convergence and phase changes
+        std::vector<BatchReq*> keep;
+        for (size_t k = 0; k < nact; ++k) {
+            BatchReq* q = b->active[k];
+            const double r2 = hout[2 * k], J = hout[2 * k + 1];
+            bool leave = false;
+            if (q->phase == 1) {
+                q->pit += M;
+                q->st->version += (uint64_t)M;
+                q->res = sqrt(r2) / q->st->r0;
+                q->J = J;
+                if (!std::isfinite(q->res) || !std::isfinite(J)) { q->pstatus = DVM_ERR_NONFINITE; leave = true; }
+                else if (q->res <= q->r.tol || q->pit >= q->r.max_iter) {
+                    q->pstatus = q->res <= q->r.tol ? DVM_OK : DVM_NOT_CONVERGED;
+                    if (q->r.n_params > 0) {
+                        if ((rc = start_adjoint(b, q))) { q->astatus = rc; leave = true; }
+                    } else {
+                        leave = true;
+                    }
+                }
+            } else {
+                q->ait += M;
+                q->ares = sqrt(r2) / q->ad->r0;
+                if (!std::isfinite(q->ares)) { q->astatus = DVM_ERR_NONFINITE; leave = true; }
+                else if (q->ares <= q->r.adjoint_tol || q->ait >= q->r.max_iter) {
+                    q->astatus = q->ares <= q->r.adjoint_tol ? DVM_OK : DVM_NOT_CONVERGED;
+                    q->grad.assign(q->r.n_params, 0.0);
+                    rc = dvm_sensitivity(ctx, q->st, q->ad, q->r.n_params, q->r.dwall_dalpha, q->r.s_j, q->r.sens_mode,
+                                         q->grad.data(), nullptr);
+                    if (rc) q->astatus = rc;
+                    leave = true;
+                }
+            }
+            if (leave) retire(b, q);
+            else keep.push_back(q);
+        }
+        b->active.swap(keep);
+    }
+    if (n_active) *n_active = (int)b->active.size();
+    if (n_queued) *n_queued = (int)b->queue.size();
+    return DVM_OK;
+}
+
+int dvm_batch_poll(dvm_batch* b, uint64_t ticket, dvm_request_result* out, double* grad_out, int forget) {
+    if (!b || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    auto itq = b->all.find(ticket);
+    if (itq == b->all.end()) return fail(DVM_ERR_INVALID_ARG, "unknown ticket");
+    BatchReq* q = itq->second;
+    std::memset(out, 0, sizeof(*out));
+    out->done = q->phase == 3;
+    out->phase = q->phase;
+    out->status = q->phase == 3 ? q->status : DVM_OK;
+    out->primal_iters = q->pit;
+    out->adjoint_iters = q->ait;
+    out->J = q->J;
+    const double U = q->r.flow.Ma * sqrt(5.0 / 3.0);
+    out->Cd = U > 0.0 ? q->J / (0.5 * U * U) : q->J;
+    out->residual = q->res;
+    out->adjoint_residual = q->ares;
+    out->warm_started = q->warm;
+    if (out->done && grad_out && !q->grad.empty()) std::memcpy(grad_out, q->grad.data(), q->grad.size() * sizeof(double));
+    if (out->done && forget) {
+        b->all.erase(itq);
+        delete q;
+    }
+    return DVM_OK;
+}
+
+}  // extern "C"

@@ -110,6 +110,29 @@ struct AdjointArgs {
     int* err;
 };
 
+// Descriptors of the batched sweeps: the arguments and tensor maps of one request for both
+// parities (slot 0 reads the buffer that is current when the tick starts).  64-byte aligned (the
+// tensor maps are read from global memory by the tiled-TMA unit).
+template <class TS>
+struct alignas(64) PrimalBatchDesc {
+    TmaMaps maps[2];
+    PrimalArgs<TS, typename std::conditional<sizeof(TS) == 8, double, float>::type> args[2];
+};
+template <class TS>
+struct alignas(64) AdjointBatchDesc {
+    TmaMaps phi_maps[2];
+    TmaMaps f_maps;
+    AdjointArgs<TS, typename std::conditional<sizeof(TS) == 8, double, float>::type> args[2];
+};
+// Residual/drag reduction of one request (see k_finalize).
+struct FinalizeDesc {
+    const double* respart;
+    int ncell, ni;
+    const double* Jpart;
+    const double* Fw;
+    const double* M;
+};
+
 // ---------------------------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return cudaGetLastError().
 cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s);
@@ -125,6 +148,12 @@ cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& ma
 // phi_maps: of phi_old; f_maps: of the primal f.
 cudaError_t launch_adjoint_sweep(int storage, const void* args, const TmaMaps& phi_maps, const TmaMaps& f_maps,
                                  bool update, bool res, cudaStream_t s);
+// Batched sweeps over work items (request, i, j0); descs is PrimalBatchDesc<TS>[] / AdjointBatchDesc<TS>[].
+cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
+                                      bool res, cudaStream_t s);
+cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
+                                       bool res, cudaStream_t s);
+cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, double* out, cudaStream_t s);
 cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
                                      void* out, cudaStream_t s);
 // out[0] = sum respart; out[1] = sum_l Jpart_l + Fw_l M_l (Fw/M may be null -> only sum Jpart)

@@ -428,8 +428,7 @@ struct BlockPipe {
 
 __device__ __forceinline__ bool block_pipe_setup(BlockPipe& B, unsigned char* smem, int rows, int nj, int ni,
                                                  unsigned nq, const CUtensorMap* col, const CUtensorMap* side,
-                                                 const CUtensorMap* extra) {
-    const int i = blockIdx.x, j0 = blockIdx.y * kWarpsPerBlock;
+                                                 const CUtensorMap* extra, int i, int j0) {
     B.A = min(kWarpsPerBlock, nj - j0);
     B.niter = (nq + 31) / 32;
     B.F.col = col; B.F.side = side; B.F.extra = extra;
@@ -456,14 +455,12 @@ __device__ __forceinline__ void block_pipe_drain(const BlockPipe& B) {
 }
 
 template <class TS, bool kRes>
-__global__ void __launch_bounds__(256, 4) k_primal_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
-                                                         const __grid_constant__ CUtensorMap m10,
-                                                         const __grid_constant__ CUtensorMap m8) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+__device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
+                                             const CUtensorMap* m8, int i, int j0, unsigned char* smem) {
     BlockPipe B;
-    if (!block_pipe_setup(B, smem, kPrimalRows, P.nj, P.ni, (unsigned)P.nq, &m10, &m8, nullptr)) return;
+    if (!block_pipe_setup(B, smem, kPrimalRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, nullptr, i, j0)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = B.F.j0 + w, c = j * P.ni + B.F.i;
+    const int j = j0 + w, c = j * P.ni + i;
     const bool producer = (threadIdx.x == 0);
     const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
     bool ok;
@@ -477,6 +474,35 @@ __global__ void __launch_bounds__(256, 4) k_primal_sweep(const PrimalArgs<TS, ty
         if (lane == 0) atomicExch(P.err, 1);
         if (producer) block_pipe_drain(B);
     }
+}
+
+template <class TS, bool kRes>
+__global__ void __launch_bounds__(256, 4) k_primal_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
+                                                         const __grid_constant__ CUtensorMap m10,
+                                                         const __grid_constant__ CUtensorMap m8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    primal_block<TS, kRes>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+}
+
+// Make the tensor maps of a descriptor in global memory visible to the tensor-map proxy.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+
+// Batched primal sweep: block b runs work item items[b] = (request, i, j0) of the descriptor
+// table; every request advances one sweep.  parity selects, per request, the buffer pair of this
+// sweep (descriptor slot 0 reads the buffer current at the start of the tick).
+template <class TS, bool kRes>
+__global__ void __launch_bounds__(256, 4) k_primal_sweep_batch(const PrimalBatchDesc<TS>* __restrict__ descs,
+                                                               const int4* __restrict__ items, int parity) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int4 it = items[blockIdx.x];
+    const PrimalBatchDesc<TS>* d = descs + it.x;
+    if (threadIdx.x == 0) {
+        tensormap_acquire(&d->maps[parity].col);
+        tensormap_acquire(&d->maps[parity].side);
+    }
+    primal_block<TS, kRes>(d->args[parity], &d->maps[parity].col, &d->maps[parity].side, it.y, it.z, smem);
 }
 
 // ================================================================== adjoint sweep (K2)
@@ -615,15 +641,13 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
 }
 
 template <class TS, bool kUpdate, bool kRes>
-__global__ void __launch_bounds__(256, 3) k_adjoint_sweep(const AdjointArgs<TS, typename Pack<TS>::TC> P,
-                                                          const __grid_constant__ CUtensorMap m10,
-                                                          const __grid_constant__ CUtensorMap m8,
-                                                          const __grid_constant__ CUtensorMap mf8) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+__device__ __forceinline__ void adjoint_block(const AdjointArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
+                                              const CUtensorMap* m8, const CUtensorMap* mf8, int i, int j0,
+                                              unsigned char* smem) {
     BlockPipe B;
-    if (!block_pipe_setup(B, smem, kAdjointRows, P.nj, P.ni, (unsigned)P.nq, &m10, &m8, &mf8)) return;
+    if (!block_pipe_setup(B, smem, kAdjointRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, mf8, i, j0)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = B.F.j0 + w, c = j * P.ni + B.F.i;
+    const int j = j0 + w, c = j * P.ni + i;
     const bool producer = (threadIdx.x == 0);
     const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
     bool ok;
@@ -637,6 +661,30 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_sweep(const AdjointArgs<TS, 
         if (lane == 0) atomicExch(P.err, 1);
         if (producer) block_pipe_drain(B);
     }
+}
+
+template <class TS, bool kUpdate, bool kRes>
+__global__ void __launch_bounds__(256, 3) k_adjoint_sweep(const AdjointArgs<TS, typename Pack<TS>::TC> P,
+                                                          const __grid_constant__ CUtensorMap m10,
+                                                          const __grid_constant__ CUtensorMap m8,
+                                                          const __grid_constant__ CUtensorMap mf8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    adjoint_block<TS, kUpdate, kRes>(P, &m10, &m8, &mf8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+}
+
+template <class TS, bool kRes>
+__global__ void __launch_bounds__(256, 3) k_adjoint_sweep_batch(const AdjointBatchDesc<TS>* __restrict__ descs,
+                                                                const int4* __restrict__ items, int parity) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int4 it = items[blockIdx.x];
+    const AdjointBatchDesc<TS>* d = descs + it.x;
+    if (threadIdx.x == 0) {
+        tensormap_acquire(&d->phi_maps[parity].col);
+        tensormap_acquire(&d->phi_maps[parity].side);
+        tensormap_acquire(&d->f_maps.side);
+    }
+    adjoint_block<TS, true, kRes>(d->args[parity], &d->phi_maps[parity].col, &d->phi_maps[parity].side,
+                                  &d->f_maps.side, it.y, it.z, smem);
 }
 
 // Per-cell constants of the adjoint linearisation from the primal moments (fixed while the
@@ -1200,6 +1248,83 @@ cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const Dev
     const int b = 256;
     if (storage == 0) k_adjoint_cellconst<double><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, m.Vd, inv_tau_inf, (AdjCell<double>*)out);
     else k_adjoint_cellconst<float><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, m.Vd, inv_tau_inf, (AdjCell<float>*)out);
+    return cudaGetLastError();
+}
+
+template <class TS, class TC>
+void primal_batch_launch(const void* descs, const int4* items, int n_items, int parity, bool res, cudaStream_t s) {
+    constexpr int sm = primal_smem_bytes();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_primal_sweep_batch<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_sweep_batch<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    const auto* d = static_cast<const PrimalBatchDesc<TS>*>(descs);
+    if (res) k_primal_sweep_batch<TS, true><<<n_items, 256, sm, s>>>(d, items, parity);
+    else k_primal_sweep_batch<TS, false><<<n_items, 256, sm, s>>>(d, items, parity);
+}
+
+cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
+                                      bool res, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (storage == 0) primal_batch_launch<double, double>(descs, items, n_items, parity, res, s);
+    else if (storage == 1) primal_batch_launch<float, float>(descs, items, n_items, parity, res, s);
+    else primal_batch_launch<__nv_bfloat16, float>(descs, items, n_items, parity, res, s);
+    return cudaGetLastError();
+}
+
+template <class TS, class TC>
+void adjoint_batch_launch(const void* descs, const int4* items, int n_items, int parity, bool res, cudaStream_t s) {
+    constexpr int sm = adjoint_smem_bytes();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_adjoint_sweep_batch<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep_batch<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    const auto* d = static_cast<const AdjointBatchDesc<TS>*>(descs);
+    if (res) k_adjoint_sweep_batch<TS, true><<<n_items, 256, sm, s>>>(d, items, parity);
+    else k_adjoint_sweep_batch<TS, false><<<n_items, 256, sm, s>>>(d, items, parity);
+}
+
+cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
+                                       bool res, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (storage == 0) adjoint_batch_launch<double, double>(descs, items, n_items, parity, res, s);
+    else if (storage == 1) adjoint_batch_launch<float, float>(descs, items, n_items, parity, res, s);
+    else adjoint_batch_launch<__nv_bfloat16, float>(descs, items, n_items, parity, res, s);
+    return cudaGetLastError();
+}
+
+// One block per request: out[2r] = sum respart_r, out[2r+1] = sum_l Jpart_l + Fw_l M_l (as k_finalize).
+__global__ void k_finalize_batch(const FinalizeDesc* __restrict__ fd, int n, double* out) {
+    const int r = blockIdx.x;
+    if (r >= n) return;
+    const FinalizeDesc d = fd[r];
+    __shared__ double s0[32], s1[32];
+    double a = 0.0, b = 0.0;
+    for (int c = threadIdx.x; c < d.ncell; c += blockDim.x) a += d.respart[c];
+    if (d.Jpart)
+        for (int l = threadIdx.x; l < d.ni; l += blockDim.x) b += d.Jpart[l] + (d.Fw ? d.Fw[l] * d.M[l] : 0.0);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = a; s1[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, Bsum = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { A += s0[i]; Bsum += s1[i]; }
+        out[2 * r] = A;
+        out[2 * r + 1] = Bsum;
+    }
+}
+
+cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, double* out, cudaStream_t s) {
+    if (n > 0) k_finalize_batch<<<n, 1024, 0, s>>>(fd, n, out);
     return cudaGetLastError();
 }
 

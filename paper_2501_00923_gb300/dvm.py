@@ -25,7 +25,10 @@ _vp = C.c_void_p
 
 
 class Options(C.Structure):
-    _fields_ = [("graph_iters", C.c_int), ("hbm_budget", C.c_size_t), ("stream", C.c_void_p)]
+    _fields_ = [("graph_iters", C.c_int), ("hbm_budget", C.c_size_t), ("stream", C.c_void_p), ("flags", C.c_int)]
+
+
+DVM_OPT_NO_GRAPHS = 1
 
 
 class Flow(C.Structure):
@@ -128,9 +131,10 @@ def _p(a):
 
 # ----------------------------------------------------------------------------------- handles
 class Context:
-    def __init__(self, device: int = 0, graph_iters: int = 20, hbm_budget: int = 0, stream=None):
+    def __init__(self, device: int = 0, graph_iters: int = 20, hbm_budget: int = 0, stream=None,
+                 graphs: bool = True):
         h = C.c_void_p()
-        opt = Options(graph_iters, hbm_budget, stream)
+        opt = Options(graph_iters, hbm_budget, stream, 0 if graphs else DVM_OPT_NO_GRAPHS)
         _check(lib().dvm_context_create(C.byref(h), device, C.byref(opt)))
         self.h = h
         self.device = device
@@ -140,10 +144,10 @@ class Context:
         self._children.add(obj)
 
     def close(self):
-        """Release every live handle of this context (adjoints, states, then meshes and grids),
-        then the context itself."""
+        """Release every live handle of this context (batch servers, adjoints, states, then meshes
+        and grids), then the context itself."""
         if self.h:
-            for rank in (3, 2, 1):
+            for rank in (4, 3, 2, 1):
                 for ch in list(self._children):
                     if getattr(ch, "_rank", 0) == rank:
                         ch.close()

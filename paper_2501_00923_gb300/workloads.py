@@ -255,8 +255,26 @@ def range_for_mach(Ma: float) -> float:
     return 4.0 if Ma <= 0.6 else (6.0 if Ma <= 1.2 else 8.0)
 
 
+def valid_amplitude_scale(ni: int, alpha: np.ndarray, keep: float = 0.5, margin: float = 0.75) -> float:
+    """Largest factor <= 1 (times `margin`) by which `alpha` may be applied so that no wall node moves
+    toward the chord by more than (1 - keep) of its local half-thickness.  Without such a bound,
+    random bumps of 1% chord push a surface through the chord where the sharp trailing edge is
+    thinner than the bump, the section self-intersects and the radial mesh lines cross."""
+    alpha = np.asarray(alpha, dtype=np.float64)
+    theta = 2.0 * np.pi * np.arange(ni) / ni
+    xi = 0.5 * (1.0 + np.cos(theta))
+    side = np.sign(np.round(np.sin(theta), 14))
+    yt = naca4_thickness(xi)
+    _, dxw = wall_nodes(ni, np.zeros_like(alpha))
+    inward = -side * np.einsum("p,pm->m", alpha, dxw[:, :, 1])
+    m = (side != 0) & (inward > 0)
+    s = 1.0 if not m.any() else min(1.0, float(np.min((1.0 - keep) * yt[m] / inward[m])))
+    return margin * s
+
+
 def request_trace(n: int, rng: np.random.Generator, rate_hz: float = 20.0):
-    """Served-solve requests: Poisson arrivals, random airfoil, Kn, Ma, mesh and velocity grid."""
+    """Served-solve requests: Poisson arrivals, random airfoil, Kn, Ma, mesh and velocity grid.
+    Bump amplitudes are drawn U(-0.01, 0.01) and the vector is scaled by valid_amplitude_scale."""
     meshes = [(64, 32), (128, 64), (192, 96)]
     grids = [24, 32, 48]
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
@@ -266,9 +284,10 @@ def request_trace(n: int, rng: np.random.Generator, rate_hz: float = 20.0):
         nv = grids[rng.integers(3)]
         Kn = 10.0 ** rng.uniform(-3.0, 1.0)
         Ma = rng.uniform(0.3, 2.0)
-        alpha = rng.uniform(-0.01, 0.01, 24)
+        raw = rng.uniform(-0.01, 0.01, 24)
+        alpha = raw * valid_amplitude_scale(ni, raw)
         out.append({"t": float(t[r]), "ni": ni, "nj": nj, "nv": nv, "Kn": float(Kn),
-                    "Ma": float(Ma), "alpha": alpha, "range": range_for_mach(Ma)})
+                    "Ma": float(Ma), "alpha": alpha, "alpha_drawn": raw, "range": range_for_mach(Ma)})
     return out
 
 

@@ -1,0 +1,110 @@
+"""Served solves on the GPU: continuous batching through dvm_batch_*.
+
+A request's result must not depend on the rest of the batch: alone, in a mix of other sizes and
+flows, and through the one-request API (same sweeps per tick as graph size) the drag and the
+gradient agree bit for bit.  Admission by HBM budget, warm starts and the iteration cap are
+checked too."""
+import numpy as np
+import pytest
+
+from paper_2501_00923_gb300 import build, dvm, serve
+from paper_2501_00923_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+M = 20
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    c = dvm.Context(0, graph_iters=M)
+    yield c
+    c.close()
+
+
+def _specs():
+    rng = np.random.default_rng(5)
+    out = []
+    for (ni, nj, nv, Kn, Ma) in [(48, 16, 12, 1.0, 0.6), (64, 24, 16, 0.5, 1.2), (32, 12, 10, 2.0, 0.4)]:
+        out.append(serve.SolveSpec(W.omesh(ni, nj, rng.uniform(-0.01, 0.01, 6)), W.velocity_grid(nv, 4.0),
+                                   W.Flow(Kn, Ma), tol=1e-5, adjoint_tol=1e-5, max_iter=4000))
+    return out
+
+
+def _run(ctx, specs, **kw):
+    srv = serve.BatchServer(ctx, sweeps_per_tick=M, **kw)
+    tickets = [srv.submit(s) for s in specs]
+    for _ in range(10000):
+        a, q = srv.tick()
+        if a == 0 and q == 0:
+            break
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    return res
+
+
+def test_result_is_the_same_alone_in_a_mix_and_through_the_plain_api(ctx):
+    specs = _specs()
+    mixed = _run(ctx, specs)
+    for k, s in enumerate(specs):
+        alone = _run(ctx, [s])[0]
+        for key in ("J", "residual", "adjoint_residual", "primal_iters", "adjoint_iters", "status"):
+            assert alone[key] == mixed[k][key], key
+        assert np.array_equal(alone["grad"], mixed[k]["grad"])
+        m = dvm.Mesh(ctx, s.mesh.nodes)
+        g = dvm.VGrid(ctx, s.grid.vx, s.grid.vy, s.grid.w)
+        st, res = dvm.primal_solve(ctx, m, g, s.flow.Kn, s.flow.Ma, tol=s.tol, max_iter=s.max_iter)
+        ad, ares = dvm.adjoint_solve(ctx, st, tol=s.adjoint_tol, max_iter=s.max_iter)
+        grad = dvm.sensitivity(ctx, st, ad, s.mesh.dwall, s.mesh.s, mode="full")
+        assert res.J == mixed[k]["J"] and res.iters == mixed[k]["primal_iters"]
+        assert ares.iters == mixed[k]["adjoint_iters"]
+        assert np.array_equal(grad, mixed[k]["grad"])
+        assert mixed[k]["status"] == dvm.DVM_OK
+
+
+def test_admission_by_hbm_budget_queues_then_serves(ctx):
+    specs = _specs()
+    srv = serve.BatchServer(ctx, sweeps_per_tick=M, hbm_budget=int(14e6))   # room for one request at a time
+    tickets = [srv.submit(s) for s in specs]
+    a, q = srv.tick()
+    assert a == 1 and q == 2
+    for _ in range(10000):
+        a, q = srv.tick()
+        assert a <= 1
+        if a == 0 and q == 0:
+            break
+    assert all(srv.poll(t)["done"] for t in tickets)
+    with pytest.raises(dvm.DVMError) as e:
+        serve.BatchServer(ctx, sweeps_per_tick=M, hbm_budget=1000).submit(specs[0])
+    assert e.value.status == dvm.DVM_ERR_ADMISSION
+    srv.close()
+
+
+def test_warm_start_reuses_the_previous_state(ctx):
+    rng = np.random.default_rng(9)
+    alpha = rng.uniform(-0.01, 0.01, 6)
+    base = serve.SolveSpec(W.omesh(48, 16, alpha), W.velocity_grid(12, 4.0), W.Flow(1.0, 0.6), tol=1e-5,
+                           adjoint_tol=1e-5, max_iter=4000, warm_key=7)
+    nudged = serve.SolveSpec(W.omesh(48, 16, alpha + 1e-4), W.velocity_grid(12, 4.0), W.Flow(1.0, 0.6), tol=1e-5,
+                             adjoint_tol=1e-5, max_iter=4000, warm_key=7)
+    srv = serve.BatchServer(ctx, sweeps_per_tick=M)
+    t0 = srv.submit(base)
+    while srv.tick() != (0, 0):
+        pass
+    t1 = srv.submit(nudged)
+    while srv.tick() != (0, 0):
+        pass
+    r0, r1 = srv.poll(t0), srv.poll(t1)
+    assert r1["warm_started"] == 1 and r0["warm_started"] == 0
+    assert r1["primal_iters"] < r0["primal_iters"] and r1["adjoint_iters"] < r0["adjoint_iters"]
+    assert abs(r1["J"] - r0["J"]) < 1e-2 * abs(r0["J"])
+    srv.close()
+
+
+def test_iteration_cap_reports_not_converged(ctx):
+    s = _specs()[0]
+    s.max_iter = 40
+    s.tol = s.adjoint_tol = 1e-12
+    r = _run(ctx, [s])[0]
+    assert r["done"] and r["status"] == dvm.DVM_NOT_CONVERGED
+    assert r["primal_iters"] == 40 and r["adjoint_iters"] == 40
