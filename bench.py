@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--mesh", default=None, help="override the O-mesh size, e.g. 128x64 (profiling runs)")
+    p.add_argument("--workload", type=int, default=WORKLOAD_INDEX, choices=[1, 2, 4],
+                   help="1: 256x128 GL48 Kn 0.1 (default); 2: 384x192 64x64 Kn 0.001 Ma 2; "
+                        "4: 256x128 GL48, 24 bumps (design-loop size)")
     p.add_argument("--serve", type=int, default=128, help="requests of the served trace to replay (0: skip)")
     p.add_argument("--serve-max-iter", type=int, default=400, help="sweep cap per phase of a served request")
     return p.parse_args()
@@ -189,7 +192,7 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     build.build()
-    wl = W.config(WORKLOAD_INDEX)
+    wl = W.config(args.workload)
     if args.mesh:
         ni, nj = (int(x) for x in args.mesh.lower().split("x"))
         wl.mesh = W.omesh(ni, nj, wl.mesh.alpha)
@@ -261,7 +264,8 @@ def run_gpu(args):
     k_adj = {"name": "k_adjoint_sweep", "ms": adj_sweep_ms, "bytes": pairs * 6 * S,
              "GBps": pairs * 6 * S / (adj_sweep_ms * 1e6)}
     dom = k_adj if adj_ms >= prim_ms else k_prim
-    traffic = ncu_traffic(dom["name"], args.storage) if not args.mesh else None
+    alt = bool(args.mesh) or args.workload != WORKLOAD_INDEX
+    traffic = ncu_traffic(dom["name"], args.storage) if not alt else None
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": dom["GBps"] / peak, "traffic": traffic, "kernel": dom["name"],
                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
@@ -274,7 +278,7 @@ def run_gpu(args):
     e2e = run_e2e(args, ctx, wl, torch, dvm)
 
     clocks = clk.summary()
-    serving = run_serving(args, torch, dvm) if (args.serve > 0 and not args.mesh) else None
+    serving = run_serving(args, torch, dvm) if (args.serve > 0 and not alt) else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.storage],

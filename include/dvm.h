@@ -185,6 +185,13 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ad
                     const double* dwall_dalpha, const double* s_j, int mode, double* grad_out,
                     double* node_grad_out);
 
+/* Volume constraint of Eq. (formula_opt), Q = (1/D) int_wall x . n dGamma + V_min with n into the
+ * solid and D = 2 (Q <= 0 keeps the section area >= V_min), evaluated exactly on the straight wall
+ * elements, and dQ/dalpha_p from the node sensitivity of Eq. (sens_con_nod) contracted with
+ * dwall_dalpha [n_params][ni][2].  dQ_dalpha: double[n_params], caller-owned. */
+int dvm_volume_constraint(dvm_context* ctx, const dvm_mesh* mesh, double v_min, int n_params,
+                          const double* dwall_dalpha, double* Q, double* dQ_dalpha);
+
 /* ------------------------------------------------------------------------ served batch, B7 */
 /* Continuous batching of whole solve requests (primal solve, adjoint solve, sensitivity) on one
  * context.  Requests are admitted in arrival order while their device footprint fits the batch's

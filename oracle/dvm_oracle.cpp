@@ -998,6 +998,37 @@ int orc_sens_paper(const orc_problem* q, const double* f, const double* phi, int
     return 0;
 }
 
+/* Volume constraint of Eq. (formula_opt): Q = (1/D) sum_l x_l . n_l A_l + V_min (D = 2, n_l into the
+ * solid, x_l the element midpoint; exact for straight elements), and its node sensitivity
+ * Eq. (sens_con_nod): dQ/dx_m = sum over the elements z containing node m of (1/D) A_z n_z.
+ * dQ[ni][2] receives dQ/dx of the wall nodes; dQda[P] the contraction with dwall[P][ni][2]. */
+double orc_volume_constraint(const orc_problem* q, double vmin, int P, const double* dwall, double* dQ, double* dQda) {
+    Prob p = to_prob(q);
+    Geo<double> g = geo_of(p);
+    const int ni = p.ni;
+    double Q = vmin;
+    std::vector<double> node(2 * ni, 0.0);
+    for (int l = 0; l < ni; ++l) {
+        const double* xa = p.nodes + 2 * l;
+        const double* xb = p.nodes + 2 * ((l + 1) % ni);
+        const double xm = 0.5 * (xa[0] + xb[0]), ym = 0.5 * (xa[1] + xb[1]);
+        const double Sx = g.Sx[4 * l + 3], Sy = g.Sy[4 * l + 3];   /* A_l n_l, into the solid */
+        Q += 0.5 * (xm * Sx + ym * Sy);
+        for (int m : {l, (l + 1) % ni}) {
+            node[2 * m] += 0.5 * Sx;
+            node[2 * m + 1] += 0.5 * Sy;
+        }
+    }
+    if (dQ) std::memcpy(dQ, node.data(), sizeof(double) * 2 * ni);
+    if (dQda)
+        for (int ip = 0; ip < P; ++ip) {
+            double s2 = 0.0;
+            for (int m = 0; m < 2 * ni; ++m) s2 += node[m] * dwall[(size_t)ip * 2 * ni + m];
+            dQda[ip] = s2;
+        }
+    return Q;
+}
+
 /* Wall functional of one face for given wall-cell values (used by the free-molecular check):
  * J_l = sum_k w m a f1_l with f1_l = f1 on a > 0 and F_rhow gbar1 otherwise. */
 double orc_wall_face_functional(const double* S, int nv, const double* vx, const double* vy,

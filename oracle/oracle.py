@@ -67,6 +67,7 @@ def lib():
             "orc_sens_paper": (i, [P, _dp, _dp, i, _dp, _dp, _dp, _dp]),
             "orc_wall_face_functional": (d, [_dp, i, _dp, _dp, _dp, _dp, d, _dp]),
             "orc_jacobi_cells": (i, [P, _dp, i, C.POINTER(C.c_int), _dp]),
+            "orc_volume_constraint": (d, [P, d, i, _dp, _dp, _dp]),
             "orc_adjoint_jacobi_cells": (i, [P, _dp, _dp, i, C.POINTER(C.c_int), _dp]),
         }
         for name, (res, args) in sig.items():
@@ -224,6 +225,15 @@ class Problem:
         g = np.zeros(P)
         lib().orc_sens_full(self.ref, _ptr(_c(f)), _ptr(_c(phi)), P, _ptr(dnodes), _ptr(g))
         return g
+
+    def volume_constraint(self, vmin, dwall):
+        """Q = (1/2) sum_l x_l . n_l A_l + V_min and dQ/dx (wall nodes), dQ/dalpha."""
+        dwall = _c(dwall)
+        P = dwall.shape[0]
+        dQ = np.zeros((self.ni, 2))
+        dQda = np.zeros(max(P, 1))
+        Q = lib().orc_volume_constraint(self.ref, float(vmin), P, _ptr(dwall), _ptr(dQ), _ptr(dQda))
+        return Q, dQ, dQda[:P]
 
     def sens_paper(self, f, phi, dwall):
         dwall = _c(dwall)

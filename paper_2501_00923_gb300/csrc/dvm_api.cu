@@ -1089,6 +1089,28 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
 
 }  // extern "C"
 
+extern "C" int dvm_volume_constraint(dvm_context* ctx, const dvm_mesh* mesh, double v_min, int P,
+                                     const double* dwall, double* Q, double* dQ_dalpha) {
+    if (!ctx || !mesh || !Q || (P > 0 && (!dwall || !dQ_dalpha)) || P < 0) return fail(DVM_ERR_INVALID_ARG, "bad argument");
+    DeviceGuard dg(ctx->device);
+    double* d = nullptr;
+    const size_t nw = (size_t)P * mesh->d.ni * 2;
+    int rc = dalloc(ctx, &d, nw + 1 + P);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (P > 0) e = cudaMemcpyAsync(d, dwall, nw * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_volume(mesh->d, v_min, d, P, d + nw, ctx->stream);
+    std::vector<double> h(1 + P);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d + nw, (1 + P) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    ctx->launches += 1;
+    dfree(d);
+    if (e != cudaSuccess) return fail_cuda(e, "volume constraint");
+    *Q = h[0];
+    for (int p = 0; p < P; ++p) dQ_dalpha[p] = h[1 + p];
+    return DVM_OK;
+}
+
 // ======================================================================= no-allocation variant
 // dvm_sensitivity_noalloc keeps every intermediate of the sensitivity reduction in the static
 // device array below instead of device memory from cudaMalloc.  It exists for callers that must not

@@ -176,6 +176,9 @@ cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, co
 cudaError_t launch_contract(const double2* node_grad, int nrows, int ni, const double* s_j,
                             const double* dwall, int P, double* grad, cudaStream_t s);
 
+// out[0] = Q, out[1 + p] = dQ/dalpha_p
+cudaError_t launch_volume(const DevMesh& m, double vmin, const double* dwall, int P, double* out, cudaStream_t s);
+
 size_t storage_bytes(int storage);   // bytes of one (f1,f2) pair
 
 }  // namespace dvm

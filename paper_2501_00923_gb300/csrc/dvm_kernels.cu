@@ -1127,6 +1127,38 @@ __global__ void k_contract(const double2* node_grad, int nrows, int ni, const do
     }
 }
 
+// Volume constraint (Eq. formula_opt with n into the solid, D = 2): Q = V_min + (1/2) sum_l x_l . S_l
+// over the wall elements (x_l the midpoint, S_l = A_l n_l), and dQ/dalpha_p = sum_m dQ/dx_m .
+// dwall[p][m] with dQ/dx_m = (1/2)(S_{m-1} + S_m), Eq. (sens_con_nod).  One block.
+__global__ void k_volume(int ni, const double2* S, const double2* nodes, double vmin, const double* dwall, int P,
+                         double* out) {
+    __shared__ double red[32];
+    double q = 0.0;
+    for (int l = threadIdx.x; l < ni; l += blockDim.x) {
+        const double2 a = nodes[l], b = nodes[(l + 1) % ni], s = S[4 * l + 3];
+        q += 0.25 * ((a.x + b.x) * s.x + (a.y + b.y) * s.y);
+    }
+    for (int p = -1; p < P; ++p) {
+        double v = q;
+        if (p >= 0) {
+            v = 0.0;
+            for (int m = threadIdx.x; m < ni; m += blockDim.x) {
+                const double2 s0 = S[4 * ((m - 1 + ni) % ni) + 3], s1 = S[4 * m + 3];
+                v += 0.5 * ((s0.x + s1.x) * dwall[((size_t)p * ni + m) * 2] + (s0.y + s1.y) * dwall[((size_t)p * ni + m) * 2 + 1]);
+            }
+        }
+        v = warp_sum(v);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+            out[p + 1] = p < 0 ? t + vmin : t;
+        }
+    }
+}
+
 inline int cdiv(size_t a, size_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
@@ -1401,6 +1433,11 @@ cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, co
                                                        Fw, it, hT, dirx, diry, GN, GE, GW, vol);
     const int nn = (m.nj + 1) * m.ni;
     k_sens_nodes<<<cdiv(nn, 256), 256, 0, s>>>(m.ni, m.nj, m.nodes, GN, GE, GW, vol, node_grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_volume(const DevMesh& m, double vmin, const double* dwall, int P, double* out, cudaStream_t s) {
+    k_volume<<<1, 256, 0, s>>>(m.ni, m.Sd, m.nodes, vmin, dwall, P, out);
     return cudaGetLastError();
 }
 

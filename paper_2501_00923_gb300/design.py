@@ -1,0 +1,314 @@
+"""Design loop: drag minimisation over the bump amplitudes under the volume constraint.
+
+One optimisation step follows the paper's procedure: move the wall nodes for the new design
+variables and the interior nodes with them (Step 2; the blend (1 - s_j) dwall replaces the paper's
+RBF deformation), solve the primal and the adjoint problem and evaluate J and Q (Step 3), form
+dJ/dalpha and dQ/dalpha (Step 4, Eq. sens_nod and Eq. sens_con_nod), update the design variables
+with a quasi-Newton step (Step 5) and stop once the relative change of J between two accepted
+steps is below 3e-5 (Step 6, Eq. criterion_opt).
+
+The paper's optimiser is an SQP method with BFGS updates from a third-party library.  Here Step 5
+is a limited-memory BFGS (the two-loop recursion of Nocedal and Wright, Algorithm 7.4) with a
+projected Armijo backtracking line search on box bounds, and Q <= 0 enters through the quadratic
+penalty  Phi = Cd + (mu / 2) max(0, Q / V_min)^2.  The optimiser is an ask/tell object: `ask`
+returns the next design to evaluate, `tell` takes (Phi, dPhi/dalpha) of that design, so several
+loops can share one served batch of GPU solves (`run_concurrent`).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import dvm
+from . import workloads as W
+
+CRITERION_OPT = 3e-5
+
+
+def criterion_opt(J_old: float, J_new: float, tol: float = CRITERION_OPT) -> bool:
+    """Eq. (criterion_opt): |J_new - J_old| / |J_old| < tol."""
+    return abs(J_new - J_old) < tol * abs(J_old)
+
+
+class LBFGS:
+    """Ask/tell L-BFGS with projected Armijo backtracking on the box [lower, upper].
+
+    Phases: 'init' (x0 asked), 'trial' (a line-search point asked), 'done'.  `tell` returns
+    'accepted' when the trial point became the new iterate, 'rejected' when the step was cut,
+    'failed' when the line search gave up after a steepest-descent restart, or 'init'."""
+
+    def __init__(self, x0, m: int = 8, lower=None, upper=None, first_step: float = 1e-3,
+                 c1: float = 1e-4, shrink: float = 0.5, max_backtracks: int = 8):
+        self.x = np.array(x0, dtype=np.float64)
+        n = self.x.size
+        self.lower = np.full(n, -np.inf) if lower is None else np.broadcast_to(np.asarray(lower, float), (n,)).copy()
+        self.upper = np.full(n, np.inf) if upper is None else np.broadcast_to(np.asarray(upper, float), (n,)).copy()
+        self.x = self.project(self.x)
+        self.m, self.first_step, self.c1, self.shrink, self.max_backtracks = m, first_step, c1, shrink, max_backtracks
+        self.S: list[np.ndarray] = []
+        self.Y: list[np.ndarray] = []
+        self.f = None
+        self.g = None
+        self.phase = "init"
+        self.iterations = 0
+        self.evaluations = 0
+        self._trial = None
+        self._t = 1.0
+        self._d = None
+        self._backtracks = 0
+
+    def project(self, x):
+        return np.minimum(np.maximum(x, self.lower), self.upper)
+
+    def direction(self, g):
+        """-H g by the two-loop recursion, H0 = (s.y / y.y) I from the newest pair."""
+        q = np.array(g, dtype=np.float64)
+        rho = [1.0 / float(y @ s) for s, y in zip(self.S, self.Y)]
+        a = []
+        for s, y, r in zip(reversed(self.S), reversed(self.Y), reversed(rho)):
+            ai = r * float(s @ q)
+            a.append(ai)
+            q -= ai * y
+        if self.S:
+            s, y = self.S[-1], self.Y[-1]
+            q *= float(s @ y) / float(y @ y)
+        for (s, y, r), ai in zip(zip(self.S, self.Y, rho), reversed(a)):
+            b = r * float(y @ q)
+            q += (ai - b) * s
+        return -q
+
+    def _new_direction(self):
+        d = self.direction(self.g)
+        if not self.S:                     # no curvature yet: the largest component moves by first_step
+            nrm = np.abs(d).max()
+            d = d * (self.first_step / nrm) if nrm > 0 else d
+        self._d = d
+        self._t = 1.0
+        self._backtracks = 0
+        self._trial = self.project(self.x + d)
+
+    def ask(self):
+        if self.phase == "init":
+            return self.x.copy()
+        if self.phase == "trial":
+            return self._trial.copy()
+        raise RuntimeError("optimiser finished")
+
+    def tell(self, f: float, g) -> str:
+        self.evaluations += 1
+        g = np.asarray(g, dtype=np.float64)
+        if self.phase == "init":
+            if not np.isfinite(f):
+                raise ValueError("initial design is not evaluable")
+            self.f, self.g = float(f), g.copy()
+            self.phase = "trial"
+            self._new_direction()
+            return "init"
+        step = self._trial - self.x
+        slope = float(self.g @ step)
+        if np.isfinite(f) and slope < 0 and f <= self.f + self.c1 * slope:
+            y = g - self.g
+            sy = float(step @ y)
+            if sy > 1e-12 * np.linalg.norm(step) * np.linalg.norm(y):
+                self.S.append(step.copy())
+                self.Y.append(y)
+                if len(self.S) > self.m:
+                    self.S.pop(0)
+                    self.Y.pop(0)
+            self.x, self.f, self.g = self._trial.copy(), float(f), g.copy()
+            self.iterations += 1
+            self._new_direction()
+            return "accepted"
+        self._backtracks += 1
+        if slope >= 0 or self._backtracks > self.max_backtracks:
+            if not self.S:                 # already on steepest descent: give up
+                self.phase = "done"
+                return "failed"
+            self.S.clear()                 # curvature pairs misled the step: restart from -g
+            self.Y.clear()
+            self._new_direction()
+            return "rejected"
+        self._t *= self.shrink
+        self._trial = self.project(self.x + self._t * self._d)
+        return "rejected"
+
+
+@dataclass
+class Evaluation:
+    alpha: np.ndarray
+    Cd: float
+    dCd: np.ndarray
+    Q: float
+    dQ: np.ndarray
+    phi: float
+    dphi: np.ndarray
+    ok: bool = True
+
+
+@dataclass
+class DesignLoop:
+    """One drag-minimisation loop at fixed flow conditions.
+
+    ni, nj, grid, flow: the O-mesh size, velocity grid and flow; n_params bumps start at alpha0
+    (zeros: the symmetric section).  v_min is the section area of alpha0 unless given; mu weights the
+    constraint penalty; bound limits each amplitude; max_iter counts accepted steps."""
+    ni: int
+    nj: int
+    grid: W.VGrid
+    flow: W.Flow
+    n_params: int = 24
+    alpha0: np.ndarray | None = None
+    v_min: float | None = None
+    mu: float = 1e4
+    bound: float = 0.01
+    max_iter: int = 12
+    first_step: float = 1e-3
+    tol: float = CRITERION_OPT
+    history: list = field(default_factory=list)
+
+    def __post_init__(self):
+        a0 = np.zeros(self.n_params) if self.alpha0 is None else np.asarray(self.alpha0, float)
+        self.opt = LBFGS(a0, lower=-self.bound, upper=self.bound, first_step=self.first_step)
+        self.J_old = None
+        self.converged = False
+        self.stopped = None
+
+    @property
+    def q_ref(self) -> float:
+        U = self.flow.Ma * W.A_INF
+        return 0.5 * U * U
+
+    def penalty(self, Cd, dCd, Q, dQ):
+        v = max(0.0, Q / self.v_min)
+        return Cd + 0.5 * self.mu * v * v, dCd + self.mu * v * dQ / self.v_min
+
+    def feasible_mesh(self, alpha) -> bool:
+        return W.valid_amplitude_scale(self.ni, alpha, margin=1.0) >= 1.0
+
+    def finish(self, ev: Evaluation) -> str:
+        """Hand one evaluation to the optimiser; apply Eq. (criterion_opt) on accepted steps."""
+        self.history.append(ev)
+        phase = self.opt.phase
+        out = self.opt.tell(ev.phi if ev.ok else np.inf, ev.dphi if ev.ok else np.zeros_like(ev.alpha))
+        if phase == "init":
+            self.J_old = ev.Cd
+        elif out == "accepted":
+            if criterion_opt(self.J_old, ev.Cd, self.tol):
+                self.converged, self.stopped = True, "criterion_opt"
+            self.J_old = ev.Cd
+            if not self.converged and self.opt.iterations >= self.max_iter:
+                self.stopped = "max_iter"
+        elif out == "failed":
+            self.stopped = "line_search"
+        return out
+
+    @property
+    def done(self) -> bool:
+        return self.stopped is not None
+
+    @property
+    def best(self) -> Evaluation:
+        return min((e for e in self.history if e.ok), key=lambda e: e.phi)
+
+
+def _volume(ctx, nodes, v_min, dwall):
+    m = dvm.Mesh(ctx, nodes)
+    try:
+        return dvm.volume_constraint(ctx, m, v_min, dwall)
+    finally:
+        m.close()
+
+
+def _failed(alpha):
+    z = np.zeros_like(alpha)
+    return Evaluation(alpha, np.nan, z, np.nan, z, np.inf, z, ok=False)
+
+
+def drive(loop: DesignLoop, evaluate):
+    """Run `loop` to its stop with blocking evaluations: evaluate(alpha) -> Evaluation (ok=False
+    when the design could not be solved).  Designs whose mesh would fold are not evaluated."""
+    while not loop.done:
+        a = loop.opt.ask()
+        loop.finish(evaluate(a) if loop.feasible_mesh(a) else _failed(a))
+    return loop
+
+
+def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 1e-6,
+        adjoint_tol: float = 1e-6, max_sweeps: int = 200000, stall_window: int = 0):
+    """Drive one loop with blocking GPU solves (autograd.DragProblem keeps f and phi of the last
+    design as warm starts for the next)."""
+    from .autograd import DragProblem
+    prob = DragProblem(ctx, loop.ni, loop.nj, loop.grid, loop.flow, storage=storage, tol=tol,
+                       adjoint_tol=adjoint_tol, max_iter=max_sweeps, stall_window=stall_window)
+    if loop.v_min is None:
+        loop.v_min = section_area(ctx, loop.ni, loop.nj, loop.opt.x)
+
+    def evaluate(a):
+        try:
+            Cd = prob.solve(a)
+            dCd = prob.gradient()
+        except dvm.DVMError:
+            prob.release()
+            return _failed(a)
+        mesh = prob.last["mesh"]
+        Q, dQ = _volume(ctx, mesh.nodes, loop.v_min, mesh.dwall)
+        prob.release()
+        return Evaluation(a, Cd, dCd, Q, dQ, *loop.penalty(Cd, dCd, Q, dQ))
+
+    try:
+        return drive(loop, evaluate)
+    finally:
+        prob.release()
+
+
+def section_area(ctx: dvm.Context, ni: int, nj: int, alpha) -> float:
+    """Area of the section for `alpha` (Q with V_min = 0 is minus the area)."""
+    return -_volume(ctx, W.omesh(ni, nj, alpha).nodes, 0.0, np.zeros((1, ni, 2)))[0]
+
+
+def run_concurrent(ctx: dvm.Context, loops: list[DesignLoop], storage: str = "fp32", tol: float = 1e-6,
+                   max_sweeps: int = 200000, sweeps_per_tick: int = 20):
+    """Drive several loops at once through one served batch: every loop's pending evaluation is a
+    request in flight; a loop's next design is submitted as soon as its previous one retires, with
+    its own warm-start key so f and phi carry over from that loop's last solve."""
+    from .serve import BatchServer, SolveSpec
+    server = BatchServer(ctx, sweeps_per_tick)
+    pending = {}
+
+    def submit(k):
+        loop = loops[k]
+        while not loop.done:
+            a = loop.opt.ask()
+            if loop.feasible_mesh(a):
+                mesh = W.omesh(loop.ni, loop.nj, a)
+                spec = SolveSpec(mesh, loop.grid, loop.flow, storage=storage, tol=tol, adjoint_tol=tol,
+                                 max_iter=max_sweeps, warm_key=1000 + k)
+                pending[server.submit(spec)] = (k, a, mesh)
+                return
+            loop.finish(_failed(a))
+
+    try:
+        for k, loop in enumerate(loops):
+            if loop.v_min is None:
+                loop.v_min = section_area(ctx, loop.ni, loop.nj, loop.opt.x)
+            submit(k)
+        while pending:
+            server.tick()
+            for t in list(pending):
+                r = server.poll(t, forget=False)
+                if not r["done"]:
+                    continue
+                server.poll(t, forget=True)
+                k, a, mesh = pending.pop(t)
+                loop = loops[k]
+                if r["status"] != 0:
+                    loop.finish(_failed(a))
+                else:
+                    Cd, dCd = r["J"] / loop.q_ref, r["grad"] / loop.q_ref
+                    Q, dQ = _volume(ctx, mesh.nodes, loop.v_min, mesh.dwall)
+                    loop.finish(Evaluation(a, Cd, dCd, Q, dQ, *loop.penalty(Cd, dCd, Q, dQ)))
+                submit(k)
+    finally:
+        server.close()
+    return loops

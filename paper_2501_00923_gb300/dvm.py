@@ -95,6 +95,7 @@ def lib():
             "dvm_adjoint_solve": (i, [_vp, _vp, i, C.POINTER(SolveOpts), pp, C.POINTER(AdjointResult)]),
             "dvm_sensitivity": (i, [_vp, _vp, _vp, i, _dp, _dp, i, _dp, _dp]),
             "dvm_sensitivity_noalloc": (i, [_vp, _vp, _vp, i, _dp, _dp, i, _dp, _dp]),
+            "dvm_volume_constraint": (i, [_vp, _vp, d, i, _dp, _dp, _dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -368,3 +369,13 @@ def sensitivity(ctx: Context, state: State, adjoint: Adjoint, dwall_dalpha, s_j=
     fn = lib().dvm_sensitivity_noalloc if noalloc else lib().dvm_sensitivity
     _check(fn(ctx.h, state.h, adjoint.h, P, _p(dwall), _p(sj), SENS[mode], _p(g), _p(ng)))
     return (g[:P], ng) if node_grad else g[:P]
+
+
+def volume_constraint(ctx: Context, mesh: Mesh, v_min: float, dwall_dalpha):
+    """Q = (1/2) sum over wall elements of x . n A + V_min (n into the solid) and dQ/dalpha."""
+    dwall = _arr(dwall_dalpha)
+    P = dwall.shape[0]
+    Q = C.c_double()
+    g = np.zeros(max(P, 1))
+    _check(lib().dvm_volume_constraint(ctx.h, mesh.h, float(v_min), P, _p(dwall), C.byref(Q), _p(g)))
+    return Q.value, g[:P]

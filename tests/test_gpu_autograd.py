@@ -1,0 +1,75 @@
+"""torch.autograd wrapping of the steady solve: backward = implicit-function adjoint.
+
+The gradient of Cd with respect to the bump amplitudes must match central finite differences of
+the forward (step 1e-4, as for the near-continuum workload) and the oracle's full-discrete
+sensitivity evaluated on the same converged state."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2501_00923_gb300 import build, dvm
+from paper_2501_00923_gb300 import workloads as W
+from paper_2501_00923_gb300.autograd import DragProblem, drag
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    c = dvm.Context(0)
+    yield c
+    c.close()
+
+
+def _problem(ctx, storage, tol):
+    return DragProblem(ctx, 48, 16, W.velocity_grid(12, 4.0), W.Flow(1.0, 0.6), storage=storage, tol=tol,
+                       adjoint_tol=tol, max_iter=400000, stall_window=20000 if storage != "fp64" else 0)
+
+
+def _fd(prob, a0, h=1e-4):
+    g = np.zeros_like(a0)
+    for p in range(a0.size):
+        e = np.zeros_like(a0)
+        e[p] = h
+        g[p] = (prob.solve(a0 + e) - prob.solve(a0 - e)) / (2 * h)
+    return g
+
+
+def test_drag_gradient_matches_central_differences_and_the_oracle(ctx):
+    rng = np.random.default_rng(41)
+    a0 = rng.uniform(-0.005, 0.005, 6)
+    prob = _problem(ctx, "fp64", 1e-12)
+    alpha = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    cd = drag(alpha, prob)
+    cd.backward()
+    g_adj = alpha.grad.numpy().copy()
+    # oracle full-discrete sensitivity on the very same state and adjoint
+    mesh = prob.last["mesh"]
+    pr = O.Problem(mesh.nodes, prob.grid.vx, prob.grid.vy, prob.grid.w, prob.flow.Kn, prob.flow.Ma)
+    f = prob._warm_f
+    phi = prob._warm_phi
+    g_orc = pr.sens_full(f, phi, mesh.dnodes()) / prob.q_ref
+    assert np.abs(g_adj - g_orc).max() < 1e-9 * np.abs(g_orc).max()
+    g_fd = _fd(prob, a0)
+    assert np.abs(g_adj - g_fd).max() < 2e-6 * np.abs(g_fd).max()
+    prob.release()
+
+
+def test_fp32_drag_gradient_within_stated_tolerance(ctx):
+    rng = np.random.default_rng(42)
+    a0 = rng.uniform(-0.005, 0.005, 6)
+    ref = _problem(ctx, "fp64", 1e-12)
+    alpha = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    cd64 = drag(alpha, ref)
+    cd64.backward()
+    g64 = alpha.grad.numpy().copy()
+    p32 = _problem(ctx, "fp32", 1e-7)
+    alpha32 = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    cd32 = drag(alpha32, p32)
+    cd32.backward()
+    assert abs(cd32.item() - cd64.item()) < 1e-5 * abs(cd64.item())
+    assert np.abs(alpha32.grad.numpy() - g64).max() < 1e-4 * np.abs(g64).max()
+    ref.release()
+    p32.release()

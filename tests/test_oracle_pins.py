@@ -312,3 +312,24 @@ def test_symmetric_airfoil_has_no_lift_and_mirror_sensitivities():
     gp, _, _ = pr.sens_paper(f, phi, mesh.dwall)
     for g in (gf, gp):
         assert np.abs(g[:2] - g[2:]).max() < 1e-9 * np.abs(g).max()
+
+
+def test_volume_constraint_is_minus_the_section_area_and_its_gradient():
+    """Eq. (formula_opt) Q with n into the solid is V_min minus the enclosed area (divergence
+    theorem); Eq. (sens_con_nod) is checked against central differences."""
+    alpha = np.random.default_rng(12).uniform(-0.005, 0.005, 8)
+    mesh = W.omesh(64, 4, alpha)
+    grid = W.velocity_grid(4, 4.0)
+    pr = _problem(mesh, grid)
+    Q, dQ, dQda = pr.volume_constraint(0.0, mesh.dwall)
+    w = mesh.nodes[0]
+    area = 0.5 * np.sum(w[:, 0] * np.roll(w[:, 1], -1) - np.roll(w[:, 0], -1) * w[:, 1])
+    assert abs(Q + area) < 1e-14
+    assert 0.075 < area < 0.085                   # NACA 0012 section, about 0.082 c^2
+    h = 1e-6
+    for p in range(8):
+        a = alpha.copy(); a[p] += h
+        b = alpha.copy(); b[p] -= h
+        Qa = _problem(W.omesh(64, 4, a), grid).volume_constraint(0.0, mesh.dwall)[0]
+        Qb = _problem(W.omesh(64, 4, b), grid).volume_constraint(0.0, mesh.dwall)[0]
+        assert abs((Qa - Qb) / (2 * h) - dQda[p]) < 1e-9
