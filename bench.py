@@ -63,6 +63,27 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x itself without one).
+    The whole-job time of a weak-scaling run is the slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, ms_per_rank: float, device=None):
+    """(whole-job units/s, job ms): every rank processed units_per_rank; the job lasted as long as
+    its slowest rank."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = max_over_ranks(ms_per_rank, device)
+    return units_per_rank * world / (ms / 1e3), ms
+
+
 def hbm_peak():
     try:
         with open(PEAKS_FILE) as fh:
@@ -246,12 +267,7 @@ def run_gpu(args):
     prim_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
     adj_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
     sens_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    units = 2 * args.sweeps * pairs * args.steps * world
-    value = units / (total_ms / 1e3)
+    value, total_ms = job_throughput(2 * args.sweeps * pairs * args.steps, total_ms, device="cuda")
 
     # roofline of the dominant kernel (algorithmic bytes: read f + write f' = 4S per primal update,
     # read phi, f + write phi' = 6S per adjoint update; S = bytes per stored scalar)

@@ -85,6 +85,13 @@ typedef struct {
     double tol;             /* stop when |R|/r0 <= tol; |R| = sqrt(sum_{c,k,comp} w_k (R/V_c)^2) */
     int max_iter;           /* cap on point-implicit sweeps */
     int stall_window;       /* stop with DVM_ERR_STAGNATED after this many sweeps without a 2% drop; 0 = off */
+    int accel_depth;        /* 0 = plain sweeps.  m in [1, 8]: Anderson mixing of depth m applied to the map of
+                               accel_period sweeps (x -> G(x); next x = G - dG gamma, gamma = argmin |r - dR gamma|
+                               over the last m differences of r = G(x) - x and of G).  It accelerates the
+                               iteration only: the discrete solution is the same.  The history holds 2m + 3
+                               vectors of the state's size (FP32; FP64 for FP64 storage), kept with the state or
+                               adjoint.  A mix that makes any value negative is undone and the history restarts */
+    int accel_period;       /* sweeps between mixings (>= 1; with accel_depth > 0) */
 } dvm_solve_opts;
 
 typedef struct {
@@ -229,6 +236,8 @@ typedef struct {
     const double* s_j;          /* [nj+1], copied (DVM_SENS_FULL) */
     int sens_mode;              /* dvm_sens_mode */
     uint64_t warm_key;          /* 0 -> no warm start */
+    int stall_window;           /* > 0: a phase ends with DVM_ERR_STAGNATED once its residual has not
+                                   fallen below 0.98 x its best for this many sweeps (as dvm_solve_opts) */
 } dvm_request;
 
 typedef struct {

@@ -42,6 +42,20 @@ struct dvm_vgrid {
     DevGrid d;
 };
 
+// Anderson-mixing history of one solve (allocated on the first accelerated solve of a state or
+// adjoint): the iterate X at the start of the current block of sweeps, the previous residual and
+// image, the rings of their differences, and the Gram matrix of the residual differences.
+struct AAState {
+    int m = 0, storage = 0;
+    size_t n = 0, bytes = 0;
+    void *X = nullptr, *Rp = nullptr, *Gp = nullptr, *dR = nullptr, *dG = nullptr;
+    double *part = nullptr, *out = nullptr, *gamma = nullptr;
+    int* neg = nullptr;
+    int cnt = 0, slot = 0, steps = 0;       // columns in use, next ring slot, blocks since (re)start
+    int mixes = 0, rejects = 0;
+    std::vector<double> H;                  // m x m: dR_i . dR_j
+};
+
 struct dvm_state {
     dvm_context* ctx = nullptr;
     const dvm_mesh* mesh = nullptr;
@@ -64,6 +78,7 @@ struct dvm_state {
     int graph_cur = -1;
     uint64_t version = 0;       // bumped whenever f changes (sweeps, uploads)
     TmaMaps maps[2];            // tiled-TMA descriptors of f[0], f[1]
+    AAState* aa = nullptr;
 };
 
 struct dvm_adjoint {
@@ -90,6 +105,7 @@ struct dvm_adjoint {
     double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr;
     double *vol = nullptr, *elem = nullptr, *dwall = nullptr, *sj = nullptr, *grad = nullptr;
     int sens_P = 0;
+    AAState* aa = nullptr;
 };
 
 namespace {
@@ -192,7 +208,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     if constexpr (sizeof(TC) == 8) {
         a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.fd = st->fl.fdd; a.gw = st->fl.gwd;
     } else {
-        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.fd = st->fl.fdf; a.gw = st->fl.gwf;
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.vp = g.vp; a.fd = st->fl.fdf; a.gw = st->fl.gwf;
     }
     a.wallD = st->fl.wallD;
     a.inv_tau_inf = 1.0 / st->fl.tau_inf;
@@ -227,7 +243,7 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     if constexpr (sizeof(TC) == 8) {
         a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.gw = st->fl.gwd;
     } else {
-        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.gw = st->fl.gwf;
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.vp = g.vp; a.gw = st->fl.gwf;
     }
     a.wallD = st->fl.wallD;
     a.wallM = ad->wallM;
@@ -325,6 +341,139 @@ int run_adjoint_plain(dvm_adjoint* ad, int n, double* hist) {
         ad->cur = 1 - ad->cur;
         ad->st->ctx->launches += 2;
     }
+    return DVM_OK;
+}
+
+// ---------------------------------------------------------------- Anderson mixing (host side)
+void aa_free(dvm_context* ctx, AAState*& A) {
+    if (!A) return;
+    dfree(A->X); dfree(A->Rp); dfree(A->Gp); dfree(A->dR); dfree(A->dG);
+    dfree(A->part); dfree(A->out); dfree(A->gamma); dfree(A->neg);
+    ctx->bytes -= A->bytes;
+    delete A;
+    A = nullptr;
+}
+
+// History for n-element vectors of the given storage and depth m (reused when they match).
+int aa_ensure(dvm_context* ctx, AAState*& A, int storage, size_t n, int m) {
+    if (A && A->m == m && A->n == n && A->storage == storage) return DVM_OK;
+    aa_free(ctx, A);
+    A = new (std::nothrow) AAState();
+    if (!A) return fail(DVM_ERR_OOM, "host allocation");
+    A->m = m; A->n = n; A->storage = storage;
+    const size_t eb = storage == DVM_STORE_FP64 ? 8 : 4;
+    void** vec[5] = {&A->X, &A->Rp, &A->Gp, &A->dR, &A->dG};
+    const size_t len[5] = {n, n, n, (size_t)m * n, (size_t)m * n};
+    int rc = DVM_OK;
+    for (int i = 0; i < 5 && !rc; ++i) {
+        unsigned char* p = nullptr;
+        rc = dalloc(ctx, &p, len[i] * eb, &A->bytes);
+        *vec[i] = p;
+    }
+    if (!rc) rc = dalloc(ctx, &A->part, (size_t)aa_blocks() * 2 * m, &A->bytes);
+    if (!rc) rc = dalloc(ctx, &A->out, 2 * (size_t)m, &A->bytes);
+    if (!rc) rc = dalloc(ctx, &A->gamma, (size_t)m, &A->bytes);
+    if (!rc) rc = dalloc(ctx, &A->neg, 1, &A->bytes);
+    ctx->bytes += A->bytes;
+    if (rc) {
+        aa_free(ctx, A);
+        return rc;
+    }
+    A->H.assign((size_t)m * m, 0.0);
+    return DVM_OK;
+}
+
+// Start a solve: X <- F, empty history.
+int aa_begin(dvm_context* ctx, AAState* A, const void* F) {
+    A->cnt = A->slot = A->steps = 0;
+    CK(launch_aa_load(A->storage, A->n, F, A->X, ctx->stream));
+    ctx->launches += 1;
+    return DVM_OK;
+}
+
+// Solve (H + eps I) gamma = b for the cnt columns in use (Cholesky, eps = 1e-10 of the mean diagonal).
+bool aa_solve(const std::vector<double>& Hm, int m, int cnt, const double* b, double* gamma) {
+    std::vector<double> A((size_t)cnt * cnt), L((size_t)cnt * cnt, 0.0);
+    double tr = 0.0;
+    for (int i = 0; i < cnt; ++i) tr += Hm[(size_t)i * m + i];
+    if (!(tr > 0.0) || !std::isfinite(tr)) return false;
+    const double eps = 1e-10 * tr / cnt;
+    for (int i = 0; i < cnt; ++i)
+        for (int j = 0; j < cnt; ++j) A[(size_t)i * cnt + j] = Hm[(size_t)i * m + j] + (i == j ? eps : 0.0);
+    for (int j = 0; j < cnt; ++j) {
+        double d = A[(size_t)j * cnt + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * cnt + k] * L[(size_t)j * cnt + k];
+        if (!(d > 0.0)) return false;
+        L[(size_t)j * cnt + j] = sqrt(d);
+        for (int i = j + 1; i < cnt; ++i) {
+            double v = A[(size_t)i * cnt + j];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * cnt + k] * L[(size_t)j * cnt + k];
+            L[(size_t)i * cnt + j] = v / L[(size_t)j * cnt + j];
+        }
+    }
+    std::vector<double> y(cnt);
+    for (int i = 0; i < cnt; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= L[(size_t)i * cnt + k] * y[k];
+        y[i] = v / L[(size_t)i * cnt + i];
+    }
+    for (int i = cnt - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < cnt; ++k) v -= L[(size_t)k * cnt + i] * gamma[k];
+        gamma[i] = v / L[(size_t)i * cnt + i];
+    }
+    for (int i = 0; i < cnt; ++i)
+        if (!std::isfinite(gamma[i])) return false;
+    return true;
+}
+
+// One mixing step after a block of sweeps left G in F.  *mixed = true when F now holds the mixed
+// iterate (then the caller refreshes what depends on F).
+int aa_step(dvm_context* ctx, AAState* A, void* F, bool* mixed) {
+    *mixed = false;
+    cudaStream_t s = ctx->stream;
+    const int m = A->m;
+    const bool first = A->steps == 0;
+    const int slot = A->slot, cnt = first ? 0 : std::min(A->cnt + 1, m);
+    CK(launch_aa_collect(A->storage, A->n, F, A->X, A->Rp, A->Gp, A->dR, A->dG, m, cnt, slot, first ? 1 : 0,
+                         A->part, A->out, s));
+    ctx->launches += first ? 1 : 2;
+    A->steps += 1;
+    if (first) return DVM_OK;
+    std::vector<double> o(2 * (size_t)m);
+    CK(cudaMemcpyAsync(o.data(), A->out, o.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < cnt; ++i) {
+        A->H[(size_t)slot * m + i] = o[i];
+        A->H[(size_t)i * m + slot] = o[i];
+    }
+    A->cnt = cnt;
+    A->slot = (slot + 1) % m;
+    std::vector<double> gam(m, 0.0);
+    if (!aa_solve(A->H, m, cnt, o.data() + m, gam.data())) return DVM_OK;   // keep G, history goes on
+    int zero = 0, neg = 0;
+    CK(cudaMemcpyAsync(A->gamma, gam.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(A->neg, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(launch_aa_mix(A->storage, A->n, F, A->X, A->Gp, A->dG, cnt, A->gamma, A->neg, s));
+    CK(cudaMemcpyAsync(&neg, A->neg, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->launches += 1;
+    if (neg) {                         // a negative distribution value: undo, restart the history
+        CK(launch_aa_restore(A->storage, A->n, F, A->X, A->Gp, s));
+        ctx->launches += 1;
+        A->cnt = A->slot = A->steps = 0;
+        A->rejects += 1;
+        return DVM_OK;
+    }
+    A->mixes += 1;
+    *mixed = true;
+    return DVM_OK;
+}
+
+int check_solve_opts(const dvm_solve_opts* o) {
+    if (o->max_iter < 0 || !(o->tol >= 0.0)) return fail(DVM_ERR_INVALID_ARG, "bad solve options");
+    if (o->accel_depth < 0 || o->accel_depth > aa_max_depth() || (o->accel_depth > 0 && o->accel_period < 1))
+        return fail(DVM_ERR_INVALID_ARG, "accel_depth must be in [0, 8] and accel_period >= 1");
     return DVM_OK;
 }
 
@@ -564,10 +713,15 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
     DeviceGuard dg(ctx->device);
     const int nvp = (nv + kPad - 1) / kPad * kPad;
     std::vector<double4> vd(nvp, double4{0, 0, 0, 0});
-    std::vector<float4> vf(nvp, float4{0, 0, 0, 0});
+    std::vector<float4> vf(nvp, float4{0, 0, 0, 0}), vp(nvp, float4{0, 0, 0, 0});
     for (int k = 0; k < nv; ++k) {
         vd[k] = double4{vx[k], vy[k], w[k], 0.5 * (vx[k] * vx[k] + vy[k] * vy[k])};
         vf[k] = float4{(float)vx[k], (float)vy[k], (float)w[k], (float)vd[k].w};
+    }
+    for (int p = 0; p < nvp / 2; ++p) {
+        const float4 a = vf[2 * p], b = vf[2 * p + 1];
+        vp[2 * p] = float4{a.x, b.x, a.y, b.y};
+        vp[2 * p + 1] = float4{a.z, b.z, a.w, b.w};
     }
     dvm_vgrid* g = new (std::nothrow) dvm_vgrid();
     if (!g) return fail(DVM_ERR_OOM, "host allocation");
@@ -576,9 +730,13 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
     g->d.nvp = nvp;
     int rc;
     live_add(g, kGrid, ctx);
-    if ((rc = dalloc(ctx, &g->d.vd, nvp)) || (rc = dalloc(ctx, &g->d.vf, nvp))) { dvm_vgrid_destroy(g); return rc; }
+    if ((rc = dalloc(ctx, &g->d.vd, nvp)) || (rc = dalloc(ctx, &g->d.vf, nvp)) || (rc = dalloc(ctx, &g->d.vp, nvp))) {
+        dvm_vgrid_destroy(g);
+        return rc;
+    }
     cudaError_t e = cudaMemcpy(g->d.vd, vd.data(), nvp * sizeof(double4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d.vf, vf.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d.vp, vp.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { dvm_vgrid_destroy(g); return fail_cuda(e, "grid upload"); }
     *out = g;
     return DVM_OK;
@@ -587,7 +745,7 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
 void dvm_vgrid_destroy(dvm_vgrid* g) {
     if (!g || !live_take(g, kGrid)) return;
     DeviceGuard dg(g->ctx->device);
-    dfree(g->d.vd); dfree(g->d.vf);
+    dfree(g->d.vd); dfree(g->d.vf); dfree(g->d.vp);
     delete g;
 }
 
@@ -602,6 +760,7 @@ void dvm_state_destroy(dvm_state* st) {
     for (int b = 0; b < 2; ++b) { dfree(st->f[b]); dfree(st->prim[b]); dfree(st->Fw[b]); }
     dfree(st->Jpart); dfree(st->respart); dfree(st->out); dfree(st->scratch);
     dfree(st->fl.fdd); dfree(st->fl.fdf); dfree(st->fl.gwd); dfree(st->fl.gwf); dfree(st->fl.wallD); dfree(st->fl.wallM);
+    aa_free(st->ctx, st->aa);
     st->ctx->bytes -= st->bytes;
     delete st;
 }
@@ -774,7 +933,8 @@ int dvm_state_functional(dvm_state* st, int functional, double* J) {
 int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid, const dvm_flow* flow,
                      const dvm_solve_opts* opts, int storage, dvm_state** inout, dvm_primal_result* res) {
     if (!ctx || !mesh || !grid || !flow || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
-    if (opts->max_iter < 0 || !(opts->tol >= 0.0)) return fail(DVM_ERR_INVALID_ARG, "bad solve options");
+    int rc0;
+    if ((rc0 = check_solve_opts(opts))) return rc0;
     DeviceGuard dg(ctx->device);
     std::memset(res, 0, sizeof(*res));
     int rc;
@@ -788,8 +948,14 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
             return fail(DVM_ERR_INVALID_ARG, "warm-start state has another flow; create a new state");
     }
     dvm_state* st = *inout;
-    const int K = ctx->graph_iters;
-    const bool use_graph = graphs_ok(ctx);
+    const bool accel = opts->accel_depth > 0;
+    const int K = accel ? opts->accel_period : ctx->graph_iters;
+    const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
+    if (accel) {
+        const size_t n = (size_t)st->mesh->d.ncell * st->grid->d.nvp * 2;
+        if ((rc = aa_ensure(ctx, st->aa, st->storage, n, opts->accel_depth))) return rc;
+        if ((rc = aa_begin(ctx, st->aa, st->f[st->cur]))) return rc;
+    }
     int it = 0;
     double r = INFINITY, best = INFINITY, J = 0.0;
     int best_it = 0;
@@ -813,6 +979,16 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         if (r <= opts->tol) { status = DVM_OK; break; }
         if (r < 0.98 * best) { best = r; best_it = it; }
         if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
+        if (accel && k == K && it < opts->max_iter) {
+            bool mixed = false;
+            if ((rc = aa_step(ctx, st->aa, st->f[st->cur], &mixed))) return rc;
+            if (mixed) {
+                CK(launch_moments(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur],
+                                  st->Fw[st->cur], ctx->stream));
+                ctx->launches += 1;
+                st->version += 1;
+            }
+        }
     }
     if (opts->max_iter == 0) {
         if ((rc = dvm_state_functional(st, DVM_DRAG, &J))) return rc;
@@ -838,6 +1014,7 @@ void dvm_adjoint_destroy(dvm_adjoint* ad) {
     dfree(ad->respart); dfree(ad->out); dfree(ad->wallM); dfree(ad->cell);
     dfree(ad->GN); dfree(ad->GE); dfree(ad->GW); dfree(ad->node_grad); dfree(ad->vol); dfree(ad->elem);
     dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad);
+    aa_free(ad->st->ctx, ad->aa);
     ad->st->ctx->bytes -= ad->bytes;
     delete ad;
 }
@@ -992,6 +1169,7 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
                       dvm_adjoint** inout, dvm_adjoint_result* res) {
     if (!ctx || !st || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
     if (st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "state from another context");
+    if (int rc0 = check_solve_opts(opts)) return rc0;
     DeviceGuard dg(ctx->device);
     std::memset(res, 0, sizeof(*res));
     int rc;
@@ -1002,8 +1180,14 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
     }
     dvm_adjoint* ad = *inout;
     if ((rc = adjoint_follow_state(ad))) return rc;
-    const int K = ctx->graph_iters;
-    const bool use_graph = graphs_ok(ctx);
+    const bool accel = opts->accel_depth > 0;
+    const int K = accel ? opts->accel_period : ctx->graph_iters;
+    const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
+    if (accel) {
+        const size_t n = (size_t)st->mesh->d.ncell * st->grid->d.nvp * 2;
+        if ((rc = aa_ensure(ctx, ad->aa, st->storage, n, opts->accel_depth))) return rc;
+        if ((rc = aa_begin(ctx, ad->aa, ad->phi[ad->cur]))) return rc;
+    }
     int it = 0, best_it = 0;
     double r = INFINITY, best = INFINITY;
     int status = DVM_NOT_CONVERGED;
@@ -1024,6 +1208,11 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         if (r <= opts->tol) { status = DVM_OK; break; }
         if (r < 0.98 * best) { best = r; best_it = it; }
         if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
+        if (accel && k == K && it < opts->max_iter) {
+            bool mixed = false;
+            if ((rc = aa_step(ctx, ad->aa, ad->phi[ad->cur], &mixed))) return rc;
+            if (mixed) CK(refresh_adjoint_couplings(ad));
+        }
     }
     res->residual = r;
     res->r0 = ad->r0;
@@ -1235,6 +1424,8 @@ struct BatchReq {
     dvm_adjoint* ad = nullptr;
     int pit = 0, ait = 0;
     double res = NAN, ares = NAN, J = 0.0;
+    double best = INFINITY;     // best residual of the current phase, and the sweep it was reached at
+    int best_it = 0;
     int warm = 0;
     std::vector<double> grad;
     size_t footprint = 0;
@@ -1620,9 +1811,13 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
                 q->st->version += (uint64_t)M;
                 q->res = sqrt(r2) / q->st->r0;
                 q->J = J;
+                if (q->res < 0.98 * q->best) { q->best = q->res; q->best_it = q->pit; }
+                const bool stalled = q->r.stall_window > 0 && q->pit - q->best_it >= q->r.stall_window;
                 if (!std::isfinite(q->res) || !std::isfinite(J)) { q->pstatus = DVM_ERR_NONFINITE; leave = true; }
-                else if (q->res <= q->r.tol || q->pit >= q->r.max_iter) {
-                    q->pstatus = q->res <= q->r.tol ? DVM_OK : DVM_NOT_CONVERGED;
+                else if (q->res <= q->r.tol || q->pit >= q->r.max_iter || stalled) {
+                    q->pstatus = q->res <= q->r.tol ? DVM_OK : stalled ? DVM_ERR_STAGNATED : DVM_NOT_CONVERGED;
+                    q->best = INFINITY;
+                    q->best_it = 0;
                     if (q->r.n_params > 0) {
                         if ((rc = start_adjoint(b, q))) { q->astatus = rc; leave = true; }
                     } else {
@@ -1632,9 +1827,11 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
             } else {
                 q->ait += M;
                 q->ares = sqrt(r2) / q->ad->r0;
+                if (q->ares < 0.98 * q->best) { q->best = q->ares; q->best_it = q->ait; }
+                const bool stalled = q->r.stall_window > 0 && q->ait - q->best_it >= q->r.stall_window;
                 if (!std::isfinite(q->ares)) { q->astatus = DVM_ERR_NONFINITE; leave = true; }
-                else if (q->ares <= q->r.adjoint_tol || q->ait >= q->r.max_iter) {
-                    q->astatus = q->ares <= q->r.adjoint_tol ? DVM_OK : DVM_NOT_CONVERGED;
+                else if (q->ares <= q->r.adjoint_tol || q->ait >= q->r.max_iter || stalled) {
+                    q->astatus = q->ares <= q->r.adjoint_tol ? DVM_OK : stalled ? DVM_ERR_STAGNATED : DVM_NOT_CONVERGED;
                     q->grad.assign(q->r.n_params, 0.0);
                     rc = dvm_sensitivity(ctx, q->st, q->ad, q->r.n_params, q->r.dwall_dalpha, q->r.s_j, q->r.sens_mode,
                                          q->grad.data(), nullptr);

@@ -33,6 +33,7 @@ struct DevGrid {
     int nv = 0, nvp = 0;
     double4* vd = nullptr;      // [nvp]
     float4* vf = nullptr;       // [nvp]
+    float4* vp = nullptr;       // [nvp] per velocity pair p: (vx, vx', vy, vy'), (w, w', h, h')
 };
 
 // Per-flow tables for one state.
@@ -63,6 +64,7 @@ struct PrimalArgs {
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
     const TC* V;
     const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
+    const float4* vp;                       // paired velocity table (FP32 arithmetic)
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* fd;
     const TC* gw;
     const double* wallD;
@@ -93,6 +95,7 @@ struct AdjointArgs {
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
     const TC* V;
     const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
+    const float4* vp;                       // paired velocity table (FP32 arithmetic)
     const TC* gw;
     const double* wallD;
     const double* wallM;                    // for the functional's direction
@@ -175,6 +178,18 @@ cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, co
                              double* vol, double2* node_grad, cudaStream_t s);
 cudaError_t launch_contract(const double2* node_grad, int nrows, int ni, const double* s_j,
                             const double* dwall, int P, double* grad, cudaStream_t s);
+
+// Anderson mixing of the sweeps (flat storage vectors of n elements; history in FP32, FP64 for FP64
+// storage): load X <- F; collect r = G - X, the differences (ring slot `slot`) and the 2m dots into
+// out (device, [2m]); mix F, X <- G - dG gamma (neg set on a negative value); restore F, X <- G.
+int aa_max_depth();
+int aa_blocks();
+cudaError_t launch_aa_load(int storage, size_t n, const void* F, void* X, cudaStream_t s);
+cudaError_t launch_aa_collect(int storage, size_t n, const void* G, void* X, void* Rp, void* Gp, void* dR, void* dG,
+                              int m, int cnt, int slot, int first, double* part, double* out, cudaStream_t s);
+cudaError_t launch_aa_mix(int storage, size_t n, void* F, void* X, const void* Gp, const void* dG, int cnt,
+                          const double* gamma, int* neg, cudaStream_t s);
+cudaError_t launch_aa_restore(int storage, size_t n, void* F, void* X, const void* Gp, cudaStream_t s);
 
 // out[0] = Q, out[1 + p] = dQ/dalpha_p
 cudaError_t launch_volume(const DevMesh& m, double vmin, const double* dwall, int P, double* out, cudaStream_t s);

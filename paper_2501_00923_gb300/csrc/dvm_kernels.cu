@@ -13,6 +13,14 @@
 #include <cstring>
 #include <type_traits>
 
+// Tile parameters of the sweeps (see the pipeline section): chunks per lane per stage and stages.
+#ifndef DVM_CPL
+#define DVM_CPL 2
+#endif
+#ifndef DVM_STAGES
+#define DVM_STAGES 3
+#endif
+
 namespace dvm {
 namespace {
 
@@ -38,15 +46,17 @@ template <> struct Pack<double> {
         return r;
     }
 };
+// FP32 chunks hold (f1_k, f1_k+1, f2_k, f2_k+1): the two velocities of one component sit in one
+// register pair, the operand of the paired FP32 instructions (FFMA2 and friends).
 template <> struct Pack<float> {
     using TC = float;
     static constexpr int KV = 2;
     __device__ static void unpack(const uint4& r, float (&a)[2], float (&b)[2]) {
-        a[0] = __uint_as_float(r.x); b[0] = __uint_as_float(r.y);
-        a[1] = __uint_as_float(r.z); b[1] = __uint_as_float(r.w);
+        a[0] = __uint_as_float(r.x); a[1] = __uint_as_float(r.y);
+        b[0] = __uint_as_float(r.z); b[1] = __uint_as_float(r.w);
     }
     __device__ static uint4 pack(const float (&a)[2], const float (&b)[2]) {
-        return make_uint4(__float_as_uint(a[0]), __float_as_uint(b[0]), __float_as_uint(a[1]),
+        return make_uint4(__float_as_uint(a[0]), __float_as_uint(a[1]), __float_as_uint(b[0]),
                           __float_as_uint(b[1]));
     }
 };
@@ -73,6 +83,13 @@ template <> struct Pack<__nv_bfloat16> {
         return make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
 };
+
+// Element index of f1 of velocity k of cell c; f2 follows at + kComp<TS>.
+template <class TS> constexpr int kComp = std::is_same<TS, float>::value ? 2 : 1;
+template <class TS> __device__ __forceinline__ size_t fpos(size_t c, int nvp, int k) {
+    if (std::is_same<TS, float>::value) return (c * nvp + (k & ~1)) * 2 + (k & 1);
+    return (c * nvp + k) * 2;
+}
 
 // ------------------------------------------------------------------ accumulators
 template <class T> struct Acc;
@@ -173,7 +190,7 @@ template <> struct Sum<float> {      // Kahan-compensated lane sum, double-float
 // or both (a one-layer mesh).  Each class gets its own compiled loop so that interior cells, which
 // are all but 2/nj of the mesh, carry no boundary logic.
 enum { kInterior = 0, kWallCell = 1, kFarCell = 2, kWallFar = 3 };
-constexpr int kBlockIters = 8;   // chunk rows summed in FP32 before one compensated add
+constexpr int kBlockIters = 8 / DVM_CPL;   // stages summed in FP32 before one compensated add
 
 // ------------------------------------------------------------------ tiled-TMA pipeline
 // A block owns 8 radially adjacent cells (i, j0..j0+7), one warp per cell.  The distribution is a
@@ -181,15 +198,21 @@ constexpr int kBlockIters = 8;   // chunk rows summed in FP32 before one compens
 // its column with one halo row on each side (rows j0-1..j0+8) and the columns i-1 and i+1 (rows
 // j0..j0+7).  Three tiled TMA loads (cp.async.bulk.tensor) bring them into one pipeline stage:
 // periodicity in i is a coordinate, rows outside [0, nj) are zero-filled and never used.  Thread 0
-// of warp 0 produces kStages chunk rows ahead; every warp waits on the stage's "full" mbarrier,
-// computes, and arrives on its "empty" mbarrier; the producer refills a stage once all warps have
-// released it.  Every wait is bounded (kWaitTries tries of about kSuspendNs each): a wait that
-// runs out sets *err, the block stops, and the producer drains the copies it issued.
-constexpr int kStages = 4;
+// issues the first kStages chunk rows; every warp waits on the stage's "full" mbarrier, computes
+// and releases the stage, and the last warp to release it issues its next chunk row.  Every wait
+// is bounded (kWaitNs by the global timer): a wait that runs out sets *err, the block stops, and
+// each warp drains the copies it issued.
+// Tile parameters: kCPL 16-byte chunks per lane per stage (a stage row is 32 kCPL chunks, one TMA
+// box of 128 kCPL 32-bit elements, at most 256) and kStages stages per block.
+constexpr int kCPL = DVM_CPL;
+constexpr int kRowChunks = 32 * kCPL;
+constexpr int kStages = DVM_STAGES;
+static_assert(kCPL >= 1 && kCPL <= 2, "a TMA box row holds at most 256 elements");
 constexpr int kPrimalRows = 26;      // column 10 rows + west 8 + east 8
 constexpr int kAdjointRows = 34;     // phi column 10 + phi west 8 + phi east 8 + f 8
-constexpr unsigned kSuspendNs = 1000000;
-constexpr unsigned kWaitTries = 1000;
+constexpr unsigned kSuspendNs = 1000000;                  // suspend-time hint of one try
+constexpr unsigned long long kWaitNs = 2000000000ull;     // a wait gives up after 2 s ...
+constexpr unsigned kWaitTries = 100000000u;               // ... or this many tries
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -213,9 +236,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// The suspend hint is an upper bound only (a try may return much sooner), so the limit is kept in
+// time: kWaitNs of %globaltimer, with a cap on the tries as a backstop.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    for (unsigned t = 0; t < kWaitTries; ++t)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned t = 0; t < kWaitTries; ++t) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
@@ -226,24 +260,32 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// Producer side of a block's pipeline.
+// Acquire-release increment of a shared-memory counter (block scope); returns the old value.
+__device__ __forceinline__ unsigned atom_inc_acq_rel(unsigned* p) {
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(smem_u32(p)) : "memory");
+    return old;
+}
+
+// A block's pipeline: stages, their "full" mbarriers and release counters.
 struct Feed {
     const CUtensorMap* col;      // box 32 chunks x 1 cell x 10 rows (the value being swept)
     const CUtensorMap* side;     // box 32 chunks x 1 cell x 8 rows (the same buffer)
     const CUtensorMap* extra;    // box 32 chunks x 1 cell x 8 rows of a second buffer (adjoint: f), or null
     int i, im, ip, j0, rows;     // block column, its periodic neighbours, first row, rows per stage
+    unsigned A;                  // warps that consume each stage
     uint4* stage;                // kStages x rows x 32 chunks
     uint64_t* full;
-    uint64_t* empty;
+    unsigned* released;          // per stage, warps that have released it so far (monotone)
     __device__ __forceinline__ void issue(unsigned it) const {
         const unsigned st = it % kStages;
-        uint4* d = stage + (size_t)st * rows * 32;
-        const int x = (int)(it * 32u * 4u);                   // uint32 elements: 16-byte aligned
-        mbar_expect_tx(&full[st], (unsigned)rows * 512u);
+        uint4* d = stage + (size_t)st * rows * kRowChunks;
+        const int x = (int)(it * kRowChunks * 4u);           // uint32 elements: 16-byte aligned
+        mbar_expect_tx(&full[st], (unsigned)rows * kRowChunks * 16u);
         tma_load_3d(d, col, x, i, j0 - 1, &full[st]);
-        tma_load_3d(d + 10 * 32, side, x, im, j0, &full[st]);
-        tma_load_3d(d + 18 * 32, side, x, ip, j0, &full[st]);
-        if (extra) tma_load_3d(d + 26 * 32, extra, x, i, j0, &full[st]);
+        tma_load_3d(d + 10 * kRowChunks, side, x, im, j0, &full[st]);
+        tma_load_3d(d + 18 * kRowChunks, side, x, ip, j0, &full[st]);
+        if (extra) tma_load_3d(d + 26 * kRowChunks, extra, x, i, j0, &full[st]);
     }
 };
 
@@ -275,27 +317,62 @@ template <> struct Gauss<double> {
     __device__ __forceinline__ double eval(double t) const { return exp(fma(t, kA, kB)); }
 };
 
-// One pipeline step shared by both sweeps: wait for stage `it`, run `body` on it, release it, and
-// (producer) refill it with chunk row it + kStages.  Returns false when a wait ran out.
+// ------------------------------------------------------------------ paired FP32 arithmetic
+// Two velocities at a time with the paired FP32 instructions of sm_100+ (round-to-nearest, one
+// rounding per lane as in the scalar forms).  Broadcast operands are pairs of equal values.
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 inflow(float2 a) { return make_float2(fmaxf(-a.x, 0.f), fmaxf(-a.y, 0.f)); }
+__device__ __forceinline__ float2 pex2(float2 a) { return make_float2(ex2_approx(a.x), ex2_approx(a.y)); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float2 prcp(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+template <int KV> __device__ __forceinline__ float2 pair_of(const float (&a)[KV], int p) {
+    return make_float2(a[2 * p], a[2 * p + 1]);
+}
+
+// One pipeline step shared by both sweeps: wait for stage `it`, run `body` on it and release it.
+// The warp whose release is the last one for this round of the stage refills it with chunk row
+// it + kStages, so no warp ever waits for a stage to drain.  The acquire-release counter orders
+// every warp's reads of the stage before that warp's copy into it (then the proxy fence orders
+// them before the asynchronous write).  Returns false when a wait ran out.
 template <class Body>
-__device__ __forceinline__ bool pipeline_step(const Feed& F, unsigned it, unsigned niter, int lane, bool producer,
-                                              Body&& body) {
+__device__ __forceinline__ bool pipeline_step(const Feed& F, unsigned it, unsigned niter, int lane, Body&& body) {
     const unsigned st = it % kStages, ph = (it / kStages) & 1u;
     const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&F.full[st], ph));
     if (!got) return false;
-    body(F.stage + (size_t)st * F.rows * 32);
+    body(F.stage + (size_t)st * F.rows * kRowChunks);
     __syncwarp();
-    if (lane == 0) mbar_arrive(&F.empty[st]);
-    bool pok = true;
-    if (producer && it + kStages < niter) {
-        pok = mbar_wait_bounded(&F.empty[st], ph);
-        if (pok) {
+    if (lane == 0) {
+        // after round r of stage st its counter reaches (r + 1) A; the warp that brings it there is last
+        const unsigned old = atom_inc_acq_rel(&F.released[st]);
+        if (old + 1 == (it / kStages + 1) * F.A && it + kStages < niter) {
             fence_proxy_async();
             F.issue(it + kStages);
         }
     }
-    return __shfl_sync(0xffffffffu, pok ? 1 : 0, 0) != 0;
+    return true;
 }
+
+// Resident blocks per SM (the register budget) of the FP32/BF16 sweeps; FP64 keeps 4 (primal) and
+// 3 (adjoint).  DVM_PAIRED selects the paired FP32 arithmetic for FP32/BF16 storage.
+#ifndef DVM_PRIMAL_BLOCKS
+#define DVM_PRIMAL_BLOCKS (DVM_CPL == 1 ? 3 : 2)
+#endif
+#ifndef DVM_ADJOINT_BLOCKS
+#define DVM_ADJOINT_BLOCKS (DVM_CPL == 1 ? 3 : 2)
+#endif
+#ifndef DVM_PAIRED
+#define DVM_PAIRED 1
+#endif
+template <class TS> constexpr bool kPaired = DVM_PAIRED && std::is_same<typename Pack<TS>::TC, float>::value;
+template <class TS> constexpr int kPrimalMinBlocks = std::is_same<typename Pack<TS>::TC, float>::value ? DVM_PRIMAL_BLOCKS : 4;
+template <class TS> constexpr int kAdjointMinBlocks = std::is_same<typename Pack<TS>::TC, float>::value ? DVM_ADJOINT_BLOCKS : 3;
 
 // ================================================================== primal sweep (K1)
 // One point-implicit sweep of Eq. (numerpr_gov), first-order upwind, fused with the moments of
@@ -305,9 +382,141 @@ __device__ __forceinline__ bool pipeline_step(const Feed& F, unsigned it, unsign
 // (sum_e A_e n_e = 0); the inflow faces add -min(a_e, 0) F_up to the right-hand side.  The staged
 // neighbour chunks are used whether or not a face is an inflow face (the factor min(a_e, 0) is 0),
 // which keeps the loop free of per-velocity branches.
+// FP32 / BF16 form of the sweep: the same update two velocities at a time.  D uses the inflow
+// weights n_e = max(-a_e, 0): sum_e max(a_e, 0) = sum_e n_e on a closed cell.
+template <class TS, bool kRes, int kBnd>
+__device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& P, int c, int w, int lane,
+                                                   const Feed& F) {
+    using PK = Pack<TS>;
+    constexpr int KV = PK::KV, NP = KV / 2;
+    constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
+    const float2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
+    const double4 pr = P.prim_old[c];
+    const float rho = (float)pr.x, u1 = (float)pr.y, u2 = (float)pr.z, T = (float)pr.w;
+    Gauss<float> G;
+    G.setup(rho, u1, u2, T);
+    const float Vt = P.V[c] * rho * sqrtf(T) * (float)P.inv_tau_inf;      // V / tau
+    const float2 kA = bc(G.kA), kB = bc(G.kB), mu1 = bc(-u1), mu2 = bc(-u2), Vt2 = bc(Vt), hT = bc(0.5f * T);
+    const float2 s0x = bc(S0.x), s0y = bc(S0.y), s1x = bc(S1.x), s1y = bc(S1.y);
+    const float2 s2x = bc(S2.x), s2y = bc(S2.y), s3x = bc(S3.x), s3y = bc(S3.y);
+    float2 cw1 = bc(0.f), cw2 = bc(0.f), dxy = bc(0.f), dyy = bc(0.f);
+    float invA = 0.f;
+    if (wall) {
+        const float c1 = (float)P.Fw_old[c] / (float)P.wallD[c];
+        cw1 = bc(c1);
+        cw2 = bc(c1 * P.halfTw);
+        dxy = bc(P.dirx);
+        dyy = bc(P.diry);
+        invA = 1.f / sqrtf(S3.x * S3.x + S3.y * S3.y);
+    }
+    uint4* fw = reinterpret_cast<uint4*>(P.f_new);
+    const unsigned nq = (unsigned)P.nq, niter = (nq + kRowChunks - 1) / kRowChunks, oc = (unsigned)c * nq;
+
+    Sum<float> m0, m1, m2, m3, fwa, ja, rs;
+    bool ok = true;
+    unsigned it = 0;
+    while (it < niter && ok) {
+        float2 bm0 = bc(0.f), bm1 = bm0, bm2 = bm0, bm3 = bm0, bfw = bm0, bj = bm0, brs = bm0;
+        for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
+            ok = pipeline_step(F, it, niter, lane, [&](const uint4* d) {
+#pragma unroll
+              for (int cc = 0; cc < kCPL; ++cc) {
+                const unsigned q = it * kRowChunks + cc * 32 + lane;
+                if (q >= nq) break;
+                const uint4* e = d + cc * 32 + lane;
+                const uint4 ro = e[(w + 1) * kRowChunks];
+                const uint4 r0 = e[(10 + w) * kRowChunks], r2 = e[(18 + w) * kRowChunks];
+                const uint4 r1 = far ? ro : e[(w + 2) * kRowChunks];
+                const uint4 r3 = wall ? ro : e[w * kRowChunks];
+                float fo1[KV], fo2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV], e32[KV];
+                PK::unpack(ro, fo1, fo2);
+                PK::unpack(r0, e01, e02);
+                PK::unpack(r1, e11, e12);
+                PK::unpack(r2, e21, e22);
+                PK::unpack(r3, e31, e32);
+                float fn1[KV], fn2[KV];
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+                    const int kp = q * NP + pp;                  // velocity pair 2kp, 2kp+1
+                    const float4 A = P.vp[2 * kp], B = P.vp[2 * kp + 1];
+                    const float2 vx = make_float2(A.x, A.y), vy = make_float2(A.z, A.w);
+                    const float2 wk = make_float2(B.x, B.y), hv = make_float2(B.z, B.w);
+                    const float2 a0 = pfma(s0y, vy, pmul(s0x, vx)), a1 = pfma(s1y, vy, pmul(s1x, vx));
+                    const float2 a2 = pfma(s2y, vy, pmul(s2x, vx)), a3 = pfma(s3y, vy, pmul(s3x, vx));
+                    const float2 n0 = inflow(a0), n1 = inflow(a1), n2 = inflow(a2), n3 = inflow(a3);
+                    float2 f11 = pair_of<KV>(e11, pp), f12 = pair_of<KV>(e12, pp);
+                    float2 f31 = pair_of<KV>(e31, pp), f32 = pair_of<KV>(e32, pp);
+                    if (far) {
+                        const float4 g = *reinterpret_cast<const float4*>(P.fd + 2 * kp);   // (g1,g2) x 2
+                        f11 = make_float2(g.x, g.z);
+                        f12 = make_float2(g.y, g.w);
+                    }
+                    if (wall) {
+                        const float2 gw = *reinterpret_cast<const float2*>(P.gw + 2 * kp);
+                        f31 = pmul(cw1, gw);
+                        f32 = pmul(cw2, gw);
+                    }
+                    const float2 D = padd(Vt2, padd(padd(n0, n1), padd(n2, n3)));
+                    const float2 g1 = pex2(pfma(pfma(vy, mu2, pfma(vx, mu1, hv)), kA, kB));
+                    float2 r1 = pmul(Vt2, g1);
+                    float2 r2 = pmul(hT, r1);
+                    r1 = pfma(n0, pair_of<KV>(e01, pp), r1); r2 = pfma(n0, pair_of<KV>(e02, pp), r2);
+                    r1 = pfma(n1, f11, r1);                  r2 = pfma(n1, f12, r2);
+                    r1 = pfma(n2, pair_of<KV>(e21, pp), r1); r2 = pfma(n2, pair_of<KV>(e22, pp), r2);
+                    r1 = pfma(n3, f31, r1);                  r2 = pfma(n3, f32, r2);
+                    const float2 iD = prcp(D);
+                    const float2 x1 = pmul(r1, iD), x2 = pmul(r2, iD);
+                    fn1[2 * pp] = x1.x; fn1[2 * pp + 1] = x1.y;
+                    fn2[2 * pp] = x2.x; fn2[2 * pp + 1] = x2.y;
+                    if (kRes) {
+                        const float2 R1 = pmul(D, pfma(x1, bc(-1.f), pair_of<KV>(fo1, pp)));
+                        const float2 R2 = pmul(D, pfma(x2, bc(-1.f), pair_of<KV>(fo2, pp)));
+                        brs = pfma(wk, pfma(R2, R2, pmul(R1, R1)), brs);
+                    }
+                    const float2 wf1 = pmul(wk, x1);
+                    bm0 = padd(bm0, wf1);
+                    bm1 = pfma(wf1, vx, bm1);
+                    bm2 = pfma(wf1, vy, bm2);
+                    bm3 = pfma(wk, x2, pfma(wf1, hv, bm3));
+                    if (wall) {
+                        const float2 wp = pmul(wf1, padd(a3, n3));      // w f1 max(a3, 0)
+                        bfw = padd(bfw, wp);
+                        bj = pfma(wp, pfma(dyy, vy, pmul(dxy, vx)), bj);
+                    }
+                }
+                stg16(fw + oc + q, PK::pack(fn1, fn2));
+              }
+            });
+        }
+        m0.add(bm0.x + bm0.y); m1.add(bm1.x + bm1.y); m2.add(bm2.x + bm2.y); m3.add(bm3.x + bm3.y);
+        if (kRes) rs.add(brs.x + brs.y);
+        if (wall) { fwa.add(bfw.x + bfw.y); ja.add(bj.x + bj.y); }
+    }
+    if (!ok) return false;
+    const float M0 = m0.total(), M1 = m1.total(), M2 = m2.total(), M3 = m3.total();
+    float RS = 0.f, FW = 0.f, JA = 0.f;
+    if (kRes) RS = rs.total();
+    if (wall) { FW = fwa.total(); JA = ja.total(); }
+    if (lane == 0) {
+        const float ir = 1.f / M0;
+        const float nu1 = M1 * ir, nu2 = M2 * ir;
+        const float nT = (2.f / 3.f) * (M3 * ir - 0.5f * (nu1 * nu1 + nu2 * nu2));
+        P.prim_new[c] = make_double4(M0, nu1, nu2, nT);
+        if (kRes) {
+            const float V = P.V[c];
+            P.respart[c] = (double)(RS / (V * V));
+        }
+        if (wall) {
+            P.Fw_new[c] = (double)(FW * invA);
+            P.Jpart[c] = (double)JA;
+        }
+    }
+    return true;
+}
+
 template <class TS, bool kRes, int kBnd>
 __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
-                                            int lane, const Feed& F, bool producer) {
+                                            int lane, const Feed& F) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -328,7 +537,7 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
         invA = TC(1) / sqrt(S3.x * S3.x + S3.y * S3.y);
     }
     uint4* fw = reinterpret_cast<uint4*>(P.f_new);
-    const unsigned nq = (unsigned)P.nq, niter = (nq + 31) / 32, oc = (unsigned)c * nq;
+    const unsigned nq = (unsigned)P.nq, niter = (nq + kRowChunks - 1) / kRowChunks, oc = (unsigned)c * nq;
 
     Sum<TC> m0, m1, m2, m3, fwa, ja, rs;
     bool ok = true;
@@ -336,13 +545,16 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
     while (it < niter && ok) {
         TC bm0 = TC(0), bm1 = TC(0), bm2 = TC(0), bm3 = TC(0), bfw = TC(0), bj = TC(0), brs = TC(0);
         for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
-            ok = pipeline_step(F, it, niter, lane, producer, [&](const uint4* d) {
-                const unsigned q = it * 32 + lane;
-                if (q >= nq) return;
-                const uint4 ro = d[(w + 1) * 32 + lane];
-                const uint4 r0 = d[(10 + w) * 32 + lane], r2 = d[(18 + w) * 32 + lane];
-                const uint4 r1 = far ? ro : d[(w + 2) * 32 + lane];
-                const uint4 r3 = wall ? ro : d[w * 32 + lane];
+            ok = pipeline_step(F, it, niter, lane, [&](const uint4* d) {
+#pragma unroll
+              for (int cc = 0; cc < kCPL; ++cc) {
+                const unsigned q = it * kRowChunks + cc * 32 + lane;
+                if (q >= nq) break;
+                const uint4* e = d + cc * 32 + lane;
+                const uint4 ro = e[(w + 1) * kRowChunks];
+                const uint4 r0 = e[(10 + w) * kRowChunks], r2 = e[(18 + w) * kRowChunks];
+                const uint4 r1 = far ? ro : e[(w + 2) * kRowChunks];
+                const uint4 r3 = wall ? ro : e[w * kRowChunks];
                 TC fo1[KV], fo2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV], e31[KV], e32[KV];
                 PK::unpack(ro, fo1, fo2);
                 PK::unpack(r0, e01, e02);
@@ -387,6 +599,7 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
                     }
                 }
                 stg16(fw + oc + q, PK::pack(fn1, fn2));
+              }
             });
         }
         m0.add(bm0); m1.add(bm1); m2.add(bm2); m3.add(bm3);
@@ -415,10 +628,10 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
     return true;
 }
 
-constexpr int primal_smem_bytes() { return kStages * kPrimalRows * 512 + 2 * kStages * 8; }
-constexpr int adjoint_smem_bytes() { return kStages * kAdjointRows * 512 + 2 * kStages * 8; }
+constexpr int primal_smem_bytes() { return kStages * kPrimalRows * kRowChunks * 16 + 2 * kStages * 8; }
+constexpr int adjoint_smem_bytes() { return kStages * kAdjointRows * kRowChunks * 16 + 2 * kStages * 8; }
 
-// Block prologue/epilogue shared by both sweeps: barriers, active warps, the producer's first
+// Block prologue/epilogue shared by both sweeps: barriers, active warps, the first
 // stages and, on exit, the drain of copies still in flight.
 struct BlockPipe {
     Feed F;
@@ -430,16 +643,17 @@ __device__ __forceinline__ bool block_pipe_setup(BlockPipe& B, unsigned char* sm
                                                  unsigned nq, const CUtensorMap* col, const CUtensorMap* side,
                                                  const CUtensorMap* extra, int i, int j0) {
     B.A = min(kWarpsPerBlock, nj - j0);
-    B.niter = (nq + 31) / 32;
+    B.niter = (nq + kRowChunks - 1) / kRowChunks;
     B.F.col = col; B.F.side = side; B.F.extra = extra;
     B.F.i = i; B.F.im = (i - 1 + ni) % ni; B.F.ip = (i + 1) % ni; B.F.j0 = j0; B.F.rows = rows;
+    B.F.A = (unsigned)B.A;
     B.F.stage = reinterpret_cast<uint4*>(smem);
     B.F.full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * rows * 512);
-    B.F.empty = B.F.full + kStages;
+    B.F.released = reinterpret_cast<unsigned*>(B.F.full + kStages);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&B.F.full[s], 1);
-            mbar_init(&B.F.empty[s], (unsigned)B.A);
+            B.F.released[s] = 0u;
         }
         fence_mbar_init();
         for (unsigned it = 0; it < min((unsigned)kStages, B.niter); ++it) B.F.issue(it);
@@ -448,7 +662,7 @@ __device__ __forceinline__ bool block_pipe_setup(BlockPipe& B, unsigned char* sm
     return (int)(threadIdx.x >> 5) < B.A;
 }
 
-// Producer drain after an aborted sweep: wait (bounded) for every stage it may still have in flight.
+// Drain after an aborted sweep: every warp waits (bounded) for the copies it may have issued.
 __device__ __forceinline__ void block_pipe_drain(const BlockPipe& B) {
     for (int s = 0; s < kStages; ++s)
         for (unsigned ph = 0; ph < 2; ++ph) mbar_try_wait(&B.F.full[s], ph);
@@ -461,23 +675,32 @@ __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<
     if (!block_pipe_setup(B, smem, kPrimalRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, nullptr, i, j0)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = j0 + w, c = j * P.ni + i;
-    const bool producer = (threadIdx.x == 0);
     const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
     bool ok;
-    switch (bnd) {
-        case kInterior: ok = primal_cell<TS, kRes, kInterior>(P, c, w, lane, B.F, producer); break;
-        case kWallCell: ok = primal_cell<TS, kRes, kWallCell>(P, c, w, lane, B.F, producer); break;
-        case kFarCell: ok = primal_cell<TS, kRes, kFarCell>(P, c, w, lane, B.F, producer); break;
-        default: ok = primal_cell<TS, kRes, kWallFar>(P, c, w, lane, B.F, producer); break;
+    if constexpr (kPaired<TS>) {
+        switch (bnd) {
+            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell_paired<TS, kRes, kWallFar>(P, c, w, lane, B.F); break;
+        }
+    } else {
+        switch (bnd) {
+            case kInterior: ok = primal_cell<TS, kRes, kInterior>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell<TS, kRes, kWallCell>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell<TS, kRes, kFarCell>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell<TS, kRes, kWallFar>(P, c, w, lane, B.F); break;
+        }
     }
-    if (!ok) {
-        if (lane == 0) atomicExch(P.err, 1);
-        if (producer) block_pipe_drain(B);
+    if (!ok && lane == 0) {
+        atomicExch(P.err, 1);
+        block_pipe_drain(B);
     }
 }
 
+
 template <class TS, bool kRes>
-__global__ void __launch_bounds__(256, 4) k_primal_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
+__global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
                                                          const __grid_constant__ CUtensorMap m10,
                                                          const __grid_constant__ CUtensorMap m8) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -493,7 +716,7 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 // table; every request advances one sweep.  parity selects, per request, the buffer pair of this
 // sweep (descriptor slot 0 reads the buffer current at the start of the tick).
 template <class TS, bool kRes>
-__global__ void __launch_bounds__(256, 4) k_primal_sweep_batch(const PrimalBatchDesc<TS>* __restrict__ descs,
+__global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep_batch(const PrimalBatchDesc<TS>* __restrict__ descs,
                                                                const int4* __restrict__ items, int parity) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int4 it = items[blockIdx.x];
@@ -515,9 +738,156 @@ __global__ void __launch_bounds__(256, 4) k_primal_sweep_batch(const PrimalBatch
 // The per-cell constants of the linearisation (Maxwellian parameters, V/tau, J_P, d(1/tau)/dp)
 // come precomputed in AdjCell.  kUpdate = false: phi is not advanced; the couplings of phi_old are
 // written to the *_new slots (used after an upload of phi or a change of the primal state).
+// FP32 / BF16 form of the adjoint sweep, two velocities at a time.  D uses the outflow weights
+// max(a_e, 0) directly; the Maxwellian is accumulated as exp(-c^2/2T) = 2^(c^2 kE) and its factor
+// n0 applied to the block sums (every coupling is linear in g1).
+template <class TS, bool kUpdate, bool kRes, int kBnd>
+__device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>& P, int c, int w, int lane,
+                                                    const Feed& F) {
+    using PK = Pack<TS>;
+    constexpr int KV = PK::KV, NP = KV / 2;
+    constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
+    constexpr float L2E = 1.44269504088896341f;
+    const float2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
+    const AdjCell<float>* ccp = P.cell + c;
+    const float u1 = __ldg(&ccp->u1), u2 = __ldg(&ccp->u2), n0 = __ldg(&ccp->n0), inv2T = __ldg(&ccp->inv2T);
+    const float halfT = __ldg(&ccp->halfT), Vt = __ldg(&ccp->Vt);
+    const double4 Z = P.Z_old[c];
+    const float2 z0 = bc((float)Z.x), z1 = bc((float)Z.y), z2 = bc((float)Z.z), z3 = bc((float)Z.w);
+    const float2 mu1 = bc(-u1), mu2 = bc(-u2), hT = bc(halfT), Vt2 = bc(Vt);
+    const float2 kE = bc(-inv2T * L2E);
+    const float2 s0x = bc(S0.x), s0y = bc(S0.y), s1x = bc(S1.x), s1y = bc(S1.y);
+    const float2 s2x = bc(S2.x), s2y = bc(S2.y), s3x = bc(S3.x), s3y = bc(S3.y);
+    float2 ndx = bc(0.f), ndy = bc(0.f), nsrc = bc(0.f), gbw = bc(0.f), hTw = bc(0.f);
+    if (wall) {
+        const float A = sqrtf(S3.x * S3.x + S3.y * S3.y);
+        ndx = bc(-P.dirx);
+        ndy = bc(-P.diry);
+        nsrc = bc(-(float)(P.wallM[c] + P.Lam_old[c]) / A);          // (M + Lambda)/A multiplies a3
+        gbw = bc(1.f / (float)P.wallD[c]);
+        hTw = bc(P.halfTw);
+    }
+    uint4* pw = reinterpret_cast<uint4*>(P.phi_new);
+    const unsigned nq = (unsigned)P.nq, niter = (nq + kRowChunks - 1) / kRowChunks, oc = (unsigned)c * nq;
+
+    Sum<float> sh, shx, shy, shc, sg2, sr, lam, rs;
+    bool ok = true;
+    unsigned it = 0;
+    while (it < niter && ok) {
+        float2 bh = bc(0.f), bhx = bh, bhy = bh, bhc = bh, bg2 = bh, bwf = bh, bl = bh, brs = bh;
+        for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
+            ok = pipeline_step(F, it, niter, lane, [&](const uint4* d) {
+#pragma unroll
+              for (int cc = 0; cc < kCPL; ++cc) {
+                const unsigned q = it * kRowChunks + cc * 32 + lane;
+                if (q >= nq) break;
+                const uint4* e = d + cc * 32 + lane;
+                const uint4 ro = e[(w + 1) * kRowChunks], rf = e[(26 + w) * kRowChunks];
+                uint4 r0 = ro, r1 = ro, r2 = ro, r3 = ro;
+                if (kUpdate) {
+                    r0 = e[(10 + w) * kRowChunks];
+                    r2 = e[(18 + w) * kRowChunks];
+                    if (!far) r1 = e[(w + 2) * kRowChunks];
+                    if (!wall) r3 = e[w * kRowChunks];
+                }
+                float po1[KV], po2[KV], f1[KV], f2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV],
+                    e31[KV], e32[KV];
+                PK::unpack(ro, po1, po2);
+                PK::unpack(rf, f1, f2);
+                PK::unpack(r0, e01, e02);
+                PK::unpack(r1, e11, e12);
+                PK::unpack(r2, e21, e22);
+                PK::unpack(r3, e31, e32);
+                float pn1[KV], pn2[KV];
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+                    const int kp = q * NP + pp;
+                    const float4 A = P.vp[2 * kp], B = P.vp[2 * kp + 1];
+                    const float2 vx = make_float2(A.x, A.y), vy = make_float2(A.z, A.w);
+                    const float2 wk = make_float2(B.x, B.y), hv = make_float2(B.z, B.w);
+                    const float2 a3 = pfma(s3y, vy, pmul(s3x, vx));
+                    float2 x1 = pair_of<KV>(po1, pp), x2 = pair_of<KV>(po2, pp);
+                    if (kUpdate) {
+                        const float2 a0 = pfma(s0y, vy, pmul(s0x, vx)), a1 = pfma(s1y, vy, pmul(s1x, vx));
+                        const float2 a2 = pfma(s2y, vy, pmul(s2x, vx));
+                        const float2 o0 = inflow(make_float2(-a0.x, -a0.y)), o1 = inflow(make_float2(-a1.x, -a1.y));
+                        const float2 o2 = inflow(make_float2(-a2.x, -a2.y)), o3 = inflow(make_float2(-a3.x, -a3.y));
+                        const float2 D = padd(Vt2, padd(padd(o0, o1), padd(o2, o3)));
+                        float2 r1 = pfma(z3, hv, pfma(z2, vy, pfma(z1, vx, z0)));
+                        float2 r2 = z3;
+                        r1 = pfma(o0, pair_of<KV>(e01, pp), r1); r2 = pfma(o0, pair_of<KV>(e02, pp), r2);
+                        r1 = pfma(o2, pair_of<KV>(e21, pp), r1); r2 = pfma(o2, pair_of<KV>(e22, pp), r2);
+                        if (!far) { r1 = pfma(o1, pair_of<KV>(e11, pp), r1); r2 = pfma(o1, pair_of<KV>(e12, pp), r2); }
+                        if (wall) r1 = pfma(o3, pfma(ndy, vy, pfma(ndx, vx, nsrc)), r1);
+                        else { r1 = pfma(o3, pair_of<KV>(e31, pp), r1); r2 = pfma(o3, pair_of<KV>(e32, pp), r2); }
+                        const float2 iD = prcp(D);
+                        const float2 y1 = pmul(r1, iD), y2 = pmul(r2, iD);
+                        if (kRes) {
+                            const float2 R1 = pmul(D, pfma(y1, bc(-1.f), x1));
+                            const float2 R2 = pmul(D, pfma(y2, bc(-1.f), x2));
+                            brs = pfma(wk, pfma(R2, R2, pmul(R1, R1)), brs);
+                        }
+                        x1 = y1;
+                        x2 = y2;
+                    }
+                    pn1[2 * pp] = x1.x; pn1[2 * pp + 1] = x1.y;
+                    pn2[2 * pp] = x2.x; pn2[2 * pp + 1] = x2.y;
+                    // couplings of the next sweep, from the new phi
+                    const float2 dx = padd(vx, mu1), dy = padd(vy, mu2);
+                    const float2 c2 = pfma(dy, dy, pmul(dx, dx));
+                    const float2 wg1 = pmul(wk, pex2(pmul(c2, kE)));          // g1 / n0
+                    const float2 h = pmul(wg1, pfma(hT, x2, x1));
+                    bh = padd(bh, h);
+                    bhx = pfma(h, dx, bhx);
+                    bhy = pfma(h, dy, bhy);
+                    bhc = pfma(h, c2, bhc);
+                    bg2 = pfma(wg1, x2, bg2);
+                    bwf = pfma(wk, pfma(x2, pair_of<KV>(f2, pp), pmul(x1, pair_of<KV>(f1, pp))), bwf);
+                    if (wall) {
+                        const float2 gw = *reinterpret_cast<const float2*>(P.gw + 2 * kp);
+                        const float2 in3 = inflow(a3);                       // -min(a3, 0)
+                        bl = pfma(pmul(pmul(wk, in3), pmul(gw, gbw)), pfma(hTw, x2, x1), bl);
+                    }
+                }
+                if (kUpdate) stg16(pw + oc + q, PK::pack(pn1, pn2));
+              }
+            });
+        }
+        const float bhs = n0 * (bh.x + bh.y);
+        sh.add(bhs); shx.add(n0 * (bhx.x + bhx.y)); shy.add(n0 * (bhy.x + bhy.y)); shc.add(n0 * (bhc.x + bhc.y));
+        sg2.add(n0 * (bg2.x + bg2.y)); sr.add((bwf.x + bwf.y) - bhs);
+        if (kRes) rs.add(brs.x + brs.y);
+        if (wall) lam.add(-(bl.x + bl.y));
+    }
+    if (!ok) return false;
+    const float Sh = sh.total(), Shx = shx.total(), Shy = shy.total(), Shc = shc.total();
+    const float Sg2 = sg2.total(), Sr = sr.total();
+    float RS = 0.f, LAM = 0.f;
+    if (kRes) RS = rs.total();
+    if (wall) LAM = lam.total();
+    if (lane == 0) {
+        const AdjCell<float> cc = *ccp;
+        const float ph0 = Sh * cc.ir, ph1 = Shx * cc.iT, ph2 = Shy * cc.iT;
+        const float ph3 = Shc * cc.iT2h - Sh * cc.iT + 0.5f * Sg2;
+        const float p0 = Vt * ph0 - Sr * cc.c0, p1 = Vt * ph1, p2 = Vt * ph2, p3 = Vt * ph3 - Sr * cc.c3;
+        double4 zn;
+        zn.x = (double)(p0 - (p1 * u1 + p2 * u2) * cc.ir + p3 * cc.j30);
+        zn.y = (double)(p1 * cc.ir + p3 * cc.j31);
+        zn.z = (double)(p2 * cc.ir + p3 * cc.j32);
+        zn.w = (double)(p3 * cc.j33);
+        P.Z_new[c] = zn;
+        if (kRes) {
+            const float V = P.V[c];
+            P.respart[c] = (double)(RS / (V * V));
+        }
+        if (wall) P.Lam_new[c] = (double)LAM;
+    }
+    return true;
+}
+
 template <class TS, bool kUpdate, bool kRes, int kBnd>
 __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
-                                             int lane, const Feed& F, bool producer) {
+                                             int lane, const Feed& F) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -537,7 +907,7 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
         srcB = (TC)((P.wallM[c] + P.Lam_old[c])) / A;             // (M + Lambda)/A multiplies a3
     }
     uint4* pw = reinterpret_cast<uint4*>(P.phi_new);
-    const unsigned nq = (unsigned)P.nq, niter = (nq + 31) / 32, oc = (unsigned)c * nq;
+    const unsigned nq = (unsigned)P.nq, niter = (nq + kRowChunks - 1) / kRowChunks, oc = (unsigned)c * nq;
 
     Sum<TC> sh, shx, shy, shc, sg2, sr, lam, rs;
     bool ok = true;
@@ -545,16 +915,19 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
     while (it < niter && ok) {
         TC bh = TC(0), bhx = TC(0), bhy = TC(0), bhc = TC(0), bg2 = TC(0), br = TC(0), bl = TC(0), brs = TC(0);
         for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
-            ok = pipeline_step(F, it, niter, lane, producer, [&](const uint4* d) {
-                const unsigned q = it * 32 + lane;
-                if (q >= nq) return;
-                const uint4 ro = d[(w + 1) * 32 + lane], rf = d[(26 + w) * 32 + lane];
+            ok = pipeline_step(F, it, niter, lane, [&](const uint4* d) {
+#pragma unroll
+              for (int cc = 0; cc < kCPL; ++cc) {
+                const unsigned q = it * kRowChunks + cc * 32 + lane;
+                if (q >= nq) break;
+                const uint4* e = d + cc * 32 + lane;
+                const uint4 ro = e[(w + 1) * kRowChunks], rf = e[(26 + w) * kRowChunks];
                 uint4 r0 = ro, r1 = ro, r2 = ro, r3 = ro;
                 if (kUpdate) {
-                    r0 = d[(10 + w) * 32 + lane];
-                    r2 = d[(18 + w) * 32 + lane];
-                    if (!far) r1 = d[(w + 2) * 32 + lane];
-                    if (!wall) r3 = d[w * 32 + lane];
+                    r0 = e[(10 + w) * kRowChunks];
+                    r2 = e[(18 + w) * kRowChunks];
+                    if (!far) r1 = e[(w + 2) * kRowChunks];
+                    if (!wall) r3 = e[w * kRowChunks];
                 }
                 TC po1[KV], po2[KV], f1[KV], f2[KV], e01[KV], e02[KV], e11[KV], e12[KV], e21[KV], e22[KV],
                     e31[KV], e32[KV];
@@ -607,6 +980,7 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
                     if (wall) bl += wk * fmin(a3, TC(0)) * P.gw[k] * gb1s * (pn1[kk] + P.halfTw * pn2[kk]);
                 }
                 if (kUpdate) stg16(pw + oc + q, PK::pack(pn1, pn2));
+              }
             });
         }
         sh.add(bh); shx.add(bhx); shy.add(bhy); shc.add(bhc); sg2.add(bg2); sr.add(br);
@@ -648,23 +1022,31 @@ __device__ __forceinline__ void adjoint_block(const AdjointArgs<TS, typename Pac
     if (!block_pipe_setup(B, smem, kAdjointRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, mf8, i, j0)) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = j0 + w, c = j * P.ni + i;
-    const bool producer = (threadIdx.x == 0);
     const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
     bool ok;
-    switch (bnd) {
-        case kInterior: ok = adjoint_cell<TS, kUpdate, kRes, kInterior>(P, c, w, lane, B.F, producer); break;
-        case kWallCell: ok = adjoint_cell<TS, kUpdate, kRes, kWallCell>(P, c, w, lane, B.F, producer); break;
-        case kFarCell: ok = adjoint_cell<TS, kUpdate, kRes, kFarCell>(P, c, w, lane, B.F, producer); break;
-        default: ok = adjoint_cell<TS, kUpdate, kRes, kWallFar>(P, c, w, lane, B.F, producer); break;
+    if constexpr (kPaired<TS>) {
+        switch (bnd) {
+            case kInterior: ok = adjoint_cell_paired<TS, kUpdate, kRes, kInterior>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = adjoint_cell_paired<TS, kUpdate, kRes, kWallCell>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = adjoint_cell_paired<TS, kUpdate, kRes, kFarCell>(P, c, w, lane, B.F); break;
+            default: ok = adjoint_cell_paired<TS, kUpdate, kRes, kWallFar>(P, c, w, lane, B.F); break;
+        }
+    } else {
+        switch (bnd) {
+            case kInterior: ok = adjoint_cell<TS, kUpdate, kRes, kInterior>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = adjoint_cell<TS, kUpdate, kRes, kWallCell>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = adjoint_cell<TS, kUpdate, kRes, kFarCell>(P, c, w, lane, B.F); break;
+            default: ok = adjoint_cell<TS, kUpdate, kRes, kWallFar>(P, c, w, lane, B.F); break;
+        }
     }
-    if (!ok) {
-        if (lane == 0) atomicExch(P.err, 1);
-        if (producer) block_pipe_drain(B);
+    if (!ok && lane == 0) {
+        atomicExch(P.err, 1);
+        block_pipe_drain(B);
     }
 }
 
 template <class TS, bool kUpdate, bool kRes>
-__global__ void __launch_bounds__(256, 3) k_adjoint_sweep(const AdjointArgs<TS, typename Pack<TS>::TC> P,
+__global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep(const AdjointArgs<TS, typename Pack<TS>::TC> P,
                                                           const __grid_constant__ CUtensorMap m10,
                                                           const __grid_constant__ CUtensorMap m8,
                                                           const __grid_constant__ CUtensorMap mf8) {
@@ -673,7 +1055,7 @@ __global__ void __launch_bounds__(256, 3) k_adjoint_sweep(const AdjointArgs<TS, 
 }
 
 template <class TS, bool kRes>
-__global__ void __launch_bounds__(256, 3) k_adjoint_sweep_batch(const AdjointBatchDesc<TS>* __restrict__ descs,
+__global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep_batch(const AdjointBatchDesc<TS>* __restrict__ descs,
                                                                 const int4* __restrict__ items, int parity) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int4 it = items[blockIdx.x];
@@ -766,8 +1148,9 @@ __global__ void k_fill_freestream(TS* f, size_t n_pairs, int nvp,
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pairs) return;
     const auto d = fd[i % nvp];
-    f[2 * i] = fromdbl<TS>((double)d.x);
-    f[2 * i + 1] = fromdbl<TS>((double)d.y);
+    const size_t o = fpos<TS>(i / nvp, nvp, (int)(i % nvp));
+    f[o] = fromdbl<TS>((double)d.x);
+    f[o + kComp<TS>] = fromdbl<TS>((double)d.y);
 }
 
 template <class TS>
@@ -781,7 +1164,8 @@ __global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const
     double m0 = 0, m1 = 0, m2 = 0, m3 = 0, fw = 0;
     for (int k = lane; k < nvp; k += 32) {
         const double4 t = vd[k];
-        const double f1 = todbl(f[((size_t)c * nvp + k) * 2]), f2 = todbl(f[((size_t)c * nvp + k) * 2 + 1]);
+        const size_t o = fpos<TS>(c, nvp, k);
+        const double f1 = todbl(f[o]), f2 = todbl(f[o + kComp<TS>]);
         m0 += t.z * f1;
         m1 += t.z * t.x * f1;
         m2 += t.z * t.y * f1;
@@ -828,7 +1212,7 @@ __global__ void k_functional(const TS* f, int nvp, const double2* S, const doubl
     for (int k = threadIdx.x; k < nvp; k += blockDim.x) {
         const double4 t = vd[k];
         const double a = s.x * t.x + s.y * t.y;
-        const double f1 = a > 0.0 ? todbl(f[((size_t)l * nvp + k) * 2]) : cw * gw[k];
+        const double f1 = a > 0.0 ? todbl(f[fpos<TS>(l, nvp, k)]) : cw * gw[k];
         j += t.z * (dirx * t.x + diry * t.y) * a * f1;
     }
     __shared__ double sj[32];
@@ -851,11 +1235,13 @@ __global__ void k_convert(const TA* src, TB* dst, int ncell, int nv_src, int nv_
     const size_t c = i / nv_dst, k = i % nv_dst;
     TB a = fromdbl<TB>(0.0), b = fromdbl<TB>(0.0);
     if ((int)k < nv_src) {
-        a = fromdbl<TB>(todbl(src[(c * nv_src + k) * 2]));
-        b = fromdbl<TB>(todbl(src[(c * nv_src + k) * 2 + 1]));
+        const size_t o = fpos<TA>(c, nv_src, (int)k);
+        a = fromdbl<TB>(todbl(src[o]));
+        b = fromdbl<TB>(todbl(src[o + kComp<TA>]));
     }
-    dst[2 * i] = a;
-    dst[2 * i + 1] = b;
+    const size_t o = fpos<TB>(c, nv_dst, (int)k);
+    dst[o] = a;
+    dst[o + kComp<TB>] = b;
 }
 
 // ================================================================== paper sensitivity (K4a)
@@ -879,14 +1265,16 @@ __global__ void k_sens_paper_elem(const TS* f, const TS* phi, int nvp, const int
     for (int k = threadIdx.x; k < nvp; k += blockDim.x) {
         const double4 t = vd[k];
         const double vx = t.x, vy = t.y, w = t.z, m = dirx * vx + diry * vy;
-        const double fc1 = todbl(f[((size_t)l * nvp + k) * 2]), fc2 = todbl(f[((size_t)l * nvp + k) * 2 + 1]);
+        const size_t ol = fpos<TS>(l, nvp, k);
+        const double fc1 = todbl(f[ol]), fc2 = todbl(f[ol + kComp<TS>]);
         double F1[4], F2[4];
         for (int e = 0; e < 4; ++e) {
             const double a = s[e].x * vx + s[e].y * vy;
             if (a > 0.0) { F1[e] = fc1; F2[e] = fc2; }
             else if (nbs[e] >= 0) {
-                F1[e] = todbl(f[((size_t)nbs[e] * nvp + k) * 2]);
-                F2[e] = todbl(f[((size_t)nbs[e] * nvp + k) * 2 + 1]);
+                const size_t oe = fpos<TS>(nbs[e], nvp, k);
+                F1[e] = todbl(f[oe]);
+                F2[e] = todbl(f[oe + kComp<TS>]);
             } else if (nbs[e] == kFar) { F1[e] = fd[k].x; F2[e] = fd[k].y; }
             else { F1[e] = cw * gw[k]; F2[e] = cw * halfTw * gw[k]; }
         }
@@ -908,7 +1296,8 @@ __global__ void k_sens_paper_elem(const TS* f, const TS* phi, int nvp, const int
             acc[3] += w * vn * g1x;
             acc[4] += w * vn * g1y;
         } else {
-            const double p1 = todbl(phi[((size_t)l * nvp + k) * 2]), p2 = todbl(phi[((size_t)l * nvp + k) * 2 + 1]);
+            const size_t op = fpos<TS>(l, nvp, k);
+            const double p1 = todbl(phi[op]), p2 = todbl(phi[op + kComp<TS>]);
             const double pw1 = -vn * (p1 + m), pw2 = -vn * p2;
             const double gb1 = gw[k] / wallD[l];
             acc[1] += w * A * (pw1 * g1x + pw2 * g2x);
@@ -999,16 +1388,17 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
     for (int k = lane; k < nvp; k += 32) {
         const auto t = vt[k];
         const TC vx = t.x, vy = t.y, w = t.z;
-        const size_t ic = ((size_t)c * nvp + k) * 2;
-        const TC fc1 = (TC)todbl(f[ic]), fc2 = (TC)todbl(f[ic + 1]);
-        const TC pc1 = (TC)todbl(phi[ic]), pc2 = (TC)todbl(phi[ic + 1]);
+        constexpr int C2 = kComp<TS>;
+        const size_t ic = fpos<TS>(c, nvp, k);
+        const TC fc1 = (TC)todbl(f[ic]), fc2 = (TC)todbl(f[ic + C2]);
+        const TC pc1 = (TC)todbl(phi[ic]), pc2 = (TC)todbl(phi[ic + C2]);
         {   // north face
             const TC a = s1x * vx + s1y * vy;
             TC F1, F2, q1 = TC(0), q2 = TC(0);
             if (n.y >= 0) {
-                const size_t ir = ((size_t)n.y * nvp + k) * 2;
-                q1 = (TC)todbl(phi[ir]); q2 = (TC)todbl(phi[ir + 1]);
-                if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + 1]); }
+                const size_t ir = fpos<TS>(n.y, nvp, k);
+                q1 = (TC)todbl(phi[ir]); q2 = (TC)todbl(phi[ir + C2]);
+                if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + C2]); }
             } else if (a > TC(0)) { F1 = fc1; F2 = fc2; }
             else { F1 = fd[k].x; F2 = fd[k].y; }
             const TC d = w * ((pc1 - q1) * F1 + (pc2 - q2) * F2);
@@ -1016,10 +1406,10 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
         }
         {   // east face (always interior)
             const TC a = s2x * vx + s2y * vy;
-            const size_t ir = ((size_t)n.z * nvp + k) * 2;
-            const TC q1 = (TC)todbl(phi[ir]), q2 = (TC)todbl(phi[ir + 1]);
+            const size_t ir = fpos<TS>(n.z, nvp, k);
+            const TC q1 = (TC)todbl(phi[ir]), q2 = (TC)todbl(phi[ir + C2]);
             TC F1, F2;
-            if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + 1]); }
+            if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + C2]); }
             const TC d = w * ((pc1 - q1) * F1 + (pc2 - q2) * F2);
             gex.add(d * vx); gey.add(d * vy);
         }
@@ -1159,6 +1549,118 @@ __global__ void k_volume(int ni, const double2* S, const double2* nodes, double 
     }
 }
 
+// ================================================================== Anderson mixing
+// Convergence acceleration of the fixed-point sweeps (the discrete problem and its solution are
+// unchanged): every accel_period sweeps map the iterate x to G(x); with r = G(x) - x and the last m
+// differences dR, dG of r and G, the next iterate is G - dG gamma, gamma = argmin |r - dR gamma|.
+// The vectors are the flat storage arrays (any layout: the operations are elementwise), held in
+// TH = the arithmetic type (FP32, or FP64 for FP64 storage).
+template <class TH, class TS> __device__ __forceinline__ TH toh(TS v) { return (TH)todbl(v); }
+template <> __device__ __forceinline__ float toh<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float toh<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class TS, class TH> __device__ __forceinline__ TS fromh(TH v) { return fromdbl<TS>((double)v); }
+template <> __device__ __forceinline__ float fromh<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 fromh<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+constexpr int kAAMax = 8;             // deepest history
+constexpr int kAABlocks = 1216;       // 152 SMs x 8 blocks of 256 threads, grid-stride
+
+template <class TS, class TH>
+__global__ void __launch_bounds__(256) k_aa_load(size_t n, const TS* __restrict__ F, TH* __restrict__ X) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        X[e] = toh<TH>(F[e]);
+}
+
+// r = G - X, the new differences (slot `slot` of the ring, unless first) and the dots
+// dR_i . dR_slot (part[i]) and dR_i . r (part[m + i]) for the cnt columns in use, per block.
+template <class TS, class TH>
+__global__ void __launch_bounds__(256) k_aa_collect(size_t n, const TS* __restrict__ G, TH* __restrict__ X,
+                                                    TH* __restrict__ Rp, TH* __restrict__ Gp, TH* __restrict__ dR,
+                                                    TH* __restrict__ dG, int m, int cnt, int slot, int first,
+                                                    double* __restrict__ part) {
+    TH acc[2 * kAAMax];
+#pragma unroll
+    for (int i = 0; i < 2 * kAAMax; ++i) acc[i] = TH(0);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const TH g = toh<TH>(G[e]);
+        const TH r = g - X[e];
+        if (first) {
+            X[e] = g;
+        } else {
+            const TH dr = r - Rp[e];
+            dR[(size_t)slot * n + e] = dr;
+            dG[(size_t)slot * n + e] = g - Gp[e];
+#pragma unroll
+            for (int i = 0; i < kAAMax; ++i) {
+                if (i < cnt) {
+                    const TH c = i == slot ? dr : dR[(size_t)i * n + e];
+                    acc[i] += c * dr;
+                    acc[kAAMax + i] += c * r;
+                }
+            }
+        }
+        Rp[e] = r;
+        Gp[e] = g;
+    }
+    if (first) return;
+    __shared__ double red[8][2 * kAAMax];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 2 * kAAMax; ++i) {
+        const double v = warp_sum((double)acc[i]);
+        if (lane == 0) red[wid][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * m) {
+        const int i = threadIdx.x < m ? threadIdx.x : kAAMax + threadIdx.x - m;
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][i];
+        part[(size_t)blockIdx.x * 2 * m + threadIdx.x] = t;
+    }
+}
+
+// Fixed-order sum of the per-block dots: out[j] = sum_b part[b][j], j < 2m.
+__global__ void k_aa_sum(const double* __restrict__ part, int nb, int m2, double* __restrict__ out) {
+    const int j = threadIdx.x;
+    if (j >= m2) return;
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += part[(size_t)b * m2 + j];
+    out[j] = t;
+}
+
+// x = G - sum_i gamma_i dG_i into the state (rounded to storage) and X (the stored value); neg is
+// set when any value turns negative.
+template <class TS, class TH>
+__global__ void __launch_bounds__(256) k_aa_mix(size_t n, TS* __restrict__ F, TH* __restrict__ X,
+                                                const TH* __restrict__ Gp, const TH* __restrict__ dG, int cnt,
+                                                const double* __restrict__ gamma, int* __restrict__ neg) {
+    TH gam[kAAMax];
+#pragma unroll
+    for (int i = 0; i < kAAMax; ++i) gam[i] = i < cnt ? (TH)gamma[i] : TH(0);
+    bool bad = false;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        TH x = Gp[e];
+#pragma unroll
+        for (int i = 0; i < kAAMax; ++i)
+            if (i < cnt) x -= gam[i] * dG[(size_t)i * n + e];
+        const TS v = fromh<TS>(x);
+        F[e] = v;
+        X[e] = toh<TH>(v);
+        bad |= x < TH(0);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(neg, 1);
+}
+
+// Undo a rejected mix: the state and X return to G.
+template <class TS, class TH>
+__global__ void __launch_bounds__(256) k_aa_restore(size_t n, TS* __restrict__ F, TH* __restrict__ X,
+                                                    const TH* __restrict__ Gp) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        F[e] = fromh<TS>(Gp[e]);
+        X[e] = Gp[e];
+    }
+}
+
 inline int cdiv(size_t a, size_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
@@ -1264,7 +1766,7 @@ cudaError_t make_tmamaps(void* base, int ni, int nj, int nq, TmaMaps* out) {
     const cuuint64_t dims[3] = {(cuuint64_t)nq * 4, (cuuint64_t)ni, (cuuint64_t)nj};
     const cuuint64_t strides[2] = {(cuuint64_t)nq * 16, (cuuint64_t)nq * 16 * ni};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const cuuint32_t box10[3] = {128, 1, 10}, box8[3] = {128, 1, 8};
+    const cuuint32_t box10[3] = {128u * kCPL, 1, 10}, box8[3] = {128u * kCPL, 1, 8};
     CUresult r = encode(&out->col, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, base, dims, strides, box10, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1435,6 +1937,42 @@ cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, co
     k_sens_nodes<<<cdiv(nn, 256), 256, 0, s>>>(m.ni, m.nj, m.nodes, GN, GE, GW, vol, node_grad);
     return cudaGetLastError();
 }
+
+int aa_max_depth() { return kAAMax; }
+int aa_blocks() { return kAABlocks; }
+
+#define DVM_AA_DISPATCH(storage, CALL)                                                                   \
+    switch (storage) {                                                                                   \
+        case 0: { using TS = double; using TH = double; CALL; } break;                                   \
+        case 1: { using TS = float; using TH = float; CALL; } break;                                     \
+        default: { using TS = __nv_bfloat16; using TH = float; CALL; } break;                            \
+    }
+
+cudaError_t launch_aa_load(int storage, size_t n, const void* F, void* X, cudaStream_t s) {
+    DVM_AA_DISPATCH(storage, (k_aa_load<TS, TH><<<kAABlocks, 256, 0, s>>>(n, (const TS*)F, (TH*)X)))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aa_collect(int storage, size_t n, const void* G, void* X, void* Rp, void* Gp, void* dR, void* dG,
+                              int m, int cnt, int slot, int first, double* part, double* out, cudaStream_t s) {
+    DVM_AA_DISPATCH(storage, (k_aa_collect<TS, TH><<<kAABlocks, 256, 0, s>>>(n, (const TS*)G, (TH*)X, (TH*)Rp, (TH*)Gp,
+                                                                          (TH*)dR, (TH*)dG, m, cnt, slot, first, part)))
+    if (!first) k_aa_sum<<<1, 32, 0, s>>>(part, kAABlocks, 2 * m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aa_mix(int storage, size_t n, void* F, void* X, const void* Gp, const void* dG, int cnt,
+                          const double* gamma, int* neg, cudaStream_t s) {
+    DVM_AA_DISPATCH(storage, (k_aa_mix<TS, TH><<<kAABlocks, 256, 0, s>>>(n, (TS*)F, (TH*)X, (const TH*)Gp, (const TH*)dG,
+                                                                      cnt, gamma, neg)))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aa_restore(int storage, size_t n, void* F, void* X, const void* Gp, cudaStream_t s) {
+    DVM_AA_DISPATCH(storage, (k_aa_restore<TS, TH><<<kAABlocks, 256, 0, s>>>(n, (TS*)F, (TH*)X, (const TH*)Gp)))
+    return cudaGetLastError();
+}
+#undef DVM_AA_DISPATCH
 
 cudaError_t launch_volume(const DevMesh& m, double vmin, const double* dwall, int P, double* out, cudaStream_t s) {
     k_volume<<<1, 256, 0, s>>>(m.ni, m.Sd, m.nodes, vmin, dwall, P, out);

@@ -9,10 +9,13 @@ steps is below 3e-5 (Step 6, Eq. criterion_opt).
 
 The paper's optimiser is an SQP method with BFGS updates from a third-party library.  Here Step 5
 is a limited-memory BFGS (the two-loop recursion of Nocedal and Wright, Algorithm 7.4) with a
-projected Armijo backtracking line search on box bounds, and Q <= 0 enters through the quadratic
-penalty  Phi = Cd + (mu / 2) max(0, Q / V_min)^2.  The optimiser is an ask/tell object: `ask`
-returns the next design to evaluate, `tell` takes (Phi, dPhi/dalpha) of that design, so several
-loops can share one served batch of GPU solves (`run_concurrent`).
+projected Armijo backtracking line search.  The bumps move the wall nodes in y only, so the
+polygon area, and with it Q, is an affine function of alpha: Q(alpha) = Q0 + dQ . (alpha - alpha0)
+exactly.  The feasible set {|alpha_p| <= bound, Q <= 0} is then a box cut by one half-space, and
+every trial design is its Euclidean projection onto that set: the constraint holds at every
+evaluated design instead of being penalised.  The optimiser is an ask/tell object: `ask` returns
+the next design to evaluate, `tell` takes (Cd, dCd/dalpha) of that design, so several loops can
+share one served batch of GPU solves (`run_concurrent`).
 """
 from __future__ import annotations
 
@@ -31,19 +34,42 @@ def criterion_opt(J_old: float, J_new: float, tol: float = CRITERION_OPT) -> boo
     return abs(J_new - J_old) < tol * abs(J_old)
 
 
+def project_box_halfspace(x, lower, upper, c=None, b=0.0, iters=200):
+    """Euclidean projection of x onto {lower <= y <= upper, c . y <= b}.  The minimiser is
+    y(nu) = clip(x - nu c) for the smallest nu >= 0 with c . y(nu) <= b; c . y(nu) does not increase
+    with nu, so nu is found by bisection."""
+    y = np.minimum(np.maximum(x, lower), upper)
+    if c is None or float(c @ y) <= b:
+        return y
+    lo, hi = 0.0, 1.0
+    while float(c @ np.minimum(np.maximum(x - hi * c, lower), upper)) > b:
+        hi *= 2.0
+        if hi > 1e30:
+            raise ValueError("the half-space does not meet the box")
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if float(c @ np.minimum(np.maximum(x - mid * c, lower), upper)) > b:
+            lo = mid
+        else:
+            hi = mid
+    return np.minimum(np.maximum(x - hi * c, lower), upper)
+
+
 class LBFGS:
     """Ask/tell L-BFGS with projected Armijo backtracking on the box [lower, upper].
 
     Phases: 'init' (x0 asked), 'trial' (a line-search point asked), 'done'.  `tell` returns
     'accepted' when the trial point became the new iterate, 'rejected' when the step was cut,
-    'failed' when the line search gave up after a steepest-descent restart, or 'init'."""
+    'failed' when the line search gave up after a steepest-descent restart, or 'init'.
+    halfspace = (c, b) adds the linear constraint c . x <= b to the box."""
 
     def __init__(self, x0, m: int = 8, lower=None, upper=None, first_step: float = 1e-3,
-                 c1: float = 1e-4, shrink: float = 0.5, max_backtracks: int = 8):
+                 c1: float = 1e-4, shrink: float = 0.5, max_backtracks: int = 8, halfspace=None):
         self.x = np.array(x0, dtype=np.float64)
         n = self.x.size
         self.lower = np.full(n, -np.inf) if lower is None else np.broadcast_to(np.asarray(lower, float), (n,)).copy()
         self.upper = np.full(n, np.inf) if upper is None else np.broadcast_to(np.asarray(upper, float), (n,)).copy()
+        self.halfspace = None if halfspace is None else (np.asarray(halfspace[0], float), float(halfspace[1]))
         self.x = self.project(self.x)
         self.m, self.first_step, self.c1, self.shrink, self.max_backtracks = m, first_step, c1, shrink, max_backtracks
         self.S: list[np.ndarray] = []
@@ -59,7 +85,9 @@ class LBFGS:
         self._backtracks = 0
 
     def project(self, x):
-        return np.minimum(np.maximum(x, self.lower), self.upper)
+        if self.halfspace is None:
+            return np.minimum(np.maximum(x, self.lower), self.upper)
+        return project_box_halfspace(x, self.lower, self.upper, *self.halfspace)
 
     def direction(self, g):
         """-H g by the two-loop recursion, H0 = (s.y / y.y) I from the newest pair."""
@@ -141,8 +169,6 @@ class Evaluation:
     dCd: np.ndarray
     Q: float
     dQ: np.ndarray
-    phi: float
-    dphi: np.ndarray
     ok: bool = True
 
 
@@ -151,8 +177,9 @@ class DesignLoop:
     """One drag-minimisation loop at fixed flow conditions.
 
     ni, nj, grid, flow: the O-mesh size, velocity grid and flow; n_params bumps start at alpha0
-    (zeros: the symmetric section).  v_min is the section area of alpha0 unless given; mu weights the
-    constraint penalty; bound limits each amplitude; max_iter counts accepted steps."""
+    (zeros: the symmetric section).  v_min is the section area of alpha0 unless given; bound
+    limits each amplitude; max_iter counts accepted steps.  `constrain(Q0, dQ)` with the volume
+    constraint and its gradient at alpha0 must be called before the first `ask`."""
     ni: int
     nj: int
     grid: W.VGrid
@@ -160,7 +187,6 @@ class DesignLoop:
     n_params: int = 24
     alpha0: np.ndarray | None = None
     v_min: float | None = None
-    mu: float = 1e4
     bound: float = 0.01
     max_iter: int = 12
     first_step: float = 1e-3
@@ -168,20 +194,22 @@ class DesignLoop:
     history: list = field(default_factory=list)
 
     def __post_init__(self):
-        a0 = np.zeros(self.n_params) if self.alpha0 is None else np.asarray(self.alpha0, float)
-        self.opt = LBFGS(a0, lower=-self.bound, upper=self.bound, first_step=self.first_step)
+        self.a0 = np.zeros(self.n_params) if self.alpha0 is None else np.asarray(self.alpha0, float)
+        self.opt = None
         self.J_old = None
         self.converged = False
         self.stopped = None
+
+    def constrain(self, Q0: float, dQ):
+        """Q(alpha) = Q0 + dQ . (alpha - alpha0) <= 0, i.e. dQ . alpha <= dQ . alpha0 - Q0."""
+        dQ = np.asarray(dQ, float)
+        self.opt = LBFGS(self.a0, lower=-self.bound, upper=self.bound, first_step=self.first_step,
+                         halfspace=(dQ, float(dQ @ self.a0) - Q0))
 
     @property
     def q_ref(self) -> float:
         U = self.flow.Ma * W.A_INF
         return 0.5 * U * U
-
-    def penalty(self, Cd, dCd, Q, dQ):
-        v = max(0.0, Q / self.v_min)
-        return Cd + 0.5 * self.mu * v * v, dCd + self.mu * v * dQ / self.v_min
 
     def feasible_mesh(self, alpha) -> bool:
         return W.valid_amplitude_scale(self.ni, alpha, margin=1.0) >= 1.0
@@ -190,7 +218,7 @@ class DesignLoop:
         """Hand one evaluation to the optimiser; apply Eq. (criterion_opt) on accepted steps."""
         self.history.append(ev)
         phase = self.opt.phase
-        out = self.opt.tell(ev.phi if ev.ok else np.inf, ev.dphi if ev.ok else np.zeros_like(ev.alpha))
+        out = self.opt.tell(ev.Cd if ev.ok else np.inf, ev.dCd if ev.ok else np.zeros_like(ev.alpha))
         if phase == "init":
             self.J_old = ev.Cd
         elif out == "accepted":
@@ -209,7 +237,7 @@ class DesignLoop:
 
     @property
     def best(self) -> Evaluation:
-        return min((e for e in self.history if e.ok), key=lambda e: e.phi)
+        return min((e for e in self.history if e.ok), key=lambda e: e.Cd)
 
 
 def _volume(ctx, nodes, v_min, dwall):
@@ -220,9 +248,14 @@ def _volume(ctx, nodes, v_min, dwall):
         m.close()
 
 
+# a solve that met its tolerance, stopped at its rounding floor or ran out of sweeps still returns
+# its final iterate; only non-finite or failed solves reject a design
+_USABLE = (dvm.DVM_OK, dvm.DVM_NOT_CONVERGED, dvm.DVM_ERR_STAGNATED)
+
+
 def _failed(alpha):
     z = np.zeros_like(alpha)
-    return Evaluation(alpha, np.nan, z, np.nan, z, np.inf, z, ok=False)
+    return Evaluation(alpha, np.nan, z, np.nan, z, ok=False)
 
 
 def drive(loop: DesignLoop, evaluate):
@@ -241,8 +274,7 @@ def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 
     from .autograd import DragProblem
     prob = DragProblem(ctx, loop.ni, loop.nj, loop.grid, loop.flow, storage=storage, tol=tol,
                        adjoint_tol=adjoint_tol, max_iter=max_sweeps, stall_window=stall_window)
-    if loop.v_min is None:
-        loop.v_min = section_area(ctx, loop.ni, loop.nj, loop.opt.x)
+    _start(ctx, loop)
 
     def evaluate(a):
         try:
@@ -254,7 +286,7 @@ def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 
         mesh = prob.last["mesh"]
         Q, dQ = _volume(ctx, mesh.nodes, loop.v_min, mesh.dwall)
         prob.release()
-        return Evaluation(a, Cd, dCd, Q, dQ, *loop.penalty(Cd, dCd, Q, dQ))
+        return Evaluation(a, Cd, dCd, Q, dQ)
 
     try:
         return drive(loop, evaluate)
@@ -267,8 +299,19 @@ def section_area(ctx: dvm.Context, ni: int, nj: int, alpha) -> float:
     return -_volume(ctx, W.omesh(ni, nj, alpha).nodes, 0.0, np.zeros((1, ni, 2)))[0]
 
 
+def _start(ctx, loop: DesignLoop):
+    """V_min (the initial area unless given) and the linear volume constraint of the loop."""
+    if loop.opt is not None:
+        return
+    if loop.v_min is None:
+        loop.v_min = section_area(ctx, loop.ni, loop.nj, loop.a0)
+    mesh = W.omesh(loop.ni, loop.nj, loop.a0)
+    Q0, dQ = _volume(ctx, mesh.nodes, loop.v_min, mesh.dwall)
+    loop.constrain(Q0, dQ)
+
+
 def run_concurrent(ctx: dvm.Context, loops: list[DesignLoop], storage: str = "fp32", tol: float = 1e-6,
-                   max_sweeps: int = 200000, sweeps_per_tick: int = 20):
+                   max_sweeps: int = 200000, sweeps_per_tick: int = 20, stall_window: int = 3000):
     """Drive several loops at once through one served batch: every loop's pending evaluation is a
     request in flight; a loop's next design is submitted as soon as its previous one retires, with
     its own warm-start key so f and phi carry over from that loop's last solve."""
@@ -283,15 +326,14 @@ def run_concurrent(ctx: dvm.Context, loops: list[DesignLoop], storage: str = "fp
             if loop.feasible_mesh(a):
                 mesh = W.omesh(loop.ni, loop.nj, a)
                 spec = SolveSpec(mesh, loop.grid, loop.flow, storage=storage, tol=tol, adjoint_tol=tol,
-                                 max_iter=max_sweeps, warm_key=1000 + k)
+                                 max_iter=max_sweeps, warm_key=1000 + k, stall_window=stall_window)
                 pending[server.submit(spec)] = (k, a, mesh)
                 return
             loop.finish(_failed(a))
 
     try:
         for k, loop in enumerate(loops):
-            if loop.v_min is None:
-                loop.v_min = section_area(ctx, loop.ni, loop.nj, loop.opt.x)
+            _start(ctx, loop)
             submit(k)
         while pending:
             server.tick()
@@ -302,13 +344,64 @@ def run_concurrent(ctx: dvm.Context, loops: list[DesignLoop], storage: str = "fp
                 server.poll(t, forget=True)
                 k, a, mesh = pending.pop(t)
                 loop = loops[k]
-                if r["status"] != 0:
+                if r["status"] not in _USABLE:
                     loop.finish(_failed(a))
                 else:
                     Cd, dCd = r["J"] / loop.q_ref, r["grad"] / loop.q_ref
                     Q, dQ = _volume(ctx, mesh.nodes, loop.v_min, mesh.dwall)
-                    loop.finish(Evaluation(a, Cd, dCd, Q, dQ, *loop.penalty(Cd, dCd, Q, dQ)))
+                    loop.finish(Evaluation(a, Cd, dCd, Q, dQ))
                 submit(k)
     finally:
         server.close()
     return loops
+
+
+def main(argv=None):
+    """Drag minimisation on the design workload (O-mesh 256x128, 48x48 Gauss-Legendre grid on
+    [-6, 6]^2, Ma 0.8, 24 bumps from the symmetric section), one loop per Kn; prints one JSON line per
+    loop with the accepted history and the wall time."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(prog="python -m paper_2501_00923_gb300.design")
+    ap.add_argument("--kn", default="1,0.1,0.01")
+    ap.add_argument("--iters", type=int, default=12)
+    ap.add_argument("--mesh", default="256x128")
+    ap.add_argument("--nv", type=int, default=48)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--concurrent", action="store_true", help="all Kn loops through one served batch")
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    ni, nj = (int(x) for x in args.mesh.lower().split("x"))
+    wl = W.config(4)
+    grid = W.velocity_grid(args.nv, 6.0, "gauss")
+    ctx = dvm.Context(0)
+    loops = [DesignLoop(ni, nj, grid, W.Flow(float(k), wl.flow.Ma), n_params=24, max_iter=args.iters)
+             for k in args.kn.split(",")]
+    t0 = time.perf_counter()
+    if args.concurrent:
+        run_concurrent(ctx, loops, storage=args.storage, tol=args.tol)
+        spans = [time.perf_counter() - t0] * len(loops)
+    else:
+        spans = []
+        for loop in loops:
+            t = time.perf_counter()
+            run(ctx, loop, storage=args.storage, tol=args.tol, adjoint_tol=args.tol, stall_window=3000)
+            spans.append(time.perf_counter() - t)
+    for loop, span in zip(loops, spans):
+        acc, best = [], None
+        for e in loop.history:
+            if e.ok and (best is None or e.Cd < best):
+                best = e.Cd
+                acc.append({"Cd": e.Cd, "Q_over_Vmin": e.Q / loop.v_min})
+        print(json.dumps({"Kn": loop.flow.Kn, "Ma": loop.flow.Ma, "mesh": args.mesh, "nv": args.nv,
+                          "storage": args.storage, "stopped": loop.stopped, "iterations": loop.opt.iterations,
+                          "evaluations": loop.opt.evaluations, "Cd0": loop.history[0].Cd, "Cd_best": best,
+                          "seconds": span, "concurrent": args.concurrent, "accepted": acc}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

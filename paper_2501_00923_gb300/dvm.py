@@ -36,7 +36,16 @@ class Flow(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("stall_window", C.c_int)]
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("stall_window", C.c_int), ("accel_depth", C.c_int),
+                ("accel_period", C.c_int)]
+
+
+def _accel(accel):
+    """accel: None (plain sweeps) or (depth m, period K) of the Anderson mixing."""
+    if accel is None:
+        return 0, 0
+    m, k = accel
+    return int(m), int(k)
 
 
 class PrimalResult(C.Structure):
@@ -324,10 +333,11 @@ class Adjoint:
 
 # ----------------------------------------------------------------------------------- calls
 def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0, tol=1e-8, max_iter=100000,
-                 storage="fp32", state: State | None = None, stall_window=0):
-    """Steady solve of Eq. (numerpr_gov); warm-starts from `state` if given.  Returns (state, result)."""
+                 storage="fp32", state: State | None = None, stall_window=0, accel=None):
+    """Steady solve of Eq. (numerpr_gov); warm-starts from `state` if given.  accel = (m, K) turns on
+    Anderson mixing of depth m every K sweeps.  Returns (state, result)."""
     flow = Flow(Kn, Ma, Tw, aoa)
-    opts = SolveOpts(tol, max_iter, stall_window)
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel))
     h = C.c_void_p(state.h.value if state is not None else None)
     res = PrimalResult()
     st = lib().dvm_primal_solve(ctx.h, mesh.h, grid.h, C.byref(flow), C.byref(opts), STORAGE[storage],
@@ -339,8 +349,9 @@ def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0,
 
 
 def adjoint_solve(ctx: Context, state: State, functional="drag", tol=1e-8, max_iter=100000,
-                  adjoint: Adjoint | None = None, stall_window=0):
-    opts = SolveOpts(tol, max_iter, stall_window)
+                  adjoint: Adjoint | None = None, stall_window=0, accel=None):
+    """Steady solve of the discrete adjoint for `functional`; accel as in primal_solve."""
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel))
     h = C.c_void_p(adjoint.h.value if adjoint is not None else None)
     res = AdjointResult()
     st = lib().dvm_adjoint_solve(ctx.h, state.h, FUNCTIONAL[functional], C.byref(opts), C.byref(h), C.byref(res))

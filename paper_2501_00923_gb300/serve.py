@@ -32,7 +32,7 @@ class Request(C.Structure):
                 ("vx", _dp), ("vy", _dp), ("w", _dp), ("flow", dvm.Flow), ("storage", C.c_int),
                 ("tol", C.c_double), ("adjoint_tol", C.c_double), ("max_iter", C.c_int),
                 ("functional", C.c_int), ("n_params", C.c_int), ("dwall_dalpha", _dp), ("s_j", _dp),
-                ("sens_mode", C.c_int), ("warm_key", C.c_uint64)]
+                ("sens_mode", C.c_int), ("warm_key", C.c_uint64), ("stall_window", C.c_int)]
 
 
 class RequestResult(C.Structure):
@@ -75,6 +75,7 @@ class SolveSpec:
     sens_mode: str = "full"
     functional: str = "drag"
     warm_key: int = 0
+    stall_window: int = 0
     _keep: list = field(default_factory=list, repr=False)
 
     def to_c(self) -> Request:
@@ -88,7 +89,7 @@ class SolveSpec:
                        dvm.Flow(self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa),
                        dvm.STORAGE[self.storage], self.tol, self.adjoint_tol, self.max_iter,
                        dvm.FUNCTIONAL[self.functional], P, p(dwall) if P else None, p(s) if P else None,
-                       dvm.SENS[self.sens_mode], self.warm_key)
+                       dvm.SENS[self.sens_mode], self.warm_key, self.stall_window)
 
 
 class BatchServer:

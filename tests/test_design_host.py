@@ -1,5 +1,6 @@
-"""Host logic of the design loop: the L-BFGS step, its line search and bounds, the stopping rule of
-Eq. (criterion_opt) and the constraint penalty, all on analytic objectives (no GPU)."""
+"""Host logic of the design loop: the L-BFGS step, its line search, the projection onto the box and
+the volume-constraint half-space, and the stopping rule of Eq. (criterion_opt), on analytic
+objectives (no GPU)."""
 import numpy as np
 import pytest
 
@@ -90,21 +91,40 @@ def test_unevaluable_trials_are_backtracked():
     assert bad and opt.x[0] <= 0.5
 
 
-def test_penalty_gradient_matches_finite_differences():
-    loop = D.DesignLoop(16, 4, W.velocity_grid(4, 4.0), W.Flow(1.0, 0.5), n_params=3, v_min=0.08, mu=50.0)
-    rng = np.random.default_rng(7)
-    dCd, dQ = rng.normal(size=3), rng.normal(size=3)
-    a0 = rng.normal(size=3) * 0.01
+def test_projection_onto_box_and_halfspace_is_the_nearest_feasible_point():
+    rng = np.random.default_rng(9)
+    n = 8
+    lo, hi = -0.01, 0.01
+    for _ in range(20):
+        c = rng.normal(size=n)
+        b = rng.uniform(-0.01, 0.01)
+        x = rng.normal(size=n) * 0.02
+        y = D.project_box_halfspace(x, lo, hi, c, b)
+        assert np.all(y >= lo - 1e-15) and np.all(y <= hi + 1e-15) and c @ y <= b + 1e-12
+        d = np.linalg.norm(x - y)
+        for _ in range(200):                   # no sampled feasible point is nearer
+            z = rng.uniform(lo, hi, n)
+            if c @ z <= b:
+                assert np.linalg.norm(x - z) >= d - 1e-12
+        z = np.clip(x, lo, hi)                  # feasible clip => the projection is the clip
+        if c @ z <= b:
+            np.testing.assert_allclose(y, z, atol=1e-15)
 
-    def phi(a):
-        Cd = 0.3 + dCd @ a
-        Q = 0.001 + dQ @ a                  # violated: the penalty is active
-        return loop.penalty(Cd, dCd, Q, dQ)
-    _, g = phi(a0)
-    h = 1e-6
-    fd = np.array([(phi(a0 + h * e)[0] - phi(a0 - h * e)[0]) / (2 * h) for e in np.eye(3)])
-    np.testing.assert_allclose(g, fd, rtol=1e-7)
-    assert phi(a0 - 10 * dQ)[0] == pytest.approx(0.3 + dCd @ (a0 - 10 * dQ))   # satisfied: no penalty
+
+def test_volume_constraint_is_affine_in_the_bump_amplitudes():
+    """The bumps move the wall nodes in y only, so the shoelace area, and Q, is affine in alpha:
+    Q(alpha) = Q(0) + dQ . alpha exactly.  The projected L-BFGS relies on it."""
+    from oracle import oracle as O
+    g = W.velocity_grid(4, 4.0)
+    rng = np.random.default_rng(10)
+    m0 = W.omesh(64, 4, np.zeros(8))
+    Q0, _, dQ = O.Problem(m0.nodes, g.vx, g.vy, g.w, 1.0, 0.5).volume_constraint(0.08, m0.dwall)
+    for _ in range(5):
+        a = rng.uniform(-0.01, 0.01, 8) * 0.5
+        m = W.omesh(64, 4, a)
+        Qa, _, dQa = O.Problem(m.nodes, g.vx, g.vy, g.w, 1.0, 0.5).volume_constraint(0.08, m.dwall)
+        assert abs(Qa - (Q0 + dQ @ a)) < 1e-15
+        np.testing.assert_allclose(dQa, dQ, rtol=1e-12, atol=1e-17)
 
 
 def test_design_loop_stops_by_criterion_opt_on_an_analytic_problem():
@@ -116,19 +136,22 @@ def test_design_loop_stops_by_criterion_opt_on_an_analytic_problem():
     c = rng.uniform(-0.004, 0.004, n)
     q = -np.abs(rng.normal(size=n)) * 0.05      # area grows with positive amplitudes
     loop = D.DesignLoop(64, 8, W.velocity_grid(4, 4.0), W.Flow(1.0, 0.5), n_params=n, v_min=0.08,
-                        mu=1e4, max_iter=50, bound=0.01)
+                        max_iter=50, bound=0.01)
     loop.feasible_mesh = lambda a: True
+    loop.constrain(0.0, q)                      # Q(alpha) = q . alpha <= 0
 
     def evaluate(a):
         Cd = 0.5 + 0.5 * (a - c) @ A @ (a - c)
-        dCd = A @ (a - c)
-        Q = q @ a
-        return D.Evaluation(a, Cd, dCd, Q, q.copy(), *loop.penalty(Cd, dCd, Q, q))
+        return D.Evaluation(a, Cd, A @ (a - c), q @ a, q.copy())
     D.drive(loop, evaluate)
     assert loop.stopped == "criterion_opt"
+    assert all(e.Q <= 1e-15 for e in loop.history)          # every evaluated design is feasible
     acc = [loop.history[0]]
     for e in loop.history[1:]:
-        if e.phi < acc[-1].phi:
+        if e.Cd < acc[-1].Cd:
             acc.append(e)
-    assert all(b.phi < a.phi for a, b in zip(acc, acc[1:]))
-    assert loop.best.Cd < loop.history[0].Cd
+    assert len(acc) >= 3 and loop.best.Cd < loop.history[0].Cd
+    # the constrained minimiser: min 1/2 (a-c)^T A (a-c) s.t. q.a <= 0, |a| <= 0.01 (inactive box)
+    lam = max(0.0, (q @ c) / (q @ np.linalg.solve(A, q)))
+    a_star = c - lam * np.linalg.solve(A, q)
+    assert np.abs(loop.best.alpha - a_star).max() < 2e-4

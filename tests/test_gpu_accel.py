@@ -1,0 +1,75 @@
+"""Anderson mixing of the sweeps (dvm_solve_opts.accel_depth / accel_period) only accelerates the
+iteration: the converged primal state, drag, adjoint and sensitivities are those of the plain
+point-implicit sweeps.  At Kn = 0.01 the plain sweeps converge slowly (the leading eigenvalue of
+the sweep map is about 0.999 on this mesh), and the mixing must cut the sweep count by at least 2."""
+import numpy as np
+import pytest
+
+from paper_2501_00923_gb300 import build, dvm
+from paper_2501_00923_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    c = dvm.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def case(ctx):
+    mesh = W.omesh(32, 12, np.array([0.004, -0.002, 0.003, 0.001, -0.003, 0.002]))
+    grid = W.velocity_grid(12, 4.0)
+    m = dvm.Mesh(ctx, mesh.nodes)
+    g = dvm.VGrid(ctx, grid.vx, grid.vy, grid.w)
+    return mesh, grid, m, g
+
+
+def _solve(ctx, case, storage, accel, tol, stall=0):
+    mesh, grid, m, g = case
+    st, pr = dvm.primal_solve(ctx, m, g, 0.01, 0.6, tol=tol, max_iter=400000, storage=storage, accel=accel,
+                              stall_window=stall)
+    ad, ar = dvm.adjoint_solve(ctx, st, tol=tol, max_iter=400000, accel=accel, stall_window=stall)
+    grad = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    out = (pr.J, pr.iters, pr.status, ar.iters, ar.status, grad)
+    ad.close()
+    st.close()
+    return out
+
+
+def test_fp64_mixing_converges_to_the_plain_solution_in_fewer_sweeps(ctx, case):
+    J0, ip0, sp0, ia0, sa0, g0 = _solve(ctx, case, "fp64", None, 1e-10)
+    J1, ip1, sp1, ia1, sa1, g1 = _solve(ctx, case, "fp64", (5, 10), 1e-10)
+    assert sp0 == sp1 == dvm.DVM_OK and sa0 == sa1 == dvm.DVM_OK
+    assert abs(J1 - J0) < 1e-8 * abs(J0)
+    assert np.abs(g1 - g0).max() < 1e-7 * np.abs(g0).max()
+    assert ip1 < ip0 / 2 and ia1 < ia0 / 2, (ip0, ip1, ia0, ia1)
+
+
+def test_fp32_mixing_meets_the_stated_tolerances(ctx, case):
+    J0, *_, g0 = _solve(ctx, case, "fp64", None, 1e-10)
+    J1, ip1, sp1, ia1, sa1, g1 = _solve(ctx, case, "fp32", (5, 10), 1e-9, stall=3000)
+    assert sp1 in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED) and sa1 in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED)
+    assert abs(J1 - J0) < 1e-5 * abs(J0)
+    assert np.abs(g1 - g0).max() < 1e-4 * np.abs(g0).max()
+
+
+def test_bf16_mixing_ends_where_plain_bf16_sweeps_end(ctx, case):
+    """BF16 storage stalls at its rounding floor; with or without mixing it ends at the same
+    solution up to that floor."""
+    J0, *_, g0 = _solve(ctx, case, "bf16", None, 1e-9, stall=3000)
+    J1, ip1, sp1, ia1, sa1, g1 = _solve(ctx, case, "bf16", (5, 10), 1e-9, stall=3000)
+    assert sp1 in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED) and sa1 in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED)
+    assert abs(J1 - J0) < 3e-2 * abs(J0)
+    assert np.abs(g1 - g0).max() < 0.1 * np.abs(g0).max()
+
+
+def test_bad_accel_options_are_rejected(ctx, case):
+    mesh, grid, m, g = case
+    for accel in [(9, 10), (3, 0), (-1, 10)]:
+        with pytest.raises(dvm.DVMError) as e:
+            dvm.primal_solve(ctx, m, g, 0.1, 0.6, tol=1e-6, max_iter=10, accel=accel)
+        assert e.value.status == dvm.DVM_ERR_INVALID_ARG

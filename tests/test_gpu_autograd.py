@@ -1,8 +1,11 @@
 """torch.autograd wrapping of the steady solve: backward = implicit-function adjoint.
 
-The gradient of Cd with respect to the bump amplitudes must match central finite differences of
-the forward (step 1e-4, as for the near-continuum workload) and the oracle's full-discrete
-sensitivity evaluated on the same converged state."""
+The gradient of Cd with respect to the bump amplitudes must match the oracle's full-discrete
+sensitivity evaluated on the same converged state, and central finite differences of the forward.
+The discrete drag is only piecewise smooth in the shape: the upwind choice of a face flips when
+v_k . n_f changes sign as the face turns, so a difference step that straddles such a flip carries
+an error of its own.  On this case one of the six components does at step 1e-4 (5.7e-5 of the
+largest component) and none does at 1e-5, where the differences agree with the adjoint to 1e-6."""
 import numpy as np
 import pytest
 import torch
@@ -52,8 +55,10 @@ def test_drag_gradient_matches_central_differences_and_the_oracle(ctx):
     phi = prob._warm_phi
     g_orc = pr.sens_full(f, phi, mesh.dnodes()) / prob.q_ref
     assert np.abs(g_adj - g_orc).max() < 1e-9 * np.abs(g_orc).max()
-    g_fd = _fd(prob, a0)
-    assert np.abs(g_adj - g_fd).max() < 2e-6 * np.abs(g_fd).max()
+    g_fd = _fd(prob, a0, h=1e-5)
+    assert np.abs(g_adj - g_fd).max() < 1e-6 * np.abs(g_fd).max()
+    g_fd4 = _fd(prob, a0, h=1e-4)
+    assert np.abs(g_adj - g_fd4).max() < 1e-4 * np.abs(g_fd4).max()
     prob.release()
 
 

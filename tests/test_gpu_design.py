@@ -19,7 +19,7 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("ni,nj,P", [(64, 32, 8), (130, 7, 24), (16, 1, 1)])
+@pytest.mark.parametrize("ni,nj,P", [(64, 32, 8), (130, 7, 24), (16, 1, 2)])
 def test_volume_constraint_matches_the_oracle(ctx, ni, nj, P):
     rng = np.random.default_rng(ni + P)
     raw = rng.uniform(-0.01, 0.01, P)
@@ -43,7 +43,7 @@ def _loop(Kn, n_params=6, max_iter=4):
 def _accepted(loop):
     acc = [loop.history[0]]
     for e in loop.history[1:]:
-        if e.ok and e.phi < acc[-1].phi:
+        if e.ok and e.Cd < acc[-1].Cd:
             acc.append(e)
     return acc
 
@@ -53,11 +53,9 @@ def test_design_loop_reduces_drag_under_the_volume_constraint(ctx):
     assert loop.stopped in ("criterion_opt", "max_iter")
     acc = _accepted(loop)
     assert len(acc) >= 3
-    assert all(b.phi < a.phi for a, b in zip(acc, acc[1:]))
     assert acc[-1].Cd < acc[0].Cd
-    # the penalty keeps the area near V_min: at most 2% below it
-    assert acc[-1].Q <= 0.02 * loop.v_min
-    # criterion_opt was applied to successive accepted objectives
+    # every evaluated design keeps the area >= V_min (Q is affine in alpha; projection is exact)
+    assert all(e.Q <= 1e-12 for e in loop.history if e.ok)
     if loop.stopped == "criterion_opt":
         assert design.criterion_opt(acc[-2].Cd, acc[-1].Cd)
 
@@ -69,7 +67,8 @@ def test_concurrent_loops_share_one_served_batch(ctx):
     for loop in loops:
         assert loop.done
         acc = _accepted(loop)
-        assert len(acc) >= 2 and acc[-1].phi < acc[0].phi
+        assert len(acc) >= 2 and acc[-1].Cd < acc[0].Cd
+        assert all(e.Q <= 1e-12 for e in loop.history if e.ok)
     ref = design.DesignLoop(48, 16, W.velocity_grid(12, 4.0), W.Flow(1.0, 0.6), n_params=6, max_iter=0)
     from paper_2501_00923_gb300.autograd import DragProblem
     prob = DragProblem(ctx, 48, 16, ref.grid, ref.flow, storage="fp32", tol=1e-7, stall_window=20000)
