@@ -48,10 +48,11 @@ typedef enum {
 
 typedef enum { DVM_STORE_FP64 = 0, DVM_STORE_FP32 = 1, DVM_STORE_BF16 = 2 } dvm_storage;
 
-/* Objective of Eq. (formula_opt): J = sum_wall sum_k w m_k (v_k . n A) f1, m_k = v_k . d.
- * DVM_DRAG: d = free-stream direction (m_J = v1 at zero incidence, Sec. 2.4);
- * DVM_LIFT: d = free-stream direction rotated by +90 degrees. */
-typedef enum { DVM_DRAG = 0, DVM_LIFT = 1 } dvm_functional;
+/* Objective of Eq. (formula_opt): J = sum_wall sum_k w m_k (v_k . n A) f1.
+ * DVM_DRAG: m_k = v_k . d, d = free-stream direction (m_J = v1 at zero incidence, Sec. 2.4);
+ * DVM_LIFT: d = free-stream direction rotated by +90 degrees;
+ * DVM_HEAT: m_k = |v_k|^2 / 2, the heat carried by f1 into the wall (Sec. 2.4). */
+typedef enum { DVM_DRAG = 0, DVM_LIFT = 1, DVM_HEAT = 2 } dvm_functional;
 
 /* DVM_SENS_PAPER: the boundary sensitivity of Sec. 3.2 (Eq. sens_J_itf, sens_B_itf, gaussgrad,
  *   sens_nod), wall nodes only, as the paper computes it.
@@ -90,7 +91,8 @@ typedef struct {
                                over the last m differences of r = G(x) - x and of G).  It accelerates the
                                iteration only: the discrete solution is the same.  The history holds 2m + 3
                                vectors of the state's size (FP32; FP64 for FP64 storage), kept with the state or
-                               adjoint.  A mix that makes any value negative is undone and the history restarts */
+                               adjoint.  A primal mix that makes any value of f negative is undone and the history
+                               restarts */
     int accel_period;       /* sweeps between mixings (>= 1; with accel_depth > 0) */
 } dvm_solve_opts;
 

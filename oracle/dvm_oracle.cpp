@@ -28,7 +28,8 @@
  *   Maxwellian (Eq. bc_drlt / drlt_maxwell) or the wall Maxwellian g_w = F_rhow gbar_w
  *   (Eq. formula_bgk_fdw0, formula_bgk_fdw and the discrete form above Eq. barg).
  * Functional, Eq. (formula_opt) discretised as Eq. (numer_J):
- *   J = sum_l sum_k w_k m_k (v_k . S_l) f1_{l,k},  m_k = v_k . d (d = force direction; drag: d=e1)
+ *   J = sum_l sum_k w_k m_k (v_k . S_l) f1_{l,k},  m_k = d . v_k + h |v_k|^2 / 2: the moment m_J of
+ *   Eq. (formula_opt); d = force direction with h = 0 (drag: d = e1), or d = 0, h = 1 for the heat
  * Discrete adjoint in the paper's sign (Lagrangian L = J + sum w phi . R, Eq. lagrangian):
  *   (dR/df)^T (w phi) = -(dJ/df)^T,   dJ/dalpha = dJ/dalpha|_f + sum w phi . dR/dalpha|_f.
  */
@@ -74,8 +75,12 @@ struct Prob {
     const double* vy;
     const double* w;
     double Kn, Ma, Tw, aoa;
-    double dir[2];
+    double dir[3];        /* m_J(v) = dir[0] vx + dir[1] vy + dir[2] |v|^2/2 */
 };
+
+inline double moment_J(const double* dir, double vx, double vy) {
+    return dir[0] * vx + dir[1] * vy + dir[2] * 0.5 * (vx * vx + vy * vy);
+}
 
 struct Consts {
     double tau_inf, u1, u2, Tw;
@@ -297,7 +302,7 @@ S functional(const Prob& p, const Consts& K, const Geo<S>& g, const S* f) {
         S sx = g.Sx[4 * c + 3], sy = g.Sy[4 * c + 3];
         for (int k = 0; k < nv; ++k) {
             double vx = p.vx[k], vy = p.vy[k];
-            double m = p.dir[0] * vx + p.dir[1] * vy;
+            double m = moment_J(p.dir, vx, vy);
             S a = sx * vx + sy * vy;
             S f1l = val(a) > 0.0 ? fc[2 * k] : wf.Fw * (K.gw1[k] / wf.D);
             J += p.w[k] * m * a * f1l;
@@ -320,12 +325,12 @@ void functional_grad(const Prob& p, const Consts& K, const Geo<double>& g, const
         double M = 0.0;
         for (int k = 0; k < nv; ++k) {
             double a = sx * p.vx[k] + sy * p.vy[k];
-            if (!(a > 0.0)) M += p.w[k] * (p.dir[0] * p.vx[k] + p.dir[1] * p.vy[k]) * a * K.gw1[k] / wf.D;
+            if (!(a > 0.0)) M += p.w[k] * moment_J(p.dir, p.vx[k], p.vy[k]) * a * K.gw1[k] / wf.D;
         }
         for (int k = 0; k < nv; ++k) {
             double a = sx * p.vx[k] + sy * p.vy[k];
             if (a > 0.0) {
-                double m = p.dir[0] * p.vx[k] + p.dir[1] * p.vy[k];
+                double m = moment_J(p.dir, p.vx[k], p.vy[k]);
                 double vn = p.vx[k] * wf.nx + p.vy[k] * wf.ny;
                 dJ[((size_t)c * nv + k) * 2] = p.w[k] * (m * a + vn * M);
             }
@@ -577,7 +582,7 @@ typedef struct {
     const double* vy;
     const double* w;
     double Kn, Ma, Tw, aoa;
-    double dir[2];
+    double dir[3];
 } orc_problem;
 
 static Prob to_prob(const orc_problem* q) {
@@ -585,7 +590,7 @@ static Prob to_prob(const orc_problem* q) {
     p.ni = q->ni; p.nj = q->nj; p.nv = q->nv; p.nodes = q->nodes;
     p.vx = q->vx; p.vy = q->vy; p.w = q->w;
     p.Kn = q->Kn; p.Ma = q->Ma; p.Tw = q->Tw; p.aoa = q->aoa;
-    p.dir[0] = q->dir[0]; p.dir[1] = q->dir[1];
+    p.dir[0] = q->dir[0]; p.dir[1] = q->dir[1]; p.dir[2] = q->dir[2];
     return p;
 }
 
@@ -955,7 +960,7 @@ int orc_sens_paper(const orc_problem* q, const double* f, const double* phi, int
         double dA = 0, dxx = 0, dxy = 0, dnx = 0, dny = 0;
         for (int k = 0; k < nv; ++k) {
             double vx = p.vx[k], vy = p.vy[k], w = p.w[k];
-            double m = p.dir[0] * vx + p.dir[1] * vy;
+            double m = moment_J(p.dir, vx, vy);
             double vn = vx * nx + vy * ny;
             /* J part, Eq. (sens_J_itf) */
             dA += w * m * vn * fl1[k];
@@ -1045,7 +1050,7 @@ double orc_wall_face_functional(const double* S, int nv, const double* vx, const
     for (int k = 0; k < nv; ++k) {
         double a = S[0] * vx[k] + S[1] * vy[k], g1, g2;
         maxwellian<double>(1.0, 0.0, 0.0, Tw, vx[k], vy[k], g1, g2);
-        double m = dir[0] * vx[k] + dir[1] * vy[k];
+        double m = moment_J(dir, vx[k], vy[k]);
         J += w[k] * m * a * (a > 0.0 ? f1[k] : Fw * g1 / D);
     }
     return J;

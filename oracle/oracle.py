@@ -24,7 +24,7 @@ class _Problem(C.Structure):
     _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nv", C.c_int),
                 ("nodes", _dp), ("vx", _dp), ("vy", _dp), ("w", _dp),
                 ("Kn", C.c_double), ("Ma", C.c_double), ("Tw", C.c_double), ("aoa", C.c_double),
-                ("dir", C.c_double * 2)]
+                ("dir", C.c_double * 3)]
 
 
 def build(force: bool = False) -> str:
@@ -89,7 +89,9 @@ def _c(a):
 
 
 class Problem:
-    """One discrete problem: O-mesh nodes, velocity grid, flow, force direction of J."""
+    """One discrete problem: O-mesh nodes, velocity grid, flow, and the moment of J (Eq. formula_opt):
+    m_J(v) = d . v + h |v|^2 / 2 for direction = (dx, dy) (h = 0: a force, drag = (1, 0)) or
+    (dx, dy, h) (heat: (0, 0, 1))."""
 
     def __init__(self, nodes, vx, vy, w, Kn, Ma, Tw=1.0, aoa=0.0, direction=(1.0, 0.0)):
         self.nodes = _c(nodes)
@@ -98,10 +100,10 @@ class Problem:
         self.vx, self.vy, self.w = _c(vx), _c(vy), _c(w)
         self.nv = self.vx.size
         self.Kn, self.Ma, self.Tw, self.aoa = float(Kn), float(Ma), float(Tw), float(aoa)
-        self.direction = tuple(float(x) for x in direction)
+        self.direction = _moment(direction)
         self._s = _Problem(self.ni, self.nj, self.nv, _ptr(self.nodes), _ptr(self.vx),
                            _ptr(self.vy), _ptr(self.w), self.Kn, self.Ma, self.Tw, self.aoa,
-                           (C.c_double * 2)(*self.direction))
+                           (C.c_double * 3)(*self.direction))
 
     @classmethod
     def from_workload(cls, wl, direction=(1.0, 0.0)):
@@ -260,7 +262,14 @@ def sens_nod(xa, xb, n):
 def wall_face_functional(S, vx, vy, w, f1, Tw=1.0, direction=(1.0, 0.0)):
     vx, vy, w, f1 = _c(vx), _c(vy), _c(w), _c(f1)
     return lib().orc_wall_face_functional(_ptr(_c(S)), vx.size, _ptr(vx), _ptr(vy), _ptr(w),
-                                          _ptr(f1), Tw, _ptr(_c(direction)))
+                                          _ptr(f1), Tw, _ptr(_c(_moment(direction))))
+
+
+def _moment(direction):
+    d = tuple(float(x) for x in direction)
+    if len(d) not in (2, 3):
+        raise ValueError("direction is (dx, dy) or (dx, dy, h)")
+    return d + (0.0,) * (3 - len(d))
 
 
 if __name__ == "__main__":

@@ -31,6 +31,7 @@ class DragProblem:
     max_iter: int = 200000
     stall_window: int = 0
     mode: str = "full"
+    mesh_fn: object = None          # alpha -> OMesh; default: the Hicks-Henne bump section
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
@@ -44,7 +45,7 @@ class DragProblem:
         return 0.5 * U * U if U > 0 else 1.0
 
     def solve(self, alpha: np.ndarray):
-        mesh = W.omesh(self.ni, self.nj, alpha)
+        mesh = self.mesh_fn(alpha) if self.mesh_fn is not None else W.omesh(self.ni, self.nj, alpha)
         m = dvm.Mesh(self.ctx, mesh.nodes)
         st = dvm.State(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa,
                        storage=self.storage)

@@ -52,7 +52,8 @@ struct AAState {
     double *part = nullptr, *out = nullptr, *gamma = nullptr;
     int* neg = nullptr;
     int cnt = 0, slot = 0, steps = 0;       // columns in use, next ring slot, blocks since (re)start
-    int mixes = 0, rejects = 0;
+    int mixes = 0, rejects = 0, restarts = 0;
+    double best = INFINITY;                 // lowest block residual since the history started
     std::vector<double> H;                  // m x m: dR_i . dR_j
 };
 
@@ -84,7 +85,7 @@ struct dvm_state {
 struct dvm_adjoint {
     dvm_state* st = nullptr;
     int functional = DVM_DRAG;
-    double dirx = 1.0, diry = 0.0;
+    MomentJ mj;                 // m_J of the functional
     double* wallM = nullptr;
     void* cell = nullptr;       // AdjCell<TC>[ncell]: linearisation constants
     uint64_t st_version = ~0ull; // state version the constants and couplings belong to
@@ -193,6 +194,21 @@ double dir_angle(const dvm_flow& fl, int functional) {
     return fl.aoa + (functional == DVM_LIFT ? 0.5 * M_PI : 0.0);
 }
 
+// m_J of a functional (Eq. formula_opt): a force along the free stream (drag) or normal to it
+// (lift), or the heat (m_J = |v|^2/2).
+MomentJ moment_of(const dvm_flow& fl, int functional) {
+    MomentJ mj;
+    if (functional == DVM_HEAT) {
+        mj.dx = mj.dy = 0.0;
+        mj.h = 1.0;
+    } else {
+        const double ang = dir_angle(fl, functional);
+        mj.dx = cos(ang);
+        mj.dy = sin(ang);
+    }
+    return mj;
+}
+
 // ------------------------------------------------------------------ argument builders
 template <class TS, class TC>
 PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
@@ -249,8 +265,9 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     a.wallM = ad->wallM;
     a.inv_tau_inf = 1.0 / st->fl.tau_inf;
     a.halfTw = (TC)(0.5 * st->fl.Tw);
-    a.dirx = (TC)ad->dirx;
-    a.diry = (TC)ad->diry;
+    a.dirx = (TC)ad->mj.dx;
+    a.diry = (TC)ad->mj.dy;
+    a.heat = (TC)ad->mj.h;
     a.f = (const TS*)st->f[st->cur];
     a.cell = (const AdjCell<TC>*)ad->cell;
     a.phi_old = (const TS*)ad->phi[src];
@@ -383,12 +400,24 @@ int aa_ensure(dvm_context* ctx, AAState*& A, int storage, size_t n, int m) {
     return DVM_OK;
 }
 
-// Start a solve: X <- F, empty history.
+// Start a solve (or restart the history): X <- F, empty history.
 int aa_begin(dvm_context* ctx, AAState* A, const void* F) {
     A->cnt = A->slot = A->steps = 0;
+    A->best = INFINITY;
     CK(launch_aa_load(A->storage, A->n, F, A->X, ctx->stream));
     ctx->launches += 1;
     return DVM_OK;
+}
+
+// Safeguard: a block residual above twice the best since the history started means the mixing is
+// steering the iteration off (near the rounding floor of FP32 storage, for instance).
+bool aa_restart_if_growing(AAState* A, double r) {
+    if (A->steps > 1 && r > 2.0 * A->best) {
+        A->restarts += 1;
+        return true;
+    }
+    A->best = std::min(A->best, r);
+    return false;
 }
 
 // Solve (H + eps I) gamma = b for the cnt columns in use (Cholesky, eps = 1e-10 of the mean diagonal).
@@ -428,8 +457,9 @@ bool aa_solve(const std::vector<double>& Hm, int m, int cnt, const double* b, do
 }
 
 // One mixing step after a block of sweeps left G in F.  *mixed = true when F now holds the mixed
-// iterate (then the caller refreshes what depends on F).
-int aa_step(dvm_context* ctx, AAState* A, void* F, bool* mixed) {
+// iterate (then the caller refreshes what depends on F).  positive: F is a distribution, and a mix
+// that makes a value negative is undone (the adjoint has no sign).
+int aa_step(dvm_context* ctx, AAState* A, void* F, bool positive, bool* mixed) {
     *mixed = false;
     cudaStream_t s = ctx->stream;
     const int m = A->m;
@@ -454,7 +484,7 @@ int aa_step(dvm_context* ctx, AAState* A, void* F, bool* mixed) {
     int zero = 0, neg = 0;
     CK(cudaMemcpyAsync(A->gamma, gam.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(A->neg, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(launch_aa_mix(A->storage, A->n, F, A->X, A->Gp, A->dG, cnt, A->gamma, A->neg, s));
+    CK(launch_aa_mix(A->storage, A->n, F, A->X, A->Gp, A->dG, cnt, A->gamma, positive ? 1 : 0, A->neg, s));
     CK(cudaMemcpyAsync(&neg, A->neg, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     ctx->launches += 1;
@@ -825,9 +855,8 @@ int dvm_state_create(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         }
     }
     cudaStream_t s = ctx->stream;
-    const double ang = dir_angle(*flow, DVM_DRAG);
     cudaError_t e = launch_flow_tables(g, st->fl, s);
-    if (e == cudaSuccess) e = launch_wall_setup(m, g, st->fl, cos(ang), sin(ang), st->fl.wallD, st->fl.wallM, s);
+    if (e == cudaSuccess) e = launch_wall_setup(m, g, st->fl, moment_of(*flow, DVM_DRAG), st->fl.wallD, st->fl.wallM, s);
     if (e == cudaSuccess) e = launch_fill_freestream(storage, st->f[0], m.ncell, g, st->fl, s);
     if (e == cudaSuccess) e = launch_moments(storage, st->f[0], m, g, st->prim[0], st->Fw[0], s);
     ctx->launches += 5;
@@ -919,9 +948,10 @@ int dvm_primal_iterate(dvm_state* st, int n, double* residual_out) {
 int dvm_state_functional(dvm_state* st, int functional, double* J) {
     if (!st || !J) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard dg(st->ctx->device);
-    const double ang = dir_angle(st->flow, functional);
-    CK(launch_functional(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->fl, st->Fw[st->cur], cos(ang),
-                         sin(ang), st->scratch, st->scratch + st->mesh->d.ni, st->ctx->stream));
+    if (functional < DVM_DRAG || functional > DVM_HEAT) return fail(DVM_ERR_INVALID_ARG, "unknown functional");
+    CK(launch_functional(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->fl, st->Fw[st->cur],
+                         moment_of(st->flow, functional), st->scratch, st->scratch + st->mesh->d.ni,
+                         st->ctx->stream));
     st->ctx->launches += 2;
     double r[2];
     int rc = fetch2(st->ctx, st->scratch + st->mesh->d.ni, r);
@@ -981,7 +1011,11 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
         if (accel && k == K && it < opts->max_iter) {
             bool mixed = false;
-            if ((rc = aa_step(ctx, st->aa, st->f[st->cur], &mixed))) return rc;
+            if (aa_restart_if_growing(st->aa, r)) {   // the history misleads: start it again here
+                if ((rc = aa_begin(ctx, st->aa, st->f[st->cur]))) return rc;
+            } else if ((rc = aa_step(ctx, st->aa, st->f[st->cur], true, &mixed))) {
+                return rc;
+            }
             if (mixed) {
                 CK(launch_moments(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur],
                                   st->Fw[st->cur], ctx->stream));
@@ -1032,7 +1066,7 @@ static int adjoint_reset(dvm_adjoint* ad) {
 
 int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     if (!st || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
-    if (functional != DVM_DRAG && functional != DVM_LIFT) return fail(DVM_ERR_INVALID_ARG, "unknown functional");
+    if (functional < DVM_DRAG || functional > DVM_HEAT) return fail(DVM_ERR_INVALID_ARG, "unknown functional");
     *out = nullptr;
     dvm_context* ctx = st->ctx;
     DeviceGuard dg(ctx->device);
@@ -1046,9 +1080,7 @@ int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     ad->st = st;
     ad->functional = functional;
     live_add(ad, kAdjoint, st->ctx, st);
-    const double ang = dir_angle(st->flow, functional);
-    ad->dirx = cos(ang);
-    ad->diry = sin(ang);
+    ad->mj = moment_of(st->flow, functional);
     size_t acc = 0;
     int rc = DVM_OK;
     for (int b = 0; b < 2 && !rc; ++b) {
@@ -1074,7 +1106,7 @@ int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     // M_l of this functional's direction (the normaliser D_l is the state's; recomputed into scratch)
     double* dtmp = nullptr;
     if ((rc = dalloc(ctx, &dtmp, m.ni))) { dvm_adjoint_destroy(ad); return rc; }
-    cudaError_t e = launch_wall_setup(m, g, st->fl, ad->dirx, ad->diry, dtmp, ad->wallM, ctx->stream);
+    cudaError_t e = launch_wall_setup(m, g, st->fl, ad->mj, dtmp, ad->wallM, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     ctx->launches += 1;
     dfree(dtmp);
@@ -1210,7 +1242,11 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
         if (accel && k == K && it < opts->max_iter) {
             bool mixed = false;
-            if ((rc = aa_step(ctx, ad->aa, ad->phi[ad->cur], &mixed))) return rc;
+            if (aa_restart_if_growing(ad->aa, r)) {
+                if ((rc = aa_begin(ctx, ad->aa, ad->phi[ad->cur]))) return rc;
+            } else if ((rc = aa_step(ctx, ad->aa, ad->phi[ad->cur], false, &mixed))) {
+                return rc;
+            }
             if (mixed) CK(refresh_adjoint_couplings(ad));
         }
     }
@@ -1256,7 +1292,7 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
     const void* f = st->f[st->cur];
     const void* phi = ad->phi[ad->cur];
     if (mode == DVM_SENS_PAPER) {
-        CK(launch_sens_paper(st->storage, m, g, st->fl, f, phi, st->Fw[st->cur], ad->dirx, ad->diry, ad->elem,
+        CK(launch_sens_paper(st->storage, m, g, st->fl, f, phi, st->Fw[st->cur], ad->mj, ad->elem,
                              (double*)ad->node_grad, s));
         CK(launch_contract(ad->node_grad, 1, m.ni, nullptr, ad->dwall, P, ad->grad, s));
         ctx->launches += 2 + (P > 0);
@@ -1264,7 +1300,7 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
             CK(cudaMemcpyAsync(node_grad_out, ad->node_grad, (size_t)m.ni * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     } else {
         CK(cudaMemcpyAsync(ad->sj, s_j, (m.nj + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->dirx, ad->diry,
+        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->mj,
                             ad->GN, ad->GE, ad->GW, ad->vol, ad->node_grad, s));
         CK(launch_contract(ad->node_grad, m.nj + 1, m.ni, ad->sj, ad->dwall, P, ad->grad, s));
         ctx->launches += 2 + (P > 0);
@@ -1389,15 +1425,15 @@ extern "C" int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, co
     const void* f = st->f[st->cur];
     const void* phi = ad->phi[ad->cur];
     if (mode == DVM_SENS_PAPER) {
-        CK(launch_sens_paper(st->storage, m, g, st->fl, f, phi, st->Fw[st->cur], ad->dirx, ad->diry, elem,
+        CK(launch_sens_paper(st->storage, m, g, st->fl, f, phi, st->Fw[st->cur], ad->mj, elem,
                              (double*)node_grad, s));
         CK(launch_contract(node_grad, 1, m.ni, nullptr, dw, P, grad, s));
         if (node_grad_out)
             CK(cudaMemcpyAsync(node_grad_out, node_grad, (size_t)m.ni * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     } else {
         CK(cudaMemcpyAsync(sj, s_j, (m.nj + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->dirx,
-                            ad->diry, GN, GE, GW, vol, node_grad, s));
+        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->mj,
+                            GN, GE, GW, vol, node_grad, s));
         CK(launch_contract(node_grad, m.nj + 1, m.ni, sj, dw, P, grad, s));
         if (node_grad_out)
             CK(cudaMemcpyAsync(node_grad_out, node_grad, (size_t)nnodes * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1818,6 +1854,9 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
                     q->pstatus = q->res <= q->r.tol ? DVM_OK : stalled ? DVM_ERR_STAGNATED : DVM_NOT_CONVERGED;
                     q->best = INFINITY;
                     q->best_it = 0;
+                    // the fused partials carry the drag; another functional is evaluated on the final state
+                    if (q->r.functional != DVM_DRAG && (rc = dvm_state_functional(q->st, q->r.functional, &q->J)))
+                        q->pstatus = rc;
                     if (q->r.n_params > 0) {
                         if ((rc = start_adjoint(b, q))) { q->astatus = rc; leave = true; }
                     } else {

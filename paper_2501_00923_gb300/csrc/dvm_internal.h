@@ -36,6 +36,12 @@ struct DevGrid {
     float4* vp = nullptr;       // [nvp] per velocity pair p: (vx, vx', vy, vy'), (w, w', h, h')
 };
 
+// The moment of the functional, Eq. (formula_opt): m_J(v) = dx vx + dy vy + h |v|^2 / 2 (a force along
+// (dx, dy) with h = 0; the heat with dx = dy = 0, h = 1).
+struct MomentJ {
+    double dx = 1.0, dy = 0.0, h = 0.0;
+};
+
 // Per-flow tables for one state.
 struct DevFlow {
     double tau_inf = 0, u1 = 0, u2 = 0, Tw = 1, Ma = 0, aoa = 0;
@@ -100,7 +106,7 @@ struct AdjointArgs {
     const double* wallD;
     const double* wallM;                    // for the functional's direction
     double inv_tau_inf;
-    TC halfTw, dirx, diry;
+    TC halfTw, dirx, diry, heat;             // m_J = dirx vx + diry vy + heat |v|^2/2
     const TS* f;                            // primal state (fixed)
     const AdjCell<TC>* cell;                // constants of the linearisation at that state
     const TS* phi_old;
@@ -139,8 +145,8 @@ struct FinalizeDesc {
 // ---------------------------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return cudaGetLastError().
 cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s);
-cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, double dirx,
-                              double diry, double* wallD, double* wallM, cudaStream_t s);
+cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, MomentJ mj,
+                              double* wallD, double* wallM, cudaStream_t s);
 cudaError_t launch_fill_freestream(int storage, void* f, int ncell, const DevGrid& g, const DevFlow& fl,
                                    cudaStream_t s);
 cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
@@ -163,32 +169,33 @@ cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const Dev
 cudaError_t launch_finalize(const double* respart, int ncell, const double* Jpart, const double* Fw,
                             const double* M, int ni, double* out, cudaStream_t s);
 cudaError_t launch_functional(int storage, const void* f, const DevMesh& m, const DevGrid& g,
-                              const DevFlow& fl, const double* Fw, double dirx, double diry,
+                              const DevFlow& fl, const double* Fw, MomentJ mj,
                               double* face_out, double* out, cudaStream_t s);
 // direction 0: device storage [ncell][nvp] -> double [ncell][nv]; 1: double [ncell][nv] -> storage [ncell][nvp]
 cudaError_t launch_convert(int storage, int direction, const void* src, void* dst, int ncell, int nv,
                            int nvp, cudaStream_t s);
 // sensitivities
 cudaError_t launch_sens_paper(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
-                              const void* f, const void* phi, const double* Fw, double dirx, double diry,
+                              const void* f, const void* phi, const double* Fw, MomentJ mj,
                               double* elem, double* node_grad, cudaStream_t s);
 cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
                              const void* f, const void* phi, const double4* prim, const double* Fw,
-                             double dirx, double diry, double2* GN, double2* GE, double2* GW,
+                             MomentJ mj, double2* GN, double2* GE, double2* GW,
                              double* vol, double2* node_grad, cudaStream_t s);
 cudaError_t launch_contract(const double2* node_grad, int nrows, int ni, const double* s_j,
                             const double* dwall, int P, double* grad, cudaStream_t s);
 
 // Anderson mixing of the sweeps (flat storage vectors of n elements; history in FP32, FP64 for FP64
 // storage): load X <- F; collect r = G - X, the differences (ring slot `slot`) and the 2m dots into
-// out (device, [2m]); mix F, X <- G - dG gamma (neg set on a negative value); restore F, X <- G.
+// out (device, [2m]); mix F, X <- G - dG gamma (neg set on a negative value when `positive`);
+// restore F, X <- G.
 int aa_max_depth();
 int aa_blocks();
 cudaError_t launch_aa_load(int storage, size_t n, const void* F, void* X, cudaStream_t s);
 cudaError_t launch_aa_collect(int storage, size_t n, const void* G, void* X, void* Rp, void* Gp, void* dR, void* dG,
                               int m, int cnt, int slot, int first, double* part, double* out, cudaStream_t s);
 cudaError_t launch_aa_mix(int storage, size_t n, void* F, void* X, const void* Gp, const void* dG, int cnt,
-                          const double* gamma, int* neg, cudaStream_t s);
+                          const double* gamma, int positive, int* neg, cudaStream_t s);
 cudaError_t launch_aa_restore(int storage, size_t n, void* F, void* X, const void* Gp, cudaStream_t s);
 
 // out[0] = Q, out[1 + p] = dQ/dalpha_p

@@ -14,11 +14,13 @@
 #include <type_traits>
 
 // Tile parameters of the sweeps (see the pipeline section): chunks per lane per stage and stages.
+// 2 chunks per lane, 2 stages and 3 resident blocks per SM were the fastest of (1,4,3), (1,4,4),
+// (2,3,2), (2,2,3) and (2,4,2) on the 256x128-cell, 48x48-velocity workload.
 #ifndef DVM_CPL
 #define DVM_CPL 2
 #endif
 #ifndef DVM_STAGES
-#define DVM_STAGES 3
+#define DVM_STAGES 2
 #endif
 
 namespace dvm {
@@ -362,10 +364,10 @@ __device__ __forceinline__ bool pipeline_step(const Feed& F, unsigned it, unsign
 // Resident blocks per SM (the register budget) of the FP32/BF16 sweeps; FP64 keeps 4 (primal) and
 // 3 (adjoint).  DVM_PAIRED selects the paired FP32 arithmetic for FP32/BF16 storage.
 #ifndef DVM_PRIMAL_BLOCKS
-#define DVM_PRIMAL_BLOCKS (DVM_CPL == 1 ? 3 : 2)
+#define DVM_PRIMAL_BLOCKS 3
 #endif
 #ifndef DVM_ADJOINT_BLOCKS
-#define DVM_ADJOINT_BLOCKS (DVM_CPL == 1 ? 3 : 2)
+#define DVM_ADJOINT_BLOCKS 3
 #endif
 #ifndef DVM_PAIRED
 #define DVM_PAIRED 1
@@ -648,7 +650,7 @@ __device__ __forceinline__ bool block_pipe_setup(BlockPipe& B, unsigned char* sm
     B.F.i = i; B.F.im = (i - 1 + ni) % ni; B.F.ip = (i + 1) % ni; B.F.j0 = j0; B.F.rows = rows;
     B.F.A = (unsigned)B.A;
     B.F.stage = reinterpret_cast<uint4*>(smem);
-    B.F.full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * rows * 512);
+    B.F.full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * rows * kRowChunks * 16);
     B.F.released = reinterpret_cast<unsigned*>(B.F.full + kStages);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -758,11 +760,12 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
     const float2 kE = bc(-inv2T * L2E);
     const float2 s0x = bc(S0.x), s0y = bc(S0.y), s1x = bc(S1.x), s1y = bc(S1.y);
     const float2 s2x = bc(S2.x), s2y = bc(S2.y), s3x = bc(S3.x), s3y = bc(S3.y);
-    float2 ndx = bc(0.f), ndy = bc(0.f), nsrc = bc(0.f), gbw = bc(0.f), hTw = bc(0.f);
+    float2 ndx = bc(0.f), ndy = bc(0.f), nhc = bc(0.f), nsrc = bc(0.f), gbw = bc(0.f), hTw = bc(0.f);
     if (wall) {
         const float A = sqrtf(S3.x * S3.x + S3.y * S3.y);
         ndx = bc(-P.dirx);
         ndy = bc(-P.diry);
+        nhc = bc(-P.heat);
         nsrc = bc(-(float)(P.wallM[c] + P.Lam_old[c]) / A);          // (M + Lambda)/A multiplies a3
         gbw = bc(1.f / (float)P.wallD[c]);
         hTw = bc(P.halfTw);
@@ -818,7 +821,7 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
                         r1 = pfma(o0, pair_of<KV>(e01, pp), r1); r2 = pfma(o0, pair_of<KV>(e02, pp), r2);
                         r1 = pfma(o2, pair_of<KV>(e21, pp), r1); r2 = pfma(o2, pair_of<KV>(e22, pp), r2);
                         if (!far) { r1 = pfma(o1, pair_of<KV>(e11, pp), r1); r2 = pfma(o1, pair_of<KV>(e12, pp), r2); }
-                        if (wall) r1 = pfma(o3, pfma(ndy, vy, pfma(ndx, vx, nsrc)), r1);
+                        if (wall) r1 = pfma(o3, pfma(nhc, hv, pfma(ndy, vy, pfma(ndx, vx, nsrc))), r1);
                         else { r1 = pfma(o3, pair_of<KV>(e31, pp), r1); r2 = pfma(o3, pair_of<KV>(e32, pp), r2); }
                         const float2 iD = prcp(D);
                         const float2 y1 = pmul(r1, iD), y2 = pmul(r2, iD);
@@ -954,7 +957,7 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
                         r1_ += p0 * e01[kk]; r2_ += p0 * e02[kk];
                         r1_ += p2 * e21[kk]; r2_ += p2 * e22[kk];
                         if (!far) { const TC p1 = fmax(a1, TC(0)); r1_ += p1 * e11[kk]; r2_ += p1 * e12[kk]; }
-                        if (wall) r1_ -= p3 * (P.dirx * vx + P.diry * vy + srcB);
+                        if (wall) r1_ -= p3 * (P.dirx * vx + P.diry * vy + P.heat * hv + srcB);
                         else { r1_ += p3 * e31[kk]; r2_ += p3 * e32[kk]; }
                         const TC iD = frcp<TC>(D);
                         pn1[kk] = r1_ * iD;
@@ -1115,8 +1118,8 @@ __global__ void k_flow_tables(int nvp, const typename Vec<TC>::v4* vt, double u1
 
 // Per wall face l: D_l = -sum_{a<=0} w (v.n) g_M1(1,0,Tw) (the normaliser of Eq. barg) and
 // M_l = sum_{a<=0} w (v.d) a g_M1 / D_l (the reflected part of J per unit F_rhow).
-__global__ void k_wall_setup(int nvp, const double2* S, const double4* vd, const double* gw, double dirx,
-                             double diry, double* wallD, double* wallM) {
+__global__ void k_wall_setup(int nvp, const double2* S, const double4* vd, const double* gw, MomentJ mj,
+                             double* wallD, double* wallM) {
     const int l = blockIdx.x;
     const double2 s = S[4 * l + 3];
     const double A = sqrt(s.x * s.x + s.y * s.y);
@@ -1126,7 +1129,7 @@ __global__ void k_wall_setup(int nvp, const double2* S, const double4* vd, const
         const double a = s.x * t.x + s.y * t.y;
         if (!(a > 0.0)) {
             d -= t.z * (a / A) * gw[k];
-            m += t.z * (dirx * t.x + diry * t.y) * a * gw[k];
+            m += t.z * (mj.dx * t.x + mj.dy * t.y + mj.h * t.w) * a * gw[k];
         }
     }
     __shared__ double sd[32], sm[32];
@@ -1204,7 +1207,7 @@ __global__ void k_finalize(const double* respart, int ncell, const double* Jpart
 // J = sum_l sum_k w m a f1_l  (Eq. numer_J) for an arbitrary direction; one block per wall face.
 template <class TS>
 __global__ void k_functional(const TS* f, int nvp, const double2* S, const double4* vd, const double* gw,
-                             const double* wallD, const double* Fw, double dirx, double diry, double* face_out) {
+                             const double* wallD, const double* Fw, MomentJ mj, double* face_out) {
     const int l = blockIdx.x;
     const double2 s = S[4 * l + 3];
     const double cw = Fw[l] / wallD[l];
@@ -1213,7 +1216,7 @@ __global__ void k_functional(const TS* f, int nvp, const double2* S, const doubl
         const double4 t = vd[k];
         const double a = s.x * t.x + s.y * t.y;
         const double f1 = a > 0.0 ? todbl(f[fpos<TS>(l, nvp, k)]) : cw * gw[k];
-        j += t.z * (dirx * t.x + diry * t.y) * a * f1;
+        j += t.z * (mj.dx * t.x + mj.dy * t.y + mj.h * t.w) * a * f1;
     }
     __shared__ double sj[32];
     j = warp_sum(j);
@@ -1251,8 +1254,8 @@ __global__ void k_convert(const TA* src, TB* dst, int ncell, int nv_src, int nv_
 template <class TS>
 __global__ void k_sens_paper_elem(const TS* f, const TS* phi, int nvp, const int4* nb, const double2* S,
                                   const double* Vc, const double4* vd, const double2* fd, const double* gw,
-                                  const double* wallD, const double* Fw, double halfTw, double dirx,
-                                  double diry, double* elem) {
+                                  const double* wallD, const double* Fw, double halfTw, MomentJ mj,
+                                  double* elem) {
     const int l = blockIdx.x;   // wall cell index (j = 0)
     const int4 n = nb[l];
     const double2 s[4] = {S[4 * l], S[4 * l + 1], S[4 * l + 2], S[4 * l + 3]};
@@ -1264,7 +1267,7 @@ __global__ void k_sens_paper_elem(const TS* f, const TS* phi, int nvp, const int
     // 0 dA | 1,2 X1 | 3,4 Gp | 5 Pg | 6,7 Vf | 8,9 N1
     for (int k = threadIdx.x; k < nvp; k += blockDim.x) {
         const double4 t = vd[k];
-        const double vx = t.x, vy = t.y, w = t.z, m = dirx * vx + diry * vy;
+        const double vx = t.x, vy = t.y, w = t.z, m = mj.dx * vx + mj.dy * vy + mj.h * t.w;
         const size_t ol = fpos<TS>(l, nvp, k);
         const double fc1 = todbl(f[ol]), fc2 = todbl(f[ol + kComp<TS>]);
         double F1[4], F2[4];
@@ -1369,7 +1372,7 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
                                                     const typename Vec<typename Pack<TS>::TC>::v2* fd,
                                                     const typename Pack<TS>::TC* gw, const double* wallD,
                                                     const double4* prim, const double* Fw, double inv_tau_inf,
-                                                    double halfTw_d, double dirx_d, double diry_d, double2* GN,
+                                                    double halfTw_d, MomentJ mj, double2* GN,
                                                     double2* GE, double2* GW, double* vol) {
     using TC = typename Pack<TS>::TC;
     const int lane = threadIdx.x & 31;
@@ -1380,7 +1383,7 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
     const TC s1x = (TC)s1d.x, s1y = (TC)s1d.y, s2x = (TC)s2d.x, s2y = (TC)s2d.y, s3x = (TC)s3d.x, s3y = (TC)s3d.y;
     const double4 pr = prim[c];
     const TC u1 = (TC)pr.y, u2 = (TC)pr.z, n0 = (TC)(pr.x / (2.0 * kPi * pr.w)), inv2T = (TC)(0.5 / pr.w);
-    const TC halfT = (TC)(0.5 * pr.w), halfTw = (TC)halfTw_d, dirx = (TC)dirx_d, diry = (TC)diry_d;
+    const TC halfT = (TC)(0.5 * pr.w), halfTw = (TC)halfTw_d, dirx = (TC)mj.dx, diry = (TC)mj.dy, hcoef = (TC)mj.h;
     const bool wall = n.w == kWall;
     const TC cw = wall ? (TC)(Fw[c] / wallD[c]) : TC(0);
     const TC gbs = wall ? (TC)(1.0 / wallD[c]) : TC(0);
@@ -1415,7 +1418,7 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
         }
         if (wall) {
             const TC a = s3x * vx + s3y * vy;
-            const TC m = dirx * vx + diry * vy;
+            const TC m = dirx * vx + diry * vy + hcoef * t.w;
             TC F1, F2;
             if (a > TC(0)) { F1 = fc1; F2 = fc2; }
             else {
@@ -1555,59 +1558,107 @@ __global__ void k_volume(int ni, const double2* S, const double2* nodes, double 
 // differences dR, dG of r and G, the next iterate is G - dG gamma, gamma = argmin |r - dR gamma|.
 // The vectors are the flat storage arrays (any layout: the operations are elementwise), held in
 // TH = the arithmetic type (FP32, or FP64 for FP64 storage).
-template <class TH, class TS> __device__ __forceinline__ TH toh(TS v) { return (TH)todbl(v); }
-template <> __device__ __forceinline__ float toh<float, float>(float v) { return v; }
-template <> __device__ __forceinline__ float toh<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <class TS, class TH> __device__ __forceinline__ TS fromh(TH v) { return fromdbl<TS>((double)v); }
-template <> __device__ __forceinline__ float fromh<float, float>(float v) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 fromh<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
-
 constexpr int kAAMax = 8;             // deepest history
 constexpr int kAABlocks = 1216;       // 152 SMs x 8 blocks of 256 threads, grid-stride
 
+// Four consecutive elements (n is a multiple of 8: cells x padded velocities x 2).
+template <class T> struct Quad;
+template <> struct Quad<float> {
+    template <class TH> __device__ static void ld(const float* p, TH (&v)[4]) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    template <class TH> __device__ static void st(float* p, const TH (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    }
+};
+template <> struct Quad<double> {
+    template <class TH> __device__ static void ld(const double* p, TH (&v)[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = (TH)a.x; v[1] = (TH)a.y; v[2] = (TH)b.x; v[3] = (TH)b.y;
+    }
+    template <class TH> __device__ static void st(double* p, const TH (&v)[4]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+template <> struct Quad<__nv_bfloat16> {
+    template <class TH> __device__ static void ld(const __nv_bfloat16* p, TH (&v)[4]) {
+        const uint2 a = *reinterpret_cast<const uint2*>(p);
+        v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xffff0000u);
+        v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
+    }
+    template <class TH> __device__ static void st(__nv_bfloat16* p, const TH (&v)[4]) {
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+        const __nv_bfloat162 h1 = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+        uint2 u;
+        memcpy(&u.x, &h0, 4);
+        memcpy(&u.y, &h1, 4);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+};
+
 template <class TS, class TH>
 __global__ void __launch_bounds__(256) k_aa_load(size_t n, const TS* __restrict__ F, TH* __restrict__ X) {
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        X[e] = toh<TH>(F[e]);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (size_t)gridDim.x * blockDim.x) {
+        TH v[4];
+        Quad<TS>::ld(F + 4 * q, v);
+        Quad<TH>::st(X + 4 * q, v);
+    }
 }
 
 // r = G - X, the new differences (slot `slot` of the ring, unless first) and the dots
-// dR_i . dR_slot (part[i]) and dR_i . r (part[m + i]) for the cnt columns in use, per block.
+// dR_i . dR_slot (part[i]) and dR_i . r (part[m + i]) for the cnt columns in use, per block.  The
+// dots of FP32 vectors are Kahan-compensated per thread: the least-squares problem of the mixing is
+// ill-conditioned (its columns become nearly parallel as the iteration slows), and plain FP32 sums
+// of a few hundred terms per thread are not accurate enough for it.
 template <class TS, class TH>
 __global__ void __launch_bounds__(256) k_aa_collect(size_t n, const TS* __restrict__ G, TH* __restrict__ X,
                                                     TH* __restrict__ Rp, TH* __restrict__ Gp, TH* __restrict__ dR,
                                                     TH* __restrict__ dG, int m, int cnt, int slot, int first,
                                                     double* __restrict__ part) {
-    TH acc[2 * kAAMax];
+    Acc<TH> acc[2 * kAAMax];
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = 4 * q;
+        TH g[4], x[4], r[4];
+        Quad<TS>::ld(G + e, g);
+        Quad<TH>::ld(X + e, x);
 #pragma unroll
-    for (int i = 0; i < 2 * kAAMax; ++i) acc[i] = TH(0);
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        const TH g = toh<TH>(G[e]);
-        const TH r = g - X[e];
+        for (int u = 0; u < 4; ++u) r[u] = g[u] - x[u];
         if (first) {
-            X[e] = g;
+            Quad<TH>::st(X + e, g);
         } else {
-            const TH dr = r - Rp[e];
-            dR[(size_t)slot * n + e] = dr;
-            dG[(size_t)slot * n + e] = g - Gp[e];
+            TH rp[4], gp[4], dr[4], dg[4];
+            Quad<TH>::ld(Rp + e, rp);
+            Quad<TH>::ld(Gp + e, gp);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { dr[u] = r[u] - rp[u]; dg[u] = g[u] - gp[u]; }
+            Quad<TH>::st(dR + (size_t)slot * n + e, dr);
+            Quad<TH>::st(dG + (size_t)slot * n + e, dg);
 #pragma unroll
             for (int i = 0; i < kAAMax; ++i) {
                 if (i < cnt) {
-                    const TH c = i == slot ? dr : dR[(size_t)i * n + e];
-                    acc[i] += c * dr;
-                    acc[kAAMax + i] += c * r;
+                    TH c[4];
+                    if (i == slot) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) c[u] = dr[u];
+                    } else {
+                        Quad<TH>::ld(dR + (size_t)i * n + e, c);
+                    }
+                    acc[i].add((c[0] * dr[0] + c[1] * dr[1]) + (c[2] * dr[2] + c[3] * dr[3]));
+                    acc[kAAMax + i].add((c[0] * r[0] + c[1] * r[1]) + (c[2] * r[2] + c[3] * r[3]));
                 }
             }
         }
-        Rp[e] = r;
-        Gp[e] = g;
+        Quad<TH>::st(Rp + e, r);
+        Quad<TH>::st(Gp + e, g);
     }
     if (first) return;
     __shared__ double red[8][2 * kAAMax];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < 2 * kAAMax; ++i) {
-        const double v = warp_sum((double)acc[i]);
+        const double v = warp_sum(acc[i].get());
         if (lane == 0) red[wid][i] = v;
     }
     __syncthreads();
@@ -1628,25 +1679,36 @@ __global__ void k_aa_sum(const double* __restrict__ part, int nb, int m2, double
     out[j] = t;
 }
 
-// x = G - sum_i gamma_i dG_i into the state (rounded to storage) and X (the stored value); neg is
-// set when any value turns negative.
+// x = G - sum_i gamma_i dG_i into the state (rounded to storage) and X (the stored value); with
+// `positive` (a distribution), neg is set when any value turns negative.
 template <class TS, class TH>
 __global__ void __launch_bounds__(256) k_aa_mix(size_t n, TS* __restrict__ F, TH* __restrict__ X,
                                                 const TH* __restrict__ Gp, const TH* __restrict__ dG, int cnt,
-                                                const double* __restrict__ gamma, int* __restrict__ neg) {
+                                                const double* __restrict__ gamma, int positive,
+                                                int* __restrict__ neg) {
     TH gam[kAAMax];
 #pragma unroll
     for (int i = 0; i < kAAMax; ++i) gam[i] = i < cnt ? (TH)gamma[i] : TH(0);
     bool bad = false;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        TH x = Gp[e];
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = 4 * q;
+        TH x[4];
+        Quad<TH>::ld(Gp + e, x);
 #pragma unroll
-        for (int i = 0; i < kAAMax; ++i)
-            if (i < cnt) x -= gam[i] * dG[(size_t)i * n + e];
-        const TS v = fromh<TS>(x);
-        F[e] = v;
-        X[e] = toh<TH>(v);
-        bad |= x < TH(0);
+        for (int i = 0; i < kAAMax; ++i) {
+            if (i < cnt) {
+                TH d[4];
+                Quad<TH>::ld(dG + (size_t)i * n + e, d);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] -= gam[i] * d[u];
+            }
+        }
+        Quad<TS>::st(F + e, x);
+        TH v[4];
+        Quad<TS>::ld(F + e, v);                  // X holds the stored (rounded) value
+        Quad<TH>::st(X + e, v);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bad |= positive && x[u] < TH(0);
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(neg, 1);
 }
@@ -1655,9 +1717,11 @@ __global__ void __launch_bounds__(256) k_aa_mix(size_t n, TS* __restrict__ F, TH
 template <class TS, class TH>
 __global__ void __launch_bounds__(256) k_aa_restore(size_t n, TS* __restrict__ F, TH* __restrict__ X,
                                                     const TH* __restrict__ Gp) {
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        F[e] = fromh<TS>(Gp[e]);
-        X[e] = Gp[e];
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (size_t)gridDim.x * blockDim.x) {
+        TH v[4];
+        Quad<TH>::ld(Gp + 4 * q, v);
+        Quad<TS>::st(F + 4 * q, v);
+        Quad<TH>::st(X + 4 * q, v);
     }
 }
 
@@ -1675,9 +1739,9 @@ cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, double dirx, double diry,
+cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, MomentJ mj,
                               double* wallD, double* wallM, cudaStream_t s) {
-    k_wall_setup<<<m.ni, 256, 0, s>>>(g.nvp, m.Sd, g.vd, fl.gwd, dirx, diry, wallD, wallM);
+    k_wall_setup<<<m.ni, 256, 0, s>>>(g.nvp, m.Sd, g.vd, fl.gwd, mj, wallD, wallM);
     return cudaGetLastError();
 }
 
@@ -1869,14 +1933,14 @@ cudaError_t launch_finalize(const double* respart, int ncell, const double* Jpar
 }
 
 cudaError_t launch_functional(int storage, const void* f, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
-                              const double* Fw, double dirx, double diry, double* face_out, double* out,
+                              const double* Fw, MomentJ mj, double* face_out, double* out,
                               cudaStream_t s) {
     if (storage == 0)
-        k_functional<double><<<m.ni, 256, 0, s>>>((const double*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, dirx, diry, face_out);
+        k_functional<double><<<m.ni, 256, 0, s>>>((const double*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, mj, face_out);
     else if (storage == 1)
-        k_functional<float><<<m.ni, 256, 0, s>>>((const float*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, dirx, diry, face_out);
+        k_functional<float><<<m.ni, 256, 0, s>>>((const float*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, mj, face_out);
     else
-        k_functional<__nv_bfloat16><<<m.ni, 256, 0, s>>>((const __nv_bfloat16*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, dirx, diry, face_out);
+        k_functional<__nv_bfloat16><<<m.ni, 256, 0, s>>>((const __nv_bfloat16*)f, g.nvp, m.Sd, g.vd, fl.gwd, fl.wallD, Fw, mj, face_out);
     k_finalize<<<1, 1024, 0, s>>>(face_out, 0, face_out, nullptr, nullptr, m.ni, out);
     return cudaGetLastError();
 }
@@ -1899,40 +1963,40 @@ cudaError_t launch_convert(int storage, int direction, const void* src, void* ds
 }
 
 cudaError_t launch_sens_paper(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl, const void* f,
-                              const void* phi, const double* Fw, double dirx, double diry, double* elem,
+                              const void* phi, const double* Fw, MomentJ mj, double* elem,
                               double* node_grad, cudaStream_t s) {
     const double hT = 0.5 * fl.Tw;
     if (storage == 0)
         k_sens_paper_elem<double><<<m.ni, 256, 0, s>>>((const double*)f, (const double*)phi, g.nvp, m.nb, m.Sd, m.Vd, g.vd,
-                                                       fl.fdd, fl.gwd, fl.wallD, Fw, hT, dirx, diry, elem);
+                                                       fl.fdd, fl.gwd, fl.wallD, Fw, hT, mj, elem);
     else if (storage == 1)
         k_sens_paper_elem<float><<<m.ni, 256, 0, s>>>((const float*)f, (const float*)phi, g.nvp, m.nb, m.Sd, m.Vd, g.vd,
-                                                      fl.fdd, fl.gwd, fl.wallD, Fw, hT, dirx, diry, elem);
+                                                      fl.fdd, fl.gwd, fl.wallD, Fw, hT, mj, elem);
     else
         k_sens_paper_elem<__nv_bfloat16><<<m.ni, 256, 0, s>>>((const __nv_bfloat16*)f, (const __nv_bfloat16*)phi, g.nvp,
                                                               m.nb, m.Sd, m.Vd, g.vd, fl.fdd, fl.gwd, fl.wallD, Fw, hT,
-                                                              dirx, diry, elem);
+                                                              mj, elem);
     k_sens_paper_nodes<<<cdiv(m.ni, 128), 128, 0, s>>>(m.ni, m.nodes, m.Sd, elem, node_grad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl, const void* f,
-                             const void* phi, const double4* prim, const double* Fw, double dirx, double diry,
+                             const void* phi, const double4* prim, const double* Fw, MomentJ mj,
                              double2* GN, double2* GE, double2* GW, double* vol, double2* node_grad, cudaStream_t s) {
     const int nb = cdiv(m.ncell, kWarpsPerBlock);
     const double hT = 0.5 * fl.Tw, it = 1.0 / fl.tau_inf;
     if (storage == 0)
         k_sens_faces<double><<<nb, 256, 0, s>>>((const double*)f, (const double*)phi, m.ncell, g.nvp, m.nb, m.Sd, m.Vd,
-                                                g.vd, fl.fdd, fl.gwd, fl.wallD, prim, Fw, it, hT, dirx, diry, GN, GE,
+                                                g.vd, fl.fdd, fl.gwd, fl.wallD, prim, Fw, it, hT, mj, GN, GE,
                                                 GW, vol);
     else if (storage == 1)
         k_sens_faces<float><<<nb, 256, 0, s>>>((const float*)f, (const float*)phi, m.ncell, g.nvp, m.nb, m.Sd, m.Vd,
-                                               g.vf, fl.fdf, fl.gwf, fl.wallD, prim, Fw, it, hT, dirx, diry, GN, GE,
+                                               g.vf, fl.fdf, fl.gwf, fl.wallD, prim, Fw, it, hT, mj, GN, GE,
                                                GW, vol);
     else
         k_sens_faces<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, (const __nv_bfloat16*)phi, m.ncell,
                                                        g.nvp, m.nb, m.Sd, m.Vd, g.vf, fl.fdf, fl.gwf, fl.wallD, prim,
-                                                       Fw, it, hT, dirx, diry, GN, GE, GW, vol);
+                                                       Fw, it, hT, mj, GN, GE, GW, vol);
     const int nn = (m.nj + 1) * m.ni;
     k_sens_nodes<<<cdiv(nn, 256), 256, 0, s>>>(m.ni, m.nj, m.nodes, GN, GE, GW, vol, node_grad);
     return cudaGetLastError();
@@ -1962,9 +2026,9 @@ cudaError_t launch_aa_collect(int storage, size_t n, const void* G, void* X, voi
 }
 
 cudaError_t launch_aa_mix(int storage, size_t n, void* F, void* X, const void* Gp, const void* dG, int cnt,
-                          const double* gamma, int* neg, cudaStream_t s) {
+                          const double* gamma, int positive, int* neg, cudaStream_t s) {
     DVM_AA_DISPATCH(storage, (k_aa_mix<TS, TH><<<kAABlocks, 256, 0, s>>>(n, (TS*)F, (TH*)X, (const TH*)Gp, (const TH*)dG,
-                                                                      cnt, gamma, neg)))
+                                                                      cnt, gamma, positive, neg)))
     return cudaGetLastError();
 }
 

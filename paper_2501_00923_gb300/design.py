@@ -191,19 +191,44 @@ class DesignLoop:
     max_iter: int = 12
     first_step: float = 1e-3
     tol: float = CRITERION_OPT
+    shape: str = "bumps"
     history: list = field(default_factory=list)
 
     def __post_init__(self):
-        self.a0 = np.zeros(self.n_params) if self.alpha0 is None else np.asarray(self.alpha0, float)
+        if self.shape == "cst":
+            # Sec. 3.3: CST variables of the base section by Eq. (cstini); bounds of Eq. (cst_constraint)
+            nb = (self.n_params - 6) // 2
+            if self.n_params != W.cst_count(nb):
+                raise ValueError("a CST section has 2 N_B + 6 design variables")
+            self.nb = nb
+            self.a0 = W.cst_naca(self.ni, nb) if self.alpha0 is None else np.asarray(self.alpha0, float)
+            lo = np.full(self.n_params, -np.inf)
+            hi = np.full(self.n_params, np.inf)
+            lo[0] = lo[1] = 0.01                              # N1, N2 >= 0.01
+            lo[2:3 + nb] = 0.0                                # A_u >= 0
+            hi[3 + nb:4 + 2 * nb] = 0.0                       # A_l <= 0
+            lo[4 + 2 * nb:] = hi[4 + 2 * nb:] = 0.0           # sharp trailing edge
+            self.lower, self.upper = lo, hi
+        elif self.shape == "bumps":
+            self.a0 = np.zeros(self.n_params) if self.alpha0 is None else np.asarray(self.alpha0, float)
+            self.lower, self.upper = -self.bound, self.bound
+        else:
+            raise ValueError(f"unknown shape parameterisation {self.shape!r}")
         self.opt = None
         self.J_old = None
         self.converged = False
         self.stopped = None
 
+    def mesh(self, alpha) -> W.OMesh:
+        if self.shape == "cst":
+            return W.omesh_cst(self.ni, self.nj, alpha, self.nb)
+        return W.omesh(self.ni, self.nj, alpha)
+
     def constrain(self, Q0: float, dQ):
-        """Q(alpha) = Q0 + dQ . (alpha - alpha0) <= 0, i.e. dQ . alpha <= dQ . alpha0 - Q0."""
+        """Q(alpha) ~ Q0 + dQ . (alpha - alpha0) <= 0, i.e. dQ . alpha <= dQ . alpha0 - Q0 (exact for
+        the bumps, re-linearised at every accepted design otherwise)."""
         dQ = np.asarray(dQ, float)
-        self.opt = LBFGS(self.a0, lower=-self.bound, upper=self.bound, first_step=self.first_step,
+        self.opt = LBFGS(self.a0, lower=self.lower, upper=self.upper, first_step=self.first_step,
                          halfspace=(dQ, float(dQ @ self.a0) - Q0))
 
     @property
@@ -212,6 +237,8 @@ class DesignLoop:
         return 0.5 * U * U
 
     def feasible_mesh(self, alpha) -> bool:
+        if self.shape == "cst":        # A_u >= 0 >= A_l: the surfaces cannot cross
+            return True
         return W.valid_amplitude_scale(self.ni, alpha, margin=1.0) >= 1.0
 
     def finish(self, ev: Evaluation) -> str:
@@ -219,6 +246,9 @@ class DesignLoop:
         self.history.append(ev)
         phase = self.opt.phase
         out = self.opt.tell(ev.Cd if ev.ok else np.inf, ev.dCd if ev.ok else np.zeros_like(ev.alpha))
+        if ev.ok and out in ("init", "accepted") and self.opt.phase != "done":
+            # the volume half-space through the accepted design (unchanged when Q is affine)
+            self.opt.halfspace = (np.asarray(ev.dQ, float), float(ev.dQ @ ev.alpha) - ev.Q)
         if phase == "init":
             self.J_old = ev.Cd
         elif out == "accepted":
@@ -273,7 +303,8 @@ def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 
     design as warm starts for the next)."""
     from .autograd import DragProblem
     prob = DragProblem(ctx, loop.ni, loop.nj, loop.grid, loop.flow, storage=storage, tol=tol,
-                       adjoint_tol=adjoint_tol, max_iter=max_sweeps, stall_window=stall_window)
+                       adjoint_tol=adjoint_tol, max_iter=max_sweeps, stall_window=stall_window,
+                       mesh_fn=loop.mesh)
     _start(ctx, loop)
 
     def evaluate(a):
@@ -303,9 +334,9 @@ def _start(ctx, loop: DesignLoop):
     """V_min (the initial area unless given) and the linear volume constraint of the loop."""
     if loop.opt is not None:
         return
+    mesh = loop.mesh(loop.a0)
     if loop.v_min is None:
-        loop.v_min = section_area(ctx, loop.ni, loop.nj, loop.a0)
-    mesh = W.omesh(loop.ni, loop.nj, loop.a0)
+        loop.v_min = -_volume(ctx, mesh.nodes, 0.0, np.zeros((1, loop.ni, 2)))[0]
     Q0, dQ = _volume(ctx, mesh.nodes, loop.v_min, mesh.dwall)
     loop.constrain(Q0, dQ)
 
@@ -324,7 +355,7 @@ def run_concurrent(ctx: dvm.Context, loops: list[DesignLoop], storage: str = "fp
         while not loop.done:
             a = loop.opt.ask()
             if loop.feasible_mesh(a):
-                mesh = W.omesh(loop.ni, loop.nj, a)
+                mesh = loop.mesh(a)
                 spec = SolveSpec(mesh, loop.grid, loop.flow, storage=storage, tol=tol, adjoint_tol=tol,
                                  max_iter=max_sweeps, warm_key=1000 + k, stall_window=stall_window)
                 pending[server.submit(spec)] = (k, a, mesh)
@@ -371,6 +402,8 @@ def main(argv=None):
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--concurrent", action="store_true", help="all Kn loops through one served batch")
+    ap.add_argument("--shape", default="bumps", choices=["bumps", "cst"],
+                    help="24 Hicks-Henne bumps, or the 18 CST variables (N_B = 6) of Sec. 3.3")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -378,8 +411,9 @@ def main(argv=None):
     wl = W.config(4)
     grid = W.velocity_grid(args.nv, 6.0, "gauss")
     ctx = dvm.Context(0)
-    loops = [DesignLoop(ni, nj, grid, W.Flow(float(k), wl.flow.Ma), n_params=24, max_iter=args.iters)
-             for k in args.kn.split(",")]
+    P = 24 if args.shape == "bumps" else W.cst_count()
+    loops = [DesignLoop(ni, nj, grid, W.Flow(float(k), wl.flow.Ma), n_params=P, max_iter=args.iters,
+                        shape=args.shape) for k in args.kn.split(",")]
     t0 = time.perf_counter()
     if args.concurrent:
         run_concurrent(ctx, loops, storage=args.storage, tol=args.tol)
@@ -396,7 +430,7 @@ def main(argv=None):
             if e.ok and (best is None or e.Cd < best):
                 best = e.Cd
                 acc.append({"Cd": e.Cd, "Q_over_Vmin": e.Q / loop.v_min})
-        print(json.dumps({"Kn": loop.flow.Kn, "Ma": loop.flow.Ma, "mesh": args.mesh, "nv": args.nv,
+        print(json.dumps({"Kn": loop.flow.Kn, "Ma": loop.flow.Ma, "mesh": args.mesh, "nv": args.nv, "shape": args.shape,
                           "storage": args.storage, "stopped": loop.stopped, "iterations": loop.opt.iterations,
                           "evaluations": loop.opt.evaluations, "Cd0": loop.history[0].Cd, "Cd_best": best,
                           "seconds": span, "concurrent": args.concurrent, "accepted": acc}))

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libdvm.so")
 DVM_OK, DVM_ERR_INVALID_ARG, DVM_ERR_OOM, DVM_ERR_ADMISSION = 0, 1, 2, 3
 DVM_NOT_CONVERGED, DVM_ERR_NONFINITE, DVM_ERR_CUDA, DVM_ERR_TIMEOUT, DVM_ERR_STAGNATED = 4, 5, 6, 7, 8
 STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2}
-FUNCTIONAL = {"drag": 0, "lift": 1}
+FUNCTIONAL = {"drag": 0, "lift": 1, "heat": 2}
 SENS = {"paper": 0, "full": 1}
 
 _dp = C.POINTER(C.c_double)

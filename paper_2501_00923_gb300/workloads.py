@@ -140,6 +140,117 @@ def omesh(ni: int, nj: int, alpha=None, first: float = 1e-3, radius: float = 10.
     return OMesh(ni, nj, np.ascontiguousarray(nodes), s, dxw, alpha)
 
 
+# --------------------------------------------------------------------------- CST parameterisation
+CST_NB = 6
+
+
+def cst_count(nb: int = CST_NB) -> int:
+    """Design variables of the CST section: N1, N2, A_u[0..nb], A_l[0..nb], eta_T,u, eta_T,l."""
+    return 2 * nb + 6
+
+
+def _bernstein(xi: np.ndarray, nb: int) -> np.ndarray:
+    """S_beta(xi) = C(nb, beta) xi^beta (1 - xi)^(nb - beta), [nb+1, len(xi)]."""
+    return np.stack([math.comb(nb, b) * xi ** b * (1.0 - xi) ** (nb - b) for b in range(nb + 1)])
+
+
+def cst_wall_nodes(ni: int, params, nb: int = CST_NB):
+    """Wall nodes of the CST section (Sec. 3.3, Eq. cstsuf, cst_classfunc, cst_shapefunc) at the
+    fixed abscissae of the O-mesh, xi_m = (1 + cos theta_m)/2, upper surface first, and their
+    derivatives with respect to the design variables.
+
+    eta = C(xi) S(xi) + xi eta_T with C = xi^N1 (1 - xi)^N2 and S = sum_beta A_beta S_beta(xi) on each
+    surface; params = (N1, N2, A_u[0..nb], A_l[0..nb], eta_T,u, eta_T,l).  x stays fixed (only eta
+    moves).  dC/dN1 = ln(xi) C and dC/dN2 = ln(1 - xi) C vanish where C does (xi = 0 or 1 with N > 0).
+
+    Returns (xw [ni,2], dxw [2nb+6, ni, 2]).
+    """
+    q = np.asarray(params, dtype=np.float64).reshape(-1)
+    if q.size != cst_count(nb):
+        raise ValueError(f"CST with nb={nb} has {cst_count(nb)} design variables")
+    N1, N2 = q[0], q[1]
+    Au, Al = q[2:3 + nb], q[3 + nb:4 + 2 * nb]
+    tu, tl = q[4 + 2 * nb], q[5 + 2 * nb]
+    theta = 2.0 * np.pi * np.arange(ni) / ni
+    xi = 0.5 * (1.0 + np.cos(theta))
+    xi = np.clip(xi, 0.0, 1.0)
+    side = np.sign(np.round(np.sin(theta), 14))
+    up = side > 0
+    lo = side < 0
+    Bs = _bernstein(xi, nb)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        C = np.where((xi > 0) & (xi < 1), xi ** N1 * (1.0 - xi) ** N2, 0.0)
+        l1 = np.where(xi > 0, np.log(np.where(xi > 0, xi, 1.0)), 0.0)
+        l2 = np.where(xi < 1, np.log(np.where(xi < 1, 1.0 - xi, 1.0)), 0.0)
+    Su, Sl = Au @ Bs, Al @ Bs
+    eta = np.zeros(ni)
+    eta[up] = C[up] * Su[up] + xi[up] * tu
+    eta[lo] = C[lo] * Sl[lo] + xi[lo] * tl
+    P = cst_count(nb)
+    d = np.zeros((P, ni))
+    d[0, up] = l1[up] * C[up] * Su[up]
+    d[0, lo] = l1[lo] * C[lo] * Sl[lo]
+    d[1, up] = l2[up] * C[up] * Su[up]
+    d[1, lo] = l2[lo] * C[lo] * Sl[lo]
+    d[2:3 + nb][:, up] = C[up] * Bs[:, up]
+    d[3 + nb:4 + 2 * nb][:, lo] = C[lo] * Bs[:, lo]
+    d[4 + 2 * nb, up] = xi[up]
+    d[5 + 2 * nb, lo] = xi[lo]
+    xw = np.stack([xi, eta], 1)
+    dxw = np.zeros((P, ni, 2))
+    dxw[:, :, 1] = d
+    return xw, dxw
+
+
+def cst_fit(ni: int, target_eta: np.ndarray, nb: int = CST_NB, sharp_te: bool = True):
+    """Eq. (cstini): the CST design variables whose nodes best fit the given wall ordinates (least
+    squares over the nodes, xi fixed).  With N1, N2 fixed the fit is linear in A and eta_T; N1 and N2
+    are then refined by Gauss-Newton on all variables.  sharp_te fixes eta_T = 0."""
+    P = cst_count(nb)
+    q = np.zeros(P)
+    q[0], q[1] = 0.5, 1.0                          # round nose, sharp trailing edge
+    free = np.ones(P, bool)
+    if sharp_te:
+        free[4 + 2 * nb:] = False
+    for it in range(60):
+        xw, dxw = cst_wall_nodes(ni, q, nb)
+        r = xw[:, 1] - target_eta
+        Jm = dxw[:, :, 1].T[:, free]
+        if it == 0:                                   # linear stage: A only
+            lin = free.copy()
+            lin[:2] = False
+            step = np.linalg.lstsq(dxw[:, :, 1].T[:, lin], -r, rcond=None)[0]
+            q[lin] += step
+            continue
+        step = np.linalg.lstsq(Jm, -r, rcond=None)[0]
+        q[free] += step
+        q[0] = max(q[0], 0.01)
+        q[1] = max(q[1], 0.01)
+        if np.abs(step).max() < 1e-13:
+            break
+    return q
+
+
+def omesh_from_wall(ni: int, nj: int, xw: np.ndarray, dxw: np.ndarray, alpha, first: float = 1e-3,
+                    radius: float = 10.0) -> OMesh:
+    xf = far_nodes(ni, radius)
+    s = radial_blend(nj, first, radius)
+    nodes = xw[None, :, :] + s[:, None, None] * (xf - xw)[None, :, :]
+    return OMesh(ni, nj, np.ascontiguousarray(nodes), s, dxw, np.asarray(alpha, dtype=np.float64))
+
+
+def omesh_cst(ni: int, nj: int, params, nb: int = CST_NB, first: float = 1e-3, radius: float = 10.0) -> OMesh:
+    """O-mesh around the CST section of `params` (dwall = d(wall nodes)/d(params))."""
+    xw, dxw = cst_wall_nodes(ni, params, nb)
+    return omesh_from_wall(ni, nj, xw, dxw, params, first, radius)
+
+
+def cst_naca(ni: int, nb: int = CST_NB, thickness: float = 0.12):
+    """CST variables of the base section (symmetric NACA 4-digit thickness law) by Eq. (cstini)."""
+    xw, _ = wall_nodes(ni, np.zeros(0), thickness)
+    return cst_fit(ni, xw[:, 1], nb)
+
+
 def ellipse_mesh(ni: int, nj: int, thickness: float, aoa_deg: float, first: float = 1e-3,
                  radius: float = 10.0) -> OMesh:
     """O-mesh around a thin ellipse of unit chord rotated by aoa (nose up), for the

@@ -155,3 +155,40 @@ def test_design_loop_stops_by_criterion_opt_on_an_analytic_problem():
     lam = max(0.0, (q @ c) / (q @ np.linalg.solve(A, q)))
     a_star = c - lam * np.linalg.solve(A, q)
     assert np.abs(loop.best.alpha - a_star).max() < 2e-4
+
+
+# ----------------------------------------------------------------------------- CST (Sec. 3.3)
+def test_cst_tangents_match_central_differences():
+    rng = np.random.default_rng(12)
+    q = W.cst_naca(48, 4)
+    q[2:] += rng.uniform(-0.01, 0.01, q.size - 2) * np.r_[np.ones(10), 0, 0]
+    q[-2:] = [0.002, -0.001]
+    _, d = W.cst_wall_nodes(48, q, 4)
+    h = 1e-6
+    for p in range(q.size):
+        e = np.zeros(q.size)
+        e[p] = h
+        fd = (W.cst_wall_nodes(48, q + e, 4)[0] - W.cst_wall_nodes(48, q - e, 4)[0]) / (2 * h)
+        np.testing.assert_allclose(d[p], fd, atol=1e-8)
+
+
+def test_cst_closed_form_and_least_squares_recovery():
+    """N_B = 0 with N1 = 1/2, N2 = 1: eta_u = A sqrt(xi) (1 - xi) + xi eta_T; and the fit of
+    Eq. (cstini) recovers the nodes of a CST section to round-off."""
+    ni = 40
+    xw, _ = W.cst_wall_nodes(ni, [0.5, 1.0, 0.2, -0.1, 0.003, -0.002], 0)
+    xi = xw[:, 0]
+    up = np.sign(np.round(np.sin(2 * np.pi * np.arange(ni) / ni), 14)) > 0
+    np.testing.assert_allclose(xw[up, 1], 0.2 * np.sqrt(xi[up]) * (1 - xi[up]) + 0.003 * xi[up], atol=1e-15)
+    q = W.cst_naca(64, 6)
+    q[0], q[1] = 0.52, 0.95
+    q[2:9] *= 1.05
+    target = W.cst_wall_nodes(64, q, 6)[0][:, 1]
+    fit = W.cst_fit(64, target, 6)
+    assert np.abs(W.cst_wall_nodes(64, fit, 6)[0][:, 1] - target).max() < 1e-10
+
+
+def test_cst_fits_the_base_section():
+    for ni in (64, 256):
+        xw, _ = W.cst_wall_nodes(ni, W.cst_naca(ni))
+        assert np.abs(xw[:, 1] - W.wall_nodes(ni, np.zeros(0))[0][:, 1]).max() < 1e-4

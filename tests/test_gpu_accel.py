@@ -41,16 +41,18 @@ def _solve(ctx, case, storage, accel, tol, stall=0):
 
 
 def test_fp64_mixing_converges_to_the_plain_solution_in_fewer_sweeps(ctx, case):
-    J0, ip0, sp0, ia0, sa0, g0 = _solve(ctx, case, "fp64", None, 1e-10)
-    J1, ip1, sp1, ia1, sa1, g1 = _solve(ctx, case, "fp64", (5, 10), 1e-10)
+    # both to 1e-12: the R/V-weighted residual norm leaves iteration errors in the drag some orders
+    # above it (3.6e-8 relative between the two at 1e-10)
+    J0, ip0, sp0, ia0, sa0, g0 = _solve(ctx, case, "fp64", None, 1e-12)
+    J1, ip1, sp1, ia1, sa1, g1 = _solve(ctx, case, "fp64", (5, 10), 1e-12)
     assert sp0 == sp1 == dvm.DVM_OK and sa0 == sa1 == dvm.DVM_OK
-    assert abs(J1 - J0) < 1e-8 * abs(J0)
+    assert abs(J1 - J0) < 1e-9 * abs(J0)
     assert np.abs(g1 - g0).max() < 1e-7 * np.abs(g0).max()
     assert ip1 < ip0 / 2 and ia1 < ia0 / 2, (ip0, ip1, ia0, ia1)
 
 
 def test_fp32_mixing_meets_the_stated_tolerances(ctx, case):
-    J0, *_, g0 = _solve(ctx, case, "fp64", None, 1e-10)
+    J0, *_, g0 = _solve(ctx, case, "fp64", None, 1e-12)
     J1, ip1, sp1, ia1, sa1, g1 = _solve(ctx, case, "fp32", (5, 10), 1e-9, stall=3000)
     assert sp1 in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED) and sa1 in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED)
     assert abs(J1 - J0) < 1e-5 * abs(J0)

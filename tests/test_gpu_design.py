@@ -75,3 +75,36 @@ def test_concurrent_loops_share_one_served_batch(ctx):
     cd0 = prob.solve(np.zeros(6))
     prob.release()
     assert abs(loops[0].history[0].Cd - cd0) < 1e-5 * abs(cd0)
+
+
+def test_cst_sensitivities_match_the_oracle(ctx):
+    """The 18 CST variables of Sec. 3.3 through the same sensitivity path: parity with the oracle's
+    full-discrete gradient on the same converged state."""
+    params = W.cst_naca(48)
+    mesh = W.omesh_cst(48, 12, params)
+    grid = W.velocity_grid(12, 4.0)
+    m = dvm.Mesh(ctx, mesh.nodes)
+    g = dvm.VGrid(ctx, grid.vx, grid.vy, grid.w)
+    st, _ = dvm.primal_solve(ctx, m, g, 1.0, 0.6, tol=1e-12, max_iter=100000, storage="fp64")
+    ad, _ = dvm.adjoint_solve(ctx, st, tol=1e-12, max_iter=100000)
+    grad = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    pr = O.Problem(mesh.nodes, grid.vx, grid.vy, grid.w, 1.0, 0.6)
+    ref = pr.sens_full(st.get(), ad.get(), mesh.dnodes())
+    assert np.abs(grad - ref).max() < 1e-9 * np.abs(ref).max()
+    for h in (ad, st, g, m):
+        h.close()
+
+
+def test_cst_design_loop_keeps_the_constraints(ctx):
+    loop = design.DesignLoop(48, 12, W.velocity_grid(12, 4.0), W.Flow(1.0, 0.6), n_params=W.cst_count(),
+                             shape="cst", max_iter=3, first_step=2e-3)
+    design.run(ctx, loop, storage="fp32", tol=1e-7, adjoint_tol=1e-7, stall_window=20000)
+    acc = _accepted(loop)
+    assert len(acc) >= 2 and acc[-1].Cd < acc[0].Cd
+    nb = loop.nb
+    for e in loop.history:
+        a = e.alpha
+        assert a[0] >= 0.01 and a[1] >= 0.01 and np.all(a[2:3 + nb] >= 0) and np.all(a[3 + nb:4 + 2 * nb] <= 0)
+        assert np.all(a[4 + 2 * nb:] == 0)
+        if e.ok:    # Q is not affine in N1, N2: the re-linearised half-space keeps it to second order
+            assert e.Q <= 1e-4 * loop.v_min

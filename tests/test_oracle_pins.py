@@ -333,3 +333,71 @@ def test_volume_constraint_is_minus_the_section_area_and_its_gradient():
         Qa = _problem(W.omesh(64, 4, a), grid).volume_constraint(0.0, mesh.dwall)[0]
         Qb = _problem(W.omesh(64, 4, b), grid).volume_constraint(0.0, mesh.dwall)[0]
         assert abs((Qa - Qb) / (2 * h) - dQda[p]) < 1e-9
+
+
+# ----------------------------------------------------------------------------- heat functional (m_J = |v|^2/2)
+def _half_moments(mu):
+    """Half-range moments of a unit-variance Gaussian of mean mu: int_{x>0} x^k N(x; mu, 1) dx, k = 1, 3."""
+    Phi = 0.5 * (1.0 + erf(mu / math.sqrt(2.0)))
+    phi = math.exp(-0.5 * mu * mu) / math.sqrt(2.0 * math.pi)
+    return mu * Phi + phi, (mu ** 3 + 3.0 * mu) * Phi + (mu * mu + 2.0) * phi
+
+
+@pytest.mark.parametrize("angle,Ma,Tw", [(0.0, 0.5, 1.0), (0.7, 2.0, 1.0), (2.4, 0.8, 0.6), (-1.9, 1.3, 2.0)])
+def test_free_molecular_panel_heat_closed_form(angle, Ma, Tw):
+    """The heat functional (Eq. formula_opt with m_J = |v|^2/2) on a panel in free-molecular flow:
+    the incident energy flux of the free stream over v.n > 0 (n into the body),
+    (1/2) [M3(U_n) + (U_t^2 + 1) M1(U_n)], plus the diffusely re-emitted flux at T_w, which carries
+    3 T_w / 2 per unit of the incident number flux M1(U_n) in the reduced 2D model."""
+    n = np.array([math.cos(angle), math.sin(angle)])
+    t = np.array([-n[1], n[0]])
+    L, m = 14.0, 72
+    xh, wh = np.polynomial.legendre.leggauss(m)
+    a = np.concatenate([-L / 2 * (xh + 1), L / 2 * (xh + 1)])
+    wa = np.concatenate([L / 2 * wh, L / 2 * wh])
+    b, wb = L * xh, L * wh
+    A, B = np.meshgrid(a, b, indexing="ij")
+    V = A[..., None] * n + B[..., None] * t
+    vx, vy = V[..., 0].ravel(), V[..., 1].ravel()
+    w = np.outer(wa, wb).ravel()
+    U = Ma * W.A_INF * np.array([1.0, 0.0])
+    f1 = np.exp(-((vx - U[0]) ** 2 + (vy - U[1]) ** 2) / 2) / (2 * np.pi)
+    area = 0.37
+    M1, M3 = _half_moments(U @ n)
+    ref = area * (0.5 * (M3 + ((U @ t) ** 2 + 1.0) * M1) - 1.5 * Tw * M1)
+    J = O.wall_face_functional(area * n, vx, vy, w, f1, Tw, (0.0, 0.0, 1.0))
+    assert abs(J - ref) <= 1e-11 * max(1.0, abs(ref))
+    # the moment is linear in its coefficients: drag + heat = the sum of the two functionals
+    Jd = O.wall_face_functional(area * n, vx, vy, w, f1, Tw, (1.0, 0.0))
+    Jdh = O.wall_face_functional(area * n, vx, vy, w, f1, Tw, (1.0, 0.0, 1.0))
+    assert abs(Jdh - (Jd + J)) <= 1e-12 * max(1.0, abs(Jdh))
+
+
+def test_heat_sensitivity_matches_central_fd():
+    """The discrete adjoint of the heat functional and its full-discrete sensitivity against central
+    differences of the heat on the same discretisation (wall hotter than the gas, so the heat is
+    not zero), both solves to round-off."""
+    rng = np.random.default_rng(16)
+    alpha = rng.uniform(-0.01, 0.01, 4)
+    grid = W.velocity_grid(8, 4.0)
+    heat = (0.0, 0.0, 1.0)
+
+    def prob(a):
+        mesh = W.omesh(16, 8, a)
+        return mesh, O.Problem(mesh.nodes, grid.vx, grid.vy, grid.w, 1.0, 0.5, Tw=1.5, direction=heat)
+    mesh, pr = prob(alpha)
+    f, _ = pr.primal_solve(tol=1e-30, max_sweeps=2400)
+    phi, _ = pr.adjoint_solve(f, tol=1e-30, max_sweeps=2400)
+    g = pr.sens_full(f, phi, mesh.dnodes())
+    assert abs(pr.functional(f)) > 1e-3
+    h = 1e-5
+    for p in range(alpha.size):
+        vals = []
+        for sgn in (1, -1):
+            a = alpha.copy()
+            a[p] += sgn * h
+            _, pp = prob(a)
+            ff, _ = pp.primal_solve(tol=1e-30, max_sweeps=1200, f0=f)
+            vals.append(pp.functional(ff))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[p]) <= 1e-6 * max(abs(g).max(), 1e-12)
