@@ -92,7 +92,10 @@ typedef struct {
                                iteration only: the discrete solution is the same.  The history holds 2m + 3
                                vectors of the state's size (FP32; FP64 for FP64 storage), kept with the state or
                                adjoint.  A primal mix that makes any value of f negative is undone and the history
-                               restarts */
+                               restarts; so does a block residual above twice the best since the history
+                               started.  On the second such restart, or when the stall window runs out
+                               while mixing, the solve finishes with plain sweeps (with a stall window of
+                               their own), so FP32/BF16 solves end on the plain sweeps' rounding floor */
     int accel_period;       /* sweeps between mixings (>= 1; with accel_depth > 0) */
 } dvm_solve_opts;
 

@@ -5,6 +5,8 @@
 #include "dvm.h"
 #include "dvm_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -176,6 +178,13 @@ int dalloc(dvm_context* ctx, T** p, size_t count, size_t* acc = nullptr) {
 void dfree(void* p) {
     if (p) cudaFree(p);
 }
+
+// NVTX range over one library call (solve phases, sensitivity, batch tick) for timeline tools;
+// header-only, inert unless a profiler is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -963,6 +972,7 @@ int dvm_state_functional(dvm_state* st, int functional, double* J) {
 int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid, const dvm_flow* flow,
                      const dvm_solve_opts* opts, int storage, dvm_state** inout, dvm_primal_result* res) {
     if (!ctx || !mesh || !grid || !flow || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    Range nvtx("dvm_primal_solve");
     int rc0;
     if ((rc0 = check_solve_opts(opts))) return rc0;
     DeviceGuard dg(ctx->device);
@@ -986,6 +996,8 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         if ((rc = aa_ensure(ctx, st->aa, st->storage, n, opts->accel_depth))) return rc;
         if ((rc = aa_begin(ctx, st->aa, st->f[st->cur]))) return rc;
     }
+    bool mixing = accel;
+    int restarts = 0;
     int it = 0;
     double r = INFINITY, best = INFINITY, J = 0.0;
     int best_it = 0;
@@ -1008,11 +1020,17 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         if (!std::isfinite(r) || !std::isfinite(J)) { status = DVM_ERR_NONFINITE; fail(status, "residual is not finite"); break; }
         if (r <= opts->tol) { status = DVM_OK; break; }
         if (r < 0.98 * best) { best = r; best_it = it; }
-        if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
-        if (accel && k == K && it < opts->max_iter) {
+        if (opts->stall_window > 0 && it - best_it >= opts->stall_window) {
+            if (!mixing) { status = DVM_ERR_STAGNATED; break; }
+            mixing = false;                 // a stall while mixing: finish with plain sweeps, new window
+            best = r;
+            best_it = it;
+        }
+        if (mixing && k == K && it < opts->max_iter) {
             bool mixed = false;
-            if (aa_restart_if_growing(st->aa, r)) {   // the history misleads: start it again here
-                if ((rc = aa_begin(ctx, st->aa, st->f[st->cur]))) return rc;
+            if (aa_restart_if_growing(st->aa, r)) {   // the history misleads: start it again here,
+                if (++restarts >= 2) mixing = false;    // and on the second time finish with plain sweeps
+                else if ((rc = aa_begin(ctx, st->aa, st->f[st->cur]))) return rc;
             } else if ((rc = aa_step(ctx, st->aa, st->f[st->cur], true, &mixed))) {
                 return rc;
             }
@@ -1202,6 +1220,7 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
     if (!ctx || !st || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
     if (st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "state from another context");
     if (int rc0 = check_solve_opts(opts)) return rc0;
+    Range nvtx("dvm_adjoint_solve");
     DeviceGuard dg(ctx->device);
     std::memset(res, 0, sizeof(*res));
     int rc;
@@ -1220,6 +1239,8 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         if ((rc = aa_ensure(ctx, ad->aa, st->storage, n, opts->accel_depth))) return rc;
         if ((rc = aa_begin(ctx, ad->aa, ad->phi[ad->cur]))) return rc;
     }
+    bool mixing = accel;
+    int restarts = 0;
     int it = 0, best_it = 0;
     double r = INFINITY, best = INFINITY;
     int status = DVM_NOT_CONVERGED;
@@ -1239,11 +1260,17 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         if (!std::isfinite(r)) { status = DVM_ERR_NONFINITE; fail(status, "adjoint residual is not finite"); break; }
         if (r <= opts->tol) { status = DVM_OK; break; }
         if (r < 0.98 * best) { best = r; best_it = it; }
-        if (opts->stall_window > 0 && it - best_it >= opts->stall_window) { status = DVM_ERR_STAGNATED; break; }
-        if (accel && k == K && it < opts->max_iter) {
+        if (opts->stall_window > 0 && it - best_it >= opts->stall_window) {
+            if (!mixing) { status = DVM_ERR_STAGNATED; break; }
+            mixing = false;                 // a stall while mixing: finish with plain sweeps, new window
+            best = r;
+            best_it = it;
+        }
+        if (mixing && k == K && it < opts->max_iter) {
             bool mixed = false;
             if (aa_restart_if_growing(ad->aa, r)) {
-                if ((rc = aa_begin(ctx, ad->aa, ad->phi[ad->cur]))) return rc;
+                if (++restarts >= 2) mixing = false;
+                else if ((rc = aa_begin(ctx, ad->aa, ad->phi[ad->cur]))) return rc;
             } else if ((rc = aa_step(ctx, ad->aa, ad->phi[ad->cur], false, &mixed))) {
                 return rc;
             }
@@ -1266,6 +1293,7 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
     if (cad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
     if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
     DeviceGuard dg(ctx->device);
+    Range nvtx("dvm_sensitivity");
     dvm_adjoint* ad = const_cast<dvm_adjoint*>(cad);
     const DevMesh& m = st->mesh->d;
     const DevGrid& g = st->grid->d;
@@ -1723,6 +1751,7 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
     if (!b) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
     dvm_context* ctx = b->ctx;
     DeviceGuard dg(ctx->device);
+    Range nvtx("dvm_batch_tick");
     const int M = b->opt.sweeps_per_tick;
     int rc;
     // 1. admission, arrival order
