@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=60000)
     ap.add_argument("--tol", type=float, default=1e-11)
     ap.add_argument("--stall", type=int, default=3000, help="stagnation window of the FP32/BF16 solves")
+    ap.add_argument("--storages", default="fp64,fp32,bf16", help="fp64 first: it is the reference")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     build.build()
@@ -44,7 +45,9 @@ def main():
     report = {"workload": "omesh256x128-gl48x48-24bumps-Ma0.8", "alpha_seed": 2024, "runs": []}
     for Kn in [float(x) for x in args.kn.split(",")]:
         res = {}
-        for storage in ["fp64", "fp32", "bf16"]:
+        storages = args.storages.split(",")
+        assert storages[0] == "fp64", "the FP64 solve is the reference"
+        for storage in storages:
             sw = 0 if storage == "fp64" else args.stall
             t0 = time.time()
             st, pr_ = dvm.primal_solve(ctx, m, g, Kn, Ma, tol=args.tol, max_iter=args.max_sweeps, storage=storage,
@@ -67,7 +70,7 @@ def main():
         ref = res["fp64"]
         gref = np.array(ref["grad_full"])
         cmp = {}
-        for s in ["fp32", "bf16"]:
+        for s in storages[1:]:
             gs = np.array(res[s]["grad_full"])
             cmp[s] = {"drag_rel": abs(res[s]["J"] - ref["J"]) / abs(ref["J"]),
                       "sens_max_rel_to_max": float(np.abs(gs - gref).max() / np.abs(gref).max()),
