@@ -297,9 +297,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// g1 = n0 exp(-|v-u|^2/(2T)) written as exp(t kA + kB) with t = |v|^2/2 - v.u (FP64 sweep); the
-// FP32 sweep evaluates 2^(t kA' + kB') with base-2 constants set up per cell in primal_cell_paired.
+// g1 = n0 exp(-|v-u|^2/(2T)) written as 2^(t kA + kB) with t = |v|^2/2 - v.u (one FMA chain).
+// FP64: exp(t kA + kB) with the natural-log constants.
 template <class TC> struct Gauss;
+template <> struct Gauss<float> {
+    float kA, kB;
+    __device__ __forceinline__ void setup(float rho, float u1, float u2, float T) {   // FP32 only
+        constexpr float L2E = 1.44269504088896341f;
+        const float iT = 1.0f / T;
+        kA = -L2E * iT;
+        kB = log2f(rho * iT * 0.159154943091895336f) - L2E * 0.5f * (u1 * u1 + u2 * u2) * iT;
+    }
+    __device__ __forceinline__ float eval(float t) const { return ex2_approx(fmaf(t, kA, kB)); }
+};
 template <> struct Gauss<double> {
     double kA, kB;
     __device__ __forceinline__ void setup(double rho, double u1, double u2, double T) {
@@ -384,20 +394,11 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
     const float2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
     const double4 pr = P.prim_old[c];
-    const float u1 = (float)pr.y, u2 = (float)pr.z;
-    // The Maxwellian's per-cell constants come from the FP64 moments in FP64, and the FP32 rounding
-    // of kB is returned exactly as the factor 2^(kB - fl(kB)) on the collision source.  A per-cell
-    // scale error of g (from log2f and the FP32 moments it is about 3e-7) is a mass source of the
-    // collision term, which the slow contraction of the sweeps amplifies at small Kn; D keeps V/tau.
-    constexpr double L2Ed = 1.4426950408889634;
-    const double iTd = 1.0 / pr.w;
-    const double kBd = log2(pr.x * iTd * 0.15915494309189535) - L2Ed * 0.5 * (pr.y * pr.y + pr.z * pr.z) * iTd;
-    const float kBf = (float)kBd;
-    const double Vtd = (double)P.V[c] * pr.x * sqrt(pr.w) * P.inv_tau_inf;   // V / tau
-    const float Vt = (float)Vtd;
-    const float Vg = (float)(Vtd * exp2(kBd - (double)kBf));               // V / tau on the source
-    const float2 kA = bc((float)(-L2Ed * iTd)), kB = bc(kBf), mu1 = bc(-u1), mu2 = bc(-u2), Vt2 = bc(Vt);
-    const float2 Vg2 = bc(Vg), hT = bc((float)(0.5 * pr.w));
+    const float rho = (float)pr.x, u1 = (float)pr.y, u2 = (float)pr.z, T = (float)pr.w;
+    Gauss<float> G;
+    G.setup(rho, u1, u2, T);
+    const float Vt = P.V[c] * rho * sqrtf(T) * (float)P.inv_tau_inf;      // V / tau
+    const float2 kA = bc(G.kA), kB = bc(G.kB), mu1 = bc(-u1), mu2 = bc(-u2), Vt2 = bc(Vt), hT = bc(0.5f * T);
     const float2 s0x = bc(S0.x), s0y = bc(S0.y), s1x = bc(S1.x), s1y = bc(S1.y);
     const float2 s2x = bc(S2.x), s2y = bc(S2.y), s3x = bc(S3.x), s3y = bc(S3.y);
     float2 cw1 = bc(0.f), cw2 = bc(0.f), dxy = bc(0.f), dyy = bc(0.f);
@@ -459,7 +460,7 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                     }
                     const float2 D = padd(Vt2, padd(padd(n0, n1), padd(n2, n3)));
                     const float2 g1 = pex2(pfma(pfma(vy, mu2, pfma(vx, mu1, hv)), kA, kB));
-                    float2 r1 = pmul(Vg2, g1);
+                    float2 r1 = pmul(Vt2, g1);
                     float2 r2 = pmul(hT, r1);
                     r1 = pfma(n0, pair_of<KV>(e01, pp), r1); r2 = pfma(n0, pair_of<KV>(e02, pp), r2);
                     r1 = pfma(n1, f11, r1);                  r2 = pfma(n1, f12, r2);
