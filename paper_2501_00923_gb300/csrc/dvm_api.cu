@@ -233,7 +233,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     if constexpr (sizeof(TC) == 8) {
         a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.fd = st->fl.fdd; a.gw = st->fl.gwd;
     } else {
-        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.vp = g.vp; a.fd = st->fl.fdf; a.gw = st->fl.gwf;
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.vpa = g.vpa; a.vpb = g.vpb; a.fd = st->fl.fdf; a.gw = st->fl.gwf;
     }
     a.wallD = st->fl.wallD;
     a.inv_tau_inf = 1.0 / st->fl.tau_inf;
@@ -268,7 +268,7 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     if constexpr (sizeof(TC) == 8) {
         a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.gw = st->fl.gwd;
     } else {
-        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.vp = g.vp; a.gw = st->fl.gwf;
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.vpa = g.vpa; a.vpb = g.vpb; a.gw = st->fl.gwf;
     }
     a.wallD = st->fl.wallD;
     a.wallM = ad->wallM;
@@ -752,15 +752,16 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
     DeviceGuard dg(ctx->device);
     const int nvp = (nv + kPad - 1) / kPad * kPad;
     std::vector<double4> vd(nvp, double4{0, 0, 0, 0});
-    std::vector<float4> vf(nvp, float4{0, 0, 0, 0}), vp(nvp, float4{0, 0, 0, 0});
+    const int npair = (nvp / 2 + 127) / 128 * 128;            // whole stage rows of pairs
+    std::vector<float4> vf(nvp, float4{0, 0, 0, 0}), vpa(npair, float4{0, 0, 0, 0}), vpb(npair, float4{0, 0, 0, 0});
     for (int k = 0; k < nv; ++k) {
         vd[k] = double4{vx[k], vy[k], w[k], 0.5 * (vx[k] * vx[k] + vy[k] * vy[k])};
         vf[k] = float4{(float)vx[k], (float)vy[k], (float)w[k], (float)vd[k].w};
     }
     for (int p = 0; p < nvp / 2; ++p) {
         const float4 a = vf[2 * p], b = vf[2 * p + 1];
-        vp[2 * p] = float4{a.x, b.x, a.y, b.y};
-        vp[2 * p + 1] = float4{a.z, b.z, a.w, b.w};
+        vpa[p] = float4{a.x, b.x, a.y, b.y};
+        vpb[p] = float4{a.z, b.z, a.w, b.w};
     }
     dvm_vgrid* g = new (std::nothrow) dvm_vgrid();
     if (!g) return fail(DVM_ERR_OOM, "host allocation");
@@ -769,13 +770,15 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
     g->d.nvp = nvp;
     int rc;
     live_add(g, kGrid, ctx);
-    if ((rc = dalloc(ctx, &g->d.vd, nvp)) || (rc = dalloc(ctx, &g->d.vf, nvp)) || (rc = dalloc(ctx, &g->d.vp, nvp))) {
+    if ((rc = dalloc(ctx, &g->d.vd, nvp)) || (rc = dalloc(ctx, &g->d.vf, nvp)) || (rc = dalloc(ctx, &g->d.vpa, npair)) ||
+        (rc = dalloc(ctx, &g->d.vpb, npair))) {
         dvm_vgrid_destroy(g);
         return rc;
     }
     cudaError_t e = cudaMemcpy(g->d.vd, vd.data(), nvp * sizeof(double4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d.vf, vf.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d.vp, vp.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d.vpa, vpa.data(), npair * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d.vpb, vpb.data(), npair * sizeof(float4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { dvm_vgrid_destroy(g); return fail_cuda(e, "grid upload"); }
     *out = g;
     return DVM_OK;
@@ -784,7 +787,7 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
 void dvm_vgrid_destroy(dvm_vgrid* g) {
     if (!g || !live_take(g, kGrid)) return;
     DeviceGuard dg(g->ctx->device);
-    dfree(g->d.vd); dfree(g->d.vf); dfree(g->d.vp);
+    dfree(g->d.vd); dfree(g->d.vf); dfree(g->d.vpa); dfree(g->d.vpb);
     delete g;
 }
 

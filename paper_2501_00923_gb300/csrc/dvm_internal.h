@@ -33,7 +33,8 @@ struct DevGrid {
     int nv = 0, nvp = 0;
     double4* vd = nullptr;      // [nvp]
     float4* vf = nullptr;       // [nvp]
-    float4* vp = nullptr;       // [nvp] per velocity pair p: (vx, vx', vy, vy'), (w, w', h, h')
+    float4* vpa = nullptr;      // per velocity pair p (padded to a multiple of 128 pairs): (vx, vx', vy, vy')
+    float4* vpb = nullptr;      // (w, w', h, h'), h = |v|^2/2
 };
 
 // The moment of the functional, Eq. (formula_opt): m_J(v) = dx vx + dy vy + h |v|^2 / 2 (a force along
@@ -70,7 +71,8 @@ struct PrimalArgs {
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
     const TC* V;
     const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
-    const float4* vp;                       // paired velocity table (FP32 arithmetic)
+    const float4* vpa;                      // paired velocity table (FP32 arithmetic): (vx, vy) pairs
+    const float4* vpb;                      // (w, h) pairs
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* fd;
     const TC* gw;
     const double* wallD;
@@ -101,7 +103,8 @@ struct AdjointArgs {
     const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
     const TC* V;
     const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
-    const float4* vp;                       // paired velocity table (FP32 arithmetic)
+    const float4* vpa;                      // paired velocity table (FP32 arithmetic): (vx, vy) pairs
+    const float4* vpb;                      // (w, h) pairs
     const TC* gw;
     const double* wallD;
     const double* wallM;                    // for the functional's direction

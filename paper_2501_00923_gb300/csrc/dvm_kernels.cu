@@ -269,6 +269,14 @@ __device__ __forceinline__ unsigned atom_inc_acq_rel(unsigned* p) {
     return old;
 }
 
+// Non-tensor bulk copy global -> shared (16-byte aligned, size a multiple of 16) on the same mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes),
+                 "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // A block's pipeline: stages, their "full" mbarriers and release counters.
 struct Feed {
     const CUtensorMap* col;      // box 32 chunks x 1 cell x 10 rows (the value being swept)
@@ -276,18 +284,27 @@ struct Feed {
     const CUtensorMap* extra;    // box 32 chunks x 1 cell x 8 rows of a second buffer (adjoint: f), or null
     int i, im, ip, j0, rows;     // block column, its periodic neighbours, first row, rows per stage
     unsigned A;                  // warps that consume each stage
-    uint4* stage;                // kStages x rows x 32 chunks
+    const float4* vpa;           // paired velocity table, (vx, vx', vy, vy') per pair, or null
+    const float4* vpb;           // (w, w', h, h') per pair
+    unsigned vprow;              // velocity pairs per stage row (0: the table is not staged)
+    unsigned stride;             // 16-byte units per stage: rows x kRowChunks chunks, then 2 vprow pairs
+    uint4* stage;                // kStages x stride
     uint64_t* full;
     unsigned* released;          // per stage, warps that have released it so far (monotone)
     __device__ __forceinline__ void issue(unsigned it) const {
         const unsigned st = it % kStages;
-        uint4* d = stage + (size_t)st * rows * kRowChunks;
+        uint4* d = stage + (size_t)st * stride;
         const int x = (int)(it * kRowChunks * 4u);           // uint32 elements: 16-byte aligned
-        mbar_expect_tx(&full[st], (unsigned)rows * kRowChunks * 16u);
+        mbar_expect_tx(&full[st], stride * 16u);
         tma_load_3d(d, col, x, i, j0 - 1, &full[st]);
         tma_load_3d(d + 10 * kRowChunks, side, x, im, j0, &full[st]);
         tma_load_3d(d + 18 * kRowChunks, side, x, ip, j0, &full[st]);
         if (extra) tma_load_3d(d + 26 * kRowChunks, extra, x, i, j0, &full[st]);
+        if (vprow) {                 // the velocity pairs of this row: (vx, vy) block, then (w, h) block
+            uint4* t = d + (size_t)rows * kRowChunks;
+            bulk_load(t, vpa + (size_t)it * vprow, vprow * 16u, &full[st]);
+            bulk_load(t + vprow, vpb + (size_t)it * vprow, vprow * 16u, &full[st]);
+        }
     }
 };
 
@@ -348,7 +365,7 @@ __device__ __forceinline__ bool pipeline_step(const Feed& F, unsigned it, unsign
     const unsigned st = it % kStages, ph = (it / kStages) & 1u;
     const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&F.full[st], ph));
     if (!got) return false;
-    body(F.stage + (size_t)st * F.rows * kRowChunks);
+    body(F.stage + (size_t)st * F.stride);
     __syncwarp();
     if (lane == 0) {
         // after round r of stage st its counter reaches (r + 1) A; the warp that brings it there is last
@@ -440,7 +457,9 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
                     const int kp = q * NP + pp;                  // velocity pair 2kp, 2kp+1
-                    const float4 A = P.vp[2 * kp], B = P.vp[2 * kp + 1];
+                    const int lp = (cc * 32 + lane) * NP + pp;   // its slot in the staged table
+                    const float4* sA = reinterpret_cast<const float4*>(d + F.rows * kRowChunks);
+                    const float4 A = sA[lp], B = sA[F.vprow + lp];
                     const float2 vx = make_float2(A.x, A.y), vy = make_float2(A.z, A.w);
                     const float2 wk = make_float2(B.x, B.y), hv = make_float2(B.z, B.w);
                     const float2 a0 = pfma(s0y, vy, pmul(s0x, vx)), a1 = pfma(s1y, vy, pmul(s1x, vx));
@@ -630,8 +649,14 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
     return true;
 }
 
-constexpr int primal_smem_bytes() { return kStages * kPrimalRows * kRowChunks * 16 + 2 * kStages * 8; }
-constexpr int adjoint_smem_bytes() { return kStages * kAdjointRows * kRowChunks * 16 + 2 * kStages * 8; }
+// Velocity pairs per stage row staged with the distribution (paired FP32 arithmetic only).
+template <class TS> constexpr unsigned kVpRow = kPaired<TS> ? kRowChunks * (Pack<TS>::KV / 2) : 0;
+template <class TS> constexpr int primal_smem_bytes() {
+    return kStages * (kPrimalRows * kRowChunks + 2 * kVpRow<TS>) * 16 + 2 * kStages * 8;
+}
+template <class TS> constexpr int adjoint_smem_bytes() {
+    return kStages * (kAdjointRows * kRowChunks + 2 * kVpRow<TS>) * 16 + 2 * kStages * 8;
+}
 
 // Block prologue/epilogue shared by both sweeps: barriers, active warps, the first
 // stages and, on exit, the drain of copies still in flight.
@@ -643,14 +668,17 @@ struct BlockPipe {
 
 __device__ __forceinline__ bool block_pipe_setup(BlockPipe& B, unsigned char* smem, int rows, int nj, int ni,
                                                  unsigned nq, const CUtensorMap* col, const CUtensorMap* side,
-                                                 const CUtensorMap* extra, int i, int j0) {
+                                                 const CUtensorMap* extra, int i, int j0, const float4* vpa,
+                                                 const float4* vpb, unsigned vprow) {
     B.A = min(kWarpsPerBlock, nj - j0);
     B.niter = (nq + kRowChunks - 1) / kRowChunks;
     B.F.col = col; B.F.side = side; B.F.extra = extra;
     B.F.i = i; B.F.im = (i - 1 + ni) % ni; B.F.ip = (i + 1) % ni; B.F.j0 = j0; B.F.rows = rows;
     B.F.A = (unsigned)B.A;
+    B.F.vpa = vpa; B.F.vpb = vpb; B.F.vprow = vprow;
+    B.F.stride = (unsigned)rows * kRowChunks + 2u * vprow;
     B.F.stage = reinterpret_cast<uint4*>(smem);
-    B.F.full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * rows * kRowChunks * 16);
+    B.F.full = reinterpret_cast<uint64_t*>(smem + (size_t)kStages * B.F.stride * 16);
     B.F.released = reinterpret_cast<unsigned*>(B.F.full + kStages);
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -674,7 +702,9 @@ template <class TS, bool kRes>
 __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
                                              const CUtensorMap* m8, int i, int j0, unsigned char* smem) {
     BlockPipe B;
-    if (!block_pipe_setup(B, smem, kPrimalRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, nullptr, i, j0)) return;
+    if (!block_pipe_setup(B, smem, kPrimalRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, nullptr, i, j0, P.vpa, P.vpb,
+                          kVpRow<TS>))
+        return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = j0 + w, c = j * P.ni + i;
     const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
@@ -805,7 +835,9 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
                     const int kp = q * NP + pp;
-                    const float4 A = P.vp[2 * kp], B = P.vp[2 * kp + 1];
+                    const int lp = (cc * 32 + lane) * NP + pp;
+                    const float4* sA = reinterpret_cast<const float4*>(d + F.rows * kRowChunks);
+                    const float4 A = sA[lp], B = sA[F.vprow + lp];
                     const float2 vx = make_float2(A.x, A.y), vy = make_float2(A.z, A.w);
                     const float2 wk = make_float2(B.x, B.y), hv = make_float2(B.z, B.w);
                     const float2 a3 = pfma(s3y, vy, pmul(s3x, vx));
@@ -1022,7 +1054,9 @@ __device__ __forceinline__ void adjoint_block(const AdjointArgs<TS, typename Pac
                                               const CUtensorMap* m8, const CUtensorMap* mf8, int i, int j0,
                                               unsigned char* smem) {
     BlockPipe B;
-    if (!block_pipe_setup(B, smem, kAdjointRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, mf8, i, j0)) return;
+    if (!block_pipe_setup(B, smem, kAdjointRows, P.nj, P.ni, (unsigned)P.nq, m10, m8, mf8, i, j0, P.vpa, P.vpb,
+                          kVpRow<TS>))
+        return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = j0 + w, c = j * P.ni + i;
     const int bnd = (j == 0 ? kWallCell : 0) | (j == P.nj - 1 ? kFarCell : 0);
@@ -1768,7 +1802,7 @@ template <class TS, class TC>
 void primal_launch(const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
     const auto& a = *static_cast<const PrimalArgs<TS, TC>*>(args);
     const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
-    constexpr int sm = primal_smem_bytes();
+    constexpr int sm = primal_smem_bytes<TS>();
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1793,7 +1827,7 @@ void adjoint_launch(const void* args, const TmaMaps& phi_maps, const TmaMaps& f_
                     cudaStream_t s) {
     const auto& a = *static_cast<const AdjointArgs<TS, TC>*>(args);
     const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
-    constexpr int sm = adjoint_smem_bytes();
+    constexpr int sm = adjoint_smem_bytes<TS>();
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1851,7 +1885,7 @@ cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const Dev
 
 template <class TS, class TC>
 void primal_batch_launch(const void* descs, const int4* items, int n_items, int parity, bool res, cudaStream_t s) {
-    constexpr int sm = primal_smem_bytes();
+    constexpr int sm = primal_smem_bytes<TS>();
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1876,7 +1910,7 @@ cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4
 
 template <class TS, class TC>
 void adjoint_batch_launch(const void* descs, const int4* items, int n_items, int parity, bool res, cudaStream_t s) {
-    constexpr int sm = adjoint_smem_bytes();
+    constexpr int sm = adjoint_smem_bytes<TS>();
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
