@@ -159,11 +159,12 @@ def ncu_traffic(kernel: str, storage: str):
 
 
 # ----------------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(wl, rows=16):
+def cpu_oracle_sample(wl, rows=16, threads=0):
     """One point-implicit primal sweep and one adjoint sweep of the FP64 oracle over the first
-    `rows` cell rows of the workload's mesh (same velocity grid and flow); updates/s."""
+    `rows` cell rows of the workload's mesh (same velocity grid and flow); updates/s.  threads = 0:
+    every host core."""
     from oracle import oracle as O
-    cores = O.threads(os.cpu_count() or 1)
+    cores = O.threads(threads if threads > 0 else (os.cpu_count() or 1))
     nodes = np.ascontiguousarray(wl.mesh.nodes[: rows + 1])
     pr = O.Problem(nodes, wl.grid.vx, wl.grid.vy, wl.grid.w, wl.flow.Kn, wl.flow.Ma, wl.flow.Tw, wl.flow.aoa)
     rng = np.random.default_rng(W.SEED_BASE + 99)
@@ -173,6 +174,7 @@ def cpu_oracle_sample(wl, rows=16):
     pr.jacobi(f)
     pr.adjoint_jacobi(f, phi)
     dt = time.perf_counter() - t
+    O.threads(os.cpu_count() or 1)
     pairs = pr.ncell * wl.grid.nv
     return {"value": 2 * pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "seconds": dt,
@@ -310,6 +312,7 @@ def run_gpu(args):
         line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample(wl).items() if k != "seconds"}
+        line["cpu_baseline"]["value_1_thread"] = cpu_oracle_sample(wl, rows=2, threads=1)["value"]
     if rank == 0:
         print(json.dumps(line))
     ad.close(); st.close(); grid.close(); mesh.close(); ctx.close()

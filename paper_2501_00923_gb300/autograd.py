@@ -98,3 +98,64 @@ class DragFn(torch.autograd.Function):
 
 def drag(alpha: torch.Tensor, problem: DragProblem) -> torch.Tensor:
     return DragFn.apply(alpha, problem)
+
+
+def main(argv=None):
+    """Cd and dCd/dalpha through DragFn on a workload at full size, with central differences of the
+    forward on the first `--fd` amplitudes.  One JSON line: times, sweep counts and statuses of the
+    forward and backward solves, the gradient, and the largest difference from the differences."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(prog="python -m paper_2501_00923_gb300.autograd")
+    ap.add_argument("--workload", type=int, default=2, help="recipe index (2: 384x192, 64x64, Kn 0.001, Ma 2)")
+    ap.add_argument("--kn", type=float, default=None, help="override the recipe's Kn")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-sweeps", type=int, default=200000)
+    ap.add_argument("--stall", type=int, default=3000)
+    ap.add_argument("--fd", type=int, default=0, help="amplitudes checked by central differences")
+    ap.add_argument("--h", type=float, default=1e-4, help="difference step")
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    wl = W.config(args.workload)
+    flow = W.Flow(args.kn if args.kn is not None else wl.flow.Kn, wl.flow.Ma, wl.flow.Tw, wl.flow.aoa)
+    ctx = dvm.Context(0)
+    a0 = wl.mesh.alpha
+    prob = DragProblem(ctx, wl.mesh.ni, wl.mesh.nj, wl.grid, flow, storage=args.storage, tol=args.tol,
+                       adjoint_tol=args.tol, max_iter=args.max_sweeps, stall_window=args.stall)
+    alpha = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    t0 = time.perf_counter()
+    cd = drag(alpha, prob)
+    t1 = time.perf_counter()
+    cd.backward()
+    t2 = time.perf_counter()
+    g = alpha.grad.numpy().copy()
+    pres, ares = prob.last["primal"], prob.last["adjoint"]
+    out = {"workload": wl.name, "Kn": flow.Kn, "storage": args.storage, "cells": wl.mesh.ncell, "velocities": wl.grid.nv,
+           "Cd": float(cd.item()), "forward_s": t1 - t0, "backward_s": t2 - t1,
+           "primal_sweeps": pres.iters, "primal_status": dvm.status_string(pres.status), "primal_residual": pres.residual,
+           "adjoint_sweeps": ares.iters, "adjoint_status": dvm.status_string(ares.status),
+           "adjoint_residual": ares.residual, "grad": g.tolist()}
+    prob.release()
+    if args.fd > 0:
+        fd = []
+        t3 = time.perf_counter()
+        for p in range(args.fd):
+            e = np.zeros_like(a0)
+            e[p] = args.h
+            up = prob.solve(a0 + e)
+            prob.release()
+            dn = prob.solve(a0 - e)
+            prob.release()
+            fd.append((up - dn) / (2 * args.h))
+        fd = np.array(fd)
+        out.update({"fd_params": args.fd, "fd_step": args.h, "fd": fd.tolist(), "fd_s": time.perf_counter() - t3,
+                    "fd_max_diff_rel_to_max_grad": float(np.abs(fd - g[:args.fd]).max() / np.abs(g).max())})
+    print(json.dumps(out))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
