@@ -724,6 +724,15 @@ int orc_apply_RT(const orc_problem* q, const double* f, const double* lam, doubl
     return 0;
 }
 
+/* the point-implicit diagonal D = V/tau + sum_e max(a_e, 0) at the state f, [ncell][nv] */
+int orc_diagonal(const orc_problem* q, const double* f, double* D) {
+    Prob p = to_prob(q);
+    Consts K = make_consts(p);
+    Geo<double> g = geo_of(p);
+    diagonal_all(p, K, g, f, D);
+    return 0;
+}
+
 /* point-implicit (Jacobi) update of every cell: f_new = f - R(f)/D.  Returns the residual norm of
  * the input state in *norm. */
 int orc_jacobi(const orc_problem* q, const double* f, double* fnew, double* norm) {

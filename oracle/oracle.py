@@ -66,6 +66,7 @@ def lib():
             "orc_sens_nod": (i, [_dp, _dp, _dp, _dp, _dp]),
             "orc_sens_paper": (i, [P, _dp, _dp, i, _dp, _dp, _dp, _dp]),
             "orc_wall_face_functional": (d, [_dp, i, _dp, _dp, _dp, _dp, d, _dp]),
+            "orc_diagonal": (i, [P, _dp, _dp]),
             "orc_jacobi_cells": (i, [P, _dp, i, C.POINTER(C.c_int), _dp]),
             "orc_volume_constraint": (d, [P, d, i, _dp, _dp, _dp]),
             "orc_adjoint_jacobi_cells": (i, [P, _dp, _dp, i, C.POINTER(C.c_int), _dp]),
@@ -179,6 +180,12 @@ class Problem:
         return out
 
     # ---------------------------------------------------------------- iterations and solves
+    def diagonal(self, f):
+        """Point-implicit diagonal D = V/tau + sum_e max(a_e, 0), [ncell, nv]."""
+        D = np.zeros((self.ncell, self.nv))
+        lib().orc_diagonal(self.ref, _ptr(_c(f)), _ptr(D))
+        return D
+
     def jacobi(self, f):
         f = _c(f)
         fn = np.zeros(self.fshape())

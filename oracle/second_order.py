@@ -1,0 +1,181 @@
+"""TEST INFRASTRUCTURE (oracle): the second-order spatial reconstruction, in plain numpy.
+
+The first-order residual R1 of the oracle (Eq. numerpr_gov with upwind face values) gains, on every
+interior face, the linear reconstruction of the upwind cell:
+
+    F2_e = F1_e + grad f_up . (x_e - x_up),   up = own cell if a_e = S_e . v > 0, else the neighbour,
+
+with the unlimited Gauss gradient of Eq. (gaussgrad),
+
+    grad f_c = (1 / V_c) sum_e fbar_e S_e,   fbar_e = (f_c + f_nb) / 2 on interior faces, and on the
+    wall and far-field faces the first-order face value (own f where a_e > 0; the diffuse-wall
+    Maxwellian F_rhow gbar, or the free-stream Maxwellian, where a_e <= 0).
+
+x_c is the mean of the cell's four corners and x_e the midpoint of the face.  Boundary faces keep
+their first-order values.  So R2 = R1 + dR with
+
+    dR_c = sum_{interior e} a_e grad f_up . (x_e - x_up),
+
+which is affine in f: the far-field values are constants, and the wall values are linear in f through
+F_rhow.  Its transpose is therefore a constant matrix, assembled here column by column from dR itself
+for small problems.  The point-implicit sweep keeps the first-order diagonal D:
+f <- f - R2 / D (deferred correction).  The adjoint transposes R2: Ra = ((dR2/df)^T (w phi) + dJ/df) / w.
+The wall functional is unchanged (boundary face values are first order).
+
+Nothing here is shared with the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import oracle as O
+
+
+class SecondOrder:
+    """dR, its transpose and the second-order Jacobi sweeps of one oracle Problem."""
+
+    def __init__(self, pr: O.Problem):
+        self.pr = pr
+        ni, nj, nv = pr.ni, pr.nj, pr.nv
+        self.ni, self.nj, self.nv = ni, nj, nv
+        V, S = pr.geometry()
+        self.V, self.S = V, S                                        # [nc], [nc, 4, 2]
+        X = pr.nodes                                                 # [(nj+1), ni, 2]
+        ip = (np.arange(ni) + 1) % ni
+        P = np.stack([X[:-1, :, :], X[1:, :, :], X[1:, ip, :], X[:-1, ip, :]], 2)  # [nj, ni, 4, 2]
+        P = P.reshape(ni * nj, 4, 2)
+        self.xc = P.mean(1)                                          # [nc, 2]
+        self.xe = 0.5 * (P + np.roll(P, -1, axis=1))                 # face e: P_e -> P_{e+1}
+        # neighbours: face 0 (i-1), 1 (j+1 or far field), 2 (i+1), 3 (j-1 or wall); -1 far, -2 wall
+        c = np.arange(ni * nj)
+        i, j = c % ni, c // ni
+        self.nb = np.stack([j * ni + (i - 1) % ni,
+                            np.where(j < nj - 1, (j + 1) * ni + i, -1),
+                            j * ni + (i + 1) % ni,
+                            np.where(j > 0, (j - 1) * ni + i, -2)], 1)
+        vx, vy = pr.vx, pr.vy
+        self.a = S[:, :, 0, None] * vx[None, None, :] + S[:, :, 1, None] * vy[None, None, :]   # [nc, 4, nv]
+        self.f_far = pr.freestream()[0]                              # [nv, 2]
+        Tw = pr.Tw
+        g1 = np.exp(-(vx ** 2 + vy ** 2) / (2 * Tw)) / (2 * np.pi * Tw)
+        self.gbar = np.stack([g1, 0.5 * Tw * g1], 1)                 # [nv, 2], unnormalised
+        A = np.linalg.norm(S[:, 3, :], axis=1)
+        self.vn_wall = self.a[:, 3, :] / A[:, None]                  # v . n on the wall face
+
+    # ------------------------------------------------------------------ face values and gradients
+    def _boundary_values(self, f):
+        """First-order values on the far-field (face 1) and wall (face 3) faces, [nc, nv, 2] each."""
+        w = self.pr.w
+        far = np.where((self.a[:, 1, :] > 0)[..., None], f, self.f_far[None])
+        vn = self.vn_wall
+        D = -np.sum(np.where(vn <= 0, w[None] * vn * self.gbar[None, :, 0], 0.0), 1)            # [nc]
+        Fw = np.sum(np.where(vn > 0, w[None] * vn * f[:, :, 0], 0.0), 1)
+        gw = (Fw / D)[:, None, None] * self.gbar[None]
+        wall = np.where((self.a[:, 3, :] > 0)[..., None], f, gw)
+        return far, wall
+
+    def gradients(self, f):
+        """Gauss gradient of Eq. (gaussgrad) per cell, velocity and component: [nc, nv, 2 comp, 2 xy]."""
+        far, wall = self._boundary_values(f)
+        gsum = np.zeros(f.shape + (2,))
+        for e in range(4):
+            n = self.nb[:, e]
+            inside = n >= 0
+            fbar = np.where(inside[:, None, None], 0.5 * (f + f[np.where(inside, n, 0)]), 0.0)
+            if e == 1:
+                fbar = np.where(inside[:, None, None], fbar, far)
+            if e == 3:
+                fbar = np.where(inside[:, None, None], fbar, wall)
+            gsum += fbar[..., None] * self.S[:, e, None, None, :]
+        return gsum / self.V[:, None, None, None]
+
+    def delta_r(self, f):
+        """dR = R2 - R1, [nc, nv, 2]."""
+        f = np.asarray(f, dtype=np.float64)
+        G = self.gradients(f)
+        out = np.zeros_like(f)
+        for e in range(4):
+            n = self.nb[:, e]
+            inside = n >= 0
+            ns = np.where(inside, n, 0)
+            a = self.a[:, e, :]                                       # [nc, nv]
+            own = np.einsum("cvkx,cx->cvk", G, self.xe[:, e] - self.xc)
+            nbr = np.einsum("cvkx,cx->cvk", G[ns], self.xe[:, e] - self.xc[ns])
+            corr = np.where((a > 0)[..., None], own, nbr)
+            out += np.where(inside[:, None, None], a[..., None] * corr, 0.0)
+        return out
+
+    def face_values(self, f, e):
+        """First- and second-order values on face e of every cell (interior faces), [nc, nv, 2] x 2."""
+        G = self.gradients(f)
+        n = self.nb[:, e]
+        ns = np.where(n >= 0, n, 0)
+        a = self.a[:, e, :]
+        up_own = (a > 0)[..., None]
+        F1 = np.where(up_own, f, f[ns])
+        own = np.einsum("cvkx,cx->cvk", G, self.xe[:, e] - self.xc)
+        nbr = np.einsum("cvkx,cx->cvk", G[ns], self.xe[:, e] - self.xc[ns])
+        return F1, F1 + np.where(up_own, own, nbr)
+
+    # ------------------------------------------------------------------ linear structure
+    def matrix(self):
+        """dR(f) = L f + b: L assembled column by column (small problems only), b = dR(0)."""
+        n = self.pr.ncell * self.nv * 2
+        b = self.delta_r(np.zeros(self.pr.fshape())).ravel()
+        L = np.zeros((n, n))
+        for col in range(n):
+            e = np.zeros(n)
+            e[col] = 1.0
+            L[:, col] = self.delta_r(e.reshape(self.pr.fshape())).ravel() - b
+        return L, b
+
+    # ------------------------------------------------------------------ sweeps
+    def diagonal(self, f):
+        """First-order point-implicit diagonal D = V/tau + sum_e max(a_e, 0), [nc, nv]."""
+        return self.pr.diagonal(f)
+
+    def residual(self, f):
+        R1, _ = self.pr.residual(f)
+        return R1 + self.delta_r(f)
+
+    def jacobi(self, f, source=None):
+        """One point-implicit sweep of the second-order residual: f - (R2 + source) / D."""
+        f = np.asarray(f, dtype=np.float64)
+        D = self.diagonal(f)
+        R = self.residual(f) if source is None else self.residual(f) + source
+        return f - R / D[..., None]
+
+    def solve(self, f0=None, source=None, tol=1e-13, max_sweeps=20000):
+        """Second-order steady state by repeated point-implicit sweeps (small problems)."""
+        f = self.pr.freestream() if f0 is None else np.array(f0, dtype=np.float64)
+        for it in range(max_sweeps):
+            fn = self.jacobi(f, source)
+            step = np.abs(fn - f).max()
+            f = fn
+            if step < tol * np.abs(f).max():
+                return f, it + 1
+        return f, max_sweeps
+
+    def adjoint_solve(self, f, tol=1e-13, max_sweeps=20000):
+        L, _ = self.matrix()
+        phi = np.zeros(self.pr.fshape())
+        for it in range(max_sweeps):
+            pn = self.adjoint_jacobi(f, phi, L)
+            step = np.abs(pn - phi).max()
+            phi = pn
+            if step < tol * max(np.abs(phi).max(), 1e-300):
+                return phi, it + 1
+        return phi, max_sweeps
+
+    def adjoint_jacobi(self, f, phi, L=None):
+        """One point-implicit sweep of the second-order adjoint: phi - Ra / D with
+        Ra = ((dR1/df + L)^T (w phi) + dJ/df) / w (L from matrix(), passed to avoid rebuilding it)."""
+        f = np.asarray(f, dtype=np.float64)
+        if L is None:
+            L, _ = self.matrix()
+        w = self.pr.w[None, :, None]
+        lam = (w * phi).ravel()
+        Ra1 = self.pr.apply_RT(f, (w * phi)) + self.pr.functional_grad(f)
+        Ra = (Ra1 + (L.T @ lam).reshape(Ra1.shape)) / w
+        D = self.diagonal(f)
+        return phi - Ra / D[..., None]
