@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--workload", type=int, default=WORKLOAD_INDEX, choices=[1, 2, 4],
                    help="1: 256x128 GL48 Kn 0.1 (default); 2: 384x192 64x64 Kn 0.001 Ma 2; "
                         "4: 256x128 GL48, 24 bumps (design-loop size)")
+    p.add_argument("--order", type=int, default=1, choices=[1, 2],
+                   help="spatial order of the face values (2: linear reconstruction, defect correction)")
+    p.add_argument("--defect-period", type=int, default=4, help="sweeps per second-order defect")
     p.add_argument("--serve", type=int, default=128, help="requests of the served trace to replay (0: skip)")
     p.add_argument("--serve-max-iter", type=int, default=400, help="sweep cap per phase of a served request")
     return p.parse_args()
@@ -230,6 +233,8 @@ def run_gpu(args):
     grid = dvm.VGrid(ctx, wl.grid.vx, wl.grid.vy, wl.grid.w)
     Kn, Ma = wl.flow.Kn, wl.flow.Ma
     st, _ = dvm.primal_solve(ctx, mesh, grid, Kn, Ma, tol=0.0, max_iter=args.sweeps, storage=args.storage)
+    if args.order == 2:
+        st.set_order(2, args.defect_period)
     ad, _ = dvm.adjoint_solve(ctx, st, tol=0.0, max_iter=args.sweeps)
 
     def step(events=None):
@@ -241,7 +246,7 @@ def run_gpu(args):
         dvm.adjoint_solve(ctx, st, tol=0.0, max_iter=args.sweeps, adjoint=ad)
         if events:
             events[2].record(stream)
-        g_full = dvm.sensitivity(ctx, st, ad, wl.mesh.dwall, wl.mesh.s, mode="full")
+        g_full = dvm.sensitivity(ctx, st, ad, wl.mesh.dwall, wl.mesh.s, mode="full") if args.order == 1 else None
         g_paper = dvm.sensitivity(ctx, st, ad, wl.mesh.dwall, mode="paper")
         if events:
             events[3].record(stream)
@@ -272,17 +277,21 @@ def run_gpu(args):
     value, total_ms = job_throughput(2 * args.sweeps * pairs * args.steps, total_ms, device="cuda")
 
     # roofline of the dominant kernel (algorithmic bytes: read f + write f' = 4S per primal update,
-    # read phi, f + write phi' = 6S per adjoint update; S = bytes per stored scalar)
+    # read phi, f + write phi' = 6S per adjoint update; S = bytes per stored scalar).  Second order adds
+    # the defect read (2S) to every sweep and, once per defect period, the reconstruction: read f or phi
+    # (2S), write and read the two gradient components (4S + 4S), write the defect (2S).
     S = {"fp32": 4, "bf16": 2, "fp64": 8}[args.storage]
     n_sw = args.sweeps * args.steps
     prim_sweep_ms, adj_sweep_ms = prim_ms / n_sw, adj_ms / n_sw
     peak, peak_kind = hbm_peak()
-    k_prim = {"name": "k_primal_sweep", "ms": prim_sweep_ms, "bytes": pairs * 4 * S,
-              "GBps": pairs * 4 * S / (prim_sweep_ms * 1e6)}
-    k_adj = {"name": "k_adjoint_sweep", "ms": adj_sweep_ms, "bytes": pairs * 6 * S,
-             "GBps": pairs * 6 * S / (adj_sweep_ms * 1e6)}
+    extra = 0.0 if args.order == 1 else 2 + 12.0 / args.defect_period
+    suffix = "" if args.order == 1 else " + reconstruction (per sweep)"
+    k_prim = {"name": "k_primal_sweep" + suffix, "ms": prim_sweep_ms, "bytes": pairs * (4 + extra) * S,
+              "GBps": pairs * (4 + extra) * S / (prim_sweep_ms * 1e6)}
+    k_adj = {"name": "k_adjoint_sweep" + suffix, "ms": adj_sweep_ms, "bytes": pairs * (6 + extra) * S,
+             "GBps": pairs * (6 + extra) * S / (adj_sweep_ms * 1e6)}
     dom = k_adj if adj_ms >= prim_ms else k_prim
-    alt = bool(args.mesh) or args.workload != WORKLOAD_INDEX
+    alt = bool(args.mesh) or args.workload != WORKLOAD_INDEX or args.order != 1
     traffic = ncu_traffic(dom["name"], args.storage) if not alt else None
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": dom["GBps"] / peak, "traffic": traffic, "kernel": dom["name"],
@@ -293,7 +302,7 @@ def run_gpu(args):
                           for k in (k_prim, k_adj)}}
 
     # end-to-end through the public API with host buffers
-    e2e = run_e2e(args, ctx, wl, torch, dvm)
+    e2e = run_e2e(args, ctx, wl, torch, dvm) if args.order == 1 else None
 
     clocks = clk.summary()
     serving = run_serving(args, torch, dvm) if (args.serve > 0 and not alt) else None
@@ -303,6 +312,7 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {"workload": wl.name, "cells": wl.mesh.ncell, "velocities": wl.grid.nv,
                        "sweeps_per_phase": args.sweeps, "sensitivity_params": P,
+                       "order": args.order, **({"defect_period": args.defect_period} if args.order == 2 else {}),
                        "l2": "inputs larger than L2 (f = %.0f MB)" % (pairs * 2 * S / 1e6),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "phase_ms_per_step": {"primal": prim_ms / args.steps, "adjoint": adj_ms / args.steps,
@@ -310,7 +320,7 @@ def run_gpu(args):
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches)}
     if serving:
         line["serving"] = serving
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.order == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample(wl).items() if k != "seconds"}
         line["cpu_baseline"]["value_1_thread"] = cpu_oracle_sample(wl, rows=2, threads=1)["value"]
     if rank == 0:

@@ -155,6 +155,27 @@ int dvm_state_set(dvm_state* st, const double* f_host);
 int dvm_state_get(const dvm_state* st, double* f_host);
 /* Download per-cell primitive variables (rho, u1, u2, T) [ncell][4] of the current f. */
 int dvm_state_moments(const dvm_state* st, double* prim_host);
+/* Spatial order of the face values used by every later sweep of this state and of its adjoints.
+ * order 1 (the default): first-order upwind values, Eq. (numerpr_gov).  order 2: on interior faces the
+ * upwind cell's linear reconstruction F_e = f_up + grad f_up . (x_e - x_up), with the unlimited Gauss
+ * gradient of Eq. (gaussgrad) (face averages inside, the first-order value on wall and far-field faces;
+ * x_c the mean of the cell's corners, x_e the face midpoint).  Sweeps of order 2 are defect correction:
+ * the added flux dR is taken from the sweep's input at the first sweep of every group of
+ * defect_period sweeps (0 -> 4) and frozen for the rest of the group, while each sweep keeps the
+ * first-order point-implicit form,
+ *   f_new = [ V g/tau + sum_{a<=0} (-a) F_up - dR ] / [ V/tau + sum_{a>0} a ],
+ * so a converged solve satisfies R1(f) + dR(f) = 0 whatever the period.  (A period of 1 can diverge:
+ * with the unlimited reconstruction the point-implicit map is unstable in weakly collisional modes.)
+ * Adjoint sweeps take the exact transpose of dR, (dR/df)^T (w phi) / w, frozen the same way.  Boundary
+ * faces, the drag and the wall density stay first order.  The first call with order 2 allocates three
+ * buffers of the size of f for the state and one for each adjoint swept later (counted against the HBM
+ * budget: DVM_ERR_ADMISSION).  dvm_state_set and an adjoint upload retake the defect at the next sweep;
+ * the residual normaliser r0 keeps its value from state creation.  With order 2, dvm_sensitivity
+ * accepts DVM_SENS_PAPER only (DVM_ERR_INVALID_ARG for DVM_SENS_FULL); dvm_batch requests stay first
+ * order.  Errors: DVM_ERR_INVALID_ARG (NULL, order not 1 or 2, defect_period < 0), DVM_ERR_ADMISSION,
+ * DVM_ERR_OOM. */
+int dvm_state_set_order(dvm_state* st, int order, int defect_period);
+int dvm_state_get_order(const dvm_state* st, int* order);
 /* Run exactly n point-implicit sweeps (Eq. numerpr_gov solved for f_{c,k} with the neighbours,
  * moments and wall density of the previous sweep):
  *   f_new = [ V g/tau + sum_{a<=0} (-a) F_up ] / [ V/tau + sum_{a>0} a ],  a = A n . v_k.

@@ -19,8 +19,13 @@ their first-order values.  So R2 = R1 + dR with
 which is affine in f: the far-field values are constants, and the wall values are linear in f through
 F_rhow.  Its transpose is therefore a constant matrix, assembled here column by column from dR itself
 for small problems.  The point-implicit sweep keeps the first-order diagonal D:
-f <- f - R2 / D (deferred correction).  The adjoint transposes R2: Ra = ((dR2/df)^T (w phi) + dJ/df) / w.
-The wall functional is unchanged (boundary face values are first order).
+f <- f - (R1(f) + dR) / D, with dR taken from the state at the start of each group of `period`
+sweeps and frozen inside the group (defect correction: each group is a few first-order sweeps on
+R1(f) = -dR).  period = 1 recomputes dR every sweep; with the unlimited reconstruction that plain
+iteration can diverge in weakly collisional modes, while frozen groups of a few sweeps converge to the
+same fixed point R1 + dR = 0.  The adjoint transposes R2: Ra = ((dR2/df)^T (w phi) + dJ/df) / w, with
+the transposed defect frozen the same way.  The wall functional is unchanged (boundary face values
+are first order).
 
 Nothing here is shared with the CUDA path.
 """
@@ -138,44 +143,59 @@ class SecondOrder:
         R1, _ = self.pr.residual(f)
         return R1 + self.delta_r(f)
 
-    def jacobi(self, f, source=None):
-        """One point-implicit sweep of the second-order residual: f - (R2 + source) / D."""
+    def jacobi(self, f, source=None, defect=None):
+        """One point-implicit sweep f - (R1(f) + dR + source) / D; dR = delta_r(f) unless a frozen
+        defect is given."""
         f = np.asarray(f, dtype=np.float64)
         D = self.diagonal(f)
-        R = self.residual(f) if source is None else self.residual(f) + source
+        R1, _ = self.pr.residual(f)
+        R = R1 + (self.delta_r(f) if defect is None else defect)
+        if source is not None:
+            R = R + source
         return f - R / D[..., None]
 
-    def solve(self, f0=None, source=None, tol=1e-13, max_sweeps=20000):
-        """Second-order steady state by repeated point-implicit sweeps (small problems)."""
+    def solve(self, f0=None, source=None, tol=1e-13, max_sweeps=20000, period=4):
+        """Second-order steady state by point-implicit sweeps with the defect frozen over groups of
+        `period` sweeps (small problems).  Stops when a sweep moves f by less than tol max|f|."""
         f = self.pr.freestream() if f0 is None else np.array(f0, dtype=np.float64)
         for it in range(max_sweeps):
-            fn = self.jacobi(f, source)
+            if it % period == 0:
+                dR = self.delta_r(f)
+            fn = self.jacobi(f, source, dR)
             step = np.abs(fn - f).max()
             f = fn
             if step < tol * np.abs(f).max():
                 return f, it + 1
         return f, max_sweeps
 
-    def adjoint_solve(self, f, tol=1e-13, max_sweeps=20000):
+    def adjoint_defect(self, phi, L):
+        """Transposed defect (dR/df)^T (w phi) / w, [nc, nv, 2]."""
+        w = self.pr.w[None, :, None]
+        return (L.T @ (w * phi).ravel()).reshape(phi.shape) / w
+
+    def adjoint_solve(self, f, tol=1e-13, max_sweeps=20000, period=4):
         L, _ = self.matrix()
         phi = np.zeros(self.pr.fshape())
         for it in range(max_sweeps):
-            pn = self.adjoint_jacobi(f, phi, L)
+            if it % period == 0:
+                E = self.adjoint_defect(phi, L)
+            pn = self.adjoint_jacobi(f, phi, defect=E)
             step = np.abs(pn - phi).max()
             phi = pn
             if step < tol * max(np.abs(phi).max(), 1e-300):
                 return phi, it + 1
         return phi, max_sweeps
 
-    def adjoint_jacobi(self, f, phi, L=None):
+    def adjoint_jacobi(self, f, phi, L=None, defect=None):
         """One point-implicit sweep of the second-order adjoint: phi - Ra / D with
-        Ra = ((dR1/df + L)^T (w phi) + dJ/df) / w (L from matrix(), passed to avoid rebuilding it)."""
+        Ra = (dR1/df)^T (w phi) / w + dJ/df / w + E, E = (dR/df)^T (w phi) / w from L (matrix(), passed
+        to avoid rebuilding it) unless a frozen defect E is given."""
         f = np.asarray(f, dtype=np.float64)
-        if L is None:
-            L, _ = self.matrix()
         w = self.pr.w[None, :, None]
-        lam = (w * phi).ravel()
-        Ra1 = self.pr.apply_RT(f, (w * phi)) + self.pr.functional_grad(f)
-        Ra = (Ra1 + (L.T @ lam).reshape(Ra1.shape)) / w
+        if defect is None:
+            if L is None:
+                L, _ = self.matrix()
+            defect = self.adjoint_defect(phi, L)
+        Ra = (self.pr.apply_RT(f, (w * phi)) + self.pr.functional_grad(f)) / w + defect
         D = self.diagonal(f)
         return phi - Ra / D[..., None]

@@ -82,6 +82,14 @@ struct dvm_state {
     uint64_t version = 0;       // bumped whenever f changes (sweeps, uploads)
     TmaMaps maps[2];            // tiled-TMA descriptors of f[0], f[1]
     AAState* aa = nullptr;
+    int order = 1;              // spatial order of the face values (2: linear reconstruction)
+    int graph_order = 1;        // order the captured graph was built for
+    void* so[3] = {nullptr, nullptr, nullptr};   // second order: gradient x, y and the frozen defect
+    int so_period = 4;          // sweeps per defect (defect correction groups)
+    int so_phase = 0;           // sweeps since the defect was taken (0: take it at the next sweep)
+    int graph_phase = 0;        // so_phase at the start of the captured graph
+    int graph_so = 0;           // reconstruction launches inside the captured graph
+    bool capturing = false;
 };
 
 struct dvm_adjoint {
@@ -103,6 +111,12 @@ struct dvm_adjoint {
     int graph_n = 0;
     int graph_cur = -1;
     int graph_st_cur = -1;
+    int graph_order = 1;
+    int graph_phase = 0;
+    int graph_so = 0;
+    bool capturing = false;
+    void* so_def = nullptr;     // second order: frozen transposed defect (dR/df)^T (w phi) / w
+    int so_phase = 0;
     TmaMaps maps[2];            // tiled-TMA descriptors of phi[0], phi[1]
     // sensitivity scratch, allocated on first use
     double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr;
@@ -250,6 +264,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     a.Jpart = st->Jpart;
     a.respart = st->respart;
     a.err = st->ctx->derr;
+    a.defect = st->order == 2 ? (const TS*)st->so[2] : nullptr;
     return a;
 }
 
@@ -287,10 +302,68 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     a.Lam_new = ad->Lam[1 - src];
     a.respart = ad->respart;
     a.err = st->ctx->derr;
+    a.defect = st->order == 2 ? (const TS*)ad->so_def : nullptr;
     return a;
 }
 
+// Second-order reconstruction of `in` (f of the state, or an adjoint phi) into the state's scratch.
+template <class TS, class TC>
+SOArgs<TS, TC> so_args(const dvm_state* st, const void* in, const double* Fw, void* out) {
+    SOArgs<TS, TC> a{};
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    constexpr int KV = 16 / (2 * (int)sizeof(TS));
+    a.ncell = m.ncell;
+    a.nq = g.nvp / KV;
+    a.ni = m.ni;
+    a.nb = m.nb;
+    if constexpr (sizeof(TC) == 8) {
+        a.S = m.Sd; a.V = m.Vd; a.vt = g.vd; a.fd = st->fl.fdd; a.gw = st->fl.gwd;
+    } else {
+        a.S = m.Sf; a.V = m.Vf; a.vt = g.vf; a.fd = st->fl.fdf; a.gw = st->fl.gwf;
+    }
+    a.wallD = st->fl.wallD;
+    a.halfTw = (TC)(0.5 * st->fl.Tw);
+    a.nodes = m.nodes;
+    a.in = (const TS*)in;
+    a.Fw = Fw;
+    a.gx = (TS*)st->so[0];
+    a.gy = (TS*)st->so[1];
+    a.out = (TS*)out;
+    return a;
+}
+
+cudaError_t enqueue_second_order(const dvm_state* st, const void* in, const double* Fw, void* out, bool adjoint) {
+    cudaStream_t s = st->ctx->stream;
+    switch (st->storage) {
+        case DVM_STORE_FP64: { auto a = so_args<double, double>(st, in, Fw, out); return launch_second_order(0, &a, adjoint, s); }
+        case DVM_STORE_FP32: { auto a = so_args<float, float>(st, in, Fw, out); return launch_second_order(1, &a, adjoint, s); }
+        default: { auto a = so_args<__nv_bfloat16, float>(st, in, Fw, out); return launch_second_order(2, &a, adjoint, s); }
+    }
+}
+
+// Defect correction: the defect is taken from the sweep's input at the first sweep of each group of
+// so_period sweeps and frozen for the rest of the group.  Counts its launches (into the graph's count
+// while a graph is being captured).
+cudaError_t enqueue_defect_if_due(dvm_state* st, int& phase, bool& capturing, int& graph_so, const void* in,
+                                  const double* Fw, void* out, bool adjoint) {
+    cudaError_t e = cudaSuccess;
+    if (!out || !st->so[0] || !st->so[1]) return cudaErrorInvalidValue;   // buffers of order 2 missing
+    if (phase == 0) {
+        e = enqueue_second_order(st, in, Fw, out, adjoint);
+        if (capturing) graph_so += 2;
+        else st->ctx->launches += 2;
+    }
+    phase = (phase + 1) % st->so_period;
+    return e;
+}
+
 cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
+    if (st->order == 2) {
+        cudaError_t e = enqueue_defect_if_due(st, st->so_phase, st->capturing, st->graph_so, st->f[src], st->Fw[src],
+                                              st->so[2], false);
+        if (e != cudaSuccess) return e;
+    }
     switch (st->storage) {
         case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); return launch_primal_sweep(0, &a, st->maps[src], res, st->ctx->stream); }
         case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); return launch_primal_sweep(1, &a, st->maps[src], res, st->ctx->stream); }
@@ -300,6 +373,11 @@ cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
 
 cudaError_t enqueue_adjoint(dvm_adjoint* ad, int src, bool update = true, bool res = true) {
     cudaStream_t s = ad->st->ctx->stream;
+    if (update && ad->st->order == 2) {
+        cudaError_t e = enqueue_defect_if_due(ad->st, ad->so_phase, ad->capturing, ad->graph_so, ad->phi[src], nullptr,
+                                              ad->so_def, true);
+        if (e != cudaSuccess) return e;
+    }
     const TmaMaps& pm = ad->maps[src];
     const TmaMaps& fm = ad->st->maps[ad->st->cur];
     switch (ad->st->storage) {
@@ -322,6 +400,7 @@ cudaError_t adjoint_relinearise(dvm_adjoint* ad) {
 // Rebuild the couplings (Z, Lambda) of phi[cur] in place: a non-updating pass whose outputs land in
 // the slot the next sweep reads.
 cudaError_t refresh_adjoint_couplings(dvm_adjoint* ad) {
+    ad->so_phase = 0;           // phi changed outside the sweeps: retake the second-order defect
     // the non-updating pass reads phi[cur] and writes Z/Lam of slot 1-cur; copy them to slot cur
     cudaError_t e = enqueue_adjoint(ad, ad->cur, false);
     const DevMesh& m = ad->st->mesh->d;
@@ -520,38 +599,55 @@ bool graphs_ok(const dvm_context* ctx) { return ctx->stream != nullptr && !(ctx-
 
 // Capture K (even) sweeps + one finalize.  Buffers return to the same parity after K sweeps.
 int build_primal_graph(dvm_state* st, int K) {
-    if (st->graph && st->graph_n == K && st->graph_cur == st->cur) return DVM_OK;
+    if (st->graph && st->graph_n == K && st->graph_cur == st->cur && st->graph_order == st->order &&
+        st->graph_phase == st->so_phase)
+        return DVM_OK;
     if (st->graph) { cudaGraphExecDestroy(st->graph); st->graph = nullptr; }
     cudaStream_t s = st->ctx->stream;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int cur = st->cur;
+    const int phase0 = st->so_phase;
+    st->capturing = true;
+    st->graph_so = 0;
     for (int i = 0; i < K; ++i) {
         enqueue_primal(st, cur, i == K - 1);
         if (i == K - 1) enqueue_primal_finalize(st, 1 - cur, st->out);
         cur = 1 - cur;
     }
+    st->capturing = false;
+    st->so_phase = phase0;      // the sweeps run when the graph is launched
+    st->graph_phase = phase0;
     CK(cudaStreamEndCapture(s, &g));
     cudaError_t e = cudaGraphInstantiate(&st->graph, g, 0);
     cudaGraphDestroy(g);
     CK(e);
     st->graph_n = K;
     st->graph_cur = st->cur;
+    st->graph_order = st->order;
     return DVM_OK;
 }
 
 int build_adjoint_graph(dvm_adjoint* ad, int K) {
-    if (ad->graph && ad->graph_n == K && ad->graph_cur == ad->cur && ad->graph_st_cur == ad->st->cur) return DVM_OK;
+    if (ad->graph && ad->graph_n == K && ad->graph_cur == ad->cur && ad->graph_st_cur == ad->st->cur &&
+        ad->graph_order == ad->st->order && ad->graph_phase == ad->so_phase)
+        return DVM_OK;
     if (ad->graph) { cudaGraphExecDestroy(ad->graph); ad->graph = nullptr; }
     cudaStream_t s = ad->st->ctx->stream;
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int cur = ad->cur;
+    const int phase0 = ad->so_phase;
+    ad->capturing = true;
+    ad->graph_so = 0;
     for (int i = 0; i < K; ++i) {
         enqueue_adjoint(ad, cur, true, i == K - 1);
         if (i == K - 1) enqueue_adjoint_finalize(ad, ad->out);
         cur = 1 - cur;
     }
+    ad->capturing = false;
+    ad->so_phase = phase0;
+    ad->graph_phase = phase0;
     CK(cudaStreamEndCapture(s, &g));
     cudaError_t e = cudaGraphInstantiate(&ad->graph, g, 0);
     cudaGraphDestroy(g);
@@ -559,6 +655,7 @@ int build_adjoint_graph(dvm_adjoint* ad, int K) {
     ad->graph_n = K;
     ad->graph_cur = ad->cur;
     ad->graph_st_cur = ad->st->cur;
+    ad->graph_order = ad->st->order;
     return DVM_OK;
 }
 
@@ -801,6 +898,7 @@ void dvm_state_destroy(dvm_state* st) {
     if (st->graph) cudaGraphExecDestroy(st->graph);
     for (int b = 0; b < 2; ++b) { dfree(st->f[b]); dfree(st->prim[b]); dfree(st->Fw[b]); }
     dfree(st->Jpart); dfree(st->respart); dfree(st->out); dfree(st->scratch);
+    for (void* p : st->so) dfree(p);
     dfree(st->fl.fdd); dfree(st->fl.fdf); dfree(st->fl.gwd); dfree(st->fl.gwf); dfree(st->fl.wallD); dfree(st->fl.wallM);
     aa_free(st->ctx, st->aa);
     st->ctx->bytes -= st->bytes;
@@ -901,6 +999,7 @@ int dvm_state_set(dvm_state* st, const double* f_host) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
     st->ctx->launches += 2;
     st->version += 1;
+    st->so_phase = 0;
     dfree(tmp);
     if (e != cudaSuccess) return fail_cuda(e, "state upload");
     return DVM_OK;
@@ -930,6 +1029,54 @@ int dvm_state_moments(const dvm_state* st, double* prim_host) {
     CK(cudaMemcpyAsync(prim_host, st->prim[st->cur], st->mesh->d.ncell * sizeof(double4), cudaMemcpyDeviceToHost,
                        st->ctx->stream));
     CK(cudaStreamSynchronize(st->ctx->stream));
+    return DVM_OK;
+}
+
+int dvm_state_set_order(dvm_state* st, int order, int defect_period) {
+    if (!st) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (order != 1 && order != 2) return fail(DVM_ERR_INVALID_ARG, "order must be 1 or 2");
+    if (defect_period < 0) return fail(DVM_ERR_INVALID_ARG, "defect_period must be >= 0");
+    if (order == 2 && !st->so[0]) {
+        dvm_context* ctx = st->ctx;
+        const size_t nb = (size_t)st->mesh->d.ncell * st->grid->d.nvp * storage_bytes(st->storage);
+        if (ctx->budget && ctx->bytes + 3 * nb > ctx->budget)
+            return fail(DVM_ERR_ADMISSION, "second-order buffers do not fit the context's HBM budget");
+        DeviceGuard dg(ctx->device);
+        size_t acc = 0;
+        int rc = DVM_OK;
+        for (int b = 0; b < 3 && !rc; ++b) rc = dalloc(ctx, (unsigned char**)&st->so[b], nb, &acc);
+        if (rc) {
+            for (void*& p : st->so) { dfree(p); p = nullptr; }
+            return rc;
+        }
+        st->bytes += acc;
+        ctx->bytes += acc;
+    }
+    st->order = order;
+    st->so_period = defect_period > 0 ? defect_period : 4;
+    st->so_phase = 0;
+    return DVM_OK;
+}
+
+// The adjoint's frozen defect buffer, allocated when a sweep of a second-order state first needs it.
+static int adjoint_so_ensure(dvm_adjoint* ad) {
+    if (ad->st->order != 2 || ad->so_def) return DVM_OK;
+    dvm_context* ctx = ad->st->ctx;
+    const size_t nb = (size_t)ad->st->mesh->d.ncell * ad->st->grid->d.nvp * storage_bytes(ad->st->storage);
+    if (ctx->budget && ctx->bytes + nb > ctx->budget)
+        return fail(DVM_ERR_ADMISSION, "second-order adjoint buffer does not fit the context's HBM budget");
+    size_t acc = 0;
+    int rc = dalloc(ctx, (unsigned char**)&ad->so_def, nb, &acc);
+    if (rc) return rc;
+    ad->bytes += acc;
+    ctx->bytes += acc;
+    ad->so_phase = 0;
+    return DVM_OK;
+}
+
+int dvm_state_get_order(const dvm_state* st, int* order) {
+    if (!st || !order) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    *order = st->order;
     return DVM_OK;
 }
 
@@ -1010,7 +1157,8 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         if (use_graph && k == K) {
             if ((rc = build_primal_graph(st, K))) return rc;
             CK(cudaGraphLaunch(st->graph, ctx->stream));
-            ctx->launches += K + 1;
+            ctx->launches += K + 1 + st->graph_so;
+            if (st->order == 2) st->so_phase = (st->so_phase + K) % st->so_period;
             st->version += (uint64_t)K;
         } else if ((rc = run_primal_plain(st, k, nullptr))) {
             return rc;
@@ -1038,6 +1186,7 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
                 return rc;
             }
             if (mixed) {
+                st->so_phase = 0;
                 CK(launch_moments(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur],
                                   st->Fw[st->cur], ctx->stream));
                 ctx->launches += 1;
@@ -1068,7 +1217,7 @@ void dvm_adjoint_destroy(dvm_adjoint* ad) {
     for (int b = 0; b < 2; ++b) { dfree(ad->phi[b]); dfree(ad->Z[b]); dfree(ad->Lam[b]); }
     dfree(ad->respart); dfree(ad->out); dfree(ad->wallM); dfree(ad->cell);
     dfree(ad->GN); dfree(ad->GE); dfree(ad->GW); dfree(ad->node_grad); dfree(ad->vol); dfree(ad->elem);
-    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad);
+    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad); dfree(ad->so_def);
     aa_free(ad->st->ctx, ad->aa);
     ad->st->ctx->bytes -= ad->bytes;
     delete ad;
@@ -1079,6 +1228,7 @@ static int adjoint_reset(dvm_adjoint* ad) {
     const DevGrid& g = ad->st->grid->d;
     cudaStream_t s = ad->st->ctx->stream;
     ad->cur = 0;
+    ad->so_phase = 0;
     CK(cudaMemsetAsync(ad->phi[0], 0, (size_t)m.ncell * g.nvp * storage_bytes(ad->st->storage), s));
     CK(cudaMemsetAsync(ad->Z[0], 0, m.ncell * sizeof(double4), s));
     CK(cudaMemsetAsync(ad->Lam[0], 0, m.ni * sizeof(double), s));
@@ -1133,6 +1283,7 @@ int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     dfree(dtmp);
     if (e != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(e, "adjoint setup"); }
     if ((rc = adjoint_reset(ad))) { dvm_adjoint_destroy(ad); return rc; }
+    if ((rc = adjoint_so_ensure(ad))) { dvm_adjoint_destroy(ad); return rc; }
     if ((e = adjoint_relinearise(ad)) != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(e, "adjoint constants"); }
     // r0: adjoint residual at phi = 0 from one discarded sweep
     e = enqueue_adjoint(ad, 0);
@@ -1141,6 +1292,7 @@ int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     if (e != cudaSuccess) { dvm_adjoint_destroy(ad); return fail_cuda(e, "adjoint r0"); }
     double r[2];
     if ((rc = fetch2(ctx, ad->out, r))) { dvm_adjoint_destroy(ad); return rc; }
+    ad->so_phase = 0;          // the r0 sweep is discarded
     ad->r0 = sqrt(r[0]);
     if (!std::isfinite(ad->r0)) { dvm_adjoint_destroy(ad); return fail(DVM_ERR_NONFINITE, "adjoint source not finite"); }
     if (ad->r0 == 0.0) ad->r0 = 1.0;
@@ -1197,6 +1349,7 @@ int dvm_adjoint_iterate(dvm_adjoint* ad, int n, double* residual_out) {
     if (n == 0) return DVM_OK;
     DeviceGuard dg(ad->st->ctx->device);
     int rc0 = adjoint_follow_state(ad);
+    if (!rc0) rc0 = adjoint_so_ensure(ad);
     if (rc0) return rc0;
     double* hist = nullptr;
     int rc = dalloc(ad->st->ctx, &hist, 2 * (size_t)n);
@@ -1234,6 +1387,7 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
     }
     dvm_adjoint* ad = *inout;
     if ((rc = adjoint_follow_state(ad))) return rc;
+    if ((rc = adjoint_so_ensure(ad))) return rc;
     const bool accel = opts->accel_depth > 0;
     const int K = accel ? opts->accel_period : ctx->graph_iters;
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
@@ -1252,7 +1406,8 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         if (use_graph && k == K) {
             if ((rc = build_adjoint_graph(ad, K))) return rc;
             CK(cudaGraphLaunch(ad->graph, ctx->stream));
-            ctx->launches += K + 1;
+            ctx->launches += K + 1 + ad->graph_so;
+            if (st->order == 2) ad->so_phase = (ad->so_phase + K) % st->so_period;
         } else if ((rc = run_adjoint_plain(ad, k, nullptr))) {
             return rc;
         }
@@ -1295,6 +1450,8 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
     if (mode == DVM_SENS_FULL && !s_j) return fail(DVM_ERR_INVALID_ARG, "full mode needs s_j");
     if (cad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
     if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
+    if (mode == DVM_SENS_FULL && st->order != 1)
+        return fail(DVM_ERR_INVALID_ARG, "the full discrete gradient is first-order only; use DVM_SENS_PAPER");
     DeviceGuard dg(ctx->device);
     Range nvtx("dvm_sensitivity");
     dvm_adjoint* ad = const_cast<dvm_adjoint*>(cad);
@@ -1422,6 +1579,8 @@ extern "C" int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, co
     if (mode == DVM_SENS_FULL && !s_j) return fail(DVM_ERR_INVALID_ARG, "full mode needs s_j");
     if (ad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
     if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
+    if (mode == DVM_SENS_FULL && st->order != 1)
+        return fail(DVM_ERR_INVALID_ARG, "the full discrete gradient is first-order only; use DVM_SENS_PAPER");
     const DevMesh& m = st->mesh->d;
     const DevGrid& g = st->grid->d;
     const int nnodes = (m.nj + 1) * m.ni;

@@ -87,6 +87,28 @@ struct PrimalArgs {
     double* Jpart;
     double* respart;
     int* err;                               // set when a staged copy never completed
+    const TS* defect;                       // second order: dR(f_old), subtracted before the division by D
+};
+
+// Second-order reconstruction (Eq. gaussgrad): the gradient (or, for the adjoint, the transposed
+// reconstruction weights mu) and the defect live in buffers of the state's storage and layout.
+template <class TS, class TC>
+struct SOArgs {
+    int ncell, nq, ni;
+    const int4* nb;
+    const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* S;
+    const TC* V;
+    const typename std::conditional<sizeof(TC) == 8, double4, float4>::type* vt;
+    const typename std::conditional<sizeof(TC) == 8, double2, float2>::type* fd;
+    const TC* gw;
+    const double* wallD;
+    TC halfTw;
+    const double2* nodes;                   // [(nj+1)][ni]
+    const TS* in;                           // f (primal) or phi (adjoint)
+    const double* Fw;                       // wall density of f (primal)
+    TS* gx;                                 // d/dx (primal gradient) or the x part of mu (adjoint)
+    TS* gy;
+    TS* out;                                // dR (primal) or (dR/df)^T (w phi) / w (adjoint)
 };
 
 // Per-cell constants of the adjoint linearisation (see k_adjoint_cellconst).
@@ -120,6 +142,7 @@ struct AdjointArgs {
     double* Lam_new;
     double* respart;
     int* err;
+    const TS* defect;                       // second order: (dR/df)^T (w phi_old) / w, subtracted likewise
 };
 
 // Descriptors of the batched sweeps: the arguments and tensor maps of one request for both
@@ -200,6 +223,10 @@ cudaError_t launch_aa_collect(int storage, size_t n, const void* G, void* X, voi
 cudaError_t launch_aa_mix(int storage, size_t n, void* F, void* X, const void* Gp, const void* dG, int cnt,
                           const double* gamma, int positive, int* neg, cudaStream_t s);
 cudaError_t launch_aa_restore(int storage, size_t n, void* F, void* X, const void* Gp, cudaStream_t s);
+
+// Second order: adjoint = false -> gradient of args.in, then dR into args.out; adjoint = true -> mu of
+// args.in (phi), then the transposed defect into args.out.  args is SOArgs<TS, TC>.
+cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cudaStream_t s);
 
 // out[0] = Q, out[1 + p] = dQ/dalpha_p
 cudaError_t launch_volume(const DevMesh& m, double vmin, const double* dwall, int P, double* out, cudaStream_t s);

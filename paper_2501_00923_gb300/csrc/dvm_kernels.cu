@@ -403,7 +403,7 @@ template <class TS> constexpr int kAdjointMinBlocks = std::is_same<typename Pack
 // which keeps the loop free of per-velocity branches.
 // FP32 / BF16 form of the sweep: the same update two velocities at a time.  D uses the inflow
 // weights n_e = max(-a_e, 0): sum_e max(a_e, 0) = sum_e n_e on a closed cell.
-template <class TS, bool kRes, int kBnd>
+template <class TS, bool kRes, int kBnd, bool kDef>
 __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& P, int c, int w, int lane,
                                                    const Feed& F) {
     using PK = Pack<TS>;
@@ -453,6 +453,8 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                 PK::unpack(r1, e11, e12);
                 PK::unpack(r2, e21, e22);
                 PK::unpack(r3, e31, e32);
+                float dq1[KV], dq2[KV];
+                if (kDef) PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.defect) + oc + q), dq1, dq2);
                 float fn1[KV], fn2[KV];
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
@@ -485,6 +487,10 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                     r1 = pfma(n1, f11, r1);                  r2 = pfma(n1, f12, r2);
                     r1 = pfma(n2, pair_of<KV>(e21, pp), r1); r2 = pfma(n2, pair_of<KV>(e22, pp), r2);
                     r1 = pfma(n3, f31, r1);                  r2 = pfma(n3, f32, r2);
+                    if (kDef) {
+                        r1 = pfma(pair_of<KV>(dq1, pp), bc(-1.f), r1);
+                        r2 = pfma(pair_of<KV>(dq2, pp), bc(-1.f), r2);
+                    }
                     const float2 iD = prcp(D);
                     const float2 x1 = pmul(r1, iD), x2 = pmul(r2, iD);
                     fn1[2 * pp] = x1.x; fn1[2 * pp + 1] = x1.y;
@@ -535,7 +541,7 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     return true;
 }
 
-template <class TS, bool kRes, int kBnd>
+template <class TS, bool kRes, int kBnd, bool kDef>
 __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
                                             int lane, const Feed& F) {
     using PK = Pack<TS>;
@@ -582,6 +588,8 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
                 PK::unpack(r1, e11, e12);
                 PK::unpack(r2, e21, e22);
                 PK::unpack(r3, e31, e32);
+                TC dq1[KV], dq2[KV];
+                if (kDef) PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.defect) + oc + q), dq1, dq2);
                 TC fn1[KV], fn2[KV];
 #pragma unroll
                 for (int kk = 0; kk < KV; ++kk) {
@@ -601,6 +609,7 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
                     r1_ -= b1 * e11[kk]; r2_ -= b1 * e12[kk];
                     r1_ -= b2 * e21[kk]; r2_ -= b2 * e22[kk];
                     r1_ -= b3 * e31[kk]; r2_ -= b3 * e32[kk];
+                    if (kDef) { r1_ -= dq1[kk]; r2_ -= dq2[kk]; }
                     const TC iD = frcp<TC>(D);
                     fn1[kk] = r1_ * iD;
                     fn2[kk] = r2_ * iD;
@@ -698,7 +707,7 @@ __device__ __forceinline__ void block_pipe_drain(const BlockPipe& B) {
         for (unsigned ph = 0; ph < 2; ++ph) mbar_try_wait(&B.F.full[s], ph);
 }
 
-template <class TS, bool kRes>
+template <class TS, bool kRes, bool kDef>
 __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
                                              const CUtensorMap* m8, int i, int j0, unsigned char* smem) {
     BlockPipe B;
@@ -711,17 +720,17 @@ __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<
     bool ok;
     if constexpr (kPaired<TS>) {
         switch (bnd) {
-            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell>(P, c, w, lane, B.F); break;
-            default: ok = primal_cell_paired<TS, kRes, kWallFar>(P, c, w, lane, B.F); break;
+            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior, kDef>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell, kDef>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell, kDef>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell_paired<TS, kRes, kWallFar, kDef>(P, c, w, lane, B.F); break;
         }
     } else {
         switch (bnd) {
-            case kInterior: ok = primal_cell<TS, kRes, kInterior>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = primal_cell<TS, kRes, kWallCell>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = primal_cell<TS, kRes, kFarCell>(P, c, w, lane, B.F); break;
-            default: ok = primal_cell<TS, kRes, kWallFar>(P, c, w, lane, B.F); break;
+            case kInterior: ok = primal_cell<TS, kRes, kInterior, kDef>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell<TS, kRes, kWallCell, kDef>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell<TS, kRes, kFarCell, kDef>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell<TS, kRes, kWallFar, kDef>(P, c, w, lane, B.F); break;
         }
     }
     if (!ok && lane == 0) {
@@ -731,12 +740,12 @@ __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<
 }
 
 
-template <class TS, bool kRes>
+template <class TS, bool kRes, bool kDef>
 __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
                                                          const __grid_constant__ CUtensorMap m10,
                                                          const __grid_constant__ CUtensorMap m8) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    primal_block<TS, kRes>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+    primal_block<TS, kRes, kDef>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
 }
 
 // Make the tensor maps of a descriptor in global memory visible to the tensor-map proxy.
@@ -757,7 +766,7 @@ __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep_batc
         tensormap_acquire(&d->maps[parity].col);
         tensormap_acquire(&d->maps[parity].side);
     }
-    primal_block<TS, kRes>(d->args[parity], &d->maps[parity].col, &d->maps[parity].side, it.y, it.z, smem);
+    primal_block<TS, kRes, false>(d->args[parity], &d->maps[parity].col, &d->maps[parity].side, it.y, it.z, smem);
 }
 
 // ================================================================== adjoint sweep (K2)
@@ -773,7 +782,7 @@ __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep_batc
 // FP32 / BF16 form of the adjoint sweep, two velocities at a time.  D uses the outflow weights
 // max(a_e, 0) directly; the Maxwellian is accumulated as exp(-c^2/2T) = 2^(c^2 kE) and its factor
 // n0 applied to the block sums (every coupling is linear in g1).
-template <class TS, bool kUpdate, bool kRes, int kBnd>
+template <class TS, bool kUpdate, bool kRes, int kBnd, bool kDef>
 __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>& P, int c, int w, int lane,
                                                     const Feed& F) {
     using PK = Pack<TS>;
@@ -831,6 +840,8 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
                 PK::unpack(r1, e11, e12);
                 PK::unpack(r2, e21, e22);
                 PK::unpack(r3, e31, e32);
+                float dq1[KV], dq2[KV];
+                if (kDef) PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.defect) + oc + q), dq1, dq2);
                 float pn1[KV], pn2[KV];
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
@@ -855,6 +866,10 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
                         if (!far) { r1 = pfma(o1, pair_of<KV>(e11, pp), r1); r2 = pfma(o1, pair_of<KV>(e12, pp), r2); }
                         if (wall) r1 = pfma(o3, pfma(nhc, hv, pfma(ndy, vy, pfma(ndx, vx, nsrc))), r1);
                         else { r1 = pfma(o3, pair_of<KV>(e31, pp), r1); r2 = pfma(o3, pair_of<KV>(e32, pp), r2); }
+                        if (kDef) {
+                            r1 = pfma(pair_of<KV>(dq1, pp), bc(-1.f), r1);
+                            r2 = pfma(pair_of<KV>(dq2, pp), bc(-1.f), r2);
+                        }
                         const float2 iD = prcp(D);
                         const float2 y1 = pmul(r1, iD), y2 = pmul(r2, iD);
                         if (kRes) {
@@ -920,7 +935,7 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
     return true;
 }
 
-template <class TS, bool kUpdate, bool kRes, int kBnd>
+template <class TS, bool kUpdate, bool kRes, int kBnd, bool kDef>
 __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
                                              int lane, const Feed& F) {
     using PK = Pack<TS>;
@@ -972,6 +987,8 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
                 PK::unpack(r1, e11, e12);
                 PK::unpack(r2, e21, e22);
                 PK::unpack(r3, e31, e32);
+                TC dq1[KV], dq2[KV];
+                if (kDef) PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.defect) + oc + q), dq1, dq2);
                 TC pn1[KV], pn2[KV];
 #pragma unroll
                 for (int kk = 0; kk < KV; ++kk) {
@@ -991,6 +1008,7 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
                         if (!far) { const TC p1 = fmax(a1, TC(0)); r1_ += p1 * e11[kk]; r2_ += p1 * e12[kk]; }
                         if (wall) r1_ -= p3 * (P.dirx * vx + P.diry * vy + P.heat * hv + srcB);
                         else { r1_ += p3 * e31[kk]; r2_ += p3 * e32[kk]; }
+                        if (kDef) { r1_ -= dq1[kk]; r2_ -= dq2[kk]; }
                         const TC iD = frcp<TC>(D);
                         pn1[kk] = r1_ * iD;
                         pn2[kk] = r2_ * iD;
@@ -1049,7 +1067,7 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
     return true;
 }
 
-template <class TS, bool kUpdate, bool kRes>
+template <class TS, bool kUpdate, bool kRes, bool kDef>
 __device__ __forceinline__ void adjoint_block(const AdjointArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
                                               const CUtensorMap* m8, const CUtensorMap* mf8, int i, int j0,
                                               unsigned char* smem) {
@@ -1063,17 +1081,17 @@ __device__ __forceinline__ void adjoint_block(const AdjointArgs<TS, typename Pac
     bool ok;
     if constexpr (kPaired<TS>) {
         switch (bnd) {
-            case kInterior: ok = adjoint_cell_paired<TS, kUpdate, kRes, kInterior>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = adjoint_cell_paired<TS, kUpdate, kRes, kWallCell>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = adjoint_cell_paired<TS, kUpdate, kRes, kFarCell>(P, c, w, lane, B.F); break;
-            default: ok = adjoint_cell_paired<TS, kUpdate, kRes, kWallFar>(P, c, w, lane, B.F); break;
+            case kInterior: ok = adjoint_cell_paired<TS, kUpdate, kRes, kInterior, kDef>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = adjoint_cell_paired<TS, kUpdate, kRes, kWallCell, kDef>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = adjoint_cell_paired<TS, kUpdate, kRes, kFarCell, kDef>(P, c, w, lane, B.F); break;
+            default: ok = adjoint_cell_paired<TS, kUpdate, kRes, kWallFar, kDef>(P, c, w, lane, B.F); break;
         }
     } else {
         switch (bnd) {
-            case kInterior: ok = adjoint_cell<TS, kUpdate, kRes, kInterior>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = adjoint_cell<TS, kUpdate, kRes, kWallCell>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = adjoint_cell<TS, kUpdate, kRes, kFarCell>(P, c, w, lane, B.F); break;
-            default: ok = adjoint_cell<TS, kUpdate, kRes, kWallFar>(P, c, w, lane, B.F); break;
+            case kInterior: ok = adjoint_cell<TS, kUpdate, kRes, kInterior, kDef>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = adjoint_cell<TS, kUpdate, kRes, kWallCell, kDef>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = adjoint_cell<TS, kUpdate, kRes, kFarCell, kDef>(P, c, w, lane, B.F); break;
+            default: ok = adjoint_cell<TS, kUpdate, kRes, kWallFar, kDef>(P, c, w, lane, B.F); break;
         }
     }
     if (!ok && lane == 0) {
@@ -1082,13 +1100,13 @@ __device__ __forceinline__ void adjoint_block(const AdjointArgs<TS, typename Pac
     }
 }
 
-template <class TS, bool kUpdate, bool kRes>
+template <class TS, bool kUpdate, bool kRes, bool kDef>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep(const AdjointArgs<TS, typename Pack<TS>::TC> P,
                                                           const __grid_constant__ CUtensorMap m10,
                                                           const __grid_constant__ CUtensorMap m8,
                                                           const __grid_constant__ CUtensorMap mf8) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    adjoint_block<TS, kUpdate, kRes>(P, &m10, &m8, &mf8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+    adjoint_block<TS, kUpdate, kRes, kDef>(P, &m10, &m8, &mf8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
 }
 
 template <class TS, bool kRes>
@@ -1102,7 +1120,7 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep_ba
         tensormap_acquire(&d->phi_maps[parity].side);
         tensormap_acquire(&d->f_maps.side);
     }
-    adjoint_block<TS, true, kRes>(d->args[parity], &d->phi_maps[parity].col, &d->phi_maps[parity].side,
+    adjoint_block<TS, true, kRes, false>(d->args[parity], &d->phi_maps[parity].col, &d->phi_maps[parity].side,
                                   &d->f_maps.side, it.y, it.z, smem);
 }
 
@@ -1215,6 +1233,307 @@ __global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const
         const double u1 = m1 / m0, u2 = m2 / m0;
         prim[c] = make_double4(m0, u1, u2, (2.0 / 3.0) * (m3 / m0 - 0.5 * (u1 * u1 + u2 * u2)));
         if (wall) Fw[c] = fw / sqrt(s.x * s.x + s.y * s.y);
+    }
+}
+
+// ================================================================== second order (reconstruction)
+// Linear reconstruction of the upwind cell on interior faces, F_e = f_up + grad f_up . (x_e - x_up),
+// with the unlimited Gauss gradient of Eq. (gaussgrad), grad f_c = (1/V_c) sum_e fbar_e A_e n_e: fbar_e
+// is the face average (f_c + f_nb)/2 inside and the first-order face value on the far-field and wall
+// faces (own f on an outflow face; the free stream, or the diffuse-wall Maxwellian (F_rhow/D) g_M, on
+// an inflow face).  x_c is the mean of the four corners and x_e the midpoint of face e.  Boundary faces
+// keep their first-order values, so the added flux is
+//     dR_c = sum_{interior e} a_e grad f_up . (x_e - x_up),
+// taken by the sweep as a defect of the previous state (the first-order diagonal D stays).  dR is
+// affine in f; with lambda = w phi its transpose gathers, per cell u and interior face e with a_e > 0,
+//     mu_u = sum_e a_e (phi_u - phi_nb) (x_e - x_u)          (the weight of grad f_u in sum lambda.dR)
+// and then spreads s_{u,e} = A_e n_e . mu_u / V_u over the values fbar_{u,e} depends on: half to each
+// side of an interior face, all to u on an outflow boundary face, and through F_rhow to the outgoing
+// velocities of a wall cell.  Four kernels, each a warp per cell over 16-byte chunks.
+__device__ __forceinline__ void so_points(const double2* X, int ni, int c, double2& xc, double2 (&xe)[4]) {
+    const int i = c % ni, j = c / ni, ip = (i + 1) % ni;
+    const double2 P[4] = {X[j * ni + i], X[(j + 1) * ni + i], X[(j + 1) * ni + ip], X[j * ni + ip]};
+    xc = make_double2(0.25 * ((P[0].x + P[1].x) + (P[2].x + P[3].x)), 0.25 * ((P[0].y + P[1].y) + (P[2].y + P[3].y)));
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        xe[e] = make_double2(0.5 * (P[e].x + P[(e + 1) & 3].x), 0.5 * (P[e].y + P[(e + 1) & 3].y));
+}
+
+// Offsets x_e - x_c of the cell's faces and x_e - x_nb of its interior neighbours (0 on boundary faces).
+template <class TC2>
+__device__ __forceinline__ void so_offsets(const double2* X, int ni, int c, const int (&nb)[4], TC2 (&dc)[4],
+                                           TC2 (&dn)[4]) {
+    double2 xc, xe[4];
+    so_points(X, ni, c, xc, xe);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        dc[e].x = xe[e].x - xc.x;
+        dc[e].y = xe[e].y - xc.y;
+        dn[e].x = 0;
+        dn[e].y = 0;
+        if (nb[e] >= 0) {
+            double2 xm, xx[4];
+            so_points(X, ni, nb[e], xm, xx);
+            dn[e].x = xe[e].x - xm.x;
+            dn[e].y = xe[e].y - xm.y;
+        }
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_so_gradient(const SOArgs<TS, typename Pack<TS>::TC> A) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= A.ncell) return;
+    const int4 n4 = A.nb[c];
+    const int nb[4] = {n4.x, n4.y, n4.z, n4.w};
+    TC2 S[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) S[e] = A.S[4 * c + e];
+    const TC iV = TC(1) / A.V[c];
+    TC cw1 = TC(0), cw2 = TC(0);
+    if (nb[3] == kWall) {
+        cw1 = (TC)(A.Fw[c] / A.wallD[c]);
+        cw2 = cw1 * A.halfTw;
+    }
+    const size_t nq = (size_t)A.nq;
+    const uint4* f = reinterpret_cast<const uint4*>(A.in);
+    uint4* gx = reinterpret_cast<uint4*>(A.gx);
+    uint4* gy = reinterpret_cast<uint4*>(A.gy);
+    for (int q = lane; q < A.nq; q += 32) {
+        TC o1[KV], o2[KV], m1[4][KV], m2[4][KV];
+        PK::unpack(ldg16(f + c * nq + q), o1, o2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (nb[e] >= 0) PK::unpack(ldg16(f + (size_t)nb[e] * nq + q), m1[e], m2[e]);
+            else PK::unpack(make_uint4(0u, 0u, 0u, 0u), m1[e], m2[e]);
+        }
+        TC x1[KV], x2[KV], y1[KV], y2[KV];
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const int k = q * KV + kk;
+            const TC4 t = A.vt[k];
+            TC sx1 = TC(0), sy1 = TC(0), sx2 = TC(0), sy2 = TC(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                TC b1, b2;
+                if (nb[e] >= 0) {
+                    b1 = TC(0.5) * (o1[kk] + m1[e][kk]);
+                    b2 = TC(0.5) * (o2[kk] + m2[e][kk]);
+                } else if (S[e].x * t.x + S[e].y * t.y > TC(0)) {
+                    b1 = o1[kk];
+                    b2 = o2[kk];
+                } else if (nb[e] == kFar) {
+                    const TC2 g = A.fd[k];
+                    b1 = g.x;
+                    b2 = g.y;
+                } else {
+                    const TC g = A.gw[k];
+                    b1 = cw1 * g;
+                    b2 = cw2 * g;
+                }
+                sx1 += b1 * S[e].x; sy1 += b1 * S[e].y;
+                sx2 += b2 * S[e].x; sy2 += b2 * S[e].y;
+            }
+            x1[kk] = sx1 * iV; y1[kk] = sy1 * iV;
+            x2[kk] = sx2 * iV; y2[kk] = sy2 * iV;
+        }
+        gx[c * nq + q] = PK::pack(x1, x2);
+        gy[c * nq + q] = PK::pack(y1, y2);
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_so_defect(const SOArgs<TS, typename Pack<TS>::TC> A) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= A.ncell) return;
+    const int4 n4 = A.nb[c];
+    const int nb[4] = {n4.x, n4.y, n4.z, n4.w};
+    TC2 S[4], dc[4], dn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) S[e] = A.S[4 * c + e];
+    so_offsets(A.nodes, A.ni, c, nb, dc, dn);
+    const size_t nq = (size_t)A.nq;
+    const uint4* gx = reinterpret_cast<const uint4*>(A.gx);
+    const uint4* gy = reinterpret_cast<const uint4*>(A.gy);
+    uint4* out = reinterpret_cast<uint4*>(A.out);
+    for (int q = lane; q < A.nq; q += 32) {
+        TC ox1[KV], ox2[KV], oy1[KV], oy2[KV], nx1[4][KV], nx2[4][KV], ny1[4][KV], ny2[4][KV];
+        PK::unpack(ldg16(gx + c * nq + q), ox1, ox2);
+        PK::unpack(ldg16(gy + c * nq + q), oy1, oy2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const size_t m = nb[e] >= 0 ? (size_t)nb[e] : (size_t)c;
+            PK::unpack(ldg16(gx + m * nq + q), nx1[e], nx2[e]);
+            PK::unpack(ldg16(gy + m * nq + q), ny1[e], ny2[e]);
+        }
+        TC d1[KV], d2[KV];
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const TC4 t = A.vt[q * KV + kk];
+            TC r1 = TC(0), r2 = TC(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (nb[e] < 0) continue;
+                const TC a = S[e].x * t.x + S[e].y * t.y;
+                if (a > TC(0)) {
+                    r1 += a * (ox1[kk] * dc[e].x + oy1[kk] * dc[e].y);
+                    r2 += a * (ox2[kk] * dc[e].x + oy2[kk] * dc[e].y);
+                } else {
+                    r1 += a * (nx1[e][kk] * dn[e].x + ny1[e][kk] * dn[e].y);
+                    r2 += a * (nx2[e][kk] * dn[e].x + ny2[e][kk] * dn[e].y);
+                }
+            }
+            d1[kk] = r1;
+            d2[kk] = r2;
+        }
+        out[c * nq + q] = PK::pack(d1, d2);
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_so_adjoint_mu(const SOArgs<TS, typename Pack<TS>::TC> A) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= A.ncell) return;
+    const int4 n4 = A.nb[c];
+    const int nb[4] = {n4.x, n4.y, n4.z, n4.w};
+    TC2 S[4], dc[4], dn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) S[e] = A.S[4 * c + e];
+    so_offsets(A.nodes, A.ni, c, nb, dc, dn);
+    const size_t nq = (size_t)A.nq;
+    const uint4* phi = reinterpret_cast<const uint4*>(A.in);
+    uint4* gx = reinterpret_cast<uint4*>(A.gx);
+    uint4* gy = reinterpret_cast<uint4*>(A.gy);
+    for (int q = lane; q < A.nq; q += 32) {
+        TC o1[KV], o2[KV], m1[4][KV], m2[4][KV];
+        PK::unpack(ldg16(phi + c * nq + q), o1, o2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const size_t m = nb[e] >= 0 ? (size_t)nb[e] : (size_t)c;
+            PK::unpack(ldg16(phi + m * nq + q), m1[e], m2[e]);
+        }
+        TC x1[KV], x2[KV], y1[KV], y2[KV];
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const TC4 t = A.vt[q * KV + kk];
+            TC mx1 = TC(0), my1 = TC(0), mx2 = TC(0), my2 = TC(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (nb[e] < 0) continue;
+                const TC a = S[e].x * t.x + S[e].y * t.y;
+                if (a > TC(0)) {
+                    const TC d1 = a * (o1[kk] - m1[e][kk]), d2 = a * (o2[kk] - m2[e][kk]);
+                    mx1 += d1 * dc[e].x; my1 += d1 * dc[e].y;
+                    mx2 += d2 * dc[e].x; my2 += d2 * dc[e].y;
+                }
+            }
+            x1[kk] = mx1; y1[kk] = my1;
+            x2[kk] = mx2; y2[kk] = my2;
+        }
+        gx[c * nq + q] = PK::pack(x1, x2);
+        gy[c * nq + q] = PK::pack(y1, y2);
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_so_adjoint_defect(const SOArgs<TS, typename Pack<TS>::TC> A) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= A.ncell) return;
+    const int4 n4 = A.nb[c];
+    const int nb[4] = {n4.x, n4.y, n4.z, n4.w};
+    TC2 S[4];
+    TC iVn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        S[e] = A.S[4 * c + e];
+        iVn[e] = nb[e] >= 0 ? TC(1) / A.V[nb[e]] : TC(0);
+    }
+    const TC iV = TC(1) / A.V[c];
+    const size_t nq = (size_t)A.nq;
+    const uint4* gx = reinterpret_cast<const uint4*>(A.gx);
+    const uint4* gy = reinterpret_cast<const uint4*>(A.gy);
+    uint4* out = reinterpret_cast<uint4*>(A.out);
+    // wall: the inflow values (F_rhow / D) g_M depend on f1 of the outgoing velocities through F_rhow
+    TC wcoef = TC(0);
+    if (nb[3] == kWall) {
+        double lam = 0.0;
+        for (int q = lane; q < A.nq; q += 32) {
+            TC ox1[KV], ox2[KV], oy1[KV], oy2[KV];
+            PK::unpack(ldg16(gx + c * nq + q), ox1, ox2);
+            PK::unpack(ldg16(gy + c * nq + q), oy1, oy2);
+#pragma unroll
+            for (int kk = 0; kk < KV; ++kk) {
+                const int k = q * KV + kk;
+                const TC4 t = A.vt[k];
+                if (S[3].x * t.x + S[3].y * t.y <= TC(0)) {
+                    const TC s1 = (S[3].x * ox1[kk] + S[3].y * oy1[kk]) * iV;
+                    const TC s2 = (S[3].x * ox2[kk] + S[3].y * oy2[kk]) * iV;
+                    lam += (double)(t.z * A.gw[k] * (s1 + A.halfTw * s2));
+                }
+            }
+        }
+        lam = warp_sum(lam);
+        const double area = sqrt((double)S[3].x * (double)S[3].x + (double)S[3].y * (double)S[3].y);
+        wcoef = (TC)(lam / (A.wallD[c] * area));
+    }
+    for (int q = lane; q < A.nq; q += 32) {
+        TC ox1[KV], ox2[KV], oy1[KV], oy2[KV], nx1[4][KV], nx2[4][KV], ny1[4][KV], ny2[4][KV];
+        PK::unpack(ldg16(gx + c * nq + q), ox1, ox2);
+        PK::unpack(ldg16(gy + c * nq + q), oy1, oy2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const size_t m = nb[e] >= 0 ? (size_t)nb[e] : (size_t)c;
+            PK::unpack(ldg16(gx + m * nq + q), nx1[e], nx2[e]);
+            PK::unpack(ldg16(gy + m * nq + q), ny1[e], ny2[e]);
+        }
+        TC d1[KV], d2[KV];
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const TC4 t = A.vt[q * KV + kk];
+            TC r1 = TC(0), r2 = TC(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const TC s1 = (S[e].x * ox1[kk] + S[e].y * oy1[kk]) * iV;
+                const TC s2 = (S[e].x * ox2[kk] + S[e].y * oy2[kk]) * iV;
+                if (nb[e] >= 0) {
+                    // own share of the face average, and the neighbour's (its face vector is -S_e)
+                    const TC u1 = (S[e].x * nx1[e][kk] + S[e].y * ny1[e][kk]) * iVn[e];
+                    const TC u2 = (S[e].x * nx2[e][kk] + S[e].y * ny2[e][kk]) * iVn[e];
+                    r1 += TC(0.5) * (s1 - u1);
+                    r2 += TC(0.5) * (s2 - u2);
+                } else if (S[e].x * t.x + S[e].y * t.y > TC(0)) {
+                    r1 += s1;
+                    r2 += s2;
+                }
+            }
+            if (nb[3] == kWall) {
+                const TC a3 = S[3].x * t.x + S[3].y * t.y;
+                if (a3 > TC(0)) r1 += a3 * wcoef;
+            }
+            d1[kk] = r1;
+            d2[kk] = r2;
+        }
+        out[c * nq + q] = PK::pack(d1, d2);
     }
 }
 
@@ -1789,6 +2108,26 @@ cudaError_t launch_fill_freestream(int storage, void* f, int ncell, const DevGri
     return cudaGetLastError();
 }
 
+template <class TS, class TC>
+void second_order_launch(const void* args, bool adjoint, cudaStream_t s) {
+    const auto& a = *static_cast<const SOArgs<TS, TC>*>(args);
+    const int nb = cdiv(a.ncell, kWarpsPerBlock);
+    if (adjoint) {
+        k_so_adjoint_mu<TS><<<nb, 256, 0, s>>>(a);
+        k_so_adjoint_defect<TS><<<nb, 256, 0, s>>>(a);
+    } else {
+        k_so_gradient<TS><<<nb, 256, 0, s>>>(a);
+        k_so_defect<TS><<<nb, 256, 0, s>>>(a);
+    }
+}
+
+cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cudaStream_t s) {
+    if (storage == 0) second_order_launch<double, double>(args, adjoint, s);
+    else if (storage == 1) second_order_launch<float, float>(args, adjoint, s);
+    else second_order_launch<__nv_bfloat16, float>(args, adjoint, s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
                            double* Fw, cudaStream_t s) {
     const int nb = cdiv(m.ncell, kWarpsPerBlock);
@@ -1807,12 +2146,19 @@ void primal_launch(const void* args, const TmaMaps& maps, bool res, cudaStream_t
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr[dev]) {
-        cudaFuncSetAttribute(k_primal_sweep<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_primal_sweep<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_sweep<TS, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_sweep<TS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_sweep<TS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_sweep<TS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         attr[dev] = true;
     }
-    if (res) k_primal_sweep<TS, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
-    else k_primal_sweep<TS, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    if (a.defect) {
+        if (res) k_primal_sweep<TS, true, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+        else k_primal_sweep<TS, false, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    } else {
+        if (res) k_primal_sweep<TS, true, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+        else k_primal_sweep<TS, false, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    }
 }
 
 cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
@@ -1832,14 +2178,20 @@ void adjoint_launch(const void* args, const TmaMaps& phi_maps, const TmaMaps& f_
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr[dev]) {
-        cudaFuncSetAttribute(k_adjoint_sweep<TS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_adjoint_sweep<TS, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         attr[dev] = true;
     }
-    if (!update) k_adjoint_sweep<TS, false, false><<<grid, 256, sm, s>>>(a, phi_maps.col, phi_maps.side, f_maps.side);
-    else if (res) k_adjoint_sweep<TS, true, true><<<grid, 256, sm, s>>>(a, phi_maps.col, phi_maps.side, f_maps.side);
-    else k_adjoint_sweep<TS, true, false><<<grid, 256, sm, s>>>(a, phi_maps.col, phi_maps.side, f_maps.side);
+    const CUtensorMap &pc = phi_maps.col, &ps = phi_maps.side, &fs = f_maps.side;
+    if (!update) k_adjoint_sweep<TS, false, false, false><<<grid, 256, sm, s>>>(a, pc, ps, fs);
+    else if (a.defect) {
+        if (res) k_adjoint_sweep<TS, true, true, true><<<grid, 256, sm, s>>>(a, pc, ps, fs);
+        else k_adjoint_sweep<TS, true, false, true><<<grid, 256, sm, s>>>(a, pc, ps, fs);
+    } else if (res) k_adjoint_sweep<TS, true, true, false><<<grid, 256, sm, s>>>(a, pc, ps, fs);
+    else k_adjoint_sweep<TS, true, false, false><<<grid, 256, sm, s>>>(a, pc, ps, fs);
 }
 
 cudaError_t launch_adjoint_sweep(int storage, const void* args, const TmaMaps& phi_maps, const TmaMaps& f_maps,

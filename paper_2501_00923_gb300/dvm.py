@@ -92,6 +92,8 @@ def lib():
             "dvm_state_set": (i, [_vp, _dp]),
             "dvm_state_get": (i, [_vp, _dp]),
             "dvm_state_moments": (i, [_vp, _dp]),
+            "dvm_state_set_order": (i, [_vp, i, i]),
+            "dvm_state_get_order": (i, [_vp, C.POINTER(i)]),
             "dvm_primal_iterate": (i, [_vp, i, _dp]),
             "dvm_state_functional": (i, [_vp, i, _dp]),
             "dvm_primal_solve": (i, [_vp, _vp, _vp, C.POINTER(Flow), C.POINTER(SolveOpts), i, pp,
@@ -270,6 +272,22 @@ class State:
         r = np.empty(max(n, 1))
         _check(lib().dvm_primal_iterate(self.h, n, _p(r)))
         return r[:n]
+
+    @property
+    def order(self) -> int:
+        """Spatial order of the face values (1 upwind, 2 linear reconstruction)."""
+        o = C.c_int()
+        _check(lib().dvm_state_get_order(self.h, C.byref(o)))
+        return o.value
+
+    @order.setter
+    def order(self, order: int):
+        self.set_order(order)
+
+    def set_order(self, order: int, defect_period: int = 0):
+        """order 2: linear reconstruction with the defect frozen over groups of defect_period sweeps
+        (0 -> 4); order 1: first-order upwind."""
+        _check(lib().dvm_state_set_order(self.h, int(order), int(defect_period)))
 
     def functional(self, which="drag"):
         J = C.c_double()

@@ -101,3 +101,15 @@ def test_second_order_adjoint_is_exact_through_a_source():
     Jm = pr.functional(so.solve(f0=f, source=-eps * s, tol=1e-15, max_sweeps=8000)[0])
     fd = (Jp - Jm) / (2 * eps)
     assert abs(fd - pred) < 1e-7 * abs(pred)
+
+
+def test_frozen_defect_groups_reach_the_same_fixed_point():
+    """Sweeps with dR recomputed every sweep (where that converges) and with dR frozen over groups of
+    4 sweeps end at the same second-order steady state, R1 + dR = 0."""
+    mesh, g, pr, so = _so(8, 4, 6)
+    f1, it1 = so.solve(tol=1e-14, max_sweeps=8000, period=1)
+    f4, it4 = so.solve(tol=1e-14, max_sweeps=8000, period=4)
+    assert it1 < 8000 and it4 < 8000
+    assert np.abs(f1 - f4).max() < 1e-11 * np.abs(f1).max()
+    R = so.residual(f4)
+    assert np.abs(R).max() < 1e-10 * np.abs(so.a).max() * np.abs(f4).max()
