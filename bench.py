@@ -53,7 +53,7 @@ def parse():
                         "4: 256x128 GL48, 24 bumps (design-loop size)")
     p.add_argument("--order", type=int, default=1, choices=[1, 2],
                    help="spatial order of the face values (2: linear reconstruction, defect correction)")
-    p.add_argument("--defect-period", type=int, default=4, help="sweeps per second-order defect")
+    p.add_argument("--defect-period", type=int, default=20, help="sweeps per second-order defect")
     p.add_argument("--serve", type=int, default=128, help="requests of the served trace to replay (0: skip)")
     p.add_argument("--serve-max-iter", type=int, default=400, help="sweep cap per phase of a served request")
     return p.parse_args()

@@ -154,7 +154,7 @@ class SecondOrder:
             R = R + source
         return f - R / D[..., None]
 
-    def solve(self, f0=None, source=None, tol=1e-13, max_sweeps=20000, period=4):
+    def solve(self, f0=None, source=None, tol=1e-13, max_sweeps=20000, period=20):
         """Second-order steady state by point-implicit sweeps with the defect frozen over groups of
         `period` sweeps (small problems).  Stops when a sweep moves f by less than tol max|f|."""
         f = self.pr.freestream() if f0 is None else np.array(f0, dtype=np.float64)
@@ -173,7 +173,7 @@ class SecondOrder:
         w = self.pr.w[None, :, None]
         return (L.T @ (w * phi).ravel()).reshape(phi.shape) / w
 
-    def adjoint_solve(self, f, tol=1e-13, max_sweeps=20000, period=4):
+    def adjoint_solve(self, f, tol=1e-13, max_sweeps=20000, period=20):
         L, _ = self.matrix()
         phi = np.zeros(self.pr.fshape())
         for it in range(max_sweeps):

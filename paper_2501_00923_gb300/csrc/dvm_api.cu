@@ -85,7 +85,7 @@ struct dvm_state {
     int order = 1;              // spatial order of the face values (2: linear reconstruction)
     int graph_order = 1;        // order the captured graph was built for
     void* so[3] = {nullptr, nullptr, nullptr};   // second order: gradient x, y and the frozen defect
-    int so_period = 4;          // sweeps per defect (defect correction groups)
+    int so_period = 20;         // sweeps per defect (defect correction groups)
     int so_phase = 0;           // sweeps since the defect was taken (0: take it at the next sweep)
     int graph_phase = 0;        // so_phase at the start of the captured graph
     int graph_so = 0;           // reconstruction launches inside the captured graph
@@ -1053,7 +1053,7 @@ int dvm_state_set_order(dvm_state* st, int order, int defect_period) {
         ctx->bytes += acc;
     }
     st->order = order;
-    st->so_period = defect_period > 0 ? defect_period : 4;
+    st->so_period = defect_period > 0 ? defect_period : 20;
     st->so_phase = 0;
     return DVM_OK;
 }

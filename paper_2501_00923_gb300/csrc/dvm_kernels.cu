@@ -22,6 +22,10 @@
 #ifndef DVM_STAGES
 #define DVM_STAGES 2
 #endif
+// Resident 256-thread blocks per SM asked of the second-order reconstruction kernels.
+#ifndef DVM_SO_BLOCKS
+#define DVM_SO_BLOCKS 1
+#endif
 
 namespace dvm {
 namespace {
@@ -1281,7 +1285,7 @@ __device__ __forceinline__ void so_offsets(const double2* X, int ni, int c, cons
 }
 
 template <class TS>
-__global__ void __launch_bounds__(256) k_so_gradient(const SOArgs<TS, typename Pack<TS>::TC> A) {
+__global__ void __launch_bounds__(256, DVM_SO_BLOCKS) k_so_gradient(const SOArgs<TS, typename Pack<TS>::TC> A) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -1348,7 +1352,7 @@ __global__ void __launch_bounds__(256) k_so_gradient(const SOArgs<TS, typename P
 }
 
 template <class TS>
-__global__ void __launch_bounds__(256) k_so_defect(const SOArgs<TS, typename Pack<TS>::TC> A) {
+__global__ void __launch_bounds__(256, DVM_SO_BLOCKS) k_so_defect(const SOArgs<TS, typename Pack<TS>::TC> A) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -1367,24 +1371,37 @@ __global__ void __launch_bounds__(256) k_so_defect(const SOArgs<TS, typename Pac
     const uint4* gy = reinterpret_cast<const uint4*>(A.gy);
     uint4* out = reinterpret_cast<uint4*>(A.out);
     for (int q = lane; q < A.nq; q += 32) {
-        TC ox1[KV], ox2[KV], oy1[KV], oy2[KV], nx1[4][KV], nx2[4][KV], ny1[4][KV], ny2[4][KV];
+        TC ox1[KV], ox2[KV], oy1[KV], oy2[KV], nx1[4][KV], nx2[4][KV], ny1[4][KV], ny2[4][KV], av[4][KV];
         PK::unpack(ldg16(gx + c * nq + q), ox1, ox2);
         PK::unpack(ldg16(gy + c * nq + q), oy1, oy2);
 #pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const TC4 t = A.vt[q * KV + kk];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) av[e][kk] = S[e].x * t.x + S[e].y * t.y;
+        }
+        // a neighbour's gradient enters only through its inflow faces (a <= 0): load it where needed
+#pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const size_t m = nb[e] >= 0 ? (size_t)nb[e] : (size_t)c;
-            PK::unpack(ldg16(gx + m * nq + q), nx1[e], nx2[e]);
-            PK::unpack(ldg16(gy + m * nq + q), ny1[e], ny2[e]);
+            bool need = false;
+#pragma unroll
+            for (int kk = 0; kk < KV; ++kk) need |= av[e][kk] <= TC(0);
+            uint4 qx = make_uint4(0u, 0u, 0u, 0u), qy = qx;
+            if (need && nb[e] >= 0) {
+                qx = ldg16(gx + (size_t)nb[e] * nq + q);
+                qy = ldg16(gy + (size_t)nb[e] * nq + q);
+            }
+            PK::unpack(qx, nx1[e], nx2[e]);
+            PK::unpack(qy, ny1[e], ny2[e]);
         }
         TC d1[KV], d2[KV];
 #pragma unroll
         for (int kk = 0; kk < KV; ++kk) {
-            const TC4 t = A.vt[q * KV + kk];
             TC r1 = TC(0), r2 = TC(0);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (nb[e] < 0) continue;
-                const TC a = S[e].x * t.x + S[e].y * t.y;
+                const TC a = av[e][kk];
                 if (a > TC(0)) {
                     r1 += a * (ox1[kk] * dc[e].x + oy1[kk] * dc[e].y);
                     r2 += a * (ox2[kk] * dc[e].x + oy2[kk] * dc[e].y);
@@ -1401,7 +1418,7 @@ __global__ void __launch_bounds__(256) k_so_defect(const SOArgs<TS, typename Pac
 }
 
 template <class TS>
-__global__ void __launch_bounds__(256) k_so_adjoint_mu(const SOArgs<TS, typename Pack<TS>::TC> A) {
+__global__ void __launch_bounds__(256, DVM_SO_BLOCKS) k_so_adjoint_mu(const SOArgs<TS, typename Pack<TS>::TC> A) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -1420,22 +1437,32 @@ __global__ void __launch_bounds__(256) k_so_adjoint_mu(const SOArgs<TS, typename
     uint4* gx = reinterpret_cast<uint4*>(A.gx);
     uint4* gy = reinterpret_cast<uint4*>(A.gy);
     for (int q = lane; q < A.nq; q += 32) {
-        TC o1[KV], o2[KV], m1[4][KV], m2[4][KV];
+        TC o1[KV], o2[KV], m1[4][KV], m2[4][KV], av[4][KV];
         PK::unpack(ldg16(phi + c * nq + q), o1, o2);
 #pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const TC4 t = A.vt[q * KV + kk];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) av[e][kk] = S[e].x * t.x + S[e].y * t.y;
+        }
+        // only the outflow faces (a > 0) of u carry its reconstruction: load those neighbours
+#pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const size_t m = nb[e] >= 0 ? (size_t)nb[e] : (size_t)c;
-            PK::unpack(ldg16(phi + m * nq + q), m1[e], m2[e]);
+            bool need = false;
+#pragma unroll
+            for (int kk = 0; kk < KV; ++kk) need |= av[e][kk] > TC(0);
+            uint4 qm = make_uint4(0u, 0u, 0u, 0u);
+            if (need && nb[e] >= 0) qm = ldg16(phi + (size_t)nb[e] * nq + q);
+            PK::unpack(qm, m1[e], m2[e]);
         }
         TC x1[KV], x2[KV], y1[KV], y2[KV];
 #pragma unroll
         for (int kk = 0; kk < KV; ++kk) {
-            const TC4 t = A.vt[q * KV + kk];
             TC mx1 = TC(0), my1 = TC(0), mx2 = TC(0), my2 = TC(0);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (nb[e] < 0) continue;
-                const TC a = S[e].x * t.x + S[e].y * t.y;
+                const TC a = av[e][kk];
                 if (a > TC(0)) {
                     const TC d1 = a * (o1[kk] - m1[e][kk]), d2 = a * (o2[kk] - m2[e][kk]);
                     mx1 += d1 * dc[e].x; my1 += d1 * dc[e].y;
@@ -1451,7 +1478,7 @@ __global__ void __launch_bounds__(256) k_so_adjoint_mu(const SOArgs<TS, typename
 }
 
 template <class TS>
-__global__ void __launch_bounds__(256) k_so_adjoint_defect(const SOArgs<TS, typename Pack<TS>::TC> A) {
+__global__ void __launch_bounds__(256, DVM_SO_BLOCKS) k_so_adjoint_defect(const SOArgs<TS, typename Pack<TS>::TC> A) {
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;

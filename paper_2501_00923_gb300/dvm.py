@@ -286,7 +286,7 @@ class State:
 
     def set_order(self, order: int, defect_period: int = 0):
         """order 2: linear reconstruction with the defect frozen over groups of defect_period sweeps
-        (0 -> 4); order 1: first-order upwind."""
+        (0 -> 20); order 1: first-order upwind."""
         _check(lib().dvm_state_set_order(self.h, int(order), int(defect_period)))
 
     def functional(self, which="drag"):
