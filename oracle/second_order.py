@@ -59,53 +59,84 @@ class SecondOrder:
                             j * ni + (i + 1) % ni,
                             np.where(j > 0, (j - 1) * ni + i, -2)], 1)
         vx, vy = pr.vx, pr.vy
-        self.a = S[:, :, 0, None] * vx[None, None, :] + S[:, :, 1, None] * vy[None, None, :]   # [nc, 4, nv]
-        self.f_far = pr.freestream()[0]                              # [nv, 2]
+        self._a = None
+        self.f_far = pr.freestream()[0].copy()                       # [nv, 2]
         Tw = pr.Tw
         g1 = np.exp(-(vx ** 2 + vy ** 2) / (2 * Tw)) / (2 * np.pi * Tw)
         self.gbar = np.stack([g1, 0.5 * Tw * g1], 1)                 # [nv, 2], unnormalised
-        A = np.linalg.norm(S[:, 3, :], axis=1)
-        self.vn_wall = self.a[:, 3, :] / A[:, None]                  # v . n on the wall face
+        self.area_wall = np.linalg.norm(S[:, 3, :], axis=1)
+
+    def face_weights(self, cells=None):
+        """a_e = A_e n_e . v_k of the listed cells' faces, [n, 4, nv]."""
+        c = slice(None) if cells is None else np.asarray(cells)
+        S = self.S[c]
+        return S[:, :, 0, None] * self.pr.vx[None, None, :] + S[:, :, 1, None] * self.pr.vy[None, None, :]
+
+    @property
+    def a(self):
+        if self._a is None:
+            self._a = self.face_weights()
+        return self._a
 
     # ------------------------------------------------------------------ face values and gradients
-    def _boundary_values(self, f):
-        """First-order values on the far-field (face 1) and wall (face 3) faces, [nc, nv, 2] each."""
+    def _cells(self, cells):
+        return np.arange(self.pr.ncell) if cells is None else np.asarray(cells)
+
+    def _boundary_values(self, f, cells=None):
+        """First-order values on the far-field (face 1) and wall (face 3) faces of the listed cells
+        (all by default), [n, nv, 2] each."""
+        c = self._cells(cells)
         w = self.pr.w
-        far = np.where((self.a[:, 1, :] > 0)[..., None], f, self.f_far[None])
-        vn = self.vn_wall
-        D = -np.sum(np.where(vn <= 0, w[None] * vn * self.gbar[None, :, 0], 0.0), 1)            # [nc]
-        Fw = np.sum(np.where(vn > 0, w[None] * vn * f[:, :, 0], 0.0), 1)
+        fc = f[c]
+        a = self.face_weights(c)
+        far = np.where((a[:, 1, :] > 0)[..., None], fc, self.f_far[None])
+        vn = a[:, 3, :] / self.area_wall[c, None]                      # v . n on the wall face
+        D = -np.sum(np.where(vn <= 0, w[None] * vn * self.gbar[None, :, 0], 0.0), 1)
+        Fw = np.sum(np.where(vn > 0, w[None] * vn * fc[:, :, 0], 0.0), 1)
         gw = (Fw / D)[:, None, None] * self.gbar[None]
-        wall = np.where((self.a[:, 3, :] > 0)[..., None], f, gw)
+        wall = np.where((a[:, 3, :] > 0)[..., None], fc, gw)
         return far, wall
 
-    def gradients(self, f):
-        """Gauss gradient of Eq. (gaussgrad) per cell, velocity and component: [nc, nv, 2 comp, 2 xy]."""
-        far, wall = self._boundary_values(f)
-        gsum = np.zeros(f.shape + (2,))
+    def gradients(self, f, cells=None):
+        """Gauss gradient of Eq. (gaussgrad) per cell, velocity and component of the listed cells (all
+        by default): [n, nv, 2 comp, 2 xy]."""
+        c = self._cells(cells)
+        far, wall = self._boundary_values(f, c)
+        fc = f[c]
+        gsum = np.zeros(fc.shape + (2,))
         for e in range(4):
-            n = self.nb[:, e]
+            n = self.nb[c, e]
             inside = n >= 0
-            fbar = np.where(inside[:, None, None], 0.5 * (f + f[np.where(inside, n, 0)]), 0.0)
+            fbar = np.where(inside[:, None, None], 0.5 * (fc + f[np.where(inside, n, 0)]), 0.0)
             if e == 1:
                 fbar = np.where(inside[:, None, None], fbar, far)
             if e == 3:
                 fbar = np.where(inside[:, None, None], fbar, wall)
-            gsum += fbar[..., None] * self.S[:, e, None, None, :]
-        return gsum / self.V[:, None, None, None]
+            gsum += fbar[..., None] * self.S[c, e, None, None, :]
+        return gsum / self.V[c, None, None, None]
 
-    def delta_r(self, f):
-        """dR = R2 - R1, [nc, nv, 2]."""
+    def delta_r(self, f, cells=None):
+        """dR = R2 - R1 of the listed cells (all by default), [n, nv, 2]."""
         f = np.asarray(f, dtype=np.float64)
-        G = self.gradients(f)
-        out = np.zeros_like(f)
+        c = self._cells(cells)
+        if cells is None:
+            U = c
+        else:
+            nbs = self.nb[c].ravel()
+            U = np.unique(np.concatenate([c, nbs[nbs >= 0]]))
+        G = self.gradients(f, U)
+        pos = np.full(self.pr.ncell, -1)
+        pos[U] = np.arange(U.size)
+        Gc = G[pos[c]]
+        a_all = self.face_weights(c)
+        out = np.zeros((c.size,) + f.shape[1:])
         for e in range(4):
-            n = self.nb[:, e]
+            n = self.nb[c, e]
             inside = n >= 0
-            ns = np.where(inside, n, 0)
-            a = self.a[:, e, :]                                       # [nc, nv]
-            own = np.einsum("cvkx,cx->cvk", G, self.xe[:, e] - self.xc)
-            nbr = np.einsum("cvkx,cx->cvk", G[ns], self.xe[:, e] - self.xc[ns])
+            ns = np.where(inside, n, c)
+            a = a_all[:, e, :]                                        # [n, nv]
+            own = np.einsum("cvkx,cx->cvk", Gc, self.xe[c, e] - self.xc[c])
+            nbr = np.einsum("cvkx,cx->cvk", G[pos[ns]], self.xe[c, e] - self.xc[ns])
             corr = np.where((a > 0)[..., None], own, nbr)
             out += np.where(inside[:, None, None], a[..., None] * corr, 0.0)
         return out
@@ -172,6 +203,31 @@ class SecondOrder:
         """Transposed defect (dR/df)^T (w phi) / w, [nc, nv, 2]."""
         w = self.pr.w[None, :, None]
         return (L.T @ (w * phi).ravel()).reshape(phi.shape) / w
+
+    def adjoint_defect_cells(self, phi, cells):
+        """(dR/df)^T (w phi) / w at the listed cells, each at least three rows from the wall (large
+        problems).  There dR does not reach the wall value, so it is diagonal in velocity and
+        component, and one probe per component gives a whole column block: with h the unit state on
+        component kappa of cell m, E_{m,k,kappa} = sum_c phi_{c,k,kappa} (dR(h) - dR(0))_{c,k,kappa}
+        over the cells c whose dR sees f_m (m, its neighbours and theirs)."""
+        cells = np.asarray(cells)
+        ni = self.ni
+        if np.any(cells // ni < 3):
+            raise ValueError("adjoint_defect_cells: cells must be three or more rows from the wall")
+        h = np.zeros(self.pr.fshape())
+        out = np.zeros((cells.size, self.nv, 2))
+        for i, m in enumerate(cells):
+            ring = {int(m)}
+            for _ in range(2):
+                ring |= {int(n) for r in ring for n in self.nb[r] if n >= 0}
+            R = np.array(sorted(ring))
+            b = self.delta_r(h, R)
+            for kap in range(2):
+                h[m, :, kap] = 1.0
+                col = self.delta_r(h, R) - b
+                h[m, :, kap] = 0.0
+                out[i, :, kap] = np.sum(phi[R, :, kap] * col[:, :, kap], axis=0)
+        return out
 
     def adjoint_solve(self, f, tol=1e-13, max_sweeps=20000, period=20):
         L, _ = self.matrix()

@@ -221,3 +221,46 @@ def test_order_arguments(ctx):
     fn1, _ = pr.jacobi(f_in)
     st.iterate(1)
     assert np.abs(st.get() - fn1).max() < 3e-6 * np.abs(fn1).max()
+
+
+@pytest.mark.parametrize("index,storage,ptol,atol", [(1, "fp32", 3e-6, 6e-6), (2, "fp32", 3e-6, 6e-6)],
+                         ids=["256x128-gl48-fp32", "384x192-v64-Kn0.001-Ma2-fp32"])
+def test_full_size_second_order_sweeps_sampled_cells(ctx, index, storage, ptol, atol):
+    """The full-size workloads in the benchmark's launch configuration at order 2: one primal sweep
+    from a seeded random state on sampled cells (wall row, far-field row, the periodic seam,
+    interior) against the oracle's first-order update less dR / D; one adjoint sweep on sampled
+    cells three or more rows from the wall against the oracle's first-order adjoint update less the
+    probed transposed defect over D."""
+    wl = W.config(index)
+    rng = np.random.default_rng(22)
+    m = dvm.Mesh(ctx, wl.mesh.nodes)
+    g = dvm.VGrid(ctx, wl.grid.vx, wl.grid.vy, wl.grid.w)
+    st = dvm.State(ctx, m, g, wl.flow.Kn, wl.flow.Ma, storage=storage)
+    st.order = 2
+    pr = O.Problem.from_workload(wl)
+    so = SecondOrder(pr)
+    f = W.random_state(pr.ncell, wl.grid, rng)
+    st.set(f)
+    f_in = st.get()
+    ni, nj = wl.mesh.ni, wl.mesh.nj
+    cells = np.unique(np.concatenate([[0, ni - 1, ni, (nj - 1) * ni, nj * ni - 1, (nj // 2) * ni + ni // 2],
+                                      rng.integers(0, ni, 4), rng.integers(0, ni * nj, 8)]))
+    D = pr.diagonal(f_in)
+    ref = pr.jacobi_cells(f_in, cells) - so.delta_r(f_in, cells) / D[cells][..., None]
+    acells = np.unique(np.concatenate([[3 * ni, 3 * ni + ni - 1, (nj - 1) * ni + 7],
+                                       rng.integers(3 * ni, ni * nj, 6)]))
+    ad = dvm.Adjoint(st)
+    phi = W.random_adjoint(pr.ncell, wl.grid.nv, rng)
+    ad.set(phi)
+    phi_in = ad.get()
+    aref = pr.adjoint_jacobi_cells(f_in, phi_in, acells) - so.adjoint_defect_cells(phi_in, acells) / D[acells][..., None]
+    ad.iterate(1)                    # the adjoint is linearised at f_in: sweep it before f moves
+    aout = ad.get()[acells]
+    ascale = np.abs(aref).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(aout - aref) / ascale).max() < atol
+    st.iterate(1)
+    out = st.get()[cells]
+    scale = np.abs(ref).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(out - ref) / scale).max() < ptol
+    for h in (ad, st, g, m):
+        h.close()

@@ -113,3 +113,17 @@ def test_frozen_defect_groups_reach_the_same_fixed_point():
     assert np.abs(f1 - f4).max() < 1e-11 * np.abs(f1).max()
     R = so.residual(f4)
     assert np.abs(R).max() < 1e-10 * np.abs(so.a).max() * np.abs(f4).max()
+
+
+def test_probed_transpose_at_interior_cells_equals_the_assembled_one():
+    """The large-problem form of the transposed defect (one probe per component of each listed cell,
+    valid three or more rows from the wall) against the transpose assembled column by column."""
+    mesh, g, pr, so = _so(10, 9, 4, Kn=0.3, Ma=0.9)
+    rng = np.random.default_rng(4)
+    phi = W.random_adjoint(pr.ncell, g.nv, rng)
+    L, _ = so.matrix()
+    E = so.adjoint_defect(phi, L)
+    cells = np.array([30, 35, 44, 51, 59, 79])
+    assert np.abs(so.adjoint_defect_cells(phi, cells) - E[cells]).max() < 1e-13 * np.abs(E).max()
+    with pytest.raises(ValueError):
+        so.adjoint_defect_cells(phi, np.array([5]))
