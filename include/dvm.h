@@ -47,6 +47,8 @@ typedef enum {
 } dvm_status;
 
 typedef enum { DVM_STORE_FP64 = 0, DVM_STORE_FP32 = 1, DVM_STORE_BF16 = 2 } dvm_storage;
+/* cell Maxwellian of the collision term (dvm_state_set_maxwellian) */
+typedef enum { DVM_MAXWELL_PLAIN = 0, DVM_MAXWELL_CONSERVATIVE = 1 } dvm_maxwellian;
 
 /* Objective of Eq. (formula_opt): J = sum_wall sum_k w m_k (v_k . n A) f1.
  * DVM_DRAG: m_k = v_k . d, d = free-stream direction (m_J = v1 at zero incidence, Sec. 2.4);
@@ -176,6 +178,19 @@ int dvm_state_moments(const dvm_state* st, double* prim_host);
  * DVM_ERR_OOM. */
 int dvm_state_set_order(dvm_state* st, int order, int defect_period);
 int dvm_state_get_order(const dvm_state* st, int* order);
+/* Cell Maxwellian of the collision term for every later sweep of this state and its adjoints.
+ * DVM_MAXWELL_PLAIN (the default): g of Eq. (maxwell_reduce) at the cell's primitive variables, whose
+ * discrete moments on a truncated velocity grid differ slightly from the cell's.
+ * DVM_MAXWELL_CONSERVATIVE: g at the parameters p = (rho, u, T) whose discrete moments equal the
+ * cell's exactly, sum_k w_k Psi_k g_k(p) = W (Newton's method per cell: from the primitive variables on
+ * this call and after dvm_state_set, two warm steps after every sweep), so the collision term conserves
+ * mass, momentum and energy on the grid itself.  The relaxation time stays that of the primitive
+ * variables.  The adjoint takes the fit's implicit derivative dp/dW = (dM/dp)^{-1}, and both
+ * sensitivity modes use the fitted g.  Allocates a small per-cell buffer for the state and one for
+ * each adjoint (16 doubles per cell; DVM_ERR_ADMISSION); dvm_batch requests use the plain Maxwellian.
+ * Errors: DVM_ERR_INVALID_ARG (NULL, unknown kind), DVM_ERR_ADMISSION, DVM_ERR_OOM, DVM_ERR_CUDA. */
+int dvm_state_set_maxwellian(dvm_state* st, int kind);
+int dvm_state_get_maxwellian(const dvm_state* st, int* kind);
 /* Run exactly n point-implicit sweeps (Eq. numerpr_gov solved for f_{c,k} with the neighbours,
  * moments and wall density of the previous sweep):
  *   f_new = [ V g/tau + sum_{a<=0} (-a) F_up ] / [ V/tau + sum_{a>0} a ],  a = A n . v_k.

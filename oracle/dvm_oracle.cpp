@@ -33,6 +33,7 @@
  * Discrete adjoint in the paper's sign (Lagrangian L = J + sum w phi . R, Eq. lagrangian):
  *   (dR/df)^T (w phi) = -(dJ/df)^T,   dJ/dalpha = dJ/dalpha|_f + sum w phi . dR/dalpha|_f.
  */
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -76,6 +77,7 @@ struct Prob {
     const double* w;
     double Kn, Ma, Tw, aoa;
     double dir[3];        /* m_J(v) = dir[0] vx + dir[1] vy + dir[2] |v|^2/2 */
+    int conservative;     /* 1: the cell Maxwellian matches the cell's discrete moments exactly */
 };
 
 inline double moment_J(const double* dir, double vx, double vy) {
@@ -180,6 +182,73 @@ void primitives(const S W[4], S& rho, S& u1, S& u2, S& T) {
     T = (2.0 / 3.0) * (W[3] / rho - 0.5 * (u1 * u1 + u2 * u2));
 }
 
+/* Solve the 4x4 system A x = b in place (Gaussian elimination, pivots chosen on the values). */
+template <class S>
+void solve4(S A[4][4], S b[4], S x[4]) {
+    int piv[4] = {0, 1, 2, 3};
+    for (int col = 0; col < 4; ++col) {
+        int best = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (std::fabs(val(A[piv[r]][col])) > std::fabs(val(A[piv[best]][col]))) best = r;
+        std::swap(piv[col], piv[best]);
+        for (int r = col + 1; r < 4; ++r) {
+            S m = A[piv[r]][col] / A[piv[col]][col];
+            for (int c2 = col; c2 < 4; ++c2) A[piv[r]][c2] -= m * A[piv[col]][c2];
+            b[piv[r]] -= m * b[piv[col]];
+        }
+    }
+    for (int col = 3; col >= 0; --col) {
+        S acc = b[piv[col]];
+        for (int c2 = col + 1; c2 < 4; ++c2) acc -= A[piv[col]][c2] * x[c2];
+        x[col] = acc / A[piv[col]][col];
+    }
+}
+
+/* Parameters (rho, u1, u2, T) of the cell Maxwellian g in the collision term.  Plain: the
+ * primitives of W.  Conservative: the parameters whose discrete Maxwellian has exactly the cell's
+ * discrete moments, sum_k w_k Psi_k g_k = W (Psi = 1, vx, vy and |v|^2/2 on g1 plus 1 on g2), by
+ * Newton's method from the primitives.  With dual numbers the converged iteration carries the
+ * implicit derivative (dM/dp)^{-1} dW, so the transposed operator and the sensitivities follow. */
+template <class S>
+void maxwell_params(const Prob& p, const S W[4], S& rho, S& u1, S& u2, S& T) {
+    primitives(W, rho, u1, u2, T);
+    if (!p.conservative) return;
+    int extra = -1;
+    for (int it = 0; it < 60; ++it) {
+        S M[4] = {S(0.0), S(0.0), S(0.0), S(0.0)};
+        S J[4][4];
+        for (int m = 0; m < 4; ++m)
+            for (int q = 0; q < 4; ++q) J[m][q] = S(0.0);
+        for (int k = 0; k < p.nv; ++k) {
+            double vx = p.vx[k], vy = p.vy[k], w = p.w[k], h = 0.5 * (vx * vx + vy * vy);
+            S g1, g2;
+            maxwellian(rho, u1, u2, T, vx, vy, g1, g2);
+            S cx = vx - u1, cy = vy - u2;
+            S c2 = cx * cx + cy * cy;
+            S d1[4] = {g1 / rho, g1 * cx / T, g1 * cy / T, g1 * (c2 / (2.0 * T * T) - 1.0 / T)};
+            const double psi[3] = {1.0, vx, vy};
+            for (int m = 0; m < 3; ++m) {
+                M[m] += w * psi[m] * g1;
+                for (int q = 0; q < 4; ++q) J[m][q] += w * psi[m] * d1[q];
+            }
+            M[3] += w * (h * g1 + g2);
+            for (int q = 0; q < 4; ++q) {
+                S d2 = 0.5 * T * d1[q];                       /* g2 = T g1 / 2 */
+                if (q == 3) d2 += 0.5 * g1;
+                J[3][q] += w * (h * d1[q] + d2);
+            }
+        }
+        S r[4] = {M[0] - W[0], M[1] - W[1], M[2] - W[2], M[3] - W[3]};
+        S x[4];
+        solve4(J, r, x);
+        rho -= x[0]; u1 -= x[1]; u2 -= x[2]; T -= x[3];
+        double step = std::fabs(val(x[0])) / std::fabs(val(rho)) + std::fabs(val(x[3])) / std::fabs(val(T)) +
+                      std::fabs(val(x[1])) + std::fabs(val(x[2]));
+        if (extra < 0 && step < 1e-14) extra = 2;    /* values converged: two more steps for the duals */
+        if (extra >= 0 && extra-- == 0) break;
+    }
+}
+
 template <class S>
 S relax_time(double tau_inf, S rho, S T) { return tau_inf / (rho * sqrt(T)); }
 
@@ -211,9 +280,10 @@ template <class S>
 void residual_cell(const Prob& p, const Consts& K, const Geo<S>& g, const S* f, int c, S* Rc) {
     const int nv = p.nv;
     const S* fc = f + (size_t)c * nv * 2;
-    S W[4], rho, u1, u2, T;
+    S W[4], rho, u1, u2, T, gr, gu1, gu2, gT;
     cell_moments(p, fc, W);
     primitives(W, rho, u1, u2, T);
+    maxwell_params(p, W, gr, gu1, gu2, gT);
     S Vt = g.V[c] / relax_time(K.tau_inf, rho, T);
     bool wall = (c / p.ni) == 0;
     WallFace<S> wf;
@@ -221,7 +291,7 @@ void residual_cell(const Prob& p, const Consts& K, const Geo<S>& g, const S* f, 
     for (int k = 0; k < nv; ++k) {
         double vx = p.vx[k], vy = p.vy[k];
         S g1, g2;
-        maxwellian(rho, u1, u2, T, vx, vy, g1, g2);
+        maxwellian(gr, gu1, gu2, gT, vx, vy, g1, g2);
         S R1 = Vt * (fc[2 * k] - g1);
         S R2 = Vt * (fc[2 * k + 1] - g2);
         for (int e = 0; e < 4; ++e) {
@@ -409,9 +479,10 @@ void apply_RT(const Prob& p, const Consts& K, const Geo<double>& g, const double
 void gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g, const double* f, int c, double* dst) {
     const int nv = p.nv;
     const double* fc = f + (size_t)c * nv * 2;
-    double W[4], rho, u1, u2, T;
+    double W[4], rho, u1, u2, T, gr, gu1, gu2, gT;
     cell_moments(p, fc, W);
     primitives(W, rho, u1, u2, T);
+    maxwell_params(p, W, gr, gu1, gu2, gT);
     double Vt = g.V[c] / relax_time(K.tau_inf, rho, T);
     bool wall = (c / p.ni) == 0;
     WallFace<double> wf;
@@ -419,7 +490,7 @@ void gs_update_cell(const Prob& p, const Consts& K, const Geo<double>& g, const 
     std::vector<double> nf(2 * nv);
     for (int k = 0; k < nv; ++k) {
         double vx = p.vx[k], vy = p.vy[k], g1, g2;
-        maxwellian<double>(rho, u1, u2, T, vx, vy, g1, g2);
+        maxwellian<double>(gr, gu1, gu2, gT, vx, vy, g1, g2);
         double d = Vt, r1 = Vt * g1, r2 = Vt * g2;
         for (int e = 0; e < 4; ++e) {
             double a = g.Sx[4 * c + e] * vx + g.Sy[4 * c + e] * vy;
@@ -466,13 +537,14 @@ void collision_partials_cell(const Prob& p, const Consts& K, const Geo<double>& 
     for (int m = 0; m < 4; ++m) {
         Dual Wd[4];
         for (int n = 0; n < 4; ++n) Wd[n] = Dual(W[n], n == m ? 1.0 : 0.0);
-        Dual rd, ud1, ud2, Td;
+        Dual rd, ud1, ud2, Td, gr, gu1, gu2, gT;
         primitives(Wd, rd, ud1, ud2, Td);
+        maxwell_params(p, Wd, gr, gu1, gu2, gT);
         Dual Vtd = Dual(g.V[c]) / relax_time(K.tau_inf, rd, Td);
         double* out = dCc + (size_t)m * nv * 2;
         for (int k = 0; k < nv; ++k) {
             Dual g1, g2;
-            maxwellian(rd, ud1, ud2, Td, p.vx[k], p.vy[k], g1, g2);
+            maxwellian(gr, gu1, gu2, gT, p.vx[k], p.vy[k], g1, g2);
             out[2 * k] = (Vtd * (Dual(fc[2 * k]) - g1)).d;
             out[2 * k + 1] = (Vtd * (Dual(fc[2 * k + 1]) - g2)).d;
         }
@@ -583,6 +655,7 @@ typedef struct {
     const double* w;
     double Kn, Ma, Tw, aoa;
     double dir[3];
+    int conservative;
 } orc_problem;
 
 static Prob to_prob(const orc_problem* q) {
@@ -591,6 +664,7 @@ static Prob to_prob(const orc_problem* q) {
     p.vx = q->vx; p.vy = q->vy; p.w = q->w;
     p.Kn = q->Kn; p.Ma = q->Ma; p.Tw = q->Tw; p.aoa = q->aoa;
     p.dir[0] = q->dir[0]; p.dir[1] = q->dir[1]; p.dir[2] = q->dir[2];
+    p.conservative = q->conservative;
     return p;
 }
 
@@ -642,7 +716,7 @@ int orc_collision(const orc_problem* q, const double* f, double* Q) {
         const double* fc = f + (size_t)c * p.nv * 2;
         double W[4], rho, u1, u2, T;
         cell_moments(p, fc, W);
-        primitives(W, rho, u1, u2, T);
+        maxwell_params(p, W, rho, u1, u2, T);
         for (int k = 0; k < p.nv; ++k) {
             double g1, g2;
             maxwellian<double>(rho, u1, u2, T, p.vx[k], p.vy[k], g1, g2);

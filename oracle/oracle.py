@@ -24,7 +24,7 @@ class _Problem(C.Structure):
     _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nv", C.c_int),
                 ("nodes", _dp), ("vx", _dp), ("vy", _dp), ("w", _dp),
                 ("Kn", C.c_double), ("Ma", C.c_double), ("Tw", C.c_double), ("aoa", C.c_double),
-                ("dir", C.c_double * 3)]
+                ("dir", C.c_double * 3), ("conservative", C.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -94,7 +94,7 @@ class Problem:
     m_J(v) = d . v + h |v|^2 / 2 for direction = (dx, dy) (h = 0: a force, drag = (1, 0)) or
     (dx, dy, h) (heat: (0, 0, 1))."""
 
-    def __init__(self, nodes, vx, vy, w, Kn, Ma, Tw=1.0, aoa=0.0, direction=(1.0, 0.0)):
+    def __init__(self, nodes, vx, vy, w, Kn, Ma, Tw=1.0, aoa=0.0, direction=(1.0, 0.0), conservative=False):
         self.nodes = _c(nodes)
         self.nj = self.nodes.shape[0] - 1
         self.ni = self.nodes.shape[1]
@@ -102,14 +102,15 @@ class Problem:
         self.nv = self.vx.size
         self.Kn, self.Ma, self.Tw, self.aoa = float(Kn), float(Ma), float(Tw), float(aoa)
         self.direction = _moment(direction)
+        self.conservative = bool(conservative)
         self._s = _Problem(self.ni, self.nj, self.nv, _ptr(self.nodes), _ptr(self.vx),
                            _ptr(self.vy), _ptr(self.w), self.Kn, self.Ma, self.Tw, self.aoa,
-                           (C.c_double * 3)(*self.direction))
+                           (C.c_double * 3)(*self.direction), int(self.conservative))
 
     @classmethod
-    def from_workload(cls, wl, direction=(1.0, 0.0)):
+    def from_workload(cls, wl, direction=(1.0, 0.0), conservative=False):
         return cls(wl.mesh.nodes, wl.grid.vx, wl.grid.vy, wl.grid.w, wl.flow.Kn, wl.flow.Ma,
-                   wl.flow.Tw, wl.flow.aoa, direction)
+                   wl.flow.Tw, wl.flow.aoa, direction, conservative)
 
     @property
     def ncell(self):

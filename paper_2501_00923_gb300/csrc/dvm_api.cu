@@ -90,6 +90,8 @@ struct dvm_state {
     int graph_phase = 0;        // so_phase at the start of the captured graph
     int graph_so = 0;           // reconstruction launches inside the captured graph
     bool capturing = false;
+    int maxwell = 0;            // 1: conservative discrete Maxwellian (fitted to the cell's discrete moments)
+    double4* fit = nullptr;     // its parameters for the current f
 };
 
 struct dvm_adjoint {
@@ -117,6 +119,7 @@ struct dvm_adjoint {
     bool capturing = false;
     void* so_def = nullptr;     // second order: frozen transposed defect (dR/df)^T (w phi) / w
     int so_phase = 0;
+    double* Kinv = nullptr;     // conservative Maxwellian: dp/dW per cell, [ncell][4][4]
     TmaMaps maps[2];            // tiled-TMA descriptors of phi[0], phi[1]
     // sensitivity scratch, allocated on first use
     double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr;
@@ -259,6 +262,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     a.f_new = (TS*)st->f[1 - src];
     a.prim_old = st->prim[src];
     a.prim_new = st->prim[1 - src];
+    a.maxw_old = st->maxwell ? st->fit : st->prim[src];
     a.Fw_old = st->Fw[src];
     a.Fw_new = st->Fw[1 - src];
     a.Jpart = st->Jpart;
@@ -303,6 +307,7 @@ AdjointArgs<TS, TC> adjoint_args(const dvm_adjoint* ad, int src) {
     a.respart = ad->respart;
     a.err = st->ctx->derr;
     a.defect = st->order == 2 ? (const TS*)ad->so_def : nullptr;
+    a.Kinv = st->maxwell ? ad->Kinv : nullptr;
     return a;
 }
 
@@ -342,6 +347,9 @@ cudaError_t enqueue_second_order(const dvm_state* st, const void* in, const doub
     }
 }
 
+// Identity of the discretisation a captured graph was built for (spatial order, Maxwellian).
+int scheme_of(const dvm_state* st) { return 2 * st->order + st->maxwell; }
+
 // Defect correction: the defect is taken from the sweep's input at the first sweep of each group of
 // so_period sweeps and frozen for the rest of the group.  Counts its launches (into the graph's count
 // while a graph is being captured).
@@ -364,11 +372,20 @@ cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
                                               st->so[2], false);
         if (e != cudaSuccess) return e;
     }
+    cudaError_t e;
     switch (st->storage) {
-        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); return launch_primal_sweep(0, &a, st->maps[src], res, st->ctx->stream); }
-        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); return launch_primal_sweep(1, &a, st->maps[src], res, st->ctx->stream); }
-        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); return launch_primal_sweep(2, &a, st->maps[src], res, st->ctx->stream); }
+        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); e = launch_primal_sweep(0, &a, st->maps[src], res, st->ctx->stream); break; }
+        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); e = launch_primal_sweep(1, &a, st->maps[src], res, st->ctx->stream); break; }
+        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); e = launch_primal_sweep(2, &a, st->maps[src], res, st->ctx->stream); break; }
     }
+    if (e == cudaSuccess && st->maxwell) {
+        // the next sweep's Maxwellian: two Newton steps from the previous fit
+        e = launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[1 - src], st->fit, true, 2, nullptr,
+                               st->ctx->stream);
+        if (st->capturing) st->graph_so += 1;
+        else st->ctx->launches += 1;
+    }
+    return e;
 }
 
 cudaError_t enqueue_adjoint(dvm_adjoint* ad, int src, bool update = true, bool res = true) {
@@ -390,7 +407,15 @@ cudaError_t enqueue_adjoint(dvm_adjoint* ad, int src, bool update = true, bool r
 // Recompute the linearisation constants from the state's current moments.
 cudaError_t adjoint_relinearise(dvm_adjoint* ad) {
     const dvm_state* st = ad->st;
-    cudaError_t e = launch_adjoint_cellconst(st->storage, st->prim[st->cur], st->mesh->d, 1.0 / st->fl.tau_inf,
+    cudaError_t e = cudaSuccess;
+    if (st->maxwell && ad->Kinv) {
+        e = launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[st->cur], st->fit, true, 0, ad->Kinv,
+                               st->ctx->stream);
+        st->ctx->launches += 1;
+    }
+    if (e == cudaSuccess)
+        e = launch_adjoint_cellconst(st->storage, st->prim[st->cur], st->maxwell ? st->fit : st->prim[st->cur],
+                                     st->mesh->d, 1.0 / st->fl.tau_inf,
                                              ad->cell, st->ctx->stream);
     st->ctx->launches += 1;
     ad->st_version = st->version;
@@ -599,7 +624,7 @@ bool graphs_ok(const dvm_context* ctx) { return ctx->stream != nullptr && !(ctx-
 
 // Capture K (even) sweeps + one finalize.  Buffers return to the same parity after K sweeps.
 int build_primal_graph(dvm_state* st, int K) {
-    if (st->graph && st->graph_n == K && st->graph_cur == st->cur && st->graph_order == st->order &&
+    if (st->graph && st->graph_n == K && st->graph_cur == st->cur && st->graph_order == scheme_of(st) &&
         st->graph_phase == st->so_phase)
         return DVM_OK;
     if (st->graph) { cudaGraphExecDestroy(st->graph); st->graph = nullptr; }
@@ -624,13 +649,13 @@ int build_primal_graph(dvm_state* st, int K) {
     CK(e);
     st->graph_n = K;
     st->graph_cur = st->cur;
-    st->graph_order = st->order;
+    st->graph_order = scheme_of(st);
     return DVM_OK;
 }
 
 int build_adjoint_graph(dvm_adjoint* ad, int K) {
     if (ad->graph && ad->graph_n == K && ad->graph_cur == ad->cur && ad->graph_st_cur == ad->st->cur &&
-        ad->graph_order == ad->st->order && ad->graph_phase == ad->so_phase)
+        ad->graph_order == scheme_of(ad->st) && ad->graph_phase == ad->so_phase)
         return DVM_OK;
     if (ad->graph) { cudaGraphExecDestroy(ad->graph); ad->graph = nullptr; }
     cudaStream_t s = ad->st->ctx->stream;
@@ -655,7 +680,7 @@ int build_adjoint_graph(dvm_adjoint* ad, int K) {
     ad->graph_n = K;
     ad->graph_cur = ad->cur;
     ad->graph_st_cur = ad->st->cur;
-    ad->graph_order = ad->st->order;
+    ad->graph_order = scheme_of(ad->st);
     return DVM_OK;
 }
 
@@ -899,6 +924,7 @@ void dvm_state_destroy(dvm_state* st) {
     for (int b = 0; b < 2; ++b) { dfree(st->f[b]); dfree(st->prim[b]); dfree(st->Fw[b]); }
     dfree(st->Jpart); dfree(st->respart); dfree(st->out); dfree(st->scratch);
     for (void* p : st->so) dfree(p);
+    dfree(st->fit);
     dfree(st->fl.fdd); dfree(st->fl.fdf); dfree(st->fl.gwd); dfree(st->fl.gwf); dfree(st->fl.wallD); dfree(st->fl.wallM);
     aa_free(st->ctx, st->aa);
     st->ctx->bytes -= st->bytes;
@@ -996,6 +1022,10 @@ int dvm_state_set(dvm_state* st, const double* f_host) {
     cudaError_t e = cudaMemcpyAsync(tmp, f_host, n * sizeof(double), cudaMemcpyHostToDevice, st->ctx->stream);
     if (e == cudaSuccess) e = launch_convert(st->storage, 1, tmp, st->f[st->cur], m.ncell, g.nv, g.nvp, st->ctx->stream);
     if (e == cudaSuccess) e = launch_moments(st->storage, st->f[st->cur], m, g, st->prim[st->cur], st->Fw[st->cur], st->ctx->stream);
+    if (e == cudaSuccess && st->maxwell) {
+        e = launch_maxwell_fit(st->storage, m, g, st->prim[st->cur], st->fit, false, 8, nullptr, st->ctx->stream);
+        st->ctx->launches += 1;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st->ctx->stream);
     st->ctx->launches += 2;
     st->version += 1;
@@ -1060,8 +1090,19 @@ int dvm_state_set_order(dvm_state* st, int order, int defect_period) {
 
 // The adjoint's frozen defect buffer, allocated when a sweep of a second-order state first needs it.
 static int adjoint_so_ensure(dvm_adjoint* ad) {
-    if (ad->st->order != 2 || ad->so_def) return DVM_OK;
     dvm_context* ctx = ad->st->ctx;
+    if (ad->st->maxwell && !ad->Kinv) {
+        const size_t nb = (size_t)ad->st->mesh->d.ncell * 16 * sizeof(double);
+        if (ctx->budget && ctx->bytes + nb > ctx->budget)
+            return fail(DVM_ERR_ADMISSION, "the adjoint's Maxwellian Jacobians do not fit the context's HBM budget");
+        size_t acc = 0;
+        int rc = dalloc(ctx, &ad->Kinv, (size_t)ad->st->mesh->d.ncell * 16, &acc);
+        if (rc) return rc;
+        ad->bytes += acc;
+        ctx->bytes += acc;
+        ad->st_version = ~0ull;   // relinearise with the Jacobians
+    }
+    if (ad->st->order != 2 || ad->so_def) return DVM_OK;
     const size_t nb = (size_t)ad->st->mesh->d.ncell * ad->st->grid->d.nvp * storage_bytes(ad->st->storage);
     if (ctx->budget && ctx->bytes + nb > ctx->budget)
         return fail(DVM_ERR_ADMISSION, "second-order adjoint buffer does not fit the context's HBM budget");
@@ -1077,6 +1118,38 @@ static int adjoint_so_ensure(dvm_adjoint* ad) {
 int dvm_state_get_order(const dvm_state* st, int* order) {
     if (!st || !order) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
     *order = st->order;
+    return DVM_OK;
+}
+
+int dvm_state_set_maxwellian(dvm_state* st, int kind) {
+    if (!st) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (kind != DVM_MAXWELL_PLAIN && kind != DVM_MAXWELL_CONSERVATIVE) return fail(DVM_ERR_INVALID_ARG, "unknown Maxwellian");
+    dvm_context* ctx = st->ctx;
+    DeviceGuard dg(ctx->device);
+    if (kind == DVM_MAXWELL_CONSERVATIVE && !st->fit) {
+        const size_t nb = (size_t)st->mesh->d.ncell * sizeof(double4);
+        if (ctx->budget && ctx->bytes + nb > ctx->budget)
+            return fail(DVM_ERR_ADMISSION, "the fitted Maxwellian does not fit the context's HBM budget");
+        size_t acc = 0;
+        int rc = dalloc(ctx, &st->fit, st->mesh->d.ncell, &acc);
+        if (rc) return rc;
+        st->bytes += acc;
+        ctx->bytes += acc;
+    }
+    st->maxwell = kind;
+    st->version += 1;           // adjoints relinearise
+    if (kind == DVM_MAXWELL_CONSERVATIVE) {
+        CK(launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[st->cur], st->fit, false, 8, nullptr,
+                              ctx->stream));
+        ctx->launches += 1;
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return DVM_OK;
+}
+
+int dvm_state_get_maxwellian(const dvm_state* st, int* kind) {
+    if (!st || !kind) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    *kind = st->maxwell;
     return DVM_OK;
 }
 
@@ -1189,6 +1262,11 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
                 st->so_phase = 0;
                 CK(launch_moments(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur],
                                   st->Fw[st->cur], ctx->stream));
+                if (st->maxwell) {
+                    CK(launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[st->cur], st->fit, true, 3,
+                                          nullptr, ctx->stream));
+                    ctx->launches += 1;
+                }
                 ctx->launches += 1;
                 st->version += 1;
             }
@@ -1217,7 +1295,7 @@ void dvm_adjoint_destroy(dvm_adjoint* ad) {
     for (int b = 0; b < 2; ++b) { dfree(ad->phi[b]); dfree(ad->Z[b]); dfree(ad->Lam[b]); }
     dfree(ad->respart); dfree(ad->out); dfree(ad->wallM); dfree(ad->cell);
     dfree(ad->GN); dfree(ad->GE); dfree(ad->GW); dfree(ad->node_grad); dfree(ad->vol); dfree(ad->elem);
-    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad); dfree(ad->so_def);
+    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad); dfree(ad->so_def); dfree(ad->Kinv);
     aa_free(ad->st->ctx, ad->aa);
     ad->st->ctx->bytes -= ad->bytes;
     delete ad;
@@ -1348,8 +1426,8 @@ int dvm_adjoint_iterate(dvm_adjoint* ad, int n, double* residual_out) {
     if (!ad || n < 0) return fail(DVM_ERR_INVALID_ARG, "bad argument");
     if (n == 0) return DVM_OK;
     DeviceGuard dg(ad->st->ctx->device);
-    int rc0 = adjoint_follow_state(ad);
-    if (!rc0) rc0 = adjoint_so_ensure(ad);
+    int rc0 = adjoint_so_ensure(ad);            // buffers first: a new Jacobian buffer forces relinearisation
+    if (!rc0) rc0 = adjoint_follow_state(ad);
     if (rc0) return rc0;
     double* hist = nullptr;
     int rc = dalloc(ad->st->ctx, &hist, 2 * (size_t)n);
@@ -1386,8 +1464,8 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         return fail(DVM_ERR_INVALID_ARG, "warm-start adjoint belongs to another state/functional");
     }
     dvm_adjoint* ad = *inout;
-    if ((rc = adjoint_follow_state(ad))) return rc;
     if ((rc = adjoint_so_ensure(ad))) return rc;
+    if ((rc = adjoint_follow_state(ad))) return rc;
     const bool accel = opts->accel_depth > 0;
     const int K = accel ? opts->accel_period : ctx->graph_iters;
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
@@ -1488,7 +1566,8 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
             CK(cudaMemcpyAsync(node_grad_out, ad->node_grad, (size_t)m.ni * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     } else {
         CK(cudaMemcpyAsync(ad->sj, s_j, (m.nj + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->mj,
+        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur],
+                            st->maxwell ? st->fit : st->prim[st->cur], st->Fw[st->cur], ad->mj,
                             ad->GN, ad->GE, ad->GW, ad->vol, ad->node_grad, s));
         CK(launch_contract(ad->node_grad, m.nj + 1, m.ni, ad->sj, ad->dwall, P, ad->grad, s));
         ctx->launches += 2 + (P > 0);
@@ -1622,7 +1701,8 @@ extern "C" int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, co
             CK(cudaMemcpyAsync(node_grad_out, node_grad, (size_t)m.ni * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     } else {
         CK(cudaMemcpyAsync(sj, s_j, (m.nj + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur], st->Fw[st->cur], ad->mj,
+        CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur],
+                            st->maxwell ? st->fit : st->prim[st->cur], st->Fw[st->cur], ad->mj,
                             GN, GE, GW, vol, node_grad, s));
         CK(launch_contract(node_grad, m.nj + 1, m.ni, sj, dw, P, grad, s));
         if (node_grad_out)

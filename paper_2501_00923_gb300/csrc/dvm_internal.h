@@ -82,6 +82,7 @@ struct PrimalArgs {
     TS* f_new;
     const double4* prim_old;
     double4* prim_new;
+    const double4* maxw_old;                // parameters of the cell Maxwellian: prim_old, or the fit
     const double* Fw_old;
     double* Fw_new;
     double* Jpart;
@@ -114,7 +115,7 @@ struct SOArgs {
 // Per-cell constants of the adjoint linearisation (see k_adjoint_cellconst).
 template <class TC>
 struct alignas(sizeof(TC) * 4) AdjCell {
-    TC n0, inv2T, halfT, Vt, u1, u2, ir, iT, iT2h, c0, c3, j30, j31, j32, j33, pad;
+    TC n0, inv2T, halfT, Vt, u1, u2, ir, iT, iT2h, c0, c3, j30, j31, j32, j33, irg;
 };
 
 template <class TS, class TC>
@@ -143,6 +144,7 @@ struct AdjointArgs {
     double* respart;
     int* err;
     const TS* defect;                       // second order: (dR/df)^T (w phi_old) / w, subtracted likewise
+    const double* Kinv;                     // conservative Maxwellian: dp/dW per cell ([16]), else null
 };
 
 // Descriptors of the batched sweeps: the arguments and tensor maps of one request for both
@@ -189,8 +191,12 @@ cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4
 cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
                                        bool res, cudaStream_t s);
 cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, double* out, cudaStream_t s);
-cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
-                                     void* out, cudaStream_t s);
+// maxw: parameters of the cell Maxwellian (prim itself, or the conservative fit)
+cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const double4* maxw, const DevMesh& m,
+                                     double inv_tau_inf, void* out, cudaStream_t s);
+// Conservative discrete Maxwellian of every cell from its primitive variables (see k_maxwell_fit).
+cudaError_t launch_maxwell_fit(int storage, const DevMesh& m, const DevGrid& g, const double4* prim, double4* fit,
+                               bool warm, int iters, double* Kinv, cudaStream_t s);
 // out[0] = sum respart; out[1] = sum_l Jpart_l + Fw_l M_l (Fw/M may be null -> only sum Jpart)
 cudaError_t launch_finalize(const double* respart, int ncell, const double* Jpart, const double* Fw,
                             const double* M, int ni, double* out, cudaStream_t s);
@@ -205,7 +211,7 @@ cudaError_t launch_sens_paper(int storage, const DevMesh& m, const DevGrid& g, c
                               const void* f, const void* phi, const double* Fw, MomentJ mj,
                               double* elem, double* node_grad, cudaStream_t s);
 cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
-                             const void* f, const void* phi, const double4* prim, const double* Fw,
+                             const void* f, const void* phi, const double4* prim, const double4* maxw, const double* Fw,
                              MomentJ mj, double2* GN, double2* GE, double2* GW,
                              double* vol, double2* node_grad, cudaStream_t s);
 cudaError_t launch_contract(const double2* node_grad, int nrows, int ni, const double* s_j,

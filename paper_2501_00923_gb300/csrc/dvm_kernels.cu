@@ -414,11 +414,11 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     constexpr int KV = PK::KV, NP = KV / 2;
     constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
     const float2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
-    const double4 pr = P.prim_old[c];
-    const float rho = (float)pr.x, u1 = (float)pr.y, u2 = (float)pr.z, T = (float)pr.w;
+    const double4 pr = P.prim_old[c], pm = P.maxw_old[c];   // moments (tau), Maxwellian parameters (g)
+    const float rho = (float)pm.x, u1 = (float)pm.y, u2 = (float)pm.z, T = (float)pm.w;
     Gauss<float> G;
     G.setup(rho, u1, u2, T);
-    const float Vt = P.V[c] * rho * sqrtf(T) * (float)P.inv_tau_inf;      // V / tau
+    const float Vt = P.V[c] * (float)pr.x * sqrtf((float)pr.w) * (float)P.inv_tau_inf;      // V / tau
     const float2 kA = bc(G.kA), kB = bc(G.kB), mu1 = bc(-u1), mu2 = bc(-u2), Vt2 = bc(Vt), hT = bc(0.5f * T);
     const float2 s0x = bc(S0.x), s0y = bc(S0.y), s1x = bc(S1.x), s1y = bc(S1.y);
     const float2 s2x = bc(S2.x), s2y = bc(S2.y), s3x = bc(S3.x), s3y = bc(S3.y);
@@ -555,12 +555,12 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
     constexpr int KV = PK::KV;
     constexpr bool wall = (kBnd & kWallCell) != 0, far = (kBnd & kFarCell) != 0;
     const TC2 S0 = P.S[4 * c], S1 = P.S[4 * c + 1], S2 = P.S[4 * c + 2], S3 = P.S[4 * c + 3];
-    const double4 pr = P.prim_old[c];
-    const TC rho = (TC)pr.x, u1 = (TC)pr.y, u2 = (TC)pr.z, T = (TC)pr.w;
+    const double4 pr = P.prim_old[c], pm = P.maxw_old[c];   // moments (tau), Maxwellian parameters (g)
+    const TC rho = (TC)pm.x, u1 = (TC)pm.y, u2 = (TC)pm.z, T = (TC)pm.w;
     Gauss<TC> G;
     G.setup(rho, u1, u2, T);
     const TC halfT = TC(0.5) * T;
-    const TC Vt = P.V[c] * rho * sqrt(T) * (TC)P.inv_tau_inf;        // V / tau
+    const TC Vt = P.V[c] * (TC)pr.x * sqrt((TC)pr.w) * (TC)P.inv_tau_inf;        // V / tau
     TC cw1 = TC(0), cw2 = TC(0), invA = TC(0);
     if (wall) {
         cw1 = (TC)P.Fw_old[c] / (TC)P.wallD[c];
@@ -780,6 +780,19 @@ __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep_batc
 // (Eq. adjoint_eqdefines / adjoint_macdefines) of the previous sweep; it is rebuilt here from
 // the new phi: What = J_P^T Phat with Phat = sum_k w (phi1 dg1/dp + phi2 dg2/dp), p = (rho,u,T),
 // and rhohat' = sum_k w phi . (f - g).  Lambda = sum_{a<=0} w a phi . gbar_w (Eq. formula_adjointbgk).
+// Z with the conservative Maxwellian: the Maxwellian part p_g (derivatives with respect to the fitted
+// parameters) maps to W through dp/dW = (dM/dp)^{-1} (K, row-major [q][m]), the relaxation-time part
+// (a, b) = d/d(rho, T) of the physical moments through J_P.
+__device__ __forceinline__ double4 z_fitted(const double* K, double g0, double g1, double g2, double g3,
+                                            double a, double b, double j30, double j31, double j32, double j33) {
+    double4 z;
+    z.x = a + b * j30 + K[0] * g0 + K[4] * g1 + K[8] * g2 + K[12] * g3;
+    z.y = b * j31 + K[1] * g0 + K[5] * g1 + K[9] * g2 + K[13] * g3;
+    z.z = b * j32 + K[2] * g0 + K[6] * g1 + K[10] * g2 + K[14] * g3;
+    z.w = b * j33 + K[3] * g0 + K[7] * g1 + K[11] * g2 + K[15] * g3;
+    return z;
+}
+
 // The per-cell constants of the linearisation (Maxwellian parameters, V/tau, J_P, d(1/tau)/dp)
 // come precomputed in AdjCell.  kUpdate = false: phi is not advanced; the couplings of phi_old are
 // written to the *_new slots (used after an upload of phi or a change of the primal state).
@@ -921,14 +934,19 @@ __device__ __forceinline__ bool adjoint_cell_paired(const AdjointArgs<TS, float>
     if (wall) LAM = lam.total();
     if (lane == 0) {
         const AdjCell<float> cc = *ccp;
-        const float ph0 = Sh * cc.ir, ph1 = Shx * cc.iT, ph2 = Shy * cc.iT;
+        const float ph0 = Sh * cc.irg, ph1 = Shx * cc.iT, ph2 = Shy * cc.iT;
         const float ph3 = Shc * cc.iT2h - Sh * cc.iT + 0.5f * Sg2;
-        const float p0 = Vt * ph0 - Sr * cc.c0, p1 = Vt * ph1, p2 = Vt * ph2, p3 = Vt * ph3 - Sr * cc.c3;
         double4 zn;
-        zn.x = (double)(p0 - (p1 * u1 + p2 * u2) * cc.ir + p3 * cc.j30);
-        zn.y = (double)(p1 * cc.ir + p3 * cc.j31);
-        zn.z = (double)(p2 * cc.ir + p3 * cc.j32);
-        zn.w = (double)(p3 * cc.j33);
+        if (P.Kinv) {
+            zn = z_fitted(P.Kinv + 16 * (size_t)c, Vt * ph0, Vt * ph1, Vt * ph2, Vt * ph3, -Sr * cc.c0,
+                          -Sr * cc.c3, cc.j30, cc.j31, cc.j32, cc.j33);
+        } else {
+            const float p0 = Vt * ph0 - Sr * cc.c0, p1 = Vt * ph1, p2 = Vt * ph2, p3 = Vt * ph3 - Sr * cc.c3;
+            zn.x = (double)(p0 - (p1 * u1 + p2 * u2) * cc.ir + p3 * cc.j30);
+            zn.y = (double)(p1 * cc.ir + p3 * cc.j31);
+            zn.z = (double)(p2 * cc.ir + p3 * cc.j32);
+            zn.w = (double)(p3 * cc.j33);
+        }
         P.Z_new[c] = zn;
         if (kRes) {
             const float V = P.V[c];
@@ -1053,14 +1071,19 @@ __device__ __forceinline__ bool adjoint_cell(const AdjointArgs<TS, typename Pack
     if (lane == 0) {
         const AdjCell<TC> cc = *ccp;   // epilogue-only constants, loaded after the loop
         // Phat in primitive variables, then p = (V/tau) Phat - V rhohat' d(1/tau)/dp, Z = J_P^T p
-        const TC ph0 = Sh * cc.ir, ph1 = Shx * cc.iT, ph2 = Shy * cc.iT;
+        const TC ph0 = Sh * cc.irg, ph1 = Shx * cc.iT, ph2 = Shy * cc.iT;
         const TC ph3 = Shc * cc.iT2h - Sh * cc.iT + TC(0.5) * Sg2;
-        const TC p0 = Vt * ph0 - Sr * cc.c0, p1 = Vt * ph1, p2 = Vt * ph2, p3 = Vt * ph3 - Sr * cc.c3;
         double4 zn;
-        zn.x = (double)(p0 - (p1 * u1 + p2 * u2) * cc.ir + p3 * cc.j30);
-        zn.y = (double)(p1 * cc.ir + p3 * cc.j31);
-        zn.z = (double)(p2 * cc.ir + p3 * cc.j32);
-        zn.w = (double)(p3 * cc.j33);
+        if (P.Kinv) {
+            zn = z_fitted(P.Kinv + 16 * (size_t)c, Vt * ph0, Vt * ph1, Vt * ph2, Vt * ph3, -Sr * cc.c0,
+                          -Sr * cc.c3, cc.j30, cc.j31, cc.j32, cc.j33);
+        } else {
+            const TC p0 = Vt * ph0 - Sr * cc.c0, p1 = Vt * ph1, p2 = Vt * ph2, p3 = Vt * ph3 - Sr * cc.c3;
+            zn.x = (double)(p0 - (p1 * u1 + p2 * u2) * cc.ir + p3 * cc.j30);
+            zn.y = (double)(p1 * cc.ir + p3 * cc.j31);
+            zn.z = (double)(p2 * cc.ir + p3 * cc.j32);
+            zn.w = (double)(p3 * cc.j33);
+        }
         P.Z_new[c] = zn;
         if (kRes) {
             const TC V = P.V[c];
@@ -1132,20 +1155,22 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep_ba
 // primal state does not change): Maxwellian parameters, V/tau, the Jacobian J_P = d(rho,u,T)/dW
 // and V d(1/tau)/d(rho, T).
 template <class TC>
-__global__ void k_adjoint_cellconst(int ncell, const double4* prim, const double* V, double inv_tau_inf,
-                                    AdjCell<TC>* out) {
+__global__ void k_adjoint_cellconst(int ncell, const double4* prim, const double4* maxw, const double* V,
+                                    double inv_tau_inf, AdjCell<TC>* out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
-    const double4 p = prim[c];
-    const double rho = p.x, u1 = p.y, u2 = p.z, T = p.w, sT = sqrt(T), ir = 1.0 / rho, iT = 1.0 / T;
+    const double4 p = prim[c], q = maxw[c];            // moments (tau, J_P); Maxwellian parameters (g)
+    const double rho = p.x, u1 = p.y, u2 = p.z, T = p.w, sT = sqrt(T), ir = 1.0 / rho;
+    const double iT = 1.0 / q.w;
     AdjCell<TC> a;
-    a.n0 = (TC)(rho * iT / (2.0 * kPi));
+    a.n0 = (TC)(q.x * iT / (2.0 * kPi));
     a.inv2T = (TC)(0.5 * iT);
-    a.halfT = (TC)(0.5 * T);
+    a.halfT = (TC)(0.5 * q.w);
     a.Vt = (TC)(V[c] * rho * sT * inv_tau_inf);
-    a.u1 = (TC)u1;
-    a.u2 = (TC)u2;
+    a.u1 = (TC)q.y;
+    a.u2 = (TC)q.z;
     a.ir = (TC)ir;
+    a.irg = (TC)(1.0 / q.x);
     a.iT = (TC)iT;
     a.iT2h = (TC)(0.5 * iT * iT);
     a.c0 = (TC)(V[c] * sT * inv_tau_inf);
@@ -1154,7 +1179,6 @@ __global__ void k_adjoint_cellconst(int ncell, const double4* prim, const double
     a.j31 = (TC)(-(2.0 / 3.0) * u1 * ir);
     a.j32 = (TC)(-(2.0 / 3.0) * u2 * ir);
     a.j33 = (TC)((2.0 / 3.0) * ir);
-    a.pad = (TC)0;
     out[c] = a;
 }
 
@@ -1238,6 +1262,98 @@ __global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const
         prim[c] = make_double4(m0, u1, u2, (2.0 / 3.0) * (m3 / m0 - 0.5 * (u1 * u1 + u2 * u2)));
         if (wall) Fw[c] = fw / sqrt(s.x * s.x + s.y * s.y);
     }
+}
+
+// ================================================================== conservative discrete Maxwellian
+// The cell Maxwellian of the collision term with parameters p = (rho, u1, u2, T) chosen so that its
+// discrete moments equal the cell's: M(p) = sum_k w_k Psi_k g_k(p) = W, Psi = (1, vx, vy, |v|^2/2) on g1
+// and 1 on g2 = T g1 / 2 (the conservative discrete velocity schemes the paper builds on).  Newton's
+// method, `iters` steps from the previous fit (warm) or from the primitive variables; with Kinv the
+// inverse Jacobian dp/dW = (dM/dp)^{-1} at the final p (row-major [q][m]) for the adjoint.  One warp
+// per cell: per-lane sums, a fixed butterfly, and every lane solves the same 4x4 system in FP64.
+__device__ __forceinline__ bool lu4_solve(double A[4][4], double b[4], double x[4]) {
+    int piv[4] = {0, 1, 2, 3};
+    for (int col = 0; col < 4; ++col) {
+        int best = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (fabs(A[piv[r]][col]) > fabs(A[piv[best]][col])) best = r;
+        const int t = piv[col]; piv[col] = piv[best]; piv[best] = t;
+        if (A[piv[col]][col] == 0.0) return false;
+        for (int r = col + 1; r < 4; ++r) {
+            const double m = A[piv[r]][col] / A[piv[col]][col];
+            for (int c2 = col; c2 < 4; ++c2) A[piv[r]][c2] -= m * A[piv[col]][c2];
+            b[piv[r]] -= m * b[piv[col]];
+        }
+    }
+    for (int col = 3; col >= 0; --col) {
+        double acc = b[piv[col]];
+        for (int c2 = col + 1; c2 < 4; ++c2) acc -= A[piv[col]][c2] * x[c2];
+        x[col] = acc / A[piv[col]][col];
+    }
+    return true;
+}
+
+template <class TC>
+__global__ void __launch_bounds__(256) k_maxwell_fit(int ncell, int nvp, const typename Vec<TC>::v4* __restrict__ vt,
+                                                     const double4* __restrict__ prim, double4* __restrict__ fit,
+                                                     int warm, int iters, double* __restrict__ Kinv) {
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 pr = prim[c];
+    const double W[4] = {pr.x, pr.x * pr.y, pr.x * pr.z, pr.x * (0.5 * (pr.y * pr.y + pr.z * pr.z) + 1.5 * pr.w)};
+    double4 p = warm ? fit[c] : pr;
+    for (int it = 0; it <= iters; ++it) {
+        if (it == iters && !Kinv) break;
+        const TC rho = (TC)p.x, u1 = (TC)p.y, u2 = (TC)p.z, T = (TC)p.w;
+        const TC n0 = rho / (TC(2.0 * kPi) * T), i2T = TC(0.5) / T, iT = TC(1) / T, ir = TC(1) / rho;
+        const TC hT = TC(0.5) * T;
+        // sums: M (4) and J (16): J[m][q] = sum w psi_m dg1/dp_q (m < 3), J[3][q] = sum w (h + T/2) dg1/dp_q
+        // + [q = 3] sum w g1 / 2; dg1/dp = g1 (1/rho, cx/T, cy/T, c^2/(2T^2) - 1/T)
+        TC s[20];
+#pragma unroll
+        for (int i = 0; i < 20; ++i) s[i] = TC(0);
+        for (int k = lane; k < nvp; k += 32) {
+            const auto t = vt[k];
+            const TC vx = t.x, vy = t.y, w = t.z, h = t.w;
+            const TC cx = vx - u1, cy = vy - u2, c2 = cx * cx + cy * cy;
+            const TC wg = w * n0 * dexp<TC>(-c2 * i2T);
+            const TC d[4] = {ir, cx * iT, cy * iT, c2 * i2T * iT - iT};
+            const TC psi[4] = {TC(1), vx, vy, h + hT};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                s[m] += wg * psi[m];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s[4 + 4 * m + q] += wg * psi[m] * d[q];
+            }
+            s[19] += TC(0.5) * wg;                 // d g2 / dT = g1 / 2 + (T/2) d g1 / dT
+        }
+        double M[4], A[4][4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            M[m] = warp_sum((double)s[m]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) A[m][q] = warp_sum((double)s[4 + 4 * m + q]);
+        }
+        if (it == iters) {                         // inverse Jacobian, column by column
+            double Inv[4][4];
+            for (int col = 0; col < 4; ++col) {
+                double B[4][4], e[4] = {0, 0, 0, 0}, x[4];
+                for (int m = 0; m < 4; ++m)
+                    for (int q = 0; q < 4; ++q) B[m][q] = A[m][q];
+                e[col] = 1.0;
+                if (!lu4_solve(B, e, x)) x[0] = x[1] = x[2] = x[3] = 0.0;
+                for (int q = 0; q < 4; ++q) Inv[q][col] = x[q];
+            }
+            if (lane == 0)
+                for (int q = 0; q < 4; ++q)
+                    for (int m = 0; m < 4; ++m) Kinv[16 * (size_t)c + 4 * q + m] = Inv[q][m];
+            break;
+        }
+        double r[4] = {M[0] - W[0], M[1] - W[1], M[2] - W[2], M[3] - W[3]}, x[4];
+        if (!lu4_solve(A, r, x)) break;
+        p.x -= x[0]; p.y -= x[1]; p.z -= x[2]; p.w -= x[3];
+    }
+    if (lane == 0) fit[c] = p;
 }
 
 // ================================================================== second order (reconstruction)
@@ -1751,8 +1867,8 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
                                                     const typename Vec<typename Pack<TS>::TC>::v4* vt,
                                                     const typename Vec<typename Pack<TS>::TC>::v2* fd,
                                                     const typename Pack<TS>::TC* gw, const double* wallD,
-                                                    const double4* prim, const double* Fw, double inv_tau_inf,
-                                                    double halfTw_d, MomentJ mj, double2* GN,
+                                                    const double4* prim, const double4* maxw, const double* Fw,
+                                                    double inv_tau_inf, double halfTw_d, MomentJ mj, double2* GN,
                                                     double2* GE, double2* GW, double* vol) {
     using TC = typename Pack<TS>::TC;
     const int lane = threadIdx.x & 31;
@@ -1761,9 +1877,9 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
     const int4 n = nb[c];
     const double2 s1d = S[4 * c + 1], s2d = S[4 * c + 2], s3d = S[4 * c + 3];
     const TC s1x = (TC)s1d.x, s1y = (TC)s1d.y, s2x = (TC)s2d.x, s2y = (TC)s2d.y, s3x = (TC)s3d.x, s3y = (TC)s3d.y;
-    const double4 pr = prim[c];
-    const TC u1 = (TC)pr.y, u2 = (TC)pr.z, n0 = (TC)(pr.x / (2.0 * kPi * pr.w)), inv2T = (TC)(0.5 / pr.w);
-    const TC halfT = (TC)(0.5 * pr.w), halfTw = (TC)halfTw_d, dirx = (TC)mj.dx, diry = (TC)mj.dy, hcoef = (TC)mj.h;
+    const double4 pr = prim[c], pm = maxw[c];          // moments (tau); Maxwellian parameters (g)
+    const TC u1 = (TC)pm.y, u2 = (TC)pm.z, n0 = (TC)(pm.x / (2.0 * kPi * pm.w)), inv2T = (TC)(0.5 / pm.w);
+    const TC halfT = (TC)(0.5 * pm.w), halfTw = (TC)halfTw_d, dirx = (TC)mj.dx, diry = (TC)mj.dy, hcoef = (TC)mj.h;
     const bool wall = n.w == kWall;
     const TC cw = wall ? (TC)(Fw[c] / wallD[c]) : TC(0);
     const TC gbs = wall ? (TC)(1.0 / wallD[c]) : TC(0);
@@ -2155,6 +2271,14 @@ cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cud
     return cudaGetLastError();
 }
 
+cudaError_t launch_maxwell_fit(int storage, const DevMesh& m, const DevGrid& g, const double4* prim, double4* fit,
+                               bool warm, int iters, double* Kinv, cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0) k_maxwell_fit<double><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vd, prim, fit, warm, iters, Kinv);
+    else k_maxwell_fit<float><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vf, prim, fit, warm, iters, Kinv);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
                            double* Fw, cudaStream_t s) {
     const int nb = cdiv(m.ncell, kWarpsPerBlock);
@@ -2254,11 +2378,12 @@ cudaError_t make_tmamaps(void* base, int ni, int nj, int nq, TmaMaps* out) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const DevMesh& m, double inv_tau_inf,
+cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const double4* maxw, const DevMesh& m,
+                                     double inv_tau_inf,
                                      void* out, cudaStream_t s) {
     const int b = 256;
-    if (storage == 0) k_adjoint_cellconst<double><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, m.Vd, inv_tau_inf, (AdjCell<double>*)out);
-    else k_adjoint_cellconst<float><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, m.Vd, inv_tau_inf, (AdjCell<float>*)out);
+    if (storage == 0) k_adjoint_cellconst<double><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, maxw, m.Vd, inv_tau_inf, (AdjCell<double>*)out);
+    else k_adjoint_cellconst<float><<<cdiv(m.ncell, b), b, 0, s>>>(m.ncell, prim, maxw, m.Vd, inv_tau_inf, (AdjCell<float>*)out);
     return cudaGetLastError();
 }
 
@@ -2394,22 +2519,22 @@ cudaError_t launch_sens_paper(int storage, const DevMesh& m, const DevGrid& g, c
 }
 
 cudaError_t launch_sens_full(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl, const void* f,
-                             const void* phi, const double4* prim, const double* Fw, MomentJ mj,
+                             const void* phi, const double4* prim, const double4* maxw, const double* Fw, MomentJ mj,
                              double2* GN, double2* GE, double2* GW, double* vol, double2* node_grad, cudaStream_t s) {
     const int nb = cdiv(m.ncell, kWarpsPerBlock);
     const double hT = 0.5 * fl.Tw, it = 1.0 / fl.tau_inf;
     if (storage == 0)
         k_sens_faces<double><<<nb, 256, 0, s>>>((const double*)f, (const double*)phi, m.ncell, g.nvp, m.nb, m.Sd, m.Vd,
-                                                g.vd, fl.fdd, fl.gwd, fl.wallD, prim, Fw, it, hT, mj, GN, GE,
+                                                g.vd, fl.fdd, fl.gwd, fl.wallD, prim, maxw, Fw, it, hT, mj, GN, GE,
                                                 GW, vol);
     else if (storage == 1)
         k_sens_faces<float><<<nb, 256, 0, s>>>((const float*)f, (const float*)phi, m.ncell, g.nvp, m.nb, m.Sd, m.Vd,
-                                               g.vf, fl.fdf, fl.gwf, fl.wallD, prim, Fw, it, hT, mj, GN, GE,
+                                               g.vf, fl.fdf, fl.gwf, fl.wallD, prim, maxw, Fw, it, hT, mj, GN, GE,
                                                GW, vol);
     else
         k_sens_faces<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, (const __nv_bfloat16*)phi, m.ncell,
                                                        g.nvp, m.nb, m.Sd, m.Vd, g.vf, fl.fdf, fl.gwf, fl.wallD, prim,
-                                                       Fw, it, hT, mj, GN, GE, GW, vol);
+                                                       maxw, Fw, it, hT, mj, GN, GE, GW, vol);
     const int nn = (m.nj + 1) * m.ni;
     k_sens_nodes<<<cdiv(nn, 256), 256, 0, s>>>(m.ni, m.nj, m.nodes, GN, GE, GW, vol, node_grad);
     return cudaGetLastError();

@@ -94,6 +94,8 @@ def lib():
             "dvm_state_moments": (i, [_vp, _dp]),
             "dvm_state_set_order": (i, [_vp, i, i]),
             "dvm_state_get_order": (i, [_vp, C.POINTER(i)]),
+            "dvm_state_set_maxwellian": (i, [_vp, i]),
+            "dvm_state_get_maxwellian": (i, [_vp, C.POINTER(i)]),
             "dvm_primal_iterate": (i, [_vp, i, _dp]),
             "dvm_state_functional": (i, [_vp, i, _dp]),
             "dvm_primal_solve": (i, [_vp, _vp, _vp, C.POINTER(Flow), C.POINTER(SolveOpts), i, pp,
@@ -283,6 +285,17 @@ class State:
     @order.setter
     def order(self, order: int):
         self.set_order(order)
+
+    @property
+    def maxwellian(self) -> str:
+        """Cell Maxwellian of the collision term: "plain" or "conservative" (fitted moments)."""
+        k = C.c_int()
+        _check(lib().dvm_state_get_maxwellian(self.h, C.byref(k)))
+        return ("plain", "conservative")[k.value]
+
+    @maxwellian.setter
+    def maxwellian(self, kind: str):
+        _check(lib().dvm_state_set_maxwellian(self.h, {"plain": 0, "conservative": 1}[kind]))
 
     def set_order(self, order: int, defect_period: int = 0):
         """order 2: linear reconstruction with the defect frozen over groups of defect_period sweeps
