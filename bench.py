@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--order", type=int, default=1, choices=[1, 2],
                    help="spatial order of the face values (2: linear reconstruction, defect correction)")
     p.add_argument("--defect-period", type=int, default=20, help="sweeps per second-order defect")
+    p.add_argument("--maxwellian", default="plain", choices=["plain", "conservative"],
+                   help="cell Maxwellian of the collision term (conservative: fitted to the discrete moments)")
     p.add_argument("--serve", type=int, default=128, help="requests of the served trace to replay (0: skip)")
     p.add_argument("--serve-max-iter", type=int, default=400, help="sweep cap per phase of a served request")
     return p.parse_args()
@@ -235,6 +237,8 @@ def run_gpu(args):
     st, _ = dvm.primal_solve(ctx, mesh, grid, Kn, Ma, tol=0.0, max_iter=args.sweeps, storage=args.storage)
     if args.order == 2:
         st.set_order(2, args.defect_period)
+    if args.maxwellian != "plain":
+        st.maxwellian = args.maxwellian
     ad, _ = dvm.adjoint_solve(ctx, st, tol=0.0, max_iter=args.sweeps)
 
     def step(events=None):
@@ -285,13 +289,14 @@ def run_gpu(args):
     prim_sweep_ms, adj_sweep_ms = prim_ms / n_sw, adj_ms / n_sw
     peak, peak_kind = hbm_peak()
     extra = 0.0 if args.order == 1 else 2 + 12.0 / args.defect_period
-    suffix = "" if args.order == 1 else " + reconstruction (per sweep)"
+    suffix = ("" if args.order == 1 else " + reconstruction") + ("" if args.maxwellian == "plain" else " + Maxwellian fit")
+    suffix += " (per sweep)" if suffix else ""
     k_prim = {"name": "k_primal_sweep" + suffix, "ms": prim_sweep_ms, "bytes": pairs * (4 + extra) * S,
               "GBps": pairs * (4 + extra) * S / (prim_sweep_ms * 1e6)}
     k_adj = {"name": "k_adjoint_sweep" + suffix, "ms": adj_sweep_ms, "bytes": pairs * (6 + extra) * S,
              "GBps": pairs * (6 + extra) * S / (adj_sweep_ms * 1e6)}
     dom = k_adj if adj_ms >= prim_ms else k_prim
-    alt = bool(args.mesh) or args.workload != WORKLOAD_INDEX or args.order != 1
+    alt = bool(args.mesh) or args.workload != WORKLOAD_INDEX or args.order != 1 or args.maxwellian != "plain"
     traffic = ncu_traffic(dom["name"], args.storage) if not alt else None
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": dom["GBps"] / peak, "traffic": traffic, "kernel": dom["name"],
@@ -302,7 +307,7 @@ def run_gpu(args):
                           for k in (k_prim, k_adj)}}
 
     # end-to-end through the public API with host buffers
-    e2e = run_e2e(args, ctx, wl, torch, dvm) if args.order == 1 else None
+    e2e = run_e2e(args, ctx, wl, torch, dvm) if (args.order == 1 and args.maxwellian == "plain") else None
 
     clocks = clk.summary()
     serving = run_serving(args, torch, dvm) if (args.serve > 0 and not alt) else None
@@ -313,6 +318,7 @@ def run_gpu(args):
             "config": {"workload": wl.name, "cells": wl.mesh.ncell, "velocities": wl.grid.nv,
                        "sweeps_per_phase": args.sweeps, "sensitivity_params": P,
                        "order": args.order, **({"defect_period": args.defect_period} if args.order == 2 else {}),
+                       "maxwellian": args.maxwellian,
                        "l2": "inputs larger than L2 (f = %.0f MB)" % (pairs * 2 * S / 1e6),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "phase_ms_per_step": {"primal": prim_ms / args.steps, "adjoint": adj_ms / args.steps,
@@ -320,7 +326,7 @@ def run_gpu(args):
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches)}
     if serving:
         line["serving"] = serving
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.order == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.order == 1 and args.maxwellian == "plain":
         line["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample(wl).items() if k != "seconds"}
         line["cpu_baseline"]["value_1_thread"] = cpu_oracle_sample(wl, rows=2, threads=1)["value"]
     if rank == 0:

@@ -379,8 +379,8 @@ cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
         default: { auto a = primal_args<__nv_bfloat16, float>(st, src); e = launch_primal_sweep(2, &a, st->maps[src], res, st->ctx->stream); break; }
     }
     if (e == cudaSuccess && st->maxwell) {
-        // the next sweep's Maxwellian: two Newton steps from the previous fit
-        e = launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[1 - src], st->fit, true, 2, nullptr,
+        // the next sweep's Maxwellian: one Newton step from the previous fit
+        e = launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[1 - src], st->fit, true, 1, nullptr,
                                st->ctx->stream);
         if (st->capturing) st->graph_so += 1;
         else st->ctx->launches += 1;

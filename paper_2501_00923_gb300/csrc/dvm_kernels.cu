@@ -1270,29 +1270,43 @@ __global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const
 // and 1 on g2 = T g1 / 2 (the conservative discrete velocity schemes the paper builds on).  Newton's
 // method, `iters` steps from the previous fit (warm) or from the primitive variables; with Kinv the
 // inverse Jacobian dp/dW = (dM/dp)^{-1} at the final p (row-major [q][m]) for the adjoint.  One warp
-// per cell: per-lane sums, a fixed butterfly, and every lane solves the same 4x4 system in FP64.
-__device__ __forceinline__ bool lu4_solve(double A[4][4], double b[4], double x[4]) {
+// per cell: per-lane sums and a fixed xor butterfly, which leaves bitwise-equal totals in every lane,
+// so every lane takes the same Newton step.
+template <class T>
+__device__ __forceinline__ bool lu4_solve(T A[4][4], T b[4], T x[4]) {
     int piv[4] = {0, 1, 2, 3};
+#pragma unroll
     for (int col = 0; col < 4; ++col) {
         int best = col;
         for (int r = col + 1; r < 4; ++r)
             if (fabs(A[piv[r]][col]) > fabs(A[piv[best]][col])) best = r;
         const int t = piv[col]; piv[col] = piv[best]; piv[best] = t;
-        if (A[piv[col]][col] == 0.0) return false;
+        if (A[piv[col]][col] == T(0)) return false;
         for (int r = col + 1; r < 4; ++r) {
-            const double m = A[piv[r]][col] / A[piv[col]][col];
+            const T m = A[piv[r]][col] / A[piv[col]][col];
             for (int c2 = col; c2 < 4; ++c2) A[piv[r]][c2] -= m * A[piv[col]][c2];
             b[piv[r]] -= m * b[piv[col]];
         }
     }
     for (int col = 3; col >= 0; --col) {
-        double acc = b[piv[col]];
+        T acc = b[piv[col]];
         for (int c2 = col + 1; c2 < 4; ++c2) acc -= A[piv[col]][c2] * x[c2];
         x[col] = acc / A[piv[col]][col];
     }
     return true;
 }
 
+template <class T> __device__ __forceinline__ T warp_sum_t(T v);
+template <> __device__ __forceinline__ double warp_sum_t<double>(double v) { return warp_sum(v); }
+template <> __device__ __forceinline__ float warp_sum_t<float>(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The residual M - W decides where Newton's method stops, so M is summed in two levels (partial sums
+// of 8 velocities) and reduced across the warp in FP64; the Jacobian only steers the steps and is summed and solved in the compute type
+// (FP64 for the inverse Jacobian that the adjoint uses).
 template <class TC>
 __global__ void __launch_bounds__(256) k_maxwell_fit(int ncell, int nvp, const typename Vec<TC>::v4* __restrict__ vt,
                                                      const double4* __restrict__ prim, double4* __restrict__ fit,
@@ -1303,55 +1317,72 @@ __global__ void __launch_bounds__(256) k_maxwell_fit(int ncell, int nvp, const t
     const double W[4] = {pr.x, pr.x * pr.y, pr.x * pr.z, pr.x * (0.5 * (pr.y * pr.y + pr.z * pr.z) + 1.5 * pr.w)};
     double4 p = warm ? fit[c] : pr;
     for (int it = 0; it <= iters; ++it) {
-        if (it == iters && !Kinv) break;
+        const bool inverse = it == iters;
+        if (inverse && !Kinv) break;
         const TC rho = (TC)p.x, u1 = (TC)p.y, u2 = (TC)p.z, T = (TC)p.w;
-        const TC n0 = rho / (TC(2.0 * kPi) * T), i2T = TC(0.5) / T, iT = TC(1) / T, ir = TC(1) / rho;
+        const TC i2T = TC(0.5) / T, iT = TC(1) / T, ir = TC(1) / rho;
         const TC hT = TC(0.5) * T;
-        // sums: M (4) and J (16): J[m][q] = sum w psi_m dg1/dp_q (m < 3), J[3][q] = sum w (h + T/2) dg1/dp_q
-        // + [q = 3] sum w g1 / 2; dg1/dp = g1 (1/rho, cx/T, cy/T, c^2/(2T^2) - 1/T)
-        TC s[20];
+        Gauss<TC> G;                               // g1 exactly as the sweeps evaluate it
+        G.setup(rho, u1, u2, T);
+        // M_m = sum w psi_m g1, psi = (1, vx, vy, h + T/2) (g2 = T g1 / 2); J[m][q] = sum w psi_m dg1/dp_q,
+        // dg1/dp = g1 (1/rho, cx/T, cy/T, c^2/(2T^2) - 1/T), plus sum w g1 / 2 in J[3][3] (dg2/dT).
+        // M: partial sums of 8 velocities added into a second accumulator (no FP64 inside the loop)
+        TC md[4] = {TC(0), TC(0), TC(0), TC(0)};
+        TC mb[4] = {TC(0), TC(0), TC(0), TC(0)};
+        TC sj[16];
 #pragma unroll
-        for (int i = 0; i < 20; ++i) s[i] = TC(0);
+        for (int i = 0; i < 16; ++i) sj[i] = TC(0);
+        int nb = 0;
+#pragma unroll 4
         for (int k = lane; k < nvp; k += 32) {
             const auto t = vt[k];
             const TC vx = t.x, vy = t.y, w = t.z, h = t.w;
             const TC cx = vx - u1, cy = vy - u2, c2 = cx * cx + cy * cy;
-            const TC wg = w * n0 * dexp<TC>(-c2 * i2T);
+            const TC wg = w * G.eval(fma(vy, -u2, fma(vx, -u1, h)));
             const TC d[4] = {ir, cx * iT, cy * iT, c2 * i2T * iT - iT};
             const TC psi[4] = {TC(1), vx, vy, h + hT};
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                s[m] += wg * psi[m];
+                const TC wp = wg * psi[m];
+                mb[m] += wp;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) s[4 + 4 * m + q] += wg * psi[m] * d[q];
+                for (int q = 0; q < 4; ++q) sj[4 * m + q] += wp * d[q];
             }
-            s[19] += TC(0.5) * wg;                 // d g2 / dT = g1 / 2 + (T/2) d g1 / dT
-        }
-        double M[4], A[4][4];
+            sj[15] += TC(0.5) * wg;
+            if (++nb == 8) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            M[m] = warp_sum((double)s[m]);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) A[m][q] = warp_sum((double)s[4 + 4 * m + q]);
+                for (int m = 0; m < 4; ++m) { md[m] += mb[m]; mb[m] = TC(0); }
+                nb = 0;
+            }
         }
-        if (it == iters) {                         // inverse Jacobian, column by column
-            double Inv[4][4];
-            for (int col = 0; col < 4; ++col) {
-                double B[4][4], e[4] = {0, 0, 0, 0}, x[4];
+        double M[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) M[m] = warp_sum((double)md[m] + (double)mb[m]);
+        if (inverse) {                             // dp/dW = J^{-1}, column by column, in FP64
+            double A[4][4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) A[m][q] = warp_sum((double)sj[4 * m + q]);
+            if (lane < 4) {                        // lane = column of the inverse
+                double B[4][4], e[4] = {0.0, 0.0, 0.0, 0.0}, x[4];
                 for (int m = 0; m < 4; ++m)
                     for (int q = 0; q < 4; ++q) B[m][q] = A[m][q];
-                e[col] = 1.0;
-                if (!lu4_solve(B, e, x)) x[0] = x[1] = x[2] = x[3] = 0.0;
-                for (int q = 0; q < 4; ++q) Inv[q][col] = x[q];
+                e[lane] = 1.0;
+                if (!lu4_solve<double>(B, e, x)) x[0] = x[1] = x[2] = x[3] = 0.0;
+                for (int q = 0; q < 4; ++q) Kinv[16 * (size_t)c + 4 * q + lane] = x[q];
             }
-            if (lane == 0)
-                for (int q = 0; q < 4; ++q)
-                    for (int m = 0; m < 4; ++m) Kinv[16 * (size_t)c + 4 * q + m] = Inv[q][m];
             break;
         }
-        double r[4] = {M[0] - W[0], M[1] - W[1], M[2] - W[2], M[3] - W[3]}, x[4];
-        if (!lu4_solve(A, r, x)) break;
-        p.x -= x[0]; p.y -= x[1]; p.z -= x[2]; p.w -= x[3];
+        TC A[4][4], r[4], x[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            r[m] = (TC)(M[m] - W[m]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) A[m][q] = warp_sum_t<TC>(sj[4 * m + q]);
+        }
+        if (!lu4_solve<TC>(A, r, x)) break;
+        p.x -= (double)x[0]; p.y -= (double)x[1]; p.z -= (double)x[2]; p.w -= (double)x[3];
     }
     if (lane == 0) fit[c] = p;
 }
