@@ -163,11 +163,15 @@ int dvm_state_moments(const dvm_state* st, double* prim_host);
  * gradient of Eq. (gaussgrad) (face averages inside, the first-order value on wall and far-field faces;
  * x_c the mean of the cell's corners, x_e the face midpoint).  Sweeps of order 2 are defect correction:
  * the added flux dR is taken from the sweep's input at the first sweep of every group of
- * defect_period sweeps (0 -> 4) and frozen for the rest of the group, while each sweep keeps the
+ * defect_period sweeps (0 -> 20) and frozen for the rest of the group, while each sweep keeps the
  * first-order point-implicit form,
  *   f_new = [ V g/tau + sum_{a<=0} (-a) F_up - dR ] / [ V/tau + sum_{a>0} a ],
  * so a converged solve satisfies R1(f) + dR(f) = 0 whatever the period.  (A period of 1 can diverge:
- * with the unlimited reconstruction the point-implicit map is unstable in weakly collisional modes.)
+ * with the unlimited reconstruction the point-implicit map is unstable in weakly collisional modes,
+ * and on fine meshes the group must be long enough for its first-order sweeps to contract: 4 diverges
+ * and 8 stalls on a 256x128 mesh at Kn 0.1, 16 and more converge.  Start second-order solves from a
+ * converged first-order state: from the free stream the unlimited reconstruction can drive f
+ * negative on coarse meshes.)
  * Adjoint sweeps take the exact transpose of dR, (dR/df)^T (w phi) / w, frozen the same way.  Boundary
  * faces, the drag and the wall density stay first order.  The first call with order 2 allocates three
  * buffers of the size of f for the state and one for each adjoint swept later (counted against the HBM
@@ -183,7 +187,7 @@ int dvm_state_get_order(const dvm_state* st, int* order);
  * discrete moments on a truncated velocity grid differ slightly from the cell's.
  * DVM_MAXWELL_CONSERVATIVE: g at the parameters p = (rho, u, T) whose discrete moments equal the
  * cell's exactly, sum_k w_k Psi_k g_k(p) = W (Newton's method per cell: from the primitive variables on
- * this call and after dvm_state_set, two warm steps after every sweep), so the collision term conserves
+ * this call and after dvm_state_set, one warm step after every sweep), so the collision term conserves
  * mass, momentum and energy on the grid itself.  The relaxation time stays that of the primitive
  * variables.  The adjoint takes the fit's implicit derivative dp/dW = (dM/dp)^{-1}, and both
  * sensitivity modes use the fitted g.  Allocates a small per-cell buffer for the state and one for
