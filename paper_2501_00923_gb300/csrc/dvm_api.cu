@@ -177,23 +177,72 @@ int fail_cuda(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return fail_cuda(e_, #x); \
     } while (0)
 
+// Device memory of states, adjoints, meshes and grids: stream-ordered allocations on the context's
+// stream from one pool per device that keeps freed blocks (release threshold at its maximum), so a
+// state created after another is destroyed reuses its memory without cudaMalloc or cudaFree, and a
+// free never waits for the device.  Every block is freed on the stream it was allocated on, after
+// the work queued there that uses it.  dvm_context_destroy trims the pool.
+std::mutex g_pool_mu;
+std::unordered_map<int, cudaMemPool_t> g_pools;
+std::unordered_map<void*, cudaStream_t> g_block_stream;
+
+cudaError_t device_pool(int device, cudaMemPool_t* out) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(device);
+    if (it != g_pools.end()) { *out = it->second; return cudaSuccess; }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) { cudaMemPoolDestroy(pool); return e; }
+    g_pools[device] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
 template <class T>
 int dalloc(dvm_context* ctx, T** p, size_t count, size_t* acc = nullptr) {
     size_t b = count * sizeof(T);
     if (b == 0) b = sizeof(T);
-    cudaError_t e = cudaMalloc((void**)p, b);
+    cudaMemPool_t pool;
+    cudaError_t e = device_pool(ctx->device, &pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)p, b, pool, ctx->stream);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
-        return fail(DVM_ERR_OOM, "cudaMalloc failed: out of device memory");
+        return fail(DVM_ERR_OOM, "device allocation failed: out of device memory");
     }
-    if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    if (e != cudaSuccess) return fail_cuda(e, "device allocation");
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        g_block_stream[(void*)*p] = ctx->stream;
+    }
     if (acc) *acc += b;
-    (void)ctx;
     return DVM_OK;
 }
 
 void dfree(void* p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    cudaStream_t s = nullptr;
+    bool pooled = false;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto it = g_block_stream.find(p);
+        if (it != g_block_stream.end()) { s = it->second; pooled = true; g_block_stream.erase(it); }
+    }
+    if (pooled) cudaFreeAsync(p, s);
+    else cudaFree(p);
+}
+
+// Return the pool's unused blocks to the device (after the context's work has finished).
+void trim_pool(int device) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(device);
+    if (it != g_pools.end()) cudaMemPoolTrimTo(it->second, 0);
 }
 
 // NVTX range over one library call (solve phases, sensitivity, batch tick) for timeline tools;
@@ -787,9 +836,11 @@ void dvm_context_destroy(dvm_context* c) {
     if (!live_take(c, kCtx)) return;
     DeviceGuard dg(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->derr) cudaFree(c->derr);
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    trim_pool(c->device);
     delete c;
 }
 
@@ -844,12 +895,13 @@ int dvm_mesh_create(dvm_context* ctx, int ni, int nj, const double* X, dvm_mesh*
         return rc;
     }
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpy(m->d.nb, nb.data(), nc * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d.Sd, S.data(), S.size() * sizeof(double2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d.Vd, V.data(), nc * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d.Sf, Sf.data(), Sf.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d.Vf, Vf.data(), nc * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d.nodes, X, (size_t)(nj + 1) * ni * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d.nb, nb.data(), nc * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d.Sd, S.data(), S.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d.Vd, V.data(), nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d.Sf, Sf.data(), Sf.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d.Vf, Vf.data(), nc * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d.nodes, X, (size_t)(nj + 1) * ni * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);     // the host arrays are local
     if (e != cudaSuccess) { live_add(m, kMesh, ctx); dvm_mesh_destroy(m); return fail_cuda(e, "mesh upload"); }
     live_add(m, kMesh, ctx);
     *out = m;
@@ -897,10 +949,11 @@ int dvm_vgrid_create(dvm_context* ctx, int nv, const double* vx, const double* v
         dvm_vgrid_destroy(g);
         return rc;
     }
-    cudaError_t e = cudaMemcpy(g->d.vd, vd.data(), nvp * sizeof(double4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d.vf, vf.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d.vpa, vpa.data(), npair * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d.vpb, vpb.data(), npair * sizeof(float4), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(g->d.vd, vd.data(), nvp * sizeof(double4), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d.vf, vf.data(), nvp * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d.vpa, vpa.data(), npair * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d.vpb, vpb.data(), npair * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);     // the host arrays are local
     if (e != cudaSuccess) { dvm_vgrid_destroy(g); return fail_cuda(e, "grid upload"); }
     *out = g;
     return DVM_OK;
