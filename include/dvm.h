@@ -99,6 +99,12 @@ typedef struct {
                                while mixing, the solve finishes with plain sweeps (with a stall window of
                                their own), so FP32/BF16 solves end on the plain sweeps' rounding floor */
     int accel_period;       /* sweeps between mixings (>= 1; with accel_depth > 0) */
+    int accel_space;        /* what is mixed: 0 = the whole state (f, or phi for the adjoint); 1 = the cell moments
+                               W = (rho, rho u, rho E) of the primal, one FP64 vector of 4 values per cell, the
+                               mixed moments imposed on f by f += g(W_mixed) - g(W) (the non-equilibrium part of
+                               f is kept; cells whose mixed moments lose positive density or temperature are left
+                               unshifted).  The shift vanishes at a fixed point, so the solution is unchanged.
+                               Adjoint solves ignore 1 and mix phi */
 } dvm_solve_opts;
 
 typedef struct {

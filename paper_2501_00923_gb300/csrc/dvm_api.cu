@@ -92,6 +92,8 @@ struct dvm_state {
     bool capturing = false;
     int maxwell = 0;            // 1: conservative discrete Maxwellian (fitted to the cell's discrete moments)
     double4* fit = nullptr;     // its parameters for the current f
+    AAState* aaW = nullptr;     // moment-space mixing: history over the cell moments
+    double* Wbuf = nullptr;     // [ncell][4] FP64 moments
 };
 
 struct dvm_adjoint {
@@ -666,6 +668,7 @@ int check_solve_opts(const dvm_solve_opts* o) {
     if (o->max_iter < 0 || !(o->tol >= 0.0)) return fail(DVM_ERR_INVALID_ARG, "bad solve options");
     if (o->accel_depth < 0 || o->accel_depth > aa_max_depth() || (o->accel_depth > 0 && o->accel_period < 1))
         return fail(DVM_ERR_INVALID_ARG, "accel_depth must be in [0, 8] and accel_period >= 1");
+    if (o->accel_space != 0 && o->accel_space != 1) return fail(DVM_ERR_INVALID_ARG, "accel_space must be 0 or 1");
     return DVM_OK;
 }
 
@@ -980,6 +983,8 @@ void dvm_state_destroy(dvm_state* st) {
     dfree(st->fit);
     dfree(st->fl.fdd); dfree(st->fl.fdf); dfree(st->fl.gwd); dfree(st->fl.gwf); dfree(st->fl.wallD); dfree(st->fl.wallM);
     aa_free(st->ctx, st->aa);
+    aa_free(st->ctx, st->aaW);
+    dfree(st->Wbuf);
     st->ctx->bytes -= st->bytes;
     delete st;
 }
@@ -1267,10 +1272,24 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     const bool accel = opts->accel_depth > 0;
     const int K = accel ? opts->accel_period : ctx->graph_iters;
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
-    if (accel) {
-        const size_t n = (size_t)st->mesh->d.ncell * st->grid->d.nvp * 2;
+    const bool wspace = accel && opts->accel_space == 1;
+    const int nc = st->mesh->d.ncell;
+    if (accel && !wspace) {
+        const size_t n = (size_t)nc * st->grid->d.nvp * 2;
         if ((rc = aa_ensure(ctx, st->aa, st->storage, n, opts->accel_depth))) return rc;
         if ((rc = aa_begin(ctx, st->aa, st->f[st->cur]))) return rc;
+    }
+    if (wspace) {               // the cell moments as one FP64 vector
+        if ((rc = aa_ensure(ctx, st->aaW, DVM_STORE_FP64, 4 * (size_t)nc, opts->accel_depth))) return rc;
+        if (!st->Wbuf) {
+            size_t acc = 0;
+            if ((rc = dalloc(ctx, &st->Wbuf, 4 * (size_t)nc, &acc))) return rc;
+            st->bytes += acc;
+            ctx->bytes += acc;
+        }
+        CK(launch_prim_to_W(nc, st->prim[st->cur], st->Wbuf, ctx->stream));
+        ctx->launches += 1;
+        if ((rc = aa_begin(ctx, st->aaW, st->Wbuf))) return rc;
     }
     bool mixing = accel;
     int restarts = 0;
@@ -1303,7 +1322,35 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
             best = r;
             best_it = it;
         }
-        if (mixing && k == K && it < opts->max_iter) {
+        if (mixing && k == K && it < opts->max_iter && wspace) {
+            // moments after the block are G(x); mix them, impose the mixed moments on f by a
+            // Maxwellian shift, and restart the next block from the moments f then has
+            bool mixed = false;
+            CK(launch_prim_to_W(nc, st->prim[st->cur], st->Wbuf, ctx->stream));
+            ctx->launches += 1;
+            if (aa_restart_if_growing(st->aaW, r)) {
+                if (++restarts >= 2) mixing = false;
+                else if ((rc = aa_begin(ctx, st->aaW, st->Wbuf))) return rc;
+            } else if ((rc = aa_step(ctx, st->aaW, st->Wbuf, false, &mixed))) {
+                return rc;
+            }
+            if (mixed) {
+                CK(launch_moment_shift(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur],
+                                       st->Wbuf, ctx->stream));
+                CK(launch_moments(st->storage, st->f[st->cur], st->mesh->d, st->grid->d, st->prim[st->cur],
+                                  st->Fw[st->cur], ctx->stream));
+                CK(launch_prim_to_W(nc, st->prim[st->cur], st->Wbuf, ctx->stream));
+                CK(launch_aa_load(DVM_STORE_FP64, 4 * (size_t)nc, st->Wbuf, st->aaW->X, ctx->stream));
+                ctx->launches += 4;
+                if (st->maxwell) {
+                    CK(launch_maxwell_fit(st->storage, st->mesh->d, st->grid->d, st->prim[st->cur], st->fit, true, 3,
+                                          nullptr, ctx->stream));
+                    ctx->launches += 1;
+                }
+                st->so_phase = 0;
+                st->version += 1;
+            }
+        } else if (mixing && k == K && it < opts->max_iter) {
             bool mixed = false;
             if (aa_restart_if_growing(st->aa, r)) {   // the history misleads: start it again here,
                 if (++restarts >= 2) mixing = false;    // and on the second time finish with plain sweeps

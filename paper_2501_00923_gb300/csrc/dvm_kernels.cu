@@ -1387,6 +1387,45 @@ __global__ void __launch_bounds__(256) k_maxwell_fit(int ncell, int nvp, const t
     if (lane == 0) fit[c] = p;
 }
 
+// ================================================================== moment-space mixing
+// Anderson mixing of the cell moments: W = (rho, rho u1, rho u2, rho E) of every cell as one FP64
+// vector, and the shift that imposes mixed moments on f, f += g(W_mix) - g(W) per cell and velocity
+// (both components), which keeps the non-equilibrium part of f and vanishes at a fixed point.  A cell
+// whose mixed moments have no positive density and temperature is left as it is.
+__global__ void k_prim_to_W(int ncell, const double4* __restrict__ prim, double* __restrict__ W) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double4 p = prim[c];
+    W[4 * c] = p.x;
+    W[4 * c + 1] = p.x * p.y;
+    W[4 * c + 2] = p.x * p.z;
+    W[4 * c + 3] = p.x * (0.5 * (p.y * p.y + p.z * p.z) + 1.5 * p.w);
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_moment_shift(TS* __restrict__ f, int ncell, int nvp, const double4* __restrict__ vd,
+                                                      const double4* __restrict__ prim, const double* __restrict__ W) {
+    using TC = typename Pack<TS>::TC;
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 p = prim[c];
+    const double r1 = W[4 * c], u1 = W[4 * c + 1] / r1, u2 = W[4 * c + 2] / r1;
+    const double T1 = (2.0 / 3.0) * (W[4 * c + 3] / r1 - 0.5 * (u1 * u1 + u2 * u2));
+    if (!(r1 > 0.0) || !(T1 > 0.0)) return;
+    Gauss<TC> Ga, Gb;
+    Ga.setup((TC)r1, (TC)u1, (TC)u2, (TC)T1);
+    Gb.setup((TC)p.x, (TC)p.y, (TC)p.z, (TC)p.w);
+    const TC hA = (TC)(0.5 * T1), hB = (TC)(0.5 * p.w);
+    for (int k = lane; k < nvp; k += 32) {
+        const double4 t = vd[k];
+        const TC ga = Ga.eval((TC)(t.w - t.x * u1 - t.y * u2));
+        const TC gb = Gb.eval((TC)(t.w - t.x * p.y - t.y * p.z));
+        const size_t o = fpos<TS>(c, nvp, k);
+        f[o] = fromdbl<TS>(todbl(f[o]) + (double)(ga - gb));
+        f[o + kComp<TS>] = fromdbl<TS>(todbl(f[o + kComp<TS>]) + (double)(hA * ga - hB * gb));
+    }
+}
+
 // ================================================================== second order (reconstruction)
 // Linear reconstruction of the upwind cell on interior faces, F_e = f_up + grad f_up . (x_e - x_up),
 // with the unlimited Gauss gradient of Eq. (gaussgrad), grad f_c = (1/V_c) sum_e fbar_e A_e n_e: fbar_e
@@ -2299,6 +2338,20 @@ cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cud
     if (storage == 0) second_order_launch<double, double>(args, adjoint, s);
     else if (storage == 1) second_order_launch<float, float>(args, adjoint, s);
     else second_order_launch<__nv_bfloat16, float>(args, adjoint, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prim_to_W(int ncell, const double4* prim, double* W, cudaStream_t s) {
+    k_prim_to_W<<<cdiv(ncell, 256), 256, 0, s>>>(ncell, prim, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moment_shift(int storage, void* f, const DevMesh& m, const DevGrid& g, const double4* prim,
+                                const double* W, cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0) k_moment_shift<double><<<nb, 256, 0, s>>>((double*)f, m.ncell, g.nvp, g.vd, prim, W);
+    else if (storage == 1) k_moment_shift<float><<<nb, 256, 0, s>>>((float*)f, m.ncell, g.nvp, g.vd, prim, W);
+    else k_moment_shift<__nv_bfloat16><<<nb, 256, 0, s>>>((__nv_bfloat16*)f, m.ncell, g.nvp, g.vd, prim, W);
     return cudaGetLastError();
 }
 

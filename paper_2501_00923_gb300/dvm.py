@@ -37,15 +37,17 @@ class Flow(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("stall_window", C.c_int), ("accel_depth", C.c_int),
-                ("accel_period", C.c_int)]
+                ("accel_period", C.c_int), ("accel_space", C.c_int)]
 
 
 def _accel(accel):
-    """accel: None (plain sweeps) or (depth m, period K) of the Anderson mixing."""
+    """accel: None (plain sweeps), (depth m, period K) of the Anderson mixing of the state, or
+    (m, K, "moments") to mix the primal's cell moments instead."""
     if accel is None:
-        return 0, 0
-    m, k = accel
-    return int(m), int(k)
+        return 0, 0, 0
+    m, k = accel[0], accel[1]
+    space = accel[2] if len(accel) > 2 else "state"
+    return int(m), int(k), {"state": 0, "moments": 1}[space]
 
 
 class PrimalResult(C.Structure):

@@ -51,6 +51,22 @@ def test_fp64_mixing_converges_to_the_plain_solution_in_fewer_sweeps(ctx, case):
     assert ip1 < ip0 / 2 and ia1 < ia0 / 2, (ip0, ip1, ia0, ia1)
 
 
+def test_moment_space_mixing_reaches_the_plain_solution(ctx, case):
+    """Mixing only the cell moments (accel_space = 1, the mixed moments imposed on f by a Maxwellian
+    shift) ends at the plain sweeps' FP64 solution, in fewer sweeps at Kn = 0.01 (measured: 3520
+    against 14240 to 1e-10 on this case; mixing the whole state: 2350)."""
+    mesh, grid, m, g = case
+    st0, r0 = dvm.primal_solve(ctx, m, g, 0.01, 0.6, tol=1e-12, max_iter=400000, storage="fp64")
+    st1, r1 = dvm.primal_solve(ctx, m, g, 0.01, 0.6, tol=1e-12, max_iter=400000, storage="fp64",
+                               accel=(5, 10, "moments"))
+    assert r0.status == r1.status == dvm.DVM_OK
+    assert abs(r1.J - r0.J) < 1e-9 * abs(r0.J)
+    assert np.abs(st1.get() - st0.get()).max() < 1e-8 * np.abs(st0.get()).max()
+    assert r1.iters < r0.iters / 2, (r0.iters, r1.iters)
+    st0.close()
+    st1.close()
+
+
 def test_fp32_mixing_ends_where_plain_fp32_sweeps_end(ctx, case):
     """FP32 storage stalls at its rounding floor, and at Kn = 0.01 the floor is amplified by the slow
     contraction of the sweeps (1 / (1 - rho) ~ 1e3): on this 32x12 case the plain FP32 drag itself is
