@@ -32,9 +32,13 @@ class DragProblem:
     stall_window: int = 0
     mode: str = "full"
     mesh_fn: object = None          # alpha -> OMesh; default: the Hicks-Henne bump section
+    order: int = 1                  # 2: second-order reconstruction (mode "paper" only)
+    maxwellian: str = "plain"       # or "conservative"
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
+        if self.order == 2 and self.mode == "full":
+            raise ValueError("the full discrete gradient is first-order only: use mode='paper' with order 2")
         self._grid = dvm.VGrid(self.ctx, self.grid.vx, self.grid.vy, self.grid.w)
         self._warm_f = None
         self._warm_phi = None
@@ -49,8 +53,15 @@ class DragProblem:
         m = dvm.Mesh(self.ctx, mesh.nodes)
         st = dvm.State(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa,
                        storage=self.storage)
+        if self.maxwellian != "plain":
+            st.maxwellian = self.maxwellian
         if self._warm_f is not None:
             st.set(self._warm_f)
+        elif self.order == 2:               # second order starts from the converged first-order state
+            dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa,
+                             tol=self.tol, max_iter=self.max_iter, storage=self.storage, state=st,
+                             stall_window=self.stall_window)
+        st.order = self.order
         st, res = dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw,
                                    self.flow.aoa, tol=self.tol, max_iter=self.max_iter, storage=self.storage,
                                    state=st, stall_window=self.stall_window)

@@ -298,13 +298,16 @@ def drive(loop: DesignLoop, evaluate):
 
 
 def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 1e-6,
-        adjoint_tol: float = 1e-6, max_sweeps: int = 200000, stall_window: int = 0):
+        adjoint_tol: float = 1e-6, max_sweeps: int = 200000, stall_window: int = 0, order: int = 1,
+        maxwellian: str = "plain", mode: str | None = None):
     """Drive one loop with blocking GPU solves (autograd.DragProblem keeps f and phi of the last
-    design as warm starts for the next)."""
+    design as warm starts for the next).  order 2 (second-order reconstruction) takes the paper's
+    boundary sensitivity (mode "paper"); order 1 the full discrete gradient unless mode says otherwise."""
     from .autograd import DragProblem
+    mode = mode or ("paper" if order == 2 else "full")
     prob = DragProblem(ctx, loop.ni, loop.nj, loop.grid, loop.flow, storage=storage, tol=tol,
                        adjoint_tol=adjoint_tol, max_iter=max_sweeps, stall_window=stall_window,
-                       mesh_fn=loop.mesh)
+                       mesh_fn=loop.mesh, order=order, maxwellian=maxwellian, mode=mode)
     _start(ctx, loop)
 
     def evaluate(a):
@@ -404,7 +407,12 @@ def main(argv=None):
     ap.add_argument("--concurrent", action="store_true", help="all Kn loops through one served batch")
     ap.add_argument("--shape", default="bumps", choices=["bumps", "cst"],
                     help="24 Hicks-Henne bumps, or the 18 CST variables (N_B = 6) of Sec. 3.3")
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
+                    help="2: second-order reconstruction with the paper's boundary sensitivity")
+    ap.add_argument("--maxwellian", default="plain", choices=["plain", "conservative"])
     args = ap.parse_args(argv)
+    if args.concurrent and (args.order != 1 or args.maxwellian != "plain"):
+        ap.error("served batches are first order with the plain Maxwellian")
     from . import build
     build.build()
     ni, nj = (int(x) for x in args.mesh.lower().split("x"))
@@ -422,7 +430,8 @@ def main(argv=None):
         spans = []
         for loop in loops:
             t = time.perf_counter()
-            run(ctx, loop, storage=args.storage, tol=args.tol, adjoint_tol=args.tol, stall_window=3000)
+            run(ctx, loop, storage=args.storage, tol=args.tol, adjoint_tol=args.tol, stall_window=3000,
+                order=args.order, maxwellian=args.maxwellian)
             spans.append(time.perf_counter() - t)
     for loop, span in zip(loops, spans):
         acc, best = [], None
@@ -431,6 +440,7 @@ def main(argv=None):
                 best = e.Cd
                 acc.append({"Cd": e.Cd, "Q_over_Vmin": e.Q / loop.v_min})
         print(json.dumps({"Kn": loop.flow.Kn, "Ma": loop.flow.Ma, "mesh": args.mesh, "nv": args.nv, "shape": args.shape,
+                          "order": args.order, "maxwellian": args.maxwellian,
                           "storage": args.storage, "stopped": loop.stopped, "iterations": loop.opt.iterations,
                           "evaluations": loop.opt.evaluations, "Cd0": loop.history[0].Cd, "Cd_best": best,
                           "seconds": span, "concurrent": args.concurrent, "accepted": acc}))
