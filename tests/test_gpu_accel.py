@@ -85,6 +85,18 @@ def test_fp32_mixing_ends_where_plain_fp32_sweeps_end(ctx, case):
     assert np.abs(g1 - g64).max() < 1e-3 * np.abs(g64).max()
 
 
+def test_fp32_moment_mixing_ends_where_plain_fp32_sweeps_end(ctx, case):
+    """In FP32 the moment-space mixing brings no speed-up (measured), but it must end at the plain
+    FP32 solution within the FP32 floor."""
+    mesh, grid, m, g = case
+    J0, *_, g0 = _solve(ctx, case, "fp32", None, 1e-9, stall=3000)
+    st, r = dvm.primal_solve(ctx, m, g, 0.01, 0.6, tol=1e-9, max_iter=400000, storage="fp32",
+                             accel=(5, 10, "moments"), stall_window=3000)
+    assert r.status in (dvm.DVM_OK, dvm.DVM_ERR_STAGNATED)
+    assert abs(r.J - J0) < 1e-4 * abs(J0)
+    st.close()
+
+
 def test_bf16_mixing_ends_where_plain_bf16_sweeps_end(ctx, case):
     """BF16 storage stalls at its rounding floor; with or without mixing it ends at the same
     solution up to that floor."""

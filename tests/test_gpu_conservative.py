@@ -32,7 +32,7 @@ def _case(ctx, ni, nj, nvx, nvy, Kn, Ma, storage, seed, bumps=True):
     return rng, mesh, grid, m, g, st, pr
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("bf16", 2e-2)])
 @pytest.mark.parametrize("shape", [(24, 6, 11, 9), (16, 6, 33, 31), (3, 1, 8, 8)])
 def test_one_conservative_primal_sweep_matches_oracle(ctx, storage, tol, shape):
     """A ragged velocity count, a count that refills the pipeline stages, and the one-layer mesh;
@@ -52,7 +52,7 @@ def test_one_conservative_primal_sweep_matches_oracle(ctx, storage, tol, shape):
         assert np.abs(plain - ref).max() > 1e3 * tol * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-11), ("fp32", 1e-5), ("bf16", 2e-2)])
 def test_one_conservative_adjoint_sweep_matches_oracle(ctx, storage, tol):
     rng, mesh, grid, m, g, st, pr = _case(ctx, 36, 10, 12, 10, 0.5, 0.7, storage, 7)
     st.set(W.random_state(pr.ncell, grid, rng))

@@ -75,7 +75,7 @@ def test_one_second_order_primal_sweep_matches_oracle(ctx, storage, tol, shape):
     assert np.abs(prim[:, 0] - W_ref[:, 0]).max() < max(tol, 1e-13) * 10
 
 
-@pytest.mark.parametrize("storage,tol", [("fp64", 1e-11), ("fp32", 5e-6)])
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-11), ("fp32", 5e-6), ("bf16", 2e-2)])
 @pytest.mark.parametrize("shape", [(8, 3, 4, 4), (5, 2, 6, 5), (3, 1, 4, 4)])
 def test_one_second_order_adjoint_sweep_matches_oracle(ctx, storage, tol, shape):
     """Element by element against the oracle's assembled transpose (small cases: the oracle builds
@@ -95,7 +95,8 @@ def test_one_second_order_adjoint_sweep_matches_oracle(ctx, storage, tol, shape)
     out = ad.get()
     assert np.abs(out - ref).max() < tol * np.abs(ref).max()
     ref1, _ = pr.adjoint_jacobi(f_in, phi_in)
-    assert np.abs(ref1 - ref).max() > 5 * tol * np.abs(ref).max()
+    if storage != "bf16":
+        assert np.abs(ref1 - ref).max() > 5 * tol * np.abs(ref).max()
     ad.close()
 
 
