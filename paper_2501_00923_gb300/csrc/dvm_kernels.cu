@@ -1948,58 +1948,72 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
     const double2 s1d = S[4 * c + 1], s2d = S[4 * c + 2], s3d = S[4 * c + 3];
     const TC s1x = (TC)s1d.x, s1y = (TC)s1d.y, s2x = (TC)s2d.x, s2y = (TC)s2d.y, s3x = (TC)s3d.x, s3y = (TC)s3d.y;
     const double4 pr = prim[c], pm = maxw[c];          // moments (tau); Maxwellian parameters (g)
-    const TC u1 = (TC)pm.y, u2 = (TC)pm.z, n0 = (TC)(pm.x / (2.0 * kPi * pm.w)), inv2T = (TC)(0.5 / pm.w);
+    const TC u1 = (TC)pm.y, u2 = (TC)pm.z;
     const TC halfT = (TC)(0.5 * pm.w), halfTw = (TC)halfTw_d, dirx = (TC)mj.dx, diry = (TC)mj.dy, hcoef = (TC)mj.h;
     const bool wall = n.w == kWall;
     const TC cw = wall ? (TC)(Fw[c] / wallD[c]) : TC(0);
     const TC gbs = wall ? (TC)(1.0 / wallD[c]) : TC(0);
     Acc<TC> gnx, gny, gex, gey, gwx, gwy, H, vfx, vfy, vs;
-    for (int k = lane; k < nvp; k += 32) {
-        const auto t = vt[k];
-        const TC vx = t.x, vy = t.y, w = t.z;
-        constexpr int C2 = kComp<TS>;
-        const size_t ic = fpos<TS>(c, nvp, k);
-        const TC fc1 = (TC)todbl(f[ic]), fc2 = (TC)todbl(f[ic + C2]);
-        const TC pc1 = (TC)todbl(phi[ic]), pc2 = (TC)todbl(phi[ic + C2]);
-        {   // north face
-            const TC a = s1x * vx + s1y * vy;
-            TC F1, F2, q1 = TC(0), q2 = TC(0);
-            if (n.y >= 0) {
-                const size_t ir = fpos<TS>(n.y, nvp, k);
-                q1 = (TC)todbl(phi[ir]); q2 = (TC)todbl(phi[ir + C2]);
-                if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + C2]); }
-            } else if (a > TC(0)) { F1 = fc1; F2 = fc2; }
-            else { F1 = fd[k].x; F2 = fd[k].y; }
-            const TC d = w * ((pc1 - q1) * F1 + (pc2 - q2) * F2);
-            gnx.add(d * vx); gny.add(d * vy);
-        }
-        {   // east face (always interior)
-            const TC a = s2x * vx + s2y * vy;
-            const size_t ir = fpos<TS>(n.z, nvp, k);
-            const TC q1 = (TC)todbl(phi[ir]), q2 = (TC)todbl(phi[ir + C2]);
-            TC F1, F2;
-            if (a > TC(0)) { F1 = fc1; F2 = fc2; } else { F1 = (TC)todbl(f[ir]); F2 = (TC)todbl(f[ir + C2]); }
-            const TC d = w * ((pc1 - q1) * F1 + (pc2 - q2) * F2);
-            gex.add(d * vx); gey.add(d * vy);
-        }
-        if (wall) {
-            const TC a = s3x * vx + s3y * vy;
-            const TC m = dirx * vx + diry * vy + hcoef * t.w;
-            TC F1, F2;
-            if (a > TC(0)) { F1 = fc1; F2 = fc2; }
-            else {
-                const TC gb1 = gw[k] * gbs;
-                F1 = cw * gw[k]; F2 = cw * halfTw * gw[k];
-                H.add(w * a * gb1 * (m + pc1 + halfTw * pc2));
+    // 16-byte chunks of f and phi of the cell and of its north and east neighbours (coalesced, as in
+    // the sweeps); the Maxwellian of the volume term evaluated as in the sweeps
+    using PK = Pack<TS>;
+    constexpr int KV = PK::KV;
+    Gauss<TC> G;
+    G.setup((TC)pm.x, u1, u2, (TC)pm.w);
+    const size_t nq = (size_t)nvp / KV;
+    const uint4* fq = reinterpret_cast<const uint4*>(f);
+    const uint4* pq = reinterpret_cast<const uint4*>(phi);
+    const size_t north = n.y >= 0 ? (size_t)n.y : (size_t)c;    // far field: own chunk, not used
+    const size_t east = (size_t)n.z;
+    for (size_t q = lane; q < nq; q += 32) {
+        TC fc1[KV], fc2[KV], pc1[KV], pc2[KV], fn1[KV], fn2[KV], pn1[KV], pn2[KV], fe1[KV], fe2[KV], pe1[KV], pe2[KV];
+        PK::unpack(ldg16(fq + (size_t)c * nq + q), fc1, fc2);
+        PK::unpack(ldg16(pq + (size_t)c * nq + q), pc1, pc2);
+        PK::unpack(ldg16(fq + north * nq + q), fn1, fn2);
+        PK::unpack(ldg16(pq + north * nq + q), pn1, pn2);
+        PK::unpack(ldg16(fq + east * nq + q), fe1, fe2);
+        PK::unpack(ldg16(pq + east * nq + q), pe1, pe2);
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const int k = (int)q * KV + kk;
+            const auto t = vt[k];
+            const TC vx = t.x, vy = t.y, w = t.z;
+            {   // north face
+                const TC a = s1x * vx + s1y * vy;
+                TC F1, F2, q1 = TC(0), q2 = TC(0);
+                if (n.y >= 0) {
+                    q1 = pn1[kk]; q2 = pn2[kk];
+                    if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; } else { F1 = fn1[kk]; F2 = fn2[kk]; }
+                } else if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; }
+                else { F1 = fd[k].x; F2 = fd[k].y; }
+                const TC d = w * ((pc1[kk] - q1) * F1 + (pc2[kk] - q2) * F2);
+                gnx.add(d * vx); gny.add(d * vy);
             }
-            const TC d = w * (pc1 * F1 + pc2 * F2 + m * F1);
-            gwx.add(d * vx); gwy.add(d * vy);
-            vfx.add(w * vx * F1); vfy.add(w * vy * F1);
-        }
-        {   // volume term
-            const TC dx = vx - u1, dy = vy - u2;
-            const TC g1 = n0 * dexp<TC>(-(dx * dx + dy * dy) * inv2T);
-            vs.add(w * (pc1 * (fc1 - g1) + pc2 * (fc2 - halfT * g1)));
+            {   // east face (always interior)
+                const TC a = s2x * vx + s2y * vy;
+                TC F1, F2;
+                if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; } else { F1 = fe1[kk]; F2 = fe2[kk]; }
+                const TC d = w * ((pc1[kk] - pe1[kk]) * F1 + (pc2[kk] - pe2[kk]) * F2);
+                gex.add(d * vx); gey.add(d * vy);
+            }
+            if (wall) {
+                const TC a = s3x * vx + s3y * vy;
+                const TC m = dirx * vx + diry * vy + hcoef * t.w;
+                TC F1, F2;
+                if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; }
+                else {
+                    const TC gb1 = gw[k] * gbs;
+                    F1 = cw * gw[k]; F2 = cw * halfTw * gw[k];
+                    H.add(w * a * gb1 * (m + pc1[kk] + halfTw * pc2[kk]));
+                }
+                const TC d = w * (pc1[kk] * F1 + pc2[kk] * F2 + m * F1);
+                gwx.add(d * vx); gwy.add(d * vy);
+                vfx.add(w * vx * F1); vfy.add(w * vy * F1);
+            }
+            {   // volume term
+                const TC g1 = G.eval(fma(vy, -u2, fma(vx, -u1, (TC)t.w)));
+                vs.add(w * (pc1[kk] * (fc1[kk] - g1) + pc2[kk] * (fc2[kk] - halfT * g1)));
+            }
         }
     }
     const double GNX = warp_sum(gnx.get()), GNY = warp_sum(gny.get()), GEX = warp_sum(gex.get());
