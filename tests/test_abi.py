@@ -41,3 +41,35 @@ def test_status_strings_without_gpu():
 
 def test_sm103a_only():
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the public structs have the C sizes and field offsets: a C program
+    compiled against include/dvm.h prints them (gcc; no GPU)."""
+    import shutil
+    import subprocess
+    from paper_2501_00923_gb300 import serve
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    pairs = [("dvm_options", dvm.Options), ("dvm_flow", dvm.Flow), ("dvm_solve_opts", dvm.SolveOpts),
+             ("dvm_primal_result", dvm.PrimalResult), ("dvm_adjoint_result", dvm.AdjointResult),
+             ("dvm_batch_options", serve.BatchOptions), ("dvm_request", serve.Request),
+             ("dvm_request_result", serve.RequestResult)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dvm.h"', 'int main(void) {']
+    for cname, py in pairs:
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
