@@ -135,6 +135,12 @@ const char* dvm_last_error(void);
 /* number of kernel launches issued by this context since creation (graph launches count each
  * captured kernel) */
 uint64_t dvm_context_launches(const dvm_context* ctx);
+/* Self-test of the failure path of the bounded device waits.  One kernel waits on an mbarrier that
+ * nothing completes, with the same bound as the sweeps' pipeline waits (2 s of the device's global
+ * timer); the wait gives up, the kernel sets the context's device flag and returns.  Returns
+ * DVM_ERR_TIMEOUT (the flag is cleared) after about 2 s; the context stays usable.  No fault and no
+ * hang is involved.  Errors: DVM_ERR_INVALID_ARG (NULL), DVM_ERR_CUDA. */
+int dvm_selftest_wait_timeout(dvm_context* ctx);
 
 /* ------------------------------------------------------------------------ mesh, B2 */
 /* Copy the O-mesh nodes (double [(nj+1)][ni][2]) and build on the host the cell volumes, the

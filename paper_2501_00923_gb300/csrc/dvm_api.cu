@@ -847,6 +847,15 @@ void dvm_context_destroy(dvm_context* c) {
     delete c;
 }
 
+int dvm_selftest_wait_timeout(dvm_context* ctx) {
+    if (!ctx) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard dg(ctx->device);
+    CK(launch_wait_probe(ctx->derr, ctx->stream));
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_device_flag(ctx);
+}
+
 size_t dvm_context_bytes(const dvm_context* c) { return c ? c->bytes : 0; }
 uint64_t dvm_context_launches(const dvm_context* c) { return c ? c->launches : 0; }
 

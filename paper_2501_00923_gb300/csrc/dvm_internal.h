@@ -194,6 +194,8 @@ cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, double* out, cu
 // maxw: parameters of the cell Maxwellian (prim itself, or the conservative fit)
 cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const double4* maxw, const DevMesh& m,
                                      double inv_tau_inf, void* out, cudaStream_t s);
+// A wait that nothing completes, bounded like the sweeps' waits: sets *err after the wait limit.
+cudaError_t launch_wait_probe(int* err, cudaStream_t s);
 // Moment-space mixing: W = (rho, rho u, rho E) per cell from the primitives, and f += g(W) - g(prim).
 cudaError_t launch_prim_to_W(int ncell, const double4* prim, double* W, cudaStream_t s);
 cudaError_t launch_moment_shift(int storage, void* f, const DevMesh& m, const DevGrid& g, const double4* prim,

@@ -1387,6 +1387,21 @@ __global__ void __launch_bounds__(256) k_maxwell_fit(int ncell, int nvp, const t
     if (lane == 0) fit[c] = p;
 }
 
+// ================================================================== failure path of the bounded waits
+// One warp waits on an mbarrier that nothing completes, with the sweeps' bounded wait: after
+// kWaitNs of the global timer the wait gives up, the kernel sets *err and returns (no fault, no
+// hang), and the host reads the flag as DVM_ERR_TIMEOUT.
+__global__ void k_wait_probe(int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 // ================================================================== moment-space mixing
 // Anderson mixing of the cell moments: W = (rho, rho u1, rho u2, rho E) of every cell as one FP64
 // vector, and the shift that imposes mixed moments on f, f += g(W_mix) - g(W) per cell and velocity
@@ -2352,6 +2367,11 @@ cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cud
     if (storage == 0) second_order_launch<double, double>(args, adjoint, s);
     else if (storage == 1) second_order_launch<float, float>(args, adjoint, s);
     else second_order_launch<__nv_bfloat16, float>(args, adjoint, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(int* err, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(err);
     return cudaGetLastError();
 }
 

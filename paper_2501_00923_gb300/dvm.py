@@ -83,6 +83,7 @@ def lib():
             "dvm_context_destroy": (None, [_vp]),
             "dvm_context_bytes": (s, [_vp]),
             "dvm_context_launches": (u64, [_vp]),
+            "dvm_selftest_wait_timeout": (i, [_vp]),
             "dvm_status_string": (C.c_char_p, [i]),
             "dvm_last_error": (C.c_char_p, []),
             "dvm_mesh_create": (i, [_vp, i, i, _dp, pp]),
