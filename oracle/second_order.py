@@ -31,6 +31,8 @@ Nothing here is shared with the CUDA path.
 """
 from __future__ import annotations
 
+import copy
+
 import numpy as np
 
 from . import oracle as O
@@ -64,7 +66,7 @@ class SecondOrder:
         Tw = pr.Tw
         g1 = np.exp(-(vx ** 2 + vy ** 2) / (2 * Tw)) / (2 * np.pi * Tw)
         self.gbar = np.stack([g1, 0.5 * Tw * g1], 1)                 # [nv, 2], unnormalised
-        self.area_wall = np.linalg.norm(S[:, 3, :], axis=1)
+        self.area_wall = np.sqrt(S[:, 3, 0] ** 2 + S[:, 3, 1] ** 2)
 
     def face_weights(self, cells=None):
         """a_e = A_e n_e . v_k of the listed cells' faces, [n, 4, nv]."""
@@ -103,7 +105,7 @@ class SecondOrder:
         c = self._cells(cells)
         far, wall = self._boundary_values(f, c)
         fc = f[c]
-        gsum = np.zeros(fc.shape + (2,))
+        gsum = np.zeros(fc.shape + (2,), dtype=np.result_type(fc, self.S))
         for e in range(4):
             n = self.nb[c, e]
             inside = n >= 0
@@ -129,7 +131,7 @@ class SecondOrder:
         pos[U] = np.arange(U.size)
         Gc = G[pos[c]]
         a_all = self.face_weights(c)
-        out = np.zeros((c.size,) + f.shape[1:])
+        out = np.zeros((c.size,) + f.shape[1:], dtype=np.result_type(f, self.S))
         for e in range(4):
             n = self.nb[c, e]
             inside = n >= 0
@@ -152,6 +154,37 @@ class SecondOrder:
         own = np.einsum("cvkx,cx->cvk", G, self.xe[:, e] - self.xc)
         nbr = np.einsum("cvkx,cx->cvk", G[ns], self.xe[:, e] - self.xc[ns])
         return F1, F1 + np.where(up_own, own, nbr)
+
+    # ------------------------------------------------------------------ geometry and its derivative
+    def geometry_of(self, nodes):
+        """Face vectors A n [nc, 4, 2], volumes [nc], cell centres [nc, 2] and face midpoints [nc, 4, 2]
+        of the O-mesh with the given nodes [(nj+1), ni, 2] (real or complex): face e runs from
+        corner P_e to P_{e+1}, A n = (dy, -dx) along it, V by the shoelace formula."""
+        ni, nj = self.ni, self.nj
+        ip = (np.arange(ni) + 1) % ni
+        P = np.stack([nodes[:-1, :, :], nodes[1:, :, :], nodes[1:, ip, :], nodes[:-1, ip, :]], 2).reshape(ni * nj, 4, 2)
+        Q = np.roll(P, -1, axis=1)
+        S = np.stack([Q[..., 1] - P[..., 1], -(Q[..., 0] - P[..., 0])], -1)
+        V = 0.5 * np.sum(P[..., 0] * Q[..., 1] - Q[..., 0] * P[..., 1], axis=1)
+        return S, V, P.mean(1), 0.5 * (P + Q)
+
+    def delta_r_shape_dir(self, f, dnodes, h=1e-30):
+        """Derivative of dR along a node motion dnodes [(nj+1), ni, 2] at fixed f, by a complex step
+        of size h in the nodes (dR is analytic in them away from a_e = 0): [nc, nv, 2]."""
+        S, V, xc, xe = self.geometry_of(self.pr.nodes + 1j * h * np.asarray(dnodes))
+        c = copy.copy(self)
+        c.S, c.V, c.xc, c.xe, c._a = S, V, xc, xe, None
+        c.area_wall = np.sqrt(S[:, 3, 0] ** 2 + S[:, 3, 1] ** 2)
+        return np.imag(c.delta_r(np.asarray(f, dtype=np.float64))) / h
+
+    def sens_full(self, f, phi, dnodes):
+        """dJ/dalpha_p of the second-order discrete problem at its steady state f and adjoint phi
+        ((dR2/df)^T (w phi) = -dJ/df): dJ/dalpha = dJ/dalpha|_f + sum w phi . dR2/dalpha, the first-order
+        part from the oracle's full discrete sensitivity with this phi, plus sum w phi . d(dR)/dalpha.
+        dnodes: [P, (nj+1), ni, 2]."""
+        g = self.pr.sens_full(f, phi, dnodes)
+        w = self.pr.w[None, :, None]
+        return np.array([g[p] + np.sum(w * phi * self.delta_r_shape_dir(f, dnodes[p])) for p in range(len(dnodes))])
 
     # ------------------------------------------------------------------ linear structure
     def matrix(self):

@@ -127,3 +127,39 @@ def test_probed_transpose_at_interior_cells_equals_the_assembled_one():
     assert np.abs(so.adjoint_defect_cells(phi, cells) - E[cells]).max() < 1e-13 * np.abs(E).max()
     with pytest.raises(ValueError):
         so.adjoint_defect_cells(phi, np.array([5]))
+
+
+def test_geometry_of_reproduces_the_oracle_geometry():
+    mesh, g, pr, so = _so(10, 5, 4)
+    S, V, xc, xe = so.geometry_of(mesh.nodes)
+    assert np.abs(S - so.S).max() < 1e-15 * np.abs(so.S).max()
+    assert np.abs(V - so.V).max() < 1e-15 * np.abs(so.V).max()
+    assert np.abs(xc - so.xc).max() == 0.0 and np.abs(xe - so.xe).max() == 0.0
+
+
+@pytest.mark.slow
+def test_second_order_full_gradient_matches_central_differences():
+    """dJ/dalpha of the second-order discrete problem (the first-order full sensitivity with the
+    second-order adjoint, plus sum w phi . d(dR)/dalpha by a complex step in the nodes) against central
+    differences of two second-order solves per bump amplitude (step 1e-5), all solves to round-off."""
+    alpha = np.array([0.004, -0.003, 0.002, 0.001])
+    mesh, g, pr, so = _so(8, 4, 6, alpha=alpha)
+    f, it = so.solve(tol=1e-15, max_sweeps=20000)
+    assert it < 20000
+    phi, ait = so.adjoint_solve(f, tol=1e-15, max_sweeps=20000)
+    assert ait < 20000
+    grad = so.sens_full(f, phi, mesh.dnodes())
+    h = 1e-5
+    for p in range(alpha.size):
+        J = []
+        for s in (1, -1):
+            a = alpha.copy()
+            a[p] += s * h
+            _, _, pp, sp = _so(8, 4, 6, alpha=a)
+            fp, _ = sp.solve(f0=f, tol=1e-15, max_sweeps=20000)
+            J.append(pp.functional(fp))
+        fd = (J[0] - J[1]) / (2 * h)
+        assert abs(fd - grad[p]) <= 1e-6 * np.abs(grad).max(), (p, fd, grad[p])
+    # the second-order term matters: the first-order formula with the same phi differs
+    g1 = pr.sens_full(f, phi, mesh.dnodes())
+    assert np.abs(g1 - grad).max() > 1e-4 * np.abs(grad).max()
