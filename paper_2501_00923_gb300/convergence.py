@@ -157,7 +157,8 @@ def _observed(J):
     if d1 == 0.0 or d2 == 0.0 or d1 / d2 <= 0.0:
         return None, None
     p = float(np.log2(d1 / d2))
-    return p, float(J[-1] + d2 / (2.0 ** p - 1.0))
+    # J_h = J* + c h^p: J[-2] - J[-1] = (2^p - 1) (J[-1] - J*)
+    return p, float(J[-1] - d2 / (2.0 ** p - 1.0))
 
 
 def _mesh_study(args):
