@@ -188,9 +188,10 @@ int dvm_state_moments(const dvm_state* st, double* prim_host);
  * faces, the drag and the wall density stay first order.  The first call with order 2 allocates three
  * buffers of the size of f for the state and one for each adjoint swept later (counted against the HBM
  * budget: DVM_ERR_ADMISSION).  dvm_state_set and an adjoint upload retake the defect at the next sweep;
- * the residual normaliser r0 keeps its value from state creation.  With order 2, dvm_sensitivity
- * accepts DVM_SENS_PAPER only (DVM_ERR_INVALID_ARG for DVM_SENS_FULL); dvm_batch requests stay first
- * order.  Errors: DVM_ERR_INVALID_ARG (NULL, order not 1 or 2, defect_period < 0), DVM_ERR_ADMISSION,
+ * the residual normaliser r0 keeps its value from state creation.  With order 2, DVM_SENS_FULL adds
+ * the derivative of the reconstruction's added flux with respect to the nodes (face vectors, volumes,
+ * cell centres and face midpoints in the Gauss gradient and the offsets, and the wall inflow values);
+ * dvm_sensitivity_noalloc accepts DVM_SENS_PAPER only for it; dvm_batch requests stay first order.  Errors: DVM_ERR_INVALID_ARG (NULL, order not 1 or 2, defect_period < 0), DVM_ERR_ADMISSION,
  * DVM_ERR_OOM. */
 int dvm_state_set_order(dvm_state* st, int order, int defect_period);
 int dvm_state_get_order(const dvm_state* st, int* order);

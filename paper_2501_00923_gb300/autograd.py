@@ -32,13 +32,11 @@ class DragProblem:
     stall_window: int = 0
     mode: str = "full"
     mesh_fn: object = None          # alpha -> OMesh; default: the Hicks-Henne bump section
-    order: int = 1                  # 2: second-order reconstruction (mode "paper" only)
+    order: int = 1                  # 2: second-order reconstruction
     maxwellian: str = "plain"       # or "conservative"
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
-        if self.order == 2 and self.mode == "full":
-            raise ValueError("the full discrete gradient is first-order only: use mode='paper' with order 2")
         self._grid = dvm.VGrid(self.ctx, self.grid.vx, self.grid.vy, self.grid.w)
         self._warm_f = None
         self._warm_phi = None

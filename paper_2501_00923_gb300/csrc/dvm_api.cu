@@ -124,7 +124,7 @@ struct dvm_adjoint {
     double* Kinv = nullptr;     // conservative Maxwellian: dp/dW per cell, [ncell][4][4]
     TmaMaps maps[2];            // tiled-TMA descriptors of phi[0], phi[1]
     // sensitivity scratch, allocated on first use
-    double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr;
+    double2 *GN = nullptr, *GE = nullptr, *GW = nullptr, *node_grad = nullptr, *so_corner = nullptr;
     double *vol = nullptr, *elem = nullptr, *dwall = nullptr, *sj = nullptr, *grad = nullptr;
     int sens_P = 0;
     AAState* aa = nullptr;
@@ -1404,7 +1404,7 @@ void dvm_adjoint_destroy(dvm_adjoint* ad) {
     for (int b = 0; b < 2; ++b) { dfree(ad->phi[b]); dfree(ad->Z[b]); dfree(ad->Lam[b]); }
     dfree(ad->respart); dfree(ad->out); dfree(ad->wallM); dfree(ad->cell);
     dfree(ad->GN); dfree(ad->GE); dfree(ad->GW); dfree(ad->node_grad); dfree(ad->vol); dfree(ad->elem);
-    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad); dfree(ad->so_def); dfree(ad->Kinv);
+    dfree(ad->dwall); dfree(ad->sj); dfree(ad->grad); dfree(ad->so_def); dfree(ad->Kinv); dfree(ad->so_corner);
     aa_free(ad->st->ctx, ad->aa);
     ad->st->ctx->bytes -= ad->bytes;
     delete ad;
@@ -1637,8 +1637,6 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
     if (mode == DVM_SENS_FULL && !s_j) return fail(DVM_ERR_INVALID_ARG, "full mode needs s_j");
     if (cad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
     if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
-    if (mode == DVM_SENS_FULL && st->order != 1)
-        return fail(DVM_ERR_INVALID_ARG, "the full discrete gradient is first-order only; use DVM_SENS_PAPER");
     DeviceGuard dg(ctx->device);
     Range nvtx("dvm_sensitivity");
     dvm_adjoint* ad = const_cast<dvm_adjoint*>(cad);
@@ -1678,6 +1676,23 @@ int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* ca
         CK(launch_sens_full(st->storage, m, g, st->fl, f, phi, st->prim[st->cur],
                             st->maxwell ? st->fit : st->prim[st->cur], st->Fw[st->cur], ad->mj,
                             ad->GN, ad->GE, ad->GW, ad->vol, ad->node_grad, s));
+        if (st->order == 2) {          // + d(sum w phi . dR)/dx of the reconstruction
+            if (!ad->so_corner) {
+                size_t acc = 0;
+                if ((rc = dalloc(ctx, &ad->so_corner, 4 * (size_t)m.ncell, &acc))) return rc;
+                ad->bytes += acc;
+                ctx->bytes += acc;
+            }
+            switch (st->storage) {
+                case DVM_STORE_FP64: { auto a = so_args<double, double>(st, f, st->Fw[st->cur], nullptr);
+                                       CK(launch_so_sens(0, &a, phi, ad->so_corner, m.ni, m.nj, ad->node_grad, s)); break; }
+                case DVM_STORE_FP32: { auto a = so_args<float, float>(st, f, st->Fw[st->cur], nullptr);
+                                       CK(launch_so_sens(1, &a, phi, ad->so_corner, m.ni, m.nj, ad->node_grad, s)); break; }
+                default: { auto a = so_args<__nv_bfloat16, float>(st, f, st->Fw[st->cur], nullptr);
+                           CK(launch_so_sens(2, &a, phi, ad->so_corner, m.ni, m.nj, ad->node_grad, s)); break; }
+            }
+            ctx->launches += 2;
+        }
         CK(launch_contract(ad->node_grad, m.nj + 1, m.ni, ad->sj, ad->dwall, P, ad->grad, s));
         ctx->launches += 2 + (P > 0);
         if (node_grad_out)
@@ -1768,7 +1783,7 @@ extern "C" int dvm_sensitivity_noalloc(dvm_context* ctx, const dvm_state* st, co
     if (ad->st != st || st->ctx != ctx) return fail(DVM_ERR_INVALID_ARG, "adjoint/state/context mismatch");
     if (P < 0) return fail(DVM_ERR_INVALID_ARG, "n_params < 0");
     if (mode == DVM_SENS_FULL && st->order != 1)
-        return fail(DVM_ERR_INVALID_ARG, "the full discrete gradient is first-order only; use DVM_SENS_PAPER");
+        return fail(DVM_ERR_INVALID_ARG, "the scratch-free full gradient is first-order only; use dvm_sensitivity");
     const DevMesh& m = st->mesh->d;
     const DevGrid& g = st->grid->d;
     const int nnodes = (m.nj + 1) * m.ni;

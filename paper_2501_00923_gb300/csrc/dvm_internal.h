@@ -239,6 +239,10 @@ cudaError_t launch_aa_restore(int storage, size_t n, void* F, void* X, const voi
 // Second order: adjoint = false -> gradient of args.in, then dR into args.out; adjoint = true -> mu of
 // args.in (phi), then the transposed defect into args.out.  args is SOArgs<TS, TC>.
 cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cudaStream_t s);
+// Full discrete sensitivity of a second-order state: adds d(sum w phi . dR)/dx to node_grad
+// [(nj+1)][ni] (args: SOArgs with in = f, Fw of f; corner: [ncell][4] scratch).
+cudaError_t launch_so_sens(int storage, const void* args, const void* phi, double2* corner, int ni, int nj,
+                           double2* node_grad, cudaStream_t s);
 
 // out[0] = Q, out[1 + p] = dQ/dalpha_p
 cudaError_t launch_volume(const DevMesh& m, double vmin, const double* dwall, int P, double* out, cudaStream_t s);

@@ -1618,6 +1618,179 @@ __global__ void __launch_bounds__(256, DVM_SO_BLOCKS) k_so_defect(const SOArgs<T
     }
 }
 
+// Node gradient of Lambda = sum_c lambda_c . dR_c (lambda = w phi) for the full discrete sensitivity
+// of a second-order state.  With mu_u of the transposed reconstruction, Lambda = sum_u grad f_u . mu_u,
+// and its geometric derivative gathers, per cell u, five terms: the volume in the Gauss gradient
+// (-(grad f_u . mu_u) / V_u dV_u), its face vectors (fbar_e mu_u / V_u . dS_e), the wall inflow values'
+// dependence on the wall face vector through F_rhow / D, the face weights a_e = S_e . v of mu_u
+// ((grad f_u . d_e) (lambda_u - lambda_nb) v . dS_e on outflow faces) and the offsets d_e = x_e - x_u
+// (a_e (lambda_u - lambda_nb) grad f_u . d(d_e)).  k_so_sens_cells writes each cell's share of the
+// derivative at its four corners; k_so_sens_nodes adds, per node, the shares of the cells around it.
+template <class TS>
+__global__ void __launch_bounds__(256) k_so_sens_cells(const SOArgs<TS, typename Pack<TS>::TC> A, const TS* __restrict__ phi,
+                                                       double2* __restrict__ corner) {
+    using PK = Pack<TS>;
+    using TC = typename PK::TC;
+    using TC2 = typename Vec<TC>::v2;
+    using TC4 = typename Vec<TC>::v4;
+    constexpr int KV = PK::KV;
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= A.ncell) return;
+    const int4 n4 = A.nb[c];
+    const int nb[4] = {n4.x, n4.y, n4.z, n4.w};
+    const bool wall = nb[3] == kWall;
+    TC2 S[4], dc[4], dn[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) S[e] = A.S[4 * c + e];
+    so_offsets(A.nodes, A.ni, c, nb, dc, dn);
+    const TC iV = TC(1) / A.V[c];
+    TC cw1 = TC(0), cw2 = TC(0);
+    if (wall) {
+        cw1 = (TC)(A.Fw[c] / A.wallD[c]);
+        cw2 = cw1 * A.halfTw;
+    }
+    const size_t nq = (size_t)A.nq;
+    const uint4* fq = reinterpret_cast<const uint4*>(A.in);
+    const uint4* pq = reinterpret_cast<const uint4*>(phi);
+    // sums: 0 sV; 1..8 T_e; 9..16 U_e; 17..24 Y_e; wall: 25 Lam2, 26 Fw, 27..28 dFw, 29 D, 30..31 dD
+    TC s[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) s[i] = TC(0);
+    for (size_t q = lane; q < nq; q += 32) {
+        TC o1[KV], o2[KV], m1[4][KV], m2[4][KV], l1[KV], l2[KV], k1[4][KV], k2[4][KV];
+        PK::unpack(ldg16(fq + (size_t)c * nq + q), o1, o2);
+        PK::unpack(ldg16(pq + (size_t)c * nq + q), l1, l2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const size_t m = nb[e] >= 0 ? (size_t)nb[e] : (size_t)c;
+            PK::unpack(ldg16(fq + m * nq + q), m1[e], m2[e]);
+            PK::unpack(ldg16(pq + m * nq + q), k1[e], k2[e]);
+        }
+#pragma unroll
+        for (int kk = 0; kk < KV; ++kk) {
+            const int k = (int)q * KV + kk;
+            const TC4 t = A.vt[k];
+            const TC w = t.z;
+            TC a[4], fb1[4], fb2[4];
+            TC gx1 = TC(0), gy1 = TC(0), gx2 = TC(0), gy2 = TC(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                a[e] = S[e].x * t.x + S[e].y * t.y;
+                if (nb[e] >= 0) {
+                    fb1[e] = TC(0.5) * (o1[kk] + m1[e][kk]);
+                    fb2[e] = TC(0.5) * (o2[kk] + m2[e][kk]);
+                } else if (a[e] > TC(0)) {
+                    fb1[e] = o1[kk]; fb2[e] = o2[kk];
+                } else if (nb[e] == kFar) {
+                    const TC2 fd = A.fd[k]; fb1[e] = fd.x; fb2[e] = fd.y;
+                } else {
+                    const TC gk = A.gw[k]; fb1[e] = cw1 * gk; fb2[e] = cw2 * gk;
+                }
+                gx1 += fb1[e] * S[e].x; gy1 += fb1[e] * S[e].y;
+                gx2 += fb2[e] * S[e].x; gy2 += fb2[e] * S[e].y;
+            }
+            gx1 *= iV; gy1 *= iV; gx2 *= iV; gy2 *= iV;
+            // mu and the outflow-face terms, lambda = w phi
+            TC mx1 = TC(0), my1 = TC(0), mx2 = TC(0), my2 = TC(0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (nb[e] < 0 || !(a[e] > TC(0))) continue;
+                const TC dl1 = w * (l1[kk] - k1[e][kk]), dl2 = w * (l2[kk] - k2[e][kk]);
+                const TC ad1 = a[e] * dl1, ad2 = a[e] * dl2;
+                mx1 += ad1 * dc[e].x; my1 += ad1 * dc[e].y;
+                mx2 += ad2 * dc[e].x; my2 += ad2 * dc[e].y;
+                const TC gd = (gx1 * dc[e].x + gy1 * dc[e].y) * dl1 + (gx2 * dc[e].x + gy2 * dc[e].y) * dl2;
+                s[9 + 2 * e] += gd * t.x;
+                s[10 + 2 * e] += gd * t.y;
+                s[17 + 2 * e] += ad1 * gx1 + ad2 * gx2;
+                s[18 + 2 * e] += ad1 * gy1 + ad2 * gy2;
+            }
+            s[0] += gx1 * mx1 + gy1 * my1 + gx2 * mx2 + gy2 * my2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                s[1 + 2 * e] += (fb1[e] * mx1 + fb2[e] * mx2) * iV;
+                s[2 + 2 * e] += (fb1[e] * my1 + fb2[e] * my2) * iV;
+            }
+            if (wall) {
+                const TC gk = A.gw[k];
+                if (a[3] > TC(0)) {
+                    s[26] += w * a[3] * o1[kk];
+                    s[27] += w * t.x * o1[kk];
+                    s[28] += w * t.y * o1[kk];
+                } else {
+                    const TC sm1 = (S[3].x * mx1 + S[3].y * my1) * iV, sm2 = (S[3].x * mx2 + S[3].y * my2) * iV;
+                    s[25] += sm1 * gk + sm2 * A.halfTw * gk;
+                    s[29] -= w * a[3] * gk;
+                    s[30] -= w * t.x * gk;
+                    s[31] -= w * t.y * gk;
+                }
+            }
+        }
+    }
+    double r[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = warp_sum((double)s[i]);
+    if (lane != 0) return;
+    const int ni = A.ni, i = c % ni, j = c / ni, ip = (i + 1) % ni;
+    const double2 P[4] = {A.nodes[j * ni + i], A.nodes[(j + 1) * ni + i], A.nodes[(j + 1) * ni + ip], A.nodes[j * ni + ip]};
+    const double V = (double)A.V[c];
+    double2 C[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) C[q] = make_double2(0.0, 0.0);
+    double X[4][2];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        X[e][0] = r[1 + 2 * e] + r[9 + 2 * e];
+        X[e][1] = r[2 + 2 * e] + r[10 + 2 * e];
+    }
+    if (wall && r[29] != 0.0) {            // F_rhow / D as a function of the wall face vector
+        const double Fw = r[26], D = r[29];
+        X[3][0] += r[25] * (r[27] * D - Fw * r[30]) / (D * D);
+        X[3][1] += r[25] * (r[28] * D - Fw * r[31]) / (D * D);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {          // S_e = (Qy - Py, -(Qx - Px)): d/dP = (X_y, -X_x), d/dQ = (-X_y, X_x)
+        const int e1 = (e + 1) & 3;
+        C[e].x += X[e][1]; C[e].y -= X[e][0];
+        C[e1].x -= X[e][1]; C[e1].y += X[e][0];
+    }
+    const double kv = -r[0] / V;           // volume: dV/dP_e = ((P_{e+1} - P_{e-1})_y, (P_{e-1} - P_{e+1})_x) / 2
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const double2 Pn = P[(e + 1) & 3], Pp = P[(e + 3) & 3];
+        C[e].x += kv * 0.5 * (Pn.y - Pp.y);
+        C[e].y += kv * 0.5 * (Pp.x - Pn.x);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {          // d_e = x_e - x_u: x_e the midpoint of P_e P_{e+1}, x_u the corner mean
+        const double yx = r[17 + 2 * e], yy = r[18 + 2 * e];
+        const int e1 = (e + 1) & 3;
+        C[e].x += 0.5 * yx; C[e].y += 0.5 * yy;
+        C[e1].x += 0.5 * yx; C[e1].y += 0.5 * yy;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { C[q].x -= 0.25 * yx; C[q].y -= 0.25 * yy; }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) corner[4 * (size_t)c + q] = C[q];
+}
+
+// node (jj, ii) is corner 0 of cell (jj, ii), 1 of (jj-1, ii), 2 of (jj-1, ii-1) and 3 of (jj, ii-1)
+__global__ void k_so_sens_nodes(int ni, int nj, const double2* __restrict__ corner, double2* __restrict__ node_grad) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (nj + 1) * ni) return;
+    const int jj = id / ni, ii = id % ni, im = (ii - 1 + ni) % ni;
+    double2 g = node_grad[id];
+    if (jj < nj) {
+        const double2 a = corner[4 * (size_t)(jj * ni + ii) + 0], b = corner[4 * (size_t)(jj * ni + im) + 3];
+        g.x += a.x + b.x; g.y += a.y + b.y;
+    }
+    if (jj > 0) {
+        const double2 a = corner[4 * (size_t)((jj - 1) * ni + ii) + 1], b = corner[4 * (size_t)((jj - 1) * ni + im) + 2];
+        g.x += a.x + b.x; g.y += a.y + b.y;
+    }
+    node_grad[id] = g;
+}
+
 template <class TS>
 __global__ void __launch_bounds__(256, DVM_SO_BLOCKS) k_so_adjoint_mu(const SOArgs<TS, typename Pack<TS>::TC> A) {
     using PK = Pack<TS>;
@@ -2361,6 +2534,21 @@ void second_order_launch(const void* args, bool adjoint, cudaStream_t s) {
         k_so_gradient<TS><<<nb, 256, 0, s>>>(a);
         k_so_defect<TS><<<nb, 256, 0, s>>>(a);
     }
+}
+
+cudaError_t launch_so_sens(int storage, const void* args, const void* phi, double2* corner, int ni, int nj,
+                           double2* node_grad, cudaStream_t s) {
+    const int ncell = ni * nj, nb = cdiv(ncell, kWarpsPerBlock);
+    if (storage == 0)
+        k_so_sens_cells<double><<<nb, 256, 0, s>>>(*static_cast<const SOArgs<double, double>*>(args), (const double*)phi, corner);
+    else if (storage == 1)
+        k_so_sens_cells<float><<<nb, 256, 0, s>>>(*static_cast<const SOArgs<float, float>*>(args), (const float*)phi, corner);
+    else
+        k_so_sens_cells<__nv_bfloat16><<<nb, 256, 0, s>>>(*static_cast<const SOArgs<__nv_bfloat16, float>*>(args),
+                                                           (const __nv_bfloat16*)phi, corner);
+    const int nn = (nj + 1) * ni;
+    k_so_sens_nodes<<<cdiv(nn, 256), 256, 0, s>>>(ni, nj, corner, node_grad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_second_order(int storage, const void* args, bool adjoint, cudaStream_t s) {

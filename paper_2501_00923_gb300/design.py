@@ -302,7 +302,7 @@ def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 
         maxwellian: str = "plain", mode: str | None = None):
     """Drive one loop with blocking GPU solves (autograd.DragProblem keeps f and phi of the last
     design as warm starts for the next).  order 2 (second-order reconstruction) takes the paper's
-    boundary sensitivity (mode "paper"); order 1 the full discrete gradient unless mode says otherwise."""
+    boundary sensitivity (mode "paper") unless mode says otherwise; order 1 the full discrete gradient."""
     from .autograd import DragProblem
     mode = mode or ("paper" if order == 2 else "full")
     prob = DragProblem(ctx, loop.ni, loop.nj, loop.grid, loop.flow, storage=storage, tol=tol,

@@ -184,12 +184,17 @@ def test_second_order_steady_state_and_adjoint_match_oracle(ctx):
     phi_ref, ait = so.adjoint_solve(f_gpu, tol=1e-15, max_sweeps=20000)
     assert ait < 20000
     assert np.abs(ad.get() - phi_ref).max() < 1e-9 * np.abs(phi_ref).max()
-    # PAPER-mode sensitivities are available; the full discrete gradient is first-order only
+    # both sensitivity modes: the paper's boundary formula, and the full discrete gradient of the
+    # second-order problem (its oracle is pinned by central differences of second-order solves)
+    phi_gpu = ad.get()
     grad = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="paper")
-    pref, _, _ = pr.sens_paper(f_gpu, ad.get(), mesh.dwall)
+    pref, _, _ = pr.sens_paper(f_gpu, phi_gpu, mesh.dwall)
     assert np.abs(grad - pref).max() < 1e-9 * np.abs(pref).max()
-    with pytest.raises(dvm.DVMError) as e:
-        dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    full = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    fref = so.sens_full(f_gpu, phi_gpu, mesh.dnodes())
+    assert np.abs(full - fref).max() < 1e-9 * np.abs(fref).max()
+    with pytest.raises(dvm.DVMError) as e:        # the scratch-free entry point stays first order in FULL
+        dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full", noalloc=True)
     assert e.value.status == dvm.DVM_ERR_INVALID_ARG
     ad.close()
 
