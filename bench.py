@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the DVM-BGK hot path on one GB300 (or N independent replicas).
 
-A step is one pass of the whole path over the 256x128-cell, 48x48 Gauss-Legendre workload
-(Kn 0.1, Ma 0.8, 16 bump amplitudes, FP32 storage, FP64 reductions):
+A step is one pass of the whole path over the largest single-GPU workload, the near-continuum
+airfoil: 384x192-cell O-mesh, 64x64 uniform velocity grid on +-8 a_inf, Kn 0.001, Ma 2, 24 bump
+amplitudes, FP32 storage with compensated reductions:
   `--sweeps` primal point-implicit sweeps (one CUDA graph) with the fused moments, wall density,
   drag and residual; `--sweeps` adjoint sweeps (one graph); the full-discrete and the paper
-  sensitivities over the 16 bump amplitudes.
-Metric: primal+adjoint (cell, velocity) updates per second, whole job.  f is 604 MB in FP32, far
-larger than the 126 MB L2, so no flush is needed between iterations.
+  sensitivities over the 24 bump amplitudes.
+`--workload 1` runs the 256x128-cell, 48x48 Gauss-Legendre workload (Kn 0.1, Ma 0.8, 16 bumps).
+Metric: primal+adjoint (cell, velocity) updates per second, whole job.  f is 2.4 GB in FP32 (604 MB
+for workload 1), far larger than the 126 MB L2, so no flush is needed between iterations.
 
 `--impl reference` times the FP64 CPU oracle (the only reference this method has) on a bounded
 sample of the same workload on the host cores.
@@ -32,7 +34,7 @@ from paper_2501_00923_gb300 import workloads as W  # noqa: E402
 
 METRIC = "primal+adjoint DVM updates/s"
 UNIT = "updates/s"
-WORKLOAD_INDEX = 1
+WORKLOAD_INDEX = 2
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
@@ -49,7 +51,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--mesh", default=None, help="override the O-mesh size, e.g. 128x64 (profiling runs)")
     p.add_argument("--workload", type=int, default=WORKLOAD_INDEX, choices=[1, 2, 4],
-                   help="1: 256x128 GL48 Kn 0.1 (default); 2: 384x192 64x64 Kn 0.001 Ma 2; "
+                   help="2: 384x192 64x64 Kn 0.001 Ma 2 (default); 1: 256x128 GL48 Kn 0.1; "
                         "4: 256x128 GL48, 24 bumps (design-loop size)")
     p.add_argument("--order", type=int, default=1, choices=[1, 2],
                    help="spatial order of the face values (2: linear reconstruction, defect correction)")
@@ -146,9 +148,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def ncu_traffic(kernel: str, storage: str):
-    """DRAM read+write bytes per launch from the committed ncu summary, scaled to this workload,
-    or None when the kernel source changed since the counters were taken."""
+def ncu_traffic(kernel: str, storage: str, workload: str):
+    """DRAM read+write bytes per launch of the kernel's hot instance on this workload, from the
+    committed ncu record (one full-size capture), or None when the kernel source changed since the
+    counters were taken or the workload was not captured."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
@@ -158,7 +161,7 @@ def ncu_traffic(kernel: str, storage: str):
             cur = hashlib.sha256(fh.read()).hexdigest()[:16]
         if rec.get("kernel_source_sha256_16") != cur:
             return None
-        return rec.get(f"{kernel}/{storage}")
+        return rec.get("workloads", {}).get(workload, {}).get(f"{kernel}/{storage}")
     except Exception:
         return None
 
@@ -297,7 +300,8 @@ def run_gpu(args):
              "GBps": pairs * (6 + extra) * S / (adj_sweep_ms * 1e6)}
     dom = k_adj if adj_ms >= prim_ms else k_prim
     alt = bool(args.mesh) or args.workload != WORKLOAD_INDEX or args.order != 1 or args.maxwellian != "plain"
-    traffic = ncu_traffic(dom["name"], args.storage) if not alt else None
+    traffic = ncu_traffic(dom["name"], args.storage, wl.name) if not (args.mesh or args.order != 1
+                                                                       or args.maxwellian != "plain") else None
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": dom["GBps"] / peak, "traffic": traffic, "kernel": dom["name"],
                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"

@@ -18,8 +18,10 @@
  *   chosen at state creation (FP64, FP32 or BF16), the velocity count padded to a multiple of 4 with
  *   zero-weight velocities.
  * Ownership: host arrays are caller-owned and only read (or written, for outputs) during the call.
- *   Every handle is library-owned and released by its *_destroy.  Device memory is allocated with
- *   cudaMalloc on the context's device; the context's stream orders all work.
+ *   Every handle is library-owned and released by its *_destroy.  Device memory comes from one
+ *   stream-ordered pool per device (cudaMallocFromPoolAsync on the context's stream; freed blocks are
+ *   kept by the pool and reused, so a state created after another is destroyed does not call
+ *   cudaMalloc); dvm_context_destroy trims the pool.  The context's stream orders all work.
  * Errors: every call returns a dvm_status; DVM_OK = 0.  No C++ exception crosses the ABI.  After
  *   DVM_ERR_CUDA the context should be destroyed.  dvm_last_error() gives a message for the
  *   calling thread.  Calls are thread-compatible per context (one thread at a time per context).
@@ -135,6 +137,9 @@ const char* dvm_last_error(void);
 /* number of kernel launches issued by this context since creation (graph launches count each
  * captured kernel) */
 uint64_t dvm_context_launches(const dvm_context* ctx);
+/* number of device allocations made for this context since creation (blocks taken from the
+ * library's stream-ordered pool, transient ones included) */
+uint64_t dvm_context_allocations(const dvm_context* ctx);
 /* Self-test of the failure path of the bounded device waits.  One kernel waits on an mbarrier that
  * nothing completes, with the same bound as the sweeps' pipeline waits (2 s of the device's global
  * timer); the wait gives up, the kernel sets the context's device flag and returns.  Returns
@@ -167,6 +172,14 @@ void dvm_state_destroy(dvm_state* st);
 int dvm_state_set(dvm_state* st, const double* f_host);
 /* Download f (converted to double). */
 int dvm_state_get(const dvm_state* st, double* f_host);
+/* Device-to-device warm start: copy the current f of src into dst (no host round trip) and recompute
+ * dst's moments W and wall density F_rhow (Eq. macint_reduce, formula_bgk_fdw) on dst's own mesh, as
+ * dvm_state_set does after an upload.  The two states need the same context, the same mesh shape
+ * (ni, nj), the same velocity count and the same storage; their meshes and flows may differ (a new
+ * design of the same shape, Sec. 3.4, Steps 2-3), and the velocity lists should be the same.
+ * Enqueued on the context's stream; src is only read.  Errors: DVM_ERR_INVALID_ARG (NULL or a
+ * layout mismatch), DVM_ERR_CUDA. */
+int dvm_state_copy_from(dvm_state* dst, const dvm_state* src);
 /* Download per-cell primitive variables (rho, u1, u2, T) [ncell][4] of the current f. */
 int dvm_state_moments(const dvm_state* st, double* prim_host);
 /* Spatial order of the face values used by every later sweep of this state and of its adjoints.
@@ -188,10 +201,13 @@ int dvm_state_moments(const dvm_state* st, double* prim_host);
  * faces, the drag and the wall density stay first order.  The first call with order 2 allocates three
  * buffers of the size of f for the state and one for each adjoint swept later (counted against the HBM
  * budget: DVM_ERR_ADMISSION).  dvm_state_set and an adjoint upload retake the defect at the next sweep;
- * the residual normaliser r0 keeps its value from state creation.  With order 2, DVM_SENS_FULL adds
- * the derivative of the reconstruction's added flux with respect to the nodes (face vectors, volumes,
- * cell centres and face midpoints in the Gauss gradient and the offsets, and the wall inflow values);
- * dvm_sensitivity_noalloc accepts DVM_SENS_PAPER only for it; dvm_batch requests stay first order.  Errors: DVM_ERR_INVALID_ARG (NULL, order not 1 or 2, defect_period < 0), DVM_ERR_ADMISSION,
+ * the residual normaliser r0 keeps its value from state creation.
+ * With order 2, DVM_SENS_FULL adds the derivative of the reconstruction's added flux with respect to
+ * the nodes (face vectors, volumes, cell centres and face midpoints in the Gauss gradient and the
+ * offsets, and the wall inflow values); its first call on an adjoint allocates a per-cell corner
+ * buffer (4 ncell double2, counted against the HBM budget).  dvm_sensitivity_noalloc accepts only
+ * DVM_SENS_PAPER for order-2 states.  dvm_batch requests stay first order.
+ * Errors: DVM_ERR_INVALID_ARG (NULL, order not 1 or 2, defect_period < 0), DVM_ERR_ADMISSION,
  * DVM_ERR_OOM. */
 int dvm_state_set_order(dvm_state* st, int order, int defect_period);
 int dvm_state_get_order(const dvm_state* st, int* order);
@@ -229,6 +245,10 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
 int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out);
 void dvm_adjoint_destroy(dvm_adjoint* adj);
 int dvm_adjoint_set(dvm_adjoint* adj, const double* phi_host);
+/* Device-to-device warm start of the adjoint: copy the current phi of src into dst and rebuild dst's
+ * collision and wall couplings from it, as dvm_adjoint_set does after an upload.  Same layout rules as
+ * dvm_state_copy_from (for the adjoints' states).  Errors: DVM_ERR_INVALID_ARG, DVM_ERR_CUDA. */
+int dvm_adjoint_copy_from(dvm_adjoint* dst, const dvm_adjoint* src);
 int dvm_adjoint_get(const dvm_adjoint* adj, double* phi_host);
 /* Exactly n sweeps of the transposed (downwind) point-implicit update of Eq. (numerad_gov) in
  * discrete form, (dR/df)^T (w phi) = -(dJ/df)^T:
@@ -245,7 +265,9 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
  * (double [n_params][ni][2], caller-owned) and the interior nodes by (1 - s_j) times that
  * (s_j: double [nj+1], s_0 = 0, s_nj = 1; used by DVM_SENS_FULL only).  grad_out: double[n_params].
  * node_grad_out (optional): DVM_SENS_PAPER -> dJ/dx of the wall nodes, double [ni][2];
- * DVM_SENS_FULL -> dJ/dx of every node, double [(nj+1)][ni][2]. */
+ * DVM_SENS_FULL -> dJ/dx of every node, double [(nj+1)][ni][2].
+ * The first call on an adjoint allocates its scratch (per-cell face sums, node gradient, tangents;
+ * counted against the HBM budget) and later calls reuse it. */
 int dvm_sensitivity(dvm_context* ctx, const dvm_state* st, const dvm_adjoint* adj, int n_params,
                     const double* dwall_dalpha, const double* s_j, int mode, double* grad_out,
                     double* node_grad_out);

@@ -5,7 +5,9 @@ forward(alpha) builds the O-mesh for the bump amplitudes alpha, solves the stead
 implicit-function adjoint: the discrete adjoint solve (Eq. numerad_gov, transposed) at the converged
 state followed by the full-discrete sensitivity, so grad = grad_out * dCd/dalpha.  The device state
 and adjoint are kept by the problem object and reused as warm starts by the next evaluation of the
-same problem (a line search or a design sweep moves alpha only a little).
+same problem (a line search or a design sweep moves alpha only a little): the next design's state
+and adjoint start from them by device-to-device copies (dvm_state_copy_from, dvm_adjoint_copy_from),
+so no f or phi crosses to the host between evaluations.
 """
 from __future__ import annotations
 
@@ -38,8 +40,7 @@ class DragProblem:
 
     def __post_init__(self):
         self._grid = dvm.VGrid(self.ctx, self.grid.vx, self.grid.vy, self.grid.w)
-        self._warm_f = None
-        self._warm_phi = None
+        self._warm = None           # (mesh, state, adjoint) of the last design whose gradient was taken
 
     @property
     def q_ref(self) -> float:
@@ -53,8 +54,8 @@ class DragProblem:
                        storage=self.storage)
         if self.maxwellian != "plain":
             st.maxwellian = self.maxwellian
-        if self._warm_f is not None:
-            st.set(self._warm_f)
+        if self._warm is not None:
+            st.copy_from(self._warm[1])
         elif self.order == 2:               # second order starts from the converged first-order state
             dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa,
                              tol=self.tol, max_iter=self.max_iter, storage=self.storage, state=st,
@@ -69,22 +70,39 @@ class DragProblem:
     def gradient(self):
         st, mesh = self.last["state"], self.last["mesh"]
         ad = dvm.Adjoint(st)
-        if self._warm_phi is not None:
-            ad.set(self._warm_phi)
+        if self._warm is not None:
+            ad.copy_from(self._warm[2])
         ad, ares = dvm.adjoint_solve(self.ctx, st, tol=self.adjoint_tol, max_iter=self.max_iter, adjoint=ad,
                                      stall_window=self.stall_window)
         g = dvm.sensitivity(self.ctx, st, ad, mesh.dwall, mesh.s, mode=self.mode)
-        self._warm_f = st.get()
-        self._warm_phi = ad.get()
+        self._drop_warm()
+        self._warm = (self.last["m"], st, ad)     # stays on the device as the next design's warm start
         self.last["adjoint"] = ares
-        ad.close()
         return g / self.q_ref
 
+    def _is_warm(self, obj) -> bool:
+        return self._warm is not None and any(obj is w for w in self._warm)
+
+    def _drop_warm(self):
+        if self._warm is not None:
+            m, st, ad = self._warm
+            self._warm = None
+            for obj in (ad, st, m):
+                if not any(obj is self.last.get(k) for k in ("state", "m")):
+                    obj.close()
+
     def release(self):
+        """Free the last design's state and mesh unless they are kept as the warm start."""
         for k in ("state", "m"):
-            if k in self.last:
+            if k in self.last and not self._is_warm(self.last[k]):
                 self.last[k].close()
         self.last = {}
+
+    def close(self):
+        """Free everything, the warm start included."""
+        self.release()
+        self._drop_warm()
+        self._grid.close()
 
 
 class DragFn(torch.autograd.Function):

@@ -28,6 +28,7 @@ struct dvm_context {
     size_t budget = 0;
     size_t bytes = 0;
     uint64_t launches = 0;
+    uint64_t allocs = 0;        // device allocations made for this context (pool blocks)
     double* pinned = nullptr;   // 64 doubles for small device->host results
     int* derr = nullptr;        // device flag: a kernel's bounded wait ran out
     int flags = 0;
@@ -223,6 +224,7 @@ int dalloc(dvm_context* ctx, T** p, size_t count, size_t* acc = nullptr) {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         g_block_stream[(void*)*p] = ctx->stream;
     }
+    ctx->allocs += 1;
     if (acc) *acc += b;
     return DVM_OK;
 }
@@ -858,6 +860,7 @@ int dvm_selftest_wait_timeout(dvm_context* ctx) {
 
 size_t dvm_context_bytes(const dvm_context* c) { return c ? c->bytes : 0; }
 uint64_t dvm_context_launches(const dvm_context* c) { return c ? c->launches : 0; }
+uint64_t dvm_context_allocations(const dvm_context* c) { return c ? c->allocs : 0; }
 
 // ------------------------------------------------------------------------------------- mesh
 int dvm_mesh_create(dvm_context* ctx, int ni, int nj, const double* X, dvm_mesh** out) {
@@ -1117,6 +1120,40 @@ int dvm_state_get(const dvm_state* st, double* f_host) {
     st->ctx->launches += 1;
     dfree(tmp);
     if (e != cudaSuccess) return fail_cuda(e, "state download");
+    return DVM_OK;
+}
+
+// Shape check shared by the device-to-device copies: same context, cell layout, velocity count and
+// storage.
+static int same_layout(const dvm_state* a, const dvm_state* b) {
+    if (a->ctx != b->ctx) return fail(DVM_ERR_INVALID_ARG, "states of different contexts");
+    if (a->mesh->d.ni != b->mesh->d.ni || a->mesh->d.nj != b->mesh->d.nj)
+        return fail(DVM_ERR_INVALID_ARG, "meshes of different shapes");
+    if (a->grid->d.nv != b->grid->d.nv) return fail(DVM_ERR_INVALID_ARG, "velocity grids of different sizes");
+    if (a->storage != b->storage) return fail(DVM_ERR_INVALID_ARG, "different storage precisions");
+    return DVM_OK;
+}
+
+int dvm_state_copy_from(dvm_state* dst, const dvm_state* src) {
+    if (!dst || !src) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (dst == src) return DVM_OK;
+    int rc = same_layout(dst, src);
+    if (rc) return rc;
+    DeviceGuard dg(dst->ctx->device);
+    const DevMesh& m = dst->mesh->d;
+    const DevGrid& g = dst->grid->d;
+    cudaStream_t s = dst->ctx->stream;
+    const size_t bytes = (size_t)m.ncell * g.nvp * storage_bytes(dst->storage);
+    cudaError_t e = cudaMemcpyAsync(dst->f[dst->cur], src->f[src->cur], bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = launch_moments(dst->storage, dst->f[dst->cur], m, g, dst->prim[dst->cur], dst->Fw[dst->cur], s);
+    dst->ctx->launches += 1;
+    if (e == cudaSuccess && dst->maxwell) {
+        e = launch_maxwell_fit(dst->storage, m, g, dst->prim[dst->cur], dst->fit, false, 8, nullptr, s);
+        dst->ctx->launches += 1;
+    }
+    dst->version += 1;
+    dst->so_phase = 0;
+    if (e != cudaSuccess) return fail_cuda(e, "state copy");
     return DVM_OK;
 }
 
@@ -1521,6 +1558,22 @@ int dvm_adjoint_get(const dvm_adjoint* ad, double* phi_host) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dfree(tmp);
     if (e != cudaSuccess) return fail_cuda(e, "adjoint download");
+    return DVM_OK;
+}
+
+int dvm_adjoint_copy_from(dvm_adjoint* dst, const dvm_adjoint* src) {
+    if (!dst || !src) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (dst == src) return DVM_OK;
+    int rc = same_layout(dst->st, src->st);
+    if (rc) return rc;
+    DeviceGuard dg(dst->st->ctx->device);
+    const DevMesh& m = dst->st->mesh->d;
+    const DevGrid& g = dst->st->grid->d;
+    cudaStream_t s = dst->st->ctx->stream;
+    const size_t bytes = (size_t)m.ncell * g.nvp * storage_bytes(dst->st->storage);
+    cudaError_t e = cudaMemcpyAsync(dst->phi[dst->cur], src->phi[src->cur], bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = refresh_adjoint_couplings(dst);
+    if (e != cudaSuccess) return fail_cuda(e, "adjoint copy");
     return DVM_OK;
 }
 

@@ -325,7 +325,7 @@ def run(ctx: dvm.Context, loop: DesignLoop, storage: str = "fp32", tol: float = 
     try:
         return drive(loop, evaluate)
     finally:
-        prob.release()
+        prob.close()
 
 
 def section_area(ctx: dvm.Context, ni: int, nj: int, alpha) -> float:

@@ -83,6 +83,7 @@ def lib():
             "dvm_context_destroy": (None, [_vp]),
             "dvm_context_bytes": (s, [_vp]),
             "dvm_context_launches": (u64, [_vp]),
+            "dvm_context_allocations": (u64, [_vp]),
             "dvm_selftest_wait_timeout": (i, [_vp]),
             "dvm_status_string": (C.c_char_p, [i]),
             "dvm_last_error": (C.c_char_p, []),
@@ -94,6 +95,7 @@ def lib():
             "dvm_state_destroy": (None, [_vp]),
             "dvm_state_set": (i, [_vp, _dp]),
             "dvm_state_get": (i, [_vp, _dp]),
+            "dvm_state_copy_from": (i, [_vp, _vp]),
             "dvm_state_moments": (i, [_vp, _dp]),
             "dvm_state_set_order": (i, [_vp, i, i]),
             "dvm_state_get_order": (i, [_vp, C.POINTER(i)]),
@@ -107,6 +109,7 @@ def lib():
             "dvm_adjoint_destroy": (None, [_vp]),
             "dvm_adjoint_set": (i, [_vp, _dp]),
             "dvm_adjoint_get": (i, [_vp, _dp]),
+            "dvm_adjoint_copy_from": (i, [_vp, _vp]),
             "dvm_adjoint_iterate": (i, [_vp, i, _dp]),
             "dvm_adjoint_solve": (i, [_vp, _vp, i, C.POINTER(SolveOpts), pp, C.POINTER(AdjointResult)]),
             "dvm_sensitivity": (i, [_vp, _vp, _vp, i, _dp, _dp, i, _dp, _dp]),
@@ -184,6 +187,11 @@ class Context:
     @property
     def launches(self) -> int:
         return lib().dvm_context_launches(self.h)
+
+    @property
+    def allocations(self) -> int:
+        """Device allocations made for this context so far (pool blocks, transient ones included)."""
+        return lib().dvm_context_allocations(self.h)
 
 
 class Mesh:
@@ -268,6 +276,10 @@ class State:
         _check(lib().dvm_state_get(self.h, _p(f)))
         return f
 
+    def copy_from(self, other: "State"):
+        """Device-to-device warm start: f of `other` (same shape and storage) becomes this state's f."""
+        _check(lib().dvm_state_copy_from(self.h, other.h))
+
     def moments(self):
         m = np.empty((self.mesh.ncell, 4))
         _check(lib().dvm_state_moments(self.h, _p(m)))
@@ -347,6 +359,10 @@ class Adjoint:
         phi = np.empty(self.state.shape())
         _check(lib().dvm_adjoint_get(self.h, _p(phi)))
         return phi
+
+    def copy_from(self, other: "Adjoint"):
+        """Device-to-device warm start: phi of `other` (same shape and storage) becomes this adjoint's phi."""
+        _check(lib().dvm_adjoint_copy_from(self.h, other.h))
 
     def iterate(self, n: int):
         r = np.empty(max(n, 1))

@@ -51,15 +51,15 @@ def test_drag_gradient_matches_central_differences_and_the_oracle(ctx):
     # oracle full-discrete sensitivity on the very same state and adjoint
     mesh = prob.last["mesh"]
     pr = O.Problem(mesh.nodes, prob.grid.vx, prob.grid.vy, prob.grid.w, prob.flow.Kn, prob.flow.Ma)
-    f = prob._warm_f
-    phi = prob._warm_phi
+    f = prob._warm[1].get()
+    phi = prob._warm[2].get()
     g_orc = pr.sens_full(f, phi, mesh.dnodes()) / prob.q_ref
     assert np.abs(g_adj - g_orc).max() < 1e-9 * np.abs(g_orc).max()
     g_fd = _fd(prob, a0, h=1e-5)
     assert np.abs(g_adj - g_fd).max() < 1e-6 * np.abs(g_fd).max()
     g_fd4 = _fd(prob, a0, h=1e-4)
     assert np.abs(g_adj - g_fd4).max() < 1e-4 * np.abs(g_fd4).max()
-    prob.release()
+    prob.close()
 
 
 def test_fp32_drag_gradient_within_stated_tolerance(ctx):
@@ -76,5 +76,41 @@ def test_fp32_drag_gradient_within_stated_tolerance(ctx):
     cd32.backward()
     assert abs(cd32.item() - cd64.item()) < 1e-5 * abs(cd64.item())
     assert np.abs(alpha32.grad.numpy() - g64).max() < 1e-4 * np.abs(g64).max()
-    ref.release()
-    p32.release()
+    ref.close()
+    p32.close()
+
+
+def test_device_warm_start_equals_host_round_trip(ctx):
+    """The next design of a DragProblem starts from the last design's f and phi by device-to-device
+    copies (dvm_state_copy_from, dvm_adjoint_copy_from).  Its drag and gradient are bitwise those of
+    the same next design warm-started through the host (download f and phi, upload them into the new
+    state and adjoint): FP32 values survive the round trip through FP64 exactly, and both routes
+    recompute the moments, the wall density and the adjoint couplings with the same kernels."""
+    rng = np.random.default_rng(43)
+    a0 = rng.uniform(-0.005, 0.005, 6)
+    a1 = a0 + rng.uniform(-1e-3, 1e-3, 6)
+    prob = _problem(ctx, "fp32", 1e-6)
+    prob.solve(a0)
+    cold = prob.last["primal"].iters
+    prob.gradient()
+    f_w, phi_w = prob._warm[1].get(), prob._warm[2].get()
+    cd1 = prob.solve(a1)
+    g1 = prob.gradient()
+    assert prob.last["primal"].iters < cold                 # the warm start took
+    fl = prob.flow
+    mesh = W.omesh(48, 16, a1)
+    m = dvm.Mesh(ctx, mesh.nodes)
+    st = dvm.State(ctx, m, prob._grid, fl.Kn, fl.Ma, fl.Tw, fl.aoa, storage="fp32")
+    st.set(f_w)
+    st, res = dvm.primal_solve(ctx, m, prob._grid, fl.Kn, fl.Ma, fl.Tw, fl.aoa, tol=prob.tol,
+                               max_iter=prob.max_iter, storage="fp32", state=st, stall_window=prob.stall_window)
+    ad = dvm.Adjoint(st)
+    ad.set(phi_w)
+    ad, ares = dvm.adjoint_solve(ctx, st, tol=prob.adjoint_tol, max_iter=prob.max_iter, adjoint=ad,
+                                 stall_window=prob.stall_window)
+    g = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    assert res.iters == prob.last["primal"].iters and ares.iters == prob.last["adjoint"].iters
+    assert res.J / prob.q_ref == cd1
+    assert np.array_equal(g / prob.q_ref, g1)
+    ad.close(); st.close(); m.close()
+    prob.close()

@@ -32,13 +32,37 @@ def test_noalloc_sensitivity_matches_allocating_entry_point():
              (W.omesh(32, 10, rng.uniform(-0.01, 0.01, 4)), W.velocity_grid(10, 6.0), 1.0, 1.5)]
     for mesh, grid, Kn, Ma in cases:          # the second case reuses the scratch of the first
         m, g, st, ad = _solved(ctx, mesh, grid, Kn, Ma)
+        # on an adjoint that has never run the allocating entry point (so has no scratch of its own),
+        # the scratch-free calls take no device memory: no allocation, no bytes held
+        allocs, held = ctx.allocations, ctx.bytes
+        first = {mode: dvm.sensitivity(ctx, st, ad, mesh.dwall, sj, mode=mode, node_grad=True, noalloc=True)
+                 for mode, sj in (("full", mesh.s), ("paper", None))}
+        assert ctx.allocations == allocs and ctx.bytes == held
         for mode, sj in (("full", mesh.s), ("paper", None)):
             ref, ref_nodes = dvm.sensitivity(ctx, st, ad, mesh.dwall, sj, mode=mode, node_grad=True)
+            got, nodes = first[mode]
+            assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+            assert np.abs(nodes - ref_nodes).max() <= TOL * np.abs(ref_nodes).max()
             for _ in range(2):                # two calls in a row
+                allocs = ctx.allocations
                 got, nodes = dvm.sensitivity(ctx, st, ad, mesh.dwall, sj, mode=mode, node_grad=True,
                                              noalloc=True)
+                assert ctx.allocations == allocs
                 assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
                 assert np.abs(nodes - ref_nodes).max() <= TOL * np.abs(ref_nodes).max()
+    ctx.close()
+
+
+def test_allocating_sensitivity_moves_the_counter():
+    """Control for the test above: the allocation counter does see the allocating entry point's
+    first call on a fresh adjoint, so an unchanged counter means no allocation."""
+    build.build()
+    ctx = dvm.Context(0)
+    mesh, grid = W.omesh(24, 8, np.zeros(2)), W.velocity_grid(8, 4.0)
+    m, g, st, ad = _solved(ctx, mesh, grid, 1.0, 0.5)
+    allocs = ctx.allocations
+    dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    assert ctx.allocations > allocs
     ctx.close()
 
 
