@@ -353,19 +353,30 @@ def run_serving(args, torch, dvm):
                     f"Kn 1e-3..10, Ma 0.3..2, FP32, primal+adjoint+sensitivity, cap {args.serve_max_iter} "
                     f"sweeps per phase, tol 1e-5"}
     bstream = torch.cuda.Stream()
-    bctx = dvm.Context(torch.cuda.current_device(), graph_iters=20, stream=bstream.cuda_stream)
-    lat, span, res = serve.replay_batched(bctx, specs, arrivals, sweeps_per_tick=20)
-    out["batched"] = serve.latency_stats(lat, span)
-    out["batched"]["converged"] = int(sum(1 for r in res.values() if r["status"] == dvm.DVM_OK))
-    out["batched"]["failed"] = int(sum(1 for r in res.values()
-                                       if r["status"] not in (dvm.DVM_OK, dvm.DVM_NOT_CONVERGED)))
-    bctx.close()
+
+    def batched(arr):
+        bctx = dvm.Context(torch.cuda.current_device(), graph_iters=20, stream=bstream.cuda_stream)
+        lat, span, res, stats = serve.replay_batched(bctx, specs, arr, sweeps_per_tick=20)
+        o = serve.latency_stats(lat, span)
+        o["converged"] = int(sum(1 for r in res.values() if r["status"] == dvm.DVM_OK))
+        o["failed"] = int(sum(1 for r in res.values() if r["status"] not in (dvm.DVM_OK, dvm.DVM_NOT_CONVERGED)))
+        o.update({"ticks": stats["ticks"], "graph_launches": stats["graph_launches"],
+                  "graph_builds": stats["graph_builds"], "table_uploads": stats["table_uploads"],
+                  "peak_resident_requests": stats["peak_active"], "peak_resident_gb": stats["peak_bytes"] / 1e9})
+        bctx.close()
+        return o
+
+    out["batched"] = batched(arrivals)
     sctx = dvm.Context(torch.cuda.current_device(), graphs=False)
-    slat, sspan, sfail = serve.replay_serial(sctx, specs, arrivals)
+    slat, sspan, sfail, sstat = serve.replay_serial(sctx, specs, arrivals)
     out["serial_fp32"] = serve.latency_stats(slat, sspan)
+    out["serial_fp32"]["converged"] = int(sum(1 for v in sstat.values() if v == dvm.DVM_OK))
     out["serial_fp32"]["failed"] = int(sum(1 for v in sfail.values() if v is not None))
     sctx.close()
     out["speedup_solves_per_s"] = out["batched"]["solves_per_s"] / out["serial_fp32"]["solves_per_s"]
+    # capacity: the same requests all submitted at t = 0, so the arrival rate does not bound solves/s
+    out["saturated"] = {"arrivals": "all requests at t = 0", "batched": batched(np.zeros_like(arrivals))}
+    out["saturated"]["speedup_vs_serial"] = out["saturated"]["batched"]["solves_per_s"] / out["serial_fp32"]["solves_per_s"]
     return out
 
 

@@ -107,6 +107,24 @@ typedef struct {
                                f is kept; cells whose mixed moments lose positive density or temperature are left
                                unshifted).  The shift vanishes at a fixed point, so the solution is unchanged.
                                Adjoint solves ignore 1 and mix phi */
+    double refine_tol;      /* primal solves of FP32 states (order 1, plain Maxwellian) only; 0 = off.  > 0: after the
+                               sweeps stop (tolerance, stall window or cap), mixed-precision refinement of the same
+                               discrete problem until the FP64 residual |R(f)|/r0 <= refine_tol.  f is carried as
+                               fbar + delta, two FP32 arrays (fbar the state, delta the exact remainder of each
+                               update).  A correction step takes R(fbar + delta) exactly from one FP64 sweep of
+                               the composed state (its increment s = -R/D), then solves J e = -R for the correction
+                               e by linearised FP32 point-implicit sweeps at fbar + delta (J the Jacobian of R:
+                               upwind transport, the linearised Maxwellian and relaxation rate with lagged moment
+                               couplings, the wall density), until the linear residual falls below a tenth of |R|,
+                               stalls, or refine_sweeps; then delta += e and (fbar, delta) is renormalised by a
+                               two-sum.  Rounding in the FP32 sweeps is relative to e, not to f, so the solution
+                               reaches the FP64 one; the state ends at fl(fbar + delta) and J, Cd and residual of
+                               the result are those of fbar + delta in FP64.  Temporary device memory: an FP64
+                               state and four FP32 arrays of the state's size, freed at the end.  Errors:
+                               DVM_ERR_INVALID_ARG for another storage, order or Maxwellian */
+    int refine_max;         /* correction steps at most (0 -> 20); the refinement also stops (DVM_ERR_STAGNATED)
+                               when a step leaves the FP64 residual above 0.7 of the best so far */
+    int refine_sweeps;      /* linearised FP32 sweeps per correction step at most (0 -> 4000) */
 } dvm_solve_opts;
 
 typedef struct {
@@ -114,8 +132,12 @@ typedef struct {
     double Cd;              /* J / (rho_inf |u_inf|^2 / 2 * chord) */
     double residual;        /* |R| / r0 of the last sweep's input state */
     double r0;              /* |R| of the free-stream state */
-    int iters;              /* sweeps done by this call */
-    int status;             /* dvm_status of the solve */
+    int iters;              /* sweeps done by this call (before any refinement) */
+    int status;             /* dvm_status of the solve (of the refinement when it ran) */
+    int refine_steps;       /* refinement correction steps (FP64 residual evaluations - 1) */
+    int refine_sweeps;      /* linearised FP32 sweeps of the refinement */
+    double residual_fp32;   /* |R|/r0 of the FP32 sweeps when they stopped (= residual without refinement) */
+    double residual_fp64;   /* refinement: the FP64 residual |R|/r0 of the state the FP32 sweeps left */
 } dvm_primal_result;
 
 typedef struct {
@@ -239,6 +261,37 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
                      const dvm_flow* flow, const dvm_solve_opts* opts, int storage,
                      dvm_state** inout, dvm_primal_result* out);
 
+/* ------------------------------------------------------------------------ velocity shards */
+/* One steady primal solve split over velocity space (each GPU holds every cell for a slice of the
+ * velocity grid).  The point-implicit sweep of Eq. (numerpr_gov) couples velocities only through
+ * velocity sums: the cell moments W of Eq. (macint_reduce) that give g and tau, the wall density
+ * F_rhow of Eq. (formula_bgk_fdw), the normaliser D_l of Eq. (barg), the drag of Eq. (numer_J) and
+ * the residual norm.  A shard is a state created on its slice (a dvm_vgrid of those velocities) with
+ * the common mesh and flow; its sweeps write the slice's partial sums instead of finishing them, the
+ * caller adds the shards' buffers (an all-reduce across GPUs, or a sum on one device), and each shard
+ * installs the total before its next sweep.  The totals equal those of the whole grid up to the order
+ * of the additions, so the shards together follow the unsplit sweeps.
+ * Buffer layout (doubles, dvm_state_shard_count of them): [4 ncell] the sums (w f1, w f1 vx, w f1 vy,
+ * w (f1 |v|^2/2 + f2)) per cell; [ncell] the residual sums w (R/V)^2; [ni] F_rhow; [ni] the outflow
+ * part of the drag; [ni] D_l; [ni] M_l D_l of the drag direction.  Per sweep that is
+ * 8 (5 ncell + 4 ni) bytes to all-reduce.
+ * dvm_state_set_shard(st, 1): first-order states with the plain Maxwellian only; fills the buffer
+ *   from the current f (moments, F_rhow and the slice's D_l, M_l D_l; residual and drag entries 0).
+ *   Allocates two buffers of the count (HBM budget).  (st, 0) returns the state to a grid of its own.
+ * dvm_state_shard_partials: copy the buffer to `out` (host or device memory, count doubles).
+ * dvm_state_shard_combine: install the summed buffer `total` (host or device memory): the primitive
+ *   variables and F_rhow of the whole grid for the next sweep, and D_l, M_l of the whole grid; returns
+ *   the residual sum sum w (R/V)^2 of the last sweep's input (0 after dvm_state_set_shard) and the drag
+ *   of the current f (its outflow part as summed; meaningful after a sweep).
+ * dvm_primal_iterate on a shard takes n = 1 (residual_out receives NaN).  dvm_primal_solve, adjoints,
+ * order 2 and the conservative Maxwellian are refused on shards (DVM_ERR_INVALID_ARG).
+ * Errors: DVM_ERR_INVALID_ARG (NULL, not a shard, wrong count), DVM_ERR_OOM, DVM_ERR_ADMISSION,
+ * DVM_ERR_CUDA. */
+int dvm_state_set_shard(dvm_state* st, int on);
+size_t dvm_state_shard_count(const dvm_state* st);
+int dvm_state_shard_partials(const dvm_state* st, double* out, size_t count);
+int dvm_state_shard_combine(dvm_state* st, const double* total, size_t count, double* residual_sq, double* J);
+
 /* ------------------------------------------------------------------------ adjoint, B5 */
 /* Allocate the adjoint phi of `st` (same storage), zero it, linearised at the state's current f.
  * The state must not change while the adjoint is used. */
@@ -284,7 +337,10 @@ int dvm_volume_constraint(dvm_context* ctx, const dvm_mesh* mesh, double v_min, 
  * context.  Requests are admitted in arrival order while their device footprint fits the batch's
  * HBM budget; every tick advances each admitted request by `sweeps_per_tick` point-implicit
  * sweeps of its current phase in one batched launch per sweep (all requests of the tick share the
- * launch), then checks convergence; a converged primal moves to its adjoint, a converged adjoint to
+ * launch; the launches read their work lists and counts from device tables of fixed capacity, so the
+ * tick's sweeps, reductions and read-back are one captured CUDA graph, re-captured only when a table
+ * outgrows its capacity, and the tables are re-uploaded only when the admitted set changes), then
+ * checks convergence; a converged primal moves to its adjoint, a converged adjoint to
  * its sensitivity, and the request retires, freeing its memory.  Requests that arrive while others
  * run are admitted at the next tick.  A request's result does not depend on what else is in the
  * batch (same kernels, same per-request arithmetic, fixed reduction order).
@@ -329,6 +385,17 @@ typedef struct {
     int warm_started;
 } dvm_request_result;
 
+/* Counters of a batch since creation: */
+typedef struct {
+    uint64_t ticks;             /* ticks that ran sweeps */
+    uint64_t graph_launches;    /* ticks whose sweeps, reductions and read-back ran as one CUDA-graph launch */
+    uint64_t graph_builds;      /* captures of that graph: the first tick, and a table outgrowing its capacity */
+    uint64_t table_uploads;     /* ticks that rebuilt and uploaded the descriptor tables (the admitted set or a
+                                   request's phase changed); other ticks reuse the tables on the device */
+    int peak_active;            /* most requests admitted at once */
+    size_t peak_bytes;          /* most device memory held by admitted requests and the warm cache (footprints) */
+} dvm_batch_stats;
+
 int dvm_batch_create(dvm_context* ctx, const dvm_batch_options* opt, dvm_batch** out);
 /* Frees every request and the cache.  Destroy a batch before its context. */
 void dvm_batch_destroy(dvm_batch* b);
@@ -340,6 +407,8 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued);
 /* Result of a request; grad_out (optional, [n_params]) receives dJ/dalpha once retired.  A retired
  * request is forgotten after it has been polled with forget = 1. */
 int dvm_batch_poll(dvm_batch* b, uint64_t ticket, dvm_request_result* out, double* grad_out, int forget);
+/* Copy the batch's counters.  Errors: DVM_ERR_INVALID_ARG (NULL). */
+int dvm_batch_get_stats(const dvm_batch* b, dvm_batch_stats* out);
 
 /* Same result as dvm_sensitivity, for callers that must not allocate device memory during the
  * call (e.g. a serving loop whose device memory is reserved once, up front, by another allocator,

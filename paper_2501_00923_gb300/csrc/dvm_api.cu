@@ -95,6 +95,9 @@ struct dvm_state {
     double4* fit = nullptr;     // its parameters for the current f
     AAState* aaW = nullptr;     // moment-space mixing: history over the cell moments
     double* Wbuf = nullptr;     // [ncell][4] FP64 moments
+    int shard = 0;              // 1: a velocity shard (sweeps write partial sums; see dvm_state_set_shard)
+    double* part = nullptr;     // [shard_count] this shard's partial sums
+    double* part_total = nullptr;   // [shard_count] the summed buffer of all shards
 };
 
 struct dvm_adjoint {
@@ -322,6 +325,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     a.respart = st->respart;
     a.err = st->ctx->derr;
     a.defect = st->order == 2 ? (const TS*)st->so[2] : nullptr;
+    a.part = st->shard ? st->part : nullptr;
     return a;
 }
 
@@ -426,10 +430,11 @@ cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
         if (e != cudaSuccess) return e;
     }
     cudaError_t e;
+    auto launch = st->shard ? launch_primal_shard_sweep : launch_primal_sweep;
     switch (st->storage) {
-        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); e = launch_primal_sweep(0, &a, st->maps[src], res, st->ctx->stream); break; }
-        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); e = launch_primal_sweep(1, &a, st->maps[src], res, st->ctx->stream); break; }
-        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); e = launch_primal_sweep(2, &a, st->maps[src], res, st->ctx->stream); break; }
+        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); e = launch(0, &a, st->maps[src], res, st->ctx->stream); break; }
+        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); e = launch(1, &a, st->maps[src], res, st->ctx->stream); break; }
+        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); e = launch(2, &a, st->maps[src], res, st->ctx->stream); break; }
     }
     if (e == cudaSuccess && st->maxwell) {
         // the next sweep's Maxwellian: one Newton step from the previous fit
@@ -671,6 +676,8 @@ int check_solve_opts(const dvm_solve_opts* o) {
     if (o->accel_depth < 0 || o->accel_depth > aa_max_depth() || (o->accel_depth > 0 && o->accel_period < 1))
         return fail(DVM_ERR_INVALID_ARG, "accel_depth must be in [0, 8] and accel_period >= 1");
     if (o->accel_space != 0 && o->accel_space != 1) return fail(DVM_ERR_INVALID_ARG, "accel_space must be 0 or 1");
+    if (!(o->refine_tol >= 0.0) || o->refine_max < 0 || o->refine_sweeps < 0)
+        return fail(DVM_ERR_INVALID_ARG, "refine_tol, refine_max and refine_sweeps must be >= 0");
     return DVM_OK;
 }
 
@@ -997,6 +1004,8 @@ void dvm_state_destroy(dvm_state* st) {
     aa_free(st->ctx, st->aa);
     aa_free(st->ctx, st->aaW);
     dfree(st->Wbuf);
+    dfree(st->part);
+    dfree(st->part_total);
     st->ctx->bytes -= st->bytes;
     delete st;
 }
@@ -1168,6 +1177,7 @@ int dvm_state_moments(const dvm_state* st, double* prim_host) {
 
 int dvm_state_set_order(dvm_state* st, int order, int defect_period) {
     if (!st) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (st->shard && order != 1) return fail(DVM_ERR_INVALID_ARG, "velocity shards are first order");
     if (order != 1 && order != 2) return fail(DVM_ERR_INVALID_ARG, "order must be 1 or 2");
     if (defect_period < 0) return fail(DVM_ERR_INVALID_ARG, "defect_period must be >= 0");
     if (order == 2 && !st->so[0]) {
@@ -1227,6 +1237,7 @@ int dvm_state_get_order(const dvm_state* st, int* order) {
 
 int dvm_state_set_maxwellian(dvm_state* st, int kind) {
     if (!st) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (st->shard && kind != DVM_MAXWELL_PLAIN) return fail(DVM_ERR_INVALID_ARG, "velocity shards use the plain Maxwellian");
     if (kind != DVM_MAXWELL_PLAIN && kind != DVM_MAXWELL_CONSERVATIVE) return fail(DVM_ERR_INVALID_ARG, "unknown Maxwellian");
     dvm_context* ctx = st->ctx;
     DeviceGuard dg(ctx->device);
@@ -1261,6 +1272,16 @@ int dvm_primal_iterate(dvm_state* st, int n, double* residual_out) {
     if (!st || n < 0) return fail(DVM_ERR_INVALID_ARG, "bad argument");
     if (n == 0) return DVM_OK;
     DeviceGuard dg(st->ctx->device);
+    if (st->shard) {              // one sweep into the partial sums; the caller combines the shards
+        if (n != 1) return fail(DVM_ERR_INVALID_ARG, "a velocity shard sweeps once between combinations");
+        CK(enqueue_primal(st, st->cur, true));
+        st->cur = 1 - st->cur;
+        st->version += 1;
+        st->ctx->launches += 1;
+        CK(cudaStreamSynchronize(st->ctx->stream));
+        if (residual_out) residual_out[0] = NAN;
+        return check_device_flag(st->ctx);
+    }
     double* hist = nullptr;
     int rc = dalloc(st->ctx, &hist, 2 * (size_t)n);
     if (rc) return rc;
@@ -1296,6 +1317,207 @@ int dvm_state_functional(dvm_state* st, int functional, double* J) {
     return DVM_OK;
 }
 
+// ---------------------------------------------------------------- mixed-precision refinement
+// f = fbar + delta (fbar: the FP32 state, delta: an FP32 remainder).  Each correction step takes the
+// exact residual R(fbar + delta) from one FP64 sweep of the composed state (increment s = -R/D), solves
+// J e = -R by linearised FP32 sweeps (k_primal_lin_sweep) and adds e to delta, renormalised into fbar.
+namespace {
+
+struct RefineWork {
+    dvm_context* ctx = nullptr;
+    dvm_state* s64 = nullptr;
+    float* delta = nullptr;
+    float* e[2] = {nullptr, nullptr};
+    float* src = nullptr;
+    double4* dW[2] = {nullptr, nullptr};
+    double* dF[2] = {nullptr, nullptr};
+    double* Jp = nullptr;
+    double* rp = nullptr;
+    double* out = nullptr;
+    TmaMaps maps[2];
+    ~RefineWork() {
+        if (ctx) cudaStreamSynchronize(ctx->stream);
+        for (int b = 0; b < 2; ++b) { dfree(e[b]); dfree(dW[b]); dfree(dF[b]); }
+        dfree(delta); dfree(src); dfree(Jp); dfree(rp); dfree(out);
+        if (s64) dvm_state_destroy(s64);
+    }
+};
+
+int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res) {
+    if (st->storage != DVM_STORE_FP32 || st->order != 1 || st->maxwell)
+        return fail(DVM_ERR_INVALID_ARG, "refinement needs an FP32 state of order 1 with the plain Maxwellian");
+    Range nvtx("dvm_primal_refine");
+    dvm_context* ctx = st->ctx;
+    cudaStream_t s = ctx->stream;
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    const size_t nf = (size_t)m.ncell * g.nvp * 2;       // floats of one FP32 state buffer
+    RefineWork W;
+    W.ctx = ctx;
+    int rc = dvm_state_create(ctx, st->mesh, st->grid, &st->flow, DVM_STORE_FP64, &W.s64);
+    if (rc) return rc;
+    dvm_state* s64 = W.s64;
+    if ((rc = dalloc(ctx, &W.delta, nf)) || (rc = dalloc(ctx, &W.src, nf)) || (rc = dalloc(ctx, &W.Jp, m.ni)) ||
+        (rc = dalloc(ctx, &W.rp, m.ncell)) || (rc = dalloc(ctx, &W.out, 2)))
+        return rc;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dalloc(ctx, &W.e[b], nf)) || (rc = dalloc(ctx, &W.dW[b], m.ncell)) || (rc = dalloc(ctx, &W.dF[b], m.ni)))
+            return rc;
+        CK(make_tmamaps(W.e[b], m.ni, m.nj, g.nvp / 2, &W.maps[b]));
+    }
+    CK(cudaMemsetAsync(W.delta, 0, nf * sizeof(float), s));
+    const int max_steps = o->refine_max > 0 ? o->refine_max : 20;
+    const int max_sweeps = o->refine_sweeps > 0 ? o->refine_sweeps : 4000;
+    constexpr int kBlock = 20;             // linearised sweeps between residual checks
+    double r64 = INFINITY, best = INFINITY, J64 = 0.0;
+    int steps = 0, sweeps = 0, status = DVM_NOT_CONVERGED;
+    float* fbar = static_cast<float*>(st->f[st->cur]);
+    for (;;) {
+        // exact residual of fbar + delta: compose it in the FP64 state and sweep that once
+        const int c64 = s64->cur;
+        CK(launch_refine_compose(fbar, W.delta, static_cast<double*>(s64->f[c64]), m.ncell, g.nvp, s));
+        CK(launch_moments(DVM_STORE_FP64, s64->f[c64], m, g, s64->prim[c64], s64->Fw[c64], s));
+        ctx->launches += 2;
+        s64->version += 1;
+        if ((rc = dvm_state_functional(s64, DVM_DRAG, &J64))) return rc;
+        CK(enqueue_primal(s64, c64, true));
+        CK(enqueue_primal_finalize(s64, 1 - c64, s64->out));
+        ctx->launches += 2;
+        double ro[2];
+        if ((rc = fetch2(ctx, s64->out, ro))) return rc;
+        r64 = sqrt(ro[0]) / st->r0;
+        if (steps == 0) res->residual_fp64 = r64;
+        if (!std::isfinite(r64) || !std::isfinite(J64)) { status = fail(DVM_ERR_NONFINITE, "refinement residual is not finite"); break; }
+        if (r64 <= o->refine_tol) { status = DVM_OK; break; }
+        if (steps >= max_steps) { status = DVM_NOT_CONVERGED; break; }
+        if (r64 > 0.7 * best) { status = DVM_ERR_STAGNATED; break; }
+        best = r64;
+        // s = -R/D from that sweep; e solves J e = -R by linearised sweeps from e = 0
+        CK(launch_refine_diff(static_cast<const double*>(s64->f[1 - c64]), static_cast<const double*>(s64->f[c64]),
+                              W.src, m.ncell, g.nvp, s));
+        CK(cudaMemsetAsync(W.e[0], 0, nf * sizeof(float), s));
+        CK(cudaMemsetAsync(W.dW[0], 0, m.ncell * sizeof(double4), s));
+        CK(cudaMemsetAsync(W.dF[0], 0, m.ni * sizeof(double), s));
+        ctx->launches += 1;
+        int ec = 0, n = 0, best_n = 0;
+        const double target = 0.1 * r64 * st->r0;
+        double rin_best = INFINITY;
+        while (n < max_sweeps) {
+            const int k = std::min(kBlock, max_sweeps - n);
+            for (int i = 0; i < k; ++i) {
+                PrimalArgs<float, float> a = primal_args<float, float>(st, st->cur);
+                a.f_old = W.e[ec]; a.f_new = W.e[1 - ec];
+                a.prim_old = a.maxw_old = s64->prim[c64];
+                a.prim_new = nullptr;
+                a.Fw_old = W.dF[ec]; a.Fw_new = W.dF[1 - ec];
+                a.Jpart = W.Jp; a.respart = W.rp;
+                a.defect = nullptr;
+                a.lin_src = W.src; a.lin_f = fbar;
+                a.dW_old = W.dW[ec]; a.dW_new = W.dW[1 - ec];
+                CK(launch_primal_lin_sweep(&a, W.maps[ec], i == k - 1, s));
+                ec = 1 - ec;
+            }
+            CK(launch_finalize(W.rp, m.ncell, nullptr, nullptr, nullptr, m.ni, W.out, s));
+            ctx->launches += k + 1;
+            n += k;
+            double lo[2];
+            if ((rc = fetch2(ctx, W.out, lo))) return rc;
+            const double rin = sqrt(lo[0]);
+            if (!std::isfinite(rin)) return fail(DVM_ERR_NONFINITE, "refinement correction is not finite");
+            if (rin <= target) break;
+            if (rin < 0.98 * rin_best) { rin_best = rin; best_n = n; }
+            if (n - best_n >= 30 * kBlock) break;      // the linear sweeps stalled
+        }
+        CK(launch_refine_update(fbar, W.delta, W.e[ec], nf, s));
+        ctx->launches += 1;
+        steps += 1;
+        sweeps += n;
+    }
+    // the state holds fl(fbar + delta): its moments and wall density follow it
+    CK(launch_moments(st->storage, st->f[st->cur], m, g, st->prim[st->cur], st->Fw[st->cur], s));
+    ctx->launches += 1;
+    st->version += 1;
+    res->J = J64;
+    const double U = st->flow.Ma * sqrt(5.0 / 3.0);
+    res->Cd = U > 0.0 ? J64 / (0.5 * U * U) : J64;
+    res->residual = r64;
+    res->refine_steps = steps;
+    res->refine_sweeps = sweeps;
+    res->status = status;
+    return status;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ velocity shards
+int dvm_state_set_shard(dvm_state* st, int on) {
+    if (!st || (on != 0 && on != 1)) return fail(DVM_ERR_INVALID_ARG, "bad argument");
+    DeviceGuard dg(st->ctx->device);
+    dvm_context* ctx = st->ctx;
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    cudaStream_t s = ctx->stream;
+    if (on) {
+        if (st->order != 1 || st->maxwell)
+            return fail(DVM_ERR_INVALID_ARG, "velocity shards take first-order states with the plain Maxwellian");
+        const size_t n = shard_count(m.ncell, m.ni);
+        if (!st->part) {
+            size_t acc = 0;
+            int rc;
+            if ((rc = dalloc(ctx, &st->part, n, &acc)) || (rc = dalloc(ctx, &st->part_total, n, &acc))) return rc;
+            st->bytes += acc;
+            ctx->bytes += acc;
+        }
+        CK(launch_shard_moments(st->storage, st->f[st->cur], m, g, st->part, s));
+        CK(launch_wall_setup(m, g, st->fl, moment_of(st->flow, DVM_DRAG), st->part + 5 * (size_t)m.ncell + 2 * m.ni,
+                             st->part + 5 * (size_t)m.ncell + 3 * m.ni, s, true));
+        ctx->launches += 2;
+    } else if (st->shard) {        // back to a whole grid of its own: its own wall constants and moments
+        CK(launch_wall_setup(m, g, st->fl, moment_of(st->flow, DVM_DRAG), st->fl.wallD, st->fl.wallM, s));
+        CK(launch_moments(st->storage, st->f[st->cur], m, g, st->prim[st->cur], st->Fw[st->cur], s));
+        ctx->launches += 2;
+        st->version += 1;
+    }
+    st->shard = on;
+    CK(cudaStreamSynchronize(s));
+    return DVM_OK;
+}
+
+size_t dvm_state_shard_count(const dvm_state* st) {
+    return st ? shard_count(st->mesh->d.ncell, st->mesh->d.ni) : 0;
+}
+
+int dvm_state_shard_partials(const dvm_state* st, double* out, size_t count) {
+    if (!st || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (!st->shard) return fail(DVM_ERR_INVALID_ARG, "not a velocity shard");
+    if (count != shard_count(st->mesh->d.ncell, st->mesh->d.ni)) return fail(DVM_ERR_INVALID_ARG, "wrong count");
+    DeviceGuard dg(st->ctx->device);
+    CK(cudaMemcpyAsync(out, st->part, count * sizeof(double), cudaMemcpyDefault, st->ctx->stream));
+    CK(cudaStreamSynchronize(st->ctx->stream));
+    return DVM_OK;
+}
+
+int dvm_state_shard_combine(dvm_state* st, const double* total, size_t count, double* residual_sq, double* J) {
+    if (!st || !total) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (!st->shard) return fail(DVM_ERR_INVALID_ARG, "not a velocity shard");
+    const DevMesh& m = st->mesh->d;
+    if (count != shard_count(m.ncell, m.ni)) return fail(DVM_ERR_INVALID_ARG, "wrong count");
+    DeviceGuard dg(st->ctx->device);
+    cudaStream_t s = st->ctx->stream;
+    CK(cudaMemcpyAsync(st->part_total, total, count * sizeof(double), cudaMemcpyDefault, s));
+    CK(launch_shard_combine(m, st->part_total, st->prim[st->cur], st->Fw[st->cur], st->respart, st->Jpart,
+                            st->fl.wallD, st->fl.wallM, s));
+    CK(enqueue_primal_finalize(st, st->cur, st->out));
+    st->ctx->launches += 2;
+    st->version += 1;
+    double r[2];
+    int rc = fetch2(st->ctx, st->out, r);
+    if (rc) return rc;
+    if (residual_sq) *residual_sq = r[0];
+    if (J) *J = r[1];
+    return DVM_OK;
+}
+
 int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* grid, const dvm_flow* flow,
                      const dvm_solve_opts* opts, int storage, dvm_state** inout, dvm_primal_result* res) {
     if (!ctx || !mesh || !grid || !flow || !opts || !inout || !res) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
@@ -1315,6 +1537,9 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
             return fail(DVM_ERR_INVALID_ARG, "warm-start state has another flow; create a new state");
     }
     dvm_state* st = *inout;
+    if (st->shard) return fail(DVM_ERR_INVALID_ARG, "a velocity shard is swept with dvm_primal_iterate and combined");
+    if (opts->refine_tol > 0.0 && (st->storage != DVM_STORE_FP32 || st->order != 1 || st->maxwell))
+        return fail(DVM_ERR_INVALID_ARG, "refinement needs an FP32 state of order 1 with the plain Maxwellian");
     const bool accel = opts->accel_depth > 0;
     const int K = accel ? opts->accel_period : ctx->graph_iters;
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
@@ -1426,9 +1651,11 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     const double U = flow->Ma * sqrt(5.0 / 3.0);
     res->Cd = U > 0.0 ? J / (0.5 * U * U) : J;
     res->residual = r;
+    res->residual_fp32 = r;
     res->r0 = st->r0;
     res->iters = it;
     res->status = status;
+    if (opts->refine_tol > 0.0 && status != DVM_ERR_NONFINITE) return refine_primal(st, opts, res);
     return status;
 }
 
@@ -1461,6 +1688,7 @@ static int adjoint_reset(dvm_adjoint* ad) {
 
 int dvm_adjoint_create(dvm_state* st, int functional, dvm_adjoint** out) {
     if (!st || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    if (st->shard) return fail(DVM_ERR_INVALID_ARG, "adjoints of velocity shards are not provided");
     if (functional < DVM_DRAG || functional > DVM_HEAT) return fail(DVM_ERR_INVALID_ARG, "unknown functional");
     *out = nullptr;
     dvm_context* ctx = st->ctx;
@@ -1946,31 +2174,39 @@ struct dvm_batch {
     std::vector<BatchReq*> active;
     std::unordered_map<uint64_t, BatchReq*> all;
     std::vector<WarmEntry> cache;
-    void* pdesc[3] = {nullptr, nullptr, nullptr};
-    size_t pdesc_cap[3] = {0, 0, 0};
-    void* adesc[3] = {nullptr, nullptr, nullptr};
-    size_t adesc_cap[3] = {0, 0, 0};
+    // Device tables of the admitted set, in six segments k = 2 storage + (0 primal, 1 adjoint): work
+    // items and descriptors per segment, a finalize descriptor and two results per request, and the
+    // counts in use.  Capacities only grow, so the launches of a tick (grids of the capacities, counts
+    // read from the device) keep their shape, and one captured graph serves every tick until a table
+    // outgrows its capacity.
+    int cap_items[6] = {0, 0, 0, 0, 0, 0};
+    int cap_desc[6] = {0, 0, 0, 0, 0, 0};
+    int cap_act = 0;
+    size_t item_off[6] = {0, 0, 0, 0, 0, 0};
     int4* items = nullptr;
-    size_t items_cap = 0;
+    void* desc[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     FinalizeDesc* fdesc = nullptr;
-    size_t fdesc_cap = 0;
     double* dout = nullptr;
-    size_t dout_cap = 0;
-    unsigned char* host = nullptr;   // pinned staging
+    int* counts = nullptr;           // [8]: items in use per segment, then the requests in use
+    double* hout = nullptr;          // pinned [2 cap_act]: the results the tick reads back
+    unsigned char* host = nullptr;   // pinned staging of the tables
     size_t host_cap = 0;
+    std::vector<uint64_t> sig;       // (ticket, phase) of the admitted set whose tables are on the device
+    cudaGraphExec_t graph = nullptr;
+    int graph_M = 0;
+    bool graph_stale = true;
+    dvm_batch_stats stats{};
 };
 
 namespace {
 
+// Replace a device table by one of `bytes` (its contents are rewritten before the next use).
 template <class T>
-int grow_device(T** p, size_t* cap, size_t bytes) {
-    if (bytes <= *cap) return DVM_OK;
-    dfree(*p);
+int realloc_device(T** p, size_t bytes) {
+    if (*p) cudaFree(*p);
     *p = nullptr;
-    size_t nb = std::max(bytes, *cap * 2);
-    cudaError_t e = cudaMalloc((void**)p, nb);
-    if (e != cudaSuccess) { *cap = 0; return fail_cuda(e, "batch table"); }
-    *cap = nb;
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 64));
+    if (e != cudaSuccess) return fail_cuda(e, "batch table");
     return DVM_OK;
 }
 
@@ -2127,8 +2363,13 @@ void dvm_batch_destroy(dvm_batch* b) {
         delete q;
     }
     for (auto& e : b->cache) destroy_objects(e.ad, e.st, e.grid, e.mesh);
-    for (int s = 0; s < 3; ++s) { dfree(b->pdesc[s]); dfree(b->adesc[s]); }
-    dfree(b->items); dfree(b->fdesc); dfree(b->dout);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int k = 0; k < 6; ++k) if (b->desc[k]) cudaFree(b->desc[k]);
+    if (b->items) cudaFree(b->items);
+    if (b->fdesc) cudaFree(b->fdesc);
+    if (b->dout) cudaFree(b->dout);
+    if (b->counts) cudaFree(b->counts);
+    if (b->hout) cudaFreeHost(b->hout);
     if (b->host) cudaFreeHost(b->host);
     delete b;
 }
@@ -2194,96 +2435,159 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
         }
         b->active.push_back(q);
     }
-    // 2. work lists and descriptors, per storage type and phase
-    std::vector<BatchReq*> plist[3], alist[3];
-    for (BatchReq* q : b->active) (q->phase == 1 ? plist : alist)[q->r.storage].push_back(q);
-    size_t n_items = 0;
-    std::vector<size_t> pitem0(3), pitemn(3), aitem0(3), aitemn(3);
-    for (int s = 0; s < 3; ++s) {
-        pitem0[s] = n_items;
-        for (BatchReq* q : plist[s]) n_items += (size_t)q->r.ni * ((q->r.nj + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        pitemn[s] = n_items - pitem0[s];
-        aitem0[s] = n_items;
-        for (BatchReq* q : alist[s]) n_items += (size_t)q->r.ni * ((q->r.nj + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        aitemn[s] = n_items - aitem0[s];
-    }
+    // 2. the admitted set in six segments (storage, phase); tables grow to fit it
+    std::vector<BatchReq*> seg[6];
+    for (BatchReq* q : b->active) seg[2 * q->r.storage + (q->phase == 1 ? 0 : 1)].push_back(q);
     const size_t nact = b->active.size();
-    size_t off_p[3], off_a[3], host_bytes = 0;
-    for (int s = 0; s < 3; ++s) {
-        off_p[s] = host_bytes;
-        host_bytes = align_up(host_bytes + plist[s].size() * pdesc_size(s), 128);
-        off_a[s] = host_bytes;
-        host_bytes = align_up(host_bytes + alist[s].size() * adesc_size(s), 128);
-    }
-    const size_t off_items = host_bytes;
-    host_bytes = align_up(host_bytes + n_items * sizeof(int4), 128);
-    const size_t off_fd = host_bytes;
-    host_bytes = align_up(host_bytes + nact * sizeof(FinalizeDesc), 128);
-    const size_t off_out = host_bytes;
-    host_bytes += 2 * nact * sizeof(double) + 64;
+    b->stats.peak_active = std::max(b->stats.peak_active, (int)nact);
+    b->stats.peak_bytes = std::max(b->stats.peak_bytes, b->used);
     if (nact > 0) {
-        if ((rc = grow_host(b, host_bytes))) return rc;
-        int4* hitems = reinterpret_cast<int4*>(b->host + off_items);
-        size_t it = 0;
-        for (int s = 0; s < 3; ++s) {
-            for (size_t r = 0; r < plist[s].size(); ++r) {
-                dvm_state* st = plist[s][r]->st;
-                unsigned char* d = b->host + off_p[s] + r * pdesc_size(s);
-                if (s == 0) fill_primal_desc(reinterpret_cast<PrimalBatchDesc<double>*>(d), st);
-                else if (s == 1) fill_primal_desc(reinterpret_cast<PrimalBatchDesc<float>*>(d), st);
-                else fill_primal_desc(reinterpret_cast<PrimalBatchDesc<__nv_bfloat16>*>(d), st);
-                for (int i = 0; i < st->mesh->d.ni; ++i)
-                    for (int j0 = 0; j0 < st->mesh->d.nj; j0 += kWarpsPerBlock) hitems[it++] = int4{(int)r, i, j0, 0};
-            }
-            for (size_t r = 0; r < alist[s].size(); ++r) {
-                dvm_adjoint* ad = alist[s][r]->ad;
-                unsigned char* d = b->host + off_a[s] + r * adesc_size(s);
-                if (s == 0) fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<double>*>(d), ad);
-                else if (s == 1) fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<float>*>(d), ad);
-                else fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<__nv_bfloat16>*>(d), ad);
-                const DevMesh& m = ad->st->mesh->d;
-                for (int i = 0; i < m.ni; ++i)
-                    for (int j0 = 0; j0 < m.nj; j0 += kWarpsPerBlock) hitems[it++] = int4{(int)r, i, j0, 0};
-            }
-        }
-        FinalizeDesc* hfd = reinterpret_cast<FinalizeDesc*>(b->host + off_fd);
-        for (size_t k = 0; k < nact; ++k) {
-            BatchReq* q = b->active[k];
-            const DevMesh& m = q->st->mesh->d;
-            if (q->phase == 1) hfd[k] = FinalizeDesc{q->st->respart, m.ncell, m.ni, q->st->Jpart, q->st->Fw[q->st->cur], q->st->fl.wallM};
-            else hfd[k] = FinalizeDesc{q->ad->respart, m.ncell, m.ni, nullptr, nullptr, nullptr};
-        }
-        for (int s = 0; s < 3; ++s) {
-            if ((rc = grow_device((unsigned char**)&b->pdesc[s], &b->pdesc_cap[s], plist[s].size() * pdesc_size(s) + 64)) ||
-                (rc = grow_device((unsigned char**)&b->adesc[s], &b->adesc_cap[s], alist[s].size() * adesc_size(s) + 64)))
-                return rc;
-        }
-        if ((rc = grow_device(&b->items, &b->items_cap, n_items * sizeof(int4) + 16)) ||
-            (rc = grow_device(&b->fdesc, &b->fdesc_cap, nact * sizeof(FinalizeDesc))) ||
-            (rc = grow_device(&b->dout, &b->dout_cap, 2 * nact * sizeof(double))))
-            return rc;
         cudaStream_t s = ctx->stream;
-        for (int t = 0; t < 3; ++t) {
-            if (!plist[t].empty()) CK(cudaMemcpyAsync(b->pdesc[t], b->host + off_p[t], plist[t].size() * pdesc_size(t), cudaMemcpyHostToDevice, s));
-            if (!alist[t].empty()) CK(cudaMemcpyAsync(b->adesc[t], b->host + off_a[t], alist[t].size() * adesc_size(t), cudaMemcpyHostToDevice, s));
-        }
-        CK(cudaMemcpyAsync(b->items, hitems, n_items * sizeof(int4), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(b->fdesc, hfd, nact * sizeof(FinalizeDesc), cudaMemcpyHostToDevice, s));
-        // 3. M sweeps of every active request, one batched launch per storage type and phase
-        for (int sw = 0; sw < M; ++sw) {
-            const bool res = sw == M - 1;
-            for (int t = 0; t < 3; ++t) {
-                CK(launch_primal_sweep_batch(t, b->pdesc[t], b->items + pitem0[t], (int)pitemn[t], sw & 1, res, s));
-                CK(launch_adjoint_sweep_batch(t, b->adesc[t], b->items + aitem0[t], (int)aitemn[t], sw & 1, res, s));
-                ctx->launches += (pitemn[t] > 0) + (aitemn[t] > 0);
+        size_t need[6];
+        bool grown_items = false;
+        for (int k = 0; k < 6; ++k) {
+            need[k] = 0;
+            for (BatchReq* q : seg[k]) need[k] += (size_t)q->r.ni * ((q->r.nj + kWarpsPerBlock - 1) / kWarpsPerBlock);
+            if ((int)need[k] > b->cap_items[k]) {
+                b->cap_items[k] = (int)std::max<size_t>(need[k], std::max(2 * (size_t)b->cap_items[k], (size_t)256));
+                grown_items = true;
+            }
+            if ((int)seg[k].size() > b->cap_desc[k]) {
+                b->cap_desc[k] = std::max((int)seg[k].size(), std::max(2 * b->cap_desc[k], 4));
+                const size_t dsz = (k & 1) ? adesc_size(k / 2) : pdesc_size(k / 2);
+                if ((rc = realloc_device((unsigned char**)&b->desc[k], b->cap_desc[k] * dsz))) return rc;
+                b->graph_stale = true;
             }
         }
-        CK(launch_finalize_batch(b->fdesc, (int)nact, b->dout, s));
-        ctx->launches += 1;
-        double* hout = reinterpret_cast<double*>(b->host + off_out);
-        CK(cudaMemcpyAsync(hout, b->dout, 2 * nact * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (grown_items) {
+            size_t tot = 0;
+            for (int k = 0; k < 6; ++k) { b->item_off[k] = tot; tot += (size_t)b->cap_items[k]; }
+            if ((rc = realloc_device(&b->items, tot * sizeof(int4)))) return rc;
+            b->graph_stale = true;
+        }
+        if ((int)nact > b->cap_act) {
+            b->cap_act = std::max((int)nact, std::max(2 * b->cap_act, 16));
+            if ((rc = realloc_device(&b->fdesc, b->cap_act * sizeof(FinalizeDesc))) ||
+                (rc = realloc_device(&b->dout, 2 * (size_t)b->cap_act * sizeof(double))))
+                return rc;
+            if (b->hout) cudaFreeHost(b->hout);
+            b->hout = nullptr;
+            CK(cudaMallocHost((void**)&b->hout, 2 * (size_t)b->cap_act * sizeof(double)));
+            b->graph_stale = true;
+        }
+        if (!b->counts && (rc = realloc_device(&b->counts, 8 * sizeof(int)))) return rc;
+        if (b->graph_stale) b->sig.clear();
+        // 3. tables: rebuilt and uploaded only when the admitted set or a phase changed
+        std::vector<uint64_t> sig;
+        sig.reserve(nact);
+        for (BatchReq* q : b->active) sig.push_back(4 * q->ticket + (uint64_t)q->phase);
+        if (sig != b->sig) {
+            size_t off_d[6], hb = 0;
+            for (int k = 0; k < 6; ++k) {
+                off_d[k] = hb;
+                hb = align_up(hb + seg[k].size() * ((k & 1) ? adesc_size(k / 2) : pdesc_size(k / 2)), 128);
+            }
+            const size_t off_items = hb;
+            size_t n_items = 0;
+            for (int k = 0; k < 6; ++k) n_items += need[k];
+            hb = align_up(hb + n_items * sizeof(int4), 128);
+            const size_t off_fd = hb;
+            hb = align_up(hb + nact * sizeof(FinalizeDesc), 128);
+            const size_t off_cnt = hb;
+            hb += 8 * sizeof(int);
+            if ((rc = grow_host(b, hb))) return rc;
+            int4* hitems = reinterpret_cast<int4*>(b->host + off_items);
+            int* hcnt = reinterpret_cast<int*>(b->host + off_cnt);
+            size_t it = 0;
+            for (int k = 0; k < 6; ++k) {
+                const int t = k / 2;
+                const size_t it0 = it;
+                for (size_t r = 0; r < seg[k].size(); ++r) {
+                    BatchReq* q = seg[k][r];
+                    if (k & 1) {
+                        unsigned char* d = b->host + off_d[k] + r * adesc_size(t);
+                        if (t == 0) fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<double>*>(d), q->ad);
+                        else if (t == 1) fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<float>*>(d), q->ad);
+                        else fill_adjoint_desc(reinterpret_cast<AdjointBatchDesc<__nv_bfloat16>*>(d), q->ad);
+                    } else {
+                        unsigned char* d = b->host + off_d[k] + r * pdesc_size(t);
+                        if (t == 0) fill_primal_desc(reinterpret_cast<PrimalBatchDesc<double>*>(d), q->st);
+                        else if (t == 1) fill_primal_desc(reinterpret_cast<PrimalBatchDesc<float>*>(d), q->st);
+                        else fill_primal_desc(reinterpret_cast<PrimalBatchDesc<__nv_bfloat16>*>(d), q->st);
+                    }
+                    const DevMesh& m = q->st->mesh->d;
+                    for (int i = 0; i < m.ni; ++i)
+                        for (int j0 = 0; j0 < m.nj; j0 += kWarpsPerBlock) hitems[it++] = int4{(int)r, i, j0, 0};
+                }
+                hcnt[k] = (int)(it - it0);
+                if (!seg[k].empty()) {
+                    const size_t dsz = (k & 1) ? adesc_size(t) : pdesc_size(t);
+                    CK(cudaMemcpyAsync(b->desc[k], b->host + off_d[k], seg[k].size() * dsz, cudaMemcpyHostToDevice, s));
+                    CK(cudaMemcpyAsync(b->items + b->item_off[k], hitems + it0, (it - it0) * sizeof(int4),
+                                       cudaMemcpyHostToDevice, s));
+                }
+            }
+            hcnt[6] = (int)nact;
+            hcnt[7] = 0;
+            FinalizeDesc* hfd = reinterpret_cast<FinalizeDesc*>(b->host + off_fd);
+            for (size_t k = 0; k < nact; ++k) {
+                BatchReq* q = b->active[k];
+                const DevMesh& m = q->st->mesh->d;
+                if (q->phase == 1) hfd[k] = FinalizeDesc{q->st->respart, m.ncell, m.ni, q->st->Jpart, q->st->Fw[q->st->cur], q->st->fl.wallM};
+                else hfd[k] = FinalizeDesc{q->ad->respart, m.ncell, m.ni, nullptr, nullptr, nullptr};
+            }
+            CK(cudaMemcpyAsync(b->fdesc, hfd, nact * sizeof(FinalizeDesc), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(b->counts, hcnt, 8 * sizeof(int), cudaMemcpyHostToDevice, s));
+            b->sig.swap(sig);
+            b->stats.table_uploads += 1;
+        }
+        // M sweeps of every admitted request (one batched launch per segment and sweep), the residual
+        // and drag reduction, and the read-back: one graph launch, or the same launches directly
+        int kernels = 1;
+        for (int k = 0; k < 6; ++k) kernels += b->cap_items[k] > 0 ? M : 0;
+        auto enqueue = [&]() -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            for (int sw = 0; sw < M && e == cudaSuccess; ++sw) {
+                const bool res = sw == M - 1;
+                for (int t = 0; t < 3 && e == cudaSuccess; ++t) {
+                    e = launch_primal_sweep_batch(t, b->desc[2 * t], b->items + b->item_off[2 * t], b->cap_items[2 * t],
+                                                  b->counts + 2 * t, sw & 1, res, s);
+                    if (e == cudaSuccess)
+                        e = launch_adjoint_sweep_batch(t, b->desc[2 * t + 1], b->items + b->item_off[2 * t + 1],
+                                                       b->cap_items[2 * t + 1], b->counts + 2 * t + 1, sw & 1, res, s);
+                }
+            }
+            if (e == cudaSuccess) e = launch_finalize_batch(b->fdesc, b->cap_act, b->counts + 6, b->dout, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->hout, b->dout, 2 * (size_t)b->cap_act * sizeof(double), cudaMemcpyDeviceToHost, s);
+            return e;
+        };
+        if (graphs_ok(ctx)) {
+            if (!b->graph || b->graph_stale || b->graph_M != M) {
+                if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+                cudaGraph_t gr;
+                CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = enqueue();
+                cudaError_t ee = cudaStreamEndCapture(s, &gr);
+                CK(ce);
+                CK(ee);
+                cudaError_t ie = cudaGraphInstantiate(&b->graph, gr, 0);
+                cudaGraphDestroy(gr);
+                CK(ie);
+                b->graph_M = M;
+                b->graph_stale = false;
+                b->stats.graph_builds += 1;
+            }
+            CK(cudaGraphLaunch(b->graph, s));
+            b->stats.graph_launches += 1;
+        } else {
+            CK(enqueue());
+        }
+        ctx->launches += kernels;
+        b->stats.ticks += 1;
         CK(cudaStreamSynchronize(s));
         if ((rc = check_device_flag(ctx))) return rc;
+        const double* hout = b->hout;
         // 4. convergence and phase changes
         std::vector<BatchReq*> keep;
         for (size_t k = 0; k < nact; ++k) {
@@ -2333,6 +2637,12 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
     }
     if (n_active) *n_active = (int)b->active.size();
     if (n_queued) *n_queued = (int)b->queue.size();
+    return DVM_OK;
+}
+
+int dvm_batch_get_stats(const dvm_batch* b, dvm_batch_stats* out) {
+    if (!b || !out) return fail(DVM_ERR_INVALID_ARG, "NULL argument");
+    *out = b->stats;
     return DVM_OK;
 }
 

@@ -89,7 +89,22 @@ struct PrimalArgs {
     double* respart;
     int* err;                               // set when a staged copy never completed
     const TS* defect;                       // second order: dR(f_old), subtracted before the division by D
+    // Refinement (linearised sweep of a correction e, FP32 storage): f_old/f_new hold e; prim_old is
+    // the linearisation point; lin_src the increment s of one FP64 sweep; lin_f the FP32 state at the
+    // linearisation point; dW_old/dW_new the moment sums of e (the sweep writes them instead of prim_new).
+    const TS* lin_src;
+    const TS* lin_f;
+    const double4* dW_old;
+    double4* dW_new;
+    // Velocity-space shard (the state holds a slice of the velocity grid): the sweep writes the raw
+    // velocity sums of its slice here instead of finishing the moments (layout: see shard_layout()).
+    double* part;
 };
+
+// Partial sums of one velocity shard, doubles: [4 ncell] moment sums (sum w f1, w f1 vx, w f1 vy,
+// w (f1 |v|^2/2 + f2)); [ncell] residual sum w (R/V)^2; [ni] wall density F_rhow; [ni] outflow drag;
+// [ni] wall normaliser D_l; [ni] M_l D_l.  Adding the shards' buffers gives those of the whole grid.
+inline size_t shard_count(int ncell, int ni) { return 5 * (size_t)ncell + 4 * (size_t)ni; }
 
 // Second-order reconstruction (Eq. gaussgrad): the gradient (or, for the adjoint, the transposed
 // reconstruction weights mu) and the defect live in buffers of the state's storage and layout.
@@ -173,24 +188,46 @@ struct FinalizeDesc {
 // ---------------------------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return cudaGetLastError().
 cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s);
+// raw = true: wallM receives M_l D_l (the unnormalised sum, which adds across velocity shards).
 cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, MomentJ mj,
-                              double* wallD, double* wallM, cudaStream_t s);
+                              double* wallD, double* wallM, cudaStream_t s, bool raw = false);
 cudaError_t launch_fill_freestream(int storage, void* f, int ncell, const DevGrid& g, const DevFlow& fl,
                                    cudaStream_t s);
 cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
                            double* Fw, cudaStream_t s);
+// Velocity shards: the raw moment sums and wall density of f into a shard buffer (residual and drag
+// entries zeroed); and the combination of the shards' summed buffer into primitives, wall density,
+// residual and drag partials and the wall constants of the whole grid.
+cudaError_t launch_shard_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double* part,
+                                 cudaStream_t s);
+cudaError_t launch_shard_combine(const DevMesh& m, const double* total, double4* prim, double* Fw, double* respart,
+                                 double* Jpart, double* wallD, double* wallM, cudaStream_t s);
 // res = false: skip the residual (only the sweeps whose residual is read need it).  maps: of f_old.
 cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
+// Sweep of a velocity shard (args.part set): raw velocity sums of the slice into args.part.
+cudaError_t launch_primal_shard_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
+// Linearised correction sweep of the refinement (FP32 storage only; args: PrimalArgs<float, float> with the
+// lin_* fields set, maps: of the correction e_old).
+cudaError_t launch_primal_lin_sweep(const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
+// Refinement elementwise steps over FP32 states of ncell x nvp velocities: f64 <- fbar + delta (FP64 storage
+// layout); s <- f64_new - f64_old (FP32 layout); delta += e, then fbar <- fl(fbar + delta) and delta keeps the
+// exact remainder (two-sum).
+cudaError_t launch_refine_compose(const float* fbar, const float* delta, double* f64, int ncell, int nvp,
+                                  cudaStream_t s);
+cudaError_t launch_refine_diff(const double* f64_new, const double* f64_old, float* src, int ncell, int nvp,
+                               cudaStream_t s);
+cudaError_t launch_refine_update(float* fbar, float* delta, const float* e, size_t n, cudaStream_t s);
 // update = false: no phi update, only the couplings (Z, Lambda) of phi_old into the *_new slots.
 // phi_maps: of phi_old; f_maps: of the primal f.
 cudaError_t launch_adjoint_sweep(int storage, const void* args, const TmaMaps& phi_maps, const TmaMaps& f_maps,
                                  bool update, bool res, cudaStream_t s);
 // Batched sweeps over work items (request, i, j0); descs is PrimalBatchDesc<TS>[] / AdjointBatchDesc<TS>[].
-cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
-                                      bool res, cudaStream_t s);
-cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
-                                       bool res, cudaStream_t s);
-cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, double* out, cudaStream_t s);
+// n_items blocks are launched (the table's capacity); *count (device memory) of them are in use.
+cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4* items, int n_items, const int* count,
+                                      int parity, bool res, cudaStream_t s);
+cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, const int* count,
+                                       int parity, bool res, cudaStream_t s);
+cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, const int* count, double* out, cudaStream_t s);
 // maxw: parameters of the cell Maxwellian (prim itself, or the conservative fit)
 cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const double4* maxw, const DevMesh& m,
                                      double inv_tau_inf, void* out, cudaStream_t s);

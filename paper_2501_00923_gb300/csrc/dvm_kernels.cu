@@ -10,6 +10,7 @@
 // fixed butterfly, so results are deterministic.
 #include "dvm_internal.h"
 
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 
@@ -407,7 +408,16 @@ template <class TS> constexpr int kAdjointMinBlocks = std::is_same<typename Pack
 // which keeps the loop free of per-velocity branches.
 // FP32 / BF16 form of the sweep: the same update two velocities at a time.  D uses the inflow
 // weights n_e = max(-a_e, 0): sum_e max(a_e, 0) = sum_e n_e on a closed cell.
-template <class TS, bool kRes, int kBnd, bool kDef>
+//
+// kLin (refinement, FP32 storage): the same sweep applied to a correction e of the state at a fixed
+// linearisation point (prim_old): the relaxation source V/tau g of Eq. (numerpr_gov) is replaced by its
+// linearisation in the moments dW of e_old (lagged like g itself),
+//   V/tau dg + V d(1/tau) (g - f),   dg1/g1 = drho/rho + (v - u).du/T + (|v - u|^2/(2T^2) - 1/T) dT,
+//   dg2 = (T/2) dg1 + (dT/2) g1,      d(1/tau)/(1/tau) = drho/rho + dT/(2T),
+// the far field injects nothing, the wall re-emits (dF_rhow / D_l) gbar_w, and the right-hand side gains
+// D s, with s the increment of one FP64 sweep of the full problem.  One such sweep is e <- s + e - (J e)/D
+// with J the Jacobian of the steady residual, so at its fixed point J e = -R.
+template <class TS, bool kRes, int kBnd, bool kDef, bool kLin, bool kShard>
 __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& P, int c, int w, int lane,
                                                    const Feed& F) {
     using PK = Pack<TS>;
@@ -420,6 +430,20 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     G.setup(rho, u1, u2, T);
     const float Vt = P.V[c] * (float)pr.x * sqrtf((float)pr.w) * (float)P.inv_tau_inf;      // V / tau
     const float2 kA = bc(G.kA), kB = bc(G.kB), mu1 = bc(-u1), mu2 = bc(-u2), Vt2 = bc(Vt), hT = bc(0.5f * T);
+    float2 lc0 = bc(0.f), lcx = lc0, lcy = lc0, lct = lc0, lhdT = lc0, lVk = lc0;
+    if (kLin) {                      // linearised Maxwellian and relaxation rate from the moment sums of e_old
+        const double4 dw = P.dW_old[c];
+        const float drho = (float)dw.x, dmx = (float)dw.y, dmy = (float)dw.z, dE = (float)dw.w;
+        const float ir = 1.f / rho, iT = 1.f / T, uu = 0.5f * (u1 * u1 + u2 * u2);
+        const float dux = (dmx - u1 * drho) * ir, duy = (dmy - u2 * drho) * ir;
+        const float dT = (2.f / 3.f) * ir * (dE - (u1 * dmx + u2 * dmy) + (uu - 1.5f * T) * drho);
+        lcx = bc(dux * iT);
+        lcy = bc(duy * iT);
+        lct = bc(dT * iT * iT);
+        lc0 = bc(drho * ir - (u1 * dux + u2 * duy) * iT + (uu * iT - 1.f) * iT * dT);
+        lhdT = bc(0.5f * dT);
+        lVk = bc(Vt * (drho * ir + 0.5f * dT * iT));
+    }
     const float2 s0x = bc(S0.x), s0y = bc(S0.y), s1x = bc(S1.x), s1y = bc(S1.y);
     const float2 s2x = bc(S2.x), s2y = bc(S2.y), s3x = bc(S3.x), s3y = bc(S3.y);
     float2 cw1 = bc(0.f), cw2 = bc(0.f), dxy = bc(0.f), dyy = bc(0.f);
@@ -459,6 +483,11 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                 PK::unpack(r3, e31, e32);
                 float dq1[KV], dq2[KV];
                 if (kDef) PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.defect) + oc + q), dq1, dq2);
+                float ls1[KV], ls2[KV], lf1[KV], lf2[KV];
+                if (kLin) {
+                    PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.lin_src) + oc + q), ls1, ls2);
+                    PK::unpack(ldg16(reinterpret_cast<const uint4*>(P.lin_f) + oc + q), lf1, lf2);
+                }
                 float fn1[KV], fn2[KV];
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
@@ -474,9 +503,14 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                     float2 f11 = pair_of<KV>(e11, pp), f12 = pair_of<KV>(e12, pp);
                     float2 f31 = pair_of<KV>(e31, pp), f32 = pair_of<KV>(e32, pp);
                     if (far) {
-                        const float4 g = *reinterpret_cast<const float4*>(P.fd + 2 * kp);   // (g1,g2) x 2
-                        f11 = make_float2(g.x, g.z);
-                        f12 = make_float2(g.y, g.w);
+                        if (kLin) {
+                            f11 = bc(0.f);
+                            f12 = bc(0.f);
+                        } else {
+                            const float4 g = *reinterpret_cast<const float4*>(P.fd + 2 * kp);   // (g1,g2) x 2
+                            f11 = make_float2(g.x, g.z);
+                            f12 = make_float2(g.y, g.w);
+                        }
                     }
                     if (wall) {
                         const float2 gw = *reinterpret_cast<const float2*>(P.gw + 2 * kp);
@@ -484,9 +518,20 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                         f32 = pmul(cw2, gw);
                     }
                     const float2 D = padd(Vt2, padd(padd(n0, n1), padd(n2, n3)));
-                    const float2 g1 = pex2(pfma(pfma(vy, mu2, pfma(vx, mu1, hv)), kA, kB));
-                    float2 r1 = pmul(Vt2, g1);
-                    float2 r2 = pmul(hT, r1);
+                    const float2 tt = pfma(vy, mu2, pfma(vx, mu1, hv));        // |v|^2/2 - v.u
+                    const float2 g1 = pex2(pfma(tt, kA, kB));
+                    float2 r1, r2;
+                    if (kLin) {
+                        const float2 A1 = pfma(tt, lct, pfma(vy, lcy, pfma(vx, lcx, lc0)));   // dg1 / g1
+                        const float2 Vg = pmul(Vt2, g1);
+                        r1 = pfma(D, pair_of<KV>(ls1, pp), pmul(Vg, A1));
+                        r2 = pfma(D, pair_of<KV>(ls2, pp), pmul(Vg, pfma(A1, hT, lhdT)));
+                        r1 = pfma(lVk, padd(g1, pmul(bc(-1.f), pair_of<KV>(lf1, pp))), r1);
+                        r2 = pfma(lVk, pfma(hT, g1, pmul(bc(-1.f), pair_of<KV>(lf2, pp))), r2);
+                    } else {
+                        r1 = pmul(Vt2, g1);
+                        r2 = pmul(hT, r1);
+                    }
                     r1 = pfma(n0, pair_of<KV>(e01, pp), r1); r2 = pfma(n0, pair_of<KV>(e02, pp), r2);
                     r1 = pfma(n1, f11, r1);                  r2 = pfma(n1, f12, r2);
                     r1 = pfma(n2, pair_of<KV>(e21, pp), r1); r2 = pfma(n2, pair_of<KV>(e22, pp), r2);
@@ -528,11 +573,24 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     float RS = 0.f, FW = 0.f, JA = 0.f;
     if (kRes) RS = rs.total();
     if (wall) { FW = fwa.total(); JA = ja.total(); }
-    if (lane == 0) {
-        const float ir = 1.f / M0;
-        const float nu1 = M1 * ir, nu2 = M2 * ir;
-        const float nT = (2.f / 3.f) * (M3 * ir - 0.5f * (nu1 * nu1 + nu2 * nu2));
-        P.prim_new[c] = make_double4(M0, nu1, nu2, nT);
+    if (kShard && lane == 0) {           // velocity shard: raw sums of this slice
+        const size_t nc = (size_t)P.ncell;
+        reinterpret_cast<double4*>(P.part)[c] = make_double4(M0, M1, M2, M3);
+        const float V = P.V[c];
+        P.part[4 * nc + c] = kRes ? (double)(RS / (V * V)) : 0.0;
+        if (wall) {
+            P.part[5 * nc + c] = (double)(FW * invA);
+            P.part[5 * nc + P.ni + c] = (double)JA;
+        }
+    } else if (lane == 0) {
+        if (kLin) {
+            P.dW_new[c] = make_double4(M0, M1, M2, M3);
+        } else {
+            const float ir = 1.f / M0;
+            const float nu1 = M1 * ir, nu2 = M2 * ir;
+            const float nT = (2.f / 3.f) * (M3 * ir - 0.5f * (nu1 * nu1 + nu2 * nu2));
+            P.prim_new[c] = make_double4(M0, nu1, nu2, nT);
+        }
         if (kRes) {
             const float V = P.V[c];
             P.respart[c] = (double)(RS / (V * V));
@@ -545,9 +603,9 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     return true;
 }
 
-template <class TS, bool kRes, int kBnd, bool kDef>
+template <class TS, bool kRes, int kBnd, bool kDef, bool kShard>
 __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
-                                            int lane, const Feed& F) {
+                                            int lane, const Feed& F) {   // no linearised form (FP32 only)
     using PK = Pack<TS>;
     using TC = typename PK::TC;
     using TC2 = typename Vec<TC>::v2;
@@ -645,7 +703,16 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
     TC RS = TC(0), FW = TC(0), JA = TC(0);
     if (kRes) RS = rs.total();
     if (wall) { FW = fwa.total(); JA = ja.total(); }
-    if (lane == 0) {
+    if (kShard && lane == 0) {           // velocity shard: raw sums of this slice
+        const size_t nc = (size_t)P.ncell;
+        reinterpret_cast<double4*>(P.part)[c] = make_double4(M0, M1, M2, M3);
+        const TC V = P.V[c];
+        P.part[4 * nc + c] = kRes ? (double)(RS / (V * V)) : 0.0;
+        if (wall) {
+            P.part[5 * nc + c] = (double)(FW * invA);
+            P.part[5 * nc + P.ni + c] = (double)JA;
+        }
+    } else if (lane == 0) {
         const TC ir = TC(1) / M0;
         const TC nu1 = M1 * ir, nu2 = M2 * ir;
         const TC nT = TC(2.0 / 3.0) * (M3 * ir - TC(0.5) * (nu1 * nu1 + nu2 * nu2));
@@ -711,7 +778,7 @@ __device__ __forceinline__ void block_pipe_drain(const BlockPipe& B) {
         for (unsigned ph = 0; ph < 2; ++ph) mbar_try_wait(&B.F.full[s], ph);
 }
 
-template <class TS, bool kRes, bool kDef>
+template <class TS, bool kRes, bool kDef, bool kLin = false, bool kShard = false>
 __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
                                              const CUtensorMap* m8, int i, int j0, unsigned char* smem) {
     BlockPipe B;
@@ -724,17 +791,18 @@ __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<
     bool ok;
     if constexpr (kPaired<TS>) {
         switch (bnd) {
-            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior, kDef>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell, kDef>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell, kDef>(P, c, w, lane, B.F); break;
-            default: ok = primal_cell_paired<TS, kRes, kWallFar, kDef>(P, c, w, lane, B.F); break;
+            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell_paired<TS, kRes, kWallFar, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
         }
     } else {
+        static_assert(!kLin, "the linearised sweep has the paired FP32 form only");
         switch (bnd) {
-            case kInterior: ok = primal_cell<TS, kRes, kInterior, kDef>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = primal_cell<TS, kRes, kWallCell, kDef>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = primal_cell<TS, kRes, kFarCell, kDef>(P, c, w, lane, B.F); break;
-            default: ok = primal_cell<TS, kRes, kWallFar, kDef>(P, c, w, lane, B.F); break;
+            case kInterior: ok = primal_cell<TS, kRes, kInterior, kDef, kShard>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell<TS, kRes, kWallCell, kDef, kShard>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell<TS, kRes, kFarCell, kDef, kShard>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell<TS, kRes, kWallFar, kDef, kShard>(P, c, w, lane, B.F); break;
         }
     }
     if (!ok && lane == 0) {
@@ -752,6 +820,25 @@ __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep(cons
     primal_block<TS, kRes, kDef>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
 }
 
+// Sweep of a velocity shard: the same update, with the raw velocity sums of the slice written to the
+// shard buffer in place of the moments, wall density, drag and residual partials.
+template <class TS, bool kRes>
+__global__ void __launch_bounds__(256, 2) k_primal_shard_sweep(const PrimalArgs<TS, typename Pack<TS>::TC> P,
+                                                               const __grid_constant__ CUtensorMap m10,
+                                                               const __grid_constant__ CUtensorMap m8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    primal_block<TS, kRes, false, false, true>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+}
+
+// Linearised correction sweep of the refinement (FP32 storage; see primal_cell_paired).
+template <bool kRes>
+__global__ void __launch_bounds__(256, 2) k_primal_lin_sweep(const PrimalArgs<float, float> P,
+                                                                const __grid_constant__ CUtensorMap m10,
+                                                                const __grid_constant__ CUtensorMap m8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    primal_block<float, kRes, false, true>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+}
+
 // Make the tensor maps of a descriptor in global memory visible to the tensor-map proxy.
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
@@ -759,11 +846,15 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 
 // Batched primal sweep: block b runs work item items[b] = (request, i, j0) of the descriptor
 // table; every request advances one sweep.  parity selects, per request, the buffer pair of this
-// sweep (descriptor slot 0 reads the buffer current at the start of the tick).
+// sweep (descriptor slot 0 reads the buffer current at the start of the tick).  The grid is the
+// table's capacity and *count (device memory) the items in use, so one launch shape, and one captured
+// graph, serves any admitted set that fits the capacity; blocks beyond the count return at once.
 template <class TS, bool kRes>
 __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep_batch(const PrimalBatchDesc<TS>* __restrict__ descs,
-                                                               const int4* __restrict__ items, int parity) {
+                                                               const int4* __restrict__ items, const int* __restrict__ count,
+                                                               int parity) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    if ((int)blockIdx.x >= *count) return;
     const int4 it = items[blockIdx.x];
     const PrimalBatchDesc<TS>* d = descs + it.x;
     if (threadIdx.x == 0) {
@@ -1138,8 +1229,10 @@ __global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep(co
 
 template <class TS, bool kRes>
 __global__ void __launch_bounds__(256, kAdjointMinBlocks<TS>) k_adjoint_sweep_batch(const AdjointBatchDesc<TS>* __restrict__ descs,
-                                                                const int4* __restrict__ items, int parity) {
+                                                                const int4* __restrict__ items, const int* __restrict__ count,
+                                                                int parity) {
     extern __shared__ __align__(1024) unsigned char smem[];
+    if ((int)blockIdx.x >= *count) return;
     const int4 it = items[blockIdx.x];
     const AdjointBatchDesc<TS>* d = descs + it.x;
     if (threadIdx.x == 0) {
@@ -1199,7 +1292,7 @@ __global__ void k_flow_tables(int nvp, const typename Vec<TC>::v4* vt, double u1
 // Per wall face l: D_l = -sum_{a<=0} w (v.n) g_M1(1,0,Tw) (the normaliser of Eq. barg) and
 // M_l = sum_{a<=0} w (v.d) a g_M1 / D_l (the reflected part of J per unit F_rhow).
 __global__ void k_wall_setup(int nvp, const double2* S, const double4* vd, const double* gw, MomentJ mj,
-                             double* wallD, double* wallM) {
+                             double* wallD, double* wallM, int raw) {
     const int l = blockIdx.x;
     const double2 s = S[4 * l + 3];
     const double A = sqrt(s.x * s.x + s.y * s.y);
@@ -1221,7 +1314,7 @@ __global__ void k_wall_setup(int nvp, const double2* S, const double4* vd, const
         double D = 0.0, M = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { D += sd[i]; M += sm[i]; }
         wallD[l] = D;
-        wallM[l] = M / D;
+        wallM[l] = raw ? M : M / D;
     }
 }
 
@@ -1236,9 +1329,10 @@ __global__ void k_fill_freestream(TS* f, size_t n_pairs, int nvp,
     f[o + kComp<TS>] = fromdbl<TS>((double)d.y);
 }
 
+// part != null (velocity shard): the raw sums and the wall density go to the shard buffer instead.
 template <class TS>
 __global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const double2* S, const double4* vd,
-                          double4* prim, double* Fw) {
+                          double4* prim, double* Fw, double* part, int ni) {
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (c >= ncell) return;
@@ -1257,7 +1351,14 @@ __global__ void k_moments(const TS* f, int ncell, int nvp, const int4* nb, const
         if (wall && a > 0.0) fw += t.z * a * f1;
     }
     m0 = warp_sum(m0); m1 = warp_sum(m1); m2 = warp_sum(m2); m3 = warp_sum(m3); fw = warp_sum(fw);
-    if (lane == 0) {
+    if (lane == 0 && part) {
+        reinterpret_cast<double4*>(part)[c] = make_double4(m0, m1, m2, m3);
+        part[4 * (size_t)ncell + c] = 0.0;
+        if (wall) {
+            part[5 * (size_t)ncell + c] = fw / sqrt(s.x * s.x + s.y * s.y);
+            part[5 * (size_t)ncell + ni + c] = 0.0;
+        }
+    } else if (lane == 0) {
         const double u1 = m1 / m0, u2 = m2 / m0;
         prim[c] = make_double4(m0, u1, u2, (2.0 / 3.0) * (m3 / m0 - 0.5 * (u1 * u1 + u2 * u2)));
         if (wall) Fw[c] = fw / sqrt(s.x * s.x + s.y * s.y);
@@ -1652,10 +1753,13 @@ __global__ void __launch_bounds__(256) k_so_sens_cells(const SOArgs<TS, typename
     const size_t nq = (size_t)A.nq;
     const uint4* fq = reinterpret_cast<const uint4*>(A.in);
     const uint4* pq = reinterpret_cast<const uint4*>(phi);
-    // sums: 0 sV; 1..8 T_e; 9..16 U_e; 17..24 Y_e; wall: 25 Lam2, 26 Fw, 27..28 dFw, 29 D, 30..31 dD
-    TC s[32];
+    // sums: 0 sV; 1..8 T_e; 9..16 U_e; 17..24 Y_e (compensated, like the first-order face sums);
+    // wall cells: 0 Lam2, 1 Fw, 2..3 dFw, 4 D, 5..6 dD in FP64, because the wall term takes the
+    // difference (dFw D - Fw dD) / D^2 of them
+    Acc<TC> s[25];
+    double sw[7];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) s[i] = TC(0);
+    for (int i = 0; i < 7; ++i) sw[i] = 0.0;
     for (size_t q = lane; q < nq; q += 32) {
         TC o1[KV], o2[KV], m1[4][KV], m2[4][KV], l1[KV], l2[KV], k1[4][KV], k2[4][KV];
         PK::unpack(ldg16(fq + (size_t)c * nq + q), o1, o2);
@@ -1700,36 +1804,39 @@ __global__ void __launch_bounds__(256) k_so_sens_cells(const SOArgs<TS, typename
                 mx1 += ad1 * dc[e].x; my1 += ad1 * dc[e].y;
                 mx2 += ad2 * dc[e].x; my2 += ad2 * dc[e].y;
                 const TC gd = (gx1 * dc[e].x + gy1 * dc[e].y) * dl1 + (gx2 * dc[e].x + gy2 * dc[e].y) * dl2;
-                s[9 + 2 * e] += gd * t.x;
-                s[10 + 2 * e] += gd * t.y;
-                s[17 + 2 * e] += ad1 * gx1 + ad2 * gx2;
-                s[18 + 2 * e] += ad1 * gy1 + ad2 * gy2;
+                s[9 + 2 * e].add(gd * t.x);
+                s[10 + 2 * e].add(gd * t.y);
+                s[17 + 2 * e].add(ad1 * gx1 + ad2 * gx2);
+                s[18 + 2 * e].add(ad1 * gy1 + ad2 * gy2);
             }
-            s[0] += gx1 * mx1 + gy1 * my1 + gx2 * mx2 + gy2 * my2;
+            s[0].add(gx1 * mx1 + gy1 * my1 + gx2 * mx2 + gy2 * my2);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                s[1 + 2 * e] += (fb1[e] * mx1 + fb2[e] * mx2) * iV;
-                s[2 + 2 * e] += (fb1[e] * my1 + fb2[e] * my2) * iV;
+                s[1 + 2 * e].add((fb1[e] * mx1 + fb2[e] * mx2) * iV);
+                s[2 + 2 * e].add((fb1[e] * my1 + fb2[e] * my2) * iV);
             }
             if (wall) {
-                const TC gk = A.gw[k];
+                const double gk = (double)A.gw[k], wd = (double)w;
                 if (a[3] > TC(0)) {
-                    s[26] += w * a[3] * o1[kk];
-                    s[27] += w * t.x * o1[kk];
-                    s[28] += w * t.y * o1[kk];
+                    const double wo = wd * (double)o1[kk];
+                    sw[1] += wo * (double)a[3];
+                    sw[2] += wo * (double)t.x;
+                    sw[3] += wo * (double)t.y;
                 } else {
                     const TC sm1 = (S[3].x * mx1 + S[3].y * my1) * iV, sm2 = (S[3].x * mx2 + S[3].y * my2) * iV;
-                    s[25] += sm1 * gk + sm2 * A.halfTw * gk;
-                    s[29] -= w * a[3] * gk;
-                    s[30] -= w * t.x * gk;
-                    s[31] -= w * t.y * gk;
+                    sw[0] += (double)(sm1 + sm2 * A.halfTw) * gk;
+                    sw[4] -= wd * (double)a[3] * gk;
+                    sw[5] -= wd * (double)t.x * gk;
+                    sw[6] -= wd * (double)t.y * gk;
                 }
             }
         }
     }
     double r[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) r[i] = warp_sum((double)s[i]);
+    for (int i = 0; i < 25; ++i) r[i] = warp_sum(s[i].get());
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r[25 + i] = warp_sum(sw[i]);
     if (lane != 0) return;
     const int ni = A.ni, i = c % ni, j = c / ni, ip = (i + 1) % ni;
     const double2 P[4] = {A.nodes[j * ni + i], A.nodes[(j + 1) * ni + i], A.nodes[(j + 1) * ni + ip], A.nodes[j * ni + ip]};
@@ -2326,6 +2433,44 @@ __global__ void k_volume(int ni, const double2* S, const double2* nodes, double 
 // differences dR, dG of r and G, the next iterate is G - dG gamma, gamma = argmin |r - dR gamma|.
 // The vectors are the flat storage arrays (any layout: the operations are elementwise), held in
 // TH = the arithmetic type (FP32, or FP64 for FP64 storage).
+// ================================================================== refinement (elementwise)
+// FP32 chunk i of a state holds (f1_k, f1_k+1, f2_k, f2_k+1) for k = 2 (i mod nvp/2) of cell i div (nvp/2);
+// the same four values sit at 4i .. 4i+3 of the FP64 layout in the order (f1_k, f2_k, f1_k+1, f2_k+1).
+__global__ void __launch_bounds__(256) k_refine_compose(const float4* __restrict__ fbar, const float4* __restrict__ delta,
+                                                        double2* __restrict__ f64, size_t nchunk) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nchunk; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 a = fbar[i], d = delta[i];
+        f64[2 * i] = make_double2((double)a.x + (double)d.x, (double)a.z + (double)d.z);
+        f64[2 * i + 1] = make_double2((double)a.y + (double)d.y, (double)a.w + (double)d.w);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_refine_diff(const double2* __restrict__ fnew, const double2* __restrict__ fold,
+                                                     float4* __restrict__ src, size_t nchunk) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nchunk; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 a0 = fnew[2 * i], a1 = fnew[2 * i + 1], b0 = fold[2 * i], b1 = fold[2 * i + 1];
+        src[i] = make_float4((float)(a0.x - b0.x), (float)(a1.x - b1.x), (float)(a0.y - b0.y), (float)(a1.y - b1.y));
+    }
+}
+
+// delta += e, then (fbar, delta) <- (fl(fbar + delta), exact remainder) by the two-sum of Knuth.
+__device__ __forceinline__ void two_sum_into(float& a, float& b) {
+    const float s = a + b, bb = s - a;
+    b = (a - (s - bb)) + (b - bb);
+    a = s;
+}
+__global__ void __launch_bounds__(256) k_refine_update(float4* __restrict__ fbar, float4* __restrict__ delta,
+                                                       const float4* __restrict__ e, size_t n4) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        float4 a = fbar[i], d = delta[i];
+        const float4 x = e[i];
+        d.x += x.x; d.y += x.y; d.z += x.z; d.w += x.w;
+        two_sum_into(a.x, d.x); two_sum_into(a.y, d.y); two_sum_into(a.z, d.z); two_sum_into(a.w, d.w);
+        fbar[i] = a;
+        delta[i] = d;
+    }
+}
+
 constexpr int kAAMax = 8;             // deepest history
 constexpr int kAABlocks = 1216;       // 152 SMs x 8 blocks of 256 threads, grid-stride
 
@@ -2508,8 +2653,8 @@ cudaError_t launch_flow_tables(const DevGrid& g, DevFlow& fl, cudaStream_t s) {
 }
 
 cudaError_t launch_wall_setup(const DevMesh& m, const DevGrid& g, const DevFlow& fl, MomentJ mj,
-                              double* wallD, double* wallM, cudaStream_t s) {
-    k_wall_setup<<<m.ni, 256, 0, s>>>(g.nvp, m.Sd, g.vd, fl.gwd, mj, wallD, wallM);
+                              double* wallD, double* wallM, cudaStream_t s, bool raw) {
+    k_wall_setup<<<m.ni, 256, 0, s>>>(g.nvp, m.Sd, g.vd, fl.gwd, mj, wallD, wallM, raw ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -2588,9 +2733,46 @@ cudaError_t launch_maxwell_fit(int storage, const DevMesh& m, const DevGrid& g, 
 cudaError_t launch_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double4* prim,
                            double* Fw, cudaStream_t s) {
     const int nb = cdiv(m.ncell, kWarpsPerBlock);
-    if (storage == 0) k_moments<double><<<nb, 256, 0, s>>>((const double*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw);
-    else if (storage == 1) k_moments<float><<<nb, 256, 0, s>>>((const float*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw);
-    else k_moments<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw);
+    if (storage == 0) k_moments<double><<<nb, 256, 0, s>>>((const double*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw, nullptr, m.ni);
+    else if (storage == 1) k_moments<float><<<nb, 256, 0, s>>>((const float*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw, nullptr, m.ni);
+    else k_moments<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, prim, Fw, nullptr, m.ni);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_moments(int storage, const void* f, const DevMesh& m, const DevGrid& g, double* part,
+                                 cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0) k_moments<double><<<nb, 256, 0, s>>>((const double*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, nullptr, nullptr, part, m.ni);
+    else if (storage == 1) k_moments<float><<<nb, 256, 0, s>>>((const float*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, nullptr, nullptr, part, m.ni);
+    else k_moments<__nv_bfloat16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, m.ncell, g.nvp, m.nb, m.Sd, g.vd, nullptr, nullptr, part, m.ni);
+    return cudaGetLastError();
+}
+
+// The shards' summed buffer: primitives of the whole grid's moments (as the sweep's epilogue forms
+// them), the residual and drag partials and the wall density for the finalize, and the wall
+// normaliser D_l and M_l of the whole grid.
+__global__ void k_shard_combine(int ncell, int ni, const double* __restrict__ t, double4* __restrict__ prim,
+                                double* __restrict__ Fw, double* __restrict__ respart, double* __restrict__ Jpart,
+                                double* __restrict__ wallD, double* __restrict__ wallM) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double4 W = reinterpret_cast<const double4*>(t)[c];
+    const double u1 = W.y / W.x, u2 = W.z / W.x;
+    prim[c] = make_double4(W.x, u1, u2, (2.0 / 3.0) * (W.w / W.x - 0.5 * (u1 * u1 + u2 * u2)));
+    respart[c] = t[4 * (size_t)ncell + c];
+    if (c < ni) {
+        const size_t o = 5 * (size_t)ncell;
+        Fw[c] = t[o + c];
+        Jpart[c] = t[o + ni + c];
+        const double D = t[o + 2 * ni + c];
+        wallD[c] = D;
+        wallM[c] = t[o + 3 * ni + c] / D;
+    }
+}
+
+cudaError_t launch_shard_combine(const DevMesh& m, const double* total, double4* prim, double* Fw, double* respart,
+                                 double* Jpart, double* wallD, double* wallM, cudaStream_t s) {
+    k_shard_combine<<<cdiv(m.ncell, 256), 256, 0, s>>>(m.ncell, m.ni, total, prim, Fw, respart, Jpart, wallD, wallM);
     return cudaGetLastError();
 }
 
@@ -2622,6 +2804,72 @@ cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& ma
     if (storage == 0) primal_launch<double, double>(args, maps, res, s);
     else if (storage == 1) primal_launch<float, float>(args, maps, res, s);
     else primal_launch<__nv_bfloat16, float>(args, maps, res, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primal_lin_sweep(const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
+    const auto& a = *static_cast<const PrimalArgs<float, float>*>(args);
+    if (!a.lin_src || !a.lin_f || !a.dW_old || !a.dW_new) return cudaErrorInvalidValue;
+    const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
+    constexpr int sm = primal_smem_bytes<float>();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_primal_lin_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_lin_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    if (res) k_primal_lin_sweep<true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    else k_primal_lin_sweep<false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    return cudaGetLastError();
+}
+
+template <class TS, class TC>
+void shard_launch(const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
+    const auto& a = *static_cast<const PrimalArgs<TS, TC>*>(args);
+    const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
+    constexpr int sm = primal_smem_bytes<TS>();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_primal_shard_sweep<TS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_shard_sweep<TS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    if (res) k_primal_shard_sweep<TS, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    else k_primal_shard_sweep<TS, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+}
+
+cudaError_t launch_primal_shard_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
+    if (storage == 0) shard_launch<double, double>(args, maps, res, s);
+    else if (storage == 1) shard_launch<float, float>(args, maps, res, s);
+    else shard_launch<__nv_bfloat16, float>(args, maps, res, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_compose(const float* fbar, const float* delta, double* f64, int ncell, int nvp,
+                                  cudaStream_t s) {
+    const size_t n = (size_t)ncell * nvp / 2;
+    k_refine_compose<<<std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(fbar), reinterpret_cast<const float4*>(delta), reinterpret_cast<double2*>(f64), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_diff(const double* f64_new, const double* f64_old, float* src, int ncell, int nvp,
+                               cudaStream_t s) {
+    const size_t n = (size_t)ncell * nvp / 2;
+    k_refine_diff<<<std::min<size_t>(cdiv(n, 256), 152 * 16), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(f64_new), reinterpret_cast<const double2*>(f64_old),
+        reinterpret_cast<float4*>(src), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update(float* fbar, float* delta, const float* e, size_t n, cudaStream_t s) {
+    const size_t n4 = n / 4;
+    k_refine_update<<<std::min<size_t>(cdiv(n4, 256), 152 * 16), 256, 0, s>>>(
+        reinterpret_cast<float4*>(fbar), reinterpret_cast<float4*>(delta), reinterpret_cast<const float4*>(e), n4);
     return cudaGetLastError();
 }
 
@@ -2694,7 +2942,8 @@ cudaError_t launch_adjoint_cellconst(int storage, const double4* prim, const dou
 }
 
 template <class TS, class TC>
-void primal_batch_launch(const void* descs, const int4* items, int n_items, int parity, bool res, cudaStream_t s) {
+void primal_batch_launch(const void* descs, const int4* items, int n_items, const int* count, int parity, bool res,
+                         cudaStream_t s) {
     constexpr int sm = primal_smem_bytes<TS>();
     static bool attr[64] = {false};
     int dev = 0;
@@ -2705,21 +2954,22 @@ void primal_batch_launch(const void* descs, const int4* items, int n_items, int 
         attr[dev] = true;
     }
     const auto* d = static_cast<const PrimalBatchDesc<TS>*>(descs);
-    if (res) k_primal_sweep_batch<TS, true><<<n_items, 256, sm, s>>>(d, items, parity);
-    else k_primal_sweep_batch<TS, false><<<n_items, 256, sm, s>>>(d, items, parity);
+    if (res) k_primal_sweep_batch<TS, true><<<n_items, 256, sm, s>>>(d, items, count, parity);
+    else k_primal_sweep_batch<TS, false><<<n_items, 256, sm, s>>>(d, items, count, parity);
 }
 
-cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
-                                      bool res, cudaStream_t s) {
+cudaError_t launch_primal_sweep_batch(int storage, const void* descs, const int4* items, int n_items, const int* count,
+                                      int parity, bool res, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
-    if (storage == 0) primal_batch_launch<double, double>(descs, items, n_items, parity, res, s);
-    else if (storage == 1) primal_batch_launch<float, float>(descs, items, n_items, parity, res, s);
-    else primal_batch_launch<__nv_bfloat16, float>(descs, items, n_items, parity, res, s);
+    if (storage == 0) primal_batch_launch<double, double>(descs, items, n_items, count, parity, res, s);
+    else if (storage == 1) primal_batch_launch<float, float>(descs, items, n_items, count, parity, res, s);
+    else primal_batch_launch<__nv_bfloat16, float>(descs, items, n_items, count, parity, res, s);
     return cudaGetLastError();
 }
 
 template <class TS, class TC>
-void adjoint_batch_launch(const void* descs, const int4* items, int n_items, int parity, bool res, cudaStream_t s) {
+void adjoint_batch_launch(const void* descs, const int4* items, int n_items, const int* count, int parity, bool res,
+                          cudaStream_t s) {
     constexpr int sm = adjoint_smem_bytes<TS>();
     static bool attr[64] = {false};
     int dev = 0;
@@ -2730,23 +2980,24 @@ void adjoint_batch_launch(const void* descs, const int4* items, int n_items, int
         attr[dev] = true;
     }
     const auto* d = static_cast<const AdjointBatchDesc<TS>*>(descs);
-    if (res) k_adjoint_sweep_batch<TS, true><<<n_items, 256, sm, s>>>(d, items, parity);
-    else k_adjoint_sweep_batch<TS, false><<<n_items, 256, sm, s>>>(d, items, parity);
+    if (res) k_adjoint_sweep_batch<TS, true><<<n_items, 256, sm, s>>>(d, items, count, parity);
+    else k_adjoint_sweep_batch<TS, false><<<n_items, 256, sm, s>>>(d, items, count, parity);
 }
 
-cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, int parity,
-                                       bool res, cudaStream_t s) {
+cudaError_t launch_adjoint_sweep_batch(int storage, const void* descs, const int4* items, int n_items, const int* count,
+                                       int parity, bool res, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
-    if (storage == 0) adjoint_batch_launch<double, double>(descs, items, n_items, parity, res, s);
-    else if (storage == 1) adjoint_batch_launch<float, float>(descs, items, n_items, parity, res, s);
-    else adjoint_batch_launch<__nv_bfloat16, float>(descs, items, n_items, parity, res, s);
+    if (storage == 0) adjoint_batch_launch<double, double>(descs, items, n_items, count, parity, res, s);
+    else if (storage == 1) adjoint_batch_launch<float, float>(descs, items, n_items, count, parity, res, s);
+    else adjoint_batch_launch<__nv_bfloat16, float>(descs, items, n_items, count, parity, res, s);
     return cudaGetLastError();
 }
 
 // One block per request: out[2r] = sum respart_r, out[2r+1] = sum_l Jpart_l + Fw_l M_l (as k_finalize).
-__global__ void k_finalize_batch(const FinalizeDesc* __restrict__ fd, int n, double* out) {
+// *count (device memory) requests are in use; the grid is the table's capacity.
+__global__ void k_finalize_batch(const FinalizeDesc* __restrict__ fd, const int* __restrict__ count, double* out) {
     const int r = blockIdx.x;
-    if (r >= n) return;
+    if (r >= *count) return;
     const FinalizeDesc d = fd[r];
     __shared__ double s0[32], s1[32];
     double a = 0.0, b = 0.0;
@@ -2765,8 +3016,8 @@ __global__ void k_finalize_batch(const FinalizeDesc* __restrict__ fd, int n, dou
     }
 }
 
-cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, double* out, cudaStream_t s) {
-    if (n > 0) k_finalize_batch<<<n, 1024, 0, s>>>(fd, n, out);
+cudaError_t launch_finalize_batch(const FinalizeDesc* fd, int n, const int* count, double* out, cudaStream_t s) {
+    if (n > 0) k_finalize_batch<<<n, 1024, 0, s>>>(fd, count, out);
     return cudaGetLastError();
 }
 

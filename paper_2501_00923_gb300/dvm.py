@@ -37,7 +37,8 @@ class Flow(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("stall_window", C.c_int), ("accel_depth", C.c_int),
-                ("accel_period", C.c_int), ("accel_space", C.c_int)]
+                ("accel_period", C.c_int), ("accel_space", C.c_int), ("refine_tol", C.c_double),
+                ("refine_max", C.c_int), ("refine_sweeps", C.c_int)]
 
 
 def _accel(accel):
@@ -52,7 +53,8 @@ def _accel(accel):
 
 class PrimalResult(C.Structure):
     _fields_ = [("J", C.c_double), ("Cd", C.c_double), ("residual", C.c_double), ("r0", C.c_double),
-                ("iters", C.c_int), ("status", C.c_int)]
+                ("iters", C.c_int), ("status", C.c_int), ("refine_steps", C.c_int), ("refine_sweeps", C.c_int),
+                ("residual_fp32", C.c_double), ("residual_fp64", C.c_double)]
 
 
 class AdjointResult(C.Structure):
@@ -96,6 +98,10 @@ def lib():
             "dvm_state_set": (i, [_vp, _dp]),
             "dvm_state_get": (i, [_vp, _dp]),
             "dvm_state_copy_from": (i, [_vp, _vp]),
+            "dvm_state_set_shard": (i, [_vp, i]),
+            "dvm_state_shard_count": (s, [_vp]),
+            "dvm_state_shard_partials": (i, [_vp, _dp, s]),
+            "dvm_state_shard_combine": (i, [_vp, _dp, s, _dp, _dp]),
             "dvm_state_moments": (i, [_vp, _dp]),
             "dvm_state_set_order": (i, [_vp, i, i]),
             "dvm_state_get_order": (i, [_vp, C.POINTER(i)]),
@@ -276,6 +282,34 @@ class State:
         _check(lib().dvm_state_get(self.h, _p(f)))
         return f
 
+    # ---------------------------------------------------------------- velocity shards
+    def set_shard(self, on: bool = True):
+        """Make this state a velocity shard (its grid is a slice of the velocity grid): its sweeps
+        write partial sums, combined across shards with shard_combine."""
+        _check(lib().dvm_state_set_shard(self.h, int(bool(on))))
+
+    def shard_partials(self, out=None):
+        """This shard's partial sums: into a new host array, or into `out` (a host array or the data
+        pointer, an int, of device memory holding shard_count doubles)."""
+        n = lib().dvm_state_shard_count(self.h)
+        if out is None:
+            out = np.empty(n)
+        if isinstance(out, int):
+            _check(lib().dvm_state_shard_partials(self.h, C.cast(out, _dp), n))
+            return None
+        _check(lib().dvm_state_shard_partials(self.h, _p(out), n))
+        return out
+
+    def shard_combine(self, total):
+        """Install the summed partials of all shards (host array, or device data pointer as an int);
+        returns (residual sum of squares of the last sweep's input, drag of the current f)."""
+        n = lib().dvm_state_shard_count(self.h)
+        r, J = C.c_double(), C.c_double()
+        host = None if isinstance(total, int) else _arr(total, (n,))     # kept alive over the call
+        ptr = C.cast(total, _dp) if host is None else _p(host)
+        _check(lib().dvm_state_shard_combine(self.h, ptr, n, C.byref(r), C.byref(J)))
+        return r.value, J.value
+
     def copy_from(self, other: "State"):
         """Device-to-device warm start: f of `other` (same shape and storage) becomes this state's f."""
         _check(lib().dvm_state_copy_from(self.h, other.h))
@@ -383,11 +417,13 @@ class Adjoint:
 
 # ----------------------------------------------------------------------------------- calls
 def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0, tol=1e-8, max_iter=100000,
-                 storage="fp32", state: State | None = None, stall_window=0, accel=None):
+                 storage="fp32", state: State | None = None, stall_window=0, accel=None, refine_tol=0.0,
+                 refine_max=0, refine_sweeps=0):
     """Steady solve of Eq. (numerpr_gov); warm-starts from `state` if given.  accel = (m, K) turns on
-    Anderson mixing of depth m every K sweeps.  Returns (state, result)."""
+    Anderson mixing of depth m every K sweeps.  refine_tol > 0 (FP32 storage) adds mixed-precision
+    refinement to that FP64 residual after the sweeps.  Returns (state, result)."""
     flow = Flow(Kn, Ma, Tw, aoa)
-    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel))
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), refine_tol, refine_max, refine_sweeps)
     h = C.c_void_p(state.h.value if state is not None else None)
     res = PrimalResult()
     st = lib().dvm_primal_solve(ctx.h, mesh.h, grid.h, C.byref(flow), C.byref(opts), STORAGE[storage],
@@ -401,7 +437,7 @@ def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0,
 def adjoint_solve(ctx: Context, state: State, functional="drag", tol=1e-8, max_iter=100000,
                   adjoint: Adjoint | None = None, stall_window=0, accel=None):
     """Steady solve of the discrete adjoint for `functional`; accel as in primal_solve."""
-    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel))
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0)
     h = C.c_void_p(adjoint.h.value if adjoint is not None else None)
     res = AdjointResult()
     st = lib().dvm_adjoint_solve(ctx.h, state.h, FUNCTIONAL[functional], C.byref(opts), C.byref(h), C.byref(res))

@@ -35,6 +35,11 @@ class Request(C.Structure):
                 ("sens_mode", C.c_int), ("warm_key", C.c_uint64), ("stall_window", C.c_int)]
 
 
+class BatchStats(C.Structure):
+    _fields_ = [("ticks", C.c_uint64), ("graph_launches", C.c_uint64), ("graph_builds", C.c_uint64),
+                ("table_uploads", C.c_uint64), ("peak_active", C.c_int), ("peak_bytes", C.c_size_t)]
+
+
 class RequestResult(C.Structure):
     _fields_ = [("done", C.c_int), ("status", C.c_int), ("phase", C.c_int), ("primal_iters", C.c_int),
                 ("adjoint_iters", C.c_int), ("J", C.c_double), ("Cd", C.c_double), ("residual", C.c_double),
@@ -52,6 +57,7 @@ def _bind():
         "dvm_batch_submit": (i, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
         "dvm_batch_tick": (i, [vp, C.POINTER(i), C.POINTER(i)]),
         "dvm_batch_poll": (i, [vp, C.c_uint64, C.POINTER(RequestResult), _dp, i]),
+        "dvm_batch_get_stats": (i, [vp, C.POINTER(BatchStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -131,6 +137,11 @@ class BatchServer:
             self.nparams.pop(ticket, None)
         return out
 
+    def stats(self) -> dict:
+        st = BatchStats()
+        dvm._check(self.L.dvm_batch_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in BatchStats._fields_}
+
     def close(self):
         if self.h:
             self.L.dvm_batch_destroy(self.h)
@@ -193,6 +204,7 @@ def latency_stats(lat, makespan):
 
 
 def replay_batched(ctx, specs, arrivals, sweeps_per_tick=20, hbm_budget=0):
+    """Returns (latencies, makespan, {ticket: result}, batch counters)."""
     server = BatchServer(ctx, sweeps_per_tick, hbm_budget)
     results = {}
 
@@ -203,16 +215,19 @@ def replay_batched(ctx, specs, arrivals, sweeps_per_tick=20, hbm_budget=0):
         return bool(r["done"])
 
     lat, span = replay(arrivals, lambda k: server.submit(specs[k]), server.tick, poll_done)
+    stats = server.stats()
     server.close()
-    return lat, span, results
+    return lat, span, results, stats
 
 
 def replay_serial(ctx, specs, arrivals):
     """One request at a time in arrival order, no batching and no graph capture: ctx should be
-    created with graphs=False."""
+    created with graphs=False.  Returns (latencies, makespan, {k: error status or None},
+    {k: solve status})."""
     queue = []
     done_flags = {}
     failures = {}
+    statuses = {}
 
     def submit(k):
         queue.append(k)
@@ -229,14 +244,17 @@ def replay_serial(ctx, specs, arrivals):
             objs.append(m)
             g = dvm.VGrid(ctx, s.grid.vx, s.grid.vy, s.grid.w)
             objs.append(g)
-            st, _ = dvm.primal_solve(ctx, m, g, s.flow.Kn, s.flow.Ma, s.flow.Tw, s.flow.aoa, tol=s.tol,
-                                     max_iter=s.max_iter, storage=s.storage)
+            st, pres = dvm.primal_solve(ctx, m, g, s.flow.Kn, s.flow.Ma, s.flow.Tw, s.flow.aoa, tol=s.tol,
+                                        max_iter=s.max_iter, storage=s.storage)
             objs.append(st)
+            status = pres.status
             if s.sens:
-                ad, _ = dvm.adjoint_solve(ctx, st, tol=s.adjoint_tol, max_iter=s.max_iter)
+                ad, ares = dvm.adjoint_solve(ctx, st, tol=s.adjoint_tol, max_iter=s.max_iter)
                 objs.append(ad)
                 dvm.sensitivity(ctx, st, ad, s.mesh.dwall, s.mesh.s, mode=s.sens_mode)
+                status = status if status != dvm.DVM_OK else ares.status
             failures[k] = None
+            statuses[k] = status
         except dvm.DVMError as e:          # the request fails; the replay goes on
             failures[k] = e.status
         for o in reversed(objs):
@@ -244,4 +262,4 @@ def replay_serial(ctx, specs, arrivals):
         done_flags[k] = True
 
     lat, span = replay(arrivals, submit, tick, lambda k: done_flags.get(k, False))
-    return lat, span, failures
+    return lat, span, failures, statuses

@@ -56,7 +56,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     pairs = [("dvm_options", dvm.Options), ("dvm_flow", dvm.Flow), ("dvm_solve_opts", dvm.SolveOpts),
              ("dvm_primal_result", dvm.PrimalResult), ("dvm_adjoint_result", dvm.AdjointResult),
              ("dvm_batch_options", serve.BatchOptions), ("dvm_request", serve.Request),
-             ("dvm_request_result", serve.RequestResult)]
+             ("dvm_request_result", serve.RequestResult), ("dvm_batch_stats", serve.BatchStats)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dvm.h"', 'int main(void) {']
     for cname, py in pairs:
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -271,3 +271,41 @@ def test_full_size_second_order_sweeps_sampled_cells(ctx, index, storage, ptol, 
     assert (np.abs(out - ref) / scale).max() < ptol
     for h in (ad, st, g, m):
         h.close()
+
+
+@pytest.mark.parametrize("storage,maxwellian,tol", [("fp32", "plain", 1e-4), ("fp32", "conservative", 1e-4),
+                                                    ("bf16", "plain", 1e-2)])
+def test_second_order_full_sensitivity_in_reduced_storage(ctx, storage, maxwellian, tol):
+    """Mode FULL at second order (k_so_sens_cells, k_so_sens_nodes on top of the first-order face and
+    volume terms) in FP32 and BF16 storage against the oracle's full discrete gradient of the
+    second-order problem, evaluated on the very state and adjoint the GPU holds (their stored values
+    read back), after second-order solves in that storage.  16x16 velocities: 128 FP32 chunks (64 BF16)
+    per cell, so every lane of a cell's warp sums several chunks.  FP32 must meet the stated 1e-4
+    relative per component; BF16 storage changes only the inputs, which the oracle sees too, so it is
+    bounded loosely and its error printed.  (On random states and adjoints, instead of solved ones, the
+    gradient is a small remainder of large terms of both signs, and FP32 rounding of the terms alone
+    moves it by about 1%.)"""
+    rng = np.random.default_rng(61)
+    mesh = W.omesh(16, 8, rng.uniform(-0.01, 0.01, 4))
+    grid = W.velocity_grid(16, 4.0)
+    Kn, Ma = 0.4, 0.7
+    m = dvm.Mesh(ctx, mesh.nodes)
+    g = dvm.VGrid(ctx, grid.vx, grid.vy, grid.w)
+    st = dvm.State(ctx, m, g, Kn, Ma, storage=storage)
+    if maxwellian != "plain":
+        st.maxwellian = maxwellian
+    opts = dict(tol=1e-7, max_iter=200000, storage=storage, state=st, stall_window=2000)
+    dvm.primal_solve(ctx, m, g, Kn, Ma, **opts)          # second order starts from the first-order state
+    st.order = 2
+    dvm.primal_solve(ctx, m, g, Kn, Ma, **opts)
+    ad, _ = dvm.adjoint_solve(ctx, st, tol=1e-7, max_iter=200000, stall_window=2000)
+    pr = O.Problem(mesh.nodes, grid.vx, grid.vy, grid.w, Kn, Ma, conservative=(maxwellian != "plain"))
+    so = SecondOrder(pr)
+    f_in, phi_in = st.get(), ad.get()
+    got = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+    ref = so.sens_full(f_in, phi_in, mesh.dnodes())
+    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())
+    print(f"order-2 FULL sensitivity, {storage} {maxwellian}: max relative error per component {rel.max():.2e}")
+    assert rel.max() < tol
+    for h in (ad, st, g, m):
+        h.close()

@@ -108,3 +108,36 @@ def test_iteration_cap_reports_not_converged(ctx):
     r = _run(ctx, [s])[0]
     assert r["done"] and r["status"] == dvm.DVM_NOT_CONVERGED
     assert r["primal_iters"] == 40 and r["adjoint_iters"] == 40
+
+
+def test_ticks_run_as_one_graph_and_reuse_device_tables(ctx):
+    """Every tick of a graph-capable context is one CUDA-graph launch (sweeps, reductions, read-back);
+    the graph is captured again only when a table outgrows its capacity, and the tables are uploaded
+    again only when the admitted set or a request's phase changes.  A context without graphs runs the
+    same launches directly and gives bit-for-bit the same results."""
+    specs = _specs()
+    srv = serve.BatchServer(ctx, sweeps_per_tick=M)
+    tickets = [srv.submit(s) for s in specs]
+    for _ in range(10000):
+        if srv.tick() == (0, 0):
+            break
+    st = srv.stats()
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    assert st["ticks"] > 20 and st["graph_launches"] == st["ticks"]
+    assert 1 <= st["graph_builds"] <= 4
+    assert st["table_uploads"] <= 3 * len(specs)           # admission, adjoint start and retirement at most
+    assert st["peak_active"] == len(specs) and st["peak_bytes"] > 0
+    plain = dvm.Context(0, graph_iters=M, graphs=False)
+    srv2 = serve.BatchServer(plain, sweeps_per_tick=M)
+    t2 = [srv2.submit(s) for s in specs]
+    for _ in range(10000):
+        if srv2.tick() == (0, 0):
+            break
+    assert srv2.stats()["graph_launches"] == 0
+    for a, t in zip(res, t2):
+        b = srv2.poll(t)
+        assert a["J"] == b["J"] and a["primal_iters"] == b["primal_iters"]
+        assert np.array_equal(a["grad"], b["grad"])
+    srv2.close()
+    plain.close()
