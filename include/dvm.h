@@ -115,9 +115,10 @@ typedef struct {
                                the composed state (its increment s = -R/D), then solves J e = -R for the correction
                                e by linearised FP32 point-implicit sweeps at fbar + delta (J the Jacobian of R:
                                upwind transport, the linearised Maxwellian and relaxation rate with lagged moment
-                               couplings, the wall density), until the linear residual falls below a tenth of |R|,
-                               stalls, or refine_sweeps; then delta += e and (fbar, delta) is renormalised by a
-                               two-sum.  Rounding in the FP32 sweeps is relative to e, not to f, so the solution
+                               couplings, the wall density), until the linear residual falls below a tenth of |R|
+                               or after refine_sweeps (the residual of these sweeps can stay near |R| for hundreds
+                               of sweeps at small Kn before it decays, so there is no stall exit); then delta += e
+                               and (fbar, delta) is renormalised by a two-sum.  Rounding in the FP32 sweeps is relative to e, not to f, so the solution
                                reaches the FP64 one; the state ends at fl(fbar + delta) and J, Cd and residual of
                                the result are those of fbar + delta in FP64.  Temporary device memory: an FP64
                                state and four FP32 arrays of the state's size, freed at the end.  Errors:

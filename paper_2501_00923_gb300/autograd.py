@@ -36,6 +36,8 @@ class DragProblem:
     mesh_fn: object = None          # alpha -> OMesh; default: the Hicks-Henne bump section
     order: int = 1                  # 2: second-order reconstruction
     maxwellian: str = "plain"       # or "conservative"
+    refine_tol: float = 0.0         # > 0 (FP32, order 1, plain): mixed-precision refinement of the primal to this
+                                    # FP64 residual after the sweeps (dvm_solve_opts.refine_tol)
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
@@ -63,7 +65,7 @@ class DragProblem:
         st.order = self.order
         st, res = dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw,
                                    self.flow.aoa, tol=self.tol, max_iter=self.max_iter, storage=self.storage,
-                                   state=st, stall_window=self.stall_window)
+                                   state=st, stall_window=self.stall_window, refine_tol=self.refine_tol)
         self.last = {"mesh": mesh, "m": m, "state": st, "primal": res}
         return res.J / self.q_ref
 
@@ -143,6 +145,8 @@ def main(argv=None):
     ap.add_argument("--stall", type=int, default=3000)
     ap.add_argument("--fd", type=int, default=0, help="amplitudes checked by central differences")
     ap.add_argument("--h", type=float, default=1e-4, help="difference step")
+    ap.add_argument("--refine-tol", type=float, default=0.0,
+                    help="> 0: mixed-precision refinement of every primal solve to this FP64 residual")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -151,7 +155,8 @@ def main(argv=None):
     ctx = dvm.Context(0)
     a0 = wl.mesh.alpha
     prob = DragProblem(ctx, wl.mesh.ni, wl.mesh.nj, wl.grid, flow, storage=args.storage, tol=args.tol,
-                       adjoint_tol=args.tol, max_iter=args.max_sweeps, stall_window=args.stall)
+                       adjoint_tol=args.tol, max_iter=args.max_sweeps, stall_window=args.stall,
+                       refine_tol=args.refine_tol)
     alpha = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
     t0 = time.perf_counter()
     cd = drag(alpha, prob)
@@ -163,6 +168,7 @@ def main(argv=None):
     out = {"workload": wl.name, "Kn": flow.Kn, "storage": args.storage, "cells": wl.mesh.ncell, "velocities": wl.grid.nv,
            "Cd": float(cd.item()), "forward_s": t1 - t0, "backward_s": t2 - t1,
            "primal_sweeps": pres.iters, "primal_status": dvm.status_string(pres.status), "primal_residual": pres.residual,
+           "refine_steps": pres.refine_steps, "refine_sweeps": pres.refine_sweeps,
            "adjoint_sweeps": ares.iters, "adjoint_status": dvm.status_string(ares.status),
            "adjoint_residual": ares.residual, "grad": g.tolist()}
     prob.release()

@@ -4,12 +4,6 @@ adjoint to tol, then the full-discrete sensitivity; one JSON line per (Kn, mixin
 
     python -m paper_2501_00923_gb300.convergence --kn 0.1,0.01 --accel none,5x10,5x20
 
-With --refine the tool measures mixed-precision refinement instead: an FP32 solve to its rounding
-floor, then FP64 sweeps with mixing (--accel, one value) started from the FP32 state and adjoint,
-against a cold FP64 solve with the same mixing; both to --tol.
-
-    python -m paper_2501_00923_gb300.convergence --refine --kn 0.01 --accel 5x10 --tol 1e-11
-
 With --mesh-study the tool measures the spatial order of accuracy instead: the drag of the NACA 0012
 section at the first --kn on a nested family of O-meshes (--mesh-study 64x32,128x64,...: the angular
 count and the radial count double, and the radial stretching ratio goes to its square root, so every
@@ -48,7 +42,6 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--stall", type=int, default=3000)
     ap.add_argument("--max-sweeps", type=int, default=200000)
-    ap.add_argument("--refine", action="store_true", help="FP32 solve, then FP64 sweeps from it (see above)")
     ap.add_argument("--mesh-study", default="", help="comma list of nested O-mesh sizes (see above)")
     ap.add_argument("--nv", type=int, default=24, help="velocity points per axis of the mesh study")
     ap.add_argument("--ma", type=float, default=0.8)
@@ -65,11 +58,6 @@ def main(argv=None):
     ctx = dvm.Context(0)
     m = dvm.Mesh(ctx, mesh.nodes)
     g = dvm.VGrid(ctx, wl.grid.vx, wl.grid.vy, wl.grid.w)
-    if args.refine:
-        for kn in (float(x) for x in args.kn.split(",")):
-            _refine(ctx, m, g, mesh, kn, wl.flow.Ma, _accel(args.accel.split(",")[0]), args)
-        ctx.close()
-        return
     for kn in (float(x) for x in args.kn.split(",")):
         for tok in args.accel.split(","):
             accel = _accel(tok)
@@ -91,47 +79,6 @@ def main(argv=None):
             ad.close()
             st.close()
     ctx.close()
-
-
-def _refine(ctx, m, g, mesh, kn, Ma, accel, args):
-    """FP32 to its floor, FP64 with mixing from there, against a cold FP64 solve with mixing."""
-    t = [time.perf_counter()]
-    s32, p32 = dvm.primal_solve(ctx, m, g, kn, Ma, tol=args.tol, max_iter=args.max_sweeps, storage="fp32",
-                                stall_window=args.stall)
-    a32, q32 = dvm.adjoint_solve(ctx, s32, tol=args.tol, max_iter=args.max_sweeps, stall_window=args.stall)
-    t.append(time.perf_counter())
-    s64 = dvm.State(ctx, m, g, kn, Ma, storage="fp64")
-    s64.set(s32.get())
-    s64, p64 = dvm.primal_solve(ctx, m, g, kn, Ma, tol=args.tol, max_iter=args.max_sweeps, storage="fp64",
-                                state=s64, accel=accel)
-    a64 = dvm.Adjoint(s64)
-    a64.set(a32.get())
-    a64, q64 = dvm.adjoint_solve(ctx, s64, tol=args.tol, max_iter=args.max_sweeps, adjoint=a64, accel=accel)
-    t.append(time.perf_counter())
-    g_ref = dvm.sensitivity(ctx, s64, a64, mesh.dwall, mesh.s, mode="full")
-    g32 = dvm.sensitivity(ctx, s32, a32, mesh.dwall, mesh.s, mode="full")
-    for h in (a32, s32, a64, s64):
-        h.close()
-    t.append(time.perf_counter())
-    c64, cp = dvm.primal_solve(ctx, m, g, kn, Ma, tol=args.tol, max_iter=args.max_sweeps, storage="fp64", accel=accel)
-    ca, cq = dvm.adjoint_solve(ctx, c64, tol=args.tol, max_iter=args.max_sweeps, accel=accel)
-    t.append(time.perf_counter())
-    g_cold = dvm.sensitivity(ctx, c64, ca, mesh.dwall, mesh.s, mode="full")
-    ca.close()
-    c64.close()
-    scale = float(np.abs(g_cold).max())
-    print(json.dumps({
-        "Kn": kn, "accel": accel, "tol": args.tol,
-        "fp32": {"s": t[1] - t[0], "primal_sweeps": p32.iters, "adjoint_sweeps": q32.iters,
-                 "drag_rel_to_fp64": abs(p32.J - cp.J) / abs(cp.J),
-                 "sens_rel_to_fp64": float(np.abs(g32 - g_cold).max()) / scale},
-        "fp64_from_fp32": {"s": t[2] - t[1], "primal_sweeps": p64.iters, "primal_status": dvm.status_string(p64.status),
-                           "adjoint_sweeps": q64.iters, "adjoint_status": dvm.status_string(q64.status),
-                           "drag_rel_to_cold": abs(p64.J - cp.J) / abs(cp.J),
-                           "sens_rel_to_cold": float(np.abs(g_ref - g_cold).max()) / scale},
-        "fp64_cold": {"s": t[4] - t[3], "primal_sweeps": cp.iters, "primal_status": dvm.status_string(cp.status),
-                      "adjoint_sweeps": cq.iters, "adjoint_status": dvm.status_string(cq.status), "J": cp.J}}),
-          flush=True)
 
 
 def _nested_meshes(sizes, radius=10.0, first=1e-3):

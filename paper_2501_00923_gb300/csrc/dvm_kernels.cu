@@ -2227,7 +2227,7 @@ __global__ void k_sens_paper_nodes(int ni, const double2* nodes, const double2* 
 // multiplies dV_c/dalpha; the wall face adds J's own S-dependence and the n-dependence
 // (I - n n^T)/A * H * Vf with H = sum_{a<=0} w a (m gbar1 + phi . gbar), Vf = sum_k w v f1_l.
 template <class TS>
-__global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, int ncell, int nvp,
+__global__ void __launch_bounds__(256, 2) k_sens_faces(const TS* f, const TS* phi, int ncell, int nvp,
                                                     const int4* nb, const double2* S, const double* Vc,
                                                     const typename Vec<typename Pack<TS>::TC>::v4* vt,
                                                     const typename Vec<typename Pack<TS>::TC>::v2* fd,
@@ -2260,6 +2260,19 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
     const uint4* pq = reinterpret_cast<const uint4*>(phi);
     const size_t north = n.y >= 0 ? (size_t)n.y : (size_t)c;    // far field: own chunk, not used
     const size_t east = (size_t)n.z;
+    const bool far = n.y < 0;
+    // per-lane sums in plain TC over blocks of kSensBlock chunks, then one compensated add per block
+    constexpr int kSensBlock = 4;
+    TC b[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) b[i] = TC(0);
+    auto flush = [&]() {
+        gnx.add(b[0]); gny.add(b[1]); gex.add(b[2]); gey.add(b[3]); vs.add(b[4]);
+        if (wall) { gwx.add(b[5]); gwy.add(b[6]); H.add(b[7]); vfx.add(b[8]); vfy.add(b[9]); }
+#pragma unroll
+        for (int i = 0; i < 10; ++i) b[i] = TC(0);
+    };
+    int nb_ = 0;
     for (size_t q = lane; q < nq; q += 32) {
         TC fc1[KV], fc2[KV], pc1[KV], pc2[KV], fn1[KV], fn2[KV], pn1[KV], pn2[KV], fe1[KV], fe2[KV], pe1[KV], pe2[KV];
         PK::unpack(ldg16(fq + (size_t)c * nq + q), fc1, fc2);
@@ -2273,44 +2286,43 @@ __global__ void __launch_bounds__(256) k_sens_faces(const TS* f, const TS* phi, 
             const int k = (int)q * KV + kk;
             const auto t = vt[k];
             const TC vx = t.x, vy = t.y, w = t.z;
-            {   // north face
+            {   // north face: upwind value (own cell on outflow, north cell or far field on inflow)
                 const TC a = s1x * vx + s1y * vy;
-                TC F1, F2, q1 = TC(0), q2 = TC(0);
-                if (n.y >= 0) {
-                    q1 = pn1[kk]; q2 = pn2[kk];
-                    if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; } else { F1 = fn1[kk]; F2 = fn2[kk]; }
-                } else if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; }
-                else { F1 = fd[k].x; F2 = fd[k].y; }
+                TC i1 = fn1[kk], i2 = fn2[kk], q1 = pn1[kk], q2 = pn2[kk];
+                if (far) {
+                    const auto d = fd[k];
+                    i1 = d.x; i2 = d.y; q1 = TC(0); q2 = TC(0);
+                }
+                const bool out = a > TC(0);
+                const TC F1 = out ? fc1[kk] : i1, F2 = out ? fc2[kk] : i2;
                 const TC d = w * ((pc1[kk] - q1) * F1 + (pc2[kk] - q2) * F2);
-                gnx.add(d * vx); gny.add(d * vy);
+                b[0] += d * vx; b[1] += d * vy;
             }
             {   // east face (always interior)
-                const TC a = s2x * vx + s2y * vy;
-                TC F1, F2;
-                if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; } else { F1 = fe1[kk]; F2 = fe2[kk]; }
+                const bool out = s2x * vx + s2y * vy > TC(0);
+                const TC F1 = out ? fc1[kk] : fe1[kk], F2 = out ? fc2[kk] : fe2[kk];
                 const TC d = w * ((pc1[kk] - pe1[kk]) * F1 + (pc2[kk] - pe2[kk]) * F2);
-                gex.add(d * vx); gey.add(d * vy);
+                b[2] += d * vx; b[3] += d * vy;
             }
             if (wall) {
                 const TC a = s3x * vx + s3y * vy;
                 const TC m = dirx * vx + diry * vy + hcoef * t.w;
-                TC F1, F2;
-                if (a > TC(0)) { F1 = fc1[kk]; F2 = fc2[kk]; }
-                else {
-                    const TC gb1 = gw[k] * gbs;
-                    F1 = cw * gw[k]; F2 = cw * halfTw * gw[k];
-                    H.add(w * a * gb1 * (m + pc1[kk] + halfTw * pc2[kk]));
-                }
+                const bool out = a > TC(0);
+                const TC gk = gw[k];
+                const TC F1 = out ? fc1[kk] : cw * gk, F2 = out ? fc2[kk] : cw * halfTw * gk;
+                if (!out) b[7] += w * a * (gk * gbs) * (m + pc1[kk] + halfTw * pc2[kk]);
                 const TC d = w * (pc1[kk] * F1 + pc2[kk] * F2 + m * F1);
-                gwx.add(d * vx); gwy.add(d * vy);
-                vfx.add(w * vx * F1); vfy.add(w * vy * F1);
+                b[5] += d * vx; b[6] += d * vy;
+                b[8] += w * vx * F1; b[9] += w * vy * F1;
             }
             {   // volume term
                 const TC g1 = G.eval(fma(vy, -u2, fma(vx, -u1, (TC)t.w)));
-                vs.add(w * (pc1[kk] * (fc1[kk] - g1) + pc2[kk] * (fc2[kk] - halfT * g1)));
+                b[4] += w * (pc1[kk] * (fc1[kk] - g1) + pc2[kk] * (fc2[kk] - halfT * g1));
             }
         }
+        if (++nb_ == kSensBlock) { flush(); nb_ = 0; }
     }
+    flush();
     const double GNX = warp_sum(gnx.get()), GNY = warp_sum(gny.get()), GEX = warp_sum(gex.get());
     const double GEY = warp_sum(gey.get()), VS = warp_sum(vs.get());
     double GWX = 0, GWY = 0, HH = 0, VFX = 0, VFY = 0;
