@@ -117,15 +117,39 @@ typedef struct {
                                upwind transport, the linearised Maxwellian and relaxation rate with lagged moment
                                couplings, the wall density), until the linear residual falls below a tenth of |R|
                                or after refine_sweeps (the residual of these sweeps can stay near |R| for hundreds
-                               of sweeps at small Kn before it decays, so there is no stall exit); then delta += e
-                               and (fbar, delta) is renormalised by a two-sum.  Rounding in the FP32 sweeps is relative to e, not to f, so the solution
+                               of sweeps at small Kn before it decays, so there is no stall exit); with
+                               predict_iters > 0 every block of these sweeps is followed by the macroscopic
+                               prediction of e (the same moment system at fbar + delta, linear: e += (dg/dW) dW).
+                               Then delta += e and (fbar, delta) is renormalised by a two-sum.  Rounding in the
+                               FP32 sweeps is relative to e, not to f, so the solution
                                reaches the FP64 one; the state ends at fl(fbar + delta) and J, Cd and residual of
                                the result are those of fbar + delta in FP64.  Temporary device memory: an FP64
                                state and four FP32 arrays of the state's size, freed at the end.  Errors:
                                DVM_ERR_INVALID_ARG for another storage, order or Maxwellian */
     int refine_max;         /* correction steps at most (0 -> 20); the refinement also stops (DVM_ERR_STAGNATED)
-                               when a step leaves the FP64 residual above 0.7 of the best so far */
+                               when two steps in a row leave the FP64 residual above 0.7 of the best so far (one
+                               such step is allowed: far from the solution a step can raise |R| while it cuts the
+                               error, by the quadratic term of R in e) */
     int refine_sweeps;      /* linearised FP32 sweeps per correction step at most (0 -> 4000) */
+    double predict_omega;   /* damping of the macroscopic prediction's correction (0 -> 0.8) */
+    int predict_iters;      /* primal solves, FP64 or FP32 storage, order 1, plain Maxwellian; 0 = off.  > 0: after every block of
+                               graph_iters sweeps a macroscopic prediction (the prediction acceleration of
+                               Sec. 3.1 by equations for the moments): the moments of the steady residual of
+                               Eq. (numerpr_gov) per cell (from the block's last sweep) are cancelled by a moment
+                               correction dW solved, with this many block-Jacobi iterations, from the discrete
+                               transport of the Maxwellian derivative in moment form (4 x 4 blocks per cell and
+                               face: upwind outflow at the cell's moments, inflow from the neighbour, re-emission
+                               on the wall); f is then shifted by g(W + s omega dW) - g(W), s <= 1 keeping each
+                               cell's density and temperature within 30% and positive.  At small Kn the slow
+                               modes of the sweeps are these moments, so this removes most of their sweeps; the
+                               steady solution is unchanged (the shift vanishes at it).  FP32 storage: near
+                               the rounding floor the residual moments are dominated by the rounding of the
+                               relaxation term, which the moment solve amplifies into smooth errors; once a block
+                               ends with a residual above twice the best so far the prediction is switched off
+                               and the solve goes on with plain sweeps.  With refinement, stop the FP32 sweeps
+                               early (tol ~1e-5) and let the predicted refinement finish.  Temporary memory: 85
+                               doubles per cell, kept with the state */
+    int predict_reuse;      /* predictions between reassemblies of the moment system (0 -> 4) */
 } dvm_solve_opts;
 
 typedef struct {
@@ -139,6 +163,7 @@ typedef struct {
     int refine_sweeps;      /* linearised FP32 sweeps of the refinement */
     double residual_fp32;   /* |R|/r0 of the FP32 sweeps when they stopped (= residual without refinement) */
     double residual_fp64;   /* refinement: the FP64 residual |R|/r0 of the state the FP32 sweeps left */
+    int predictions;        /* macroscopic predictions applied (one per block of sweeps) */
 } dvm_primal_result;
 
 typedef struct {

@@ -38,6 +38,8 @@ class DragProblem:
     maxwellian: str = "plain"       # or "conservative"
     refine_tol: float = 0.0         # > 0 (FP32, order 1, plain): mixed-precision refinement of the primal to this
                                     # FP64 residual after the sweeps (dvm_solve_opts.refine_tol)
+    predict: int = 0                # > 0 (FP64/FP32, order 1, plain): macroscopic prediction after every block of
+                                    # primal sweeps, this many block-Jacobi iterations (dvm_solve_opts.predict_iters)
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
@@ -61,11 +63,13 @@ class DragProblem:
         elif self.order == 2:               # second order starts from the converged first-order state
             dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa,
                              tol=self.tol, max_iter=self.max_iter, storage=self.storage, state=st,
-                             stall_window=self.stall_window)
+                             stall_window=self.stall_window, predict=self.predict if self.maxwellian == "plain" else 0)
         st.order = self.order
+        plain1 = self.order == 1 and self.maxwellian == "plain"
         st, res = dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw,
                                    self.flow.aoa, tol=self.tol, max_iter=self.max_iter, storage=self.storage,
-                                   state=st, stall_window=self.stall_window, refine_tol=self.refine_tol)
+                                   state=st, stall_window=self.stall_window, refine_tol=self.refine_tol,
+                                   predict=self.predict if plain1 else 0)
         self.last = {"mesh": mesh, "m": m, "state": st, "primal": res}
         return res.J / self.q_ref
 
@@ -147,6 +151,9 @@ def main(argv=None):
     ap.add_argument("--h", type=float, default=1e-4, help="difference step")
     ap.add_argument("--refine-tol", type=float, default=0.0,
                     help="> 0: mixed-precision refinement of every primal solve to this FP64 residual")
+    ap.add_argument("--predict", type=int, default=0,
+                    help="> 0: macroscopic prediction of the primal sweeps (block-Jacobi iterations)")
+    ap.add_argument("--adjoint-tol", type=float, default=None, help="adjoint tolerance (default: --tol)")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -155,8 +162,9 @@ def main(argv=None):
     ctx = dvm.Context(0)
     a0 = wl.mesh.alpha
     prob = DragProblem(ctx, wl.mesh.ni, wl.mesh.nj, wl.grid, flow, storage=args.storage, tol=args.tol,
-                       adjoint_tol=args.tol, max_iter=args.max_sweeps, stall_window=args.stall,
-                       refine_tol=args.refine_tol)
+                       adjoint_tol=args.adjoint_tol if args.adjoint_tol is not None else args.tol,
+                       max_iter=args.max_sweeps, stall_window=args.stall, refine_tol=args.refine_tol,
+                       predict=args.predict)
     alpha = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
     t0 = time.perf_counter()
     cd = drag(alpha, prob)
@@ -168,7 +176,7 @@ def main(argv=None):
     out = {"workload": wl.name, "Kn": flow.Kn, "storage": args.storage, "cells": wl.mesh.ncell, "velocities": wl.grid.nv,
            "Cd": float(cd.item()), "forward_s": t1 - t0, "backward_s": t2 - t1,
            "primal_sweeps": pres.iters, "primal_status": dvm.status_string(pres.status), "primal_residual": pres.residual,
-           "refine_steps": pres.refine_steps, "refine_sweeps": pres.refine_sweeps,
+           "refine_steps": pres.refine_steps, "refine_sweeps": pres.refine_sweeps, "predictions": pres.predictions,
            "adjoint_sweeps": ares.iters, "adjoint_status": dvm.status_string(ares.status),
            "adjoint_residual": ares.residual, "grad": g.tolist()}
     prob.release()

@@ -95,6 +95,12 @@ struct dvm_state {
     double4* fit = nullptr;     // its parameters for the current f
     AAState* aaW = nullptr;     // moment-space mixing: history over the cell moments
     double* Wbuf = nullptr;     // [ncell][4] FP64 moments
+    // macroscopic prediction (dvm_solve_opts.predict_iters > 0; see k_coarse_assemble)
+    bool predict = false;       // the residual sweep of each block also writes the residual's moments
+    double* co_out = nullptr;   // [ncell][4][16] outflow blocks of the moment system
+    double* co_dinv = nullptr;  // [ncell][16] inverses of its diagonal blocks
+    double4* co_rW = nullptr;   // [ncell] moments of the residual
+    double4* co_x[2] = {nullptr, nullptr};
     int shard = 0;              // 1: a velocity shard (sweeps write partial sums; see dvm_state_set_shard)
     double* part = nullptr;     // [shard_count] this shard's partial sums
     double* part_total = nullptr;   // [shard_count] the summed buffer of all shards
@@ -326,6 +332,7 @@ PrimalArgs<TS, TC> primal_args(const dvm_state* st, int src) {
     a.err = st->ctx->derr;
     a.defect = st->order == 2 ? (const TS*)st->so[2] : nullptr;
     a.part = st->shard ? st->part : nullptr;
+    a.rW = st->predict ? st->co_rW : nullptr;
     return a;
 }
 
@@ -405,7 +412,7 @@ cudaError_t enqueue_second_order(const dvm_state* st, const void* in, const doub
 }
 
 // Identity of the discretisation a captured graph was built for (spatial order, Maxwellian).
-int scheme_of(const dvm_state* st) { return 2 * st->order + st->maxwell; }
+int scheme_of(const dvm_state* st) { return 2 * st->order + st->maxwell + 8 * (st->predict ? 1 : 0); }
 
 // Defect correction: the defect is taken from the sweep's input at the first sweep of each group of
 // so_period sweeps and frozen for the rest of the group.  Counts its launches (into the graph's count
@@ -431,10 +438,17 @@ cudaError_t enqueue_primal(dvm_state* st, int src, bool res = true) {
     }
     cudaError_t e;
     auto launch = st->shard ? launch_primal_shard_sweep : launch_primal_sweep;
+    const bool rm = st->predict && res && st->order == 1 && !st->shard;   // residual moments for the prediction
     switch (st->storage) {
-        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src); e = launch(0, &a, st->maps[src], res, st->ctx->stream); break; }
-        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src); e = launch(1, &a, st->maps[src], res, st->ctx->stream); break; }
-        default: { auto a = primal_args<__nv_bfloat16, float>(st, src); e = launch(2, &a, st->maps[src], res, st->ctx->stream); break; }
+        case DVM_STORE_FP64: { auto a = primal_args<double, double>(st, src);
+                               e = rm ? launch_primal_sweep_rm(0, &a, st->maps[src], st->ctx->stream)
+                                      : launch(0, &a, st->maps[src], res, st->ctx->stream); break; }
+        case DVM_STORE_FP32: { auto a = primal_args<float, float>(st, src);
+                               e = rm ? launch_primal_sweep_rm(1, &a, st->maps[src], st->ctx->stream)
+                                      : launch(1, &a, st->maps[src], res, st->ctx->stream); break; }
+        default: { auto a = primal_args<__nv_bfloat16, float>(st, src);
+                   e = rm ? launch_primal_sweep_rm(2, &a, st->maps[src], st->ctx->stream)
+                          : launch(2, &a, st->maps[src], res, st->ctx->stream); break; }
     }
     if (e == cudaSuccess && st->maxwell) {
         // the next sweep's Maxwellian: one Newton step from the previous fit
@@ -678,6 +692,11 @@ int check_solve_opts(const dvm_solve_opts* o) {
     if (o->accel_space != 0 && o->accel_space != 1) return fail(DVM_ERR_INVALID_ARG, "accel_space must be 0 or 1");
     if (!(o->refine_tol >= 0.0) || o->refine_max < 0 || o->refine_sweeps < 0)
         return fail(DVM_ERR_INVALID_ARG, "refine_tol, refine_max and refine_sweeps must be >= 0");
+    if (o->predict_iters < 0 || o->predict_iters > 1000 || o->predict_reuse < 0 ||
+        !(o->predict_omega >= 0.0 && o->predict_omega <= 1.0))
+        return fail(DVM_ERR_INVALID_ARG, "predict_iters must be in [0, 1000], predict_reuse >= 0, predict_omega in [0, 1]");
+    if (o->predict_iters > 0 && o->accel_depth > 0)
+        return fail(DVM_ERR_INVALID_ARG, "the macroscopic prediction and Anderson mixing exclude each other");
     return DVM_OK;
 }
 
@@ -1006,6 +1025,7 @@ void dvm_state_destroy(dvm_state* st) {
     dfree(st->Wbuf);
     dfree(st->part);
     dfree(st->part_total);
+    dfree(st->co_out); dfree(st->co_dinv); dfree(st->co_rW); dfree(st->co_x[0]); dfree(st->co_x[1]);
     st->ctx->bytes -= st->bytes;
     delete st;
 }
@@ -1323,6 +1343,47 @@ int dvm_state_functional(dvm_state* st, int functional, double* J) {
 // J e = -R by linearised FP32 sweeps (k_primal_lin_sweep) and adds e to delta, renormalised into fbar.
 namespace {
 
+// Buffers of the macroscopic prediction, allocated on the first predicted solve and kept with the state.
+static int predict_ensure(dvm_state* st) {
+    if (st->co_out) return DVM_OK;
+    dvm_context* ctx = st->ctx;
+    const size_t nc = (size_t)st->mesh->d.ncell;
+    size_t acc = 0;
+    int rc;
+    if ((rc = dalloc(ctx, &st->co_out, 64 * nc, &acc))) return rc;
+    if ((rc = dalloc(ctx, &st->co_dinv, 16 * nc, &acc))) return rc;
+    if ((rc = dalloc(ctx, &st->co_rW, nc, &acc))) return rc;
+    if ((rc = dalloc(ctx, &st->co_x[0], nc, &acc))) return rc;
+    if ((rc = dalloc(ctx, &st->co_x[1], nc, &acc))) return rc;
+    if (!st->Wbuf && (rc = dalloc(ctx, &st->Wbuf, 4 * nc, &acc))) return rc;
+    st->bytes += acc;
+    ctx->bytes += acc;
+    return DVM_OK;
+}
+
+// One macroscopic prediction after a block whose last sweep wrote the moments of its residual to co_rW:
+// (re)assemble the moment system at the current moments if asked, `iters` block-Jacobi iterations for dW,
+// the limited target moments, the Maxwellian shift of f to them, and the moments of the shifted f.
+static int predict_step(dvm_state* st, int iters, double omega, bool assemble) {
+    const DevMesh& m = st->mesh->d;
+    const DevGrid& g = st->grid->d;
+    cudaStream_t s = st->ctx->stream;
+    const int c = st->cur;
+    if (assemble) {
+        CK(launch_coarse_assemble(st->storage, m, g, st->fl, st->prim[c], st->co_out, st->co_dinv, s));
+        st->ctx->launches += 1;
+    }
+    for (int i = 0; i < iters; ++i)
+        CK(launch_coarse_jacobi(m, st->co_out, st->co_dinv, st->co_rW, st->co_x[(i + 1) & 1], st->co_x[i & 1],
+                                i == 0, s));
+    CK(launch_coarse_target(m.ncell, st->prim[c], st->co_x[(iters - 1) & 1], omega, 0.3, st->Wbuf, s));
+    CK(launch_moment_shift(st->storage, st->f[c], m, g, st->prim[c], st->Wbuf, s));
+    CK(launch_moments(st->storage, st->f[c], m, g, st->prim[c], st->Fw[c], s));
+    st->ctx->launches += iters + 3;
+    st->version += 1;
+    return DVM_OK;
+}
+
 struct RefineWork {
     dvm_context* ctx = nullptr;
     dvm_state* s64 = nullptr;
@@ -1366,11 +1427,15 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
         CK(make_tmamaps(W.e[b], m.ni, m.nj, g.nvp / 2, &W.maps[b]));
     }
     CK(cudaMemsetAsync(W.delta, 0, nf * sizeof(float), s));
+    const bool pred = o->predict_iters > 0;     // the macroscopic prediction of the correction sweeps
+    if (pred && (rc = predict_ensure(st))) return rc;
+    const double omega = o->predict_omega > 0.0 ? o->predict_omega : 0.8;
+    int predictions = 0;
     const int max_steps = o->refine_max > 0 ? o->refine_max : 20;
     const int max_sweeps = o->refine_sweeps > 0 ? o->refine_sweeps : 4000;
     constexpr int kBlock = 20;             // linearised sweeps between residual checks
     double r64 = INFINITY, best = INFINITY, J64 = 0.0;
-    int steps = 0, sweeps = 0, status = DVM_NOT_CONVERGED;
+    int steps = 0, sweeps = 0, misses = 0, status = DVM_NOT_CONVERGED;
     float* fbar = static_cast<float*>(st->f[st->cur]);
     for (;;) {
         // exact residual of fbar + delta: compose it in the FP64 state and sweep that once
@@ -1390,8 +1455,14 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
         if (!std::isfinite(r64) || !std::isfinite(J64)) { status = fail(DVM_ERR_NONFINITE, "refinement residual is not finite"); break; }
         if (r64 <= o->refine_tol) { status = DVM_OK; break; }
         if (steps >= max_steps) { status = DVM_NOT_CONVERGED; break; }
-        if (r64 > 0.7 * best) { status = DVM_ERR_STAGNATED; break; }
-        best = r64;
+        // a step far from the solution can raise the residual while it cuts the error (the quadratic
+        // term of the residual in the correction): stagnation is two steps in a row without a cut to 0.7
+        if (r64 > 0.7 * best) {
+            if (++misses >= 2) { status = DVM_ERR_STAGNATED; break; }
+        } else {
+            misses = 0;
+        }
+        best = std::min(best, r64);
         // s = -R/D from that sweep; e solves J e = -R by linearised sweeps from e = 0
         CK(launch_refine_diff(static_cast<const double*>(s64->f[1 - c64]), static_cast<const double*>(s64->f[c64]),
                               W.src, m.ncell, g.nvp, s));
@@ -1403,9 +1474,14 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
         // linear residual can stay near (or above) |R| for hundreds of sweeps before it decays
         int ec = 0, n = 0;
         const double target = 0.1 * r64 * st->r0;
+        if (pred) {         // the moment system of the correction, linearised at fbar + delta
+            CK(launch_coarse_assemble(st->storage, m, g, st->fl, s64->prim[c64], st->co_out, st->co_dinv, s));
+            ctx->launches += 1;
+        }
         while (n < max_sweeps) {
             const int k = std::min(kBlock, max_sweeps - n);
             for (int i = 0; i < k; ++i) {
+                const bool rm = pred && i == k - 1;
                 PrimalArgs<float, float> a = primal_args<float, float>(st, st->cur);
                 a.f_old = W.e[ec]; a.f_new = W.e[1 - ec];
                 a.prim_old = a.maxw_old = s64->prim[c64];
@@ -1415,7 +1491,8 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
                 a.defect = nullptr;
                 a.lin_src = W.src; a.lin_f = fbar;
                 a.dW_old = W.dW[ec]; a.dW_new = W.dW[1 - ec];
-                CK(launch_primal_lin_sweep(&a, W.maps[ec], i == k - 1, s));
+                a.rW = rm ? st->co_rW : nullptr;
+                CK(launch_primal_lin_sweep(&a, W.maps[ec], i == k - 1, rm, s));
                 ec = 1 - ec;
             }
             CK(launch_finalize(W.rp, m.ncell, nullptr, nullptr, nullptr, m.ni, W.out, s));
@@ -1426,6 +1503,16 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
             const double rin = sqrt(lo[0]);
             if (!std::isfinite(rin)) return fail(DVM_ERR_NONFINITE, "refinement correction is not finite");
             if (rin <= target) break;
+            if (pred && n < max_sweeps) {
+                const int it = o->predict_iters;
+                for (int i = 0; i < it; ++i)
+                    CK(launch_coarse_jacobi(m, st->co_out, st->co_dinv, st->co_rW, st->co_x[(i + 1) & 1],
+                                            st->co_x[i & 1], i == 0, s));
+                CK(launch_coarse_lin_shift(m, g, s64->prim[c64], st->co_x[(it - 1) & 1], omega, 0.3, W.e[ec],
+                                           W.dW[ec], W.dF[ec], s));
+                ctx->launches += it + 1;
+                predictions += 1;
+            }
         }
         CK(launch_refine_update(fbar, W.delta, W.e[ec], nf, s));
         ctx->launches += 1;
@@ -1442,6 +1529,7 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
     res->residual = r64;
     res->refine_steps = steps;
     res->refine_sweeps = sweeps;
+    res->predictions += predictions;
     res->status = status;
     return status;
 }
@@ -1544,6 +1632,17 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
     const bool wspace = accel && opts->accel_space == 1;
     const int nc = st->mesh->d.ncell;
+    const bool predict = opts->predict_iters > 0;
+    if (predict && (st->order != 1 || st->maxwell || st->storage == DVM_STORE_BF16))
+        return fail(DVM_ERR_INVALID_ARG,
+                    "the macroscopic prediction needs an FP64 or FP32 state of order 1 with the plain Maxwellian");
+    if (predict && (rc = predict_ensure(st))) return rc;
+    st->predict = predict;
+    const int reuse = opts->predict_reuse > 0 ? opts->predict_reuse : 4;
+    const double omega = opts->predict_omega > 0.0 ? opts->predict_omega : 0.8;
+    int predictions = 0;
+    bool predicting = predict;
+    double pred_best = INFINITY;
     if (accel && !wspace) {
         const size_t n = (size_t)nc * st->grid->d.nvp * 2;
         if ((rc = aa_ensure(ctx, st->aa, st->storage, n, opts->accel_depth))) return rc;
@@ -1591,6 +1690,21 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
             mixing = false;                 // a stall while mixing: finish with plain sweeps, new window
             best = r;
             best_it = it;
+        }
+        if (predicting && st->storage != DVM_STORE_FP64) {
+            // FP32 storage: near the rounding floor the residual moments are dominated by the rounding
+            // of the relaxation term (V/tau times a storage ulp of f, large against transport at small Kn),
+            // which the moment solve amplifies; a residual well above the best seen shows it, and the solve
+            // finishes with plain sweeps
+            if (r > 2.0 * pred_best) {
+                predicting = false;
+                st->predict = false;
+            }
+            pred_best = std::min(pred_best, r);
+        }
+        if (predicting && k == K && it < opts->max_iter) {
+            if ((rc = predict_step(st, opts->predict_iters, omega, predictions % reuse == 0))) return rc;
+            predictions += 1;
         }
         if (mixing && k == K && it < opts->max_iter && wspace) {
             // moments after the block are G(x); mix them, impose the mixed moments on f by a
@@ -1654,6 +1768,8 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     res->r0 = st->r0;
     res->iters = it;
     res->status = status;
+    res->predictions = predictions;
+    st->predict = false;
     if (opts->refine_tol > 0.0 && status != DVM_ERR_NONFINITE) return refine_primal(st, opts, res);
     return status;
 }

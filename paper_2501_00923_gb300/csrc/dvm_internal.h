@@ -97,8 +97,11 @@ struct PrimalArgs {
     const double4* dW_old;
     double4* dW_new;
     // Velocity-space shard (the state holds a slice of the velocity grid): the sweep writes the raw
-    // velocity sums of its slice here instead of finishing the moments (layout: see shard_layout()).
+    // velocity sums of its slice here instead of finishing the moments (layout: see shard_count()).
     double* part;
+    // Macroscopic prediction: the residual sweep (kRes) also writes the moments sum_k w Psi_k R_k of its
+    // input's residual per cell, or nothing when null.
+    double4* rW;
 };
 
 // Partial sums of one velocity shard, doubles: [4 ncell] moment sums (sum w f1, w f1 vx, w f1 vy,
@@ -204,11 +207,13 @@ cudaError_t launch_shard_combine(const DevMesh& m, const double* total, double4*
                                  double* Jpart, double* wallD, double* wallM, cudaStream_t s);
 // res = false: skip the residual (only the sweeps whose residual is read need it).  maps: of f_old.
 cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
+// Residual sweep that also writes the residual's moments per cell to args.rW (macroscopic prediction).
+cudaError_t launch_primal_sweep_rm(int storage, const void* args, const TmaMaps& maps, cudaStream_t s);
 // Sweep of a velocity shard (args.part set): raw velocity sums of the slice into args.part.
 cudaError_t launch_primal_shard_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
 // Linearised correction sweep of the refinement (FP32 storage only; args: PrimalArgs<float, float> with the
 // lin_* fields set, maps: of the correction e_old).
-cudaError_t launch_primal_lin_sweep(const void* args, const TmaMaps& maps, bool res, cudaStream_t s);
+cudaError_t launch_primal_lin_sweep(const void* args, const TmaMaps& maps, bool res, bool rm, cudaStream_t s);
 // Refinement elementwise steps over FP32 states of ncell x nvp velocities: f64 <- fbar + delta (FP64 storage
 // layout); s <- f64_new - f64_old (FP32 layout); delta += e, then fbar <- fl(fbar + delta) and delta keeps the
 // exact remainder (two-sum).
@@ -237,6 +242,20 @@ cudaError_t launch_wait_probe(int* err, cudaStream_t s);
 cudaError_t launch_prim_to_W(int ncell, const double4* prim, double* W, cudaStream_t s);
 cudaError_t launch_moment_shift(int storage, void* f, const DevMesh& m, const DevGrid& g, const double4* prim,
                                 const double* W, cudaStream_t s);
+// Macroscopic prediction (see k_coarse_assemble): the moment-system blocks out [ncell][4 faces][4x4] and
+// the inverses of the diagonal blocks dinv [ncell][4x4] at the primitives prim; one block-Jacobi
+// iteration x_n = D^{-1}(-rW + sum OUT x_o) (first: from x = 0); the target moments W(prim) + s omega dW
+// with s <= 1 keeping each cell's density and temperature within a relative change cap.
+cudaError_t launch_coarse_assemble(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
+                                   const double4* prim, double* out, double* dinv, cudaStream_t s);
+cudaError_t launch_coarse_jacobi(const DevMesh& m, const double* out, const double* dinv, const double4* rW,
+                                 const double4* xo, double4* xn, bool first, cudaStream_t s);
+cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
+                                 double* W, cudaStream_t s);
+// Prediction of a linear correction e (FP32): e += (dg/dW) s omega x (s <= 1 keeps the density and
+// temperature parts within cap of the state's), then its moment sums dW and wall flux dF.
+cudaError_t launch_coarse_lin_shift(const DevMesh& m, const DevGrid& g, const double4* prim, const double4* x,
+                                    double omega, double cap, float* e, double4* dW, double* dF, cudaStream_t s);
 // Conservative discrete Maxwellian of every cell from its primitive variables (see k_maxwell_fit).
 cudaError_t launch_maxwell_fit(int storage, const DevMesh& m, const DevGrid& g, const double4* prim, double4* fit,
                                bool warm, int iters, double* Kinv, cudaStream_t s);

@@ -417,7 +417,7 @@ template <class TS> constexpr int kAdjointMinBlocks = std::is_same<typename Pack
 // the far field injects nothing, the wall re-emits (dF_rhow / D_l) gbar_w, and the right-hand side gains
 // D s, with s the increment of one FP64 sweep of the full problem.  One such sweep is e <- s + e - (J e)/D
 // with J the Jacobian of the steady residual, so at its fixed point J e = -R.
-template <class TS, bool kRes, int kBnd, bool kDef, bool kLin, bool kShard>
+template <class TS, bool kRes, int kBnd, bool kDef, bool kLin, bool kShard, bool kRM>
 __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& P, int c, int w, int lane,
                                                    const Feed& F) {
     using PK = Pack<TS>;
@@ -459,11 +459,13 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     uint4* fw = reinterpret_cast<uint4*>(P.f_new);
     const unsigned nq = (unsigned)P.nq, niter = (nq + kRowChunks - 1) / kRowChunks, oc = (unsigned)c * nq;
 
-    Sum<float> m0, m1, m2, m3, fwa, ja, rs;
+    Sum<float> m0, m1, m2, m3, fwa, ja, rs, q0, q1, q2, q3;
+    constexpr bool rmom = kRes && kRM;               // moments of the residual (macroscopic prediction)
     bool ok = true;
     unsigned it = 0;
     while (it < niter && ok) {
         float2 bm0 = bc(0.f), bm1 = bm0, bm2 = bm0, bm3 = bm0, bfw = bm0, bj = bm0, brs = bm0;
+        float2 bq0 = bm0, bq1 = bm0, bq2 = bm0, bq3 = bm0;
         for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
             ok = pipeline_step(F, it, niter, lane, [&](const uint4* d) {
 #pragma unroll
@@ -548,6 +550,13 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
                         const float2 R1 = pmul(D, pfma(x1, bc(-1.f), pair_of<KV>(fo1, pp)));
                         const float2 R2 = pmul(D, pfma(x2, bc(-1.f), pair_of<KV>(fo2, pp)));
                         brs = pfma(wk, pfma(R2, R2, pmul(R1, R1)), brs);
+                        if (rmom) {
+                            const float2 wR = pmul(wk, R1);
+                            bq0 = padd(bq0, wR);
+                            bq1 = pfma(wR, vx, bq1);
+                            bq2 = pfma(wR, vy, bq2);
+                            bq3 = pfma(wk, R2, pfma(wR, hv, bq3));
+                        }
                     }
                     const float2 wf1 = pmul(wk, x1);
                     bm0 = padd(bm0, wf1);
@@ -566,12 +575,17 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
         }
         m0.add(bm0.x + bm0.y); m1.add(bm1.x + bm1.y); m2.add(bm2.x + bm2.y); m3.add(bm3.x + bm3.y);
         if (kRes) rs.add(brs.x + brs.y);
+        if (rmom) { q0.add(bq0.x + bq0.y); q1.add(bq1.x + bq1.y); q2.add(bq2.x + bq2.y); q3.add(bq3.x + bq3.y); }
         if (wall) { fwa.add(bfw.x + bfw.y); ja.add(bj.x + bj.y); }
     }
     if (!ok) return false;
     const float M0 = m0.total(), M1 = m1.total(), M2 = m2.total(), M3 = m3.total();
     float RS = 0.f, FW = 0.f, JA = 0.f;
     if (kRes) RS = rs.total();
+    if (rmom) {
+        const float Q0 = q0.total(), Q1 = q1.total(), Q2 = q2.total(), Q3 = q3.total();
+        if (lane == 0) P.rW[c] = make_double4(Q0, Q1, Q2, Q3);
+    }
     if (wall) { FW = fwa.total(); JA = ja.total(); }
     if (kShard && lane == 0) {           // velocity shard: raw sums of this slice
         const size_t nc = (size_t)P.ncell;
@@ -603,7 +617,7 @@ __device__ __forceinline__ bool primal_cell_paired(const PrimalArgs<TS, float>& 
     return true;
 }
 
-template <class TS, bool kRes, int kBnd, bool kDef, bool kShard>
+template <class TS, bool kRes, int kBnd, bool kDef, bool kShard, bool kRM>
 __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<TS>::TC>& P, int c, int w,
                                             int lane, const Feed& F) {   // no linearised form (FP32 only)
     using PK = Pack<TS>;
@@ -628,11 +642,13 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
     uint4* fw = reinterpret_cast<uint4*>(P.f_new);
     const unsigned nq = (unsigned)P.nq, niter = (nq + kRowChunks - 1) / kRowChunks, oc = (unsigned)c * nq;
 
-    Sum<TC> m0, m1, m2, m3, fwa, ja, rs;
+    Sum<TC> m0, m1, m2, m3, fwa, ja, rs, q0, q1, q2, q3;
+    constexpr bool rmom = kRes && kRM;               // moments of the residual (macroscopic prediction)
     bool ok = true;
     unsigned it = 0;
     while (it < niter && ok) {
         TC bm0 = TC(0), bm1 = TC(0), bm2 = TC(0), bm3 = TC(0), bfw = TC(0), bj = TC(0), brs = TC(0);
+        TC bq0 = TC(0), bq1 = TC(0), bq2 = TC(0), bq3 = TC(0);
         for (int b = 0; b < kBlockIters && it < niter && ok; ++b, ++it) {
             ok = pipeline_step(F, it, niter, lane, [&](const uint4* d) {
 #pragma unroll
@@ -678,6 +694,10 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
                     if (kRes) {
                         const TC R1 = D * (fo1[kk] - fn1[kk]), R2 = D * (fo2[kk] - fn2[kk]);
                         brs += wk * (R1 * R1 + R2 * R2);
+                        if (rmom) {
+                            const TC wR = wk * R1;
+                            bq0 += wR; bq1 += wR * vx; bq2 += wR * vy; bq3 += wR * hv + wk * R2;
+                        }
                     }
                     const TC wf1 = wk * fn1[kk];
                     bm0 += wf1;
@@ -696,12 +716,17 @@ __device__ __forceinline__ bool primal_cell(const PrimalArgs<TS, typename Pack<T
         }
         m0.add(bm0); m1.add(bm1); m2.add(bm2); m3.add(bm3);
         if (kRes) rs.add(brs);
+        if (rmom) { q0.add(bq0); q1.add(bq1); q2.add(bq2); q3.add(bq3); }
         if (wall) { fwa.add(bfw); ja.add(bj); }
     }
     if (!ok) return false;
     const TC M0 = m0.total(), M1 = m1.total(), M2 = m2.total(), M3 = m3.total();
     TC RS = TC(0), FW = TC(0), JA = TC(0);
     if (kRes) RS = rs.total();
+    if (rmom) {
+        const TC Q0 = q0.total(), Q1 = q1.total(), Q2 = q2.total(), Q3 = q3.total();
+        if (lane == 0) P.rW[c] = make_double4(Q0, Q1, Q2, Q3);
+    }
     if (wall) { FW = fwa.total(); JA = ja.total(); }
     if (kShard && lane == 0) {           // velocity shard: raw sums of this slice
         const size_t nc = (size_t)P.ncell;
@@ -778,7 +803,7 @@ __device__ __forceinline__ void block_pipe_drain(const BlockPipe& B) {
         for (unsigned ph = 0; ph < 2; ++ph) mbar_try_wait(&B.F.full[s], ph);
 }
 
-template <class TS, bool kRes, bool kDef, bool kLin = false, bool kShard = false>
+template <class TS, bool kRes, bool kDef, bool kLin = false, bool kShard = false, bool kRM = false>
 __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<TS>::TC>& P, const CUtensorMap* m10,
                                              const CUtensorMap* m8, int i, int j0, unsigned char* smem) {
     BlockPipe B;
@@ -791,18 +816,18 @@ __device__ __forceinline__ void primal_block(const PrimalArgs<TS, typename Pack<
     bool ok;
     if constexpr (kPaired<TS>) {
         switch (bnd) {
-            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
-            default: ok = primal_cell_paired<TS, kRes, kWallFar, kDef, kLin, kShard>(P, c, w, lane, B.F); break;
+            case kInterior: ok = primal_cell_paired<TS, kRes, kInterior, kDef, kLin, kShard, kRM>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell_paired<TS, kRes, kWallCell, kDef, kLin, kShard, kRM>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell_paired<TS, kRes, kFarCell, kDef, kLin, kShard, kRM>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell_paired<TS, kRes, kWallFar, kDef, kLin, kShard, kRM>(P, c, w, lane, B.F); break;
         }
     } else {
         static_assert(!kLin, "the linearised sweep has the paired FP32 form only");
         switch (bnd) {
-            case kInterior: ok = primal_cell<TS, kRes, kInterior, kDef, kShard>(P, c, w, lane, B.F); break;
-            case kWallCell: ok = primal_cell<TS, kRes, kWallCell, kDef, kShard>(P, c, w, lane, B.F); break;
-            case kFarCell: ok = primal_cell<TS, kRes, kFarCell, kDef, kShard>(P, c, w, lane, B.F); break;
-            default: ok = primal_cell<TS, kRes, kWallFar, kDef, kShard>(P, c, w, lane, B.F); break;
+            case kInterior: ok = primal_cell<TS, kRes, kInterior, kDef, kShard, kRM>(P, c, w, lane, B.F); break;
+            case kWallCell: ok = primal_cell<TS, kRes, kWallCell, kDef, kShard, kRM>(P, c, w, lane, B.F); break;
+            case kFarCell: ok = primal_cell<TS, kRes, kFarCell, kDef, kShard, kRM>(P, c, w, lane, B.F); break;
+            default: ok = primal_cell<TS, kRes, kWallFar, kDef, kShard, kRM>(P, c, w, lane, B.F); break;
         }
     }
     if (!ok && lane == 0) {
@@ -820,6 +845,16 @@ __global__ void __launch_bounds__(256, kPrimalMinBlocks<TS>) k_primal_sweep(cons
     primal_block<TS, kRes, kDef>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
 }
 
+// Residual sweep of a prediction block: the same update, which also writes the moments of its input's
+// residual, sum_k w Psi_k R_k, per cell to P.rW (see k_coarse_assemble).
+template <class TS>
+__global__ void __launch_bounds__(256, 2) k_primal_sweep_rm(const PrimalArgs<TS, typename Pack<TS>::TC> P,
+                                                            const __grid_constant__ CUtensorMap m10,
+                                                            const __grid_constant__ CUtensorMap m8) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    primal_block<TS, true, false, false, false, true>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+}
+
 // Sweep of a velocity shard: the same update, with the raw velocity sums of the slice written to the
 // shard buffer in place of the moments, wall density, drag and residual partials.
 template <class TS, bool kRes>
@@ -831,12 +866,12 @@ __global__ void __launch_bounds__(256, 2) k_primal_shard_sweep(const PrimalArgs<
 }
 
 // Linearised correction sweep of the refinement (FP32 storage; see primal_cell_paired).
-template <bool kRes>
+template <bool kRes, bool kRM>
 __global__ void __launch_bounds__(256, 2) k_primal_lin_sweep(const PrimalArgs<float, float> P,
                                                                 const __grid_constant__ CUtensorMap m10,
                                                                 const __grid_constant__ CUtensorMap m8) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    primal_block<float, kRes, false, true>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
+    primal_block<float, kRes, false, true, false, kRM>(P, &m10, &m8, blockIdx.x, blockIdx.y * kWarpsPerBlock, smem);
 }
 
 // Make the tensor maps of a descriptor in global memory visible to the tensor-map proxy.
@@ -1528,17 +1563,269 @@ __global__ void __launch_bounds__(256) k_moment_shift(TS* __restrict__ f, int nc
     const double r1 = W[4 * c], u1 = W[4 * c + 1] / r1, u2 = W[4 * c + 2] / r1;
     const double T1 = (2.0 / 3.0) * (W[4 * c + 3] / r1 - 0.5 * (u1 * u1 + u2 * u2));
     if (!(r1 > 0.0) || !(T1 > 0.0)) return;
-    Gauss<TC> Ga, Gb;
-    Ga.setup((TC)r1, (TC)u1, (TC)u2, (TC)T1);
+    // g(W_mix) - g = g (exp(l) - 1) with l = ln(g(W_mix) / g) = l0 + l1 vx + l2 vy + l3 |v|^2/2, its
+    // coefficients formed in FP64: the shift keeps its relative accuracy when it is small, where the
+    // difference of two rounded Gaussians would not
+    const double ia = 1.0 / T1, ib = 1.0 / p.w;
+    const TC l0 = (TC)(log(r1 * ia / (p.x * ib)) - 0.5 * (u1 * u1 + u2 * u2) * ia + 0.5 * (p.y * p.y + p.z * p.z) * ib);
+    const TC l1 = (TC)(u1 * ia - p.y * ib), l2 = (TC)(u2 * ia - p.z * ib), l3 = (TC)(ib - ia);
+    Gauss<TC> Gb;
     Gb.setup((TC)p.x, (TC)p.y, (TC)p.z, (TC)p.w);
-    const TC hA = (TC)(0.5 * T1), hB = (TC)(0.5 * p.w);
+    const TC hA = (TC)(0.5 * T1), dh = (TC)(0.5 * (T1 - p.w));
     for (int k = lane; k < nvp; k += 32) {
         const double4 t = vd[k];
-        const TC ga = Ga.eval((TC)(t.w - t.x * u1 - t.y * u2));
-        const TC gb = Gb.eval((TC)(t.w - t.x * p.y - t.y * p.z));
+        const TC vx = (TC)t.x, vy = (TC)t.y, h = (TC)t.w;
+        const TC gb = Gb.eval(h - vx * (TC)p.y - vy * (TC)p.z);
+        const TC dg = gb * expm1(l0 + l1 * vx + l2 * vy + l3 * h);
         const size_t o = fpos<TS>(c, nvp, k);
-        f[o] = fromdbl<TS>(todbl(f[o]) + (double)(ga - gb));
-        f[o + kComp<TS>] = fromdbl<TS>(todbl(f[o + kComp<TS>]) + (double)(hA * ga - hB * gb));
+        f[o] = fromdbl<TS>(todbl(f[o]) + (double)dg);
+        f[o + kComp<TS>] = fromdbl<TS>(todbl(f[o + kComp<TS>]) + (double)(hA * dg + dh * gb));
+    }
+}
+
+// ================================================================== macroscopic prediction (coarse correction)
+// At small Kn the slow modes of the point-implicit sweeps are the cell moments: collisions relax f to
+// the local Maxwellian within a sweep, and only transport moves the moments.  A prediction step solves
+// for a moment correction dW per cell the moments of the linearised steady residual restricted to
+// local Maxwellian perturbations,
+//     sum_k w Psi_k [J (dg/dW) dW]_k = -sum_k w Psi_k R_k ,
+// and shifts f by g(W + dW) - g(W).  For a Maxwellian perturbation the collision term cancels, so the
+// operator is the discrete upwind transport of dg/dW in moment form (a kinetic flux-vector splitting of
+// the linearised Euler equations on this velocity set): per cell c and face e the outflow block
+//     OUT[c][e] = sum_{k: a_e,k > 0} w_k a_e,k Psi_k (dg_k/dW)(W_c)      (4 x 4)
+// gives the diagonal block sum_e OUT[c][e] and, across face e, the neighbour's block -OUT[nb][e'] (its
+// outflow through the shared face is this cell's inflow).  On the wall the re-emitted flux
+// (dF_rhow / D_l) gbar_w adds the rank-one block u v^T (u = sum_{a<=0} w a Psi gbar_w / D_l, v = dF_rhow/dW);
+// the far field injects nothing.  Psi = (1, vx, vy, |v|^2/2) on f1 and (0, 0, 0, 1) on f2.
+template <class TC>
+__global__ void __launch_bounds__(256, 1) k_coarse_assemble(int ncell, int nvp, const typename Vec<TC>::v4* __restrict__ vt,
+                                                            const double2* __restrict__ S, const int4* __restrict__ nb,
+                                                            const double4* __restrict__ prim, const TC* __restrict__ gw,
+                                                            const double* __restrict__ wallD, double halfTw,
+                                                            double* __restrict__ out, double* __restrict__ dinv) {
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 p = prim[c];
+    const TC rho = (TC)p.x, u1 = (TC)p.y, u2 = (TC)p.z, T = (TC)p.w;
+    Gauss<TC> G;
+    G.setup(rho, u1, u2, T);
+    const TC ir = TC(1) / rho, iT = TC(1) / T, hT = TC(0.5) * T, hTw = (TC)halfTw;
+    TC sx[4], sy[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { sx[e] = (TC)S[4 * c + e].x; sy[e] = (TC)S[4 * c + e].y; }
+    const bool wall = nb[c].w == kWall;
+    TC acc[4][16];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[e][i] = TC(0);
+    TC wu[4] = {TC(0), TC(0), TC(0), TC(0)}, wv[4] = {TC(0), TC(0), TC(0), TC(0)};
+    for (int k = lane; k < nvp; k += 32) {
+        const auto t = vt[k];
+        const TC vx = t.x, vy = t.y, w = t.z, h = t.w;
+        const TC cx = vx - u1, cy = vy - u2;
+        const TC g1 = G.eval(fma(vy, -u2, fma(vx, -u1, h)));
+        const TC d[4] = {g1 * ir, g1 * cx * iT, g1 * cy * iT, g1 * ((cx * cx + cy * cy) * TC(0.5) * iT * iT - iT)};
+        TC R[16];                               // row r of Psi . dg/dp: f1 rows 0..2, energy row 3 with f2
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            R[q] = d[q];
+            R[4 + q] = vx * d[q];
+            R[8 + q] = vy * d[q];
+            R[12 + q] = (h + hT) * d[q];
+        }
+        R[15] += TC(0.5) * g1;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const TC a = sx[e] * vx + sy[e] * vy;
+            const TC wa = a > TC(0) ? w * a : TC(0);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[e][i] = fma(wa, R[i], acc[e][i]);
+        }
+        if (wall) {
+            const TC a = sx[3] * vx + sy[3] * vy;
+            if (a > TC(0)) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) wv[q] = fma(w * a, d[q], wv[q]);
+            } else {
+                const TC wg = w * a * gw[k];
+                wu[0] += wg; wu[1] += wg * vx; wu[2] += wg * vy; wu[3] += wg * (h + hTw);
+            }
+        }
+    }
+    // dp/dW for p = (rho, u1, u2, T), W = (rho, rho u, rho E), E = |u|^2/2 + 3T/2
+    const double r = p.x, a1 = p.y, a2 = p.z, Tt = p.w, uu = 0.5 * (a1 * a1 + a2 * a2);
+    const double Pm[4][4] = {{1.0, 0.0, 0.0, 0.0},
+                             {-a1 / r, 1.0 / r, 0.0, 0.0},
+                             {-a2 / r, 0.0, 1.0 / r, 0.0},
+                             {(2.0 / 3.0) * (uu - 1.5 * Tt) / r, -(2.0 / 3.0) * a1 / r, -(2.0 / 3.0) * a2 / r, (2.0 / 3.0) / r}};
+    // one face at a time: 16 warp sums, then lane 0 maps them to W and adds them to the diagonal block
+    double Dg[4][4] = {{0}};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        double Ae[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) Ae[i] = warp_sum((double)acc[e][i]);
+        if (lane == 0) {
+            double* o = out + ((size_t)c * 4 + e) * 16;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const double v = Ae[4 * i] * Pm[0][j] + Ae[4 * i + 1] * Pm[1][j] + Ae[4 * i + 2] * Pm[2][j] +
+                                     Ae[4 * i + 3] * Pm[3][j];
+                    o[4 * i + j] = v;
+                    Dg[i][j] += v;
+                }
+        }
+    }
+    double U[4] = {0, 0, 0, 0}, Vw[4] = {0, 0, 0, 0};
+    if (wall) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { U[q] = warp_sum((double)wu[q]); Vw[q] = warp_sum((double)wv[q]); }
+    }
+    if (lane != 0) return;
+    if (wall) {                       // re-emission of the outgoing mass flux: (U / D_l) (Vw / A) P
+        const double Aw = sqrt(S[4 * c + 3].x * S[4 * c + 3].x + S[4 * c + 3].y * S[4 * c + 3].y);
+        double vW[4];
+        for (int j = 0; j < 4; ++j) {
+            vW[j] = 0.0;
+            for (int q = 0; q < 4; ++q) vW[j] += Vw[q] * Pm[q][j];
+            vW[j] /= Aw;
+        }
+        const double iD = 1.0 / wallD[c];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) Dg[i][j] += U[i] * iD * vW[j];
+    }
+    double* di = dinv + (size_t)c * 16;
+    for (int col = 0; col < 4; ++col) {           // inverse column by column
+        double M[4][4], bb[4] = {0, 0, 0, 0}, x[4];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) M[i][j] = Dg[i][j];
+        bb[col] = 1.0;
+        if (!lu4_solve(M, bb, x)) x[0] = x[1] = x[2] = x[3] = 0.0;
+        for (int i = 0; i < 4; ++i) di[4 * i + col] = x[i];
+    }
+}
+
+// One block-Jacobi iteration of the moment system: x_c = D_c^{-1} (-rW_c + sum_e OUT[nb][e'] x_nb); first:
+// from x = 0.  e' = e ^ 2 pairs faces 0/2 and 1/3 of neighbouring cells.
+__global__ void k_coarse_jacobi(int ncell, const int4* __restrict__ nb, const double* __restrict__ out,
+                                const double* __restrict__ dinv, const double4* __restrict__ rW,
+                                const double4* __restrict__ xo, double4* __restrict__ xn, int first) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double4 b = rW[c];
+    double r[4] = {-b.x, -b.y, -b.z, -b.w};
+    if (!first) {
+        const int4 n4 = nb[c];
+        const int nbs[4] = {n4.x, n4.y, n4.z, n4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int n = nbs[e];
+            if (n < 0) continue;
+            const double* o = out + ((size_t)n * 4 + (e ^ 2)) * 16;
+            const double4 x = xo[n];
+            const double xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] += o[4 * i] * xv[0] + o[4 * i + 1] * xv[1] + o[4 * i + 2] * xv[2] + o[4 * i + 3] * xv[3];
+        }
+    }
+    const double* d = dinv + (size_t)c * 16;
+    double y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[i] = d[4 * i] * r[0] + d[4 * i + 1] * r[1] + d[4 * i + 2] * r[2] + d[4 * i + 3] * r[3];
+    xn[c] = make_double4(y[0], y[1], y[2], y[3]);
+}
+
+// Target moments of the prediction: W = W(prim) + s omega dW (conserved variables, [ncell][4]), with the
+// largest s in [0, 1] (by bisection) that keeps the cell's density and temperature within a relative change
+// `cap` and positive: far from the steady state the linear correction can overshoot.
+__device__ __forceinline__ bool coarse_ok(double4 p, double r, double m1, double m2, double e, double cap) {
+    if (!(r > 0.0)) return false;
+    const double u1 = m1 / r, u2 = m2 / r, T = (2.0 / 3.0) * (e / r - 0.5 * (u1 * u1 + u2 * u2));
+    return T > 0.0 && fabs(r - p.x) <= cap * p.x && fabs(T - p.w) <= cap * p.w;
+}
+__global__ void k_coarse_target(int ncell, const double4* __restrict__ prim, const double4* __restrict__ dW,
+                                double omega, double cap, double* __restrict__ W) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double4 p = prim[c], d = dW[c];
+    const double w0 = p.x, w1 = p.x * p.y, w2 = p.x * p.z, w3 = p.x * (0.5 * (p.y * p.y + p.z * p.z) + 1.5 * p.w);
+    double sc = omega;
+    if (!(isfinite(d.x) && isfinite(d.y) && isfinite(d.z) && isfinite(d.w))) {
+        sc = 0.0;                                   // a coarse solution that ran away: no shift
+    } else if (!coarse_ok(p, w0 + sc * d.x, w1 + sc * d.y, w2 + sc * d.z, w3 + sc * d.w, cap)) {
+        double lo = 0.0, hi = omega;
+        for (int i = 0; i < 24; ++i) {
+            const double m = 0.5 * (lo + hi);
+            if (coarse_ok(p, w0 + m * d.x, w1 + m * d.y, w2 + m * d.z, w3 + m * d.w, cap)) lo = m;
+            else hi = m;
+        }
+        sc = lo;
+    }
+    W[4 * c] = sc > 0.0 ? w0 + sc * d.x : w0;
+    W[4 * c + 1] = sc > 0.0 ? w1 + sc * d.y : w1;
+    W[4 * c + 2] = sc > 0.0 ? w2 + sc * d.z : w2;
+    W[4 * c + 3] = sc > 0.0 ? w3 + sc * d.w : w3;
+}
+
+// Prediction of the refinement's linear correction e (FP32, state layout): e += (dg/dW)(prim) s omega x, the
+// Maxwellian perturbation with conserved moments s omega x, then the moment sums of e and, on wall cells,
+// its outgoing wall mass flux per unit area, which the next linearised sweep reads as its lagged dW and
+// dF_rhow.  A correction is small against the state; s <= 1 keeps the density and temperature parts
+// within `cap` of the state's (s = 0 for a non-finite x), so that a coarse solution that ran away (the
+// block-Jacobi iteration is non-normal) cannot carry into e.
+__global__ void __launch_bounds__(256) k_coarse_lin_shift(int ncell, int nvp, const double4* __restrict__ vd,
+                                                          const double2* __restrict__ S, const int4* __restrict__ nb,
+                                                          const double4* __restrict__ prim, const double4* __restrict__ x,
+                                                          double omega, double cap, float* __restrict__ e,
+                                                          double4* __restrict__ dW, double* __restrict__ dF) {
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 p = prim[c], xw = x[c];
+    const double r = p.x, a1 = p.y, a2 = p.z, T = p.w, ir = 1.0 / r, iT = 1.0 / T;
+    double x0 = omega * xw.x, x1 = omega * xw.y, x2 = omega * xw.z, x3 = omega * xw.w;
+    double dT = (2.0 / 3.0) * ir * (x3 - (a1 * x1 + a2 * x2) + (0.5 * (a1 * a1 + a2 * a2) - 1.5 * T) * x0);
+    double sc = 1.0;
+    if (!(fabs(x0) <= cap * r) || !(fabs(dT) <= cap * T))
+        sc = (isfinite(x0) && isfinite(dT)) ? fmin(cap * r / fabs(x0), cap * T / fabs(dT)) : 0.0;
+    x0 *= sc; x1 *= sc; x2 *= sc; x3 *= sc; dT *= sc;
+    const double du1 = (x1 - a1 * x0) * ir, du2 = (x2 - a2 * x0) * ir;
+    // dg1 / g1 = k0 + k1 vx + k2 vy + k3 |v|^2/2 (the linearised Maxwellian in v, coefficients in FP64)
+    const double k1 = du1 * iT - a1 * dT * iT * iT, k2 = du2 * iT - a2 * dT * iT * iT, k3 = dT * iT * iT;
+    const double k0 = x0 * ir - (a1 * du1 + a2 * du2) * iT + (0.5 * (a1 * a1 + a2 * a2) * iT - 1.0) * iT * dT;
+    const float fk0 = (float)k0, fk1 = (float)k1, fk2 = (float)k2, fk3 = (float)k3;
+    const float hT = (float)(0.5 * T), hdT = (float)(0.5 * dT);
+    Gauss<float> G;
+    G.setup((float)r, (float)a1, (float)a2, (float)T);
+    const bool wall = nb[c].w == kWall;
+    const double2 s3 = S[4 * c + 3];
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, fw = 0.0;
+    for (int k = lane; k < nvp; k += 32) {
+        const double4 t = vd[k];
+        const float vx = (float)t.x, vy = (float)t.y, h = (float)t.w;
+        const float g1 = G.eval(h - vx * (float)a1 - vy * (float)a2);
+        const float d1 = g1 * (fk0 + fk1 * vx + fk2 * vy + fk3 * h);
+        const size_t o = fpos<float>(c, nvp, k);
+        const float e1 = e[o] + d1, e2 = e[o + kComp<float>] + (hT * d1 + hdT * g1);
+        e[o] = e1;
+        e[o + kComp<float>] = e2;
+        const double we = t.z * (double)e1;
+        m0 += we;
+        m1 += we * t.x;
+        m2 += we * t.y;
+        m3 += we * t.w + t.z * (double)e2;
+        if (wall) {
+            const double a = s3.x * t.x + s3.y * t.y;
+            if (a > 0.0) fw += we * a;
+        }
+    }
+    m0 = warp_sum(m0); m1 = warp_sum(m1); m2 = warp_sum(m2); m3 = warp_sum(m3);
+    if (wall) fw = warp_sum(fw);
+    if (lane == 0) {
+        dW[c] = make_double4(m0, m1, m2, m3);
+        if (wall) dF[c] = fw / sqrt(s3.x * s3.x + s3.y * s3.y);
     }
 }
 
@@ -2734,6 +3021,35 @@ cudaError_t launch_moment_shift(int storage, void* f, const DevMesh& m, const De
     return cudaGetLastError();
 }
 
+cudaError_t launch_coarse_assemble(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
+                                   const double4* prim, double* out, double* dinv, cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0)
+        k_coarse_assemble<double><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vd, m.Sd, m.nb, prim, fl.gwd, fl.wallD, 0.5 * fl.Tw, out, dinv);
+    else
+        k_coarse_assemble<float><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vf, m.Sd, m.nb, prim, fl.gwf, fl.wallD, 0.5 * fl.Tw, out, dinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_jacobi(const DevMesh& m, const double* out, const double* dinv, const double4* rW,
+                                 const double4* xo, double4* xn, bool first, cudaStream_t s) {
+    k_coarse_jacobi<<<cdiv(m.ncell, 128), 128, 0, s>>>(m.ncell, m.nb, out, dinv, rW, xo, xn, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
+                                 double* W, cudaStream_t s) {
+    k_coarse_target<<<cdiv(ncell, 256), 256, 0, s>>>(ncell, prim, dW, omega, cap, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_lin_shift(const DevMesh& m, const DevGrid& g, const double4* prim, const double4* x,
+                                    double omega, double cap, float* e, double4* dW, double* dF, cudaStream_t s) {
+    k_coarse_lin_shift<<<cdiv(m.ncell, kWarpsPerBlock), 256, 0, s>>>(m.ncell, g.nvp, g.vd, m.Sd, m.nb, prim, x, omega,
+                                                                      cap, e, dW, dF);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_maxwell_fit(int storage, const DevMesh& m, const DevGrid& g, const double4* prim, double4* fit,
                                bool warm, int iters, double* Kinv, cudaStream_t s) {
     const int nb = cdiv(m.ncell, kWarpsPerBlock);
@@ -2819,21 +3135,23 @@ cudaError_t launch_primal_sweep(int storage, const void* args, const TmaMaps& ma
     return cudaGetLastError();
 }
 
-cudaError_t launch_primal_lin_sweep(const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {
+cudaError_t launch_primal_lin_sweep(const void* args, const TmaMaps& maps, bool res, bool rm, cudaStream_t s) {
     const auto& a = *static_cast<const PrimalArgs<float, float>*>(args);
-    if (!a.lin_src || !a.lin_f || !a.dW_old || !a.dW_new) return cudaErrorInvalidValue;
+    if (!a.lin_src || !a.lin_f || !a.dW_old || !a.dW_new || (rm && (!res || !a.rW))) return cudaErrorInvalidValue;
     const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
     constexpr int sm = primal_smem_bytes<float>();
     static bool attr[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr[dev]) {
-        cudaFuncSetAttribute(k_primal_lin_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaFuncSetAttribute(k_primal_lin_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_lin_sweep<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_lin_sweep<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        cudaFuncSetAttribute(k_primal_lin_sweep<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         attr[dev] = true;
     }
-    if (res) k_primal_lin_sweep<true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
-    else k_primal_lin_sweep<false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    if (rm) k_primal_lin_sweep<true, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    else if (res) k_primal_lin_sweep<true, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+    else k_primal_lin_sweep<false, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
     return cudaGetLastError();
 }
 
@@ -2852,6 +3170,28 @@ void shard_launch(const void* args, const TmaMaps& maps, bool res, cudaStream_t 
     }
     if (res) k_primal_shard_sweep<TS, true><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
     else k_primal_shard_sweep<TS, false><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+}
+
+template <class TS, class TC>
+void rm_launch(const void* args, const TmaMaps& maps, cudaStream_t s) {
+    const auto& a = *static_cast<const PrimalArgs<TS, TC>*>(args);
+    const dim3 grid(a.ni, cdiv(a.nj, kWarpsPerBlock));
+    constexpr int sm = primal_smem_bytes<TS>();
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(k_primal_sweep_rm<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        attr[dev] = true;
+    }
+    k_primal_sweep_rm<TS><<<grid, 256, sm, s>>>(a, maps.col, maps.side);
+}
+
+cudaError_t launch_primal_sweep_rm(int storage, const void* args, const TmaMaps& maps, cudaStream_t s) {
+    if (storage == 0) rm_launch<double, double>(args, maps, s);
+    else if (storage == 1) rm_launch<float, float>(args, maps, s);
+    else rm_launch<__nv_bfloat16, float>(args, maps, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_primal_shard_sweep(int storage, const void* args, const TmaMaps& maps, bool res, cudaStream_t s) {

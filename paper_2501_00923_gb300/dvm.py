@@ -38,7 +38,8 @@ class Flow(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("stall_window", C.c_int), ("accel_depth", C.c_int),
                 ("accel_period", C.c_int), ("accel_space", C.c_int), ("refine_tol", C.c_double),
-                ("refine_max", C.c_int), ("refine_sweeps", C.c_int)]
+                ("refine_max", C.c_int), ("refine_sweeps", C.c_int), ("predict_omega", C.c_double),
+                ("predict_iters", C.c_int), ("predict_reuse", C.c_int)]
 
 
 def _accel(accel):
@@ -54,7 +55,7 @@ def _accel(accel):
 class PrimalResult(C.Structure):
     _fields_ = [("J", C.c_double), ("Cd", C.c_double), ("residual", C.c_double), ("r0", C.c_double),
                 ("iters", C.c_int), ("status", C.c_int), ("refine_steps", C.c_int), ("refine_sweeps", C.c_int),
-                ("residual_fp32", C.c_double), ("residual_fp64", C.c_double)]
+                ("residual_fp32", C.c_double), ("residual_fp64", C.c_double), ("predictions", C.c_int)]
 
 
 class AdjointResult(C.Structure):
@@ -418,12 +419,14 @@ class Adjoint:
 # ----------------------------------------------------------------------------------- calls
 def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0, tol=1e-8, max_iter=100000,
                  storage="fp32", state: State | None = None, stall_window=0, accel=None, refine_tol=0.0,
-                 refine_max=0, refine_sweeps=0):
+                 refine_max=0, refine_sweeps=0, predict=0, predict_omega=0.0, predict_reuse=0):
     """Steady solve of Eq. (numerpr_gov); warm-starts from `state` if given.  accel = (m, K) turns on
-    Anderson mixing of depth m every K sweeps.  refine_tol > 0 (FP32 storage) adds mixed-precision
-    refinement to that FP64 residual after the sweeps.  Returns (state, result)."""
+    Anderson mixing of depth m every K sweeps.  predict > 0 turns on the macroscopic prediction after every
+    block of sweeps (that many block-Jacobi iterations of the moment system).  refine_tol > 0 (FP32
+    storage) adds mixed-precision refinement to that FP64 residual after the sweeps.  Returns (state, result)."""
     flow = Flow(Kn, Ma, Tw, aoa)
-    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), refine_tol, refine_max, refine_sweeps)
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), refine_tol, refine_max, refine_sweeps,
+                     predict_omega, predict, predict_reuse)
     h = C.c_void_p(state.h.value if state is not None else None)
     res = PrimalResult()
     st = lib().dvm_primal_solve(ctx.h, mesh.h, grid.h, C.byref(flow), C.byref(opts), STORAGE[storage],
@@ -437,7 +440,7 @@ def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0,
 def adjoint_solve(ctx: Context, state: State, functional="drag", tol=1e-8, max_iter=100000,
                   adjoint: Adjoint | None = None, stall_window=0, accel=None):
     """Steady solve of the discrete adjoint for `functional`; accel as in primal_solve."""
-    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0)
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0, 0.0, 0, 0)
     h = C.c_void_p(adjoint.h.value if adjoint is not None else None)
     res = AdjointResult()
     st = lib().dvm_adjoint_solve(ctx.h, state.h, FUNCTIONAL[functional], C.byref(opts), C.byref(h), C.byref(res))
