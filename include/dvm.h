@@ -150,6 +150,12 @@ typedef struct {
                                early (tol ~1e-5) and let the predicted refinement finish.  Temporary memory: 85
                                doubles per cell, kept with the state */
     int predict_reuse;      /* predictions between reassemblies of the moment system (0 -> 4) */
+    /* Adjoint solves take predict_iters and predict_omega too: the transposed coarse problem.  The
+       prolongation of the moment prediction, dW -> (dg/dW) dW, and its restriction, r -> sum_k w Psi_k r_k,
+       swap roles in the w-weighted product of the adjoint sweep: lambda -> Psi . lambda and
+       r_a -> sum_k w (dg_k/dW)^T r_a,k, with the transposed system A^T (assembled once at the primal
+       state; the block-Jacobi iteration then uses each cell's own outflow blocks).  phi += omega Psi . lambda,
+       after which the collision and wall couplings of phi are recomputed.  The same FP32 noise rule. */
 } dvm_solve_opts;
 
 typedef struct {
@@ -171,6 +177,7 @@ typedef struct {
     double r0;
     int iters;
     int status;
+    int predictions;        /* macroscopic predictions applied (one per block of sweeps) */
 } dvm_adjoint_result;
 
 /* ------------------------------------------------------------------------ context, B1 */

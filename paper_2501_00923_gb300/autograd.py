@@ -39,7 +39,8 @@ class DragProblem:
     refine_tol: float = 0.0         # > 0 (FP32, order 1, plain): mixed-precision refinement of the primal to this
                                     # FP64 residual after the sweeps (dvm_solve_opts.refine_tol)
     predict: int = 0                # > 0 (FP64/FP32, order 1, plain): macroscopic prediction after every block of
-                                    # primal sweeps, this many block-Jacobi iterations (dvm_solve_opts.predict_iters)
+                                    # primal and adjoint sweeps, this many block-Jacobi iterations
+                                    # (dvm_solve_opts.predict_iters)
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
@@ -63,9 +64,10 @@ class DragProblem:
         elif self.order == 2:               # second order starts from the converged first-order state
             dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa,
                              tol=self.tol, max_iter=self.max_iter, storage=self.storage, state=st,
-                             stall_window=self.stall_window, predict=self.predict if self.maxwellian == "plain" else 0)
+                             stall_window=self.stall_window,
+                             predict=self.predict if self.maxwellian == "plain" and self.storage != "bf16" else 0)
         st.order = self.order
-        plain1 = self.order == 1 and self.maxwellian == "plain"
+        plain1 = self.order == 1 and self.maxwellian == "plain" and self.storage != "bf16"
         st, res = dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw,
                                    self.flow.aoa, tol=self.tol, max_iter=self.max_iter, storage=self.storage,
                                    state=st, stall_window=self.stall_window, refine_tol=self.refine_tol,
@@ -78,8 +80,9 @@ class DragProblem:
         ad = dvm.Adjoint(st)
         if self._warm is not None:
             ad.copy_from(self._warm[2])
+        plain1 = self.order == 1 and self.maxwellian == "plain" and self.storage != "bf16"
         ad, ares = dvm.adjoint_solve(self.ctx, st, tol=self.adjoint_tol, max_iter=self.max_iter, adjoint=ad,
-                                     stall_window=self.stall_window)
+                                     stall_window=self.stall_window, predict=self.predict if plain1 else 0)
         g = dvm.sensitivity(self.ctx, st, ad, mesh.dwall, mesh.s, mode=self.mode)
         self._drop_warm()
         self._warm = (self.last["m"], st, ad)     # stays on the device as the next design's warm start
@@ -177,7 +180,8 @@ def main(argv=None):
            "Cd": float(cd.item()), "forward_s": t1 - t0, "backward_s": t2 - t1,
            "primal_sweeps": pres.iters, "primal_status": dvm.status_string(pres.status), "primal_residual": pres.residual,
            "refine_steps": pres.refine_steps, "refine_sweeps": pres.refine_sweeps, "predictions": pres.predictions,
-           "adjoint_sweeps": ares.iters, "adjoint_status": dvm.status_string(ares.status),
+           "adjoint_sweeps": ares.iters, "adjoint_predictions": ares.predictions,
+           "adjoint_status": dvm.status_string(ares.status),
            "adjoint_residual": ares.residual, "grad": g.tolist()}
     prob.release()
     if args.fd > 0:

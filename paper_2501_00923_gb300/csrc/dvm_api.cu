@@ -1969,11 +1969,25 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
         return fail(DVM_ERR_INVALID_ARG, "warm-start adjoint belongs to another state/functional");
     }
     dvm_adjoint* ad = *inout;
+    const bool predict = opts->predict_iters > 0;
+    if (predict && (st->order != 1 || st->maxwell || st->storage == DVM_STORE_BF16))
+        return fail(DVM_ERR_INVALID_ARG,
+                    "the macroscopic prediction needs an FP64 or FP32 state of order 1 with the plain Maxwellian");
     if ((rc = adjoint_so_ensure(ad))) return rc;
     if ((rc = adjoint_follow_state(ad))) return rc;
     const bool accel = opts->accel_depth > 0;
     const int K = accel ? opts->accel_period : ctx->graph_iters;
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
+    const double omega = opts->predict_omega > 0.0 ? opts->predict_omega : 0.8;
+    if (predict) {              // the moment system at the (fixed) primal state
+        if ((rc = predict_ensure(st))) return rc;
+        CK(launch_coarse_assemble(st->storage, st->mesh->d, st->grid->d, st->fl, st->prim[st->cur], st->co_out,
+                                  st->co_dinv, ctx->stream));
+        ctx->launches += 1;
+    }
+    bool predicting = predict;
+    double pred_best = INFINITY;
+    int predictions = 0;
     if (accel) {
         const size_t n = (size_t)st->mesh->d.ncell * st->grid->d.nvp * 2;
         if ((rc = aa_ensure(ctx, ad->aa, st->storage, n, opts->accel_depth))) return rc;
@@ -2017,11 +2031,31 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
             }
             if (mixed) CK(refresh_adjoint_couplings(ad));
         }
+        if (predicting && st->storage != DVM_STORE_FP64) {     // FP32 noise floor: as in the primal solve
+            if (r > 2.0 * pred_best) predicting = false;
+            pred_best = std::min(pred_best, r);
+        }
+        if (predicting && k == K && it < opts->max_iter) {
+            // after a block the last sweep read phi[1 - cur] and wrote phi[cur]
+            const DevMesh& m = st->mesh->d;
+            cudaStream_t s = ctx->stream;
+            const int n = opts->predict_iters;
+            CK(launch_adjoint_restrict(st->storage, m, st->grid->d, st->prim[st->cur], 1.0 / st->fl.tau_inf,
+                                       ad->phi[1 - ad->cur], ad->phi[ad->cur], st->co_rW, s));
+            for (int i = 0; i < n; ++i)
+                CK(launch_coarse_jacobi_t(m, st->co_out, st->co_dinv, st->co_rW, st->co_x[(i + 1) & 1],
+                                          st->co_x[i & 1], i == 0, s));
+            CK(launch_adjoint_shift(st->storage, m, st->grid->d, st->co_x[(n - 1) & 1], omega, ad->phi[ad->cur], s));
+            CK(refresh_adjoint_couplings(ad));
+            ctx->launches += n + 2;
+            predictions += 1;
+        }
     }
     res->residual = r;
     res->r0 = ad->r0;
     res->iters = it;
     res->status = status;
+    res->predictions = predictions;
     return status;
 }
 

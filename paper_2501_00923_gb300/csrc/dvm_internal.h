@@ -252,6 +252,15 @@ cudaError_t launch_coarse_jacobi(const DevMesh& m, const double* out, const doub
                                  const double4* xo, double4* xn, bool first, cudaStream_t s);
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s);
+// Prediction of the adjoint sweeps (FP64/FP32 storage): restriction of the last sweep's residual
+// D (phi_old - phi_new) with (dg/dW)^T, one transposed block-Jacobi iteration, the update phi += omega Psi . x.
+cudaError_t launch_adjoint_restrict(int storage, const DevMesh& m, const DevGrid& g, const double4* prim,
+                                    double inv_tau_inf, const void* phi_o, const void* phi_n, double4* rA,
+                                    cudaStream_t s);
+cudaError_t launch_coarse_jacobi_t(const DevMesh& m, const double* out, const double* dinv, const double4* rA,
+                                   const double4* xo, double4* xn, bool first, cudaStream_t s);
+cudaError_t launch_adjoint_shift(int storage, const DevMesh& m, const DevGrid& g, const double4* x, double omega,
+                                 void* phi, cudaStream_t s);
 // Prediction of a linear correction e (FP32): e += (dg/dW) s omega x (s <= 1 keeps the density and
 // temperature parts within cap of the state's), then its moment sums dW and wall flux dF.
 cudaError_t launch_coarse_lin_shift(const DevMesh& m, const DevGrid& g, const double4* prim, const double4* x,

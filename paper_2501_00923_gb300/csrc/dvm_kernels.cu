@@ -1770,6 +1770,106 @@ __global__ void k_coarse_target(int ncell, const double4* __restrict__ prim, con
     W[4 * c + 3] = sc > 0.0 ? w3 + sc * d.w : w3;
 }
 
+// Prediction of the adjoint sweeps: the transposed coarse problem.  With the prolongation dW -> (dg/dW) dW
+// and the restriction delta f -> sum_k w Psi_k delta f_k of the primal prediction, the adjoint (in the
+// w-weighted product that the adjoint sweep uses) takes the prolongation lambda -> Psi . lambda and the
+// restriction r -> sum_k w (dg_k/dW)^T r_k, and its coarse operator is A^T.  Residual restriction of the
+// last adjoint sweep: R = D (phi_old - phi_new), D = V/tau + sum_e max(a_e, 0), at the primal moments.
+template <class TS, class TC>
+__global__ void __launch_bounds__(256) k_adjoint_restrict(int ncell, int nvp, const typename Vec<TC>::v4* __restrict__ vt,
+                                                          const double2* __restrict__ S, const double* __restrict__ V,
+                                                          const double4* __restrict__ prim, double inv_tau_inf,
+                                                          const TS* __restrict__ phi_o, const TS* __restrict__ phi_n,
+                                                          double4* __restrict__ rA) {
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 p = prim[c];
+    const TC u1 = (TC)p.y, u2 = (TC)p.z, hT = (TC)(0.5 * p.w);
+    const TC Vt = (TC)(V[c] * p.x * sqrt(p.w) * inv_tau_inf);
+    Gauss<TC> G;
+    G.setup((TC)p.x, u1, u2, (TC)p.w);
+    TC sx[4], sy[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { sx[e] = (TC)S[4 * c + e].x; sy[e] = (TC)S[4 * c + e].y; }
+    TC q0 = TC(0), qx = TC(0), qy = TC(0), qc = TC(0), q2 = TC(0);
+    for (int k = lane; k < nvp; k += 32) {
+        const auto t = vt[k];
+        const TC vx = t.x, vy = t.y, w = t.z, h = t.w;
+        TC D = Vt;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { const TC a = sx[e] * vx + sy[e] * vy; D += a > TC(0) ? a : TC(0); }
+        const size_t o = fpos<TS>(c, nvp, k);
+        const TC R1 = D * (TC)(todbl(phi_o[o]) - todbl(phi_n[o]));
+        const TC R2 = D * (TC)(todbl(phi_o[o + kComp<TS>]) - todbl(phi_n[o + kComp<TS>]));
+        const TC cx = vx - u1, cy = vy - u2;
+        const TC wg = w * G.eval(fma(vy, -u2, fma(vx, -u1, h)));
+        const TC m = wg * fma(hT, R2, R1);
+        q0 += m;
+        qx = fma(m, cx, qx);
+        qy = fma(m, cy, qy);
+        qc = fma(m, TC(0.5) * (cx * cx + cy * cy), qc);
+        q2 = fma(wg, R2, q2);
+    }
+    const double Q0 = warp_sum((double)q0), Qx = warp_sum((double)qx), Qy = warp_sum((double)qy);
+    const double Qc = warp_sum((double)qc), Q2 = warp_sum((double)q2);
+    if (lane != 0) return;
+    // sum_k w (dg/dp)^T R, p = (rho, u1, u2, T), then (dp/dW)^T
+    const double r = p.x, a1 = p.y, a2 = p.z, T = p.w, ir = 1.0 / r, iT = 1.0 / T;
+    const double ph0 = Q0 * ir, ph1 = Qx * iT, ph2 = Qy * iT, ph3 = Qc * iT * iT - Q0 * iT + 0.5 * Q2;
+    const double uu = 0.5 * (a1 * a1 + a2 * a2);
+    rA[c] = make_double4(ph0 - (ph1 * a1 + ph2 * a2) * ir + ph3 * (2.0 / 3.0) * (uu - 1.5 * T) * ir,
+                         (ph1 - (2.0 / 3.0) * a1 * ph3) * ir, (ph2 - (2.0 / 3.0) * a2 * ph3) * ir,
+                         (2.0 / 3.0) * ph3 * ir);
+}
+
+// One block-Jacobi iteration of the transposed moment system: lambda_c = D_c^{-T} (-rA_c + sum_e OUT[c][e]^T
+// lambda_nb(e)) (the transpose of the primal coupling -OUT[nb][e'] is the cell's own outflow block); first:
+// from lambda = 0.
+__global__ void k_coarse_jacobi_t(int ncell, const int4* __restrict__ nb, const double* __restrict__ out,
+                                  const double* __restrict__ dinv, const double4* __restrict__ rA,
+                                  const double4* __restrict__ xo, double4* __restrict__ xn, int first) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double4 b = rA[c];
+    double r[4] = {-b.x, -b.y, -b.z, -b.w};
+    if (!first) {
+        const int4 n4 = nb[c];
+        const int nbs[4] = {n4.x, n4.y, n4.z, n4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int n = nbs[e];
+            if (n < 0) continue;
+            const double* o = out + ((size_t)c * 4 + e) * 16;
+            const double4 x = xo[n];
+            const double xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] += o[i] * xv[0] + o[4 + i] * xv[1] + o[8 + i] * xv[2] + o[12 + i] * xv[3];
+        }
+    }
+    const double* d = dinv + (size_t)c * 16;
+    double y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[i] = d[i] * r[0] + d[4 + i] * r[1] + d[8 + i] * r[2] + d[12 + i] * r[3];
+    xn[c] = make_double4(y[0], y[1], y[2], y[3]);
+}
+
+// The adjoint prediction's update: phi1 += omega (l0 + l1 vx + l2 vy + l3 |v|^2/2), phi2 += omega l3 (the
+// prolongation Psi . lambda); a cell whose lambda is not finite is left as it is.
+template <class TS>
+__global__ void __launch_bounds__(256) k_adjoint_shift(int ncell, int nvp, const double4* __restrict__ vd,
+                                                       const double4* __restrict__ x, double omega, TS* __restrict__ phi) {
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 l = x[c];
+    if (!(isfinite(l.x) && isfinite(l.y) && isfinite(l.z) && isfinite(l.w))) return;
+    for (int k = lane; k < nvp; k += 32) {
+        const double4 t = vd[k];
+        const size_t o = fpos<TS>(c, nvp, k);
+        phi[o] = fromdbl<TS>(todbl(phi[o]) + omega * (l.x + l.y * t.x + l.z * t.y + l.w * t.w));
+        phi[o + kComp<TS>] = fromdbl<TS>(todbl(phi[o + kComp<TS>]) + omega * l.w);
+    }
+}
+
 // Prediction of the refinement's linear correction e (FP32, state layout): e += (dg/dW)(prim) s omega x, the
 // Maxwellian perturbation with conserved moments s omega x, then the moment sums of e and, on wall cells,
 // its outgoing wall mass flux per unit area, which the next linearised sweep reads as its lagged dW and
@@ -3040,6 +3140,36 @@ cudaError_t launch_coarse_jacobi(const DevMesh& m, const double* out, const doub
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s) {
     k_coarse_target<<<cdiv(ncell, 256), 256, 0, s>>>(ncell, prim, dW, omega, cap, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_restrict(int storage, const DevMesh& m, const DevGrid& g, const double4* prim,
+                                    double inv_tau_inf, const void* phi_o, const void* phi_n, double4* rA,
+                                    cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0)
+        k_adjoint_restrict<double, double><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vd, m.Sd, m.Vd, prim, inv_tau_inf,
+                                                              (const double*)phi_o, (const double*)phi_n, rA);
+    else if (storage == 1)
+        k_adjoint_restrict<float, float><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vf, m.Sd, m.Vd, prim, inv_tau_inf,
+                                                            (const float*)phi_o, (const float*)phi_n, rA);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_jacobi_t(const DevMesh& m, const double* out, const double* dinv, const double4* rA,
+                                   const double4* xo, double4* xn, bool first, cudaStream_t s) {
+    k_coarse_jacobi_t<<<cdiv(m.ncell, 128), 128, 0, s>>>(m.ncell, m.nb, out, dinv, rA, xo, xn, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_shift(int storage, const DevMesh& m, const DevGrid& g, const double4* x, double omega,
+                                 void* phi, cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0) k_adjoint_shift<double><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vd, x, omega, (double*)phi);
+    else if (storage == 1) k_adjoint_shift<float><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vd, x, omega, (float*)phi);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -59,7 +59,8 @@ class PrimalResult(C.Structure):
 
 
 class AdjointResult(C.Structure):
-    _fields_ = [("residual", C.c_double), ("r0", C.c_double), ("iters", C.c_int), ("status", C.c_int)]
+    _fields_ = [("residual", C.c_double), ("r0", C.c_double), ("iters", C.c_int), ("status", C.c_int),
+                ("predictions", C.c_int)]
 
 
 class DVMError(RuntimeError):
@@ -438,9 +439,10 @@ def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0,
 
 
 def adjoint_solve(ctx: Context, state: State, functional="drag", tol=1e-8, max_iter=100000,
-                  adjoint: Adjoint | None = None, stall_window=0, accel=None):
-    """Steady solve of the discrete adjoint for `functional`; accel as in primal_solve."""
-    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0, 0.0, 0, 0)
+                  adjoint: Adjoint | None = None, stall_window=0, accel=None, predict=0, predict_omega=0.0):
+    """Steady solve of the discrete adjoint for `functional`; accel and predict as in primal_solve (the
+    prediction by the transposed moment system)."""
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0, predict_omega, predict, 0)
     h = C.c_void_p(adjoint.h.value if adjoint is not None else None)
     res = AdjointResult()
     st = lib().dvm_adjoint_solve(ctx.h, state.h, FUNCTIONAL[functional], C.byref(opts), C.byref(h), C.byref(res))

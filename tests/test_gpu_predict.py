@@ -51,6 +51,37 @@ def test_predicted_solve_reaches_the_oracle_solution(ctx, Kn):
         h.close()
 
 
+@pytest.mark.parametrize("Kn", [0.02, 0.5])
+def test_predicted_adjoint_reaches_the_oracle_adjoint(ctx, Kn):
+    """The transposed prediction: on the oracle-converged primal state, the FP64 predicted adjoint solve
+    agrees with the oracle's adjoint to the solve tolerance, in fewer sweeps than plain adjoint sweeps."""
+    rng = np.random.default_rng(92)
+    mesh = W.omesh(24, 8, rng.uniform(-0.01, 0.01, 4))
+    grid = W.velocity_grid(10, 4.0)
+    Ma = 0.8
+    pr = O.Problem(mesh.nodes, grid.vx, grid.vy, grid.w, Kn, Ma)
+    f_ref, info = pr.primal_solve(tol=1e-13, max_sweeps=100000)
+    assert info["status"] == 0
+    phi_ref, ainfo = pr.adjoint_solve(f_ref, tol=1e-13, max_sweeps=100000)
+    assert ainfo["status"] == 0
+    m = dvm.Mesh(ctx, mesh.nodes)
+    g = dvm.VGrid(ctx, grid.vx, grid.vy, grid.w)
+    st = dvm.State(ctx, m, g, Kn, Ma, storage="fp64")
+    st.set(f_ref)
+    ap, plain = dvm.adjoint_solve(ctx, st, tol=1e-12, max_iter=200000)
+    ad, res = dvm.adjoint_solve(ctx, st, tol=1e-12, max_iter=200000, predict=40)
+    assert plain.status == dvm.DVM_OK and res.status == dvm.DVM_OK
+    phi = ad.get()
+    err = np.abs(phi - phi_ref).max() / np.abs(phi_ref).max()
+    print(f"Kn {Kn}: adjoint sweeps plain {plain.iters}, predicted {res.iters} ({res.predictions} predictions); "
+          f"phi error {err:.1e}")
+    assert err < 1e-9
+    if Kn < 0.1:
+        assert res.iters * 5 < plain.iters
+    for h in (ap, ad, st, g, m):
+        h.close()
+
+
 def test_prediction_near_continuum_mid_size(ctx):
     """128x64 O-mesh, 24x24 velocities, Kn 0.001, Ma 0.8 (transport dominates the point-implicit sweeps'
     slow modes): the FP64 predicted solve to 1e-12 and the FP64 Anderson-mixed solve to 1e-11 agree in
@@ -86,7 +117,20 @@ def test_prediction_near_continuum_mid_size(ctx):
     assert q32.status == dvm.DVM_OK and q32.residual <= 1e-9
     assert err < 1e-6 and err_plain > 100 * err
     assert (q32.iters + q32.refine_sweeps) * 4 < r32.iters
-    for h in (p32, s32, p64, s64, g, m):
+    # adjoints on the predicted states: FP64 to 1e-11, FP32 to its floor, both predicted; the FP32 full
+    # sensitivity within 1e-4 of the FP64 one per component (largest component scale)
+    a64, b64 = dvm.adjoint_solve(ctx, p64, tol=1e-11, max_iter=600000, predict=40)
+    assert b64.status == dvm.DVM_OK
+    g64 = dvm.sensitivity(ctx, p64, a64, mesh.dwall, mesh.s, mode="full")
+    a32p, b32p = dvm.adjoint_solve(ctx, p32, tol=1e-7, max_iter=600000, stall_window=1000, predict=40)
+    a32, b32 = dvm.adjoint_solve(ctx, p32, tol=1e-7, max_iter=600000, stall_window=3000)
+    g32 = dvm.sensitivity(ctx, p32, a32p, mesh.dwall, mesh.s, mode="full")
+    gerr = np.abs(g32 - g64).max() / np.abs(g64).max()
+    print(f"adjoint sweeps: FP64 predicted {b64.iters}; FP32 predicted {b32p.iters} (residual {b32p.residual:.1e}), "
+          f"plain {b32.iters} (residual {b32.residual:.1e}); FP32 sensitivity error {gerr:.1e}")
+    assert gerr < 1e-4
+    assert b32p.iters * 4 < b32.iters
+    for h in (a32, a32p, a64, p32, s32, p64, s64, g, m):
         h.close()
 
 
@@ -131,6 +175,14 @@ def test_prediction_arguments(ctx):
         with pytest.raises(dvm.DVMError) as e:
             dvm.primal_solve(ctx, m, g, 1.0, 0.5, tol=1e-6, max_iter=4, storage="fp32", state=st, predict=5)
         assert e.value.status == dvm.DVM_ERR_INVALID_ARG
+        with pytest.raises(dvm.DVMError) as e:
+            dvm.adjoint_solve(ctx, st, tol=1e-6, max_iter=4, predict=5)
+        assert e.value.status == dvm.DVM_ERR_INVALID_ARG
         st.close()
+    st = dvm.State(ctx, m, g, 1.0, 0.5, storage="bf16")
+    with pytest.raises(dvm.DVMError) as e:
+        dvm.adjoint_solve(ctx, st, tol=1e-6, max_iter=4, predict=5)
+    assert e.value.status == dvm.DVM_ERR_INVALID_ARG
+    st.close()
     for h in (g, m):
         h.close()
