@@ -131,30 +131,35 @@ typedef struct {
                                such step is allowed: far from the solution a step can raise |R| while it cuts the
                                error, by the quadratic term of R in e) */
     int refine_sweeps;      /* linearised FP32 sweeps per correction step at most (0 -> 4000) */
-    double predict_omega;   /* damping of the macroscopic prediction's correction (0 -> 0.8) */
-    int predict_iters;      /* primal solves, FP64 or FP32 storage, order 1, plain Maxwellian; 0 = off.  > 0: after every block of
-                               graph_iters sweeps a macroscopic prediction (the prediction acceleration of
-                               Sec. 3.1 by equations for the moments): the moments of the steady residual of
-                               Eq. (numerpr_gov) per cell (from the block's last sweep) are cancelled by a moment
-                               correction dW solved, with this many block-Jacobi iterations, from the discrete
-                               transport of the Maxwellian derivative in moment form (4 x 4 blocks per cell and
-                               face: upwind outflow at the cell's moments, inflow from the neighbour, re-emission
-                               on the wall); f is then shifted by g(W + s omega dW) - g(W), s <= 1 keeping each
+    double predict_omega;   /* damping of the macroscopic prediction's correction (0 -> 0.8), its initial and
+                               largest value: it halves after a block whose residual grew by more than 1.5x and
+                               after five predicted blocks in a row without a new best residual, and recovers by
+                               1.25x after a block that set a new best */
+    int predict_iters;      /* primal solves, FP64 or FP32 storage, order 1, plain Maxwellian; 0 = off; at most 64.
+                               > 0: after every block of graph_iters sweeps a macroscopic prediction (the
+                               prediction acceleration of Sec. 3.1 by equations for the moments): the moments of
+                               the steady residual of Eq. (numerpr_gov) per cell (from the block's last sweep) are
+                               cancelled by a moment correction dW solved from the discrete transport of the
+                               Maxwellian derivative in moment form (4 x 4 blocks per cell and face: upwind
+                               outflow at the cell's moments, inflow from the neighbour, re-emission on the wall)
+                               by one GMRES cycle of this many Arnoldi steps, right-preconditioned by the diagonal
+                               blocks, on the device (no host synchronisation, fixed-order sums; workspace
+                               (steps + 2) x 4 doubles per cell); f is then shifted by g(W + s omega dW) - g(W), s <= 1 keeping each
                                cell's density and temperature within 30% and positive.  At small Kn the slow
                                modes of the sweeps are these moments, so this removes most of their sweeps; the
                                steady solution is unchanged (the shift vanishes at it).  FP32 storage: near
                                the rounding floor the residual moments are dominated by the rounding of the
-                               relaxation term, which the moment solve amplifies into smooth errors; once a block
-                               ends with a residual above twice the best so far the prediction is switched off
-                               and the solve goes on with plain sweeps.  With refinement, stop the FP32 sweeps
-                               early (tol ~1e-5) and let the predicted refinement finish.  Temporary memory: 85
-                               doubles per cell, kept with the state */
+                               relaxation term, which the moment solve amplifies into smooth errors; once two
+                               blocks in a row end with a residual above twice the best so far the prediction
+                               is switched off and the solve goes on with plain sweeps (with a new stall window).  With refinement, stop the FP32 sweeps
+                               early (tol ~1e-5) and let the predicted refinement finish.  Memory: 88 doubles per
+                               cell plus the GMRES workspace, kept with the state */
     int predict_reuse;      /* predictions between reassemblies of the moment system (0 -> 4) */
     /* Adjoint solves take predict_iters and predict_omega too: the transposed coarse problem.  The
        prolongation of the moment prediction, dW -> (dg/dW) dW, and its restriction, r -> sum_k w Psi_k r_k,
        swap roles in the w-weighted product of the adjoint sweep: lambda -> Psi . lambda and
        r_a -> sum_k w (dg_k/dW)^T r_a,k, with the transposed system A^T (assembled once at the primal
-       state; the block-Jacobi iteration then uses each cell's own outflow blocks).  phi += omega Psi . lambda,
+       state; its GMRES products use each cell's own outflow blocks).  phi += omega Psi . lambda,
        after which the collision and wall couplings of phi are recomputed.  The same FP32 noise rule. */
 } dvm_solve_opts;
 

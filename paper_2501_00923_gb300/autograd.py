@@ -32,7 +32,8 @@ class DragProblem:
     adjoint_tol: float = 1e-6
     max_iter: int = 200000
     stall_window: int = 0
-    mode: str = "full"
+    mode: str = "full"              # gradient: the full discrete one (at order 2 too); "paper": the paper's
+                                    # boundary sensitivity (design.run takes it by default at order 2)
     mesh_fn: object = None          # alpha -> OMesh; default: the Hicks-Henne bump section
     order: int = 1                  # 2: second-order reconstruction
     maxwellian: str = "plain"       # or "conservative"

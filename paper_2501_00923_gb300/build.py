@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdvm.so")
-SOURCES = ["dvm_kernels.cu", "dvm_api.cu"]
+SOURCES = ["dvm_kernels.cu", "dvm_krylov.cu", "dvm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

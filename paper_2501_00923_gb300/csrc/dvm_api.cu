@@ -100,7 +100,9 @@ struct dvm_state {
     double* co_out = nullptr;   // [ncell][4][16] outflow blocks of the moment system
     double* co_dinv = nullptr;  // [ncell][16] inverses of its diagonal blocks
     double4* co_rW = nullptr;   // [ncell] moments of the residual
-    double4* co_x[2] = {nullptr, nullptr};
+    double4* co_x = nullptr;    // [ncell] the moment correction
+    KrylovWork co_kr;           // GMRES workspace for up to co_m Arnoldi steps
+    int co_m = 0;
     int shard = 0;              // 1: a velocity shard (sweeps write partial sums; see dvm_state_set_shard)
     double* part = nullptr;     // [shard_count] this shard's partial sums
     double* part_total = nullptr;   // [shard_count] the summed buffer of all shards
@@ -692,9 +694,9 @@ int check_solve_opts(const dvm_solve_opts* o) {
     if (o->accel_space != 0 && o->accel_space != 1) return fail(DVM_ERR_INVALID_ARG, "accel_space must be 0 or 1");
     if (!(o->refine_tol >= 0.0) || o->refine_max < 0 || o->refine_sweeps < 0)
         return fail(DVM_ERR_INVALID_ARG, "refine_tol, refine_max and refine_sweeps must be >= 0");
-    if (o->predict_iters < 0 || o->predict_iters > 1000 || o->predict_reuse < 0 ||
+    if (o->predict_iters < 0 || o->predict_iters > kMaxKrylov || o->predict_reuse < 0 ||
         !(o->predict_omega >= 0.0 && o->predict_omega <= 1.0))
-        return fail(DVM_ERR_INVALID_ARG, "predict_iters must be in [0, 1000], predict_reuse >= 0, predict_omega in [0, 1]");
+        return fail(DVM_ERR_INVALID_ARG, "predict_iters must be in [0, 64], predict_reuse >= 0, predict_omega in [0, 1]");
     if (o->predict_iters > 0 && o->accel_depth > 0)
         return fail(DVM_ERR_INVALID_ARG, "the macroscopic prediction and Anderson mixing exclude each other");
     return DVM_OK;
@@ -1025,7 +1027,9 @@ void dvm_state_destroy(dvm_state* st) {
     dfree(st->Wbuf);
     dfree(st->part);
     dfree(st->part_total);
-    dfree(st->co_out); dfree(st->co_dinv); dfree(st->co_rW); dfree(st->co_x[0]); dfree(st->co_x[1]);
+    dfree(st->co_out); dfree(st->co_dinv); dfree(st->co_rW); dfree(st->co_x);
+    dfree(st->co_kr.V); dfree(st->co_kr.w); dfree(st->co_kr.part); dfree(st->co_kr.H); dfree(st->co_kr.scal);
+    dfree(st->co_kr.y);
     st->ctx->bytes -= st->bytes;
     delete st;
 }
@@ -1343,43 +1347,91 @@ int dvm_state_functional(dvm_state* st, int functional, double* J) {
 // J e = -R by linearised FP32 sweeps (k_primal_lin_sweep) and adds e to delta, renormalised into fbar.
 namespace {
 
-// Buffers of the macroscopic prediction, allocated on the first predicted solve and kept with the state.
-static int predict_ensure(dvm_state* st) {
-    if (st->co_out) return DVM_OK;
+// Damping of the prediction, adapted from block to block: a correction the moment model misjudges
+// (a mode it takes as nearly free while the kinetic sweeps damp it) raises the next block's residual,
+// at once or slowly.  The damping halves after a block that grew the residual by more than 1.5x, and
+// after five predicted blocks in a row without a new best residual (a slow growth); after a block that
+// set a new best it recovers by 1.25x up to its initial value.  As it goes to 0 the sweeps are plain.
+struct PredictDamping {
+    double w0, w;
+    double r_prev = INFINITY, best = INFINITY;
+    int since_best = 0;
+    bool after_prediction = false;
+    explicit PredictDamping(double omega) : w0(omega), w(omega) {}
+    void block(double r) {
+        if (after_prediction) {
+            if (r > 1.5 * r_prev) w *= 0.5;
+            if (r < 0.98 * best) {
+                w = std::min(w0, 1.25 * w);
+                since_best = 0;
+            } else if (++since_best >= 5) {
+                w *= 0.5;
+                since_best = 0;
+            }
+        }
+        best = std::min(best, r);
+        r_prev = r;
+        after_prediction = false;
+    }
+};
+
+// Buffers of the macroscopic prediction, allocated on the first predicted solve and kept with the state
+// (the GMRES workspace grows with the Arnoldi steps asked for).
+static int predict_ensure(dvm_state* st, int m) {
     dvm_context* ctx = st->ctx;
     const size_t nc = (size_t)st->mesh->d.ncell;
     size_t acc = 0;
     int rc;
-    if ((rc = dalloc(ctx, &st->co_out, 64 * nc, &acc))) return rc;
-    if ((rc = dalloc(ctx, &st->co_dinv, 16 * nc, &acc))) return rc;
-    if ((rc = dalloc(ctx, &st->co_rW, nc, &acc))) return rc;
-    if ((rc = dalloc(ctx, &st->co_x[0], nc, &acc))) return rc;
-    if ((rc = dalloc(ctx, &st->co_x[1], nc, &acc))) return rc;
-    if (!st->Wbuf && (rc = dalloc(ctx, &st->Wbuf, 4 * nc, &acc))) return rc;
+    if (!st->co_out) {
+        if ((rc = dalloc(ctx, &st->co_out, 64 * nc, &acc))) return rc;
+        if ((rc = dalloc(ctx, &st->co_dinv, 16 * nc, &acc))) return rc;
+        if ((rc = dalloc(ctx, &st->co_rW, nc, &acc))) return rc;
+        if ((rc = dalloc(ctx, &st->co_x, nc, &acc))) return rc;
+        if (!st->Wbuf && (rc = dalloc(ctx, &st->Wbuf, 4 * nc, &acc))) return rc;
+    }
+    if (m > st->co_m) {
+        KrylovWork& K = st->co_kr;
+        const size_t old = st->co_m > 0 ? (size_t)(st->co_m + 1) * nc * sizeof(double4) + nc * sizeof(double4) +
+                                              (krylov_part_count(st->co_m) + (size_t)st->co_m * (st->co_m + 1) +
+                                               (size_t)(st->co_m + 3) + (size_t)st->co_m) * sizeof(double)
+                                        : 0;
+        dfree(K.V); dfree(K.w); dfree(K.part); dfree(K.H); dfree(K.scal); dfree(K.y);
+        K = KrylovWork();
+        st->co_m = 0;
+        st->bytes -= old;
+        ctx->bytes -= old;
+        if ((rc = dalloc(ctx, &K.V, (size_t)(m + 1) * nc, &acc)) || (rc = dalloc(ctx, &K.w, nc, &acc)) ||
+            (rc = dalloc(ctx, &K.part, krylov_part_count(m), &acc)) ||
+            (rc = dalloc(ctx, &K.H, (size_t)m * (m + 1), &acc)) || (rc = dalloc(ctx, &K.scal, (size_t)m + 3, &acc)) ||
+            (rc = dalloc(ctx, &K.y, (size_t)m, &acc))) {
+            st->bytes += acc;
+            ctx->bytes += acc;
+            return rc;
+        }
+        st->co_m = m;
+    }
     st->bytes += acc;
     ctx->bytes += acc;
     return DVM_OK;
 }
 
 // One macroscopic prediction after a block whose last sweep wrote the moments of its residual to co_rW:
-// (re)assemble the moment system at the current moments if asked, `iters` block-Jacobi iterations for dW,
+// (re)assemble the moment system at the current moments if asked, solve it for dW by GMRES (m steps),
 // the limited target moments, the Maxwellian shift of f to them, and the moments of the shifted f.
-static int predict_step(dvm_state* st, int iters, double omega, bool assemble) {
-    const DevMesh& m = st->mesh->d;
+static int predict_step(dvm_state* st, int m, double omega, bool assemble) {
+    const DevMesh& msh = st->mesh->d;
     const DevGrid& g = st->grid->d;
     cudaStream_t s = st->ctx->stream;
     const int c = st->cur;
     if (assemble) {
-        CK(launch_coarse_assemble(st->storage, m, g, st->fl, st->prim[c], st->co_out, st->co_dinv, s));
+        CK(launch_coarse_assemble(st->storage, msh, g, st->fl, st->prim[c], st->co_out, st->co_dinv, s));
         st->ctx->launches += 1;
     }
-    for (int i = 0; i < iters; ++i)
-        CK(launch_coarse_jacobi(m, st->co_out, st->co_dinv, st->co_rW, st->co_x[(i + 1) & 1], st->co_x[i & 1],
-                                i == 0, s));
-    CK(launch_coarse_target(m.ncell, st->prim[c], st->co_x[(iters - 1) & 1], omega, 0.3, st->Wbuf, s));
-    CK(launch_moment_shift(st->storage, st->f[c], m, g, st->prim[c], st->Wbuf, s));
-    CK(launch_moments(st->storage, st->f[c], m, g, st->prim[c], st->Fw[c], s));
-    st->ctx->launches += iters + 3;
+    CK(launch_coarse_gmres(msh, st->co_out, st->co_dinv, st->co_rW, false, m, st->co_kr, st->co_x, s));
+    CK(launch_coarse_target(msh.ncell, st->prim[c], st->co_x, omega, 0.3, st->Wbuf, s));
+    CK(launch_moment_shift(st->storage, st->f[c], msh, g, st->prim[c], st->Wbuf, s));
+    CK(launch_moments(st->storage, st->f[c], msh, g, st->prim[c], st->Fw[c], s));
+    st->ctx->launches += krylov_launches(m) + 3;
     st->version += 1;
     return DVM_OK;
 }
@@ -1428,9 +1480,10 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
     }
     CK(cudaMemsetAsync(W.delta, 0, nf * sizeof(float), s));
     const bool pred = o->predict_iters > 0;     // the macroscopic prediction of the correction sweeps
-    if (pred && (rc = predict_ensure(st))) return rc;
+    if (pred && (rc = predict_ensure(st, o->predict_iters))) return rc;
     const double omega = o->predict_omega > 0.0 ? o->predict_omega : 0.8;
     int predictions = 0;
+    PredictDamping damp(omega);
     const int max_steps = o->refine_max > 0 ? o->refine_max : 20;
     const int max_sweeps = o->refine_sweeps > 0 ? o->refine_sweeps : 4000;
     constexpr int kBlock = 20;             // linearised sweeps between residual checks
@@ -1503,14 +1556,13 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
             const double rin = sqrt(lo[0]);
             if (!std::isfinite(rin)) return fail(DVM_ERR_NONFINITE, "refinement correction is not finite");
             if (rin <= target) break;
+            if (pred) damp.block(rin);
             if (pred && n < max_sweeps) {
-                const int it = o->predict_iters;
-                for (int i = 0; i < it; ++i)
-                    CK(launch_coarse_jacobi(m, st->co_out, st->co_dinv, st->co_rW, st->co_x[(i + 1) & 1],
-                                            st->co_x[i & 1], i == 0, s));
-                CK(launch_coarse_lin_shift(m, g, s64->prim[c64], st->co_x[(it - 1) & 1], omega, 0.3, W.e[ec],
-                                           W.dW[ec], W.dF[ec], s));
-                ctx->launches += it + 1;
+                CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, false, o->predict_iters, st->co_kr,
+                                       st->co_x, s));
+                CK(launch_coarse_lin_shift(m, g, s64->prim[c64], st->co_x, damp.w, 0.3, W.e[ec], W.dW[ec], W.dF[ec], s));
+                ctx->launches += krylov_launches(o->predict_iters) + 1;
+                damp.after_prediction = true;
                 predictions += 1;
             }
         }
@@ -1636,13 +1688,15 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
     if (predict && (st->order != 1 || st->maxwell || st->storage == DVM_STORE_BF16))
         return fail(DVM_ERR_INVALID_ARG,
                     "the macroscopic prediction needs an FP64 or FP32 state of order 1 with the plain Maxwellian");
-    if (predict && (rc = predict_ensure(st))) return rc;
+    if (predict && (rc = predict_ensure(st, opts->predict_iters))) return rc;
     st->predict = predict;
     const int reuse = opts->predict_reuse > 0 ? opts->predict_reuse : 4;
     const double omega = opts->predict_omega > 0.0 ? opts->predict_omega : 0.8;
     int predictions = 0;
     bool predicting = predict;
     double pred_best = INFINITY;
+    int pred_high = 0;
+    PredictDamping damp(omega);
     if (accel && !wspace) {
         const size_t n = (size_t)nc * st->grid->d.nvp * 2;
         if ((rc = aa_ensure(ctx, st->aa, st->storage, n, opts->accel_depth))) return rc;
@@ -1694,16 +1748,21 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         if (predicting && st->storage != DVM_STORE_FP64) {
             // FP32 storage: near the rounding floor the residual moments are dominated by the rounding
             // of the relaxation term (V/tau times a storage ulp of f, large against transport at small Kn),
-            // which the moment solve amplifies; a residual well above the best seen shows it, and the solve
-            // finishes with plain sweeps
-            if (r > 2.0 * pred_best) {
+            // which the moment solve amplifies; residuals well above the best seen, two blocks in a row,
+            // show it, and the solve finishes with plain sweeps under a stall window of their own
+            pred_high = r > 2.0 * pred_best ? pred_high + 1 : 0;
+            if (pred_high >= 2) {
                 predicting = false;
                 st->predict = false;
+                best = r;
+                best_it = it;
             }
             pred_best = std::min(pred_best, r);
         }
+        if (predicting) damp.block(r);
         if (predicting && k == K && it < opts->max_iter) {
-            if ((rc = predict_step(st, opts->predict_iters, omega, predictions % reuse == 0))) return rc;
+            if ((rc = predict_step(st, opts->predict_iters, damp.w, predictions % reuse == 0))) return rc;
+            damp.after_prediction = true;
             predictions += 1;
         }
         if (mixing && k == K && it < opts->max_iter && wspace) {
@@ -1980,14 +2039,16 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
     const bool use_graph = graphs_ok(ctx) && K % 2 == 0;
     const double omega = opts->predict_omega > 0.0 ? opts->predict_omega : 0.8;
     if (predict) {              // the moment system at the (fixed) primal state
-        if ((rc = predict_ensure(st))) return rc;
+        if ((rc = predict_ensure(st, opts->predict_iters))) return rc;
         CK(launch_coarse_assemble(st->storage, st->mesh->d, st->grid->d, st->fl, st->prim[st->cur], st->co_out,
                                   st->co_dinv, ctx->stream));
         ctx->launches += 1;
     }
     bool predicting = predict;
     double pred_best = INFINITY;
+    int pred_high = 0;
     int predictions = 0;
+    PredictDamping damp(omega);
     if (accel) {
         const size_t n = (size_t)st->mesh->d.ncell * st->grid->d.nvp * 2;
         if ((rc = aa_ensure(ctx, ad->aa, st->storage, n, opts->accel_depth))) return rc;
@@ -2032,9 +2093,15 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
             if (mixed) CK(refresh_adjoint_couplings(ad));
         }
         if (predicting && st->storage != DVM_STORE_FP64) {     // FP32 noise floor: as in the primal solve
-            if (r > 2.0 * pred_best) predicting = false;
+            pred_high = r > 2.0 * pred_best ? pred_high + 1 : 0;
+            if (pred_high >= 2) {
+                predicting = false;
+                best = r;
+                best_it = it;
+            }
             pred_best = std::min(pred_best, r);
         }
+        if (predicting) damp.block(r);
         if (predicting && k == K && it < opts->max_iter) {
             // after a block the last sweep read phi[1 - cur] and wrote phi[cur]
             const DevMesh& m = st->mesh->d;
@@ -2042,12 +2109,11 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
             const int n = opts->predict_iters;
             CK(launch_adjoint_restrict(st->storage, m, st->grid->d, st->prim[st->cur], 1.0 / st->fl.tau_inf,
                                        ad->phi[1 - ad->cur], ad->phi[ad->cur], st->co_rW, s));
-            for (int i = 0; i < n; ++i)
-                CK(launch_coarse_jacobi_t(m, st->co_out, st->co_dinv, st->co_rW, st->co_x[(i + 1) & 1],
-                                          st->co_x[i & 1], i == 0, s));
-            CK(launch_adjoint_shift(st->storage, m, st->grid->d, st->co_x[(n - 1) & 1], omega, ad->phi[ad->cur], s));
+            CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, true, n, st->co_kr, st->co_x, s));
+            CK(launch_adjoint_shift(st->storage, m, st->grid->d, st->co_x, damp.w, ad->phi[ad->cur], s));
             CK(refresh_adjoint_couplings(ad));
-            ctx->launches += n + 2;
+            ctx->launches += krylov_launches(n) + 2;
+            damp.after_prediction = true;
             predictions += 1;
         }
     }

@@ -248,17 +248,28 @@ cudaError_t launch_moment_shift(int storage, void* f, const DevMesh& m, const De
 // with s <= 1 keeping each cell's density and temperature within a relative change cap.
 cudaError_t launch_coarse_assemble(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
                                    const double4* prim, double* out, double* dinv, cudaStream_t s);
-cudaError_t launch_coarse_jacobi(const DevMesh& m, const double* out, const double* dinv, const double4* rW,
-                                 const double4* xo, double4* xn, bool first, cudaStream_t s);
+// GMRES on the moment system (dvm_krylov.cu): x = A^{-1} (-rhs_neg), or A^{-T} with transpose, from one
+// cycle of m <= kMaxKrylov Arnoldi steps right-preconditioned by the diagonal blocks.  Device scalars only.
+constexpr int kMaxKrylov = 64;
+struct KrylovWork {
+    double4* V = nullptr;       // [(m + 1) ncell] the Arnoldi basis
+    double4* w = nullptr;       // [ncell]
+    double* part = nullptr;     // [krylov_part_count(m)] partial dot products
+    double* H = nullptr;        // [m (m + 1)] Hessenberg columns
+    double* scal = nullptr;     // [m + 3]
+    double* y = nullptr;        // [m]
+};
+size_t krylov_part_count(int m);
+int krylov_launches(int m);
+cudaError_t launch_coarse_gmres(const DevMesh& msh, const double* out, const double* dinv, const double4* rhs_neg,
+                                bool transpose, int m, const KrylovWork& K, double4* x, cudaStream_t s);
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s);
 // Prediction of the adjoint sweeps (FP64/FP32 storage): restriction of the last sweep's residual
-// D (phi_old - phi_new) with (dg/dW)^T, one transposed block-Jacobi iteration, the update phi += omega Psi . x.
+// D (phi_old - phi_new) with (dg/dW)^T, the update phi += omega Psi . x.
 cudaError_t launch_adjoint_restrict(int storage, const DevMesh& m, const DevGrid& g, const double4* prim,
                                     double inv_tau_inf, const void* phi_o, const void* phi_n, double4* rA,
                                     cudaStream_t s);
-cudaError_t launch_coarse_jacobi_t(const DevMesh& m, const double* out, const double* dinv, const double4* rA,
-                                   const double4* xo, double4* xn, bool first, cudaStream_t s);
 cudaError_t launch_adjoint_shift(int storage, const DevMesh& m, const DevGrid& g, const double4* x, double omega,
                                  void* phi, cudaStream_t s);
 // Prediction of a linear correction e (FP32): e += (dg/dW) s omega x (s <= 1 keeps the density and

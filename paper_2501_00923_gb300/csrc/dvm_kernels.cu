@@ -1708,36 +1708,6 @@ __global__ void __launch_bounds__(256, 1) k_coarse_assemble(int ncell, int nvp, 
     }
 }
 
-// One block-Jacobi iteration of the moment system: x_c = D_c^{-1} (-rW_c + sum_e OUT[nb][e'] x_nb); first:
-// from x = 0.  e' = e ^ 2 pairs faces 0/2 and 1/3 of neighbouring cells.
-__global__ void k_coarse_jacobi(int ncell, const int4* __restrict__ nb, const double* __restrict__ out,
-                                const double* __restrict__ dinv, const double4* __restrict__ rW,
-                                const double4* __restrict__ xo, double4* __restrict__ xn, int first) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const double4 b = rW[c];
-    double r[4] = {-b.x, -b.y, -b.z, -b.w};
-    if (!first) {
-        const int4 n4 = nb[c];
-        const int nbs[4] = {n4.x, n4.y, n4.z, n4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int n = nbs[e];
-            if (n < 0) continue;
-            const double* o = out + ((size_t)n * 4 + (e ^ 2)) * 16;
-            const double4 x = xo[n];
-            const double xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) r[i] += o[4 * i] * xv[0] + o[4 * i + 1] * xv[1] + o[4 * i + 2] * xv[2] + o[4 * i + 3] * xv[3];
-        }
-    }
-    const double* d = dinv + (size_t)c * 16;
-    double y[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) y[i] = d[4 * i] * r[0] + d[4 * i + 1] * r[1] + d[4 * i + 2] * r[2] + d[4 * i + 3] * r[3];
-    xn[c] = make_double4(y[0], y[1], y[2], y[3]);
-}
-
 // Target moments of the prediction: W = W(prim) + s omega dW (conserved variables, [ncell][4]), with the
 // largest s in [0, 1] (by bisection) that keeps the cell's density and temperature within a relative change
 // `cap` and positive: far from the steady state the linear correction can overshoot.
@@ -1820,37 +1790,6 @@ __global__ void __launch_bounds__(256) k_adjoint_restrict(int ncell, int nvp, co
     rA[c] = make_double4(ph0 - (ph1 * a1 + ph2 * a2) * ir + ph3 * (2.0 / 3.0) * (uu - 1.5 * T) * ir,
                          (ph1 - (2.0 / 3.0) * a1 * ph3) * ir, (ph2 - (2.0 / 3.0) * a2 * ph3) * ir,
                          (2.0 / 3.0) * ph3 * ir);
-}
-
-// One block-Jacobi iteration of the transposed moment system: lambda_c = D_c^{-T} (-rA_c + sum_e OUT[c][e]^T
-// lambda_nb(e)) (the transpose of the primal coupling -OUT[nb][e'] is the cell's own outflow block); first:
-// from lambda = 0.
-__global__ void k_coarse_jacobi_t(int ncell, const int4* __restrict__ nb, const double* __restrict__ out,
-                                  const double* __restrict__ dinv, const double4* __restrict__ rA,
-                                  const double4* __restrict__ xo, double4* __restrict__ xn, int first) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const double4 b = rA[c];
-    double r[4] = {-b.x, -b.y, -b.z, -b.w};
-    if (!first) {
-        const int4 n4 = nb[c];
-        const int nbs[4] = {n4.x, n4.y, n4.z, n4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int n = nbs[e];
-            if (n < 0) continue;
-            const double* o = out + ((size_t)c * 4 + e) * 16;
-            const double4 x = xo[n];
-            const double xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) r[i] += o[i] * xv[0] + o[4 + i] * xv[1] + o[8 + i] * xv[2] + o[12 + i] * xv[3];
-        }
-    }
-    const double* d = dinv + (size_t)c * 16;
-    double y[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) y[i] = d[i] * r[0] + d[4 + i] * r[1] + d[8 + i] * r[2] + d[12 + i] * r[3];
-    xn[c] = make_double4(y[0], y[1], y[2], y[3]);
 }
 
 // The adjoint prediction's update: phi1 += omega (l0 + l1 vx + l2 vy + l3 |v|^2/2), phi2 += omega l3 (the
@@ -3131,12 +3070,6 @@ cudaError_t launch_coarse_assemble(int storage, const DevMesh& m, const DevGrid&
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_jacobi(const DevMesh& m, const double* out, const double* dinv, const double4* rW,
-                                 const double4* xo, double4* xn, bool first, cudaStream_t s) {
-    k_coarse_jacobi<<<cdiv(m.ncell, 128), 128, 0, s>>>(m.ncell, m.nb, out, dinv, rW, xo, xn, first ? 1 : 0);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s) {
     k_coarse_target<<<cdiv(ncell, 256), 256, 0, s>>>(ncell, prim, dW, omega, cap, W);
@@ -3155,12 +3088,6 @@ cudaError_t launch_adjoint_restrict(int storage, const DevMesh& m, const DevGrid
                                                             (const float*)phi_o, (const float*)phi_n, rA);
     else
         return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_coarse_jacobi_t(const DevMesh& m, const double* out, const double* dinv, const double4* rA,
-                                   const double4* xo, double4* xn, bool first, cudaStream_t s) {
-    k_coarse_jacobi_t<<<cdiv(m.ncell, 128), 128, 0, s>>>(m.ncell, m.nb, out, dinv, rA, xo, xn, first ? 1 : 0);
     return cudaGetLastError();
 }
 
