@@ -354,7 +354,7 @@ def run_serving(args, torch, dvm):
                     f"sweeps per phase, tol 1e-5"}
     bstream = torch.cuda.Stream()
 
-    def batched(arr):
+    def batched(arr, specs=specs):
         bctx = dvm.Context(torch.cuda.current_device(), graph_iters=20, stream=bstream.cuda_stream)
         lat, span, res, stats = serve.replay_batched(bctx, specs, arr, sweeps_per_tick=20)
         o = serve.latency_stats(lat, span)
@@ -377,6 +377,11 @@ def run_serving(args, torch, dvm):
     # capacity: the same requests all submitted at t = 0, so the arrival rate does not bound solves/s
     out["saturated"] = {"arrivals": "all requests at t = 0", "batched": batched(np.zeros_like(arrivals))}
     out["saturated"]["speedup_vs_serial"] = out["saturated"]["batched"]["solves_per_s"] / out["serial_fp32"]["solves_per_s"]
+    # the same requests with the macroscopic prediction of both phases (20 GMRES steps): the small-Kn
+    # requests converge within the cap instead of stopping at it
+    pspecs = serve.trace_specs(trace, max_iter=args.serve_max_iter, tol=1e-5, predict=20)
+    out["predicted"] = {"prediction": "20 GMRES steps after every tick, primal and adjoint",
+                        "batched": batched(arrivals, pspecs), "saturated": batched(np.zeros_like(arrivals), pspecs)}
     return out
 
 

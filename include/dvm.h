@@ -412,6 +412,13 @@ typedef struct {
     uint64_t warm_key;          /* 0 -> no warm start */
     int stall_window;           /* > 0: a phase ends with DVM_ERR_STAGNATED once its residual has not
                                    fallen below 0.98 x its best for this many sweeps (as dvm_solve_opts) */
+    int predict_iters;          /* > 0 (FP64/FP32 storage): the macroscopic prediction of dvm_solve_opts after
+                                   every tick that leaves the phase running, primal and (transposed) adjoint,
+                                   with this many GMRES steps (<= 64); its residual moments come from the
+                                   tick's last sweep (input and output), its damping and FP32 noise rule are
+                                   the request's own.  The request's result then still does not depend on
+                                   the rest of the batch.  Device memory: counted in the admission footprint */
+    double predict_omega;       /* initial damping of the prediction (0 -> 0.8) */
 } dvm_request;
 
 typedef struct {
@@ -421,6 +428,7 @@ typedef struct {
     int primal_iters, adjoint_iters;
     double J, Cd, residual, adjoint_residual;
     int warm_started;
+    int predictions;            /* macroscopic predictions applied (primal + adjoint) */
 } dvm_request_result;
 
 /* Counters of a batch since creation: */

@@ -1028,6 +1028,7 @@ void dvm_state_destroy(dvm_state* st) {
     dfree(st->part);
     dfree(st->part_total);
     dfree(st->co_out); dfree(st->co_dinv); dfree(st->co_rW); dfree(st->co_x);
+    krylov_release_graphs(st->co_kr);
     dfree(st->co_kr.V); dfree(st->co_kr.w); dfree(st->co_kr.part); dfree(st->co_kr.H); dfree(st->co_kr.scal);
     dfree(st->co_kr.y);
     st->ctx->bytes -= st->bytes;
@@ -1395,6 +1396,10 @@ static int predict_ensure(dvm_state* st, int m) {
                                               (krylov_part_count(st->co_m) + (size_t)st->co_m * (st->co_m + 1) +
                                                (size_t)(st->co_m + 3) + (size_t)st->co_m) * sizeof(double)
                                         : 0;
+        if (K.graph[0] || K.graph[1]) {   // a replay may still be in flight
+            CK(cudaStreamSynchronize(ctx->stream));
+            krylov_release_graphs(K);
+        }
         dfree(K.V); dfree(K.w); dfree(K.part); dfree(K.H); dfree(K.scal); dfree(K.y);
         K = KrylovWork();
         st->co_m = 0;
@@ -1427,7 +1432,7 @@ static int predict_step(dvm_state* st, int m, double omega, bool assemble) {
         CK(launch_coarse_assemble(st->storage, msh, g, st->fl, st->prim[c], st->co_out, st->co_dinv, s));
         st->ctx->launches += 1;
     }
-    CK(launch_coarse_gmres(msh, st->co_out, st->co_dinv, st->co_rW, false, m, st->co_kr, st->co_x, s));
+    CK(launch_coarse_gmres(msh, st->co_out, st->co_dinv, st->co_rW, false, m, st->co_kr, st->co_x, graphs_ok(st->ctx), s));
     CK(launch_coarse_target(msh.ncell, st->prim[c], st->co_x, omega, 0.3, st->Wbuf, s));
     CK(launch_moment_shift(st->storage, st->f[c], msh, g, st->prim[c], st->Wbuf, s));
     CK(launch_moments(st->storage, st->f[c], msh, g, st->prim[c], st->Fw[c], s));
@@ -1559,7 +1564,7 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
             if (pred) damp.block(rin);
             if (pred && n < max_sweeps) {
                 CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, false, o->predict_iters, st->co_kr,
-                                       st->co_x, s));
+                                       st->co_x, graphs_ok(ctx), s));
                 CK(launch_coarse_lin_shift(m, g, s64->prim[c64], st->co_x, damp.w, 0.3, W.e[ec], W.dW[ec], W.dF[ec], s));
                 ctx->launches += krylov_launches(o->predict_iters) + 1;
                 damp.after_prediction = true;
@@ -2109,7 +2114,7 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
             const int n = opts->predict_iters;
             CK(launch_adjoint_restrict(st->storage, m, st->grid->d, st->prim[st->cur], 1.0 / st->fl.tau_inf,
                                        ad->phi[1 - ad->cur], ad->phi[ad->cur], st->co_rW, s));
-            CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, true, n, st->co_kr, st->co_x, s));
+            CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, true, n, st->co_kr, st->co_x, graphs_ok(ctx), s));
             CK(launch_adjoint_shift(st->storage, m, st->grid->d, st->co_x, damp.w, ad->phi[ad->cur], s));
             CK(refresh_adjoint_couplings(ad));
             ctx->launches += krylov_launches(n) + 2;
@@ -2355,6 +2360,11 @@ struct BatchReq {
     int warm = 0;
     std::vector<double> grad;
     size_t footprint = 0;
+    // macroscopic prediction of the current phase (dvm_request.predict_iters)
+    bool predicting = false;
+    int predictions = 0, phase_predictions = 0, pred_high = 0;
+    double pred_best = INFINITY;
+    PredictDamping damp{0.8};
 };
 
 struct WarmEntry {
@@ -2375,6 +2385,9 @@ size_t request_footprint(const dvm_request& r) {
     if (r.n_params > 0)
         b += 2 * nc * nvp * pair + nc * (72 + 16 * tc) + nc * 40 + (size_t)(r.nj + 1) * r.ni * 16 +
              (size_t)r.n_params * r.ni * 16;                                              // adjoint + sensitivity
+    if (r.predict_iters > 0)                                                              // the prediction's buffers
+        b += nc * 8 * (64 + 16 + 4 + 4 + 4) + nc * 32 * (size_t)(r.predict_iters + 2) +
+             8 * ((size_t)(r.predict_iters + 1) * 256 + (size_t)r.predict_iters * (r.predict_iters + 2) + 8);
     return b;
 }
 
@@ -2479,6 +2492,11 @@ int admit(dvm_batch* b, BatchReq* q) {
         q->warm = 1;
         e->stamp = ++b->stamp;
     }
+    if (r.predict_iters > 0) {
+        if ((rc = predict_ensure(q->st, r.predict_iters))) return rc;
+        q->predicting = true;
+        q->damp = PredictDamping(r.predict_omega > 0.0 ? r.predict_omega : 0.8);
+    }
     q->phase = 1;
     return DVM_OK;
 }
@@ -2517,7 +2535,61 @@ int start_adjoint(dvm_batch* b, BatchReq* q) {
             CK(refresh_adjoint_couplings(ad));
         }
     }
+    if (q->r.predict_iters > 0) {         // the transposed moment system at the converged primal state
+        dvm_state* st = q->st;
+        CK(launch_coarse_assemble(st->storage, st->mesh->d, st->grid->d, st->fl, st->prim[st->cur], st->co_out,
+                                  st->co_dinv, b->ctx->stream));
+        b->ctx->launches += 1;
+        q->predicting = true;
+        q->phase_predictions = 0;
+        q->pred_high = 0;
+        q->pred_best = INFINITY;
+        q->damp = PredictDamping(q->r.predict_omega > 0.0 ? q->r.predict_omega : 0.8);
+    }
     q->phase = 2;
+    return DVM_OK;
+}
+
+// The macroscopic prediction of a served request after a tick that leaves its phase running: the same
+// steps as a predicted dvm_primal_solve / dvm_adjoint_solve block, with the residual moments taken from
+// the tick's last sweep (input f[1 - cur], output f[cur]; phi likewise).
+int batch_predict(dvm_batch* b, BatchReq* q) {
+    dvm_context* ctx = b->ctx;
+    cudaStream_t s = ctx->stream;
+    dvm_state* st = q->st;
+    const double r = q->phase == 1 ? q->res : q->ares;
+    if (st->storage != DVM_STORE_FP64) {            // FP32 noise rule of the solves
+        q->pred_high = r > 2.0 * q->pred_best ? q->pred_high + 1 : 0;
+        if (q->pred_high >= 2) {
+            q->predicting = false;
+            q->best = r;
+            q->best_it = q->phase == 1 ? q->pit : q->ait;
+            return DVM_OK;
+        }
+        q->pred_best = std::min(q->pred_best, r);
+    }
+    q->damp.block(r);
+    const int m = q->r.predict_iters;
+    const DevMesh& msh = st->mesh->d;
+    if (q->phase == 1) {
+        const int c = st->cur;
+        CK(launch_primal_restrict(st->storage, msh, st->grid->d, st->prim[1 - c], 1.0 / st->fl.tau_inf, st->f[1 - c],
+                                  st->f[c], st->co_rW, s));
+        ctx->launches += 1;
+        int rc = predict_step(st, m, q->damp.w, q->phase_predictions % 4 == 0);
+        if (rc) return rc;
+    } else {
+        dvm_adjoint* ad = q->ad;
+        CK(launch_adjoint_restrict(st->storage, msh, st->grid->d, st->prim[st->cur], 1.0 / st->fl.tau_inf,
+                                   ad->phi[1 - ad->cur], ad->phi[ad->cur], st->co_rW, s));
+        CK(launch_coarse_gmres(msh, st->co_out, st->co_dinv, st->co_rW, true, m, st->co_kr, st->co_x, graphs_ok(ctx), s));
+        CK(launch_adjoint_shift(st->storage, msh, st->grid->d, st->co_x, q->damp.w, ad->phi[ad->cur], s));
+        CK(refresh_adjoint_couplings(ad));
+        ctx->launches += krylov_launches(m) + 3;
+    }
+    q->damp.after_prediction = true;
+    q->phase_predictions += 1;
+    q->predictions += 1;
     return DVM_OK;
 }
 
@@ -2594,6 +2666,9 @@ int dvm_batch_submit(dvm_batch* b, const dvm_request* r, uint64_t* ticket) {
     if (r->ni < 3 || r->nj < 1 || r->nv < 1 || !r->nodes_xy || !r->vx || !r->vy || !r->w)
         return fail(DVM_ERR_INVALID_ARG, "request needs a mesh and a velocity grid");
     if (r->storage < 0 || r->storage > 2 || r->max_iter < 0) return fail(DVM_ERR_INVALID_ARG, "bad request options");
+    if (r->predict_iters < 0 || r->predict_iters > kMaxKrylov || !(r->predict_omega >= 0.0 && r->predict_omega <= 1.0) ||
+        (r->predict_iters > 0 && r->storage == DVM_STORE_BF16))
+        return fail(DVM_ERR_INVALID_ARG, "predict_iters must be in [0, 64] (FP64/FP32 storage), predict_omega in [0, 1]");
     if (r->n_params > 0 && (!r->dwall_dalpha || (r->sens_mode == DVM_SENS_FULL && !r->s_j)))
         return fail(DVM_ERR_INVALID_ARG, "sensitivity needs dwall_dalpha (and s_j in full mode)");
     BatchReq* q = new (std::nothrow) BatchReq();
@@ -2845,6 +2920,13 @@ int dvm_batch_tick(dvm_batch* b, int* n_active, int* n_queued) {
                     leave = true;
                 }
             }
+            // a primal that just moved to its adjoint starts predicting after the adjoint's first tick
+            const bool moved = q->phase == 2 && q->ait == 0;
+            if (!leave && q->predicting && !moved && (rc = batch_predict(b, q))) {
+                if (q->phase == 1) q->pstatus = rc;
+                else q->astatus = rc;
+                leave = true;
+            }
             if (leave) retire(b, q);
             else keep.push_back(q);
         }
@@ -2878,6 +2960,7 @@ int dvm_batch_poll(dvm_batch* b, uint64_t ticket, dvm_request_result* out, doubl
     out->residual = q->res;
     out->adjoint_residual = q->ares;
     out->warm_started = q->warm;
+    out->predictions = q->predictions;
     if (out->done && grad_out && !q->grad.empty()) std::memcpy(grad_out, q->grad.data(), q->grad.size() * sizeof(double));
     if (out->done && forget) {
         b->all.erase(itq);

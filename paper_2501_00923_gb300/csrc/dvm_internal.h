@@ -249,7 +249,8 @@ cudaError_t launch_moment_shift(int storage, void* f, const DevMesh& m, const De
 cudaError_t launch_coarse_assemble(int storage, const DevMesh& m, const DevGrid& g, const DevFlow& fl,
                                    const double4* prim, double* out, double* dinv, cudaStream_t s);
 // GMRES on the moment system (dvm_krylov.cu): x = A^{-1} (-rhs_neg), or A^{-T} with transpose, from one
-// cycle of m <= kMaxKrylov Arnoldi steps right-preconditioned by the diagonal blocks.  Device scalars only.
+// cycle of m <= kMaxKrylov Arnoldi steps right-preconditioned by the diagonal blocks.  Device scalars only;
+// with use_graph (a created stream) the launch sequence is captured once and replayed.
 constexpr int kMaxKrylov = 64;
 struct KrylovWork {
     double4* V = nullptr;       // [(m + 1) ncell] the Arnoldi basis
@@ -258,13 +259,23 @@ struct KrylovWork {
     double* H = nullptr;        // [m (m + 1)] Hessenberg columns
     double* scal = nullptr;     // [m + 3]
     double* y = nullptr;        // [m]
+    // The launch sequence of a solve depends only on pointers and sizes, so it is captured once per
+    // (primal/adjoint) as a CUDA graph and replayed; key = the operands it was captured with.
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    const void* key[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    int key_m[2] = {0, 0};
 };
+void krylov_release_graphs(KrylovWork& K);
 size_t krylov_part_count(int m);
 int krylov_launches(int m);
 cudaError_t launch_coarse_gmres(const DevMesh& msh, const double* out, const double* dinv, const double4* rhs_neg,
-                                bool transpose, int m, const KrylovWork& K, double4* x, cudaStream_t s);
+                                bool transpose, int m, KrylovWork& K, double4* x, bool use_graph, cudaStream_t s);
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s);
+// Residual moments of a block from its last sweep's input and output (the served batch's prediction).
+cudaError_t launch_primal_restrict(int storage, const DevMesh& m, const DevGrid& g, const double4* prim_old,
+                                   double inv_tau_inf, const void* f_old, const void* f_new, double4* rW,
+                                   cudaStream_t s);
 // Prediction of the adjoint sweeps (FP64/FP32 storage): restriction of the last sweep's residual
 // D (phi_old - phi_new) with (dg/dW)^T, the update phi += omega Psi . x.
 cudaError_t launch_adjoint_restrict(int storage, const DevMesh& m, const DevGrid& g, const double4* prim,

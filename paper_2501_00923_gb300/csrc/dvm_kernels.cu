@@ -1708,6 +1708,44 @@ __global__ void __launch_bounds__(256, 1) k_coarse_assemble(int ncell, int nvp, 
     }
 }
 
+// Residual moments of a finished block from its last sweep's input and output, for paths whose sweeps do
+// not accumulate them (the served batch): rW_c = sum_k w Psi_k R_k with R = D (f_old - f_new),
+// D = V/tau(f_old) + sum_e max(-a_e, 0) as in the sweep, Psi = (1, vx, vy, |v|^2/2) on f1 and (0, 0, 0, 1)
+// on f2.  The same moments as the sweep's own (k_primal_sweep_rm), summed in another order.
+template <class TS, class TC>
+__global__ void __launch_bounds__(256) k_primal_restrict(int ncell, int nvp, const typename Vec<TC>::v4* __restrict__ vt,
+                                                         const double2* __restrict__ S, const double* __restrict__ V,
+                                                         const double4* __restrict__ prim_old, double inv_tau_inf,
+                                                         const TS* __restrict__ f_old, const TS* __restrict__ f_new,
+                                                         double4* __restrict__ rW) {
+    const int lane = threadIdx.x & 31, c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const double4 p = prim_old[c];
+    const TC Vt = (TC)(V[c] * p.x * sqrt(p.w) * inv_tau_inf);
+    TC sx[4], sy[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) { sx[e] = (TC)S[4 * c + e].x; sy[e] = (TC)S[4 * c + e].y; }
+    TC m0 = TC(0), m1 = TC(0), m2 = TC(0), m3 = TC(0);
+    for (int k = lane; k < nvp; k += 32) {
+        const auto t = vt[k];
+        const TC vx = t.x, vy = t.y, w = t.z, h = t.w;
+        TC D = Vt;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { const TC a = sx[e] * vx + sy[e] * vy; D += a < TC(0) ? -a : TC(0); }
+        const size_t o = fpos<TS>(c, nvp, k);
+        const TC R1 = D * (TC)(todbl(f_old[o]) - todbl(f_new[o]));
+        const TC R2 = D * (TC)(todbl(f_old[o + kComp<TS>]) - todbl(f_new[o + kComp<TS>]));
+        const TC wR = w * R1;
+        m0 += wR;
+        m1 = fma(wR, vx, m1);
+        m2 = fma(wR, vy, m2);
+        m3 = fma(wR, h, fma(w, R2, m3));
+    }
+    const double M0 = warp_sum((double)m0), M1 = warp_sum((double)m1), M2 = warp_sum((double)m2);
+    const double M3 = warp_sum((double)m3);
+    if (lane == 0) rW[c] = make_double4(M0, M1, M2, M3);
+}
+
 // Target moments of the prediction: W = W(prim) + s omega dW (conserved variables, [ncell][4]), with the
 // largest s in [0, 1] (by bisection) that keeps the cell's density and temperature within a relative change
 // `cap` and positive: far from the steady state the linear correction can overshoot.
@@ -3073,6 +3111,21 @@ cudaError_t launch_coarse_assemble(int storage, const DevMesh& m, const DevGrid&
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s) {
     k_coarse_target<<<cdiv(ncell, 256), 256, 0, s>>>(ncell, prim, dW, omega, cap, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primal_restrict(int storage, const DevMesh& m, const DevGrid& g, const double4* prim_old,
+                                   double inv_tau_inf, const void* f_old, const void* f_new, double4* rW,
+                                   cudaStream_t s) {
+    const int nb = cdiv(m.ncell, kWarpsPerBlock);
+    if (storage == 0)
+        k_primal_restrict<double, double><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vd, m.Sd, m.Vd, prim_old, inv_tau_inf,
+                                                             (const double*)f_old, (const double*)f_new, rW);
+    else if (storage == 1)
+        k_primal_restrict<float, float><<<nb, 256, 0, s>>>(m.ncell, g.nvp, g.vf, m.Sd, m.Vd, prim_old, inv_tau_inf,
+                                                           (const float*)f_old, (const float*)f_new, rW);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -198,9 +198,16 @@ inline int kr_cdiv(int a, int b) { return (a + b - 1) / b; }
 
 size_t krylov_part_count(int m) { return (size_t)(m + 1) * kKB; }
 
-cudaError_t launch_coarse_gmres(const DevMesh& msh, const double* out, const double* dinv, const double4* rhs_neg,
-                                bool transpose, int m, const KrylovWork& K, double4* x, cudaStream_t s) {
-    if (m < 1 || m > kMaxKrylov || !K.V || !K.w || !K.part || !K.H || !K.scal || !K.y) return cudaErrorInvalidValue;
+void krylov_release_graphs(KrylovWork& K) {
+    for (int t = 0; t < 2; ++t) {
+        if (K.graph[t]) cudaGraphExecDestroy(K.graph[t]);
+        K.graph[t] = nullptr;
+        K.key_m[t] = 0;
+    }
+}
+
+static cudaError_t enqueue_gmres(const DevMesh& msh, const double* out, const double* dinv, const double4* rhs_neg,
+                                 bool transpose, int m, const KrylovWork& K, double4* x, cudaStream_t s) {
     const int nc = msh.ncell, gb = kr_cdiv(nc, kKT), tr = transpose ? 1 : 0;
     double* nrm2 = K.scal;             // scratch: |w|^2
     double* beta = K.scal + 1;         // |b|
@@ -225,6 +232,38 @@ cudaError_t launch_coarse_gmres(const DevMesh& msh, const double* out, const dou
     k_kr_lsq<<<1, 32, 0, s>>>(m, K.H, beta, K.y);
     k_kr_combine<<<gb, kKT, 0, s>>>(nc, m, K.V, K.y, dinv, tr, x);
     return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_gmres(const DevMesh& msh, const double* out, const double* dinv, const double4* rhs_neg,
+                                bool transpose, int m, KrylovWork& K, double4* x, bool use_graph, cudaStream_t s) {
+    if (m < 1 || m > kMaxKrylov || !K.V || !K.w || !K.part || !K.H || !K.scal || !K.y) return cudaErrorInvalidValue;
+    if (!use_graph || s == nullptr) return enqueue_gmres(msh, out, dinv, rhs_neg, transpose, m, K, x, s);
+    const int t = transpose ? 1 : 0;
+    const void* key[4] = {out, dinv, rhs_neg, x};
+    bool hit = K.graph[t] && K.key_m[t] == m;
+    for (int i = 0; i < 4 && hit; ++i) hit = K.key[t][i] == key[i];
+    if (!hit) {
+        if (K.graph[t]) {                 // a replay of the old graph may still be in flight
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
+            cudaGraphExecDestroy(K.graph[t]);
+        }
+        K.graph[t] = nullptr;
+        K.key_m[t] = 0;
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t ce = enqueue_gmres(msh, out, dinv, rhs_neg, transpose, m, K, x, s);
+        e = cudaStreamEndCapture(s, &g);
+        if (ce != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(g); return ce; }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&K.graph[t], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { K.graph[t] = nullptr; return e; }
+        for (int i = 0; i < 4; ++i) K.key[t][i] = key[i];
+        K.key_m[t] = m;
+    }
+    return cudaGraphLaunch(K.graph[t], s);
 }
 
 int krylov_launches(int m) { return 6 + 10 * m; }

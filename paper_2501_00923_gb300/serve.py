@@ -32,7 +32,8 @@ class Request(C.Structure):
                 ("vx", _dp), ("vy", _dp), ("w", _dp), ("flow", dvm.Flow), ("storage", C.c_int),
                 ("tol", C.c_double), ("adjoint_tol", C.c_double), ("max_iter", C.c_int),
                 ("functional", C.c_int), ("n_params", C.c_int), ("dwall_dalpha", _dp), ("s_j", _dp),
-                ("sens_mode", C.c_int), ("warm_key", C.c_uint64), ("stall_window", C.c_int)]
+                ("sens_mode", C.c_int), ("warm_key", C.c_uint64), ("stall_window", C.c_int),
+                ("predict_iters", C.c_int), ("predict_omega", C.c_double)]
 
 
 class BatchStats(C.Structure):
@@ -43,7 +44,7 @@ class BatchStats(C.Structure):
 class RequestResult(C.Structure):
     _fields_ = [("done", C.c_int), ("status", C.c_int), ("phase", C.c_int), ("primal_iters", C.c_int),
                 ("adjoint_iters", C.c_int), ("J", C.c_double), ("Cd", C.c_double), ("residual", C.c_double),
-                ("adjoint_residual", C.c_double), ("warm_started", C.c_int)]
+                ("adjoint_residual", C.c_double), ("warm_started", C.c_int), ("predictions", C.c_int)]
 
 
 def _bind():
@@ -82,6 +83,8 @@ class SolveSpec:
     functional: str = "drag"
     warm_key: int = 0
     stall_window: int = 0
+    predict: int = 0                 # > 0: macroscopic prediction of both phases (GMRES steps)
+    predict_omega: float = 0.0
     _keep: list = field(default_factory=list, repr=False)
 
     def to_c(self) -> Request:
@@ -95,7 +98,8 @@ class SolveSpec:
                        dvm.Flow(self.flow.Kn, self.flow.Ma, self.flow.Tw, self.flow.aoa),
                        dvm.STORAGE[self.storage], self.tol, self.adjoint_tol, self.max_iter,
                        dvm.FUNCTIONAL[self.functional], P, p(dwall) if P else None, p(s) if P else None,
-                       dvm.SENS[self.sens_mode], self.warm_key, self.stall_window)
+                       dvm.SENS[self.sens_mode], self.warm_key, self.stall_window, self.predict,
+                       self.predict_omega)
 
 
 class BatchServer:
@@ -155,15 +159,16 @@ class BatchServer:
 
 
 # ----------------------------------------------------------------------------------- traces
-def trace_specs(trace, storage="fp32", max_iter=2000, tol=1e-5, warm=False):
-    """SolveSpecs of a request trace (see workloads.request_trace)."""
+def trace_specs(trace, storage="fp32", max_iter=2000, tol=1e-5, warm=False, predict=0):
+    """SolveSpecs of a request trace (see workloads.request_trace); predict > 0 asks every request for
+    the macroscopic prediction with that many GMRES steps."""
     specs = []
     for r in trace:
         mesh = W.omesh(r["ni"], r["nj"], r["alpha"])
         grid = W.velocity_grid(r["nv"], r["range"])
         specs.append(SolveSpec(mesh, grid, W.Flow(r["Kn"], r["Ma"]), storage=storage, tol=tol, adjoint_tol=tol,
                                max_iter=max_iter, warm_key=(hash((r["ni"], r["nj"], r["nv"])) & 0xffff) + 1
-                               if warm else 0))
+                               if warm else 0, predict=predict))
     return specs
 
 
@@ -245,11 +250,13 @@ def replay_serial(ctx, specs, arrivals):
             g = dvm.VGrid(ctx, s.grid.vx, s.grid.vy, s.grid.w)
             objs.append(g)
             st, pres = dvm.primal_solve(ctx, m, g, s.flow.Kn, s.flow.Ma, s.flow.Tw, s.flow.aoa, tol=s.tol,
-                                        max_iter=s.max_iter, storage=s.storage)
+                                        max_iter=s.max_iter, storage=s.storage, predict=s.predict,
+                                        predict_omega=s.predict_omega)
             objs.append(st)
             status = pres.status
             if s.sens:
-                ad, ares = dvm.adjoint_solve(ctx, st, tol=s.adjoint_tol, max_iter=s.max_iter)
+                ad, ares = dvm.adjoint_solve(ctx, st, tol=s.adjoint_tol, max_iter=s.max_iter, predict=s.predict,
+                                             predict_omega=s.predict_omega)
                 objs.append(ad)
                 dvm.sensitivity(ctx, st, ad, s.mesh.dwall, s.mesh.s, mode=s.sens_mode)
                 status = status if status != dvm.DVM_OK else ares.status

@@ -4,6 +4,8 @@ A request's result must not depend on the rest of the batch: alone, in a mix of 
 flows, and through the one-request API (same sweeps per tick as graph size) the drag and the
 gradient agree bit for bit.  Admission by HBM budget, warm starts and the iteration cap are
 checked too."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -141,3 +143,39 @@ def test_ticks_run_as_one_graph_and_reuse_device_tables(ctx):
         assert np.array_equal(a["grad"], b["grad"])
     srv2.close()
     plain.close()
+
+
+def test_predicted_requests_converge_and_do_not_depend_on_the_batch(ctx):
+    """Requests with the macroscopic prediction (FP64, Kn 0.02 and 0.05): the result is the same alone
+    and in a mix (bit for bit: the prediction runs per request on its own buffers), the solve converges
+    where the same request without prediction stops at the cap, and drag and gradient match the
+    predicted one-request API (whose residual moments come from inside its last sweep rather than from
+    the tick's last input and output) to the solve tolerance."""
+    rng = np.random.default_rng(6)
+    specs = []
+    for (ni, nj, nv, Kn, Ma) in [(32, 12, 10, 0.02, 0.8), (48, 16, 12, 0.05, 0.6)]:
+        specs.append(serve.SolveSpec(W.omesh(ni, nj, rng.uniform(-0.01, 0.01, 6)), W.velocity_grid(nv, 4.0),
+                                     W.Flow(Kn, Ma), storage="fp64", tol=1e-11, adjoint_tol=1e-11, max_iter=2000,
+                                     predict=20))
+    mixed = _run(ctx, specs)
+    for k, s in enumerate(specs):
+        alone = _run(ctx, [s])[0]
+        for key in ("J", "residual", "adjoint_residual", "primal_iters", "adjoint_iters", "status", "predictions"):
+            assert alone[key] == mixed[k][key], key
+        assert np.array_equal(alone["grad"], mixed[k]["grad"])
+        assert mixed[k]["status"] == dvm.DVM_OK and mixed[k]["predictions"] > 0
+        unpredicted = _run(ctx, [dataclasses.replace(s, predict=0)])[0]
+        assert unpredicted["status"] == dvm.DVM_NOT_CONVERGED
+        m = dvm.Mesh(ctx, s.mesh.nodes)
+        g = dvm.VGrid(ctx, s.grid.vx, s.grid.vy, s.grid.w)
+        st, res = dvm.primal_solve(ctx, m, g, s.flow.Kn, s.flow.Ma, tol=s.tol, max_iter=s.max_iter, storage="fp64",
+                                   predict=20)
+        ad, ares = dvm.adjoint_solve(ctx, st, tol=s.adjoint_tol, max_iter=s.max_iter, predict=20)
+        grad = dvm.sensitivity(ctx, st, ad, s.mesh.dwall, s.mesh.s, mode="full")
+        print(f"Kn {s.flow.Kn}: served {mixed[k]['primal_iters']} + {mixed[k]['adjoint_iters']} sweeps "
+              f"({mixed[k]['predictions']} predictions), API {res.iters} + {ares.iters}; drag difference "
+              f"{abs(res.J - mixed[k]['J']) / abs(res.J):.1e}, gradient {np.abs(grad - mixed[k]['grad']).max() / np.abs(grad).max():.1e}")
+        assert abs(res.J - mixed[k]["J"]) < 1e-7 * abs(res.J)
+        assert np.abs(grad - mixed[k]["grad"]).max() < 1e-6 * np.abs(grad).max()
+        for h in (ad, st, g, m):
+            h.close()
