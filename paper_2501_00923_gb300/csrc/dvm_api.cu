@@ -1383,12 +1383,19 @@ static int predict_ensure(dvm_state* st, int m) {
     const size_t nc = (size_t)st->mesh->d.ncell;
     size_t acc = 0;
     int rc;
-    if (!st->co_out) {
-        if ((rc = dalloc(ctx, &st->co_out, 64 * nc, &acc))) return rc;
-        if ((rc = dalloc(ctx, &st->co_dinv, 16 * nc, &acc))) return rc;
-        if ((rc = dalloc(ctx, &st->co_rW, nc, &acc))) return rc;
-        if ((rc = dalloc(ctx, &st->co_x, nc, &acc))) return rc;
-        if (!st->Wbuf && (rc = dalloc(ctx, &st->Wbuf, 4 * nc, &acc))) return rc;
+    if (!st->co_out) {                    // all or nothing: co_out marks the set as present
+        double *out = nullptr, *dinv = nullptr, *W = st->Wbuf;
+        double4 *rW = nullptr, *x = nullptr;
+        size_t a0 = 0;
+        if ((rc = dalloc(ctx, &out, 64 * nc, &a0)) || (rc = dalloc(ctx, &dinv, 16 * nc, &a0)) ||
+            (rc = dalloc(ctx, &rW, nc, &a0)) || (rc = dalloc(ctx, &x, nc, &a0)) ||
+            (!W && (rc = dalloc(ctx, &W, 4 * nc, &a0)))) {
+            dfree(out); dfree(dinv); dfree(rW); dfree(x);
+            if (W != st->Wbuf) dfree(W);
+            return rc;
+        }
+        st->co_out = out; st->co_dinv = dinv; st->co_rW = rW; st->co_x = x; st->Wbuf = W;
+        acc += a0;
     }
     if (m > st->co_m) {
         KrylovWork& K = st->co_kr;
