@@ -1,10 +1,11 @@
 """Anderson mixing of the sweeps (dvm_solve_opts.accel_depth / accel_period) only accelerates the
 iteration: the converged primal state, drag, adjoint and sensitivities are those of the plain
-point-implicit sweeps.  At Kn = 0.01 the plain sweeps converge slowly (the leading eigenvalue of
+point-implicit sweeps and of the oracle's own converged solves.  At Kn = 0.01 the plain sweeps converge slowly (the leading eigenvalue of
 the sweep map is about 0.999 on this mesh), and the mixing must cut the sweep count by at least 2."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2501_00923_gb300 import build, dvm
 from paper_2501_00923_gb300 import workloads as W
 
@@ -49,6 +50,31 @@ def test_fp64_mixing_converges_to_the_plain_solution_in_fewer_sweeps(ctx, case):
     assert abs(J1 - J0) < 1e-9 * abs(J0)
     assert np.abs(g1 - g0).max() < 1e-7 * np.abs(g0).max()
     assert ip1 < ip0 / 2 and ia1 < ia0 / 2, (ip0, ip1, ia0, ia1)
+
+
+def test_fp64_mixing_reaches_the_oracle_solution(ctx, case):
+    """The mixed FP64 solves (whole state, and the primal's cell moments) against the oracle's own
+    converged solve, adjoint and full-discrete sensitivity on the same case, not only against the
+    plain GPU sweeps.  All solves stop at relative residuals of 1e-12 to 1e-13, which leave iteration
+    errors of ~1e-9 in the drag at this Kn."""
+    mesh, grid, m, g = case
+    pr = O.Problem(mesh.nodes, grid.vx, grid.vy, grid.w, 0.01, 0.6)
+    f_ref, info = pr.primal_solve(tol=1e-13, max_sweeps=200000)
+    assert info["status"] == 0
+    phi_ref, ainfo = pr.adjoint_solve(f_ref, tol=1e-13, max_sweeps=200000)
+    assert ainfo["status"] == 0
+    J_ref = pr.functional(f_ref)
+    g_ref = pr.sens_full(f_ref, phi_ref, mesh.dnodes())
+    for accel in ((5, 10), (5, 10, "moments")):
+        st, r = dvm.primal_solve(ctx, m, g, 0.01, 0.6, tol=1e-12, max_iter=400000, storage="fp64", accel=accel)
+        ad, ar = dvm.adjoint_solve(ctx, st, tol=1e-12, max_iter=400000, accel=accel[:2])
+        assert r.status == ar.status == dvm.DVM_OK
+        grad = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
+        assert abs(r.J - J_ref) < 5e-9 * abs(J_ref), accel
+        assert np.abs(st.get() - f_ref).max() < 5e-8 * np.abs(f_ref).max(), accel
+        assert np.abs(grad - g_ref).max() < 1e-7 * np.abs(g_ref).max(), accel
+        ad.close()
+        st.close()
 
 
 def test_moment_space_mixing_reaches_the_plain_solution(ctx, case):
