@@ -58,3 +58,16 @@ def test_trace_is_seeded_and_spans_the_workload_ranges():
     assert kn.min() < -2.5 and kn.max() > 0.5
     specs = serve.trace_specs(a[:3])
     assert specs[0].mesh.nodes.shape == (a[0]["nj"] + 1, a[0]["ni"], 2)
+
+
+def test_request_marshalling_carries_the_prediction_options():
+    """SolveSpec -> dvm_request: the prediction fields land in the C struct (the layout itself is
+    checked against the library in test_abi.py), and a trace asks every request for them."""
+    a = W.request_trace(4, np.random.default_rng(W.SEED_BASE + 3))
+    specs = serve.trace_specs(a, predict=20)
+    assert all(s.predict == 20 for s in specs)
+    req = specs[0].to_c()
+    assert req.predict_iters == 20 and req.predict_omega == 0.0
+    assert req.ni == a[0]["ni"] and req.nv == a[0]["nv"] ** 2
+    plain = serve.trace_specs(a[:1])[0].to_c()
+    assert plain.predict_iters == 0
