@@ -155,6 +155,13 @@ typedef struct {
                                early (tol ~1e-5) and let the predicted refinement finish.  Memory: 88 doubles per
                                cell plus the GMRES workspace, kept with the state */
     int predict_reuse;      /* predictions between reassemblies of the moment system (0 -> 4) */
+    int predict_precond;    /* preconditioner of the prediction's GMRES: 0 = the diagonal blocks (default);
+                               1 = one multigrid V(1,1) cycle per step: the O-mesh coarsened 2x2 while both
+                               counts are even (Galerkin levels, piecewise-constant transfer), damped
+                               block-Jacobi smoothing (0.7), 30 smoothing sweeps on the coarsest level.  Its
+                               steps are nearly mesh-independent, so 2-5 steps do what 40 diagonal ones do not;
+                               an accurate solve of the moment system overcorrects as the cell Knudsen number
+                               grows (damp it, or keep the steps few).  Memory: ~4/3 x 108 doubles per cell */
     /* Adjoint solves take predict_iters and predict_omega too: the transposed coarse problem.  The
        prolongation of the moment prediction, dW -> (dg/dW) dW, and its restriction, r -> sum_k w Psi_k r_k,
        swap roles in the w-weighted product of the adjoint sweep: lambda -> Psi . lambda and

@@ -103,6 +103,7 @@ struct dvm_state {
     double4* co_x = nullptr;    // [ncell] the moment correction
     KrylovWork co_kr;           // GMRES workspace for up to co_m Arnoldi steps
     int co_m = 0;
+    MGWork co_mg;               // multigrid levels of the moment system (dvm_solve_opts.predict_precond = 1)
     int shard = 0;              // 1: a velocity shard (sweeps write partial sums; see dvm_state_set_shard)
     double* part = nullptr;     // [shard_count] this shard's partial sums
     double* part_total = nullptr;   // [shard_count] the summed buffer of all shards
@@ -699,6 +700,8 @@ int check_solve_opts(const dvm_solve_opts* o) {
         return fail(DVM_ERR_INVALID_ARG, "predict_iters must be in [0, 64], predict_reuse >= 0, predict_omega in [0, 1]");
     if (o->predict_iters > 0 && o->accel_depth > 0)
         return fail(DVM_ERR_INVALID_ARG, "the macroscopic prediction and Anderson mixing exclude each other");
+    if (o->predict_precond != 0 && o->predict_precond != 1)
+        return fail(DVM_ERR_INVALID_ARG, "predict_precond must be 0 (block-Jacobi) or 1 (multigrid)");
     return DVM_OK;
 }
 
@@ -1029,6 +1032,10 @@ void dvm_state_destroy(dvm_state* st) {
     dfree(st->part_total);
     dfree(st->co_out); dfree(st->co_dinv); dfree(st->co_rW); dfree(st->co_x);
     krylov_release_graphs(st->co_kr);
+    for (int l = 0; l < st->co_mg.nlev; ++l) {
+        MGLevel& L = st->co_mg.lev[l];
+        dfree(L.D); dfree(L.Dinv); dfree(L.C); dfree(L.x); dfree(L.b); dfree(L.r);
+    }
     dfree(st->co_kr.V); dfree(st->co_kr.w); dfree(st->co_kr.part); dfree(st->co_kr.H); dfree(st->co_kr.scal);
     dfree(st->co_kr.y);
     st->ctx->bytes -= st->bytes;
@@ -1427,19 +1434,62 @@ static int predict_ensure(dvm_state* st, int m) {
     return DVM_OK;
 }
 
+// Multigrid levels of the moment system, allocated on first use and kept with the state.
+static int mg_ensure(dvm_state* st) {
+    if (st->co_mg.nlev > 0) return DVM_OK;
+    dvm_context* ctx = st->ctx;
+    int nis[kMaxMGLevels], njs[kMaxMGLevels];
+    const int n = mg_plan(st->mesh->d.ni, st->mesh->d.nj, nis, njs);
+    MGWork W;
+    size_t acc = 0;
+    int rc = DVM_OK;
+    for (int l = 0; l < n && !rc; ++l) {
+        MGLevel& L = W.lev[l];
+        L.ni = nis[l]; L.nj = njs[l]; L.nc = nis[l] * njs[l];
+        const size_t nc = (size_t)L.nc;
+        if ((rc = dalloc(ctx, &L.D, 16 * nc, &acc)) || (rc = dalloc(ctx, &L.Dinv, 16 * nc, &acc)) ||
+            (rc = dalloc(ctx, &L.C, 64 * nc, &acc)) || (rc = dalloc(ctx, &L.x, nc, &acc)) ||
+            (rc = dalloc(ctx, &L.b, nc, &acc)) || (rc = dalloc(ctx, &L.r, nc, &acc)))
+            break;
+    }
+    if (rc) {
+        for (int l = 0; l < n; ++l) {
+            MGLevel& L = W.lev[l];
+            dfree(L.D); dfree(L.Dinv); dfree(L.C); dfree(L.x); dfree(L.b); dfree(L.r);
+        }
+        return rc;
+    }
+    W.nlev = n;
+    st->co_mg = W;
+    st->bytes += acc;
+    ctx->bytes += acc;
+    return DVM_OK;
+}
+
+// The moment system at the moments prim, and its multigrid levels when the solve uses them.
+static cudaError_t assemble_coarse(dvm_state* st, const double4* prim, bool mg) {
+    cudaStream_t s = st->ctx->stream;
+    cudaError_t e = launch_coarse_assemble(st->storage, st->mesh->d, st->grid->d, st->fl, prim, st->co_out,
+                                           st->co_dinv, s);
+    st->ctx->launches += 1;
+    if (e == cudaSuccess && mg) {
+        e = launch_mg_setup(st->mesh->d, st->co_out, st->co_dinv, st->co_mg, s);
+        st->ctx->launches += 2 * st->co_mg.nlev - 1;
+    }
+    return e;
+}
+
 // One macroscopic prediction after a block whose last sweep wrote the moments of its residual to co_rW:
 // (re)assemble the moment system at the current moments if asked, solve it for dW by GMRES (m steps),
 // the limited target moments, the Maxwellian shift of f to them, and the moments of the shifted f.
-static int predict_step(dvm_state* st, int m, double omega, bool assemble) {
+static int predict_step(dvm_state* st, int m, double omega, bool assemble, bool mg = false) {
     const DevMesh& msh = st->mesh->d;
     const DevGrid& g = st->grid->d;
     cudaStream_t s = st->ctx->stream;
     const int c = st->cur;
-    if (assemble) {
-        CK(launch_coarse_assemble(st->storage, msh, g, st->fl, st->prim[c], st->co_out, st->co_dinv, s));
-        st->ctx->launches += 1;
-    }
-    CK(launch_coarse_gmres(msh, st->co_out, st->co_dinv, st->co_rW, false, m, st->co_kr, st->co_x, graphs_ok(st->ctx), s));
+    if (assemble) CK(assemble_coarse(st, st->prim[c], mg));
+    CK(launch_coarse_gmres(msh, st->co_out, st->co_dinv, st->co_rW, false, m, st->co_kr, st->co_x, graphs_ok(st->ctx), s,
+                           mg ? &st->co_mg : nullptr));
     CK(launch_coarse_target(msh.ncell, st->prim[c], st->co_x, omega, 0.3, st->Wbuf, s));
     CK(launch_moment_shift(st->storage, st->f[c], msh, g, st->prim[c], st->Wbuf, s));
     CK(launch_moments(st->storage, st->f[c], msh, g, st->prim[c], st->Fw[c], s));
@@ -1493,6 +1543,8 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
     CK(cudaMemsetAsync(W.delta, 0, nf * sizeof(float), s));
     const bool pred = o->predict_iters > 0;     // the macroscopic prediction of the correction sweeps
     if (pred && (rc = predict_ensure(st, o->predict_iters))) return rc;
+    const bool mg = pred && o->predict_precond == 1;
+    if (mg && (rc = mg_ensure(st))) return rc;
     const double omega = o->predict_omega > 0.0 ? o->predict_omega : 0.8;
     int predictions = 0;
     PredictDamping damp(omega);
@@ -1540,8 +1592,7 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
         int ec = 0, n = 0;
         const double target = 0.1 * r64 * st->r0;
         if (pred) {         // the moment system of the correction, linearised at fbar + delta
-            CK(launch_coarse_assemble(st->storage, m, g, st->fl, s64->prim[c64], st->co_out, st->co_dinv, s));
-            ctx->launches += 1;
+            CK(assemble_coarse(st, s64->prim[c64], mg));
         }
         while (n < max_sweeps) {
             const int k = std::min(kBlock, max_sweeps - n);
@@ -1571,7 +1622,7 @@ int refine_primal(dvm_state* st, const dvm_solve_opts* o, dvm_primal_result* res
             if (pred) damp.block(rin);
             if (pred && n < max_sweeps) {
                 CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, false, o->predict_iters, st->co_kr,
-                                       st->co_x, graphs_ok(ctx), s));
+                                       st->co_x, graphs_ok(ctx), s, mg ? &st->co_mg : nullptr));
                 CK(launch_coarse_lin_shift(m, g, s64->prim[c64], st->co_x, damp.w, 0.3, W.e[ec], W.dW[ec], W.dF[ec], s));
                 ctx->launches += krylov_launches(o->predict_iters) + 1;
                 damp.after_prediction = true;
@@ -1701,6 +1752,8 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         return fail(DVM_ERR_INVALID_ARG,
                     "the macroscopic prediction needs an FP64 or FP32 state of order 1 with the plain Maxwellian");
     if (predict && (rc = predict_ensure(st, opts->predict_iters))) return rc;
+    const bool use_mg = predict && opts->predict_precond == 1;
+    if (use_mg && (rc = mg_ensure(st))) return rc;
     st->predict = predict;
     const int reuse = opts->predict_reuse > 0 ? opts->predict_reuse : 4;
     const double omega = opts->predict_omega > 0.0 ? opts->predict_omega : 0.8;
@@ -1773,7 +1826,7 @@ int dvm_primal_solve(dvm_context* ctx, const dvm_mesh* mesh, const dvm_vgrid* gr
         }
         if (predicting) damp.block(r);
         if (predicting && k == K && it < opts->max_iter) {
-            if ((rc = predict_step(st, opts->predict_iters, damp.w, predictions % reuse == 0))) return rc;
+            if ((rc = predict_step(st, opts->predict_iters, damp.w, predictions % reuse == 0, use_mg))) return rc;
             damp.after_prediction = true;
             predictions += 1;
         }
@@ -2052,9 +2105,8 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
     const double omega = opts->predict_omega > 0.0 ? opts->predict_omega : 0.8;
     if (predict) {              // the moment system at the (fixed) primal state
         if ((rc = predict_ensure(st, opts->predict_iters))) return rc;
-        CK(launch_coarse_assemble(st->storage, st->mesh->d, st->grid->d, st->fl, st->prim[st->cur], st->co_out,
-                                  st->co_dinv, ctx->stream));
-        ctx->launches += 1;
+        if (opts->predict_precond == 1 && (rc = mg_ensure(st))) return rc;
+        CK(assemble_coarse(st, st->prim[st->cur], opts->predict_precond == 1));
     }
     bool predicting = predict;
     double pred_best = INFINITY;
@@ -2121,7 +2173,8 @@ int dvm_adjoint_solve(dvm_context* ctx, dvm_state* st, int functional, const dvm
             const int n = opts->predict_iters;
             CK(launch_adjoint_restrict(st->storage, m, st->grid->d, st->prim[st->cur], 1.0 / st->fl.tau_inf,
                                        ad->phi[1 - ad->cur], ad->phi[ad->cur], st->co_rW, s));
-            CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, true, n, st->co_kr, st->co_x, graphs_ok(ctx), s));
+            CK(launch_coarse_gmres(m, st->co_out, st->co_dinv, st->co_rW, true, n, st->co_kr, st->co_x, graphs_ok(ctx), s,
+                                   opts->predict_precond == 1 ? &st->co_mg : nullptr));
             CK(launch_adjoint_shift(st->storage, m, st->grid->d, st->co_x, damp.w, ad->phi[ad->cur], s));
             CK(refresh_adjoint_couplings(ad));
             ctx->launches += krylov_launches(n) + 2;

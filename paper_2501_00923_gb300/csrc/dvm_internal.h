@@ -262,14 +262,37 @@ struct KrylovWork {
     // The launch sequence of a solve depends only on pointers and sizes, so it is captured once per
     // (primal/adjoint) as a CUDA graph and replayed; key = the operands it was captured with.
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    const void* key[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    const void* key[2][5] = {{nullptr, nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr, nullptr}};
     int key_m[2] = {0, 0};
 };
 void krylov_release_graphs(KrylovWork& K);
+// Multigrid preconditioner of the moment system (dvm_krylov.cu): levels of the structured O-mesh
+// coarsened 2x2 while both counts are even (Galerkin operators with piecewise-constant transfer),
+// per level the 4x4 blocks of the 5-point stencil: D (diagonal), C[e] (the block that multiplies the
+// neighbour across face e), D^{-1}, and three vectors.
+constexpr int kMaxMGLevels = 12;
+struct MGLevel {
+    int ni = 0, nj = 0, nc = 0;
+    double* D = nullptr;        // [16 nc]
+    double* Dinv = nullptr;     // [16 nc]
+    double* C = nullptr;        // [64 nc]
+    double4* x = nullptr;       // [nc]
+    double4* b = nullptr;
+    double4* r = nullptr;
+};
+struct MGWork {
+    int nlev = 0;
+    MGLevel lev[kMaxMGLevels];
+};
+// The level sizes for a fine ni x nj mesh (ni, nj of every level), returns the level count.
+int mg_plan(int ni, int nj, int* nis, int* njs);
+// Builds every level from the assembled outflow blocks and inverse diagonal blocks of the fine mesh.
+cudaError_t launch_mg_setup(const DevMesh& msh, const double* out, const double* dinv, const MGWork& mg, cudaStream_t s);
 size_t krylov_part_count(int m);
 int krylov_launches(int m);
 cudaError_t launch_coarse_gmres(const DevMesh& msh, const double* out, const double* dinv, const double4* rhs_neg,
-                                bool transpose, int m, KrylovWork& K, double4* x, bool use_graph, cudaStream_t s);
+                                bool transpose, int m, KrylovWork& K, double4* x, bool use_graph, cudaStream_t s,
+                                const MGWork* mg = nullptr);
 cudaError_t launch_coarse_target(int ncell, const double4* prim, const double4* dW, double omega, double cap,
                                  double* W, cudaStream_t s);
 // Residual moments of a block from its last sweep's input and output (the served batch's prediction).

@@ -39,7 +39,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("stall_window", C.c_int), ("accel_depth", C.c_int),
                 ("accel_period", C.c_int), ("accel_space", C.c_int), ("refine_tol", C.c_double),
                 ("refine_max", C.c_int), ("refine_sweeps", C.c_int), ("predict_omega", C.c_double),
-                ("predict_iters", C.c_int), ("predict_reuse", C.c_int)]
+                ("predict_iters", C.c_int), ("predict_reuse", C.c_int), ("predict_precond", C.c_int)]
 
 
 def _accel(accel):
@@ -420,14 +420,15 @@ class Adjoint:
 # ----------------------------------------------------------------------------------- calls
 def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0, tol=1e-8, max_iter=100000,
                  storage="fp32", state: State | None = None, stall_window=0, accel=None, refine_tol=0.0,
-                 refine_max=0, refine_sweeps=0, predict=0, predict_omega=0.0, predict_reuse=0):
+                 refine_max=0, refine_sweeps=0, predict=0, predict_omega=0.0, predict_reuse=0, predict_precond=0):
     """Steady solve of Eq. (numerpr_gov); warm-starts from `state` if given.  accel = (m, K) turns on
     Anderson mixing of depth m every K sweeps.  predict > 0 turns on the macroscopic prediction after every
-    block of sweeps (that many block-Jacobi iterations of the moment system).  refine_tol > 0 (FP32
+    block of sweeps (that many GMRES steps on the moment system; predict_precond = 1 preconditions them
+    with a multigrid V-cycle instead of the diagonal blocks).  refine_tol > 0 (FP32
     storage) adds mixed-precision refinement to that FP64 residual after the sweeps.  Returns (state, result)."""
     flow = Flow(Kn, Ma, Tw, aoa)
     opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), refine_tol, refine_max, refine_sweeps,
-                     predict_omega, predict, predict_reuse)
+                     predict_omega, predict, predict_reuse, predict_precond)
     h = C.c_void_p(state.h.value if state is not None else None)
     res = PrimalResult()
     st = lib().dvm_primal_solve(ctx.h, mesh.h, grid.h, C.byref(flow), C.byref(opts), STORAGE[storage],
@@ -439,10 +440,11 @@ def primal_solve(ctx: Context, mesh: Mesh, grid: VGrid, Kn, Ma, Tw=1.0, aoa=0.0,
 
 
 def adjoint_solve(ctx: Context, state: State, functional="drag", tol=1e-8, max_iter=100000,
-                  adjoint: Adjoint | None = None, stall_window=0, accel=None, predict=0, predict_omega=0.0):
+                  adjoint: Adjoint | None = None, stall_window=0, accel=None, predict=0, predict_omega=0.0,
+                  predict_precond=0):
     """Steady solve of the discrete adjoint for `functional`; accel and predict as in primal_solve (the
     prediction by the transposed moment system)."""
-    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0, predict_omega, predict, 0)
+    opts = SolveOpts(tol, max_iter, stall_window, *_accel(accel), 0.0, 0, 0, predict_omega, predict, 0, predict_precond)
     h = C.c_void_p(adjoint.h.value if adjoint is not None else None)
     res = AdjointResult()
     st = lib().dvm_adjoint_solve(ctx.h, state.h, FUNCTIONAL[functional], C.byref(opts), C.byref(h), C.byref(res))
