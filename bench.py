@@ -348,10 +348,10 @@ def run_gpu(args):
 
 def run_solve(torch, dvm, wl):
     """Time to solution on the workload, outside the timed region: the steady primal solve by FP32
-    sweeps with the macroscopic prediction (40 GMRES steps) to 1e-5 and mixed-precision refinement
-    with predicted correction sweeps to an FP64 residual of 1e-10, the FP32 adjoint with the
-    transposed prediction to 1e-6, and the full-discrete sensitivity.  Wall time of each call (each
-    ends with its result on the host).  Errors are reported in the record, not raised."""
+    sweeps with the macroscopic prediction (4 multigrid-preconditioned GMRES steps) to 1e-5 and
+    mixed-precision refinement with predicted correction sweeps to an FP64 residual of 1e-10, the FP32
+    adjoint with the transposed prediction to 1e-6, and the full-discrete sensitivity.  Wall time of
+    each call (each ends with its result on the host).  Errors are reported in the record, not raised."""
     try:
         ctx = dvm.Context(torch.cuda.current_device(), graph_iters=20)
         m = dvm.Mesh(ctx, wl.mesh.nodes)
@@ -359,12 +359,12 @@ def run_solve(torch, dvm, wl):
         fl = wl.flow
         t0 = time.perf_counter()
         st, pr = dvm.primal_solve(ctx, m, g, fl.Kn, fl.Ma, fl.Tw, fl.aoa, tol=1e-5, max_iter=200000, storage="fp32",
-                                  stall_window=1000, predict=40, refine_tol=1e-10)
+                                  stall_window=1000, predict=4, predict_precond=1, refine_tol=1e-10)
         t1 = time.perf_counter()
-        ad, ar = dvm.adjoint_solve(ctx, st, tol=1e-6, max_iter=200000, stall_window=1000, predict=40)
+        ad, ar = dvm.adjoint_solve(ctx, st, tol=1e-6, max_iter=200000, stall_window=1000, predict=4, predict_precond=1)
         grad = dvm.sensitivity(ctx, st, ad, wl.mesh.dwall, wl.mesh.s, mode="full")
         t2 = time.perf_counter()
-        out = {"method": "FP32 sweeps + macroscopic prediction (GMRES 40) to 1e-5, refinement to FP64 1e-10; "
+        out = {"method": "FP32 sweeps + macroscopic prediction (GMRES 4, multigrid) to 1e-5, refinement to FP64 1e-10; "
                          "FP32 adjoint + transposed prediction to 1e-6; full sensitivity",
                "primal_s": t1 - t0, "adjoint_and_sensitivity_s": t2 - t1,
                "primal_sweeps": pr.iters, "refinement_sweeps": pr.refine_sweeps, "refine_steps": pr.refine_steps,

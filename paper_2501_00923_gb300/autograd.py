@@ -40,8 +40,8 @@ class DragProblem:
     refine_tol: float = 0.0         # > 0 (FP32, order 1, plain): mixed-precision refinement of the primal to this
                                     # FP64 residual after the sweeps (dvm_solve_opts.refine_tol)
     predict: int = 0                # > 0 (FP64/FP32, order 1, plain): macroscopic prediction after every block of
-                                    # primal and adjoint sweeps, this many block-Jacobi iterations
-                                    # (dvm_solve_opts.predict_iters)
+                                    # primal and adjoint sweeps, this many GMRES steps (dvm_solve_opts.predict_iters)
+    predict_precond: int = 0        # 1: those steps preconditioned by a multigrid V-cycle
     last: dict = field(default_factory=dict, repr=False)
 
     def __post_init__(self):
@@ -72,7 +72,7 @@ class DragProblem:
         st, res = dvm.primal_solve(self.ctx, m, self._grid, self.flow.Kn, self.flow.Ma, self.flow.Tw,
                                    self.flow.aoa, tol=self.tol, max_iter=self.max_iter, storage=self.storage,
                                    state=st, stall_window=self.stall_window, refine_tol=self.refine_tol,
-                                   predict=self.predict if plain1 else 0)
+                                   predict=self.predict if plain1 else 0, predict_precond=self.predict_precond)
         self.last = {"mesh": mesh, "m": m, "state": st, "primal": res}
         return res.J / self.q_ref
 
@@ -83,7 +83,8 @@ class DragProblem:
             ad.copy_from(self._warm[2])
         plain1 = self.order == 1 and self.maxwellian == "plain" and self.storage != "bf16"
         ad, ares = dvm.adjoint_solve(self.ctx, st, tol=self.adjoint_tol, max_iter=self.max_iter, adjoint=ad,
-                                     stall_window=self.stall_window, predict=self.predict if plain1 else 0)
+                                     stall_window=self.stall_window, predict=self.predict if plain1 else 0,
+                                     predict_precond=self.predict_precond)
         g = dvm.sensitivity(self.ctx, st, ad, mesh.dwall, mesh.s, mode=self.mode)
         self._drop_warm()
         self._warm = (self.last["m"], st, ad)     # stays on the device as the next design's warm start
@@ -158,6 +159,8 @@ def main(argv=None):
     ap.add_argument("--predict", type=int, default=0,
                     help="> 0: macroscopic prediction of the primal sweeps (block-Jacobi iterations)")
     ap.add_argument("--adjoint-tol", type=float, default=None, help="adjoint tolerance (default: --tol)")
+    ap.add_argument("--predict-precond", type=int, default=0, choices=[0, 1],
+                    help="1: multigrid-preconditioned prediction steps")
     args = ap.parse_args(argv)
     from . import build
     build.build()
@@ -168,7 +171,7 @@ def main(argv=None):
     prob = DragProblem(ctx, wl.mesh.ni, wl.mesh.nj, wl.grid, flow, storage=args.storage, tol=args.tol,
                        adjoint_tol=args.adjoint_tol if args.adjoint_tol is not None else args.tol,
                        max_iter=args.max_sweeps, stall_window=args.stall, refine_tol=args.refine_tol,
-                       predict=args.predict)
+                       predict=args.predict, predict_precond=args.predict_precond)
     alpha = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
     t0 = time.perf_counter()
     cd = drag(alpha, prob)

@@ -26,7 +26,8 @@ from . import build, dvm
 from . import workloads as W
 
 
-def _run(ctx, m, g, mesh, Kn, Ma, storage, args, refine=0.0, accel=None, predict=0, tol=None, stall=None):
+def _run(ctx, m, g, mesh, Kn, Ma, storage, args, refine=0.0, accel=None, predict=0, tol=None, stall=None,
+         precond=0):
     asw = 0 if storage == "fp64" else args.stall
     sw = asw if stall is None else stall
     if tol is None:
@@ -34,9 +35,10 @@ def _run(ctx, m, g, mesh, Kn, Ma, storage, args, refine=0.0, accel=None, predict
     atol = args.tol64 if storage == "fp64" else args.tol
     t0 = time.time()
     st, pr = dvm.primal_solve(ctx, m, g, Kn, Ma, tol=tol, max_iter=args.max_sweeps, storage=storage, stall_window=sw,
-                              accel=accel, refine_tol=refine, predict=predict)
+                              accel=accel, refine_tol=refine, predict=predict, predict_precond=precond)
     t1 = time.time()
-    ad, ar = dvm.adjoint_solve(ctx, st, tol=atol, max_iter=args.max_sweeps, stall_window=asw, predict=predict)
+    ad, ar = dvm.adjoint_solve(ctx, st, tol=atol, max_iter=args.max_sweeps, stall_window=asw, predict=predict,
+                               predict_precond=precond)
     t2 = time.time()
     grad = dvm.sensitivity(ctx, st, ad, mesh.dwall, mesh.s, mode="full")
     out = {"J": pr.J, "Cd": pr.Cd, "primal_sweeps": pr.iters, "primal_status": dvm.status_string(pr.status),
@@ -65,6 +67,8 @@ def main(argv=None):
     ap.add_argument("--arms", default="fp32,fp32_refined,bf16", help="comma list of arms (module docstring)")
     ap.add_argument("--predict", type=int, default=0, help="> 0: block-Jacobi iterations of the prediction")
     ap.add_argument("--tol-predicted", type=float, default=1e-5, help="FP32 sweeps of the predicted arm")
+    ap.add_argument("--predict-precond", type=int, default=0, choices=[0, 1],
+                    help="preconditioner of the prediction's GMRES: 0 diagonal blocks, 1 multigrid")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     build.build()
@@ -83,7 +87,8 @@ def main(argv=None):
         res = {}
         arms = args.arms.split(",")
         if args.fp64:
-            res["fp64"] = (_run(ctx, m, g, mesh, Kn, Ma, "fp64", args, predict=args.predict) if args.predict else
+            res["fp64"] = (_run(ctx, m, g, mesh, Kn, Ma, "fp64", args, predict=args.predict,
+                                precond=args.predict_precond) if args.predict else
                            _run(ctx, m, g, mesh, Kn, Ma, "fp64", args, accel=(5, 10, "moments")))
         if "fp32" in arms:
             res["fp32"] = _run(ctx, m, g, mesh, Kn, Ma, "fp32", args)
@@ -93,7 +98,8 @@ def main(argv=None):
             if args.predict <= 0:
                 raise SystemExit("the fp32_predicted arm needs --predict > 0")
             res["fp32_predicted"] = _run(ctx, m, g, mesh, Kn, Ma, "fp32", args, refine=args.refine_tol,
-                                         predict=args.predict, tol=args.tol_predicted, stall=1000)
+                                         predict=args.predict, tol=args.tol_predicted, stall=1000,
+                                         precond=args.predict_precond)
         if "bf16" in arms:
             res["bf16"] = _run(ctx, m, g, mesh, Kn, Ma, "bf16", args)
         cmp = {}
